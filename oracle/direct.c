@@ -1,0 +1,106 @@
+/*
+ * oracle/direct.c -- TEST INFRASTRUCTURE ONLY (the oracle).
+ *
+ * Plain, slow, obviously correct FP64 direct sum of the spherical Green's
+ * function and its covariant gradient.  Only tests/, the smoke check and the
+ * benchmark's CPU-baseline leg may load this library; the solver never does.
+ * It shares no code with the CUDA path.
+ *
+ * What it computes (paper Sec. 3.1, Eq. SUM; Sec. 2.1, Eqs. GRE_FUN, ALP_PSI):
+ *
+ *   psi(x_i)   = sum_j q_j G(x_i, y_j),
+ *   G(x, y)    = (1/4pi) [ log(1 - x.y) - log 2 ]  =  (1/4pi) log(d^2 / 4),
+ *                with d^2 = |x - y|^2 = 2 (1 - x.y) for unit vectors;
+ *   alpha(x_i) = covariant gradient of psi at x_i
+ *              = sum_j q_j P_x (x - y_j) / (2 pi d_j^2),   P_x = I - x x^T,
+ *                and P_x (x - y) = (x - y) - (d^2 / 2) x.
+ *
+ * d^2 is formed from the coordinate differences, never as 2(1 - x.y): the
+ * latter cancels catastrophically for close pairs.  A pair with d^2 == 0
+ * exactly (a target on a source, in particular a point and itself) is
+ * skipped and counted; this is also how self-interaction is excluded when
+ * the targets are the sources.
+ *
+ * alpha is returned as the tangent 3-vector and/or as its components on the
+ * global basis (e_theta, e_phi) at the target, with e_theta =
+ * (cos t cos p, cos t sin p, -sin t), e_phi = (-sin p, cos p, 0) and the pole
+ * convention phi = atan2(0, 0) = 0.
+ *
+ * Every sum is Neumaier-compensated (the running sum plus a running
+ * correction); OpenMP parallelises over targets only, so the result does not
+ * depend on the thread count.
+ */
+#define _GNU_SOURCE
+#include <math.h>
+#include <omp.h>
+#include <stdint.h>
+#include <stddef.h>
+
+typedef struct { double s, c; } nsum;
+
+static inline void nadd(nsum* a, double v) {
+    double t = a->s + v;
+    if (fabs(a->s) >= fabs(v)) a->c += (a->s - t) + v;
+    else                       a->c += (v - t) + a->s;
+    a->s = t;
+}
+static inline double nval(const nsum* a) { return a->s + a->c; }
+
+/* Direct sum over all sources for targets [0, M).  Any output may be NULL.
+ * psi[M], alpha2[M][2] (e_theta, e_phi), alpha3[M][3] (tangent 3-vector).
+ * Returns the number of skipped coincident (d^2 == 0) pairs. */
+int64_t oracle_direct(const double* src, const double* q, int64_t N,
+                      const double* tgt, int64_t M,
+                      double* psi, double* alpha2, double* alpha3)
+{
+    const double inv4pi = 1.0 / (4.0 * M_PI);
+    const double inv2pi = 1.0 / (2.0 * M_PI);
+    int64_t skipped = 0;
+#pragma omp parallel for schedule(dynamic, 16) reduction(+:skipped)
+    for (int64_t i = 0; i < M; ++i) {
+        const double x0 = tgt[3 * i], x1 = tgt[3 * i + 1], x2 = tgt[3 * i + 2];
+        nsum sp = {0, 0}, g0 = {0, 0}, g1 = {0, 0}, g2 = {0, 0};
+        for (int64_t j = 0; j < N; ++j) {
+            const double e0 = x0 - src[3 * j];
+            const double e1 = x1 - src[3 * j + 1];
+            const double e2 = x2 - src[3 * j + 2];
+            const double d2 = e0 * e0 + e1 * e1 + e2 * e2;
+            if (d2 == 0.0) { ++skipped; continue; }
+            const double qj = q[j];
+            nadd(&sp, qj * inv4pi * log(0.25 * d2));
+            /* P_x (x - y) / d^2 = (x - y)/d^2 - x/2 */
+            const double w = qj * inv2pi / d2;
+            nadd(&g0, w * e0 - 0.5 * qj * inv2pi * x0);
+            nadd(&g1, w * e1 - 0.5 * qj * inv2pi * x1);
+            nadd(&g2, w * e2 - 0.5 * qj * inv2pi * x2);
+        }
+        const double a0 = nval(&g0), a1 = nval(&g1), a2 = nval(&g2);
+        if (psi) psi[i] = nval(&sp);
+        if (alpha3) { alpha3[3 * i] = a0; alpha3[3 * i + 1] = a1; alpha3[3 * i + 2] = a2; }
+        if (alpha2) {
+            const double rho = sqrt(x0 * x0 + x1 * x1);
+            double cp = 1.0, sp_ = 0.0;           /* phi = atan2(0,0) = 0 at the poles */
+            if (rho > 0.0) { cp = x0 / rho; sp_ = x1 / rho; }
+            const double ct = x2, st = rho;
+            const double eth0 = ct * cp, eth1 = ct * sp_, eth2 = -st;
+            const double eph0 = -sp_, eph1 = cp;
+            alpha2[2 * i]     = a0 * eth0 + a1 * eth1 + a2 * eth2;
+            alpha2[2 * i + 1] = a0 * eph0 + a1 * eph1;
+        }
+    }
+    return skipped;
+}
+
+/* Number of OpenMP threads the direct sum will use (for reporting). */
+int oracle_threads(void)
+{
+    int n = 1;
+#pragma omp parallel
+    {
+#pragma omp single
+        {
+            n = omp_get_num_threads();
+        }
+    }
+    return n;
+}
