@@ -44,12 +44,22 @@ def basis(P):
 
 
 def local_coords(P, X):
-    """(theta^(P), phi^(P)) of the points X [..., 3] in K_P (Sec. 3.1)."""
+    """(theta^(P), phi^(P)) of the points X [..., 3] in K_P (Sec. 3.1).
+
+    The tangent components X.e_theta(P), X.e_phi(P) are evaluated as
+    (X - P).e and, when X is closer to -P than to P, as (X + P).e: the same
+    numbers, since P is normal to e_theta(P) and e_phi(P), but without the
+    cancellation of a full dot product for points close to P or to -P."""
     e_r, e_t, e_p = basis(P)
     X = np.asarray(X, dtype=np.float64)
+    P = np.asarray(P, dtype=np.float64)
+    D = X - P
+    E = X + P
+    use_e = np.sum(E * E, axis=-1) < np.sum(D * D, axis=-1)
+    V = np.where(use_e[..., None], E, D)
     c = X @ e_r
-    a = X @ e_t
-    b = X @ e_p
+    a = V @ e_t
+    b = V @ e_p
     return np.arctan2(np.hypot(a, b), c), np.arctan2(b, a)
 
 

@@ -8,7 +8,8 @@ are the 12 base boxes (Sec. 3.4):
     itself (the self pair is excluded by the d^2 == 0 rule of the sum);
   * B_T far from B_S: B_S FMM-acts on B_T (an M2L pair);
   * neither is a leaf: split the box with the larger radius (the source only
-    if r(B_S) > r(B_T), so equal radii split the target);
+    if r(B_S) > r(B_T), so equal radii -- equal to within 1e-12 relative --
+    split the target);
   * only B_T is a leaf: split B_S;  only B_S is a leaf: split B_T;
   * both leaves: B_S direct-acts on B_T (a P2P pair).
 "Far" is MAC1 d - R_T - c_s R_S > 0 and MAC2 R_T < c_t d, where d is the
@@ -21,6 +22,11 @@ target point is dropped when target counts are given.
 import sys
 
 import numpy as np
+
+# Radii within this relative difference are taken as equal (and the target is
+# split): HEALPix boxes related by a symmetry have equal radii, whose computed
+# values differ only by rounding.
+TIE = 1e-12
 
 
 def _angle(a, b):
@@ -63,7 +69,7 @@ def walk(tree, centre, radius, c_s=2.0, c_t=0.5, tcount=None):
         if d - rt - c_s * rs > 0.0 and rt < c_t * d:
             m2l.append((s, t))
         elif not is_leaf(s) and not is_leaf(t):
-            if rs > rt:
+            if rs > rt * (1.0 + TIE):
                 for i in children(s):
                     interaction(i, t)
             else:
