@@ -1,0 +1,183 @@
+/*
+ * sfmm.h -- C ABI of the GB300 spherical Fast Multipole Method (sFMM).
+ *
+ * The solver maps N point masses q_j at unit vectors y_j on the sphere S^2 to
+ * the lensing potential and its covariant gradient (the deflection) at M
+ * target unit vectors x_i:
+ *
+ *   psi(x_i)   = sum_j q_j G(x_i, y_j),                       Sec. 3.1, Eq. SUM
+ *   G(x, y)    = (1/2pi) log sin(Theta/2)
+ *              = (1/4pi) [log(1 - x.y) - log 2],              Sec. 2.1, Eq. GRE_FUN
+ *   alpha(x_i) = covariant gradient of psi at x_i,            Sec. 2.1, Eq. ALP_PSI
+ *
+ * by the tree build of Sec. 3.1, the up-pass of Lemmas 1-2 (Sec. 3.1-3.2), the
+ * interaction lists of Algorithm 1 with the MAC of Sec. 3.4-3.5, Lemma 3
+ * (FMM-act), Lemma 4 (down-pass), the evaluation of Sec. 3.6 and the near-field
+ * direct sum.  Everything runs on one CUDA device; the library never falls back
+ * to the CPU.
+ *
+ * Conventions (apply to every entry point):
+ *  - Positions are unit vectors, xyz-interleaved float64 arrays [n][3].  They
+ *    are not renormalised.
+ *  - alpha is returned as [M][2] float64: the components on the global basis
+ *    (e_theta, e_phi) at each target, e_theta = (cos t cos p, cos t sin p,
+ *    -sin t), e_phi = (-sin p, cos p, 0), with phi = atan2(0, 0) = 0 at the
+ *    poles.
+ *  - A source-target pair at distance exactly 0 contributes nothing (so when
+ *    the targets are the sources, a point does not act on itself).
+ *  - psi is the raw sum of Eq. SUM; with zero_mean set, sum_j q_j / (4 pi) is
+ *    added, which makes the integral of psi over the sphere vanish (Eq.
+ *    STAND_CONDITION, since the integral of G is -1).
+ *  - Unless stated otherwise, array pointers are DEVICE pointers owned by the
+ *    caller; the plan owns its workspace.  Work is enqueued on the plan's
+ *    stream and the call returns after the result has been written (the entry
+ *    points synchronise the stream once per solve to size the adaptive tree
+ *    and lists).
+ *  - Errors are reported as status codes, never by exceptions or device traps;
+ *    sfmm_last_error() gives a message.  No kernel of this library waits on
+ *    another kernel or on a flag.
+ */
+#ifndef SFMM_H
+#define SFMM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sfmm_plan_s* sfmm_plan_t;
+
+typedef enum {
+    SFMM_OK = 0,
+    SFMM_EINVAL = 1,       /* an argument is out of range                        */
+    SFMM_ENOMEM = 2,       /* a device allocation failed                         */
+    SFMM_ECUDA = 3,        /* a CUDA call failed (message in sfmm_last_error)    */
+    SFMM_ETIMEOUT = 4,     /* reserved: a bounded device wait gave up            */
+    SFMM_EDEGENERATE = 5   /* reserved: degenerate input (e.g. non-finite data)  */
+} sfmm_status;
+
+enum {
+    SFMM_FP64 = 0,         /* every step in float64                                     */
+    SFMM_MIXED = 1         /* near field and M2L in reduced precision  */
+};
+
+typedef struct {
+    int leaf_size;         /* m of Sec. 3.1: split boxes holding more than m particles; 0 = default 32 */
+    double c_s;            /* MAC1 constant of Sec. 3.5 (d - R_T - c_s R_S > 0); 0 = default 2.0 */
+    double c_t;            /* MAC2 constant of Sec. 3.5 (R_T < c_t d);            0 = default 0.5 */
+    int precision;         /* SFMM_FP64 or SFMM_MIXED                                             */
+    int zero_mean;         /* 1: add sum(q)/(4 pi) to psi (Eq. STAND_CONDITION)                    */
+    int q_f32;             /* 1: the mass array is float32 instead of float64                      */
+    int64_t n_max, m_max;  /* optional: size the workspace for up to n_max sources and m_max targets
+                              at plan time (0 = grow on first use)                                  */
+    void* stream;          /* cudaStream_t to enqueue on; NULL = the legacy default stream          */
+} sfmm_options;
+
+/* Fill *opt with the defaults listed above.  Returns SFMM_EINVAL if opt is NULL. */
+sfmm_status sfmm_default_options(sfmm_options* opt);
+
+/*
+ * Create a plan (Sec. 3.7, "overview").
+ *   max_depth : deepest tree level, 0..29 (r_max of Sec. 3.1; default there 29).
+ *   order_p   : truncation order p of the expansions (Eq. MUL_ERR), 1..32; 0 = derive p from tol.
+ *   tol       : target relative error, used only when order_p == 0 (must then be in (0, 1)).
+ *   opt       : options, or NULL for the defaults.
+ * On success *out holds a new plan; release it with sfmm_destroy.
+ */
+sfmm_status sfmm_plan(sfmm_plan_t* out, int max_depth, int order_p, double tol, const sfmm_options* opt);
+
+/*
+ * Potential only (Eq. SUM).  src_xyz [N][3], q [N] (float64, or float32 when
+ * opt.q_f32), tgt_xyz [M][3] and psi [M] are device pointers; psi is
+ * overwritten.  N == 0 or M == 0 is valid (psi is zero-filled).
+ * SFMM_EINVAL if a pointer needed for a non-empty problem is NULL, N or M is
+ * negative or exceeds 2^31 - 1.
+ */
+sfmm_status sfmm_potential(sfmm_plan_t plan, const double* src_xyz, const void* q, int64_t N,
+                           const double* tgt_xyz, int64_t M, double* psi);
+
+/*
+ * Potential and deflection (Eqs. SUM and ALP_PSI).  As sfmm_potential, with
+ * alpha [M][2] (device, overwritten).  psi may be NULL, in which case the
+ * potential is not formed (the near field then needs no logarithm).
+ */
+sfmm_status sfmm_deflection(sfmm_plan_t plan, const double* src_xyz, const void* q, int64_t N,
+                            const double* tgt_xyz, int64_t M, double* psi, double* alpha);
+
+/*
+ * sfmm_deflection with HOST arrays: the inputs are copied to the plan's device
+ * workspace and the results copied back inside the call (pinned host memory
+ * gives the fastest copies; pageable memory also works).  psi may be NULL.
+ */
+sfmm_status sfmm_deflection_host(sfmm_plan_t plan, const double* src_xyz, const void* q, int64_t N,
+                                 const double* tgt_xyz, int64_t M, double* psi, double* alpha);
+
+/* Release the plan and its workspace.  NULL is ignored. */
+void sfmm_destroy(sfmm_plan_t plan);
+
+/* Message for the last failing call on this plan ("" if none).  The string
+ * is owned by the plan.  With plan == NULL, the message of the last failed
+ * sfmm_plan() call of this process. */
+const char* sfmm_last_error(sfmm_plan_t plan);
+
+/* The order p in use (resolved from tol when the plan was made with order_p == 0). */
+int sfmm_order(sfmm_plan_t plan);
+
+/*
+ * Statistics of the last solve on this plan (host struct, filled by copy).
+ *   n_nodes, n_leaves, depth : the tree of Sec. 3.1 (depth = deepest level used)
+ *   n_m2l, n_p2p             : FMM-act and direct-act pairs of Algorithm 1
+ *   p2p_interactions         : source-target point pairs evaluated directly
+ *   ms[8]                    : device time of the phases: keys+sort, tree+geometry,
+ *                              up-pass, lists, M2L, L2L, evaluation, total
+ */
+typedef struct {
+    int64_t n_nodes, n_leaves, depth, n_m2l, n_p2p, p2p_interactions;
+    double ms[8];
+} sfmm_stats;
+sfmm_status sfmm_get_stats(sfmm_plan_t plan, sfmm_stats* out);
+
+/* Record per-phase device times (CUDA events) in later solves: 1 on, 0 off (default off). */
+sfmm_status sfmm_set_timing(sfmm_plan_t plan, int on);
+
+/*
+ * Introspection for tests: copy an internal array of the last solve to HOST
+ * memory `dst` of `bytes` bytes (the exact size is returned in *bytes_needed
+ * when dst is NULL).  Arrays (node arrays are in tree order: by level, then by
+ * pixel index; particles in key order):
+ *   SFMM_ARR_SRC_KEYS      uint64 [N]      sorted order-29 nested keys of the sources
+ *   SFMM_ARR_SRC_PERM      int32  [N]      original index of each sorted source
+ *   SFMM_ARR_NODE_PREFIX   uint64 [nodes]  nested pixel index of each box at its level
+ *   SFMM_ARR_NODE_LEVEL    int32  [nodes]
+ *   SFMM_ARR_NODE_RANGE    int32  [nodes][2]  first, count in the sorted sources
+ *   SFMM_ARR_NODE_CHILD0   int32  [nodes]  first child (children are consecutive) or -1
+ *   SFMM_ARR_NODE_PARENT   int32  [nodes]  parent or -1 for a base box
+ *   SFMM_ARR_NODE_GEOM     double [nodes][11]  centre xyz, e_theta xyz, e_phi xyz, R, tan(R/2)
+ *   SFMM_ARR_MULTIPOLE     double [nodes][2p+2] C, Q, Re A_1, Im A_1, ... (unscaled, frame K_P)
+ *   SFMM_ARR_LOCAL         double [nodes][2p+2] C, Q, Re A_1, Im A_1, ... (unscaled, frame K_P)
+ *   SFMM_ARR_M2L           int32  [n_m2l][2]  (source, target) pairs grouped by target
+ *   SFMM_ARR_P2P           int32  [n_p2p][2]  (source leaf, target leaf) grouped by target
+ *   SFMM_ARR_TGT_KEYS      uint64 [M]      sorted keys of the targets
+ *   SFMM_ARR_NODE_TRANGE   int32  [nodes][2]  first, count in the sorted targets
+ */
+enum {
+    SFMM_ARR_SRC_KEYS = 0, SFMM_ARR_SRC_PERM, SFMM_ARR_NODE_PREFIX, SFMM_ARR_NODE_LEVEL,
+    SFMM_ARR_NODE_RANGE, SFMM_ARR_NODE_CHILD0, SFMM_ARR_NODE_PARENT, SFMM_ARR_NODE_GEOM,
+    SFMM_ARR_MULTIPOLE, SFMM_ARR_LOCAL, SFMM_ARR_M2L, SFMM_ARR_P2P, SFMM_ARR_TGT_KEYS,
+    SFMM_ARR_NODE_TRANGE
+};
+sfmm_status sfmm_debug_copy(sfmm_plan_t plan, int which, void* dst, int64_t bytes, int64_t* bytes_needed);
+
+/*
+ * The order-29 nested HEALPix key (Sec. 3.1; Gorski et al. 2005) of n unit
+ * vectors xyz [n][3] (device) into keys [n] (device, uint64), enqueued on
+ * `stream` (cudaStream_t or NULL).  The same routine the tree build uses.
+ */
+sfmm_status sfmm_keys(const double* xyz, int64_t n, uint64_t* keys, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SFMM_H */

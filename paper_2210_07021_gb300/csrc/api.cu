@@ -1,0 +1,538 @@
+// The C ABI of include/sfmm.h: plan management and the solve pipeline
+// (Sec. 3.7 overview): keys + sort -> tree (Sec. 3.1) -> P2M / M2M (Lemmas 1-2)
+// -> interaction lists (Algorithm 1, Sec. 3.4-3.5) -> M2L (Lemma 3) -> L2L
+// (Lemma 4) -> L2P + near field (Sec. 3.6).  Every step runs on the device.
+#include "common.cuh"
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+
+namespace sfmm {
+cudaError_t build_tree(sfmm_plan_s* P, const uint64_t* keys, int64_t n, int m, int max_depth);
+cudaError_t tree_geometry(sfmm_plan_s* P);
+cudaError_t tree_target_ranges(sfmm_plan_s* P, const uint64_t* tkeys, int64_t M);
+cudaError_t collect_leaves(sfmm_plan_s* P, const int* cnt, Buf& out, int64_t* n_out);
+cudaError_t build_lists(sfmm_plan_s* P, const TreeView& T, double c_s, double c_t);
+void fill_tables(double* h);
+cudaError_t launch_p2m(const TreeView& T, const int* leaves, int64_t n_leaves, const double4_32a* src, double* mpole, int p,
+                       cudaStream_t s);
+cudaError_t launch_m2m(const TreeView& T, int a, int b, int p, const double* tables, double* mpole, cudaStream_t s);
+cudaError_t launch_m2l(const TreeView& T, const int64_t* off, const uint32_t* srcs, int p, const double* tables,
+                       const double* mpole, double* local, cudaStream_t s);
+cudaError_t launch_l2l(const TreeView& T, int a, int b, int p, const double* tables, double* local, cudaStream_t s);
+cudaError_t launch_unscale(int n_nodes, const double* geom, const double* in, double* out, int p, int is_local,
+                           cudaStream_t s);
+cudaError_t launch_eval(const TreeView& T, const int* leaves, int64_t n_leaves, const double4_32a* src, const double4_32a* tgt,
+                        const uint32_t* tperm, const int64_t* p2p_off, const uint32_t* p2p_src, const double* local,
+                        const double* mpole, int p, int zero_mean, double* psi, double* alpha, cudaStream_t s);
+
+cudaError_t ensure(Buf& b, size_t bytes)
+{
+    if (bytes <= b.cap && b.p) return cudaSuccess;
+    if (b.p) { cudaFree(b.p); b.p = nullptr; b.cap = 0; }
+    size_t nb = bytes < 256 ? 256 : bytes;
+    cudaError_t e = cudaMalloc(&b.p, nb);
+    if (e != cudaSuccess) { b.p = nullptr; return e; }
+    b.cap = nb;
+    return cudaSuccess;
+}
+
+cudaError_t ensure_keep(Buf& b, size_t bytes, size_t keep, cudaStream_t s)
+{
+    if (bytes <= b.cap && b.p) return cudaSuccess;
+    size_t nb = bytes < 256 ? 256 : bytes;
+    void* np = nullptr;
+    cudaError_t e = cudaMalloc(&np, nb);
+    if (e != cudaSuccess) return e;
+    if (b.p && keep) {
+        e = cudaMemcpyAsync(np, b.p, keep < b.cap ? keep : b.cap, cudaMemcpyDeviceToDevice, s);
+        if (e != cudaSuccess) { cudaFree(np); return e; }
+        cudaStreamSynchronize(s);
+    }
+    if (b.p) cudaFree(b.p);
+    b.p = np;
+    b.cap = nb;
+    return cudaSuccess;
+}
+
+void release(Buf& b)
+{
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.cap = 0;
+}
+
+namespace {
+
+std::mutex g_err_mu;
+std::string g_plan_err;
+
+__global__ void k_gather_src(const double* __restrict__ xyz, const void* __restrict__ q, int q_f32,
+                             const uint32_t* __restrict__ perm, int64_t n, double4_32a* __restrict__ out)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t j = perm[i];
+        const double qq = q_f32 ? (double)static_cast<const float*>(q)[j] : static_cast<const double*>(q)[j];
+        out[i] = make_double4_32a(xyz[3 * (size_t)j], xyz[3 * (size_t)j + 1], xyz[3 * (size_t)j + 2], qq);
+    }
+}
+
+__global__ void k_gather_tgt(const double* __restrict__ xyz, const uint32_t* __restrict__ perm, int64_t n,
+                             double4_32a* __restrict__ out)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t j = perm[i];
+        out[i] = make_double4_32a(xyz[3 * (size_t)j], xyz[3 * (size_t)j + 1], xyz[3 * (size_t)j + 2], 0.0);
+    }
+}
+
+inline unsigned grid_for(int64_t n)
+{
+    int64_t b = (n + 255) / 256;
+    if (b < 1) b = 1;
+    if (b > 152 * 16) b = 152 * 16;
+    return (unsigned)b;
+}
+
+// p from a tolerance: the error of the far field falls roughly as 0.5^p under
+// the default MAC; the table is refined by measurement.
+int p_from_tol(double tol)
+{
+    int p = (int)std::ceil(std::log(tol) / std::log(0.5));
+    if (p < 4) p = 4;
+    if (p > PMAX) p = PMAX;
+    return p;
+}
+
+sfmm_status fail(sfmm_plan_s* P, sfmm_status st, const std::string& msg)
+{
+    if (P) P->err = msg;
+    return st;
+}
+
+sfmm_status cuda_fail(sfmm_plan_s* P, cudaError_t e, const char* where)
+{
+    char b[256];
+    snprintf(b, sizeof b, "CUDA error in %s: %s", where, cudaGetErrorString(e));
+    return fail(P, e == cudaErrorMemoryAllocation ? SFMM_ENOMEM : SFMM_ECUDA, b);
+}
+
+TreeView view(sfmm_plan_s* P)
+{
+    TreeView T;
+    T.n_nodes = (int)P->n_nodes;
+    T.prefix = P->n_prefix.as<uint64_t>();
+    T.level = P->n_level.as<int>();
+    T.first = P->n_first.as<int>();
+    T.count = P->n_count.as<int>();
+    T.child0 = P->n_child0.as<int>();
+    T.parent = P->n_parent.as<int>();
+    T.geom = P->n_geom.as<double>();
+    T.tfirst = P->n_tfirst.as<int>();
+    T.tcount = P->n_tcount.as<int>();
+    return T;
+}
+
+struct PhaseTimer {
+    sfmm_plan_s* P;
+    cudaEvent_t ev[8];
+    int n = 0;
+    explicit PhaseTimer(sfmm_plan_s* p) : P(p)
+    {
+        if (P->timing)
+            for (auto& e : ev) cudaEventCreate(&e);
+    }
+    void mark()
+    {
+        if (P->timing && n < 8) cudaEventRecord(ev[n++], P->stream);
+    }
+    void finish()
+    {
+        if (!P->timing) return;
+        cudaEventSynchronize(ev[n - 1]);
+        for (int i = 0; i + 1 < n && i < 7; ++i) {
+            float ms = 0;
+            cudaEventElapsedTime(&ms, ev[i], ev[i + 1]);
+            P->stats.ms[i] = ms;
+        }
+        float tot = 0;
+        cudaEventElapsedTime(&tot, ev[0], ev[n - 1]);
+        P->stats.ms[7] = tot;
+    }
+    ~PhaseTimer()
+    {
+        if (P->timing)
+            for (auto& e : ev) cudaEventDestroy(e);
+    }
+};
+
+sfmm_status solve(sfmm_plan_s* P, const double* src, const void* q, int64_t N, const double* tgt, int64_t M,
+                  double* psi, double* alpha)
+{
+    cudaStream_t s = P->stream;
+    cudaError_t e;
+    const int p = P->p;
+    P->err.clear();
+    P->stats = sfmm_stats{};
+    P->last_N = N;
+    P->last_M = M;
+    P->n_nodes = 0;
+    if (M > 0 && N == 0) {
+        if (psi && (e = cudaMemsetAsync(psi, 0, (size_t)M * 8, s))) return cuda_fail(P, e, "memset psi");
+        if (alpha && (e = cudaMemsetAsync(alpha, 0, (size_t)M * 16, s))) return cuda_fail(P, e, "memset alpha");
+        if ((e = cudaStreamSynchronize(s))) return cuda_fail(P, e, "sync");
+        return SFMM_OK;
+    }
+    if (M == 0) return SFMM_OK;
+    PhaseTimer tm(P);
+    tm.mark();
+    // ---- keys and sort (sources and targets)
+    if ((e = ensure(P->small, 64 * 8))) return cuda_fail(P, e, "alloc");
+    if ((e = ensure(P->skeys, N * 8)) || (e = ensure(P->skeys2, N * 8)) || (e = ensure(P->sperm, N * 4)) ||
+        (e = ensure(P->sperm2, N * 4)) || (e = ensure(P->src4, N * 32)))
+        return cuda_fail(P, e, "alloc sources");
+    if ((e = ensure(P->tkeys, M * 8)) || (e = ensure(P->tkeys2, M * 8)) || (e = ensure(P->tperm, M * 4)) ||
+        (e = ensure(P->tperm2, M * 4)) || (e = ensure(P->tgt4, M * 32)))
+        return cuda_fail(P, e, "alloc targets");
+    if ((e = ensure(P->tmp, radix_tmp_bytes(std::max(N, M))))) return cuda_fail(P, e, "alloc");
+    if ((e = launch_keys(src, N, P->skeys.as<uint64_t>(), P->sperm.as<uint32_t>(), s))) return cuda_fail(P, e, "keys");
+    if ((e = radix_sort(P->skeys.as<uint64_t>(), P->sperm.as<uint32_t>(), P->skeys2.as<uint64_t>(),
+                        P->sperm2.as<uint32_t>(), N, 62, P->tmp.p, s, &P->skeys_alt)))
+        return cuda_fail(P, e, "sort sources");
+    const uint64_t* skeys = P->skeys_alt ? P->skeys2.as<uint64_t>() : P->skeys.as<uint64_t>();
+    const uint32_t* sperm = P->skeys_alt ? P->sperm2.as<uint32_t>() : P->sperm.as<uint32_t>();
+    k_gather_src<<<grid_for(N), 256, 0, s>>>(src, q, P->opt.q_f32, sperm, N, P->src4.as<double4_32a>());
+    if ((e = launch_keys(tgt, M, P->tkeys.as<uint64_t>(), P->tperm.as<uint32_t>(), s))) return cuda_fail(P, e, "tkeys");
+    if ((e = radix_sort(P->tkeys.as<uint64_t>(), P->tperm.as<uint32_t>(), P->tkeys2.as<uint64_t>(),
+                        P->tperm2.as<uint32_t>(), M, 62, P->tmp.p, s, &P->tkeys_alt)))
+        return cuda_fail(P, e, "sort targets");
+    const uint64_t* tkeys = P->tkeys_alt ? P->tkeys2.as<uint64_t>() : P->tkeys.as<uint64_t>();
+    const uint32_t* tperm = P->tkeys_alt ? P->tperm2.as<uint32_t>() : P->tperm.as<uint32_t>();
+    k_gather_tgt<<<grid_for(M), 256, 0, s>>>(tgt, tperm, M, P->tgt4.as<double4_32a>());
+    if ((e = cudaGetLastError())) return cuda_fail(P, e, "gather");
+    tm.mark();
+    // ---- tree and geometry
+    if ((e = build_tree(P, skeys, N, P->opt.leaf_size, P->max_depth))) return cuda_fail(P, e, "tree");
+    const int64_t nn = P->n_nodes;
+    if ((e = tree_geometry(P))) return cuda_fail(P, e, "geometry");
+    if ((e = tree_target_ranges(P, tkeys, M))) return cuda_fail(P, e, "target ranges");
+    TreeView T = view(P);
+    if ((e = collect_leaves(P, T.count, P->leaves_src, &P->n_leaves))) return cuda_fail(P, e, "leaves");
+    if ((e = collect_leaves(P, T.tcount, P->leaves_tgt, &P->n_leaves_tgt))) return cuda_fail(P, e, "target leaves");
+    tm.mark();
+    // ---- up-pass
+    if ((e = ensure(P->mpole, (size_t)nn * EXP_STRIDE * 8)) || (e = ensure(P->local, (size_t)nn * EXP_STRIDE * 8)))
+        return cuda_fail(P, e, "alloc expansions");
+    if ((e = cudaMemsetAsync(P->mpole.p, 0, (size_t)nn * EXP_STRIDE * 8, s))) return cuda_fail(P, e, "memset");
+    if ((e = launch_p2m(T, P->leaves_src.as<int>(), P->n_leaves, P->src4.as<double4_32a>(), P->mpole.as<double>(), p, s)))
+        return cuda_fail(P, e, "P2M");
+    const int depth = (int)P->level_start.size() - 2;
+    for (int l = depth - 1; l >= 0; --l)
+        if ((e = launch_m2m(T, P->level_start[l], P->level_start[l + 1], p, P->tables.as<double>(),
+                            P->mpole.as<double>(), s)))
+            return cuda_fail(P, e, "M2M");
+    tm.mark();
+    // ---- lists
+    if ((e = build_lists(P, T, P->opt.c_s, P->opt.c_t))) return cuda_fail(P, e, "lists");
+    tm.mark();
+    // ---- M2L
+    if ((e = cudaMemsetAsync(P->local.p, 0, (size_t)nn * EXP_STRIDE * 8, s))) return cuda_fail(P, e, "memset");
+    const uint32_t* m2l_s = P->m2l_alt ? P->m2l_s2.as<uint32_t>() : P->m2l_s.as<uint32_t>();
+    if ((e = launch_m2l(T, P->m2l_off.as<int64_t>(), m2l_s, p, P->tables.as<double>(), P->mpole.as<double>(),
+                        P->local.as<double>(), s)))
+        return cuda_fail(P, e, "M2L");
+    tm.mark();
+    // ---- L2L
+    for (int l = 1; l <= depth; ++l)
+        if ((e = launch_l2l(T, P->level_start[l], P->level_start[l + 1], p, P->tables.as<double>(),
+                            P->local.as<double>(), s)))
+            return cuda_fail(P, e, "L2L");
+    tm.mark();
+    // ---- evaluation
+    const uint32_t* p2p_s = P->p2p_alt ? P->p2p_s2.as<uint32_t>() : P->p2p_s.as<uint32_t>();
+    if ((e = launch_eval(T, P->leaves_tgt.as<int>(), P->n_leaves_tgt, P->src4.as<double4_32a>(), P->tgt4.as<double4_32a>(),
+                         tperm, P->p2p_off.as<int64_t>(), p2p_s, P->local.as<double>(), P->mpole.as<double>(), p,
+                         P->opt.zero_mean, psi, alpha, s)))
+        return cuda_fail(P, e, "evaluation");
+    tm.mark();
+    if ((e = cudaStreamSynchronize(s))) return cuda_fail(P, e, "solve");
+    tm.finish();
+    P->stats.n_nodes = nn;
+    P->stats.n_leaves = P->n_leaves;
+    P->stats.depth = depth;
+    P->stats.n_m2l = P->n_m2l;
+    P->stats.n_p2p = P->n_p2p;
+    return SFMM_OK;
+}
+
+sfmm_status check_args(sfmm_plan_s* P, const double* src, const void* q, int64_t N, const double* tgt, int64_t M)
+{
+    if (!P) return SFMM_EINVAL;
+    if (N < 0 || M < 0) return fail(P, SFMM_EINVAL, "N and M must be non-negative");
+    if (N > 0x7fffffffLL || M > 0x7fffffffLL) return fail(P, SFMM_EINVAL, "N and M must be below 2^31");
+    if (N > 0 && (!src || !q)) return fail(P, SFMM_EINVAL, "src_xyz and q must be non-NULL when N > 0");
+    if (M > 0 && !tgt) return fail(P, SFMM_EINVAL, "tgt_xyz must be non-NULL when M > 0");
+    return SFMM_OK;
+}
+
+}  // namespace
+}  // namespace sfmm
+
+using namespace sfmm;
+
+extern "C" {
+
+sfmm_status sfmm_default_options(sfmm_options* opt)
+{
+    if (!opt) return SFMM_EINVAL;
+    memset(opt, 0, sizeof *opt);
+    opt->leaf_size = 32;
+    opt->c_s = 2.0;
+    opt->c_t = 0.5;
+    opt->precision = SFMM_FP64;
+    return SFMM_OK;
+}
+
+sfmm_status sfmm_plan(sfmm_plan_t* out, int max_depth, int order_p, double tol, const sfmm_options* opt)
+{
+    auto plan_fail = [](const char* m) {
+        std::lock_guard<std::mutex> g(g_err_mu);
+        g_plan_err = m;
+        return SFMM_EINVAL;
+    };
+    if (!out) return plan_fail("out is NULL");
+    *out = nullptr;
+    if (max_depth < 0 || max_depth > ORDER_MAX) return plan_fail("max_depth must be in 0..29");
+    if (order_p < 0 || order_p > PMAX) return plan_fail("order_p must be in 0..32");
+    if (order_p == 0 && !(tol > 0.0 && tol < 1.0)) return plan_fail("tol must be in (0, 1) when order_p == 0");
+    sfmm_options o;
+    sfmm_default_options(&o);
+    if (opt) {
+        o = *opt;
+        if (o.leaf_size == 0) o.leaf_size = 32;
+        if (o.c_s == 0.0) o.c_s = 2.0;
+        if (o.c_t == 0.0) o.c_t = 0.5;
+    }
+    if (o.leaf_size < 1) return plan_fail("leaf_size must be >= 1");
+    if (!(o.c_s > 1.0)) return plan_fail("c_s must be > 1 (Sec. 3.5)");
+    if (!(o.c_t > 0.0 && o.c_t < 1.0)) return plan_fail("c_t must be in (0, 1) (Sec. 3.5)");
+    if (o.precision != SFMM_FP64 && o.precision != SFMM_MIXED) return plan_fail("unknown precision");
+    if (o.precision == SFMM_MIXED) return plan_fail("SFMM_MIXED is not available in this build");
+    if (o.n_max < 0 || o.m_max < 0) return plan_fail("n_max and m_max must be >= 0");
+    auto* P = new (std::nothrow) sfmm_plan_s();
+    if (!P) return SFMM_ENOMEM;
+    P->max_depth = max_depth;
+    P->p = order_p ? order_p : p_from_tol(tol);
+    P->tol = tol;
+    P->opt = o;
+    P->stream = static_cast<cudaStream_t>(o.stream);
+    std::vector<double> h(2 * PMAX * PMAX);
+    fill_tables(h.data());
+    cudaError_t e;
+    if ((e = ensure(P->tables, h.size() * 8)) ||
+        (e = cudaMemcpy(P->tables.p, h.data(), h.size() * 8, cudaMemcpyHostToDevice))) {
+        std::lock_guard<std::mutex> g(g_err_mu);
+        g_plan_err = std::string("CUDA error at plan time: ") + cudaGetErrorString(e);
+        delete P;
+        return e == cudaErrorMemoryAllocation ? SFMM_ENOMEM : SFMM_ECUDA;
+    }
+    if (o.n_max > 0 || o.m_max > 0) {
+        const int64_t N = o.n_max, M = o.m_max;
+        if ((e = ensure(P->skeys, N * 8)) || (e = ensure(P->skeys2, N * 8)) || (e = ensure(P->sperm, N * 4)) ||
+            (e = ensure(P->sperm2, N * 4)) || (e = ensure(P->src4, N * 32)) || (e = ensure(P->tkeys, M * 8)) ||
+            (e = ensure(P->tkeys2, M * 8)) || (e = ensure(P->tperm, M * 4)) || (e = ensure(P->tperm2, M * 4)) ||
+            (e = ensure(P->tgt4, M * 32)) || (e = ensure(P->tmp, radix_tmp_bytes(std::max(N, M))))) {
+            std::lock_guard<std::mutex> g(g_err_mu);
+            g_plan_err = std::string("workspace allocation failed: ") + cudaGetErrorString(e);
+            sfmm_destroy(P);
+            return SFMM_ENOMEM;
+        }
+    }
+    *out = P;
+    return SFMM_OK;
+}
+
+sfmm_status sfmm_potential(sfmm_plan_t plan, const double* src_xyz, const void* q, int64_t N, const double* tgt_xyz,
+                           int64_t M, double* psi)
+{
+    sfmm_status st = check_args(plan, src_xyz, q, N, tgt_xyz, M);
+    if (st != SFMM_OK) return st;
+    if (M > 0 && !psi) return fail(plan, SFMM_EINVAL, "psi must be non-NULL");
+    return solve(plan, src_xyz, q, N, tgt_xyz, M, psi, nullptr);
+}
+
+sfmm_status sfmm_deflection(sfmm_plan_t plan, const double* src_xyz, const void* q, int64_t N, const double* tgt_xyz,
+                            int64_t M, double* psi, double* alpha)
+{
+    sfmm_status st = check_args(plan, src_xyz, q, N, tgt_xyz, M);
+    if (st != SFMM_OK) return st;
+    if (M > 0 && !alpha) return fail(plan, SFMM_EINVAL, "alpha must be non-NULL");
+    return solve(plan, src_xyz, q, N, tgt_xyz, M, psi, alpha);
+}
+
+sfmm_status sfmm_deflection_host(sfmm_plan_t plan, const double* src_xyz, const void* q, int64_t N,
+                                 const double* tgt_xyz, int64_t M, double* psi, double* alpha)
+{
+    sfmm_status st = check_args(plan, src_xyz, q, N, tgt_xyz, M);
+    if (st != SFMM_OK) return st;
+    if (M > 0 && !alpha) return fail(plan, SFMM_EINVAL, "alpha must be non-NULL");
+    sfmm_plan_s* P = plan;
+    cudaStream_t s = P->stream;
+    cudaError_t e;
+    const size_t qb = P->opt.q_f32 ? 4 : 8;
+    if ((e = ensure(P->h_src, std::max<int64_t>(N, 1) * 24)) || (e = ensure(P->h_q, std::max<int64_t>(N, 1) * qb)) ||
+        (e = ensure(P->h_tgt, std::max<int64_t>(M, 1) * 24)) || (e = ensure(P->h_alpha, std::max<int64_t>(M, 1) * 16)) ||
+        (psi && (e = ensure(P->h_psi, std::max<int64_t>(M, 1) * 8))))
+        return cuda_fail(P, e, "alloc staging");
+    if (N > 0 && ((e = cudaMemcpyAsync(P->h_src.p, src_xyz, N * 24, cudaMemcpyHostToDevice, s)) ||
+                  (e = cudaMemcpyAsync(P->h_q.p, q, N * qb, cudaMemcpyHostToDevice, s))))
+        return cuda_fail(P, e, "copy inputs");
+    if (M > 0 && (e = cudaMemcpyAsync(P->h_tgt.p, tgt_xyz, M * 24, cudaMemcpyHostToDevice, s)))
+        return cuda_fail(P, e, "copy targets");
+    st = solve(P, P->h_src.as<double>(), P->h_q.p, N, P->h_tgt.as<double>(), M, psi ? P->h_psi.as<double>() : nullptr,
+               P->h_alpha.as<double>());
+    if (st != SFMM_OK) return st;
+    if (M > 0) {
+        if ((e = cudaMemcpyAsync(alpha, P->h_alpha.p, M * 16, cudaMemcpyDeviceToHost, s)))
+            return cuda_fail(P, e, "copy alpha");
+        if (psi && (e = cudaMemcpyAsync(psi, P->h_psi.p, M * 8, cudaMemcpyDeviceToHost, s)))
+            return cuda_fail(P, e, "copy psi");
+        if ((e = cudaStreamSynchronize(s))) return cuda_fail(P, e, "sync");
+    }
+    return SFMM_OK;
+}
+
+void sfmm_destroy(sfmm_plan_t plan)
+{
+    if (!plan) return;
+    Buf* all[] = {&plan->skeys, &plan->skeys2, &plan->sperm, &plan->sperm2, &plan->src4, &plan->tkeys, &plan->tkeys2,
+                  &plan->tperm, &plan->tperm2, &plan->tgt4, &plan->h_src, &plan->h_q, &plan->h_tgt, &plan->h_psi,
+                  &plan->h_alpha, &plan->tmp, &plan->flags, &plan->pos, &plan->small, &plan->n_prefix,
+                  &plan->n_level, &plan->n_first, &plan->n_count, &plan->n_child0, &plan->n_parent, &plan->n_geom,
+                  &plan->n_tfirst, &plan->n_tcount, &plan->mpole, &plan->local, &plan->tables, &plan->fa, &plan->fb,
+                  &plan->act, &plan->c_next, &plan->c_m2l, &plan->c_p2p, &plan->o_next, &plan->o_m2l, &plan->o_p2p,
+                  &plan->m2l_t, &plan->m2l_s, &plan->m2l_t2, &plan->m2l_s2, &plan->p2p_t, &plan->p2p_s,
+                  &plan->p2p_t2, &plan->p2p_s2, &plan->m2l_off, &plan->p2p_off, &plan->leaves_src,
+                  &plan->leaves_tgt};
+    for (Buf* b : all) release(*b);
+    delete plan;
+}
+
+const char* sfmm_last_error(sfmm_plan_t plan)
+{
+    if (!plan) {
+        std::lock_guard<std::mutex> g(g_err_mu);
+        return g_plan_err.c_str();
+    }
+    return plan->err.c_str();
+}
+
+int sfmm_order(sfmm_plan_t plan) { return plan ? plan->p : 0; }
+
+sfmm_status sfmm_get_stats(sfmm_plan_t plan, sfmm_stats* out)
+{
+    if (!plan || !out) return SFMM_EINVAL;
+    *out = plan->stats;
+    return SFMM_OK;
+}
+
+sfmm_status sfmm_set_timing(sfmm_plan_t plan, int on)
+{
+    if (!plan) return SFMM_EINVAL;
+    plan->timing = on != 0;
+    return SFMM_OK;
+}
+
+sfmm_status sfmm_debug_copy(sfmm_plan_t plan, int which, void* dst, int64_t bytes, int64_t* bytes_needed)
+{
+    if (!plan) return SFMM_EINVAL;
+    sfmm_plan_s* P = plan;
+    const int64_t N = P->last_N, M = P->last_M, nn = P->n_nodes;
+    const int p = P->p;
+    const void* srcp = nullptr;
+    int64_t need = 0;
+    Buf tmpbuf;
+    switch (which) {
+    case SFMM_ARR_SRC_KEYS: srcp = P->skeys_alt ? P->skeys2.p : P->skeys.p; need = N * 8; break;
+    case SFMM_ARR_SRC_PERM: srcp = P->skeys_alt ? P->sperm2.p : P->sperm.p; need = N * 4; break;
+    case SFMM_ARR_TGT_KEYS: srcp = P->tkeys_alt ? P->tkeys2.p : P->tkeys.p; need = M * 8; break;
+    case SFMM_ARR_NODE_PREFIX: srcp = P->n_prefix.p; need = nn * 8; break;
+    case SFMM_ARR_NODE_LEVEL: srcp = P->n_level.p; need = nn * 4; break;
+    case SFMM_ARR_NODE_CHILD0: srcp = P->n_child0.p; need = nn * 4; break;
+    case SFMM_ARR_NODE_PARENT: srcp = P->n_parent.p; need = nn * 4; break;
+    case SFMM_ARR_NODE_GEOM: need = nn * 11 * 8; break;
+    case SFMM_ARR_NODE_RANGE: need = nn * 8; break;
+    case SFMM_ARR_NODE_TRANGE: need = nn * 8; break;
+    case SFMM_ARR_MULTIPOLE: case SFMM_ARR_LOCAL: need = nn * (2 * p + 2) * 8; break;
+    case SFMM_ARR_M2L: need = P->n_m2l * 8; break;
+    case SFMM_ARR_P2P: need = P->n_p2p * 8; break;
+    default: return fail(P, SFMM_EINVAL, "unknown array");
+    }
+    if (bytes_needed) *bytes_needed = need;
+    if (!dst) return SFMM_OK;
+    if (bytes < need) return fail(P, SFMM_EINVAL, "destination too small");
+    if (need == 0) return SFMM_OK;
+    cudaError_t e = cudaStreamSynchronize(P->stream);
+    if (e) return cuda_fail(P, e, "sync");
+    if (srcp) {
+        e = cudaMemcpy(dst, srcp, need, cudaMemcpyDeviceToHost);
+        return e ? cuda_fail(P, e, "copy") : SFMM_OK;
+    }
+    std::vector<char> h;
+    char* d = static_cast<char*>(dst);
+    if (which == SFMM_ARR_NODE_GEOM) {
+        std::vector<double> g((size_t)nn * GEOM_STRIDE);
+        if ((e = cudaMemcpy(g.data(), P->n_geom.p, g.size() * 8, cudaMemcpyDeviceToHost))) return cuda_fail(P, e, "copy");
+        double* o = reinterpret_cast<double*>(d);
+        for (int64_t i = 0; i < nn; ++i)
+            for (int k = 0; k < 11; ++k) o[i * 11 + k] = g[i * GEOM_STRIDE + k];
+        return SFMM_OK;
+    }
+    if (which == SFMM_ARR_NODE_RANGE || which == SFMM_ARR_NODE_TRANGE) {
+        std::vector<int> a(nn), b(nn);
+        const Buf& fa = which == SFMM_ARR_NODE_RANGE ? P->n_first : P->n_tfirst;
+        const Buf& fb = which == SFMM_ARR_NODE_RANGE ? P->n_count : P->n_tcount;
+        if ((e = cudaMemcpy(a.data(), fa.p, nn * 4, cudaMemcpyDeviceToHost)) ||
+            (e = cudaMemcpy(b.data(), fb.p, nn * 4, cudaMemcpyDeviceToHost)))
+            return cuda_fail(P, e, "copy");
+        int* o = reinterpret_cast<int*>(d);
+        for (int64_t i = 0; i < nn; ++i) { o[2 * i] = a[i]; o[2 * i + 1] = b[i]; }
+        return SFMM_OK;
+    }
+    if (which == SFMM_ARR_MULTIPOLE || which == SFMM_ARR_LOCAL) {
+        if ((e = ensure(tmpbuf, need))) return cuda_fail(P, e, "alloc");
+        const Buf& in = which == SFMM_ARR_MULTIPOLE ? P->mpole : P->local;
+        if ((e = launch_unscale((int)nn, P->n_geom.as<double>(), in.as<double>(), tmpbuf.as<double>(), p,
+                                which == SFMM_ARR_LOCAL, P->stream)) ||
+            (e = cudaStreamSynchronize(P->stream)) || (e = cudaMemcpy(dst, tmpbuf.p, need, cudaMemcpyDeviceToHost))) {
+            release(tmpbuf);
+            return cuda_fail(P, e, "unscale");
+        }
+        release(tmpbuf);
+        return SFMM_OK;
+    }
+    // lists: (source, target) pairs grouped by target
+    const int64_t np = which == SFMM_ARR_M2L ? P->n_m2l : P->n_p2p;
+    const bool alt = which == SFMM_ARR_M2L ? P->m2l_alt : P->p2p_alt;
+    const Buf& bt = which == SFMM_ARR_M2L ? (alt ? P->m2l_t2 : P->m2l_t) : (alt ? P->p2p_t2 : P->p2p_t);
+    const Buf& bs = which == SFMM_ARR_M2L ? (alt ? P->m2l_s2 : P->m2l_s) : (alt ? P->p2p_s2 : P->p2p_s);
+    std::vector<uint64_t> t(np);
+    std::vector<uint32_t> sv(np);
+    if ((e = cudaMemcpy(t.data(), bt.p, np * 8, cudaMemcpyDeviceToHost)) ||
+        (e = cudaMemcpy(sv.data(), bs.p, np * 4, cudaMemcpyDeviceToHost)))
+        return cuda_fail(P, e, "copy");
+    int* o = reinterpret_cast<int*>(d);
+    for (int64_t i = 0; i < np; ++i) { o[2 * i] = (int)sv[i]; o[2 * i + 1] = (int)t[i]; }
+    return SFMM_OK;
+}
+
+sfmm_status sfmm_keys(const double* xyz, int64_t n, uint64_t* keys, void* stream)
+{
+    if (n < 0 || (n > 0 && (!xyz || !keys))) return SFMM_EINVAL;
+    cudaError_t e = launch_keys(xyz, n, keys, nullptr, static_cast<cudaStream_t>(stream));
+    return e ? SFMM_ECUDA : SFMM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,109 @@
+// Internal declarations shared by the CUDA translation units of libsfmm.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstddef>
+#include <string>
+#include <vector>
+
+#include "../../include/sfmm.h"
+
+namespace sfmm {
+
+constexpr int ORDER_MAX = 29;          // r_max of Sec. 3.1
+constexpr int PMAX = 32;               // largest truncation order (one coefficient per lane)
+constexpr int EXP_STRIDE = 2 * PMAX + 2;   // doubles per expansion: C, Q, (Re, Im) A_1..A_PMAX
+constexpr int GEOM_STRIDE = 12;        // centre(3) e_theta(3) e_phi(3) R r pad
+constexpr unsigned FULL = 0xffffffffu;
+
+// ------------------------------------------------------------------ complex
+struct cd { double x, y; };
+__host__ __device__ __forceinline__ cd mk(double x, double y) { cd r; r.x = x; r.y = y; return r; }
+__host__ __device__ __forceinline__ cd cadd(cd a, cd b) { return mk(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ cd csub(cd a, cd b) { return mk(a.x - b.x, a.y - b.y); }
+__host__ __device__ __forceinline__ cd cmul(cd a, cd b) { return mk(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+__host__ __device__ __forceinline__ cd cscale(cd a, double s) { return mk(a.x * s, a.y * s); }
+__host__ __device__ __forceinline__ cd cconj(cd a) { return mk(a.x, -a.y); }
+
+// ------------------------------------------------------------ device buffers
+struct Buf {
+    void* p = nullptr;
+    size_t cap = 0;
+    template <typename T> T* as() const { return static_cast<T*>(p); }
+};
+// Grow b to at least `bytes` (contents dropped).  Returns cudaSuccess or the error.
+cudaError_t ensure(Buf& b, size_t bytes);
+// Grow b to at least `bytes`, keeping the first `keep` bytes (copied on `s`).
+cudaError_t ensure_keep(Buf& b, size_t bytes, size_t keep, cudaStream_t s);
+void release(Buf& b);
+
+// ------------------------------------------------------------------- scans
+// Exclusive prefix sums on the device.  `tmp` must hold scan_tmp_bytes(n)
+// bytes; if `total` is non-null the sum of all n inputs is written there.
+size_t scan_tmp_bytes(int64_t n);
+cudaError_t exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, int64_t* total, void* tmp, cudaStream_t s);
+cudaError_t exclusive_scan_u32(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* total, void* tmp, cudaStream_t s);
+
+// ------------------------------------------------------------- radix sort
+// Stable LSD radix sort of (key, value) by the low `bits` bits of the key.
+// The sorted data ends in (k1, v1) if *in_alt is false, else in (k2, v2).
+size_t radix_tmp_bytes(int64_t n);
+cudaError_t radix_sort(uint64_t* k1, uint32_t* v1, uint64_t* k2, uint32_t* v2, int64_t n, int bits,
+                       void* tmp, cudaStream_t s, bool* in_alt);
+
+// ------------------------------------------------------------------- keys
+cudaError_t launch_keys(const double* xyz, int64_t n, uint64_t* keys, uint32_t* iota, cudaStream_t s);
+
+// --------------------------------------------------------------- the tree
+struct TreeView {
+    int n_nodes;
+    const uint64_t* prefix;
+    const int* level;
+    const int* first;     // range in key-sorted sources
+    const int* count;
+    const int* child0;    // -1 for a leaf
+    const int* parent;    // -1 for a base box
+    const double* geom;   // [node][GEOM_STRIDE]
+    const int* tfirst;    // range in key-sorted targets
+    const int* tcount;
+};
+
+}  // namespace sfmm
+
+// --------------------------------------------------------------- the plan
+struct sfmm_plan_s {
+    int max_depth = 29;
+    int p = 16;
+    double tol = 0;
+    sfmm_options opt{};
+    cudaStream_t stream = nullptr;
+    std::string err;
+    bool timing = false;
+    sfmm_stats stats{};
+
+    // sources (key-sorted)
+    sfmm::Buf skeys, skeys2, sperm, sperm2, src4;
+    // targets (key-sorted)
+    sfmm::Buf tkeys, tkeys2, tperm, tperm2, tgt4;
+    // host-array staging for sfmm_deflection_host
+    sfmm::Buf h_src, h_q, h_tgt, h_psi, h_alpha;
+    // scratch
+    sfmm::Buf tmp, flags, pos, small;   // small: a few int64 counters (device)
+    // tree (node arrays)
+    sfmm::Buf n_prefix, n_level, n_first, n_count, n_child0, n_parent, n_geom, n_tfirst, n_tcount;
+    int64_t node_cap = 0;
+    std::vector<int> level_start;      // host copy: nodes of level l are [level_start[l], level_start[l+1])
+    int64_t n_nodes = 0;
+    // expansions
+    sfmm::Buf mpole, local, tables;
+    // lists
+    sfmm::Buf fa, fb, act, c_next, c_m2l, c_p2p, o_next, o_m2l, o_p2p;
+    sfmm::Buf m2l_t, m2l_s, m2l_t2, m2l_s2, p2p_t, p2p_s, p2p_t2, p2p_s2, m2l_off, p2p_off;
+    int64_t n_m2l = 0, n_p2p = 0;
+    bool m2l_alt = false, p2p_alt = false;
+    // node work lists
+    sfmm::Buf leaves_src, leaves_tgt;
+    int64_t n_leaves = 0, n_leaves_tgt = 0;
+    bool skeys_alt = false, tkeys_alt = false;
+    int64_t last_N = 0, last_M = 0;
+};
