@@ -1,0 +1,312 @@
+#!/usr/bin/env python
+"""sFMM benchmark: Mpts/s of a full potential + deflection solve on GB300.
+
+Workload (default): N = M = 1.6e7, sources and targets drawn independently from
+one clustered sky (20,000 shared NFW clumps, 70 % clustered, 30 % uniform),
+float64 positions, float32 equal masses.  One step = one complete
+sfmm_deflection (keys, sort, tree, up-pass, lists, M2L, L2L, L2P + near field)
+with inputs resident in HBM; value = M / step time.  Inputs (384 MB of
+positions each) are larger than L2, so no flush is needed between steps.
+
+Also reported: e2e through the host-array entry point (host<->device copies
+inside the timed region), the roofline of the dominant kernel (the evaluation
+kernel: near field + L2P), the oracle timed on the host cores on a bounded
+sample of targets, the relative error against the oracle on a seeded sample,
+and the SM clocks during the timed region.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl sfmm|reference]
+
+Under torchrun (N > 1) every rank solves its own independent sky (weak
+scaling; the path has no exchange step between independent problems).
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "sFMM Mpts/s (N=M=1.6e7) FP64 vs mixed precision, at stated relative error"
+FP64_PEAK_DERIVED = 152 * 2 * 2 * 2.07e9   # SMs x FP64 FMA/clk/SM x 2 flop x max SM clock
+# algorithmic FP64 flops per near-field pair: d^2 (3 sub, 3 mul, 2 add), 1/d^2
+# (counted as 4), q/d^2 (1), alpha sums (3 mul + 3 add), sum q (1); psi adds the
+# log (counted as 4) and its multiply-add (2)
+FLOPS_PER_PAIR_DEFL = 20
+FLOPS_PER_PAIR_PSI = 26
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="sfmm", choices=["sfmm", "reference"])
+    ap.add_argument("--n", type=int, default=16_000_000, help="N = M")
+    ap.add_argument("--clumps", type=int, default=20_000)
+    ap.add_argument("--p", type=int, default=32)
+    ap.add_argument("--leaf", type=int, default=32)
+    ap.add_argument("--check", type=int, default=200, help="targets checked against the oracle")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the oracle CPU baseline")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.f = None
+
+    def __enter__(self):
+        try:
+            self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.idx), "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.f:
+            return None
+        try:
+            rows = [r.split(",") for r in open(self.f.name).read().strip().splitlines() if r.strip()]
+            os.unlink(self.f.name)
+        except Exception:
+            return None
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, r[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def make_workload(args, rank):
+    from paper_2210_07021_gb300 import workloads
+    d = workloads.clustered_pair(n=args.n, n_clumps=args.clumps, config_index=3 + 100 * rank)
+    return d
+
+
+def oracle_rate(src, q, tgt, budget_s, seed_idx):
+    """Targets per second of the oracle direct sum on the host cores, timed on
+    a seeded sample sized to about budget_s seconds."""
+    from oracle.direct import direct_sum, threads
+    from paper_2210_07021_gb300 import workloads
+    q64 = q.astype(np.float64)
+    probe = workloads.subsample(tgt.shape[0], 8, seed_idx, stream=11)
+    t0 = time.perf_counter()
+    direct_sum(src, q64, tgt[probe])
+    t_probe = max(time.perf_counter() - t0, 1e-3)
+    k = int(max(8, min(tgt.shape[0], 8 * budget_s / t_probe)))
+    idx = workloads.subsample(tgt.shape[0], k, seed_idx, stream=12)
+    t0 = time.perf_counter()
+    direct_sum(src, q64, tgt[idx])
+    t = time.perf_counter() - t0
+    return k, t, threads()
+
+
+def run_reference(args):
+    ws, rank, local = dist_env()
+    if ws > 1 and rank != 0:
+        return
+    d = make_workload(args, 0)
+    from oracle.direct import direct_sum, threads
+    from paper_2210_07021_gb300 import workloads
+    src, q, tgt = d["src"], d["q"].astype(np.float64), d["tgt"]
+    probe = workloads.subsample(tgt.shape[0], 4, 3, stream=11)
+    t0 = time.perf_counter()
+    direct_sum(src, q, tgt[probe])
+    t_probe = max(time.perf_counter() - t0, 1e-3)
+    per_step_s = min(20.0, 150.0 / max(1, args.steps + args.warmup))
+    k = int(max(4, min(tgt.shape[0], 4 * per_step_s / t_probe)))
+    for w in range(args.warmup):
+        direct_sum(src, q, tgt[workloads.subsample(tgt.shape[0], k, 3, stream=20 + w)])
+    t0 = time.perf_counter()
+    for s in range(args.steps):
+        direct_sum(src, q, tgt[workloads.subsample(tgt.shape[0], k, 3, stream=40 + s)])
+    t = time.perf_counter() - t0
+    value = args.steps * k / t / 1e6
+    line = {"metric": METRIC, "value": value, "unit": "Mpts/s", "impl": "reference", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": d["workload"], "N": int(src.shape[0]), "M": int(tgt.shape[0]),
+                       "parallelism": "host cores (OpenMP)"},
+            "cpu_baseline": {"value": value, "unit": "Mpts/s", "cores": threads(), "kind": "oracle",
+                             "sample": f"{k} seeded targets per step against all {src.shape[0]} sources "
+                                       f"(FP64 direct sum, Neumaier sums)"},
+            "e2e": {"value": value, "unit": "Mpts/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_sfmm(args):
+    import torch
+    from paper_2210_07021_gb300 import sfmm, workloads
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        dist = None
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    d = make_workload(args, rank)
+    N, M = d["src"].shape[0], d["tgt"].shape[0]
+    src = torch.as_tensor(d["src"], device=dev)
+    q = torch.as_tensor(d["q"], device=dev)
+    tgt = torch.as_tensor(d["tgt"], device=dev)
+    plan = sfmm.Plan(p=args.p, leaf_size=args.leaf, q_f32=True, n_max=N, m_max=M)
+    psi = torch.empty(M, dtype=torch.float64, device=dev)
+    alpha = torch.empty((M, 2), dtype=torch.float64, device=dev)
+
+    def barrier():
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        plan.deflection(src, q, tgt, psi=psi, alpha=alpha)
+    plan.set_timing(True)
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    eval_ms, tot_ms, pairs, launches, phase = [], [], [], 0, np.zeros(8)
+    barrier()
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            plan.deflection(src, q, tgt, psi=psi, alpha=alpha)
+            st = plan.stats()
+            eval_ms.append(st["ms"][6])
+            pairs.append(st["p2p_interactions"])
+            launches += st["launches"]
+            phase += np.array(st["ms"])
+        ev1.record(stream)
+        barrier()
+    elapsed_ms = ev0.elapsed_time(ev1)
+    if dist:
+        t = torch.tensor([elapsed_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    total_pts = M * args.steps * ws
+    value = total_pts / (elapsed_ms / 1e3) / 1e6
+    plan.set_timing(False)
+
+    # end to end through the host-array entry point, pinned buffers
+    e2e = None
+    if not args.no_e2e:
+        hs = torch.empty((N, 3), dtype=torch.float64, pin_memory=True).numpy()
+        hq = torch.empty(N, dtype=torch.float32, pin_memory=True).numpy()
+        ht = torch.empty((M, 3), dtype=torch.float64, pin_memory=True).numpy()
+        hpsi = torch.empty(M, dtype=torch.float64, pin_memory=True).numpy()
+        halpha = torch.empty((M, 2), dtype=torch.float64, pin_memory=True).numpy()
+        hs[:] = d["src"]
+        hq[:] = d["q"]
+        ht[:] = d["tgt"]
+        plan.deflection_host(hs, hq, ht, psi=hpsi, alpha=halpha)
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            plan.deflection_host(hs, hq, ht, psi=hpsi, alpha=halpha)
+        barrier()
+        t_e2e = time.perf_counter() - t0
+        if dist:
+            t = torch.tensor([t_e2e], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            t_e2e = float(t.item())
+        e2e = {"value": M * args.steps * ws / t_e2e / 1e6, "unit": "Mpts/s",
+               "h2d_bytes_per_step": int(N * 24 + N * 4 + M * 24), "d2h_bytes_per_step": int(M * 8 + M * 16)}
+
+    if rank != 0:
+        if dist:
+            dist.barrier()
+        return
+    # accuracy on a seeded sample of targets, against the oracle
+    from oracle.direct import direct_sum
+    idx = workloads.subsample(M, args.check, 3, stream=9)
+    ref = direct_sum(d["src"], d["q"].astype(np.float64), d["tgt"][idx])
+    err = {"psi_rel": rel(psi.cpu().numpy()[idx], ref["psi"]), "alpha_rel": rel(alpha.cpu().numpy()[idx], ref["alpha"]),
+           "sample": int(idx.size), "norm": "l2 over the sample (relative)"}
+    cpu = None
+    if ws == 1:
+        k, t, cores = oracle_rate(d["src"], d["q"], d["tgt"], args.cpu_seconds, 3)
+        cpu = {"value": k / t / 1e6, "unit": "Mpts/s", "cores": cores, "kind": "oracle",
+               "sample": f"{k} seeded targets against all {N} sources, FP64 direct sum, {t:.1f} s"}
+    ev_ms = float(np.mean(eval_ms))
+    pairs_mean = float(np.mean(pairs))
+    achieved = pairs_mean * FLOPS_PER_PAIR_PSI / (ev_ms / 1e3)
+    roofline = {"bound": "alu", "kernel": "k_eval (near field + L2P, FP64)", "achieved": achieved / 1e12,
+                "peak": FP64_PEAK_DERIVED / 1e12, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_DERIVED,
+                "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (FP64 is not in "
+                               "MEASURED_PEAKS.json; a plain FMA loop measured 1.19 TFLOP/s)",
+                "work_per_unit": f"{FLOPS_PER_PAIR_PSI} FP64 flop per near-field pair (1/d^2 and log counted as 4)",
+                "pairs_per_launch": pairs_mean, "launch_ms": ev_ms, "traffic": None}
+    names = ["keys_sort", "tree_geometry", "up_pass", "lists", "m2l", "l2l", "evaluation", "total"]
+    line = {"metric": METRIC, "value": value, "unit": "Mpts/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": d["workload"], "N": N, "M": M, "p": args.p, "leaf_size": args.leaf,
+                       "c_s": 2.0, "c_t": 0.5, "precision": "fp64",
+                       "l2": "inputs larger than L2 (384 MB of positions each), no flush"},
+            "error_vs_oracle": err, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": int(launches),
+            "phase_ms": {k: v / args.steps for k, v in zip(names, phase)},
+            "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_sfmm(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -129,12 +129,15 @@ int sfmm_order(sfmm_plan_t plan);
  * Statistics of the last solve on this plan (host struct, filled by copy).
  *   n_nodes, n_leaves, depth : the tree of Sec. 3.1 (depth = deepest level used)
  *   n_m2l, n_p2p             : FMM-act and direct-act pairs of Algorithm 1
- *   p2p_interactions         : source-target point pairs evaluated directly
- *   ms[8]                    : device time of the phases: keys+sort, tree+geometry,
- *                              up-pass, lists, M2L, L2L, evaluation, total
+ *   p2p_interactions         : source-target point pairs evaluated directly (counted
+ *                              only while timing is on, else 0)
+ *   launches                 : kernel launches of the solve
+ *   ms[8]                    : device time of the phases (only while timing is on):
+ *                              keys+sort, tree+geometry, up-pass, lists, M2L, L2L,
+ *                              evaluation, total
  */
 typedef struct {
-    int64_t n_nodes, n_leaves, depth, n_m2l, n_p2p, p2p_interactions;
+    int64_t n_nodes, n_leaves, depth, n_m2l, n_p2p, p2p_interactions, launches;
     double ms[8];
 } sfmm_stats;
 sfmm_status sfmm_get_stats(sfmm_plan_t plan, sfmm_stats* out);

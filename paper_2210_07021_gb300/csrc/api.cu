@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <atomic>
 #include <mutex>
 
 namespace sfmm {
@@ -24,9 +25,17 @@ cudaError_t launch_m2l(const TreeView& T, const int64_t* off, const uint32_t* sr
 cudaError_t launch_l2l(const TreeView& T, int a, int b, int p, const double* tables, double* local, cudaStream_t s);
 cudaError_t launch_unscale(int n_nodes, const double* geom, const double* in, double* out, int p, int is_local,
                            cudaStream_t s);
+cudaError_t launch_count_pairs(const TreeView& T, const int* leaves, int64_t n_leaves, const int64_t* p2p_off,
+                               const uint32_t* p2p_src, unsigned long long* out, cudaStream_t s);
 cudaError_t launch_eval(const TreeView& T, const int* leaves, int64_t n_leaves, const double4_32a* src, const double4_32a* tgt,
                         const uint32_t* tperm, const int64_t* p2p_off, const uint32_t* p2p_src, const double* local,
                         const double* mpole, int p, int zero_mean, double* psi, double* alpha, cudaStream_t s);
+
+namespace {
+std::atomic<int64_t> g_launches{0};
+}
+void count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+int64_t launch_total() { return g_launches.load(std::memory_order_relaxed); }
 
 cudaError_t ensure(Buf& b, size_t bytes)
 {
@@ -179,6 +188,7 @@ sfmm_status solve(sfmm_plan_s* P, const double* src, const void* q, int64_t N, c
     P->last_N = N;
     P->last_M = M;
     P->n_nodes = 0;
+    const int64_t launches0 = launch_total();
     if (M > 0 && N == 0) {
         if (psi && (e = cudaMemsetAsync(psi, 0, (size_t)M * 8, s))) return cuda_fail(P, e, "memset psi");
         if (alpha && (e = cudaMemsetAsync(alpha, 0, (size_t)M * 16, s))) return cuda_fail(P, e, "memset alpha");
@@ -203,14 +213,14 @@ sfmm_status solve(sfmm_plan_s* P, const double* src, const void* q, int64_t N, c
         return cuda_fail(P, e, "sort sources");
     const uint64_t* skeys = P->skeys_alt ? P->skeys2.as<uint64_t>() : P->skeys.as<uint64_t>();
     const uint32_t* sperm = P->skeys_alt ? P->sperm2.as<uint32_t>() : P->sperm.as<uint32_t>();
-    k_gather_src<<<grid_for(N), 256, 0, s>>>(src, q, P->opt.q_f32, sperm, N, P->src4.as<double4_32a>());
+    k_gather_src<<<grid_for(N), 256, 0, s>>>(src, q, P->opt.q_f32, sperm, N, P->src4.as<double4_32a>()); count_launch();
     if ((e = launch_keys(tgt, M, P->tkeys.as<uint64_t>(), P->tperm.as<uint32_t>(), s))) return cuda_fail(P, e, "tkeys");
     if ((e = radix_sort(P->tkeys.as<uint64_t>(), P->tperm.as<uint32_t>(), P->tkeys2.as<uint64_t>(),
                         P->tperm2.as<uint32_t>(), M, 62, P->tmp.p, s, &P->tkeys_alt)))
         return cuda_fail(P, e, "sort targets");
     const uint64_t* tkeys = P->tkeys_alt ? P->tkeys2.as<uint64_t>() : P->tkeys.as<uint64_t>();
     const uint32_t* tperm = P->tkeys_alt ? P->tperm2.as<uint32_t>() : P->tperm.as<uint32_t>();
-    k_gather_tgt<<<grid_for(M), 256, 0, s>>>(tgt, tperm, M, P->tgt4.as<double4_32a>());
+    k_gather_tgt<<<grid_for(M), 256, 0, s>>>(tgt, tperm, M, P->tgt4.as<double4_32a>()); count_launch();
     if ((e = cudaGetLastError())) return cuda_fail(P, e, "gather");
     tm.mark();
     // ---- tree and geometry
@@ -257,6 +267,18 @@ sfmm_status solve(sfmm_plan_s* P, const double* src, const void* q, int64_t N, c
                          P->opt.zero_mean, psi, alpha, s)))
         return cuda_fail(P, e, "evaluation");
     tm.mark();
+    if (P->timing) {
+        // near-field source-target pairs (for the throughput of the evaluation kernel)
+        unsigned long long* cnt = reinterpret_cast<unsigned long long*>(P->small.as<int64_t>() + 16);
+        if ((e = cudaMemsetAsync(cnt, 0, 8, s))) return cuda_fail(P, e, "memset");
+        if ((e = launch_count_pairs(T, P->leaves_tgt.as<int>(), P->n_leaves_tgt, P->p2p_off.as<int64_t>(), p2p_s,
+                                    cnt, s)))
+            return cuda_fail(P, e, "count pairs");
+        unsigned long long h = 0;
+        if ((e = cudaMemcpyAsync(&h, cnt, 8, cudaMemcpyDeviceToHost, s))) return cuda_fail(P, e, "copy");
+        if ((e = cudaStreamSynchronize(s))) return cuda_fail(P, e, "sync");
+        P->stats.p2p_interactions = (int64_t)h;
+    }
     if ((e = cudaStreamSynchronize(s))) return cuda_fail(P, e, "solve");
     tm.finish();
     P->stats.n_nodes = nn;
@@ -264,6 +286,7 @@ sfmm_status solve(sfmm_plan_s* P, const double* src, const void* q, int64_t N, c
     P->stats.depth = depth;
     P->stats.n_m2l = P->n_m2l;
     P->stats.n_p2p = P->n_p2p;
+    P->stats.launches = launch_total() - launches0;
     return SFMM_OK;
 }
 

@@ -25,6 +25,12 @@ __host__ __device__ __forceinline__ cd cmul(cd a, cd b) { return mk(a.x * b.x - 
 __host__ __device__ __forceinline__ cd cscale(cd a, double s) { return mk(a.x * s, a.y * s); }
 __host__ __device__ __forceinline__ cd cconj(cd a) { return mk(a.x, -a.y); }
 
+// ---------------------------------------------------------- launch counting
+// Every kernel launch of the library bumps this counter (reported per solve in
+// sfmm_stats.launches).
+void count_launch(int n = 1);
+int64_t launch_total();
+
 // ------------------------------------------------------------ device buffers
 struct Buf {
     void* p = nullptr;

@@ -144,7 +144,28 @@ __global__ void __launch_bounds__(128) k_eval(EvalArgs A)
     }
 }
 
+__global__ void k_count_pairs(TreeView T, const int* __restrict__ leaves, int64_t n, const int64_t* __restrict__ off,
+                              const uint32_t* __restrict__ src, unsigned long long* __restrict__ out)
+{
+    for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < n; w += (int64_t)gridDim.x * blockDim.x) {
+        const int leaf = leaves[w];
+        unsigned long long c = 0;
+        for (int64_t k = off[leaf]; k < off[leaf + 1]; ++k) c += (unsigned long long)T.count[src[k]];
+        atomicAdd(out, c * (unsigned long long)T.tcount[leaf]);
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_count_pairs(const TreeView& T, const int* leaves, int64_t n_leaves, const int64_t* p2p_off,
+                               const uint32_t* p2p_src, unsigned long long* out, cudaStream_t s)
+{
+    if (n_leaves == 0) return cudaSuccess;
+    int64_t blocks = (n_leaves + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    k_count_pairs<<<(unsigned)blocks, 256, 0, s>>>(T, leaves, n_leaves, p2p_off, p2p_src, out); count_launch();
+    return cudaGetLastError();
+}
 
 cudaError_t launch_eval(const TreeView& T, const int* leaves, int64_t n_leaves, const double4_32a* src, const double4_32a* tgt,
                         const uint32_t* tperm, const int64_t* p2p_off, const uint32_t* p2p_src, const double* local,
@@ -169,7 +190,7 @@ cudaError_t launch_eval(const TreeView& T, const int* leaves, int64_t n_leaves, 
     A.alpha = alpha;
     int64_t blocks = (n_leaves + 3) / 4;
     if (blocks > 152 * 64) blocks = 152 * 64;
-    k_eval<<<(unsigned)blocks, 128, 0, s>>>(A);
+    k_eval<<<(unsigned)blocks, 128, 0, s>>>(A); count_launch();
     return cudaGetLastError();
 }
 

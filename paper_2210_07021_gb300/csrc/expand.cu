@@ -387,7 +387,7 @@ cudaError_t launch_p2m(const TreeView& T, const int* leaves, int64_t n_leaves, c
 {
     if (n_leaves == 0) return cudaSuccess;
     const unsigned g = grid_for(n_leaves, 128);
-#define P2M_CASE(PP) case PP: k_p2m<PP><<<g, 128, 0, s>>>(T, leaves, n_leaves, src, mpole); break;
+#define P2M_CASE(PP) case PP: k_p2m<PP><<<g, 128, 0, s>>>(T, leaves, n_leaves, src, mpole); count_launch(); break;
     switch ((p + 3) / 4 * 4) {
         P2M_CASE(4) P2M_CASE(8) P2M_CASE(12) P2M_CASE(16) P2M_CASE(20) P2M_CASE(24) P2M_CASE(28) P2M_CASE(32)
         default: return cudaErrorInvalidValue;
@@ -399,28 +399,28 @@ cudaError_t launch_p2m(const TreeView& T, const int* leaves, int64_t n_leaves, c
 cudaError_t launch_m2m(const TreeView& T, int a, int b, int p, const double* tables, double* mpole, cudaStream_t s)
 {
     if (b <= a) return cudaSuccess;
-    k_m2m<<<grid_for(b - a, 4), 128, 0, s>>>(T, a, b, p, tables, mpole);
+    k_m2m<<<grid_for(b - a, 4), 128, 0, s>>>(T, a, b, p, tables, mpole); count_launch();
     return cudaGetLastError();
 }
 
 cudaError_t launch_m2l(const TreeView& T, const int64_t* off, const uint32_t* srcs, int p, const double* tables,
                        const double* mpole, double* local, cudaStream_t s)
 {
-    k_m2l<<<grid_for(T.n_nodes, 4), 128, 0, s>>>(T, off, srcs, p, tables, mpole, local);
+    k_m2l<<<grid_for(T.n_nodes, 4), 128, 0, s>>>(T, off, srcs, p, tables, mpole, local); count_launch();
     return cudaGetLastError();
 }
 
 cudaError_t launch_l2l(const TreeView& T, int a, int b, int p, const double* tables, double* local, cudaStream_t s)
 {
     if (b <= a) return cudaSuccess;
-    k_l2l<<<grid_for(b - a, 4), 128, 0, s>>>(T, a, b, p, tables, local);
+    k_l2l<<<grid_for(b - a, 4), 128, 0, s>>>(T, a, b, p, tables, local); count_launch();
     return cudaGetLastError();
 }
 
 cudaError_t launch_unscale(int n_nodes, const double* geom, const double* in, double* out, int p, int is_local,
                            cudaStream_t s)
 {
-    k_unscale<<<grid_for(n_nodes, 256), 256, 0, s>>>(n_nodes, geom, in, out, p, is_local);
+    k_unscale<<<grid_for(n_nodes, 256), 256, 0, s>>>(n_nodes, geom, in, out, p, is_local); count_launch();
     return cudaGetLastError();
 }
 

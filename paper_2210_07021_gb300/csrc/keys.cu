@@ -124,7 +124,7 @@ cudaError_t launch_keys(const double* xyz, int64_t n, uint64_t* keys, uint32_t* 
     if (n <= 0) return cudaSuccess;
     int64_t blocks = (n + 255) / 256;
     if (blocks > 152 * 32) blocks = 152 * 32;
-    k_keys<<<(unsigned)blocks, 256, 0, s>>>(xyz, n, keys, iota);
+    k_keys<<<(unsigned)blocks, 256, 0, s>>>(xyz, n, keys, iota); count_launch();
     return cudaGetLastError();
 }
 

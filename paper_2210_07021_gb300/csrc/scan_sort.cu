@@ -109,9 +109,9 @@ cudaError_t exclusive_scan_t(const T* in, T* out, int64_t n, T* total, void* tmp
     }
     const int64_t nb = (n + SC_TILE - 1) / SC_TILE;
     T* bsum = static_cast<T*>(tmp);
-    k_scan_reduce<T><<<(unsigned)nb, SC_T, 0, s>>>(in, n, bsum);
-    k_scan_top<T><<<1, SC_T, 0, s>>>(bsum, nb, total);
-    k_scan_down<T><<<(unsigned)nb, SC_T, 0, s>>>(in, out, n, bsum);
+    k_scan_reduce<T><<<(unsigned)nb, SC_T, 0, s>>>(in, n, bsum); count_launch();
+    k_scan_top<T><<<1, SC_T, 0, s>>>(bsum, nb, total); count_launch();
+    k_scan_down<T><<<(unsigned)nb, SC_T, 0, s>>>(in, out, n, bsum); count_launch();
     return cudaGetLastError();
 }
 
@@ -211,10 +211,10 @@ cudaError_t radix_sort(uint64_t* k1, uint32_t* v1, uint64_t* k2, uint32_t* v2, i
     uint32_t *va = v1, *vb = v2;
     bool alt = false;
     for (int shift = 0; shift < bits; shift += 8) {
-        k_rs_hist<<<(unsigned)ntiles, RS_T, 0, s>>>(ka, n, shift, hist, ntiles);
+        k_rs_hist<<<(unsigned)ntiles, RS_T, 0, s>>>(ka, n, shift, hist, ntiles); count_launch();
         cudaError_t e = exclusive_scan_u32(hist, offs, nh, nullptr, stmp, s);
         if (e != cudaSuccess) return e;
-        k_rs_scatter<<<(unsigned)ntiles, RS_T, 0, s>>>(ka, va, kb, vb, n, shift, offs, ntiles);
+        k_rs_scatter<<<(unsigned)ntiles, RS_T, 0, s>>>(ka, va, kb, vb, n, shift, offs, ntiles); count_launch();
         std::swap(ka, kb);
         std::swap(va, vb);
         alt = !alt;

@@ -214,7 +214,7 @@ cudaError_t build_tree(sfmm_plan_s* P, const uint64_t* keys, int64_t n, int m, i
     P->n_nodes = 0;
     if ((e = grow(12 + 4 * 1024))) return e;
     k_level0<<<1, 32, 0, s>>>(keys, n, P->n_prefix.as<uint64_t>(), P->n_level.as<int>(), P->n_first.as<int>(),
-                              P->n_count.as<int>(), P->n_child0.as<int>(), P->n_parent.as<int>());
+                              P->n_count.as<int>(), P->n_child0.as<int>(), P->n_parent.as<int>()); count_launch();
     P->n_nodes = 12;
     P->level_start.assign(1, 0);
     P->level_start.push_back(12);
@@ -228,7 +228,7 @@ cudaError_t build_tree(sfmm_plan_s* P, const uint64_t* keys, int64_t n, int m, i
         if ((e = ensure(P->tmp, scan_tmp_bytes(width)))) return e;
         int64_t* flags = P->flags.as<int64_t>();
         int64_t* pos = P->pos.as<int64_t>();
-        k_split_flags<<<grid_for(width), 256, 0, s>>>(P->n_count.as<int>(), a, b, lvl, m, max_depth, flags);
+        k_split_flags<<<grid_for(width), 256, 0, s>>>(P->n_count.as<int>(), a, b, lvl, m, max_depth, flags); count_launch();
         int64_t* total = P->small.as<int64_t>();
         if ((e = exclusive_scan_i64(flags, pos, width, total, P->tmp.p, s))) return e;
         int64_t splits = 0;
@@ -239,7 +239,7 @@ cudaError_t build_tree(sfmm_plan_s* P, const uint64_t* keys, int64_t n, int m, i
         k_make_children<<<grid_for(width), 256, 0, s>>>(keys, a, b, lvl, flags, pos, P->n_prefix.as<uint64_t>(),
                                                        P->n_level.as<int>(), P->n_first.as<int>(),
                                                        P->n_count.as<int>(), P->n_child0.as<int>(),
-                                                       P->n_parent.as<int>());
+                                                       P->n_parent.as<int>()); count_launch();
         P->n_nodes = b + 4 * splits;
         P->level_start.push_back((int)P->n_nodes);
         ++lvl;
@@ -253,7 +253,7 @@ cudaError_t tree_geometry(sfmm_plan_s* P)
     const int64_t nn = P->n_nodes;
     if ((e = ensure(P->n_geom, (size_t)nn * GEOM_STRIDE * 8))) return e;
     k_geometry<<<grid_for(nn), 256, 0, P->stream>>>((int)nn, P->n_prefix.as<uint64_t>(), P->n_level.as<int>(),
-                                                    P->n_geom.as<double>());
+                                                    P->n_geom.as<double>()); count_launch();
     return cudaGetLastError();
 }
 
@@ -264,7 +264,7 @@ cudaError_t tree_target_ranges(sfmm_plan_s* P, const uint64_t* tkeys, int64_t M)
     if ((e = ensure(P->n_tfirst, (size_t)nn * 4))) return e;
     if ((e = ensure(P->n_tcount, (size_t)nn * 4))) return e;
     k_target_ranges<<<grid_for(nn), 256, 0, P->stream>>>((int)nn, P->n_prefix.as<uint64_t>(), P->n_level.as<int>(),
-                                                         tkeys, M, P->n_tfirst.as<int>(), P->n_tcount.as<int>());
+                                                         tkeys, M, P->n_tfirst.as<int>(), P->n_tcount.as<int>()); count_launch();
     return cudaGetLastError();
 }
 
@@ -278,10 +278,10 @@ cudaError_t collect_leaves(sfmm_plan_s* P, const int* cnt, sfmm::Buf& out, int64
     if ((e = ensure(P->pos, (size_t)nn * 8))) return e;
     if ((e = ensure(P->tmp, scan_tmp_bytes(nn)))) return e;
     if ((e = ensure(out, (size_t)nn * 4))) return e;
-    k_collect_leaves<<<grid_for(nn), 256, 0, s>>>((int)nn, P->n_child0.as<int>(), cnt, P->flags.as<int64_t>());
+    k_collect_leaves<<<grid_for(nn), 256, 0, s>>>((int)nn, P->n_child0.as<int>(), cnt, P->flags.as<int64_t>()); count_launch();
     int64_t* total = P->small.as<int64_t>() + 1;
     if ((e = exclusive_scan_i64(P->flags.as<int64_t>(), P->pos.as<int64_t>(), nn, total, P->tmp.p, s))) return e;
-    k_compact<<<grid_for(nn), 256, 0, s>>>((int)nn, P->flags.as<int64_t>(), P->pos.as<int64_t>(), out.as<int>());
+    k_compact<<<grid_for(nn), 256, 0, s>>>((int)nn, P->flags.as<int64_t>(), P->pos.as<int64_t>(), out.as<int>()); count_launch();
     if ((e = cudaMemcpyAsync(n_out, total, 8, cudaMemcpyDeviceToHost, s))) return e;
     return cudaStreamSynchronize(s);
 }

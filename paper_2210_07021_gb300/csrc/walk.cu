@@ -142,7 +142,7 @@ cudaError_t build_lists(sfmm_plan_s* P, const TreeView& T, double c_s, double c_
     cap_front = (int64_t)std::min(P->fa.cap, P->fb.cap) / 8;
     int64_t n_front = 144;
     int64_t n_m2l = 0, n_p2p = 0;
-    k_init_frontier<<<1, 160, 0, s>>>(P->fa.as<int2>());
+    k_init_frontier<<<1, 160, 0, s>>>(P->fa.as<int2>()); count_launch();
     // list storage: grown as rounds add pairs
     auto grow_list = [&](Buf& bt, Buf& bs, int64_t used, int64_t want) -> cudaError_t {
         cudaError_t r;
@@ -169,7 +169,7 @@ cudaError_t build_lists(sfmm_plan_s* P, const TreeView& T, double c_s, double c_
         if ((e = ensure(P->tmp, scan_tmp_bytes(n_front)))) return e;
         k_classify<<<grid_for(n_front), 256, 0, s>>>(T, P->fa.as<int2>(), n_front, c_s, c_t, P->act.as<uint8_t>(),
                                                      P->c_next.as<int64_t>(), P->c_m2l.as<int64_t>(),
-                                                     P->c_p2p.as<int64_t>());
+                                                     P->c_p2p.as<int64_t>()); count_launch();
         if ((e = exclusive_scan_i64(P->c_next.as<int64_t>(), P->o_next.as<int64_t>(), n_front, totals, P->tmp.p, s)))
             return e;
         if ((e = exclusive_scan_i64(P->c_m2l.as<int64_t>(), P->o_m2l.as<int64_t>(), n_front, totals + 1, P->tmp.p, s)))
@@ -188,7 +188,7 @@ cudaError_t build_lists(sfmm_plan_s* P, const TreeView& T, double c_s, double c_
                                                  P->o_next.as<int64_t>(), P->o_m2l.as<int64_t>(),
                                                  P->o_p2p.as<int64_t>(), P->fb.as<int2>(),
                                                  P->m2l_t.as<uint64_t>() + n_m2l, P->m2l_s.as<uint32_t>() + n_m2l,
-                                                 P->p2p_t.as<uint64_t>() + n_p2p, P->p2p_s.as<uint32_t>() + n_p2p);
+                                                 P->p2p_t.as<uint64_t>() + n_p2p, P->p2p_s.as<uint32_t>() + n_p2p); count_launch();
         if ((e = cudaGetLastError())) return e;
         n_m2l += h[1];
         n_p2p += h[2];
@@ -216,8 +216,8 @@ cudaError_t build_lists(sfmm_plan_s* P, const TreeView& T, double c_s, double c_
         return e;
     const uint64_t* mt = P->m2l_alt ? P->m2l_t2.as<uint64_t>() : P->m2l_t.as<uint64_t>();
     const uint64_t* pt = P->p2p_alt ? P->p2p_t2.as<uint64_t>() : P->p2p_t.as<uint64_t>();
-    k_csr_offsets<<<grid_for(P->n_nodes + 1), 256, 0, s>>>(mt, n_m2l, (int)P->n_nodes, P->m2l_off.as<int64_t>());
-    k_csr_offsets<<<grid_for(P->n_nodes + 1), 256, 0, s>>>(pt, n_p2p, (int)P->n_nodes, P->p2p_off.as<int64_t>());
+    k_csr_offsets<<<grid_for(P->n_nodes + 1), 256, 0, s>>>(mt, n_m2l, (int)P->n_nodes, P->m2l_off.as<int64_t>()); count_launch();
+    k_csr_offsets<<<grid_for(P->n_nodes + 1), 256, 0, s>>>(pt, n_p2p, (int)P->n_nodes, P->p2p_off.as<int64_t>()); count_launch();
     return cudaGetLastError();
 }
 

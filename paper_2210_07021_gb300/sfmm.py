@@ -31,6 +31,7 @@ class Options(ctypes.Structure):
 class Stats(ctypes.Structure):
     _fields_ = [("n_nodes", ctypes.c_int64), ("n_leaves", ctypes.c_int64), ("depth", ctypes.c_int64),
                 ("n_m2l", ctypes.c_int64), ("n_p2p", ctypes.c_int64), ("p2p_interactions", ctypes.c_int64),
+                ("launches", ctypes.c_int64),
                 ("ms", ctypes.c_double * 8)]
 
 

@@ -20,7 +20,8 @@ grid        the centres of the 12 N_side^2 equal-area HEALPix pixels (ring
 The projected NFW profile is sampled by inverting its enclosed-mass CDF
 g(x) / g(20), g(x) = ln(x/2) + F(x) with F = arccosh(1/x)/sqrt(1-x^2) (x<1),
 arccos(1/x)/sqrt(x^2-1) (x>1), 1 (x=1) -- the standard closed form of the
-projected NFW mass (Wright & Brainerd 2000, cited in Sec. 4.3) -- by bisection.
+projected NFW mass (Wright & Brainerd 2000, cited in Sec. 4.3) -- tabulated on
+a fine log grid and interpolated.
 """
 import numpy as np
 
@@ -51,18 +52,17 @@ def _nfw_g(x):
     return out
 
 
-def sample_nfw_x(rng, n, xmax=20.0, iters=64):
-    """Projected radius x = r / r_s drawn from the truncated projected NFW."""
+def sample_nfw_x(rng, n, xmax=20.0, grid=200001):
+    """Projected radius x = r / r_s drawn from the truncated projected NFW:
+    the inverse of CDF(x) = g(x) / g(xmax), tabulated on a log-spaced grid of
+    x in [1e-9, xmax] (the CDF is below 1e-15 at 1e-9) and interpolated."""
     u = rng.random(n)
-    gmax = _nfw_g(np.array([xmax]))[0]
-    lo = np.full(n, 1e-12)
-    hi = np.full(n, xmax)
-    for _ in range(iters):
-        mid = 0.5 * (lo + hi)
-        below = _nfw_g(mid) / gmax < u
-        lo = np.where(below, mid, lo)
-        hi = np.where(below, hi, mid)
-    return 0.5 * (lo + hi)
+    xs = np.geomspace(1e-9, xmax, grid)
+    xs[-1] = xmax
+    cdf = _nfw_g(xs) / _nfw_g(np.array([xmax]))[0]
+    cdf[0] = 0.0
+    cdf = np.maximum.accumulate(cdf)
+    return np.interp(u, cdf, xs)
 
 
 def place_around(centres, theta, phi):
@@ -77,13 +77,20 @@ def place_around(centres, theta, phi):
     return y / np.linalg.norm(y, axis=1)[:, None]
 
 
-def clustered(rng, n, n_clumps, frac_clustered=0.7, rs_arcmin=(0.1, 2.0)):
-    """Clustered-sky positions [n, 3] (float64)."""
-    n_cl = int(round(frac_clustered * n))
-    n_un = n - n_cl
+def clump_set(rng, n_clumps, rs_arcmin=(0.1, 2.0)):
+    """Clump centres (uniform on S^2) and scale radii (log-uniform, radians)."""
     centres = uniform_sphere(rng, n_clumps)
     rs = np.exp(rng.uniform(np.log(rs_arcmin[0]), np.log(rs_arcmin[1]), n_clumps)) * ARCMIN
-    which = rng.integers(0, n_clumps, n_cl)
+    return centres, rs
+
+
+def clustered(rng, n, n_clumps, frac_clustered=0.7, rs_arcmin=(0.1, 2.0), clumps=None):
+    """Clustered-sky positions [n, 3] (float64); `clumps` = (centres, rs) to
+    reuse a clump set, else one is drawn from rng."""
+    n_cl = int(round(frac_clustered * n))
+    n_un = n - n_cl
+    centres, rs = clumps if clumps is not None else clump_set(rng, n_clumps, rs_arcmin)
+    which = rng.integers(0, centres.shape[0], n_cl)
     x = sample_nfw_x(rng, n_cl)
     theta = x * rs[which]
     phi = rng.uniform(0.0, 2.0 * np.pi, n_cl)
@@ -146,14 +153,15 @@ def clustered_sky(n=1_000_000, n_clumps=2000, nside=512, config_index=2):
 
 
 def clustered_pair(n=16_000_000, m=None, n_clumps=20_000, config_index=3, q_dtype=np.float32):
-    """N sources and M targets, two independent draws of the same clustered
-    mix; masses equal, stored as float32 by default."""
+    """N sources and M targets drawn independently from the same clustered
+    mix (the same clumps); masses equal, stored as float32 by default."""
     m = n if m is None else m
-    src = clustered(rng_for(config_index, 0), n, n_clumps)
-    tgt = clustered(rng_for(config_index, 1), m, n_clumps)
+    clumps = clump_set(rng_for(config_index, 2), n_clumps)
+    src = clustered(rng_for(config_index, 0), n, n_clumps, clumps=clumps)
+    tgt = clustered(rng_for(config_index, 1), m, n_clumps, clumps=clumps)
     q = np.full(n, 4.0 * np.pi / n, dtype=q_dtype)
     return dict(src=src, q=q, tgt=tgt,
-                workload=f"clustered N=M={n} ({n_clumps} clumps), q {np.dtype(q_dtype).name}")
+                workload=f"clustered sources and targets N=M={n} ({n_clumps} shared clumps), q {np.dtype(q_dtype).name}")
 
 
 def subsample(n, k, config_index, stream=7):
