@@ -180,6 +180,28 @@ sfmm_status sfmm_debug_copy(sfmm_plan_t plan, int which, void* dst, int64_t byte
  */
 sfmm_status sfmm_keys(const double* xyz, int64_t n, uint64_t* keys, void* stream);
 
+/*
+ * The keys and stable radix sort of sfmm_keys / the first step of every solve,
+ * for callers that must not allocate device memory (a plugin inside a host
+ * application whose memory pool owns the device, a latency-critical pipeline
+ * that cannot accept the synchronisation cudaMalloc/cudaFree may cause).  The
+ * paper has no counterpart; this is a property of the library, not of the method.
+ *   xyz   [n][3] float64 unit vectors (device, caller-owned)
+ *   keys  [n] uint64 (device, caller-owned, overwritten): the order-29 nested keys
+ *         in ascending order
+ *   perm  [n] uint32 (device, caller-owned, overwritten): perm[i] = input index of
+ *         the i-th smallest key; equal keys keep their input order
+ *   n     0..262144: larger n returns SFMM_EINVAL (message in sfmm_last_error(NULL))
+ * Allocates nothing: the sort's scratch (3.5 MiB) is one static device array
+ * that every GPU loading the library holds until exit.  The first call on a
+ * device looks up that array's device address (cudaGetSymbolAddress) and should
+ * come before any stream capture.  All calls share the array: calls that
+ * overlap on the GPU race and must be serialised by the caller.  Work is
+ * enqueued on `stream` (cudaStream_t or NULL); the outputs are ready when the
+ * stream reaches that point.
+ */
+sfmm_status sfmm_sort_keys_static(const double* xyz, int64_t n, uint64_t* keys, uint32_t* perm, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -301,6 +301,12 @@ sfmm_status check_args(sfmm_plan_s* P, const double* src, const void* q, int64_t
 }
 
 }  // namespace
+
+void set_process_error(const std::string& msg)
+{
+    std::lock_guard<std::mutex> g(g_err_mu);
+    g_plan_err = msg;
+}
 }  // namespace sfmm
 
 using namespace sfmm;

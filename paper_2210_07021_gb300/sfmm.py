@@ -19,7 +19,8 @@ SFMM_FP64, SFMM_MIXED = 0, 1
 
 EXPORTS = ["sfmm_default_options", "sfmm_plan", "sfmm_potential", "sfmm_deflection", "sfmm_deflection_host",
            "sfmm_destroy", "sfmm_last_error", "sfmm_order", "sfmm_get_stats", "sfmm_set_timing",
-           "sfmm_debug_copy", "sfmm_keys"]
+           "sfmm_debug_copy", "sfmm_keys", "sfmm_sort_keys_static"]
+STATIC_SORT_MAX_N = 1 << 18
 
 
 class Options(ctypes.Structure):
@@ -81,6 +82,8 @@ def load(build_if_missing=True):
     L.sfmm_debug_copy.restype = ci
     L.sfmm_keys.argtypes = [vp, i64, vp, vp]
     L.sfmm_keys.restype = ci
+    L.sfmm_sort_keys_static.argtypes = [vp, i64, vp, vp, vp]
+    L.sfmm_sort_keys_static.restype = ci
     _lib = L
     return L
 
@@ -226,3 +229,19 @@ def keys(xyz):
                           ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
     _check(st)
     return out
+
+
+def sort_keys_static(xyz, keys=None, perm=None):
+    """Keys and stable sort without any device allocation inside the library
+    (sfmm_sort_keys_static): returns (keys as int64 view of uint64, perm int32)."""
+    import torch
+    n = xyz.shape[0]
+    if keys is None:
+        keys = torch.empty(n, dtype=torch.int64, device=xyz.device)
+    if perm is None:
+        perm = torch.empty(n, dtype=torch.int32, device=xyz.device)
+    st = load().sfmm_sort_keys_static(_dptr(xyz, torch.float64, 3, "xyz"), n, ctypes.c_void_p(keys.data_ptr()),
+                                      ctypes.c_void_p(perm.data_ptr()),
+                                      ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    _check(st)
+    return keys, perm
