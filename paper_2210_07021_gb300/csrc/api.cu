@@ -17,12 +17,23 @@ cudaError_t tree_target_ranges(sfmm_plan_s* P, const uint64_t* tkeys, int64_t M)
 cudaError_t collect_leaves(sfmm_plan_s* P, const int* cnt, Buf& out, int64_t* n_out);
 cudaError_t build_lists(sfmm_plan_s* P, const TreeView& T, double c_s, double c_t);
 void fill_tables(double* h);
-cudaError_t launch_p2m(const TreeView& T, const int* leaves, int64_t n_leaves, const double4_32a* src, double* mpole, int p,
-                       cudaStream_t s);
-cudaError_t launch_m2m(const TreeView& T, int a, int b, int p, const double* tables, double* mpole, cudaStream_t s);
+size_t xgeo_bytes();
+cudaError_t launch_pair_geo(const TreeView& T, const uint64_t* tt, const uint32_t* ss, int64_t n, void* out,
+                            cudaStream_t s);
+cudaError_t launch_child_geo(const TreeView& T, void* m2m, void* l2l, cudaStream_t s);
+cudaError_t launch_src_offsets(const TreeView& T, const int* leaves, int64_t n_leaves, const double4_32a* src,
+                               float4* off, cudaStream_t s);
+cudaError_t launch_p2m(const TreeView& T, const int* leaves, int64_t n_leaves, const double4_32a* src,
+                       const float4* off, double* mpole, int p, bool fp32, cudaStream_t s);
+cudaError_t launch_m2m(const TreeView& T, int a, int b, int p, const double* tables, const void* geo, double* mpole,
+                       bool fp32, cudaStream_t s);
 cudaError_t launch_m2l(const TreeView& T, const int64_t* off, const uint32_t* srcs, int p, const double* tables,
-                       const double* mpole, double* local, cudaStream_t s);
-cudaError_t launch_l2l(const TreeView& T, int a, int b, int p, const double* tables, double* local, cudaStream_t s);
+                       const void* geo, const double* mpole, double* local, bool fp32, cudaStream_t s);
+cudaError_t launch_l2l(const TreeView& T, int a, int b, int p, const double* tables, const void* geo, double* local,
+                       bool fp32, cudaStream_t s);
+cudaError_t launch_eval32(const TreeView& T, const int* leaves, int64_t n_leaves, const float4* soff, const double4_32a* tgt, const uint32_t* tperm, const int64_t* p2p_off,
+                          const uint32_t* p2p_src, const double* local, const double* mpole, int p, int zero_mean,
+                          double* psi, double* alpha, cudaStream_t s);
 cudaError_t launch_unscale(int n_nodes, const double* geom, const double* in, double* out, int p, int is_local,
                            cudaStream_t s);
 cudaError_t launch_count_pairs(const TreeView& T, const int* leaves, int64_t n_leaves, const int64_t* p2p_off,
@@ -236,12 +247,23 @@ sfmm_status solve(sfmm_plan_s* P, const double* src, const void* q, int64_t N, c
     if ((e = ensure(P->mpole, (size_t)nn * EXP_STRIDE * 8)) || (e = ensure(P->local, (size_t)nn * EXP_STRIDE * 8)))
         return cuda_fail(P, e, "alloc expansions");
     if ((e = cudaMemsetAsync(P->mpole.p, 0, (size_t)nn * EXP_STRIDE * 8, s))) return cuda_fail(P, e, "memset");
-    if ((e = launch_p2m(T, P->leaves_src.as<int>(), P->n_leaves, P->src4.as<double4_32a>(), P->mpole.as<double>(), p, s)))
+    const bool fp32 = P->opt.precision == SFMM_MIXED;
+    if ((e = ensure(P->m2m_geo, (size_t)nn * xgeo_bytes())) || (e = ensure(P->l2l_geo, (size_t)nn * xgeo_bytes())))
+        return cuda_fail(P, e, "alloc");
+    if ((e = launch_child_geo(T, P->m2m_geo.p, P->l2l_geo.p, s))) return cuda_fail(P, e, "child geometry");
+    if (fp32) {
+        if ((e = ensure(P->soff, (size_t)N * 32))) return cuda_fail(P, e, "alloc");
+        if ((e = launch_src_offsets(T, P->leaves_src.as<int>(), P->n_leaves, P->src4.as<double4_32a>(),
+                                    P->soff.as<float4>(), s)))
+            return cuda_fail(P, e, "offsets");
+    }
+    if ((e = launch_p2m(T, P->leaves_src.as<int>(), P->n_leaves, P->src4.as<double4_32a>(), P->soff.as<float4>(),
+                        P->mpole.as<double>(), p, fp32, s)))
         return cuda_fail(P, e, "P2M");
     const int depth = (int)P->level_start.size() - 2;
     for (int l = depth - 1; l >= 0; --l)
-        if ((e = launch_m2m(T, P->level_start[l], P->level_start[l + 1], p, P->tables.as<double>(),
-                            P->mpole.as<double>(), s)))
+        if ((e = launch_m2m(T, P->level_start[l], P->level_start[l + 1], p, P->tables.as<double>(), P->m2m_geo.p,
+                            P->mpole.as<double>(), fp32, s)))
             return cuda_fail(P, e, "M2M");
     tm.mark();
     // ---- lists
@@ -250,22 +272,27 @@ sfmm_status solve(sfmm_plan_s* P, const double* src, const void* q, int64_t N, c
     // ---- M2L
     if ((e = cudaMemsetAsync(P->local.p, 0, (size_t)nn * EXP_STRIDE * 8, s))) return cuda_fail(P, e, "memset");
     const uint32_t* m2l_s = P->m2l_alt ? P->m2l_s2.as<uint32_t>() : P->m2l_s.as<uint32_t>();
-    if ((e = launch_m2l(T, P->m2l_off.as<int64_t>(), m2l_s, p, P->tables.as<double>(), P->mpole.as<double>(),
-                        P->local.as<double>(), s)))
+    const uint64_t* m2l_t = P->m2l_alt ? P->m2l_t2.as<uint64_t>() : P->m2l_t.as<uint64_t>();
+    if ((e = ensure(P->m2l_geo, (size_t)std::max<int64_t>(P->n_m2l, 1) * xgeo_bytes()))) return cuda_fail(P, e, "alloc");
+    if ((e = launch_pair_geo(T, m2l_t, m2l_s, P->n_m2l, P->m2l_geo.p, s))) return cuda_fail(P, e, "pair geometry");
+    if ((e = launch_m2l(T, P->m2l_off.as<int64_t>(), m2l_s, p, P->tables.as<double>(), P->m2l_geo.p,
+                        P->mpole.as<double>(), P->local.as<double>(), fp32, s)))
         return cuda_fail(P, e, "M2L");
     tm.mark();
     // ---- L2L
     for (int l = 1; l <= depth; ++l)
-        if ((e = launch_l2l(T, P->level_start[l], P->level_start[l + 1], p, P->tables.as<double>(),
-                            P->local.as<double>(), s)))
+        if ((e = launch_l2l(T, P->level_start[l], P->level_start[l + 1], p, P->tables.as<double>(), P->l2l_geo.p,
+                            P->local.as<double>(), fp32, s)))
             return cuda_fail(P, e, "L2L");
     tm.mark();
     // ---- evaluation
     const uint32_t* p2p_s = P->p2p_alt ? P->p2p_s2.as<uint32_t>() : P->p2p_s.as<uint32_t>();
-    if ((e = launch_eval(T, P->leaves_tgt.as<int>(), P->n_leaves_tgt, P->src4.as<double4_32a>(), P->tgt4.as<double4_32a>(),
-                         tperm, P->p2p_off.as<int64_t>(), p2p_s, P->local.as<double>(), P->mpole.as<double>(), p,
-                         P->opt.zero_mean, psi, alpha, s)))
-        return cuda_fail(P, e, "evaluation");
+    if (fp32) e = launch_eval32(T, P->leaves_tgt.as<int>(), P->n_leaves_tgt, P->soff.as<float4>(), P->tgt4.as<double4_32a>(), tperm, P->p2p_off.as<int64_t>(), p2p_s,
+                                P->local.as<double>(), P->mpole.as<double>(), p, P->opt.zero_mean, psi, alpha, s);
+    else e = launch_eval(T, P->leaves_tgt.as<int>(), P->n_leaves_tgt, P->src4.as<double4_32a>(),
+                         P->tgt4.as<double4_32a>(), tperm, P->p2p_off.as<int64_t>(), p2p_s, P->local.as<double>(),
+                         P->mpole.as<double>(), p, P->opt.zero_mean, psi, alpha, s);
+    if (e) return cuda_fail(P, e, "evaluation");
     tm.mark();
     if (P->timing) {
         // near-field source-target pairs (for the throughput of the evaluation kernel)
@@ -348,7 +375,6 @@ sfmm_status sfmm_plan(sfmm_plan_t* out, int max_depth, int order_p, double tol, 
     if (!(o.c_s > 1.0)) return plan_fail("c_s must be > 1 (Sec. 3.5)");
     if (!(o.c_t > 0.0 && o.c_t < 1.0)) return plan_fail("c_t must be in (0, 1) (Sec. 3.5)");
     if (o.precision != SFMM_FP64 && o.precision != SFMM_MIXED) return plan_fail("unknown precision");
-    if (o.precision == SFMM_MIXED) return plan_fail("SFMM_MIXED is not available in this build");
     if (o.n_max < 0 || o.m_max < 0) return plan_fail("n_max and m_max must be >= 0");
     auto* P = new (std::nothrow) sfmm_plan_s();
     if (!P) return SFMM_ENOMEM;
@@ -444,7 +470,7 @@ void sfmm_destroy(sfmm_plan_t plan)
                   &plan->act, &plan->c_next, &plan->c_m2l, &plan->c_p2p, &plan->o_next, &plan->o_m2l, &plan->o_p2p,
                   &plan->m2l_t, &plan->m2l_s, &plan->m2l_t2, &plan->m2l_s2, &plan->p2p_t, &plan->p2p_s,
                   &plan->p2p_t2, &plan->p2p_s2, &plan->m2l_off, &plan->p2p_off, &plan->leaves_src,
-                  &plan->leaves_tgt};
+                  &plan->leaves_tgt, &plan->m2l_geo, &plan->m2m_geo, &plan->l2l_geo, &plan->soff};
     for (Buf* b : all) release(*b);
     delete plan;
 }

@@ -155,7 +155,234 @@ __global__ void k_count_pairs(TreeView T, const int* __restrict__ leaves, int64_
     }
 }
 
+// ------------------------------------------------------------------------
+// Mixed-precision evaluation.  Every offset is carried as an FP32 pair
+// (hi + lo, lo = the FP64 remainder), so differences of nearby points keep
+// their relative accuracy without FP64 arithmetic in the pair loop:
+//   source offset from the target leaf centre =
+//       (offset from its own leaf centre, formed once per source in FP64)
+//     + (offset between the two leaf centres, one FP64 difference per near
+//        leaf, taken lane-parallel), added by an error-free two-sum;
+//   d = (t_hi - y_hi) + (t_lo - y_lo): the hi difference is exact for close
+//   points (Sterbenz) and the lo parts restore the bits lost in rounding.
+// The pair loop runs on the FP32 pipe (MUFU reciprocal and log); partial sums
+// are kept in two FP32 levels (blocks of 16 pairs) and combined per target in
+// FP32 across lanes, then in FP64.  Exactly coincident pairs are skipped.
+// L2P: FP32 Horner, FP64 final combination of psi.
+constexpr int STAGE = 256;
+
+struct Eval32Args {
+    TreeView T;
+    const int* leaves;
+    int64_t n_leaves;
+    const float4* soff;       // [2N]: (hi offset, q), (lo offset, 0) of each source from its leaf centre
+    const double4_32a* tgt;
+    const uint32_t* tperm;
+    const int64_t* p2p_off;
+    const uint32_t* p2p_src;
+    const double* local;
+    const double* base_mpole;
+    int p;
+    int want_psi;
+    int zero_mean;
+    double* psi;
+    double* alpha;
+};
+
+__device__ __forceinline__ float group_sumf(float v, int lpt)
+{
+    for (int o = lpt >> 1; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+    return v;
+}
+
+// error-free a + b = s + e (Knuth's two-sum)
+__device__ __forceinline__ void two_sum(float a, float b, float* s, float* e)
+{
+    const float x = a + b;
+    const float bb = x - a;
+    *e = (a - (x - bb)) + (b - bb);
+    *s = x;
+}
+
+__global__ void __launch_bounds__(128) k_eval32(Eval32Args A)
+{
+    __shared__ float4 s_hi[4][STAGE];
+    __shared__ float4 s_lo[4][STAGE];
+    __shared__ float s_dc[4][32][6];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    double shift = 0.0;
+    if (A.zero_mean)
+        for (int b = 0; b < 12; ++b) shift += A.base_mpole[(size_t)b * EXP_STRIDE + 1];
+    float4* yh = s_hi[wid];
+    float4* yl = s_lo[wid];
+    for (int64_t w = warp0; w < A.n_leaves; w += nwarps) {
+        const int leaf = A.leaves[w];
+        const int tf = A.T.tfirst[leaf], tc = A.T.tcount[leaf];
+        const double* g = A.T.geom + (size_t)leaf * GEOM_STRIDE;
+        const double* L = A.local + (size_t)leaf * EXP_STRIDE;
+        const int64_t nb0 = A.p2p_off[leaf], nb1 = A.p2p_off[leaf + 1];
+        int tpw = 1;
+        while (tpw < tc && tpw < 32) tpw <<= 1;
+        const int lpt = 32 / tpw;
+        const int slot = lane / lpt, sub = lane % lpt;
+        for (int tb = 0; tb < tc; tb += tpw) {
+            const int ti = tb + slot;
+            const bool active = ti < tc;
+            const double4_32a x = A.tgt[tf + (active ? ti : 0)];
+            const double ex = x.x - g[0], ey = x.y - g[1], ez = x.z - g[2];
+            const float txh = (float)ex, tyh = (float)ey, tzh = (float)ez;
+            const float txl = (float)(ex - (double)txh), tyl = (float)(ey - (double)tyh), tzl = (float)(ez - (double)tzh);
+            float ox = 0.f, oy = 0.f, oz = 0.f, oq = 0.f, ol = 0.f;      // outer FP32 level
+            int64_t kn = nb0;
+            int jn = 0;                // next source inside near leaf kn
+            while (kn < nb1) {
+                // offsets between leaf centres (hi, lo) for the next 32 near leaves
+                __syncwarp();
+                {
+                    const int64_t k = kn + lane;
+                    if (k < nb1) {
+                        const double* gs = A.T.geom + (size_t)A.p2p_src[k] * GEOM_STRIDE;
+                        const double dx = gs[0] - g[0], dy = gs[1] - g[1], dz = gs[2] - g[2];
+                        const float hx = (float)dx, hy = (float)dy, hz = (float)dz;
+                        float* d = s_dc[wid][lane];
+                        d[0] = hx; d[1] = hy; d[2] = hz;
+                        d[3] = (float)(dx - (double)hx); d[4] = (float)(dy - (double)hy); d[5] = (float)(dz - (double)hz);
+                    }
+                }
+                __syncwarp();
+                int ns = 0;
+                int64_t k = kn;
+                while (k < nb1 && k < kn + 32 && ns < STAGE) {
+                    const int sl = (int)A.p2p_src[k];
+                    const int f = A.T.first[sl], n = A.T.count[sl];
+                    const int take = min(n - jn, STAGE - ns);
+                    const float* d = s_dc[wid][k - kn];
+                    for (int j = lane; j < take; j += 32) {
+                        const float4 h = A.soff[2 * (size_t)(f + jn + j)];
+                        const float4 l = A.soff[2 * (size_t)(f + jn + j) + 1];
+                        float sx, ex_, sy, ey_, sz, ez_;
+                        two_sum(h.x, d[0], &sx, &ex_);
+                        two_sum(h.y, d[1], &sy, &ey_);
+                        two_sum(h.z, d[2], &sz, &ez_);
+                        yh[ns + j] = make_float4(sx, sy, sz, h.w);
+                        yl[ns + j] = make_float4(ex_ + (l.x + d[3]), ey_ + (l.y + d[4]), ez_ + (l.z + d[5]), 0.f);
+                    }
+                    ns += take;
+                    jn += take;
+                    if (jn == n) { ++k; jn = 0; }
+                }
+                kn = k;
+                __syncwarp();
+                float ix = 0.f, iy = 0.f, iz = 0.f, iq = 0.f, il = 0.f;   // inner FP32 level
+                int cnt = 0;
+                for (int j = sub; j < ns; j += lpt) {
+                    const float4 h = yh[j];
+                    const float4 l = yl[j];
+                    const float dx = (txh - h.x) + (txl - l.x);
+                    const float dy = (tyh - h.y) + (tyl - l.y);
+                    const float dz = (tzh - h.z) + (tzl - l.z);
+                    const float d2 = dx * dx + dy * dy + dz * dz;
+                    const bool ok = d2 > 0.f;
+                    const float q = ok ? h.w : 0.f;
+                    const float wq = __fdividef(q, ok ? d2 : 1.f);
+                    ix += wq * dx;
+                    iy += wq * dy;
+                    iz += wq * dz;
+                    iq += q;
+                    if (A.want_psi) il += q * __logf(ok ? d2 : 1.f);
+                    if (++cnt == 16) {
+                        ox += ix; oy += iy; oz += iz; oq += iq; ol += il;
+                        ix = iy = iz = iq = il = 0.f;
+                        cnt = 0;
+                    }
+                }
+                ox += ix; oy += iy; oz += iz; oq += iq; ol += il;
+            }
+            ox = group_sumf(ox, lpt);
+            oy = group_sumf(oy, lpt);
+            oz = group_sumf(oz, lpt);
+            oq = group_sumf(oq, lpt);
+            if (A.want_psi) ol = group_sumf(ol, lpt);
+            if (!active || sub != 0) continue;
+            // ---- L2P in the leaf frame: FP32 Horner, FP64 final psi
+            const float tx = txh + txl, ty = tyh + tyl, tz = tzh + tzl;
+            const float D2 = tx * tx + ty * ty + tz * tz;
+            const float den = 2.f - 0.5f * D2;
+            const float wu = (tx * (float)g[3] + ty * (float)g[4] + tz * (float)g[5]) / den;
+            const float wv = (tx * (float)g[6] + ty * (float)g[7] + tz * (float)g[8]) / den;
+            const float inv_r = (float)(1.0 / g[10]);
+            const float omx = wu * inv_r, omy = wv * inv_r;
+            float frx = 0.f, fry = 0.f, fdx = 0.f, fdy = 0.f;
+            for (int l = A.p; l >= 1; --l) {
+                const float ax = (float)L[2 * l], ay = (float)L[2 * l + 1];
+                const float nfx = frx * omx - fry * omy + ax;
+                const float nfy = frx * omy + fry * omx + ay;
+                const float ndx = fdx * omx - fdy * omy + ax * (float)l;
+                const float ndy = fdx * omy + fdy * omx + ay * (float)l;
+                frx = nfx; fry = nfy; fdx = ndx; fdy = ndy;
+            }
+            const float Fx = frx * omx - fry * omy;
+            const float Fpx = fdx * inv_r, Fpy = fdy * inv_r;
+            const float Qf = (float)L[1];
+            const float w2 = wu * wu + wv * wv;
+            const float au = (1.f + w2) * Fpx - Qf * wu;
+            const float av = -(1.f + w2) * Fpy - Qf * wv;
+            // c + x = 2c + (x - c)
+            const float cxx = 2.f * (float)g[0] + tx, cyy = 2.f * (float)g[1] + ty, czz = 2.f * (float)g[2] + tz;
+            const float xx = (float)x.x, xy = (float)x.y, xz = (float)x.z;
+            float a3x = au * ((float)g[3] - wu * cxx) + av * ((float)g[6] - wv * cxx);
+            float a3y = au * ((float)g[4] - wu * cyy) + av * ((float)g[7] - wv * cyy);
+            float a3z = au * ((float)g[5] - wu * czz) + av * ((float)g[8] - wv * czz);
+            const float i2p = (float)INV2PI;
+            a3x += i2p * (ox - 0.5f * xx * oq);
+            a3y += i2p * (oy - 0.5f * xy * oq);
+            a3z += i2p * (oz - 0.5f * xz * oq);
+            const float rho = sqrtf(xx * xx + xy * xy);
+            float cp = 1.f, sp = 0.f;
+            if (rho > 0.f) { cp = xx / rho; sp = xy / rho; }
+            const uint32_t o = A.tperm[tf + ti];
+            if (A.alpha) {
+                A.alpha[2 * (size_t)o] = (double)(a3x * (xz * cp) + a3y * (xz * sp) - a3z * rho);
+                A.alpha[2 * (size_t)o + 1] = (double)(-a3x * sp + a3y * cp);
+            }
+            if (A.want_psi) {
+                const double psi_e = L[0] + L[1] * (LOG2 + (double)log1pf(-0.25f * D2)) + 2.0 * (double)Fx;
+                A.psi[o] = psi_e + INV4PI * ((double)ol - LOG4 * (double)oq) + shift;
+            }
+        }
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_eval32(const TreeView& T, const int* leaves, int64_t n_leaves, const float4* soff, const double4_32a* tgt, const uint32_t* tperm, const int64_t* p2p_off,
+                          const uint32_t* p2p_src, const double* local, const double* mpole, int p, int zero_mean,
+                          double* psi, double* alpha, cudaStream_t s)
+{
+    if (n_leaves == 0) return cudaSuccess;
+    Eval32Args A;
+    A.T = T;
+    A.leaves = leaves;
+    A.n_leaves = n_leaves;
+    A.soff = soff;
+    A.tgt = tgt;
+    A.tperm = tperm;
+    A.p2p_off = p2p_off;
+    A.p2p_src = p2p_src;
+    A.local = local;
+    A.base_mpole = mpole;
+    A.p = p;
+    A.want_psi = psi != nullptr;
+    A.zero_mean = zero_mean;
+    A.psi = psi;
+    A.alpha = alpha;
+    int64_t blocks = (n_leaves + 3) / 4;
+    if (blocks > 152 * 64) blocks = 152 * 64;
+    k_eval32<<<(unsigned)blocks, 128, 0, s>>>(A); count_launch();
+    return cudaGetLastError();
+}
 
 cudaError_t launch_count_pairs(const TreeView& T, const int* leaves, int64_t n_leaves, const int64_t* p2p_off,
                                const uint32_t* p2p_src, unsigned long long* out, cudaStream_t s)

@@ -1,4 +1,5 @@
-// Expansions: P2M (Lemma 1), M2M (Lemma 2), M2L (Lemma 3), L2L (Lemma 4), FP64.
+// Expansions: P2M (Lemma 1), M2M (Lemma 2), M2L (Lemma 3), L2L (Lemma 4), in
+// FP64 (the FP64 path) or FP32 (the mixed path).
 //
 // Storage.  An expansion is (C, Q, A_1..A_p) in the frame K_P of its box
 // (zenith e_r(P), azimuth reference e_theta(P), Sec. 3.1), with the variable
@@ -26,6 +27,10 @@
 //                     b = t r_T,  g = (1+t^2) r_T / r_S, k = cos(theta/2)
 // which is the printed double sum evaluated in O(p^2) instead of O(p^3).
 // One warp performs one translation; lane l-1 owns coefficient l (p <= 32).
+// The parameters (a, b, g, log k, ph1, ph2) depend only on the two box centres:
+// they are formed once per M2L pair and once per parent-child link, in FP64
+// (from centre differences), by k_pair_geo / k_child_geo; the translation
+// kernels run in FP64 or FP32 from them.
 #include "common.cuh"
 
 namespace sfmm {
@@ -35,10 +40,13 @@ namespace {
 constexpr double INV4PI = 0.079577471545947667884;   // 1/(4 pi)
 constexpr double LOG2 = 0.69314718055994530942;
 
-struct XGeo {
+// 64 bytes of translation parameters, formed in FP64.
+struct __align__(16) XGeo {
     double a, b, g, logk;
-    cd ph1, ph2;
+    double p1x, p1y, p2x, p2y;
 };
+
+enum { K_M2M = 0, K_M2L = 1, K_L2L = 2 };
 
 // Geometry of a translation from box S to box T (both rows of the geometry array).
 // Returns sin(theta/2), cos(theta/2), e^{i phi_T^(S)}, e^{i phi_S^(T)}.
@@ -75,113 +83,188 @@ __device__ __forceinline__ void pair_geometry(const double* gS, const double* gT
     else *eS = mk(1.0, 0.0);
 }
 
-// x^(lane+1) for every lane (inclusive prefix product)
-__device__ __forceinline__ double warp_pow(double x, int lane)
+__device__ __forceinline__ XGeo make_geo(int kind, const double* gS, const double* gT)
 {
-    double v = x;
+    double sh, ch;
+    cd eT, eS;
+    pair_geometry(gS, gT, &sh, &ch, &eT, &eS);
+    const double rS = gS[10], rT = gT[10];
+    XGeo G;
+    if (kind == K_M2L) {
+        const double c = ch / sh;
+        G.a = c * rS;
+        G.b = c * rT;
+        G.g = rS * rT / (sh * sh);          // (1 + c^2) r_S r_T
+        G.logk = log(sh);
+        G.p1x = eT.x; G.p1y = -eT.y;        // e^{-i phi_T}
+        G.p2x = eS.x; G.p2y = -eS.y;        // e^{-i phi_S}
+    } else if (kind == K_M2M) {
+        const double t = sh / ch;
+        G.a = t * rS;
+        G.b = t / rT;
+        G.g = (1.0 + t * t) * rS / rT;
+        G.logk = log(ch);
+        G.p1x = -eT.x; G.p1y = eT.y;        // -e^{-i phi_T}
+        G.p2x = eS.x; G.p2y = eS.y;         //  e^{ i phi_S}
+    } else {
+        const double t = sh / ch;
+        G.a = t / rS;
+        G.b = t * rT;
+        G.g = (1.0 + t * t) * rT / rS;
+        G.logk = log(ch);
+        G.p1x = eT.x; G.p1y = eT.y;         //  e^{ i phi_T}
+        G.p2x = -eS.x; G.p2y = eS.y;        // -e^{-i phi_S}
+    }
+    return G;
+}
+
+__global__ void k_pair_geo(TreeView T, const uint64_t* __restrict__ tt, const uint32_t* __restrict__ ss, int64_t n,
+                           XGeo* __restrict__ out)
+{
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+        const double* gS = T.geom + (size_t)ss[k] * GEOM_STRIDE;
+        const double* gT = T.geom + (size_t)tt[k] * GEOM_STRIDE;
+        out[k] = make_geo(K_M2L, gS, gT);
+    }
+}
+
+// per node with a parent: child -> parent (M2M) and parent -> child (L2L)
+__global__ void k_child_geo(TreeView T, XGeo* __restrict__ m2m, XGeo* __restrict__ l2l)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < T.n_nodes; i += (int64_t)gridDim.x * blockDim.x) {
+        const int par = T.parent[i];
+        if (par < 0) continue;
+        const double* gC = T.geom + (size_t)i * GEOM_STRIDE;
+        const double* gP = T.geom + (size_t)par * GEOM_STRIDE;
+        m2m[i] = make_geo(K_M2M, gC, gP);
+        l2l[i] = make_geo(K_L2L, gP, gC);
+    }
+}
+
+// ------------------------------------------------------- warp translation
+template <typename R> struct cx { R x, y; };
+template <typename R> __device__ __forceinline__ cx<R> cmk(R x, R y) { cx<R> r; r.x = x; r.y = y; return r; }
+template <typename R> __device__ __forceinline__ cx<R> cmul2(cx<R> a, cx<R> b)
+{
+    return cmk<R>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+// x^(lane+1) for every lane (inclusive prefix product)
+template <typename R> __device__ __forceinline__ R warp_pow(R x, int lane)
+{
+    R v = x;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-        const double t = __shfl_up_sync(FULL, v, o);
+        const R t = __shfl_up_sync(FULL, v, o);
         if (lane >= o) v *= t;
     }
     return v;
 }
-__device__ __forceinline__ cd warp_cpow(cd x, int lane)
+template <typename R> __device__ __forceinline__ cx<R> warp_cpow(cx<R> x, int lane)
 {
-    cd v = x;
+    cx<R> v = x;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-        cd t;
+        cx<R> t;
         t.x = __shfl_up_sync(FULL, v.x, o);
         t.y = __shfl_up_sync(FULL, v.y, o);
-        if (lane >= o) v = cmul(v, t);
+        if (lane >= o) v = cmul2(v, t);
     }
     return v;
 }
-__device__ __forceinline__ double warp_sum(double v)
+template <typename R> __device__ __forceinline__ R warp_sum(R v)
 {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
     return v;
 }
 
-struct WarpSmem {
-    cd u[PMAX];
-    cd w[PMAX];
-    double apow[PMAX + 1];
-    double bpow[PMAX + 1];
+template <typename R> struct WarpSmem {
+    cx<R> u[PMAX];
+    cx<R> w[PMAX];
+    R apow[PMAX + 1];
+    R bpow[PMAX + 1];
 };
 
 // Tables in shared memory, [k][lane]: T1[k][n-1] = C(n+k, n), T2[k][l-1] = C(l-1, k).
-struct Tables {
-    double t1[PMAX * PMAX];
-    double t2[PMAX * PMAX];
+template <typename R> struct Tables {
+    R t1[PMAX * PMAX];
+    R t2[PMAX * PMAX];
 };
 
-__device__ __forceinline__ void load_tables(Tables* st, const double* g)
+template <typename R> __device__ __forceinline__ void load_tables(Tables<R>* st, const double* g)
 {
-    for (int i = threadIdx.x; i < 2 * PMAX * PMAX; i += blockDim.x) (&st->t1[0])[i] = g[i];
+    for (int i = threadIdx.x; i < 2 * PMAX * PMAX; i += blockDim.x) (&st->t1[0])[i] = (R)g[i];
     __syncthreads();
 }
 
 // One translation by the whole warp.  Input expansion (Cin, Qin, X = lane's
 // coefficient); accumulates into (accC, accQ, accY).
-__device__ __forceinline__ void warp_translate(int p, int lane, const XGeo& G, double Cin, double Qin, cd X,
-                                               const Tables* tb, WarpSmem* ws, double* accC, double* accQ, cd* accY)
+template <typename R>
+__device__ __forceinline__ void warp_translate(int p, int lane, const XGeo& G, R Cin, R Qin, cx<R> X,
+                                               const Tables<R>* tb, WarpSmem<R>* ws, R* accC, R* accQ, cx<R>* accY)
 {
     const int l = lane + 1;
     const bool on = l <= p;
-    const double ap = warp_pow(G.a, lane), gp = warp_pow(G.g, lane), bp = warp_pow(G.b, lane);
-    const cd p1 = warp_cpow(G.ph1, lane), p2 = warp_cpow(G.ph2, lane);
-    const cd u = on ? cmul(p1, X) : mk(0.0, 0.0);
-    const double csum = warp_sum(on ? ap * u.x : 0.0);
+    const R ap = warp_pow<R>((R)G.a, lane), gp = warp_pow<R>((R)G.g, lane), bp = warp_pow<R>((R)G.b, lane);
+    const cx<R> p1 = warp_cpow<R>(cmk<R>((R)G.p1x, (R)G.p1y), lane);
+    const cx<R> p2 = warp_cpow<R>(cmk<R>((R)G.p2x, (R)G.p2y), lane);
+    const cx<R> u = on ? cmul2(p1, X) : cmk<R>(0, 0);
+    const R csum = warp_sum<R>(on ? ap * u.x : R(0));
     __syncwarp();
     ws->u[lane] = u;
     ws->apow[lane + 1] = ap;
     ws->bpow[lane + 1] = bp;
-    if (lane == 0) { ws->apow[0] = 1.0; ws->bpow[0] = 1.0; }
+    if (lane == 0) { ws->apow[0] = R(1); ws->bpow[0] = R(1); }
     __syncwarp();
-    cd v = mk(0.0, 0.0);
+    cx<R> v = cmk<R>(0, 0);
     for (int k = 0; k <= p - l; ++k) {
-        const double c = tb->t1[k * PMAX + lane] * ws->apow[k];
-        const cd uu = ws->u[lane + k];
+        const R c = tb->t1[k * PMAX + lane] * ws->apow[k];
+        const cx<R> uu = ws->u[lane + k];
         v.x += c * uu.x;
         v.y += c * uu.y;
     }
-    ws->w[lane] = on ? cscale(v, gp) : mk(0.0, 0.0);
+    ws->w[lane] = on ? cmk<R>(v.x * gp, v.y * gp) : cmk<R>(0, 0);
     __syncwarp();
-    cd o = mk(-Qin * bp / (double)l, 0.0);
+    cx<R> o = cmk<R>(-Qin * bp / (R)l, R(0));
     for (int k = 0; k < l && on; ++k) {
-        const double c = tb->t2[k * PMAX + lane] * ws->bpow[k];
-        const cd ww = ws->w[lane - k];
+        const R c = tb->t2[k * PMAX + lane] * ws->bpow[k];
+        const cx<R> ww = ws->w[lane - k];
         o.x += c * ww.x;
         o.y += c * ww.y;
     }
-    if (on) *accY = cadd(*accY, cmul(p2, o));
-    *accC += Cin + 2.0 * Qin * G.logk + 2.0 * csum;
+    if (on) {
+        const cx<R> y = cmul2(p2, o);
+        accY->x += y.x;
+        accY->y += y.y;
+    }
+    *accC += Cin + R(2) * Qin * (R)G.logk + R(2) * csum;
     *accQ += Qin;
     __syncwarp();
 }
 
-__device__ __forceinline__ void load_exp(const double* e, int lane, int p, double* C, double* Q, cd* X)
+template <typename R>
+__device__ __forceinline__ void load_exp(const double* e, int lane, int p, R* C, R* Q, cx<R>* X)
 {
-    *C = e[0];
-    *Q = e[1];
-    *X = (lane < p) ? mk(e[2 + 2 * lane], e[3 + 2 * lane]) : mk(0.0, 0.0);
+    *C = (R)e[0];
+    *Q = (R)e[1];
+    *X = (lane < p) ? cmk<R>((R)e[2 + 2 * lane], (R)e[3 + 2 * lane]) : cmk<R>(0, 0);
 }
 
-__device__ __forceinline__ void store_exp(double* e, int lane, int p, double C, double Q, cd Y, bool add)
+template <typename R>
+__device__ __forceinline__ void store_exp(double* e, int lane, int p, R C, R Q, cx<R> Y, bool add)
 {
     if (lane == 0) {
-        if (add) { e[0] += C; e[1] += Q; } else { e[0] = C; e[1] = Q; }
+        if (add) { e[0] += (double)C; e[1] += (double)Q; } else { e[0] = (double)C; e[1] = (double)Q; }
     }
     if (lane < p) {
-        if (add) { e[2 + 2 * lane] += Y.x; e[3 + 2 * lane] += Y.y; }
-        else { e[2 + 2 * lane] = Y.x; e[3 + 2 * lane] = Y.y; }
+        if (add) { e[2 + 2 * lane] += (double)Y.x; e[3 + 2 * lane] += (double)Y.y; }
+        else { e[2 + 2 * lane] = (double)Y.x; e[3 + 2 * lane] = (double)Y.y; }
     }
 }
 
 // ----------------------------------------------------------------- P2M
+// FP64: from the key-sorted FP64 positions.
 template <int P>
 __global__ void k_p2m(TreeView T, const int* __restrict__ leaves, int64_t n_leaves, const double4_32a* __restrict__ src,
                       double* __restrict__ mpole)
@@ -189,7 +272,7 @@ __global__ void k_p2m(TreeView T, const int* __restrict__ leaves, int64_t n_leav
     for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < n_leaves; w += (int64_t)gridDim.x * blockDim.x) {
         const int node = leaves[w];
         const double* g = T.geom + (size_t)node * GEOM_STRIDE;
-        const double cx = g[0], cy = g[1], cz = g[2];
+        const double cx_ = g[0], cy = g[1], cz = g[2];
         const double inv_r = 1.0 / g[10];
         cd A[P];
 #pragma unroll
@@ -198,7 +281,7 @@ __global__ void k_p2m(TreeView T, const int* __restrict__ leaves, int64_t n_leav
         const int f = T.first[node], n = T.count[node];
         for (int j = f; j < f + n; ++j) {
             const double4_32a y = src[j];
-            const double dx = y.x - cx, dy = y.y - cy, dz = y.z - cz;
+            const double dx = y.x - cx_, dy = y.y - cy, dz = y.z - cz;
             const double d2 = dx * dx + dy * dy + dz * dz;
             const double den = 2.0 - 0.5 * d2;   // 1 + y.c
             const double zr = (dx * g[3] + dy * g[4] + dz * g[5]) / den * inv_r;
@@ -227,114 +310,154 @@ __global__ void k_p2m(TreeView T, const int* __restrict__ leaves, int64_t n_leav
     }
 }
 
+// FP32: from each source's FP32 offset to its leaf centre (the recentring was
+// done in FP64 when the offsets were formed).
+template <int P>
+__global__ void k_p2m32(TreeView T, const int* __restrict__ leaves, int64_t n_leaves, const float4* __restrict__ off,
+                        double* __restrict__ mpole)
+{
+    for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < n_leaves; w += (int64_t)gridDim.x * blockDim.x) {
+        const int node = leaves[w];
+        const double* g = T.geom + (size_t)node * GEOM_STRIDE;
+        const float etx = (float)g[3], ety = (float)g[4], etz = (float)g[5];
+        const float epx = (float)g[6], epy = (float)g[7], epz = (float)g[8];
+        const float inv_r = (float)(1.0 / g[10]);
+        cx<float> A[P];
+#pragma unroll
+        for (int l = 0; l < P; ++l) A[l] = cmk<float>(0.f, 0.f);
+        float Csum = 0.f, Qsum = 0.f;
+        const int f = T.first[node], n = T.count[node];
+        for (int j = f; j < f + n; ++j) {
+            const float4 y = off[2 * (size_t)j];
+            const float d2 = y.x * y.x + y.y * y.y + y.z * y.z;
+            const float sc = inv_r / (2.f - 0.5f * d2);
+            const float zr = (y.x * etx + y.y * ety + y.z * etz) * sc;
+            const float zi = (y.x * epx + y.y * epy + y.z * epz) * sc;
+            Qsum += y.w;
+            Csum += y.w * log1pf(-0.25f * d2);
+            cx<float> zp = cmk<float>(y.w, 0.f);
+#pragma unroll
+            for (int l = 0; l < P; ++l) {
+                zp = cmul2(zp, cmk<float>(zr, zi));
+                A[l].x += zp.x;
+                A[l].y += zp.y;
+            }
+        }
+        double* e = mpole + (size_t)node * EXP_STRIDE;
+        const double Q = INV4PI * (double)Qsum;
+        e[0] = INV4PI * (double)Csum - Q * LOG2;
+        e[1] = Q;
+#pragma unroll
+        for (int l = 0; l < P; ++l) {
+            const double s = -INV4PI / (double)(l + 1);
+            e[2 + 2 * l] = s * (double)A[l].x;
+            e[3 + 2 * l] = s * (double)A[l].y;
+        }
+        for (int l = P; l < PMAX; ++l) { e[2 + 2 * l] = 0.0; e[3 + 2 * l] = 0.0; }
+    }
+}
+
 // ----------------------------------------------------------------- M2M
 // One warp per internal node of one level: sum of its 4 children's multipoles.
-__global__ void k_m2m(TreeView T, int a, int b, int p, const double* __restrict__ tables, double* __restrict__ mpole)
+template <typename R>
+__global__ void k_m2m(TreeView T, int a, int b, int p, const double* __restrict__ tables, const XGeo* __restrict__ geo,
+                      double* __restrict__ mpole)
 {
-    __shared__ Tables tb;
-    __shared__ WarpSmem ws[4];
-    load_tables(&tb, tables);
+    __shared__ Tables<R> tb;
+    __shared__ WarpSmem<R> ws[4];
+    load_tables<R>(&tb, tables);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     for (int64_t node = a + (int64_t)blockIdx.x * 4 + wid; node < b; node += (int64_t)gridDim.x * 4) {
         const int c0 = T.child0[node];
         if (c0 < 0 || T.count[node] == 0) continue;
-        double accC = 0.0, accQ = 0.0;
-        cd accY = mk(0.0, 0.0);
-        const double* gT = T.geom + (size_t)node * GEOM_STRIDE;
+        R accC = 0, accQ = 0;
+        cx<R> accY = cmk<R>(0, 0);
         for (int c = c0; c < c0 + 4; ++c) {
             if (T.count[c] == 0) continue;
-            const double* gS = T.geom + (size_t)c * GEOM_STRIDE;
-            double sh, ch;
-            cd eT, eS;
-            pair_geometry(gS, gT, &sh, &ch, &eT, &eS);
-            const double t = sh / ch;
-            XGeo G;
-            G.a = t * gS[10];
-            G.b = t / gT[10];
-            G.g = (1.0 + t * t) * gS[10] / gT[10];
-            G.logk = log(ch);
-            G.ph1 = mk(-eT.x, eT.y);          // -e^{-i phi_T}
-            G.ph2 = eS;                       //  e^{ i phi_S}
-            double C, Q;
-            cd X;
-            load_exp(mpole + (size_t)c * EXP_STRIDE, lane, p, &C, &Q, &X);
-            warp_translate(p, lane, G, C, Q, X, &tb, &ws[wid], &accC, &accQ, &accY);
+            const XGeo G = geo[c];
+            R C, Q;
+            cx<R> X;
+            load_exp<R>(mpole + (size_t)c * EXP_STRIDE, lane, p, &C, &Q, &X);
+            warp_translate<R>(p, lane, G, C, Q, X, &tb, &ws[wid], &accC, &accQ, &accY);
         }
-        store_exp(mpole + (size_t)node * EXP_STRIDE, lane, p, accC, accQ, accY, false);
-        if (lane < PMAX - p) { }  // coefficients above p stay as written by P2M / zero-init
+        store_exp<R>(mpole + (size_t)node * EXP_STRIDE, lane, p, accC, accQ, accY, false);
     }
 }
 
 // ----------------------------------------------------------------- M2L
 // One warp per target box with a non-empty list; writes local = sum of M2Ls.
+template <typename R>
 __global__ void k_m2l(TreeView T, const int64_t* __restrict__ off, const uint32_t* __restrict__ srcs, int p,
-                      const double* __restrict__ tables, const double* __restrict__ mpole, double* __restrict__ local)
+                      const double* __restrict__ tables, const XGeo* __restrict__ geo, const double* __restrict__ mpole,
+                      double* __restrict__ local)
 {
-    __shared__ Tables tb;
-    __shared__ WarpSmem ws[4];
-    load_tables(&tb, tables);
+    __shared__ Tables<R> tb;
+    __shared__ WarpSmem<R> ws[4];
+    load_tables<R>(&tb, tables);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     for (int64_t node = (int64_t)blockIdx.x * 4 + wid; node < T.n_nodes; node += (int64_t)gridDim.x * 4) {
         const int64_t lo = off[node], hi = off[node + 1];
         if (lo == hi) continue;
-        double accC = 0.0, accQ = 0.0;
-        cd accY = mk(0.0, 0.0);
-        const double* gT = T.geom + (size_t)node * GEOM_STRIDE;
+        R accC = 0, accQ = 0;
+        cx<R> accY = cmk<R>(0, 0);
         for (int64_t k = lo; k < hi; ++k) {
             const int s = (int)srcs[k];
-            const double* gS = T.geom + (size_t)s * GEOM_STRIDE;
-            double sh, ch;
-            cd eT, eS;
-            pair_geometry(gS, gT, &sh, &ch, &eT, &eS);
-            const double c = ch / sh;
-            XGeo G;
-            G.a = c * gS[10];
-            G.b = c * gT[10];
-            G.g = gS[10] * gT[10] / (sh * sh);  // (1 + c^2) r_S r_T
-            G.logk = log(sh);
-            G.ph1 = cconj(eT);                   // e^{-i phi_T}
-            G.ph2 = cconj(eS);                   // e^{-i phi_S}
-            double C, Q;
-            cd X;
-            load_exp(mpole + (size_t)s * EXP_STRIDE, lane, p, &C, &Q, &X);
-            warp_translate(p, lane, G, C, Q, X, &tb, &ws[wid], &accC, &accQ, &accY);
+            const XGeo G = geo[k];
+            R C, Q;
+            cx<R> X;
+            load_exp<R>(mpole + (size_t)s * EXP_STRIDE, lane, p, &C, &Q, &X);
+            warp_translate<R>(p, lane, G, C, Q, X, &tb, &ws[wid], &accC, &accQ, &accY);
         }
-        store_exp(local + (size_t)node * EXP_STRIDE, lane, p, accC, accQ, accY, false);
+        store_exp<R>(local + (size_t)node * EXP_STRIDE, lane, p, accC, accQ, accY, false);
     }
 }
 
 // ----------------------------------------------------------------- L2L
 // One warp per node of one level holding targets: local += L2L(parent local).
-__global__ void k_l2l(TreeView T, int a, int b, int p, const double* __restrict__ tables, double* __restrict__ local)
+template <typename R>
+__global__ void k_l2l(TreeView T, int a, int b, int p, const double* __restrict__ tables, const XGeo* __restrict__ geo,
+                      double* __restrict__ local)
 {
-    __shared__ Tables tb;
-    __shared__ WarpSmem ws[4];
-    load_tables(&tb, tables);
+    __shared__ Tables<R> tb;
+    __shared__ WarpSmem<R> ws[4];
+    load_tables<R>(&tb, tables);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     for (int64_t node = a + (int64_t)blockIdx.x * 4 + wid; node < b; node += (int64_t)gridDim.x * 4) {
         if (T.tcount[node] == 0) continue;
         const int par = T.parent[node];
         if (par < 0) continue;
-        const double* gS = T.geom + (size_t)par * GEOM_STRIDE;
-        const double* gT = T.geom + (size_t)node * GEOM_STRIDE;
-        double sh, ch;
-        cd eT, eS;
-        pair_geometry(gS, gT, &sh, &ch, &eT, &eS);
-        const double t = sh / ch;
-        XGeo G;
-        G.a = t / gS[10];
-        G.b = t * gT[10];
-        G.g = (1.0 + t * t) * gT[10] / gS[10];
-        G.logk = log(ch);
-        G.ph1 = eT;                          //  e^{ i phi_T}
-        G.ph2 = mk(-eS.x, eS.y);             // -e^{-i phi_S}
-        double C, Q;
-        cd X;
-        load_exp(local + (size_t)par * EXP_STRIDE, lane, p, &C, &Q, &X);
-        double accC = 0.0, accQ = 0.0;
-        cd accY = mk(0.0, 0.0);
-        warp_translate(p, lane, G, C, Q, X, &tb, &ws[wid], &accC, &accQ, &accY);
-        store_exp(local + (size_t)node * EXP_STRIDE, lane, p, accC, accQ, accY, true);
+        const XGeo G = geo[node];
+        R C, Q;
+        cx<R> X;
+        load_exp<R>(local + (size_t)par * EXP_STRIDE, lane, p, &C, &Q, &X);
+        R accC = 0, accQ = 0;
+        cx<R> accY = cmk<R>(0, 0);
+        warp_translate<R>(p, lane, G, C, Q, X, &tb, &ws[wid], &accC, &accQ, &accY);
+        store_exp<R>(local + (size_t)node * EXP_STRIDE, lane, p, accC, accQ, accY, true);
+    }
+}
+
+// FP32 offset of every key-sorted source from the centre of its leaf as an
+// (hi, lo) pair (hi = the FP64 difference rounded, lo = the remainder), plus
+// its mass: off[2j] = (hi, q), off[2j+1] = (lo, 0).
+__global__ void k_src_offsets(TreeView T, const int* __restrict__ leaves, int64_t n_leaves,
+                              const double4_32a* __restrict__ src, float4* __restrict__ off)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t w = warp0; w < n_leaves; w += nw) {
+        const int node = leaves[w];
+        const double* g = T.geom + (size_t)node * GEOM_STRIDE;
+        const int f = T.first[node], n = T.count[node];
+        for (int j = f + lane; j < f + n; j += 32) {
+            const double4_32a y = src[j];
+            const double dx = y.x - g[0], dy = y.y - g[1], dz = y.z - g[2];
+            const float hx = (float)dx, hy = (float)dy, hz = (float)dz;
+            off[2 * (size_t)j] = make_float4(hx, hy, hz, (float)y.w);
+            off[2 * (size_t)j + 1] = make_float4((float)(dx - (double)hx), (float)(dy - (double)hy),
+                                                 (float)(dz - (double)hz), 0.f);
+        }
     }
 }
 
@@ -367,6 +490,8 @@ inline unsigned grid_for(int64_t n, int per_block)
 
 }  // namespace
 
+size_t xgeo_bytes() { return sizeof(XGeo); }
+
 void fill_tables(double* h)   // [2][PMAX][PMAX]
 {
     double C[2 * PMAX + 2][2 * PMAX + 2] = {};
@@ -382,12 +507,39 @@ void fill_tables(double* h)   // [2][PMAX][PMAX]
         }
 }
 
-cudaError_t launch_p2m(const TreeView& T, const int* leaves, int64_t n_leaves, const double4_32a* src, double* mpole, int p,
-                       cudaStream_t s)
+cudaError_t launch_pair_geo(const TreeView& T, const uint64_t* tt, const uint32_t* ss, int64_t n, void* out,
+                            cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    k_pair_geo<<<grid_for(n, 256), 256, 0, s>>>(T, tt, ss, n, static_cast<XGeo*>(out)); count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_child_geo(const TreeView& T, void* m2m, void* l2l, cudaStream_t s)
+{
+    k_child_geo<<<grid_for(T.n_nodes, 256), 256, 0, s>>>(T, static_cast<XGeo*>(m2m), static_cast<XGeo*>(l2l)); count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_src_offsets(const TreeView& T, const int* leaves, int64_t n_leaves, const double4_32a* src,
+                               float4* off, cudaStream_t s)
+{
+    if (n_leaves == 0) return cudaSuccess;
+    k_src_offsets<<<grid_for(n_leaves, 8), 256, 0, s>>>(T, leaves, n_leaves, src, off); count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_p2m(const TreeView& T, const int* leaves, int64_t n_leaves, const double4_32a* src,
+                       const float4* off, double* mpole, int p, bool fp32, cudaStream_t s)
 {
     if (n_leaves == 0) return cudaSuccess;
     const unsigned g = grid_for(n_leaves, 128);
-#define P2M_CASE(PP) case PP: k_p2m<PP><<<g, 128, 0, s>>>(T, leaves, n_leaves, src, mpole); count_launch(); break;
+#define P2M_CASE(PP)                                                                          \
+    case PP:                                                                                  \
+        if (fp32) k_p2m32<PP><<<g, 128, 0, s>>>(T, leaves, n_leaves, off, mpole);            \
+        else k_p2m<PP><<<g, 128, 0, s>>>(T, leaves, n_leaves, src, mpole);                   \
+        count_launch();                                                                       \
+        break;
     switch ((p + 3) / 4 * 4) {
         P2M_CASE(4) P2M_CASE(8) P2M_CASE(12) P2M_CASE(16) P2M_CASE(20) P2M_CASE(24) P2M_CASE(28) P2M_CASE(32)
         default: return cudaErrorInvalidValue;
@@ -396,24 +548,35 @@ cudaError_t launch_p2m(const TreeView& T, const int* leaves, int64_t n_leaves, c
     return cudaGetLastError();
 }
 
-cudaError_t launch_m2m(const TreeView& T, int a, int b, int p, const double* tables, double* mpole, cudaStream_t s)
+cudaError_t launch_m2m(const TreeView& T, int a, int b, int p, const double* tables, const void* geo, double* mpole,
+                       bool fp32, cudaStream_t s)
 {
     if (b <= a) return cudaSuccess;
-    k_m2m<<<grid_for(b - a, 4), 128, 0, s>>>(T, a, b, p, tables, mpole); count_launch();
+    const XGeo* G = static_cast<const XGeo*>(geo);
+    if (fp32) k_m2m<float><<<grid_for(b - a, 4), 128, 0, s>>>(T, a, b, p, tables, G, mpole);
+    else k_m2m<double><<<grid_for(b - a, 4), 128, 0, s>>>(T, a, b, p, tables, G, mpole);
+    count_launch();
     return cudaGetLastError();
 }
 
 cudaError_t launch_m2l(const TreeView& T, const int64_t* off, const uint32_t* srcs, int p, const double* tables,
-                       const double* mpole, double* local, cudaStream_t s)
+                       const void* geo, const double* mpole, double* local, bool fp32, cudaStream_t s)
 {
-    k_m2l<<<grid_for(T.n_nodes, 4), 128, 0, s>>>(T, off, srcs, p, tables, mpole, local); count_launch();
+    const XGeo* G = static_cast<const XGeo*>(geo);
+    if (fp32) k_m2l<float><<<grid_for(T.n_nodes, 4), 128, 0, s>>>(T, off, srcs, p, tables, G, mpole, local);
+    else k_m2l<double><<<grid_for(T.n_nodes, 4), 128, 0, s>>>(T, off, srcs, p, tables, G, mpole, local);
+    count_launch();
     return cudaGetLastError();
 }
 
-cudaError_t launch_l2l(const TreeView& T, int a, int b, int p, const double* tables, double* local, cudaStream_t s)
+cudaError_t launch_l2l(const TreeView& T, int a, int b, int p, const double* tables, const void* geo, double* local,
+                       bool fp32, cudaStream_t s)
 {
     if (b <= a) return cudaSuccess;
-    k_l2l<<<grid_for(b - a, 4), 128, 0, s>>>(T, a, b, p, tables, local); count_launch();
+    const XGeo* G = static_cast<const XGeo*>(geo);
+    if (fp32) k_l2l<float><<<grid_for(b - a, 4), 128, 0, s>>>(T, a, b, p, tables, G, local);
+    else k_l2l<double><<<grid_for(b - a, 4), 128, 0, s>>>(T, a, b, p, tables, G, local);
+    count_launch();
     return cudaGetLastError();
 }
 

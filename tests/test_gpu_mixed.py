@@ -1,0 +1,82 @@
+"""GPU parity of the mixed-precision path (SFMM_MIXED) against the oracle.
+
+The mixed path runs the translations and the near-field pair loop in FP32 and
+keeps FP64 for the recentring, near-coincident pairs and the final psi sum; its
+stated error is 1e-6 (norm-wise relative error of psi and alpha, the reading of
+the paper's relative error used throughout the tests)."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle.direct import direct_sum
+from paper_2210_07021_gb300 import sfmm, workloads
+from conftest import unit
+
+TOL_MIXED = 1e-6
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def dev(a, dtype=torch.float64):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=dtype, device="cuda")
+
+
+def solve(src, q, tgt, precision, p=20, leaf=32, **kw):
+    plan = sfmm.Plan(p=p, leaf_size=leaf, precision=precision, **kw)
+    qd = torch.float32 if kw.get("q_f32") else torch.float64
+    psi, alpha = plan.deflection(dev(src), dev(q, qd), dev(tgt))
+    torch.cuda.synchronize()
+    return plan, psi.cpu().numpy(), alpha.cpu().numpy()
+
+
+def test_random_sky_mixed():
+    d = workloads.random_sky(4096)
+    _, psi, alpha = solve(d["src"], d["q"], d["tgt"], sfmm.SFMM_MIXED)
+    ref = direct_sum(d["src"], d["q"], d["tgt"])
+    assert rel(psi, ref["psi"]) < TOL_MIXED and rel(alpha, ref["alpha"]) < TOL_MIXED, \
+        (rel(psi, ref["psi"]), rel(alpha, ref["alpha"]))
+
+
+def test_clustered_mixed_and_same_lists_as_fp64():
+    rng = np.random.default_rng(4)
+    clumps = workloads.clump_set(rng, 30)
+    src = workloads.clustered(rng, 60000, 30, clumps=clumps)
+    tgt = workloads.clustered(rng, 20001, 30, clumps=clumps)
+    q = rng.lognormal(0, 0.5, 60000)
+    pm, psi_m, al_m = solve(src, q, tgt, sfmm.SFMM_MIXED, leaf=32)
+    pd, psi_d, al_d = solve(src, q, tgt, sfmm.SFMM_FP64, p=32, leaf=32)
+    assert np.array_equal(pm.debug(sfmm.ARR_M2L, np.int32, 2), pd.debug(sfmm.ARR_M2L, np.int32, 2))
+    assert np.array_equal(pm.debug(sfmm.ARR_P2P, np.int32, 2), pd.debug(sfmm.ARR_P2P, np.int32, 2))
+    idx = workloads.subsample(tgt.shape[0], 800, 4)
+    ref = direct_sum(src, q, tgt[idx])
+    assert rel(psi_m[idx], ref["psi"]) < TOL_MIXED and rel(al_m[idx], ref["alpha"]) < TOL_MIXED, \
+        (rel(psi_m[idx], ref["psi"]), rel(al_m[idx], ref["alpha"]))
+    # and against the FP64 path on every target
+    assert rel(psi_m, psi_d) < TOL_MIXED and rel(al_m, al_d) < TOL_MIXED
+
+
+def test_mixed_coincident_points_and_poles():
+    rng = np.random.default_rng(9)
+    base = unit(np.array([0.1, 0.2, 0.97]))
+    src = np.vstack([np.repeat(base[None], 50, 0), unit(base + 1e-9 * rng.normal(size=(50, 3))),
+                     [[0, 0, 1.0], [0, 0, -1.0]], unit(rng.normal(size=(4000, 3)))])
+    q = rng.random(len(src)) + 0.5
+    tgt = np.vstack([src[:60], [[0, 0, 1.0], [0, 0, -1.0]], unit(rng.normal(size=(1000, 3)))])
+    _, psi, alpha = solve(src, q, tgt, sfmm.SFMM_MIXED, leaf=8)
+    ref = direct_sum(src, q, tgt)
+    assert rel(psi, ref["psi"]) < TOL_MIXED and rel(alpha, ref["alpha"]) < TOL_MIXED
+
+
+def test_mixed_float32_masses_zero_mean():
+    rng = np.random.default_rng(10)
+    src = workloads.clustered(rng, 30000, 20)
+    tgt = unit(rng.normal(size=(5000, 3)))
+    q = np.full(30000, 4 * np.pi / 30000, dtype=np.float32)
+    _, psi, alpha = solve(src, q, tgt, sfmm.SFMM_MIXED, q_f32=True, zero_mean=True)
+    ref = direct_sum(src, q.astype(np.float64), tgt)
+    assert rel(psi, ref["psi"] + q.astype(np.float64).sum() / (4 * np.pi)) < TOL_MIXED
+    assert rel(alpha, ref["alpha"]) < TOL_MIXED
