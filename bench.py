@@ -34,6 +34,9 @@ sys.path.insert(0, ROOT)
 
 METRIC = "sFMM Mpts/s (N=M=1.6e7) FP64 vs mixed precision, at stated relative error"
 FP64_PEAK_DERIVED = 152 * 2 * 2 * 2.07e9   # SMs x FP64 FMA/clk/SM x 2 flop x max SM clock
+FP32_PEAK_DERIVED = 152 * 128 * 2 * 2.07e9  # SMs x FP32 FMA/clk/SM x 2 flop x max SM clock
+# (path name, precision enum value, order p, stated relative error)
+MODES = [("mixed", 1, 16, 1e-6), ("fp64", 0, 32, 1e-10)]
 # algorithmic FP64 flops per near-field pair: d^2 (3 sub, 3 mul, 2 add), 1/d^2
 # (counted as 4), q/d^2 (1), alpha sums (3 mul + 3 add), sum q (1); psi adds the
 # log (counted as 4) and its multiply-add (2)
@@ -49,7 +52,7 @@ def parse():
     ap.add_argument("--impl", default="sfmm", choices=["sfmm", "reference"])
     ap.add_argument("--n", type=int, default=16_000_000, help="N = M")
     ap.add_argument("--clumps", type=int, default=20_000)
-    ap.add_argument("--p", type=int, default=32)
+    ap.add_argument("--modes", default="mixed,fp64", help="paths to run; the first is the headline value")
     ap.add_argument("--leaf", type=int, default=32)
     ap.add_argument("--check", type=int, default=200, help="targets checked against the oracle")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the oracle CPU baseline")
@@ -136,11 +139,12 @@ def oracle_rate(src, q, tgt, budget_s, seed_idx):
     from oracle.direct import direct_sum, threads
     from paper_2210_07021_gb300 import workloads
     q64 = q.astype(np.float64)
-    probe = workloads.subsample(tgt.shape[0], 8, seed_idx, stream=11)
+    n_probe = 2 * threads()
+    probe = workloads.subsample(tgt.shape[0], n_probe, seed_idx, stream=11)
     t0 = time.perf_counter()
     direct_sum(src, q64, tgt[probe])
     t_probe = max(time.perf_counter() - t0, 1e-3)
-    k = int(max(8, min(tgt.shape[0], 8 * budget_s / t_probe)))
+    k = int(max(n_probe, min(tgt.shape[0], n_probe * budget_s / t_probe)))
     idx = workloads.subsample(tgt.shape[0], k, seed_idx, stream=12)
     t0 = time.perf_counter()
     direct_sum(src, q64, tgt[idx])
@@ -156,12 +160,13 @@ def run_reference(args):
     from oracle.direct import direct_sum, threads
     from paper_2210_07021_gb300 import workloads
     src, q, tgt = d["src"], d["q"].astype(np.float64), d["tgt"]
-    probe = workloads.subsample(tgt.shape[0], 4, 3, stream=11)
+    n_probe = 2 * threads()
+    probe = workloads.subsample(tgt.shape[0], n_probe, 3, stream=11)
     t0 = time.perf_counter()
     direct_sum(src, q, tgt[probe])
     t_probe = max(time.perf_counter() - t0, 1e-3)
     per_step_s = min(20.0, 150.0 / max(1, args.steps + args.warmup))
-    k = int(max(4, min(tgt.shape[0], 4 * per_step_s / t_probe)))
+    k = int(max(n_probe, min(tgt.shape[0], n_probe * per_step_s / t_probe)))
     for w in range(args.warmup):
         direct_sum(src, q, tgt[workloads.subsample(tgt.shape[0], k, 3, stream=20 + w)])
     t0 = time.perf_counter()
@@ -199,7 +204,6 @@ def run_sfmm(args):
     src = torch.as_tensor(d["src"], device=dev)
     q = torch.as_tensor(d["q"], device=dev)
     tgt = torch.as_tensor(d["tgt"], device=dev)
-    plan = sfmm.Plan(p=args.p, leaf_size=args.leaf, q_f32=True, n_max=N, m_max=M)
     psi = torch.empty(M, dtype=torch.float64, device=dev)
     alpha = torch.empty((M, 2), dtype=torch.float64, device=dev)
 
@@ -208,93 +212,118 @@ def run_sfmm(args):
             dist.barrier()
         torch.cuda.synchronize()
 
-    for _ in range(args.warmup):
-        plan.deflection(src, q, tgt, psi=psi, alpha=alpha)
-    plan.set_timing(True)
-    stream = torch.cuda.current_stream()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    eval_ms, tot_ms, pairs, launches, phase = [], [], [], 0, np.zeros(8)
-    barrier()
-    with ClockSampler(local) as clk:
-        ev0.record(stream)
-        for _ in range(args.steps):
-            plan.deflection(src, q, tgt, psi=psi, alpha=alpha)
-            st = plan.stats()
-            eval_ms.append(st["ms"][6])
-            pairs.append(st["p2p_interactions"])
-            launches += st["launches"]
-            phase += np.array(st["ms"])
-        ev1.record(stream)
-        barrier()
-    elapsed_ms = ev0.elapsed_time(ev1)
-    if dist:
-        t = torch.tensor([elapsed_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
-    total_pts = M * args.steps * ws
-    value = total_pts / (elapsed_ms / 1e3) / 1e6
-    plan.set_timing(False)
-
-    # end to end through the host-array entry point, pinned buffers
-    e2e = None
-    if not args.no_e2e:
-        hs = torch.empty((N, 3), dtype=torch.float64, pin_memory=True).numpy()
-        hq = torch.empty(N, dtype=torch.float32, pin_memory=True).numpy()
-        ht = torch.empty((M, 3), dtype=torch.float64, pin_memory=True).numpy()
-        hpsi = torch.empty(M, dtype=torch.float64, pin_memory=True).numpy()
-        halpha = torch.empty((M, 2), dtype=torch.float64, pin_memory=True).numpy()
-        hs[:] = d["src"]
-        hq[:] = d["q"]
-        ht[:] = d["tgt"]
-        plan.deflection_host(hs, hq, ht, psi=hpsi, alpha=halpha)
-        barrier()
-        t0 = time.perf_counter()
-        for _ in range(args.steps):
-            plan.deflection_host(hs, hq, ht, psi=hpsi, alpha=halpha)
-        barrier()
-        t_e2e = time.perf_counter() - t0
+    def max_over_ranks(v):
         if dist:
-            t = torch.tensor([t_e2e], device=dev)
+            t = torch.tensor([v], device=dev)
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            t_e2e = float(t.item())
-        e2e = {"value": M * args.steps * ws / t_e2e / 1e6, "unit": "Mpts/s",
-               "h2d_bytes_per_step": int(N * 24 + N * 4 + M * 24), "d2h_bytes_per_step": int(M * 8 + M * 16)}
+            return float(t.item())
+        return v
 
+    wanted = [m for m in MODES if m[0] in args.modes.split(",")]
+    wanted.sort(key=lambda m: args.modes.split(",").index(m[0]))
+    results = {}
+    for name, prec, p, stated in wanted:
+        plan = sfmm.Plan(p=p, leaf_size=args.leaf, precision=prec, q_f32=True, n_max=N, m_max=M)
+        for _ in range(args.warmup):
+            plan.deflection(src, q, tgt, psi=psi, alpha=alpha)
+        plan.set_timing(True)
+        stream = torch.cuda.current_stream()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        eval_ms, pairs, launches, phase = [], [], 0, np.zeros(8)
+        barrier()
+        with ClockSampler(local) as clk:
+            ev0.record(stream)
+            for _ in range(args.steps):
+                plan.deflection(src, q, tgt, psi=psi, alpha=alpha)
+                st = plan.stats()
+                eval_ms.append(st["ms"][6])
+                pairs.append(st["p2p_interactions"])
+                launches += st["launches"]
+                phase += np.array(st["ms"])
+            ev1.record(stream)
+            barrier()
+        elapsed_ms = max_over_ranks(ev0.elapsed_time(ev1))
+        plan.set_timing(False)
+        r = {"precision": name, "p": p, "stated_error": stated,
+             "value": M * args.steps * ws / (elapsed_ms / 1e3) / 1e6, "ms_per_step": elapsed_ms / args.steps,
+             "gpu_launches": int(launches), "eval_ms": float(np.mean(eval_ms)), "pairs": float(np.mean(pairs)),
+             "phase_ms": {k: v / args.steps for k, v in zip(
+                 ["keys_sort", "tree_geometry", "up_pass", "lists", "m2l", "l2l", "evaluation", "total"], phase)},
+             "clocks": clk.summary()}
+        if rank == 0:
+            from oracle.direct import direct_sum
+            idx = workloads.subsample(M, args.check, 3, stream=9)
+            if "ref" not in results:
+                results["ref"] = direct_sum(d["src"], d["q"].astype(np.float64), d["tgt"][idx])
+            ref = results["ref"]
+            r["error_vs_oracle"] = {"psi_rel": rel(psi.cpu().numpy()[idx], ref["psi"]),
+                                    "alpha_rel": rel(alpha.cpu().numpy()[idx], ref["alpha"]),
+                                    "sample": int(idx.size), "norm": "l2 over the sample (relative)"}
+        # end to end through the host-array entry point (headline path only)
+        if not args.no_e2e and name == wanted[0][0]:
+            hs = torch.empty((N, 3), dtype=torch.float64, pin_memory=True).numpy()
+            hq = torch.empty(N, dtype=torch.float32, pin_memory=True).numpy()
+            ht = torch.empty((M, 3), dtype=torch.float64, pin_memory=True).numpy()
+            hpsi = torch.empty(M, dtype=torch.float64, pin_memory=True).numpy()
+            halpha = torch.empty((M, 2), dtype=torch.float64, pin_memory=True).numpy()
+            hs[:] = d["src"]
+            hq[:] = d["q"]
+            ht[:] = d["tgt"]
+            plan.deflection_host(hs, hq, ht, psi=hpsi, alpha=halpha)
+            barrier()
+            t0 = time.perf_counter()
+            for _ in range(args.steps):
+                plan.deflection_host(hs, hq, ht, psi=hpsi, alpha=halpha)
+            barrier()
+            t_e2e = max_over_ranks(time.perf_counter() - t0)
+            r["e2e"] = {"value": M * args.steps * ws / t_e2e / 1e6, "unit": "Mpts/s",
+                        "h2d_bytes_per_step": int(N * 24 + N * 4 + M * 24), "d2h_bytes_per_step": int(M * 8 + M * 16)}
+        results[name] = r
+        plan.close()
     if rank != 0:
         if dist:
             dist.barrier()
         return
-    # accuracy on a seeded sample of targets, against the oracle
-    from oracle.direct import direct_sum
-    idx = workloads.subsample(M, args.check, 3, stream=9)
-    ref = direct_sum(d["src"], d["q"].astype(np.float64), d["tgt"][idx])
-    err = {"psi_rel": rel(psi.cpu().numpy()[idx], ref["psi"]), "alpha_rel": rel(alpha.cpu().numpy()[idx], ref["alpha"]),
-           "sample": int(idx.size), "norm": "l2 over the sample (relative)"}
+    head = results[wanted[0][0]]
     cpu = None
     if ws == 1:
         k, t, cores = oracle_rate(d["src"], d["q"], d["tgt"], args.cpu_seconds, 3)
         cpu = {"value": k / t / 1e6, "unit": "Mpts/s", "cores": cores, "kind": "oracle",
                "sample": f"{k} seeded targets against all {N} sources, FP64 direct sum, {t:.1f} s"}
-    ev_ms = float(np.mean(eval_ms))
-    pairs_mean = float(np.mean(pairs))
-    achieved = pairs_mean * FLOPS_PER_PAIR_PSI / (ev_ms / 1e3)
-    roofline = {"bound": "alu", "kernel": "k_eval (near field + L2P, FP64)", "achieved": achieved / 1e12,
-                "peak": FP64_PEAK_DERIVED / 1e12, "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_DERIVED,
-                "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (FP64 is not in "
-                               "MEASURED_PEAKS.json; a plain FMA loop measured 1.19 TFLOP/s)",
-                "work_per_unit": f"{FLOPS_PER_PAIR_PSI} FP64 flop per near-field pair (1/d^2 and log counted as 4)",
-                "pairs_per_launch": pairs_mean, "launch_ms": ev_ms, "traffic": None}
-    names = ["keys_sort", "tree_geometry", "up_pass", "lists", "m2l", "l2l", "evaluation", "total"]
-    line = {"metric": METRIC, "value": value, "unit": "Mpts/s", "n_gpus": ws, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": d["workload"], "N": N, "M": M, "p": args.p, "leaf_size": args.leaf,
-                       "c_s": 2.0, "c_t": 0.5, "precision": "fp64",
+
+    def roofline_of(r):
+        if r["precision"] == "fp64":
+            peak, bound, kern, src_ = FP64_PEAK_DERIVED, "alu", "k_eval (near field + L2P, FP64)", \
+                "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (not in MEASURED_PEAKS.json; " \
+                "an FMA loop measured 1.19 TFLOP/s)"
+        else:
+            peak, bound, kern, src_ = FP32_PEAK_DERIVED, "alu", "k_eval32 (near field + L2P, FP32 pair loop)", \
+                "derived: 152 SMs x 128 FP32 FMA/clk x 2 flop x 2.07 GHz (not in MEASURED_PEAKS.json; " \
+                "an FMA loop measured 73 TFLOP/s)"
+        ach = r["pairs"] * FLOPS_PER_PAIR_PSI / (r["eval_ms"] / 1e3)
+        return {"bound": bound, "kernel": kern, "achieved": ach / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
+                "frac": ach / peak, "peak_source": src_,
+                "work_per_unit": f"{FLOPS_PER_PAIR_PSI} flop per near-field pair (1/d^2 and log counted as 4)",
+                "pairs_per_launch": r["pairs"], "launch_ms": r["eval_ms"], "traffic": None}
+
+    modes = {}
+    for name, *_ in wanted:
+        r = dict(results[name])
+        r["roofline"] = roofline_of(r)
+        modes[name] = r
+    line = {"metric": METRIC, "value": head["value"], "unit": "Mpts/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64" if head["precision"] == "mixed" else "f64", "data": "synthetic",
+            "config": {"workload": d["workload"], "N": N, "M": M, "precision": head["precision"], "p": head["p"],
+                       "stated_error": head["stated_error"], "leaf_size": args.leaf, "c_s": 2.0, "c_t": 0.5,
                        "l2": "inputs larger than L2 (384 MB of positions each), no flush"},
-            "error_vs_oracle": err, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-            "gpu_launches": int(launches),
-            "phase_ms": {k: v / args.steps for k, v in zip(names, phase)},
-            "clocks": clk.summary()}
+            "error_vs_oracle": head.get("error_vs_oracle"), "roofline": modes[head["precision"]]["roofline"],
+            "cpu_baseline": cpu, "e2e": head.get("e2e"), "gpu_launches": head["gpu_launches"],
+            "phase_ms": head["phase_ms"], "clocks": head["clocks"],
+            "modes": {k: {kk: vv for kk, vv in v.items() if kk not in ("phase_ms",)} for k, v in modes.items()}}
+    if "fp64" in results and head["precision"] != "fp64":
+        line["speedup_vs_fp64"] = head["value"] / results["fp64"]["value"]
     print(json.dumps(line), flush=True)
     if dist:
         dist.barrier()

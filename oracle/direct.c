@@ -56,7 +56,7 @@ int64_t oracle_direct(const double* src, const double* q, int64_t N,
     const double inv4pi = 1.0 / (4.0 * M_PI);
     const double inv2pi = 1.0 / (2.0 * M_PI);
     int64_t skipped = 0;
-#pragma omp parallel for schedule(dynamic, 16) reduction(+:skipped)
+#pragma omp parallel for schedule(dynamic, 1) reduction(+:skipped)
     for (int64_t i = 0; i < M; ++i) {
         const double x0 = tgt[3 * i], x1 = tgt[3 * i + 1], x2 = tgt[3 * i + 2];
         nsum sp = {0, 0}, g0 = {0, 0}, g1 = {0, 0}, g2 = {0, 0};
