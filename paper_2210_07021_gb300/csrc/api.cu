@@ -31,7 +31,11 @@ cudaError_t launch_m2l(const TreeView& T, const int64_t* off, const uint32_t* sr
                        const void* geo, const double* mpole, double* local, bool fp32, cudaStream_t s);
 cudaError_t launch_l2l(const TreeView& T, int a, int b, int p, const double* tables, const void* geo, double* local,
                        bool fp32, cudaStream_t s);
-cudaError_t launch_eval32(const TreeView& T, const int* leaves, int64_t n_leaves, const float4* soff, const double4_32a* tgt, const uint32_t* tperm, const int64_t* p2p_off,
+cudaError_t launch_eval32_prep(const TreeView& T, const int* leaves, int64_t n_leaves, const double4_32a* tgt,
+                               float4* toff, const uint64_t* p2p_t, const uint32_t* p2p_s, int64_t n_p2p, float4* dc,
+                               cudaStream_t s);
+cudaError_t launch_eval32(const TreeView& T, const int* leaves, int64_t n_leaves, const float4* soff,
+                          const float4* toff, const float4* dc, const double4_32a* tgt, const uint32_t* tperm, const int64_t* p2p_off,
                           const uint32_t* p2p_src, const double* local, const double* mpole, int p, int zero_mean,
                           double* psi, double* alpha, cudaStream_t s);
 cudaError_t launch_unscale(int n_nodes, const double* geom, const double* in, double* out, int p, int is_local,
@@ -287,7 +291,16 @@ sfmm_status solve(sfmm_plan_s* P, const double* src, const void* q, int64_t N, c
     tm.mark();
     // ---- evaluation
     const uint32_t* p2p_s = P->p2p_alt ? P->p2p_s2.as<uint32_t>() : P->p2p_s.as<uint32_t>();
-    if (fp32) e = launch_eval32(T, P->leaves_tgt.as<int>(), P->n_leaves_tgt, P->soff.as<float4>(), P->tgt4.as<double4_32a>(), tperm, P->p2p_off.as<int64_t>(), p2p_s,
+    if (fp32) {
+        const uint64_t* p2p_t = P->p2p_alt ? P->p2p_t2.as<uint64_t>() : P->p2p_t.as<uint64_t>();
+        if ((e = ensure(P->toff, (size_t)M * 32)) || (e = ensure(P->dc, (size_t)std::max<int64_t>(P->n_p2p, 1) * 32)))
+            return cuda_fail(P, e, "alloc");
+        if ((e = launch_eval32_prep(T, P->leaves_tgt.as<int>(), P->n_leaves_tgt, P->tgt4.as<double4_32a>(),
+                                    P->toff.as<float4>(), p2p_t, p2p_s, P->n_p2p, P->dc.as<float4>(), s)))
+            return cuda_fail(P, e, "offsets");
+    }
+    if (fp32) e = launch_eval32(T, P->leaves_tgt.as<int>(), P->n_leaves_tgt, P->soff.as<float4>(),
+                                P->toff.as<float4>(), P->dc.as<float4>(), P->tgt4.as<double4_32a>(), tperm, P->p2p_off.as<int64_t>(), p2p_s,
                                 P->local.as<double>(), P->mpole.as<double>(), p, P->opt.zero_mean, psi, alpha, s);
     else e = launch_eval(T, P->leaves_tgt.as<int>(), P->n_leaves_tgt, P->src4.as<double4_32a>(),
                          P->tgt4.as<double4_32a>(), tperm, P->p2p_off.as<int64_t>(), p2p_s, P->local.as<double>(),
@@ -470,7 +483,8 @@ void sfmm_destroy(sfmm_plan_t plan)
                   &plan->act, &plan->c_next, &plan->c_m2l, &plan->c_p2p, &plan->o_next, &plan->o_m2l, &plan->o_p2p,
                   &plan->m2l_t, &plan->m2l_s, &plan->m2l_t2, &plan->m2l_s2, &plan->p2p_t, &plan->p2p_s,
                   &plan->p2p_t2, &plan->p2p_s2, &plan->m2l_off, &plan->p2p_off, &plan->leaves_src,
-                  &plan->leaves_tgt, &plan->m2l_geo, &plan->m2m_geo, &plan->l2l_geo, &plan->soff};
+                  &plan->leaves_tgt, &plan->m2l_geo, &plan->m2m_geo, &plan->l2l_geo, &plan->soff,
+                  &plan->toff, &plan->dc};
     for (Buf* b : all) release(*b);
     delete plan;
 }

@@ -176,6 +176,8 @@ struct Eval32Args {
     const int* leaves;
     int64_t n_leaves;
     const float4* soff;       // [2N]: (hi offset, q), (lo offset, 0) of each source from its leaf centre
+    const float4* toff;       // [2M]: (hi, x.z), (lo, 0) offset of each sorted target from its leaf centre
+    const float4* dc;         // [2 n_p2p]: (hi, 0), (lo, 0) offset of each near leaf's centre from the target leaf's
     const double4_32a* tgt;
     const uint32_t* tperm;
     const int64_t* p2p_off;
@@ -230,10 +232,10 @@ __global__ void __launch_bounds__(128) k_eval32(Eval32Args A)
         for (int tb = 0; tb < tc; tb += tpw) {
             const int ti = tb + slot;
             const bool active = ti < tc;
-            const double4_32a x = A.tgt[tf + (active ? ti : 0)];
-            const double ex = x.x - g[0], ey = x.y - g[1], ez = x.z - g[2];
-            const float txh = (float)ex, tyh = (float)ey, tzh = (float)ez;
-            const float txl = (float)(ex - (double)txh), tyl = (float)(ey - (double)tyh), tzl = (float)(ez - (double)tzh);
+            const size_t tix = (size_t)tf + (active ? ti : 0);
+            const float4 th = A.toff[2 * tix], tl = A.toff[2 * tix + 1];
+            const float txh = th.x, tyh = th.y, tzh = th.z;
+            const float txl = tl.x, tyl = tl.y, tzl = tl.z;
             float ox = 0.f, oy = 0.f, oz = 0.f, oq = 0.f, ol = 0.f;      // outer FP32 level
             int64_t kn = nb0;
             int jn = 0;                // next source inside near leaf kn
@@ -243,12 +245,10 @@ __global__ void __launch_bounds__(128) k_eval32(Eval32Args A)
                 {
                     const int64_t k = kn + lane;
                     if (k < nb1) {
-                        const double* gs = A.T.geom + (size_t)A.p2p_src[k] * GEOM_STRIDE;
-                        const double dx = gs[0] - g[0], dy = gs[1] - g[1], dz = gs[2] - g[2];
-                        const float hx = (float)dx, hy = (float)dy, hz = (float)dz;
+                        const float4 h = A.dc[2 * k], l = A.dc[2 * k + 1];
                         float* d = s_dc[wid][lane];
-                        d[0] = hx; d[1] = hy; d[2] = hz;
-                        d[3] = (float)(dx - (double)hx); d[4] = (float)(dy - (double)hy); d[5] = (float)(dz - (double)hz);
+                        d[0] = h.x; d[1] = h.y; d[2] = h.z;
+                        d[3] = l.x; d[4] = l.y; d[5] = l.z;
                     }
                 }
                 __syncwarp();
@@ -331,6 +331,7 @@ __global__ void __launch_bounds__(128) k_eval32(Eval32Args A)
             const float av = -(1.f + w2) * Fpy - Qf * wv;
             // c + x = 2c + (x - c)
             const float cxx = 2.f * (float)g[0] + tx, cyy = 2.f * (float)g[1] + ty, czz = 2.f * (float)g[2] + tz;
+            const double4_32a x = A.tgt[tix];
             const float xx = (float)x.x, xy = (float)x.y, xz = (float)x.z;
             float a3x = au * ((float)g[3] - wu * cxx) + av * ((float)g[6] - wv * cxx);
             float a3y = au * ((float)g[4] - wu * cyy) + av * ((float)g[7] - wv * cyy);
@@ -355,9 +356,64 @@ __global__ void __launch_bounds__(128) k_eval32(Eval32Args A)
     }
 }
 
+// Offsets for the mixed evaluation, formed once in FP64 and split into FP32
+// (hi, lo) pairs: each sorted target from its leaf's centre, and each near
+// leaf's centre from its target leaf's centre (one per direct-act pair).
+__global__ void k_tgt_offsets(TreeView T, const int* __restrict__ leaves, int64_t n_leaves,
+                              const double4_32a* __restrict__ tgt, float4* __restrict__ off)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t w = warp0; w < n_leaves; w += nw) {
+        const int node = leaves[w];
+        const double* g = T.geom + (size_t)node * GEOM_STRIDE;
+        const int f = T.tfirst[node], n = T.tcount[node];
+        for (int j = f + lane; j < f + n; j += 32) {
+            const double4_32a x = tgt[j];
+            const double dx = x.x - g[0], dy = x.y - g[1], dz = x.z - g[2];
+            const float hx = (float)dx, hy = (float)dy, hz = (float)dz;
+            off[2 * (size_t)j] = make_float4(hx, hy, hz, 0.f);
+            off[2 * (size_t)j + 1] = make_float4((float)(dx - (double)hx), (float)(dy - (double)hy),
+                                                 (float)(dz - (double)hz), 0.f);
+        }
+    }
+}
+
+__global__ void k_pair_offsets(TreeView T, const uint64_t* __restrict__ tt, const uint32_t* __restrict__ ss,
+                               int64_t n, float4* __restrict__ dc)
+{
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+        const double* gs = T.geom + (size_t)ss[k] * GEOM_STRIDE;
+        const double* gt = T.geom + (size_t)tt[k] * GEOM_STRIDE;
+        const double dx = gs[0] - gt[0], dy = gs[1] - gt[1], dz = gs[2] - gt[2];
+        const float hx = (float)dx, hy = (float)dy, hz = (float)dz;
+        dc[2 * k] = make_float4(hx, hy, hz, 0.f);
+        dc[2 * k + 1] = make_float4((float)(dx - (double)hx), (float)(dy - (double)hy), (float)(dz - (double)hz), 0.f);
+    }
+}
+
 }  // namespace
 
-cudaError_t launch_eval32(const TreeView& T, const int* leaves, int64_t n_leaves, const float4* soff, const double4_32a* tgt, const uint32_t* tperm, const int64_t* p2p_off,
+cudaError_t launch_eval32_prep(const TreeView& T, const int* leaves, int64_t n_leaves, const double4_32a* tgt,
+                               float4* toff, const uint64_t* p2p_t, const uint32_t* p2p_s, int64_t n_p2p, float4* dc,
+                               cudaStream_t s)
+{
+    if (n_leaves > 0) {
+        int64_t b = (n_leaves + 7) / 8;
+        if (b > 152 * 64) b = 152 * 64;
+        k_tgt_offsets<<<(unsigned)b, 256, 0, s>>>(T, leaves, n_leaves, tgt, toff); count_launch();
+    }
+    if (n_p2p > 0) {
+        int64_t b = (n_p2p + 255) / 256;
+        if (b > 152 * 64) b = 152 * 64;
+        k_pair_offsets<<<(unsigned)b, 256, 0, s>>>(T, p2p_t, p2p_s, n_p2p, dc); count_launch();
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_eval32(const TreeView& T, const int* leaves, int64_t n_leaves, const float4* soff,
+                          const float4* toff, const float4* dc, const double4_32a* tgt, const uint32_t* tperm, const int64_t* p2p_off,
                           const uint32_t* p2p_src, const double* local, const double* mpole, int p, int zero_mean,
                           double* psi, double* alpha, cudaStream_t s)
 {
@@ -367,6 +423,8 @@ cudaError_t launch_eval32(const TreeView& T, const int* leaves, int64_t n_leaves
     A.leaves = leaves;
     A.n_leaves = n_leaves;
     A.soff = soff;
+    A.toff = toff;
+    A.dc = dc;
     A.tgt = tgt;
     A.tperm = tperm;
     A.p2p_off = p2p_off;
