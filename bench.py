@@ -61,10 +61,8 @@ def parse():
 
 
 def dist_env():
-    ws = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return ws, rank, local
+    from paper_2210_07021_gb300.shard import dist_env as env
+    return env()
 
 
 class ClockSampler:
@@ -129,7 +127,8 @@ def rel(a, b):
 
 def make_workload(args, rank):
     from paper_2210_07021_gb300 import workloads
-    d = workloads.clustered_pair(n=args.n, n_clumps=args.clumps, config_index=3 + 100 * rank)
+    from paper_2210_07021_gb300.shard import rank_config_index
+    d = workloads.clustered_pair(n=args.n, n_clumps=args.clumps, config_index=rank_config_index(3, rank))
     return d
 
 
@@ -213,11 +212,8 @@ def run_sfmm(args):
         torch.cuda.synchronize()
 
     def max_over_ranks(v):
-        if dist:
-            t = torch.tensor([v], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            return float(t.item())
-        return v
+        from paper_2210_07021_gb300.shard import max_over_ranks as mor
+        return mor(v, device=dev)
 
     wanted = [m for m in MODES if m[0] in args.modes.split(",")]
     wanted.sort(key=lambda m: args.modes.split(",").index(m[0]))
