@@ -73,6 +73,7 @@ typedef struct {
     int64_t n_max, m_max;  /* optional: size the workspace for up to n_max sources and m_max targets
                               at plan time (0 = grow on first use)                                  */
     void* stream;          /* cudaStream_t to enqueue on; NULL = the legacy default stream          */
+    int m2l_tensor_cores;  /* SFMM_MIXED only: 1 (default) = M2L as split-BF16 tcgen05 GEMMs, 0 = FP32 warp kernel */
 } sfmm_options;
 
 /* Fill *opt with the defaults listed above.  Returns SFMM_EINVAL if opt is NULL. */

@@ -17,29 +17,35 @@ cudaError_t tree_target_ranges(sfmm_plan_s* P, const uint64_t* tkeys, int64_t M)
 cudaError_t collect_leaves(sfmm_plan_s* P, const int* cnt, Buf& out, int64_t* n_out);
 cudaError_t build_lists(sfmm_plan_s* P, const TreeView& T, double c_s, double c_t);
 void fill_tables(double* h);
-size_t xgeo_bytes();
-cudaError_t launch_pair_geo(const TreeView& T, const uint64_t* tt, const uint32_t* ss, int64_t n, void* out,
+size_t xgeo_bytes(bool fp32);
+cudaError_t launch_pair_geo(const TreeView& T, const uint64_t* tt, const uint32_t* ss, int64_t n, void* out, bool fp32,
                             cudaStream_t s);
-cudaError_t launch_child_geo(const TreeView& T, void* m2m, void* l2l, cudaStream_t s);
+cudaError_t launch_child_geo(const TreeView& T, void* m2m, void* l2l, bool fp32, cudaStream_t s);
 cudaError_t launch_src_offsets(const TreeView& T, const int* leaves, int64_t n_leaves, const double4_32a* src,
                                float4* off, cudaStream_t s);
 cudaError_t launch_p2m(const TreeView& T, const int* leaves, int64_t n_leaves, const double4_32a* src,
-                       const float4* off, double* mpole, int p, bool fp32, cudaStream_t s);
-cudaError_t launch_m2m(const TreeView& T, int a, int b, int p, const double* tables, const void* geo, double* mpole,
+                       const float4* off, void* mpole, int p, bool fp32, cudaStream_t s);
+cudaError_t launch_m2m(const TreeView& T, int a, int b, int p, const double* tables, const void* geo, void* mpole,
                        bool fp32, cudaStream_t s);
 cudaError_t launch_m2l(const TreeView& T, const int64_t* off, const uint32_t* srcs, int p, const double* tables,
-                       const void* geo, const double* mpole, double* local, bool fp32, cudaStream_t s);
-cudaError_t launch_l2l(const TreeView& T, int a, int b, int p, const double* tables, const void* geo, double* local,
+                       const void* geo, const void* mpole, void* local, bool fp32, cudaStream_t s);
+cudaError_t launch_m2l_list(const uint64_t* ptgt, const uint32_t* psrc, const uint32_t* list, const uint32_t* n_list,
+                            int64_t max_list, int p, const double* tables, const void* geo, const void* mpole,
+                            void* local, cudaStream_t s);
+cudaError_t launch_m2l_tc(int64_t n_pairs, const uint64_t* ptgt, const uint32_t* psrc, const void* geo,
+                          const void* mpole, void* local, int p, uint32_t* leftover, uint32_t* n_leftover,
+                          int* status, cudaStream_t s);
+cudaError_t launch_l2l(const TreeView& T, int a, int b, int p, const double* tables, const void* geo, void* local,
                        bool fp32, cudaStream_t s);
+cudaError_t launch_unscale(int n_nodes, const double* geom, const void* in, double* out, int p, int is_local,
+                           bool fp32, cudaStream_t s);
 cudaError_t launch_eval32_prep(const TreeView& T, const int* leaves, int64_t n_leaves, const double4_32a* tgt,
                                float4* toff, const uint64_t* p2p_t, const uint32_t* p2p_s, int64_t n_p2p, float4* dc,
                                cudaStream_t s);
 cudaError_t launch_eval32(const TreeView& T, const int* leaves, int64_t n_leaves, const float4* soff,
                           const float4* toff, const float4* dc, const double4_32a* tgt, const uint32_t* tperm, const int64_t* p2p_off,
-                          const uint32_t* p2p_src, const double* local, const double* mpole, int p, int zero_mean,
+                          const uint32_t* p2p_src, const float* local, const float* mpole, int p, int zero_mean,
                           double* psi, double* alpha, cudaStream_t s);
-cudaError_t launch_unscale(int n_nodes, const double* geom, const double* in, double* out, int p, int is_local,
-                           cudaStream_t s);
 cudaError_t launch_count_pairs(const TreeView& T, const int* leaves, int64_t n_leaves, const int64_t* p2p_off,
                                const uint32_t* p2p_src, unsigned long long* out, cudaStream_t s);
 cudaError_t launch_eval(const TreeView& T, const int* leaves, int64_t n_leaves, const double4_32a* src, const double4_32a* tgt,
@@ -248,13 +254,14 @@ sfmm_status solve(sfmm_plan_s* P, const double* src, const void* q, int64_t N, c
     if ((e = collect_leaves(P, T.tcount, P->leaves_tgt, &P->n_leaves_tgt))) return cuda_fail(P, e, "target leaves");
     tm.mark();
     // ---- up-pass
-    if ((e = ensure(P->mpole, (size_t)nn * EXP_STRIDE * 8)) || (e = ensure(P->local, (size_t)nn * EXP_STRIDE * 8)))
-        return cuda_fail(P, e, "alloc expansions");
-    if ((e = cudaMemsetAsync(P->mpole.p, 0, (size_t)nn * EXP_STRIDE * 8, s))) return cuda_fail(P, e, "memset");
     const bool fp32 = P->opt.precision == SFMM_MIXED;
-    if ((e = ensure(P->m2m_geo, (size_t)nn * xgeo_bytes())) || (e = ensure(P->l2l_geo, (size_t)nn * xgeo_bytes())))
+    const size_t esz = fp32 ? 4 : 8;                   // expansion storage: float (mixed) or double
+    if ((e = ensure(P->mpole, (size_t)nn * EXP_STRIDE * esz)) || (e = ensure(P->local, (size_t)nn * EXP_STRIDE * esz)))
+        return cuda_fail(P, e, "alloc expansions");
+    if ((e = cudaMemsetAsync(P->mpole.p, 0, (size_t)nn * EXP_STRIDE * esz, s))) return cuda_fail(P, e, "memset");
+    if ((e = ensure(P->m2m_geo, (size_t)nn * xgeo_bytes(fp32))) || (e = ensure(P->l2l_geo, (size_t)nn * xgeo_bytes(fp32))))
         return cuda_fail(P, e, "alloc");
-    if ((e = launch_child_geo(T, P->m2m_geo.p, P->l2l_geo.p, s))) return cuda_fail(P, e, "child geometry");
+    if ((e = launch_child_geo(T, P->m2m_geo.p, P->l2l_geo.p, fp32, s))) return cuda_fail(P, e, "child geometry");
     if (fp32) {
         if ((e = ensure(P->soff, (size_t)N * 32))) return cuda_fail(P, e, "alloc");
         if ((e = launch_src_offsets(T, P->leaves_src.as<int>(), P->n_leaves, P->src4.as<double4_32a>(),
@@ -262,31 +269,44 @@ sfmm_status solve(sfmm_plan_s* P, const double* src, const void* q, int64_t N, c
             return cuda_fail(P, e, "offsets");
     }
     if ((e = launch_p2m(T, P->leaves_src.as<int>(), P->n_leaves, P->src4.as<double4_32a>(), P->soff.as<float4>(),
-                        P->mpole.as<double>(), p, fp32, s)))
+                        P->mpole.p, p, fp32, s)))
         return cuda_fail(P, e, "P2M");
     const int depth = (int)P->level_start.size() - 2;
     for (int l = depth - 1; l >= 0; --l)
         if ((e = launch_m2m(T, P->level_start[l], P->level_start[l + 1], p, P->tables.as<double>(), P->m2m_geo.p,
-                            P->mpole.as<double>(), fp32, s)))
+                            P->mpole.p, fp32, s)))
             return cuda_fail(P, e, "M2M");
     tm.mark();
     // ---- lists
     if ((e = build_lists(P, T, P->opt.c_s, P->opt.c_t))) return cuda_fail(P, e, "lists");
     tm.mark();
     // ---- M2L
-    if ((e = cudaMemsetAsync(P->local.p, 0, (size_t)nn * EXP_STRIDE * 8, s))) return cuda_fail(P, e, "memset");
+    if ((e = cudaMemsetAsync(P->local.p, 0, (size_t)nn * EXP_STRIDE * esz, s))) return cuda_fail(P, e, "memset");
     const uint32_t* m2l_s = P->m2l_alt ? P->m2l_s2.as<uint32_t>() : P->m2l_s.as<uint32_t>();
     const uint64_t* m2l_t = P->m2l_alt ? P->m2l_t2.as<uint64_t>() : P->m2l_t.as<uint64_t>();
-    if ((e = ensure(P->m2l_geo, (size_t)std::max<int64_t>(P->n_m2l, 1) * xgeo_bytes()))) return cuda_fail(P, e, "alloc");
-    if ((e = launch_pair_geo(T, m2l_t, m2l_s, P->n_m2l, P->m2l_geo.p, s))) return cuda_fail(P, e, "pair geometry");
-    if ((e = launch_m2l(T, P->m2l_off.as<int64_t>(), m2l_s, p, P->tables.as<double>(), P->m2l_geo.p,
-                        P->mpole.as<double>(), P->local.as<double>(), fp32, s)))
+    if ((e = ensure(P->m2l_geo, (size_t)std::max<int64_t>(P->n_m2l, 1) * xgeo_bytes(fp32)))) return cuda_fail(P, e, "alloc");
+    if ((e = launch_pair_geo(T, m2l_t, m2l_s, P->n_m2l, P->m2l_geo.p, fp32, s))) return cuda_fail(P, e, "pair geometry");
+    int* status = reinterpret_cast<int*>(P->small.as<int64_t>() + 20);
+    if (fp32 && P->opt.m2l_tensor_cores) {
+        // tensor-core M2L; pairs it cannot take (centres near antipodes) go to a list for the warp kernel
+        uint32_t* n_left = reinterpret_cast<uint32_t*>(P->small.as<int64_t>() + 21);
+        if ((e = ensure(P->leftover, (size_t)std::max<int64_t>(P->n_m2l, 1) * 4))) return cuda_fail(P, e, "alloc");
+        if ((e = cudaMemsetAsync(P->small.as<int64_t>() + 20, 0, 16, s))) return cuda_fail(P, e, "memset");
+        if ((e = launch_m2l_tc(P->n_m2l, m2l_t, m2l_s, P->m2l_geo.p, P->mpole.p, P->local.p, p, P->leftover.as<uint32_t>(),
+                               n_left, status, s)))
+            return cuda_fail(P, e, "M2L (tensor cores)");
+        if ((e = launch_m2l_list(m2l_t, m2l_s, P->leftover.as<uint32_t>(), n_left, P->n_m2l, p, P->tables.as<double>(),
+                                 P->m2l_geo.p, P->mpole.p, P->local.p, s)))
+            return cuda_fail(P, e, "M2L (leftover pairs)");
+    } else if ((e = launch_m2l(T, P->m2l_off.as<int64_t>(), m2l_s, p, P->tables.as<double>(), P->m2l_geo.p, P->mpole.p,
+                               P->local.p, fp32, s))) {
         return cuda_fail(P, e, "M2L");
+    }
     tm.mark();
     // ---- L2L
     for (int l = 1; l <= depth; ++l)
         if ((e = launch_l2l(T, P->level_start[l], P->level_start[l + 1], p, P->tables.as<double>(), P->l2l_geo.p,
-                            P->local.as<double>(), fp32, s)))
+                            P->local.p, fp32, s)))
             return cuda_fail(P, e, "L2L");
     tm.mark();
     // ---- evaluation
@@ -301,7 +321,7 @@ sfmm_status solve(sfmm_plan_s* P, const double* src, const void* q, int64_t N, c
     }
     if (fp32) e = launch_eval32(T, P->leaves_tgt.as<int>(), P->n_leaves_tgt, P->soff.as<float4>(),
                                 P->toff.as<float4>(), P->dc.as<float4>(), P->tgt4.as<double4_32a>(), tperm, P->p2p_off.as<int64_t>(), p2p_s,
-                                P->local.as<double>(), P->mpole.as<double>(), p, P->opt.zero_mean, psi, alpha, s);
+                                P->local.as<float>(), P->mpole.as<float>(), p, P->opt.zero_mean, psi, alpha, s);
     else e = launch_eval(T, P->leaves_tgt.as<int>(), P->n_leaves_tgt, P->src4.as<double4_32a>(),
                          P->tgt4.as<double4_32a>(), tperm, P->p2p_off.as<int64_t>(), p2p_s, P->local.as<double>(),
                          P->mpole.as<double>(), p, P->opt.zero_mean, psi, alpha, s);
@@ -320,6 +340,11 @@ sfmm_status solve(sfmm_plan_s* P, const double* src, const void* q, int64_t N, c
         P->stats.p2p_interactions = (int64_t)h;
     }
     if ((e = cudaStreamSynchronize(s))) return cuda_fail(P, e, "solve");
+    if (fp32 && P->opt.m2l_tensor_cores) {
+        int st = 0;
+        if ((e = cudaMemcpy(&st, status, 4, cudaMemcpyDeviceToHost))) return cuda_fail(P, e, "status");
+        if (st) return fail(P, SFMM_ETIMEOUT, "a bounded wait of the tensor-core M2L kernel ran out");
+    }
     tm.finish();
     P->stats.n_nodes = nn;
     P->stats.n_leaves = P->n_leaves;
@@ -361,6 +386,7 @@ sfmm_status sfmm_default_options(sfmm_options* opt)
     opt->c_s = 2.0;
     opt->c_t = 0.5;
     opt->precision = SFMM_FP64;
+    opt->m2l_tensor_cores = 1;
     return SFMM_OK;
 }
 
@@ -484,7 +510,7 @@ void sfmm_destroy(sfmm_plan_t plan)
                   &plan->m2l_t, &plan->m2l_s, &plan->m2l_t2, &plan->m2l_s2, &plan->p2p_t, &plan->p2p_s,
                   &plan->p2p_t2, &plan->p2p_s2, &plan->m2l_off, &plan->p2p_off, &plan->leaves_src,
                   &plan->leaves_tgt, &plan->m2l_geo, &plan->m2m_geo, &plan->l2l_geo, &plan->soff,
-                  &plan->toff, &plan->dc};
+                  &plan->toff, &plan->dc, &plan->leftover};
     for (Buf* b : all) release(*b);
     delete plan;
 }
@@ -573,8 +599,8 @@ sfmm_status sfmm_debug_copy(sfmm_plan_t plan, int which, void* dst, int64_t byte
     if (which == SFMM_ARR_MULTIPOLE || which == SFMM_ARR_LOCAL) {
         if ((e = ensure(tmpbuf, need))) return cuda_fail(P, e, "alloc");
         const Buf& in = which == SFMM_ARR_MULTIPOLE ? P->mpole : P->local;
-        if ((e = launch_unscale((int)nn, P->n_geom.as<double>(), in.as<double>(), tmpbuf.as<double>(), p,
-                                which == SFMM_ARR_LOCAL, P->stream)) ||
+        if ((e = launch_unscale((int)nn, P->n_geom.as<double>(), in.p, tmpbuf.as<double>(), p,
+                                which == SFMM_ARR_LOCAL, P->opt.precision == SFMM_MIXED, P->stream)) ||
             (e = cudaStreamSynchronize(P->stream)) || (e = cudaMemcpy(dst, tmpbuf.p, need, cudaMemcpyDeviceToHost))) {
             release(tmpbuf);
             return cuda_fail(P, e, "unscale");

@@ -182,8 +182,8 @@ struct Eval32Args {
     const uint32_t* tperm;
     const int64_t* p2p_off;
     const uint32_t* p2p_src;
-    const double* local;
-    const double* base_mpole;
+    const float* local;       // FP32 local expansions (mixed path)
+    const float* base_mpole;
     int p;
     int want_psi;
     int zero_mean;
@@ -223,7 +223,7 @@ __global__ void __launch_bounds__(128) k_eval32(Eval32Args A)
         const int leaf = A.leaves[w];
         const int tf = A.T.tfirst[leaf], tc = A.T.tcount[leaf];
         const double* g = A.T.geom + (size_t)leaf * GEOM_STRIDE;
-        const double* L = A.local + (size_t)leaf * EXP_STRIDE;
+        const float* L = A.local + (size_t)leaf * EXP_STRIDE;
         const int64_t nb0 = A.p2p_off[leaf], nb1 = A.p2p_off[leaf + 1];
         int tpw = 1;
         while (tpw < tc && tpw < 32) tpw <<= 1;
@@ -349,7 +349,7 @@ __global__ void __launch_bounds__(128) k_eval32(Eval32Args A)
                 A.alpha[2 * (size_t)o + 1] = (double)(-a3x * sp + a3y * cp);
             }
             if (A.want_psi) {
-                const double psi_e = L[0] + L[1] * (LOG2 + (double)log1pf(-0.25f * D2)) + 2.0 * (double)Fx;
+                const double psi_e = (double)L[0] + (double)L[1] * (LOG2 + (double)log1pf(-0.25f * D2)) + 2.0 * (double)Fx;
                 A.psi[o] = psi_e + INV4PI * ((double)ol - LOG4 * (double)oq) + shift;
             }
         }
@@ -414,7 +414,7 @@ cudaError_t launch_eval32_prep(const TreeView& T, const int* leaves, int64_t n_l
 
 cudaError_t launch_eval32(const TreeView& T, const int* leaves, int64_t n_leaves, const float4* soff,
                           const float4* toff, const float4* dc, const double4_32a* tgt, const uint32_t* tperm, const int64_t* p2p_off,
-                          const uint32_t* p2p_src, const double* local, const double* mpole, int p, int zero_mean,
+                          const uint32_t* p2p_src, const float* local, const float* mpole, int p, int zero_mean,
                           double* psi, double* alpha, cudaStream_t s)
 {
     if (n_leaves == 0) return cudaSuccess;

@@ -46,6 +46,18 @@ struct __align__(16) XGeo {
     double p1x, p1y, p2x, p2y;
 };
 
+// The same parameters rounded to FP32 for the mixed path, plus the fields of
+// the tensor-core M2L (u = (a ph1)^l X, Y = (b ph2)^l ..., rho = g/(a b)):
+// big = 1 when rho^32 exceeds 2^100 (centres near antipodes).
+struct __align__(16) XGeo32 {
+    float a, b, g, logk;
+    float p1x, p1y, p2x, p2y;
+    float ar, ai, br, bi;
+    float rho;
+    int big;
+    float pad[2];
+};
+
 enum { K_M2M = 0, K_M2L = 1, K_L2L = 2 };
 
 // Geometry of a translation from box S to box T (both rows of the geometry array).
@@ -118,26 +130,45 @@ __device__ __forceinline__ XGeo make_geo(int kind, const double* gS, const doubl
     return G;
 }
 
+__device__ __forceinline__ void store_geo(XGeo* out, const XGeo& G) { *out = G; }
+__device__ __forceinline__ void store_geo(XGeo32* out, const XGeo& G)
+{
+    XGeo32 H;
+    H.a = (float)G.a; H.b = (float)G.b; H.g = (float)G.g; H.logk = (float)G.logk;
+    H.p1x = (float)G.p1x; H.p1y = (float)G.p1y; H.p2x = (float)G.p2x; H.p2y = (float)G.p2y;
+    H.ar = (float)(G.a * G.p1x); H.ai = (float)(G.a * G.p1y);
+    H.br = (float)(G.b * G.p2x); H.bi = (float)(G.b * G.p2y);
+    // rho = g/(a b) = 1/cos^2(theta/2) for M2L; its 32nd power must stay below 2^100
+    const double ab = G.a * G.b;
+    const bool big = !(ab > 0.0) || G.g > ab * 8.7;
+    H.rho = big ? 0.f : (float)(G.g / ab);
+    H.big = big ? 1 : 0;
+    H.pad[0] = H.pad[1] = 0.f;
+    *out = H;
+}
+
+template <typename GR>
 __global__ void k_pair_geo(TreeView T, const uint64_t* __restrict__ tt, const uint32_t* __restrict__ ss, int64_t n,
-                           XGeo* __restrict__ out)
+                           GR* __restrict__ out)
 {
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
         const double* gS = T.geom + (size_t)ss[k] * GEOM_STRIDE;
         const double* gT = T.geom + (size_t)tt[k] * GEOM_STRIDE;
-        out[k] = make_geo(K_M2L, gS, gT);
+        store_geo(out + k, make_geo(K_M2L, gS, gT));
     }
 }
 
 // per node with a parent: child -> parent (M2M) and parent -> child (L2L)
-__global__ void k_child_geo(TreeView T, XGeo* __restrict__ m2m, XGeo* __restrict__ l2l)
+template <typename GR>
+__global__ void k_child_geo(TreeView T, GR* __restrict__ m2m, GR* __restrict__ l2l)
 {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < T.n_nodes; i += (int64_t)gridDim.x * blockDim.x) {
         const int par = T.parent[i];
         if (par < 0) continue;
         const double* gC = T.geom + (size_t)i * GEOM_STRIDE;
         const double* gP = T.geom + (size_t)par * GEOM_STRIDE;
-        m2m[i] = make_geo(K_M2M, gC, gP);
-        l2l[i] = make_geo(K_L2L, gP, gC);
+        store_geo(m2m + i, make_geo(K_M2M, gC, gP));
+        store_geo(l2l + i, make_geo(K_L2L, gP, gC));
     }
 }
 
@@ -200,8 +231,8 @@ template <typename R> __device__ __forceinline__ void load_tables(Tables<R>* st,
 
 // One translation by the whole warp.  Input expansion (Cin, Qin, X = lane's
 // coefficient); accumulates into (accC, accQ, accY).
-template <typename R>
-__device__ __forceinline__ void warp_translate(int p, int lane, const XGeo& G, R Cin, R Qin, cx<R> X,
+template <typename R, typename GR>
+__device__ __forceinline__ void warp_translate(int p, int lane, const GR& G, R Cin, R Qin, cx<R> X,
                                                const Tables<R>* tb, WarpSmem<R>* ws, R* accC, R* accQ, cx<R>* accY)
 {
     const int l = lane + 1;
@@ -243,24 +274,32 @@ __device__ __forceinline__ void warp_translate(int p, int lane, const XGeo& G, R
     __syncwarp();
 }
 
-template <typename R>
-__device__ __forceinline__ void load_exp(const double* e, int lane, int p, R* C, R* Q, cx<R>* X)
+template <typename R, typename ST>
+__device__ __forceinline__ void load_exp(const ST* e, int lane, int p, R* C, R* Q, cx<R>* X)
 {
     *C = (R)e[0];
     *Q = (R)e[1];
     *X = (lane < p) ? cmk<R>((R)e[2 + 2 * lane], (R)e[3 + 2 * lane]) : cmk<R>(0, 0);
 }
 
-template <typename R>
-__device__ __forceinline__ void store_exp(double* e, int lane, int p, R C, R Q, cx<R> Y, bool add)
+template <typename R, typename ST>
+__device__ __forceinline__ void store_exp(ST* e, int lane, int p, R C, R Q, cx<R> Y, bool add)
 {
     if (lane == 0) {
-        if (add) { e[0] += (double)C; e[1] += (double)Q; } else { e[0] = (double)C; e[1] = (double)Q; }
+        if (add) { e[0] += (ST)C; e[1] += (ST)Q; } else { e[0] = (ST)C; e[1] = (ST)Q; }
     }
     if (lane < p) {
-        if (add) { e[2 + 2 * lane] += (double)Y.x; e[3 + 2 * lane] += (double)Y.y; }
-        else { e[2 + 2 * lane] = (double)Y.x; e[3 + 2 * lane] = (double)Y.y; }
+        if (add) { e[2 + 2 * lane] += (ST)Y.x; e[3 + 2 * lane] += (ST)Y.y; }
+        else { e[2 + 2 * lane] = (ST)Y.x; e[3 + 2 * lane] = (ST)Y.y; }
     }
+}
+
+// atomic accumulation (leftover M2L pairs of the tensor-core kernel)
+template <typename R, typename ST>
+__device__ __forceinline__ void atomic_exp(ST* e, int lane, int p, R C, R Q, cx<R> Y)
+{
+    if (lane == 0) { atomicAdd(e, (ST)C); atomicAdd(e + 1, (ST)Q); }
+    if (lane < p) { atomicAdd(e + 2 + 2 * lane, (ST)Y.x); atomicAdd(e + 3 + 2 * lane, (ST)Y.y); }
 }
 
 // ----------------------------------------------------------------- P2M
@@ -314,7 +353,7 @@ __global__ void k_p2m(TreeView T, const int* __restrict__ leaves, int64_t n_leav
 // done in FP64 when the offsets were formed).
 template <int P>
 __global__ void k_p2m32(TreeView T, const int* __restrict__ leaves, int64_t n_leaves, const float4* __restrict__ off,
-                        double* __restrict__ mpole)
+                        float* __restrict__ mpole)
 {
     for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < n_leaves; w += (int64_t)gridDim.x * blockDim.x) {
         const int node = leaves[w];
@@ -343,25 +382,25 @@ __global__ void k_p2m32(TreeView T, const int* __restrict__ leaves, int64_t n_le
                 A[l].y += zp.y;
             }
         }
-        double* e = mpole + (size_t)node * EXP_STRIDE;
-        const double Q = INV4PI * (double)Qsum;
-        e[0] = INV4PI * (double)Csum - Q * LOG2;
+        float* e = mpole + (size_t)node * EXP_STRIDE;
+        const float Q = (float)INV4PI * Qsum;
+        e[0] = (float)INV4PI * Csum - Q * (float)LOG2;
         e[1] = Q;
 #pragma unroll
         for (int l = 0; l < P; ++l) {
-            const double s = -INV4PI / (double)(l + 1);
-            e[2 + 2 * l] = s * (double)A[l].x;
-            e[3 + 2 * l] = s * (double)A[l].y;
+            const float s = -(float)INV4PI / (float)(l + 1);
+            e[2 + 2 * l] = s * A[l].x;
+            e[3 + 2 * l] = s * A[l].y;
         }
-        for (int l = P; l < PMAX; ++l) { e[2 + 2 * l] = 0.0; e[3 + 2 * l] = 0.0; }
+        for (int l = P; l < PMAX; ++l) { e[2 + 2 * l] = 0.f; e[3 + 2 * l] = 0.f; }
     }
 }
 
 // ----------------------------------------------------------------- M2M
 // One warp per internal node of one level: sum of its 4 children's multipoles.
-template <typename R>
-__global__ void k_m2m(TreeView T, int a, int b, int p, const double* __restrict__ tables, const XGeo* __restrict__ geo,
-                      double* __restrict__ mpole)
+template <typename R, typename GR, typename ST>
+__global__ void k_m2m(TreeView T, int a, int b, int p, const double* __restrict__ tables, const GR* __restrict__ geo,
+                      ST* __restrict__ mpole)
 {
     __shared__ Tables<R> tb;
     __shared__ WarpSmem<R> ws[4];
@@ -374,7 +413,7 @@ __global__ void k_m2m(TreeView T, int a, int b, int p, const double* __restrict_
         cx<R> accY = cmk<R>(0, 0);
         for (int c = c0; c < c0 + 4; ++c) {
             if (T.count[c] == 0) continue;
-            const XGeo G = geo[c];
+            const GR G = geo[c];
             R C, Q;
             cx<R> X;
             load_exp<R>(mpole + (size_t)c * EXP_STRIDE, lane, p, &C, &Q, &X);
@@ -386,10 +425,10 @@ __global__ void k_m2m(TreeView T, int a, int b, int p, const double* __restrict_
 
 // ----------------------------------------------------------------- M2L
 // One warp per target box with a non-empty list; writes local = sum of M2Ls.
-template <typename R>
+template <typename R, typename GR, typename ST>
 __global__ void k_m2l(TreeView T, const int64_t* __restrict__ off, const uint32_t* __restrict__ srcs, int p,
-                      const double* __restrict__ tables, const XGeo* __restrict__ geo, const double* __restrict__ mpole,
-                      double* __restrict__ local)
+                      const double* __restrict__ tables, const GR* __restrict__ geo, const ST* __restrict__ mpole,
+                      ST* __restrict__ local)
 {
     __shared__ Tables<R> tb;
     __shared__ WarpSmem<R> ws[4];
@@ -402,7 +441,7 @@ __global__ void k_m2l(TreeView T, const int64_t* __restrict__ off, const uint32_
         cx<R> accY = cmk<R>(0, 0);
         for (int64_t k = lo; k < hi; ++k) {
             const int s = (int)srcs[k];
-            const XGeo G = geo[k];
+            const GR G = geo[k];
             R C, Q;
             cx<R> X;
             load_exp<R>(mpole + (size_t)s * EXP_STRIDE, lane, p, &C, &Q, &X);
@@ -414,9 +453,9 @@ __global__ void k_m2l(TreeView T, const int64_t* __restrict__ off, const uint32_
 
 // ----------------------------------------------------------------- L2L
 // One warp per node of one level holding targets: local += L2L(parent local).
-template <typename R>
-__global__ void k_l2l(TreeView T, int a, int b, int p, const double* __restrict__ tables, const XGeo* __restrict__ geo,
-                      double* __restrict__ local)
+template <typename R, typename GR, typename ST>
+__global__ void k_l2l(TreeView T, int a, int b, int p, const double* __restrict__ tables, const GR* __restrict__ geo,
+                      ST* __restrict__ local)
 {
     __shared__ Tables<R> tb;
     __shared__ WarpSmem<R> ws[4];
@@ -426,7 +465,7 @@ __global__ void k_l2l(TreeView T, int a, int b, int p, const double* __restrict_
         if (T.tcount[node] == 0) continue;
         const int par = T.parent[node];
         if (par < 0) continue;
-        const XGeo G = geo[node];
+        const GR G = geo[node];
         R C, Q;
         cx<R> X;
         load_exp<R>(local + (size_t)par * EXP_STRIDE, lane, p, &C, &Q, &X);
@@ -434,6 +473,34 @@ __global__ void k_l2l(TreeView T, int a, int b, int p, const double* __restrict_
         cx<R> accY = cmk<R>(0, 0);
         warp_translate<R>(p, lane, G, C, Q, X, &tb, &ws[wid], &accC, &accQ, &accY);
         store_exp<R>(local + (size_t)node * EXP_STRIDE, lane, p, accC, accQ, accY, true);
+    }
+}
+
+// ------------------------------------------------------ M2L, listed pairs
+// One warp per pair of a list (the pairs the tensor-core M2L leaves out); the
+// result is added atomically to the target's local expansion.
+template <typename R, typename GR, typename ST>
+__global__ void k_m2l_list(const uint64_t* __restrict__ ptgt, const uint32_t* __restrict__ psrc,
+                           const uint32_t* __restrict__ list, const uint32_t* __restrict__ n_list, int p,
+                           const double* __restrict__ tables, const GR* __restrict__ geo, const ST* __restrict__ mpole,
+                           ST* __restrict__ local)
+{
+    __shared__ Tables<R> tb;
+    __shared__ WarpSmem<R> ws[4];
+    load_tables<R>(&tb, tables);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int64_t n = *n_list;
+    for (int64_t w = (int64_t)blockIdx.x * 4 + wid; w < n; w += (int64_t)gridDim.x * 4) {
+        const uint32_t k = list[w];
+        const int s = (int)psrc[k], t = (int)ptgt[k];
+        const GR G = geo[k];
+        R C, Q;
+        cx<R> X;
+        load_exp<R>(mpole + (size_t)s * EXP_STRIDE, lane, p, &C, &Q, &X);
+        R accC = 0, accQ = 0;
+        cx<R> accY = cmk<R>(0, 0);
+        warp_translate<R>(p, lane, G, C, Q, X, &tb, &ws[wid], &accC, &accQ, &accY);
+        atomic_exp<R>(local + (size_t)t * EXP_STRIDE, lane, p, accC, accQ, accY);
     }
 }
 
@@ -462,20 +529,21 @@ __global__ void k_src_offsets(TreeView T, const int* __restrict__ leaves, int64_
 }
 
 // Unscale for introspection: multipole A_l * r^l, local A_l / r^l.
-__global__ void k_unscale(int n_nodes, const double* __restrict__ geom, const double* __restrict__ in,
+template <typename ST>
+__global__ void k_unscale(int n_nodes, const double* __restrict__ geom, const ST* __restrict__ in,
                           double* __restrict__ out, int p, int is_local)
 {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_nodes; i += (int64_t)gridDim.x * blockDim.x) {
         const double r = geom[(size_t)i * GEOM_STRIDE + 10];
-        const double* e = in + (size_t)i * EXP_STRIDE;
+        const ST* e = in + (size_t)i * EXP_STRIDE;
         double* o = out + (size_t)i * (2 * p + 2);
-        o[0] = e[0];
-        o[1] = e[1];
+        o[0] = (double)e[0];
+        o[1] = (double)e[1];
         double s = 1.0;
         for (int l = 0; l < p; ++l) {
             s = is_local ? s / r : s * r;
-            o[2 + 2 * l] = e[2 + 2 * l] * s;
-            o[3 + 2 * l] = e[3 + 2 * l] * s;
+            o[2 + 2 * l] = (double)e[2 + 2 * l] * s;
+            o[3 + 2 * l] = (double)e[3 + 2 * l] * s;
         }
     }
 }
@@ -490,7 +558,7 @@ inline unsigned grid_for(int64_t n, int per_block)
 
 }  // namespace
 
-size_t xgeo_bytes() { return sizeof(XGeo); }
+size_t xgeo_bytes(bool fp32) { return fp32 ? sizeof(XGeo32) : sizeof(XGeo); }
 
 void fill_tables(double* h)   // [2][PMAX][PMAX]
 {
@@ -507,17 +575,21 @@ void fill_tables(double* h)   // [2][PMAX][PMAX]
         }
 }
 
-cudaError_t launch_pair_geo(const TreeView& T, const uint64_t* tt, const uint32_t* ss, int64_t n, void* out,
+cudaError_t launch_pair_geo(const TreeView& T, const uint64_t* tt, const uint32_t* ss, int64_t n, void* out, bool fp32,
                             cudaStream_t s)
 {
     if (n == 0) return cudaSuccess;
-    k_pair_geo<<<grid_for(n, 256), 256, 0, s>>>(T, tt, ss, n, static_cast<XGeo*>(out)); count_launch();
+    if (fp32) k_pair_geo<XGeo32><<<grid_for(n, 256), 256, 0, s>>>(T, tt, ss, n, static_cast<XGeo32*>(out));
+    else k_pair_geo<XGeo><<<grid_for(n, 256), 256, 0, s>>>(T, tt, ss, n, static_cast<XGeo*>(out));
+    count_launch();
     return cudaGetLastError();
 }
 
-cudaError_t launch_child_geo(const TreeView& T, void* m2m, void* l2l, cudaStream_t s)
+cudaError_t launch_child_geo(const TreeView& T, void* m2m, void* l2l, bool fp32, cudaStream_t s)
 {
-    k_child_geo<<<grid_for(T.n_nodes, 256), 256, 0, s>>>(T, static_cast<XGeo*>(m2m), static_cast<XGeo*>(l2l)); count_launch();
+    if (fp32) k_child_geo<XGeo32><<<grid_for(T.n_nodes, 256), 256, 0, s>>>(T, static_cast<XGeo32*>(m2m), static_cast<XGeo32*>(l2l));
+    else k_child_geo<XGeo><<<grid_for(T.n_nodes, 256), 256, 0, s>>>(T, static_cast<XGeo*>(m2m), static_cast<XGeo*>(l2l));
+    count_launch();
     return cudaGetLastError();
 }
 
@@ -529,16 +601,17 @@ cudaError_t launch_src_offsets(const TreeView& T, const int* leaves, int64_t n_l
     return cudaGetLastError();
 }
 
+// mpole: double storage (FP64 path) or float storage (mixed path)
 cudaError_t launch_p2m(const TreeView& T, const int* leaves, int64_t n_leaves, const double4_32a* src,
-                       const float4* off, double* mpole, int p, bool fp32, cudaStream_t s)
+                       const float4* off, void* mpole, int p, bool fp32, cudaStream_t s)
 {
     if (n_leaves == 0) return cudaSuccess;
     const unsigned g = grid_for(n_leaves, 128);
-#define P2M_CASE(PP)                                                                          \
-    case PP:                                                                                  \
-        if (fp32) k_p2m32<PP><<<g, 128, 0, s>>>(T, leaves, n_leaves, off, mpole);            \
-        else k_p2m<PP><<<g, 128, 0, s>>>(T, leaves, n_leaves, src, mpole);                   \
-        count_launch();                                                                       \
+#define P2M_CASE(PP)                                                                                       \
+    case PP:                                                                                               \
+        if (fp32) k_p2m32<PP><<<g, 128, 0, s>>>(T, leaves, n_leaves, off, static_cast<float*>(mpole));     \
+        else k_p2m<PP><<<g, 128, 0, s>>>(T, leaves, n_leaves, src, static_cast<double*>(mpole));           \
+        count_launch();                                                                                    \
         break;
     switch ((p + 3) / 4 * 4) {
         P2M_CASE(4) P2M_CASE(8) P2M_CASE(12) P2M_CASE(16) P2M_CASE(20) P2M_CASE(24) P2M_CASE(28) P2M_CASE(32)
@@ -548,42 +621,63 @@ cudaError_t launch_p2m(const TreeView& T, const int* leaves, int64_t n_leaves, c
     return cudaGetLastError();
 }
 
-cudaError_t launch_m2m(const TreeView& T, int a, int b, int p, const double* tables, const void* geo, double* mpole,
+cudaError_t launch_m2m(const TreeView& T, int a, int b, int p, const double* tables, const void* geo, void* mpole,
                        bool fp32, cudaStream_t s)
 {
     if (b <= a) return cudaSuccess;
-    const XGeo* G = static_cast<const XGeo*>(geo);
-    if (fp32) k_m2m<float><<<grid_for(b - a, 4), 128, 0, s>>>(T, a, b, p, tables, G, mpole);
-    else k_m2m<double><<<grid_for(b - a, 4), 128, 0, s>>>(T, a, b, p, tables, G, mpole);
+    if (fp32) k_m2m<float, XGeo32, float><<<grid_for(b - a, 4), 128, 0, s>>>(
+        T, a, b, p, tables, static_cast<const XGeo32*>(geo), static_cast<float*>(mpole));
+    else k_m2m<double, XGeo, double><<<grid_for(b - a, 4), 128, 0, s>>>(
+        T, a, b, p, tables, static_cast<const XGeo*>(geo), static_cast<double*>(mpole));
     count_launch();
     return cudaGetLastError();
 }
 
 cudaError_t launch_m2l(const TreeView& T, const int64_t* off, const uint32_t* srcs, int p, const double* tables,
-                       const void* geo, const double* mpole, double* local, bool fp32, cudaStream_t s)
+                       const void* geo, const void* mpole, void* local, bool fp32, cudaStream_t s)
 {
-    const XGeo* G = static_cast<const XGeo*>(geo);
-    if (fp32) k_m2l<float><<<grid_for(T.n_nodes, 4), 128, 0, s>>>(T, off, srcs, p, tables, G, mpole, local);
-    else k_m2l<double><<<grid_for(T.n_nodes, 4), 128, 0, s>>>(T, off, srcs, p, tables, G, mpole, local);
+    if (fp32) k_m2l<float, XGeo32, float><<<grid_for(T.n_nodes, 4), 128, 0, s>>>(
+        T, off, srcs, p, tables, static_cast<const XGeo32*>(geo), static_cast<const float*>(mpole),
+        static_cast<float*>(local));
+    else k_m2l<double, XGeo, double><<<grid_for(T.n_nodes, 4), 128, 0, s>>>(
+        T, off, srcs, p, tables, static_cast<const XGeo*>(geo), static_cast<const double*>(mpole),
+        static_cast<double*>(local));
     count_launch();
     return cudaGetLastError();
 }
 
-cudaError_t launch_l2l(const TreeView& T, int a, int b, int p, const double* tables, const void* geo, double* local,
+cudaError_t launch_m2l_list(const uint64_t* ptgt, const uint32_t* psrc, const uint32_t* list, const uint32_t* n_list,
+                            int64_t max_list, int p, const double* tables, const void* geo, const void* mpole,
+                            void* local, cudaStream_t s)
+{
+    if (max_list == 0) return cudaSuccess;
+    k_m2l_list<float, XGeo32, float><<<grid_for(max_list < 152 * 64 ? max_list : 152 * 64, 4), 128, 0, s>>>(
+        ptgt, psrc, list, n_list, p, tables, static_cast<const XGeo32*>(geo), static_cast<const float*>(mpole),
+        static_cast<float*>(local));
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_l2l(const TreeView& T, int a, int b, int p, const double* tables, const void* geo, void* local,
                        bool fp32, cudaStream_t s)
 {
     if (b <= a) return cudaSuccess;
-    const XGeo* G = static_cast<const XGeo*>(geo);
-    if (fp32) k_l2l<float><<<grid_for(b - a, 4), 128, 0, s>>>(T, a, b, p, tables, G, local);
-    else k_l2l<double><<<grid_for(b - a, 4), 128, 0, s>>>(T, a, b, p, tables, G, local);
+    if (fp32) k_l2l<float, XGeo32, float><<<grid_for(b - a, 4), 128, 0, s>>>(
+        T, a, b, p, tables, static_cast<const XGeo32*>(geo), static_cast<float*>(local));
+    else k_l2l<double, XGeo, double><<<grid_for(b - a, 4), 128, 0, s>>>(
+        T, a, b, p, tables, static_cast<const XGeo*>(geo), static_cast<double*>(local));
     count_launch();
     return cudaGetLastError();
 }
 
-cudaError_t launch_unscale(int n_nodes, const double* geom, const double* in, double* out, int p, int is_local,
-                           cudaStream_t s)
+cudaError_t launch_unscale(int n_nodes, const double* geom, const void* in, double* out, int p, int is_local,
+                           bool fp32, cudaStream_t s)
 {
-    k_unscale<<<grid_for(n_nodes, 256), 256, 0, s>>>(n_nodes, geom, in, out, p, is_local); count_launch();
+    if (fp32) k_unscale<float><<<grid_for(n_nodes, 256), 256, 0, s>>>(n_nodes, geom, static_cast<const float*>(in),
+                                                                      out, p, is_local);
+    else k_unscale<double><<<grid_for(n_nodes, 256), 256, 0, s>>>(n_nodes, geom, static_cast<const double*>(in),
+                                                                  out, p, is_local);
+    count_launch();
     return cudaGetLastError();
 }
 

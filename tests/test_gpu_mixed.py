@@ -80,3 +80,28 @@ def test_mixed_float32_masses_zero_mean():
     ref = direct_sum(src, q.astype(np.float64), tgt)
     assert rel(psi, ref["psi"] + q.astype(np.float64).sum() / (4 * np.pi)) < TOL_MIXED
     assert rel(alpha, ref["alpha"]) < TOL_MIXED
+
+
+@pytest.mark.parametrize("p", [12, 16, 24, 32])
+def test_tensor_core_m2l_matches_warp_kernel(p):
+    """The tcgen05 M2L (split-BF16 GEMMs, FP32 accumulation) and the FP32 warp
+    kernel produce the same local expansions and results to FP32 accuracy."""
+    rng = np.random.default_rng(p)
+    src = workloads.clustered(rng, 40000, 25)
+    tgt = unit(rng.normal(size=(20000, 3)))
+    q = rng.lognormal(0, 0.5, 40000)
+    pt, psi_t, al_t = solve(src, q, tgt, sfmm.SFMM_MIXED, p=p, m2l_tensor_cores=True)
+    pw, psi_w, al_w = solve(src, q, tgt, sfmm.SFMM_MIXED, p=p, m2l_tensor_cores=False)
+    lt = pt.debug(sfmm.ARR_LOCAL, np.float64, 2 * p + 2)
+    lw = pw.debug(sfmm.ARR_LOCAL, np.float64, 2 * p + 2)
+    r = pt.debug(sfmm.ARR_NODE_GEOM, np.float64, 11)[:, 10]
+    ell = np.arange(1, p + 1)
+    st = (lt[:, 2::2] + 1j * lt[:, 3::2]) * r[:, None] ** ell      # scaled coefficients, O(1)
+    sw = (lw[:, 2::2] + 1j * lw[:, 3::2]) * r[:, None] ** ell
+    scale = np.abs(sw).max()
+    assert np.abs(st - sw).max() < 2e-5 * scale
+    assert np.abs(lt[:, :2] - lw[:, :2]).max() < 2e-5 * np.abs(lw[:, :2]).max()
+    assert rel(psi_t, psi_w) < 1e-6 and rel(al_t, al_w) < 1e-6
+    if p >= 16:   # at p = 12 the truncation error of this sky is above 1e-6 for both paths
+        ref = direct_sum(src, q, tgt[:2000])
+        assert rel(psi_t[:2000], ref["psi"]) < TOL_MIXED and rel(al_t[:2000], ref["alpha"]) < TOL_MIXED
