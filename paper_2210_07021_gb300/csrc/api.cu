@@ -18,9 +18,10 @@ cudaError_t collect_leaves(sfmm_plan_s* P, const int* cnt, Buf& out, int64_t* n_
 cudaError_t build_lists(sfmm_plan_s* P, const TreeView& T, double c_s, double c_t);
 void fill_tables(double* h);
 size_t xgeo_bytes(bool fp32);
-cudaError_t launch_pair_geo(const TreeView& T, const uint64_t* tt, const uint32_t* ss, int64_t n, void* out, bool fp32,
-                            cudaStream_t s);
-cudaError_t launch_child_geo(const TreeView& T, void* m2m, void* l2l, bool fp32, cudaStream_t s);
+cudaError_t launch_geom32(int n_nodes, const double* geom, float* g32, cudaStream_t s);
+cudaError_t launch_pair_geo(const TreeView& T, const float* g32, const uint64_t* tt, const uint32_t* ss, int64_t n,
+                            void* out, bool fp32, cudaStream_t s);
+cudaError_t launch_child_geo(const TreeView& T, const float* g32, void* m2m, void* l2l, bool fp32, cudaStream_t s);
 cudaError_t launch_src_offsets(const TreeView& T, const int* leaves, int64_t n_leaves, const double4_32a* src,
                                float4* off, cudaStream_t s);
 cudaError_t launch_p2m(const TreeView& T, const int* leaves, int64_t n_leaves, const double4_32a* src,
@@ -261,7 +262,13 @@ sfmm_status solve(sfmm_plan_s* P, const double* src, const void* q, int64_t N, c
     if ((e = cudaMemsetAsync(P->mpole.p, 0, (size_t)nn * EXP_STRIDE * esz, s))) return cuda_fail(P, e, "memset");
     if ((e = ensure(P->m2m_geo, (size_t)nn * xgeo_bytes(fp32))) || (e = ensure(P->l2l_geo, (size_t)nn * xgeo_bytes(fp32))))
         return cuda_fail(P, e, "alloc");
-    if ((e = launch_child_geo(T, P->m2m_geo.p, P->l2l_geo.p, fp32, s))) return cuda_fail(P, e, "child geometry");
+    if (fp32) {
+        if ((e = ensure(P->geom32, (size_t)nn * 32))) return cuda_fail(P, e, "alloc");
+        if ((e = launch_geom32((int)nn, P->n_geom.as<double>(), P->geom32.as<float>(), s)))
+            return cuda_fail(P, e, "geometry32");
+    }
+    if ((e = launch_child_geo(T, P->geom32.as<float>(), P->m2m_geo.p, P->l2l_geo.p, fp32, s)))
+        return cuda_fail(P, e, "child geometry");
     if (fp32) {
         if ((e = ensure(P->soff, (size_t)N * 32))) return cuda_fail(P, e, "alloc");
         if ((e = launch_src_offsets(T, P->leaves_src.as<int>(), P->n_leaves, P->src4.as<double4_32a>(),
@@ -285,7 +292,8 @@ sfmm_status solve(sfmm_plan_s* P, const double* src, const void* q, int64_t N, c
     const uint32_t* m2l_s = P->m2l_alt ? P->m2l_s2.as<uint32_t>() : P->m2l_s.as<uint32_t>();
     const uint64_t* m2l_t = P->m2l_alt ? P->m2l_t2.as<uint64_t>() : P->m2l_t.as<uint64_t>();
     if ((e = ensure(P->m2l_geo, (size_t)std::max<int64_t>(P->n_m2l, 1) * xgeo_bytes(fp32)))) return cuda_fail(P, e, "alloc");
-    if ((e = launch_pair_geo(T, m2l_t, m2l_s, P->n_m2l, P->m2l_geo.p, fp32, s))) return cuda_fail(P, e, "pair geometry");
+    if ((e = launch_pair_geo(T, P->geom32.as<float>(), m2l_t, m2l_s, P->n_m2l, P->m2l_geo.p, fp32, s)))
+        return cuda_fail(P, e, "pair geometry");
     int* status = reinterpret_cast<int*>(P->small.as<int64_t>() + 20);
     if (fp32 && P->opt.m2l_tensor_cores) {
         // tensor-core M2L; pairs it cannot take (centres near antipodes) go to a list for the warp kernel
@@ -510,7 +518,7 @@ void sfmm_destroy(sfmm_plan_t plan)
                   &plan->m2l_t, &plan->m2l_s, &plan->m2l_t2, &plan->m2l_s2, &plan->p2p_t, &plan->p2p_s,
                   &plan->p2p_t2, &plan->p2p_s2, &plan->m2l_off, &plan->p2p_off, &plan->leaves_src,
                   &plan->leaves_tgt, &plan->m2l_geo, &plan->m2m_geo, &plan->l2l_geo, &plan->soff,
-                  &plan->toff, &plan->dc, &plan->leftover};
+                  &plan->toff, &plan->dc, &plan->leftover, &plan->geom32};
     for (Buf* b : all) release(*b);
     delete plan;
 }

@@ -206,11 +206,14 @@ __device__ __forceinline__ void two_sum(float a, float b, float* s, float* e)
     *s = x;
 }
 
+template <bool PSI>
 __global__ void __launch_bounds__(128) k_eval32(Eval32Args A)
 {
     __shared__ float4 s_hi[4][STAGE];
     __shared__ float4 s_lo[4][STAGE];
     __shared__ float s_dc[4][32][6];
+    __shared__ int s_pre[4][33];
+    __shared__ int s_first[4][32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -219,6 +222,8 @@ __global__ void __launch_bounds__(128) k_eval32(Eval32Args A)
         for (int b = 0; b < 12; ++b) shift += A.base_mpole[(size_t)b * EXP_STRIDE + 1];
     float4* yh = s_hi[wid];
     float4* yl = s_lo[wid];
+    int* pre = s_pre[wid];
+    int* fst = s_first[wid];
     for (int64_t w = warp0; w < A.n_leaves; w += nwarps) {
         const int leaf = A.leaves[w];
         const int tf = A.T.tfirst[leaf], tc = A.T.tcount[leaf];
@@ -238,73 +243,88 @@ __global__ void __launch_bounds__(128) k_eval32(Eval32Args A)
             const float txl = tl.x, tyl = tl.y, tzl = tl.z;
             float ox = 0.f, oy = 0.f, oz = 0.f, oq = 0.f, ol = 0.f;      // outer FP32 level
             int64_t kn = nb0;
-            int jn = 0;                // next source inside near leaf kn
+            int jn = 0;                // sources of near leaf kn already done
             while (kn < nb1) {
-                // offsets between leaf centres (hi, lo) for the next 32 near leaves
+                // ---- records of the next (up to) 32 near leaves, one per lane
                 __syncwarp();
-                {
-                    const int64_t k = kn + lane;
-                    if (k < nb1) {
-                        const float4 h = A.dc[2 * k], l = A.dc[2 * k + 1];
-                        float* d = s_dc[wid][lane];
-                        d[0] = h.x; d[1] = h.y; d[2] = h.z;
-                        d[3] = l.x; d[4] = l.y; d[5] = l.z;
-                    }
+                const int64_t k = kn + lane;
+                int cnt = 0, first = 0;
+                float4 rh = make_float4(0.f, 0.f, 0.f, 0.f), rl = rh;
+                if (k < nb1) {
+                    rh = A.dc[2 * k];
+                    rl = A.dc[2 * k + 1];
+                    first = __float_as_int(rh.w) + (lane == 0 ? jn : 0);
+                    cnt = __float_as_int(rl.w) - (lane == 0 ? jn : 0);
                 }
+                int inc = cnt;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int t = __shfl_up_sync(FULL, inc, o);
+                    if (lane >= o) inc += t;
+                }
+                const unsigned fit = __ballot_sync(FULL, k < nb1 && inc <= STAGE);
+                const int nfit = __popc(fit);
+                int ns, nl;
+                if (nfit == 0) { ns = STAGE; nl = 1; }        // one leaf larger than the stage: a chunk of it
+                else { ns = __shfl_sync(FULL, inc, nfit - 1); nl = nfit; }
+                pre[lane] = inc - cnt;
+                fst[lane] = first;
+                s_dc[wid][lane][0] = rh.x; s_dc[wid][lane][1] = rh.y; s_dc[wid][lane][2] = rh.z;
+                s_dc[wid][lane][3] = rl.x; s_dc[wid][lane][4] = rl.y; s_dc[wid][lane][5] = rl.z;
                 __syncwarp();
-                int ns = 0;
-                int64_t k = kn;
-                while (k < nb1 && k < kn + 32 && ns < STAGE) {
-                    const int sl = (int)A.p2p_src[k];
-                    const int f = A.T.first[sl], n = A.T.count[sl];
-                    const int take = min(n - jn, STAGE - ns);
-                    const float* d = s_dc[wid][k - kn];
-                    for (int j = lane; j < take; j += 32) {
-                        const float4 h = A.soff[2 * (size_t)(f + jn + j)];
-                        const float4 l = A.soff[2 * (size_t)(f + jn + j) + 1];
-                        float sx, ex_, sy, ey_, sz, ez_;
-                        two_sum(h.x, d[0], &sx, &ex_);
-                        two_sum(h.y, d[1], &sy, &ey_);
-                        two_sum(h.z, d[2], &sz, &ez_);
-                        yh[ns + j] = make_float4(sx, sy, sz, h.w);
-                        yl[ns + j] = make_float4(ex_ + (l.x + d[3]), ey_ + (l.y + d[4]), ez_ + (l.z + d[5]), 0.f);
+                // ---- flattened staging: position idx -> (leaf i, source) by binary search of pre
+                for (int idx = lane; idx < ns; idx += 32) {
+                    int lo = 0, hi = nl;            // largest i < nl with pre[i] <= idx
+                    while (hi - lo > 1) {
+                        const int mid = (lo + hi) >> 1;
+                        if (pre[mid] <= idx) lo = mid; else hi = mid;
                     }
-                    ns += take;
-                    jn += take;
-                    if (jn == n) { ++k; jn = 0; }
+                    const size_t j = (size_t)(fst[lo] + (idx - pre[lo]));
+                    const float4 h = A.soff[2 * j];
+                    const float4 l = A.soff[2 * j + 1];
+                    const float* d = s_dc[wid][lo];
+                    float sx, ex_, sy, ey_, sz, ez_;
+                    two_sum(h.x, d[0], &sx, &ex_);
+                    two_sum(h.y, d[1], &sy, &ey_);
+                    two_sum(h.z, d[2], &sz, &ez_);
+                    yh[idx] = make_float4(sx, sy, sz, h.w);
+                    yl[idx] = make_float4(ex_ + (l.x + d[3]), ey_ + (l.y + d[4]), ez_ + (l.z + d[5]), 0.f);
                 }
-                kn = k;
+                if (nfit == 0) jn += STAGE;
+                else { kn += nfit; jn = 0; }
                 __syncwarp();
-                float ix = 0.f, iy = 0.f, iz = 0.f, iq = 0.f, il = 0.f;   // inner FP32 level
-                int cnt = 0;
-                for (int j = sub; j < ns; j += lpt) {
-                    const float4 h = yh[j];
-                    const float4 l = yl[j];
-                    const float dx = (txh - h.x) + (txl - l.x);
-                    const float dy = (tyh - h.y) + (tyl - l.y);
-                    const float dz = (tzh - h.z) + (tzl - l.z);
-                    const float d2 = dx * dx + dy * dy + dz * dz;
-                    const bool ok = d2 > 0.f;
-                    const float q = ok ? h.w : 0.f;
-                    const float wq = __fdividef(q, ok ? d2 : 1.f);
-                    ix += wq * dx;
-                    iy += wq * dy;
-                    iz += wq * dz;
-                    iq += q;
-                    if (A.want_psi) il += q * __logf(ok ? d2 : 1.f);
-                    if (++cnt == 16) {
-                        ox += ix; oy += iy; oz += iz; oq += iq; ol += il;
-                        ix = iy = iz = iq = il = 0.f;
-                        cnt = 0;
+                // ---- pair loop: blocks of 16 pairs per lane in FP32, then the outer level
+                for (int j0 = sub; j0 < ns; j0 += 16 * lpt) {
+                    float ix = 0.f, iy = 0.f, iz = 0.f, iq = 0.f, il = 0.f;   // inner FP32 level
+#pragma unroll 4
+                    for (int u = 0; u < 16; ++u) {
+                        const int j = j0 + u * lpt;
+                        if (j < ns) {
+                            const float4 h = yh[j];
+                            const float4 l = yl[j];
+                            const float dx = (txh - h.x) + (txl - l.x);
+                            const float dy = (tyh - h.y) + (tyl - l.y);
+                            const float dz = (tzh - h.z) + (tzl - l.z);
+                            const float d2 = dx * dx + dy * dy + dz * dz;
+                            const bool ok = d2 > 0.f;
+                            const float q = ok ? h.w : 0.f;
+                            const float den = ok ? d2 : 1.f;
+                            const float wq = __fdividef(q, den);
+                            ix += wq * dx;
+                            iy += wq * dy;
+                            iz += wq * dz;
+                            iq += q;
+                            if (PSI) il += q * __logf(den);
+                        }
                     }
+                    ox += ix; oy += iy; oz += iz; oq += iq; ol += il;
                 }
-                ox += ix; oy += iy; oz += iz; oq += iq; ol += il;
             }
             ox = group_sumf(ox, lpt);
             oy = group_sumf(oy, lpt);
             oz = group_sumf(oz, lpt);
             oq = group_sumf(oq, lpt);
-            if (A.want_psi) ol = group_sumf(ol, lpt);
+            if (PSI) ol = group_sumf(ol, lpt);
             if (!active || sub != 0) continue;
             // ---- L2P in the leaf frame: FP32 Horner, FP64 final psi
             const float tx = txh + txl, ty = tyh + tyl, tz = tzh + tzl;
@@ -316,7 +336,7 @@ __global__ void __launch_bounds__(128) k_eval32(Eval32Args A)
             const float omx = wu * inv_r, omy = wv * inv_r;
             float frx = 0.f, fry = 0.f, fdx = 0.f, fdy = 0.f;
             for (int l = A.p; l >= 1; --l) {
-                const float ax = (float)L[2 * l], ay = (float)L[2 * l + 1];
+                const float ax = L[2 * l], ay = L[2 * l + 1];
                 const float nfx = frx * omx - fry * omy + ax;
                 const float nfy = frx * omy + fry * omx + ay;
                 const float ndx = fdx * omx - fdy * omy + ax * (float)l;
@@ -325,7 +345,7 @@ __global__ void __launch_bounds__(128) k_eval32(Eval32Args A)
             }
             const float Fx = frx * omx - fry * omy;
             const float Fpx = fdx * inv_r, Fpy = fdy * inv_r;
-            const float Qf = (float)L[1];
+            const float Qf = L[1];
             const float w2 = wu * wu + wv * wv;
             const float au = (1.f + w2) * Fpx - Qf * wu;
             const float av = -(1.f + w2) * Fpy - Qf * wv;
@@ -348,7 +368,7 @@ __global__ void __launch_bounds__(128) k_eval32(Eval32Args A)
                 A.alpha[2 * (size_t)o] = (double)(a3x * (xz * cp) + a3y * (xz * sp) - a3z * rho);
                 A.alpha[2 * (size_t)o + 1] = (double)(-a3x * sp + a3y * cp);
             }
-            if (A.want_psi) {
+            if (PSI) {
                 const double psi_e = (double)L[0] + (double)L[1] * (LOG2 + (double)log1pf(-0.25f * D2)) + 2.0 * (double)Fx;
                 A.psi[o] = psi_e + INV4PI * ((double)ol - LOG4 * (double)oq) + shift;
             }
@@ -380,16 +400,19 @@ __global__ void k_tgt_offsets(TreeView T, const int* __restrict__ leaves, int64_
     }
 }
 
+// per direct-act pair: (hi offset, first source of the near leaf), (lo offset, its source count)
 __global__ void k_pair_offsets(TreeView T, const uint64_t* __restrict__ tt, const uint32_t* __restrict__ ss,
                                int64_t n, float4* __restrict__ dc)
 {
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
-        const double* gs = T.geom + (size_t)ss[k] * GEOM_STRIDE;
+        const uint32_t sl = ss[k];
+        const double* gs = T.geom + (size_t)sl * GEOM_STRIDE;
         const double* gt = T.geom + (size_t)tt[k] * GEOM_STRIDE;
         const double dx = gs[0] - gt[0], dy = gs[1] - gt[1], dz = gs[2] - gt[2];
         const float hx = (float)dx, hy = (float)dy, hz = (float)dz;
-        dc[2 * k] = make_float4(hx, hy, hz, 0.f);
-        dc[2 * k + 1] = make_float4((float)(dx - (double)hx), (float)(dy - (double)hy), (float)(dz - (double)hz), 0.f);
+        dc[2 * k] = make_float4(hx, hy, hz, __int_as_float(T.first[sl]));
+        dc[2 * k + 1] = make_float4((float)(dx - (double)hx), (float)(dy - (double)hy), (float)(dz - (double)hz),
+                                    __int_as_float(T.count[sl]));
     }
 }
 
@@ -438,7 +461,9 @@ cudaError_t launch_eval32(const TreeView& T, const int* leaves, int64_t n_leaves
     A.alpha = alpha;
     int64_t blocks = (n_leaves + 3) / 4;
     if (blocks > 152 * 64) blocks = 152 * 64;
-    k_eval32<<<(unsigned)blocks, 128, 0, s>>>(A); count_launch();
+    if (psi) k_eval32<true><<<(unsigned)blocks, 128, 0, s>>>(A);
+    else k_eval32<false><<<(unsigned)blocks, 128, 0, s>>>(A);
+    count_launch();
     return cudaGetLastError();
 }
 

@@ -196,8 +196,9 @@ __global__ void __launch_bounds__(128) k_m2l_tc(int64_t n_pairs, const uint64_t*
             const XGeo32T G = geo[k];
             const int s = (int)psrc[k];
             t_node = (int)ptgt[k];
-            const float* e = mpole + (size_t)s * EXP_STRIDE;
-            Qs = e[1];
+            const float* e = mpole + (size_t)s * EXP_STRIDE;     // rows are 8-byte aligned: float2 loads
+            const float2 cq = *reinterpret_cast<const float2*>(e);
+            Qs = cq.y;
             big = G.big != 0;
             rho = G.rho;
             const float ar = G.ar, ai = G.ai;
@@ -209,12 +210,16 @@ __global__ void __launch_bounds__(128) k_m2l_tc(int64_t n_pairs, const uint64_t*
                 const float nr = zr * ar - zi * ai, ni = zr * ai + zi * ar;
                 zr = nr; zi = ni;
                 float xr = 0.f, xi = 0.f;
-                if (l < p) { xr = e[2 + 2 * l]; xi = e[3 + 2 * l]; }
+                if (l < p) {
+                    const float2 x2 = *reinterpret_cast<const float2*>(e + 2 + 2 * l);
+                    xr = x2.x;
+                    xi = x2.y;
+                }
                 Xr[l] = zr * xr - zi * xi;
                 Xi[l] = zr * xi + zi * xr;
                 csum += Xr[l];
             }
-            Cc = e[0] + 2.f * e[1] * G.logk + 2.f * csum;
+            Cc = cq.x + 2.f * cq.y * G.logk + 2.f * csum;
             if (big && part == 0) {
                 const uint32_t slot = atomicAdd(n_leftover, 1u);
                 leftover[slot] = (uint32_t)k;
