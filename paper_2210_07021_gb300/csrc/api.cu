@@ -518,7 +518,7 @@ void sfmm_destroy(sfmm_plan_t plan)
                   &plan->m2l_t, &plan->m2l_s, &plan->m2l_t2, &plan->m2l_s2, &plan->p2p_t, &plan->p2p_s,
                   &plan->p2p_t2, &plan->p2p_s2, &plan->m2l_off, &plan->p2p_off, &plan->leaves_src,
                   &plan->leaves_tgt, &plan->m2l_geo, &plan->m2m_geo, &plan->l2l_geo, &plan->soff,
-                  &plan->toff, &plan->dc, &plan->leftover, &plan->geom32};
+                  &plan->toff, &plan->dc, &plan->leftover, &plan->geom32, &plan->macn};
     for (Buf* b : all) release(*b);
     delete plan;
 }

@@ -107,10 +107,12 @@ struct sfmm_plan_s {
     sfmm::Buf toff, dc;                    // FP32 (hi, lo) target offsets and near-leaf centre offsets
     sfmm::Buf leftover;                    // M2L pairs left to the warp kernel by the tensor-core kernel
     sfmm::Buf geom32;                      // FP32 frame vectors and scale per node (mixed path)
+    sfmm::Buf macn;                        // per-node sin/cos of the radii for the MAC
     // lists
     sfmm::Buf fa, fb, act, c_next, c_m2l, c_p2p, o_next, o_m2l, o_p2p;
     sfmm::Buf m2l_t, m2l_s, m2l_t2, m2l_s2, p2p_t, p2p_s, p2p_t2, p2p_s2, m2l_off, p2p_off;
     int64_t n_m2l = 0, n_p2p = 0;
+    int64_t walk_cap_front = 0, walk_cap_m2l = 0, walk_cap_p2p = 0;   // list capacities that sufficed last time
     bool m2l_alt = false, p2p_alt = false;
     // node work lists
     sfmm::Buf leaves_src, leaves_tgt;
