@@ -131,6 +131,89 @@ __device__ __forceinline__ XGeo make_geo(int kind, const double* gS, const doubl
 }
 
 __device__ __forceinline__ void store_geo(XGeo* out, const XGeo& G) { *out = G; }
+// Mixed path: the same parameters computed in FP32 from the FP64 centre
+// difference and sum (exact to rounding) and FP32 frame vectors; only the
+// six centre differences/sums use the FP64 pipe.
+__device__ __forceinline__ XGeo32 make_geo32(int kind, const double* gS, const double* gT, const float* fS,
+                                             const float* fT)
+{
+    const float dx = (float)(gT[0] - gS[0]), dy = (float)(gT[1] - gS[1]), dz = (float)(gT[2] - gS[2]);
+    const float sx = (float)(gT[0] + gS[0]), sy = (float)(gT[1] + gS[1]), sz = (float)(gT[2] + gS[2]);
+    const float d2 = dx * dx + dy * dy + dz * dz, s2 = sx * sx + sy * sy + sz * sz;
+    const float sh = 0.5f * sqrtf(d2), ch = 0.5f * sqrtf(s2);
+    const bool anti = s2 < d2;
+    const float vx = anti ? sx : dx, vy = anti ? sy : dy, vz = anti ? sz : dz;
+    const float sg = anti ? 1.f : -1.f;
+    float ux = vx * fS[0] + vy * fS[1] + vz * fS[2];
+    float uy = vx * fS[3] + vy * fS[4] + vz * fS[5];
+    float n2 = ux * ux + uy * uy;
+    float eTx = 1.f, eTy = 0.f, eSx = 1.f, eSy = 0.f;
+    if (n2 > 0.f) { const float inv = rsqrtf(n2); eTx = ux * inv; eTy = uy * inv; }
+    ux = sg * (vx * fT[0] + vy * fT[1] + vz * fT[2]);
+    uy = sg * (vx * fT[3] + vy * fT[4] + vz * fT[5]);
+    n2 = ux * ux + uy * uy;
+    if (n2 > 0.f) { const float inv = rsqrtf(n2); eSx = ux * inv; eSy = uy * inv; }
+    const float rS = fS[6], rT = fT[6];
+    XGeo32 H;
+    if (kind == K_M2L) {
+        const float c = ch / sh;
+        H.a = c * rS; H.b = c * rT; H.g = rS * rT / (sh * sh); H.logk = logf(sh);
+        H.p1x = eTx; H.p1y = -eTy; H.p2x = eSx; H.p2y = -eSy;
+    } else if (kind == K_M2M) {
+        const float t = sh / ch;
+        H.a = t * rS; H.b = t / rT; H.g = (1.f + t * t) * rS / rT; H.logk = logf(ch);
+        H.p1x = -eTx; H.p1y = eTy; H.p2x = eSx; H.p2y = eSy;
+    } else {
+        const float t = sh / ch;
+        H.a = t / rS; H.b = t * rT; H.g = (1.f + t * t) * rT / rS; H.logk = logf(ch);
+        H.p1x = eTx; H.p1y = eTy; H.p2x = -eSx; H.p2y = eSy;
+    }
+    H.ar = H.a * H.p1x; H.ai = H.a * H.p1y;
+    H.br = H.b * H.p2x; H.bi = H.b * H.p2y;
+    // rho = g/(a b) = 1/cos^2(theta/2) for M2L; its 32nd power must stay below 2^100
+    const float ab = H.a * H.b;
+    const bool big = !(ab > 0.f) || H.g > ab * 8.7f;
+    H.rho = big ? 0.f : H.g / ab;
+    H.big = big ? 1 : 0;
+    H.pad[0] = H.pad[1] = 0.f;
+    return H;
+}
+
+// FP32 frame vectors and scale of every node (e_theta, e_phi, r, padding)
+__global__ void k_geom32(int n_nodes, const double* __restrict__ geom, float* __restrict__ g32)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_nodes; i += (int64_t)gridDim.x * blockDim.x) {
+        const double* g = geom + (size_t)i * GEOM_STRIDE;
+        float* o = g32 + (size_t)i * 8;
+        for (int k = 0; k < 6; ++k) o[k] = (float)g[3 + k];
+        o[6] = (float)g[10];
+        o[7] = 0.f;
+    }
+}
+
+__global__ void k_pair_geo32(TreeView T, const float* __restrict__ g32, const uint64_t* __restrict__ tt,
+                             const uint32_t* __restrict__ ss, int64_t n, XGeo32* __restrict__ out)
+{
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t s = ss[k], t = (uint32_t)tt[k];
+        out[k] = make_geo32(K_M2L, T.geom + (size_t)s * GEOM_STRIDE, T.geom + (size_t)t * GEOM_STRIDE,
+                            g32 + (size_t)s * 8, g32 + (size_t)t * 8);
+    }
+}
+
+__global__ void k_child_geo32(TreeView T, const float* __restrict__ g32, XGeo32* __restrict__ m2m,
+                              XGeo32* __restrict__ l2l)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < T.n_nodes; i += (int64_t)gridDim.x * blockDim.x) {
+        const int par = T.parent[i];
+        if (par < 0) continue;
+        const double* gC = T.geom + (size_t)i * GEOM_STRIDE;
+        const double* gP = T.geom + (size_t)par * GEOM_STRIDE;
+        m2m[i] = make_geo32(K_M2M, gC, gP, g32 + (size_t)i * 8, g32 + (size_t)par * 8);
+        l2l[i] = make_geo32(K_L2L, gP, gC, g32 + (size_t)par * 8, g32 + (size_t)i * 8);
+    }
+}
+
 template <typename GR>
 __global__ void k_pair_geo(TreeView T, const uint64_t* __restrict__ tt, const uint32_t* __restrict__ ss, int64_t n,
                            GR* __restrict__ out)
