@@ -59,15 +59,18 @@ typedef enum {
 } sfmm_status;
 
 enum {
-    SFMM_FP64 = 0,         /* every step in float64                                     */
-    SFMM_MIXED = 1         /* near field and M2L in reduced precision  */
+    SFMM_FP64 = 0,         /* every step in float64                                                */
+    SFMM_MIXED = 1,        /* relative error near 1e-6: expansions, translations and the near field
+                              in float32, M2L on the tensor cores as split-bfloat16 products       */
+    SFMM_MIXED_DF = 2      /* relative error near 1e-10: expansions and translations in float64,
+                              the near field in double-float (pairs of float32) on the FP32 pipe   */
 };
 
 typedef struct {
     int leaf_size;         /* m of Sec. 3.1: split boxes holding more than m particles; 0 = default 32 */
     double c_s;            /* MAC1 constant of Sec. 3.5 (d - R_T - c_s R_S > 0); 0 = default 2.0 */
     double c_t;            /* MAC2 constant of Sec. 3.5 (R_T < c_t d);            0 = default 0.5 */
-    int precision;         /* SFMM_FP64 or SFMM_MIXED                                             */
+    int precision;         /* SFMM_FP64, SFMM_MIXED or SFMM_MIXED_DF                              */
     int zero_mean;         /* 1: add sum(q)/(4 pi) to psi (Eq. STAND_CONDITION)                    */
     int q_f32;             /* 1: the mass array is float32 instead of float64                      */
     int64_t n_max, m_max;  /* optional: size the workspace for up to n_max sources and m_max targets

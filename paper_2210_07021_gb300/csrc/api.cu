@@ -17,19 +17,19 @@ cudaError_t tree_target_ranges(sfmm_plan_s* P, const uint64_t* tkeys, int64_t M)
 cudaError_t collect_leaves(sfmm_plan_s* P, const int* cnt, Buf& out, int64_t* n_out);
 cudaError_t build_lists(sfmm_plan_s* P, const TreeView& T, double c_s, double c_t);
 void fill_tables(double* h);
-size_t xgeo_bytes(bool fp32);
+size_t xgeo_bytes(int ek);
 cudaError_t launch_geom32(int n_nodes, const double* geom, float* g32, cudaStream_t s);
 cudaError_t launch_pair_geo(const TreeView& T, const float* g32, const uint64_t* tt, const uint32_t* ss, int64_t n,
-                            void* out, bool fp32, cudaStream_t s);
-cudaError_t launch_child_geo(const TreeView& T, const float* g32, void* m2m, void* l2l, bool fp32, cudaStream_t s);
+                            void* out, int ek, cudaStream_t s);
+cudaError_t launch_child_geo(const TreeView& T, const float* g32, void* m2m, void* l2l, int ek, cudaStream_t s);
 cudaError_t launch_src_offsets(const TreeView& T, const int* leaves, int64_t n_leaves, const double4_32a* src,
                                float4* off, cudaStream_t s);
 cudaError_t launch_p2m(const TreeView& T, const int* leaves, int64_t n_leaves, const double4_32a* src,
-                       const float4* off, void* mpole, int p, bool fp32, cudaStream_t s);
+                       const float4* off, void* mpole, int p, int ek, cudaStream_t s);
 cudaError_t launch_m2m(const TreeView& T, int a, int b, int p, const double* tables, const void* geo, void* mpole,
-                       bool fp32, cudaStream_t s);
+                       int ek, cudaStream_t s);
 cudaError_t launch_m2l(const TreeView& T, const int64_t* off, const uint32_t* srcs, int p, const double* tables,
-                       const void* geo, const void* mpole, void* local, bool fp32, cudaStream_t s);
+                       const void* geo, const void* mpole, void* local, int ek, cudaStream_t s);
 cudaError_t launch_m2l_list(const uint64_t* ptgt, const uint32_t* psrc, const uint32_t* list, const uint32_t* n_list,
                             int64_t max_list, int p, const double* tables, const void* geo, const void* mpole,
                             void* local, cudaStream_t s);
@@ -37,9 +37,9 @@ cudaError_t launch_m2l_tc(int64_t n_pairs, const uint64_t* ptgt, const uint32_t*
                           const void* mpole, void* local, int p, uint32_t* leftover, uint32_t* n_leftover,
                           int* status, cudaStream_t s);
 cudaError_t launch_l2l(const TreeView& T, int a, int b, int p, const double* tables, const void* geo, void* local,
-                       bool fp32, cudaStream_t s);
+                       int ek, cudaStream_t s);
 cudaError_t launch_unscale(int n_nodes, const double* geom, const void* in, double* out, int p, int is_local,
-                           bool fp32, cudaStream_t s);
+                           int ek, cudaStream_t s);
 cudaError_t launch_eval32_prep(const TreeView& T, const int* leaves, int64_t n_leaves, const double4_32a* tgt,
                                float4* toff, const uint64_t* p2p_t, const uint32_t* p2p_s, int64_t n_p2p, float4* dc,
                                cudaStream_t s);
@@ -49,6 +49,11 @@ cudaError_t launch_eval32(const TreeView& T, const int* leaves, int64_t n_leaves
                           double* psi, double* alpha, cudaStream_t s);
 cudaError_t launch_count_pairs(const TreeView& T, const int* leaves, int64_t n_leaves, const int64_t* p2p_off,
                                const uint32_t* p2p_src, unsigned long long* out, cudaStream_t s);
+void fill_log_table(float* out);
+cudaError_t launch_eval_df(const TreeView& T, const int* leaves, int64_t n_leaves, const float4* soff,
+                           const float4* toff, const float4* dc, const double4_32a* tgt, const uint32_t* tperm,
+                           const int64_t* p2p_off, const uint32_t* p2p_src, const void* local, const void* mpole,
+                           const float4* log_tab, int p, int zero_mean, double* psi, double* alpha, cudaStream_t s);
 cudaError_t launch_eval(const TreeView& T, const int* leaves, int64_t n_leaves, const double4_32a* src, const double4_32a* tgt,
                         const uint32_t* tperm, const int64_t* p2p_off, const uint32_t* p2p_src, const double* local,
                         const double* mpole, int p, int zero_mean, double* psi, double* alpha, cudaStream_t s);
@@ -256,32 +261,35 @@ sfmm_status solve(sfmm_plan_s* P, const double* src, const void* q, int64_t N, c
     tm.mark();
     // ---- up-pass
     const bool fp32 = P->opt.precision == SFMM_MIXED;
-    const size_t esz = fp32 ? 4 : 8;                   // expansion storage: float (mixed) or double
+    const bool dfe = P->opt.precision == SFMM_MIXED_DF;
+    const bool offsets = fp32 || dfe;                  // FP32 (hi, lo) offsets feed the near field
+    const int ek = fp32 ? EXP_F32 : dfe ? EXP_DF : EXP_F64;
+    const size_t esz = fp32 ? 4 : 8;                   // expansion storage: float, double or double-float
     if ((e = ensure(P->mpole, (size_t)nn * EXP_STRIDE * esz)) || (e = ensure(P->local, (size_t)nn * EXP_STRIDE * esz)))
         return cuda_fail(P, e, "alloc expansions");
     if ((e = cudaMemsetAsync(P->mpole.p, 0, (size_t)nn * EXP_STRIDE * esz, s))) return cuda_fail(P, e, "memset");
-    if ((e = ensure(P->m2m_geo, (size_t)nn * xgeo_bytes(fp32))) || (e = ensure(P->l2l_geo, (size_t)nn * xgeo_bytes(fp32))))
+    if ((e = ensure(P->m2m_geo, (size_t)nn * xgeo_bytes(ek))) || (e = ensure(P->l2l_geo, (size_t)nn * xgeo_bytes(ek))))
         return cuda_fail(P, e, "alloc");
     if (fp32) {
         if ((e = ensure(P->geom32, (size_t)nn * 32))) return cuda_fail(P, e, "alloc");
         if ((e = launch_geom32((int)nn, P->n_geom.as<double>(), P->geom32.as<float>(), s)))
             return cuda_fail(P, e, "geometry32");
     }
-    if ((e = launch_child_geo(T, P->geom32.as<float>(), P->m2m_geo.p, P->l2l_geo.p, fp32, s)))
+    if ((e = launch_child_geo(T, P->geom32.as<float>(), P->m2m_geo.p, P->l2l_geo.p, ek, s)))
         return cuda_fail(P, e, "child geometry");
-    if (fp32) {
+    if (offsets) {
         if ((e = ensure(P->soff, (size_t)N * 32))) return cuda_fail(P, e, "alloc");
         if ((e = launch_src_offsets(T, P->leaves_src.as<int>(), P->n_leaves, P->src4.as<double4_32a>(),
                                     P->soff.as<float4>(), s)))
             return cuda_fail(P, e, "offsets");
     }
     if ((e = launch_p2m(T, P->leaves_src.as<int>(), P->n_leaves, P->src4.as<double4_32a>(), P->soff.as<float4>(),
-                        P->mpole.p, p, fp32, s)))
+                        P->mpole.p, p, ek, s)))
         return cuda_fail(P, e, "P2M");
     const int depth = (int)P->level_start.size() - 2;
     for (int l = depth - 1; l >= 0; --l)
         if ((e = launch_m2m(T, P->level_start[l], P->level_start[l + 1], p, P->tables.as<double>(), P->m2m_geo.p,
-                            P->mpole.p, fp32, s)))
+                            P->mpole.p, ek, s)))
             return cuda_fail(P, e, "M2M");
     tm.mark();
     // ---- lists
@@ -291,8 +299,8 @@ sfmm_status solve(sfmm_plan_s* P, const double* src, const void* q, int64_t N, c
     if ((e = cudaMemsetAsync(P->local.p, 0, (size_t)nn * EXP_STRIDE * esz, s))) return cuda_fail(P, e, "memset");
     const uint32_t* m2l_s = P->m2l_alt ? P->m2l_s2.as<uint32_t>() : P->m2l_s.as<uint32_t>();
     const uint64_t* m2l_t = P->m2l_alt ? P->m2l_t2.as<uint64_t>() : P->m2l_t.as<uint64_t>();
-    if ((e = ensure(P->m2l_geo, (size_t)std::max<int64_t>(P->n_m2l, 1) * xgeo_bytes(fp32)))) return cuda_fail(P, e, "alloc");
-    if ((e = launch_pair_geo(T, P->geom32.as<float>(), m2l_t, m2l_s, P->n_m2l, P->m2l_geo.p, fp32, s)))
+    if ((e = ensure(P->m2l_geo, (size_t)std::max<int64_t>(P->n_m2l, 1) * xgeo_bytes(ek)))) return cuda_fail(P, e, "alloc");
+    if ((e = launch_pair_geo(T, P->geom32.as<float>(), m2l_t, m2l_s, P->n_m2l, P->m2l_geo.p, ek, s)))
         return cuda_fail(P, e, "pair geometry");
     int* status = reinterpret_cast<int*>(P->small.as<int64_t>() + 20);
     if (fp32 && P->opt.m2l_tensor_cores) {
@@ -307,19 +315,19 @@ sfmm_status solve(sfmm_plan_s* P, const double* src, const void* q, int64_t N, c
                                  P->m2l_geo.p, P->mpole.p, P->local.p, s)))
             return cuda_fail(P, e, "M2L (leftover pairs)");
     } else if ((e = launch_m2l(T, P->m2l_off.as<int64_t>(), m2l_s, p, P->tables.as<double>(), P->m2l_geo.p, P->mpole.p,
-                               P->local.p, fp32, s))) {
+                               P->local.p, ek, s))) {
         return cuda_fail(P, e, "M2L");
     }
     tm.mark();
     // ---- L2L
     for (int l = 1; l <= depth; ++l)
         if ((e = launch_l2l(T, P->level_start[l], P->level_start[l + 1], p, P->tables.as<double>(), P->l2l_geo.p,
-                            P->local.p, fp32, s)))
+                            P->local.p, ek, s)))
             return cuda_fail(P, e, "L2L");
     tm.mark();
     // ---- evaluation
     const uint32_t* p2p_s = P->p2p_alt ? P->p2p_s2.as<uint32_t>() : P->p2p_s.as<uint32_t>();
-    if (fp32) {
+    if (offsets) {
         const uint64_t* p2p_t = P->p2p_alt ? P->p2p_t2.as<uint64_t>() : P->p2p_t.as<uint64_t>();
         if ((e = ensure(P->toff, (size_t)M * 32)) || (e = ensure(P->dc, (size_t)std::max<int64_t>(P->n_p2p, 1) * 32)))
             return cuda_fail(P, e, "alloc");
@@ -330,6 +338,10 @@ sfmm_status solve(sfmm_plan_s* P, const double* src, const void* q, int64_t N, c
     if (fp32) e = launch_eval32(T, P->leaves_tgt.as<int>(), P->n_leaves_tgt, P->soff.as<float4>(),
                                 P->toff.as<float4>(), P->dc.as<float4>(), P->tgt4.as<double4_32a>(), tperm, P->p2p_off.as<int64_t>(), p2p_s,
                                 P->local.as<float>(), P->mpole.as<float>(), p, P->opt.zero_mean, psi, alpha, s);
+    else if (dfe) e = launch_eval_df(T, P->leaves_tgt.as<int>(), P->n_leaves_tgt, P->soff.as<float4>(),
+                                     P->toff.as<float4>(), P->dc.as<float4>(), P->tgt4.as<double4_32a>(), tperm,
+                                     P->p2p_off.as<int64_t>(), p2p_s, P->local.p, P->mpole.p,
+                                     P->logtab.as<float4>(), p, P->opt.zero_mean, psi, alpha, s);
     else e = launch_eval(T, P->leaves_tgt.as<int>(), P->n_leaves_tgt, P->src4.as<double4_32a>(),
                          P->tgt4.as<double4_32a>(), tperm, P->p2p_off.as<int64_t>(), p2p_s, P->local.as<double>(),
                          P->mpole.as<double>(), p, P->opt.zero_mean, psi, alpha, s);
@@ -421,7 +433,8 @@ sfmm_status sfmm_plan(sfmm_plan_t* out, int max_depth, int order_p, double tol, 
     if (o.leaf_size < 1) return plan_fail("leaf_size must be >= 1");
     if (!(o.c_s > 1.0)) return plan_fail("c_s must be > 1 (Sec. 3.5)");
     if (!(o.c_t > 0.0 && o.c_t < 1.0)) return plan_fail("c_t must be in (0, 1) (Sec. 3.5)");
-    if (o.precision != SFMM_FP64 && o.precision != SFMM_MIXED) return plan_fail("unknown precision");
+    if (o.precision != SFMM_FP64 && o.precision != SFMM_MIXED && o.precision != SFMM_MIXED_DF)
+        return plan_fail("unknown precision");
     if (o.n_max < 0 || o.m_max < 0) return plan_fail("n_max and m_max must be >= 0");
     auto* P = new (std::nothrow) sfmm_plan_s();
     if (!P) return SFMM_ENOMEM;
@@ -432,9 +445,12 @@ sfmm_status sfmm_plan(sfmm_plan_t* out, int max_depth, int order_p, double tol, 
     P->stream = static_cast<cudaStream_t>(o.stream);
     std::vector<double> h(2 * PMAX * PMAX);
     fill_tables(h.data());
+    float lt[129 * 4];
+    fill_log_table(lt);
     cudaError_t e;
     if ((e = ensure(P->tables, h.size() * 8)) ||
-        (e = cudaMemcpy(P->tables.p, h.data(), h.size() * 8, cudaMemcpyHostToDevice))) {
+        (e = cudaMemcpy(P->tables.p, h.data(), h.size() * 8, cudaMemcpyHostToDevice)) ||
+        (e = ensure(P->logtab, sizeof lt)) || (e = cudaMemcpy(P->logtab.p, lt, sizeof lt, cudaMemcpyHostToDevice))) {
         std::lock_guard<std::mutex> g(g_err_mu);
         g_plan_err = std::string("CUDA error at plan time: ") + cudaGetErrorString(e);
         delete P;
@@ -608,7 +624,9 @@ sfmm_status sfmm_debug_copy(sfmm_plan_t plan, int which, void* dst, int64_t byte
         if ((e = ensure(tmpbuf, need))) return cuda_fail(P, e, "alloc");
         const Buf& in = which == SFMM_ARR_MULTIPOLE ? P->mpole : P->local;
         if ((e = launch_unscale((int)nn, P->n_geom.as<double>(), in.p, tmpbuf.as<double>(), p,
-                                which == SFMM_ARR_LOCAL, P->opt.precision == SFMM_MIXED, P->stream)) ||
+                                which == SFMM_ARR_LOCAL,
+                                P->opt.precision == SFMM_MIXED ? EXP_F32 : P->opt.precision == SFMM_MIXED_DF ? EXP_DF : EXP_F64,
+                                P->stream)) ||
             (e = cudaStreamSynchronize(P->stream)) || (e = cudaMemcpy(dst, tmpbuf.p, need, cudaMemcpyDeviceToHost))) {
             release(tmpbuf);
             return cuda_fail(P, e, "unscale");

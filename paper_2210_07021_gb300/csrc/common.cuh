@@ -60,6 +60,11 @@ cudaError_t radix_sort(uint64_t* k1, uint32_t* v1, uint64_t* k2, uint32_t* v2, i
 // ------------------------------------------------------------------- keys
 cudaError_t launch_keys(const double* xyz, int64_t n, uint64_t* keys, uint32_t* iota, cudaStream_t s);
 
+// ------------------------------------------------------ expansion storage
+// Number format of the expansions and translations: FP64, FP32 (mixed path)
+// or double-float pairs of FP32 (1e-10 mixed path).
+enum { EXP_F64 = 0, EXP_F32 = 1, EXP_DF = 2 };
+
 // --------------------------------------------------------------- the tree
 struct TreeView {
     int n_nodes;
@@ -106,6 +111,7 @@ struct sfmm_plan_s {
     sfmm::Buf soff;                        // FP32 (hi, lo) source offsets from their leaf centres (mixed path)
     sfmm::Buf toff, dc;                    // FP32 (hi, lo) target offsets and near-leaf centre offsets
     sfmm::Buf leftover;                    // M2L pairs left to the warp kernel by the tensor-core kernel
+    sfmm::Buf logtab;                      // double-float evaluation: log(1 + j/128), 128/(128 + j), log 2
     sfmm::Buf geom32;                      // FP32 frame vectors and scale per node (mixed path)
     sfmm::Buf macn;                        // per-node sin/cos of the radii for the MAC
     // lists

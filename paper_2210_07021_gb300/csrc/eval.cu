@@ -20,6 +20,9 @@
 // (a power of two >= the target count, at most 32); each target gets
 // 32/tpw lanes that split its sources and are combined by xor shuffles.
 #include "common.cuh"
+#include "dfloat.cuh"
+
+#include <cmath>
 
 namespace sfmm {
 
@@ -219,7 +222,7 @@ __global__ void __launch_bounds__(128) k_eval32(Eval32Args A)
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     double shift = 0.0;
     if (A.zero_mean)
-        for (int b = 0; b < 12; ++b) shift += A.base_mpole[(size_t)b * EXP_STRIDE + 1];
+        for (int b = 0; b < 12; ++b) shift += (double)A.base_mpole[(size_t)b * EXP_STRIDE + 1];
     float4* yh = s_hi[wid];
     float4* yl = s_lo[wid];
     int* pre = s_pre[wid];
@@ -376,6 +379,231 @@ __global__ void __launch_bounds__(128) k_eval32(Eval32Args A)
     }
 }
 
+// ------------------------------------------------------------------------
+// Double-float evaluation (SFMM_MIXED_DF, stated error 1e-10).  The same
+// staging as k_eval32; the pair loop carries every quantity as an unevaluated
+// sum of two FP32 numbers (about 48 significant bits), on the FP32 pipe:
+//   d = t - y from the (hi, lo) offsets with an error-free two-difference,
+//   d^2 with error-free products (fma), 1/d^2 from the MUFU reciprocal and one
+//   Newton correction, the alpha and sum-q accumulators as FP32 pairs,
+//   log d^2 = e ln2 + log c_j + log1p(r): c_j = 1 + j/128 from the top mantissa
+//   bits, log c_j and 1/c_j from a 128-entry table computed in FP64 on the host
+//   (a table-driven logarithm in the manner of Tang, ACM TOMS 16, 1990),
+//   |r| < 2^-7 so r - r^2/2 + ... + r^6/6 reaches double-float accuracy.
+// L2P (with FP64 local expansions) and the final combination are FP64.
+__device__ __forceinline__ dflt dfl_sqr(dflt a)
+{
+    const float p = __fmul_rn(a.h, a.h);
+    const float e = __fmaf_rn(a.h, a.h, -p);
+    return dfl_fast_two_sum(p, __fmaf_rn(2.f * a.h, a.l, e));
+}
+
+__device__ __forceinline__ dflt dfl_log(dflt x, const float4* __restrict__ tab)
+{
+    const int bits = __float_as_int(x.h);
+    const int ex = ((bits >> 23) & 0xFF) - 127;
+    const int j = (bits >> 16) & 0x7F;
+    const float m = __int_as_float((bits & 0x007FFFFF) | 0x3F800000);     // [1, 2)
+    const float cj = 1.f + (float)j * (1.f / 128.f);
+    const float4 t = tab[j];                                              // log c_j (hi, lo), 1/c_j (hi, lo)
+    // x = 2^ex (m + l 2^-ex); delta = m - c_j is exact, r = (delta + l 2^-ex) / c_j, |r| < 2^-7
+    const float scale = __int_as_float((127 - ex) << 23);                 // 2^-ex; ex lies in [-126, 127]
+    const dflt delta = dfl_two_sum(__fsub_rn(m, cj), x.l * scale);
+    const dflt r = delta * dflt(t.z, t.w);
+    const float rh = r.h;
+    // log1p(r) - r to within r^7/7 < 2^-52, plus the cross term -r_hi r_lo of -r^2/2
+    float poly = rh * rh * (-0.5f + rh * (1.f / 3.f + rh * (-0.25f + rh * (0.2f + rh * (-1.f / 6.f)))));
+    poly = fmaf(-rh, r.l, poly);
+    dflt lg = r + dflt(poly, 0.f);
+    lg = lg + dflt(t.x, t.y);
+    const float4 l2 = tab[128];                                           // log 2 (hi, lo)
+    return lg + dflt(l2.x, l2.y) * (float)ex;
+}
+
+struct EvalDfArgs {
+    TreeView T;
+    const int* leaves;
+    int64_t n_leaves;
+    const float4* soff;
+    const float4* toff;
+    const float4* dc;
+    const double4_32a* tgt;
+    const uint32_t* tperm;
+    const int64_t* p2p_off;
+    const uint32_t* p2p_src;
+    const dflt* local;         // double-float local expansions
+    const dflt* base_mpole;
+    const float4* log_tab;     // [129]: log c_j and 1/c_j as (hi, lo) pairs, then log 2
+    int p;
+    int zero_mean;
+    double* psi;
+    double* alpha;
+};
+
+template <bool PSI>
+__global__ void __launch_bounds__(128) k_eval_df(EvalDfArgs A)
+{
+    __shared__ float4 s_hi[4][STAGE];
+    __shared__ float4 s_lo[4][STAGE];
+    __shared__ float s_dc[4][32][6];
+    __shared__ int s_pre[4][33];
+    __shared__ int s_first[4][32];
+    __shared__ float4 s_tab[129];
+    for (int i = threadIdx.x; i < 129; i += blockDim.x) s_tab[i] = A.log_tab[i];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    double shift = 0.0;
+    if (A.zero_mean)
+        for (int b = 0; b < 12; ++b) shift += (double)A.base_mpole[(size_t)b * EXP_STRIDE + 1];
+    float4* yh = s_hi[wid];
+    float4* yl = s_lo[wid];
+    int* pre = s_pre[wid];
+    int* fst = s_first[wid];
+    for (int64_t w = warp0; w < A.n_leaves; w += nwarps) {
+        const int leaf = A.leaves[w];
+        const int tf = A.T.tfirst[leaf], tc = A.T.tcount[leaf];
+        const double* g = A.T.geom + (size_t)leaf * GEOM_STRIDE;
+        const dflt* L = A.local + (size_t)leaf * EXP_STRIDE;
+        const int64_t nb0 = A.p2p_off[leaf], nb1 = A.p2p_off[leaf + 1];
+        int tpw = 1;
+        while (tpw < tc && tpw < 32) tpw <<= 1;
+        const int lpt = 32 / tpw;
+        const int slot = lane / lpt, sub = lane % lpt;
+        for (int tb = 0; tb < tc; tb += tpw) {
+            const int ti = tb + slot;
+            const bool active = ti < tc;
+            const size_t tix = (size_t)tf + (active ? ti : 0);
+            const float4 th = A.toff[2 * tix], tl = A.toff[2 * tix + 1];
+            dflt ax{0.f, 0.f}, ay{0.f, 0.f}, az{0.f, 0.f}, aq{0.f, 0.f}, al{0.f, 0.f};
+            int64_t kn = nb0;
+            int jn = 0;
+            while (kn < nb1) {
+                __syncwarp();
+                const int64_t k = kn + lane;
+                int cnt = 0, first = 0;
+                float4 rh = make_float4(0.f, 0.f, 0.f, 0.f), rl = rh;
+                if (k < nb1) {
+                    rh = A.dc[2 * k];
+                    rl = A.dc[2 * k + 1];
+                    first = __float_as_int(rh.w) + (lane == 0 ? jn : 0);
+                    cnt = __float_as_int(rl.w) - (lane == 0 ? jn : 0);
+                }
+                int inc = cnt;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int t = __shfl_up_sync(FULL, inc, o);
+                    if (lane >= o) inc += t;
+                }
+                const unsigned fit = __ballot_sync(FULL, k < nb1 && inc <= STAGE);
+                const int nfit = __popc(fit);
+                int ns, nl;
+                if (nfit == 0) { ns = STAGE; nl = 1; }
+                else { ns = __shfl_sync(FULL, inc, nfit - 1); nl = nfit; }
+                pre[lane] = inc - cnt;
+                fst[lane] = first;
+                s_dc[wid][lane][0] = rh.x; s_dc[wid][lane][1] = rh.y; s_dc[wid][lane][2] = rh.z;
+                s_dc[wid][lane][3] = rl.x; s_dc[wid][lane][4] = rl.y; s_dc[wid][lane][5] = rl.z;
+                __syncwarp();
+                for (int idx = lane; idx < ns; idx += 32) {
+                    int lo = 0, hi = nl;
+                    while (hi - lo > 1) {
+                        const int mid = (lo + hi) >> 1;
+                        if (pre[mid] <= idx) lo = mid; else hi = mid;
+                    }
+                    const size_t j = (size_t)(fst[lo] + (idx - pre[lo]));
+                    const float4 h = A.soff[2 * j];
+                    const float4 l = A.soff[2 * j + 1];
+                    const float* d = s_dc[wid][lo];
+                    float sx, ex_, sy, ey_, sz, ez_;
+                    two_sum(h.x, d[0], &sx, &ex_);
+                    two_sum(h.y, d[1], &sy, &ey_);
+                    two_sum(h.z, d[2], &sz, &ez_);
+                    yh[idx] = make_float4(sx, sy, sz, h.w);
+                    yl[idx] = make_float4(ex_ + (l.x + d[3]), ey_ + (l.y + d[4]), ez_ + (l.z + d[5]), l.w);
+                }
+                if (nfit == 0) jn += STAGE;
+                else { kn += nfit; jn = 0; }
+                __syncwarp();
+                for (int j = sub; j < ns; j += lpt) {
+                    const float4 h = yh[j];
+                    const float4 l = yl[j];
+                    const dflt dx = dflt(th.x, tl.x) - dflt(h.x, l.x);
+                    const dflt dy = dflt(th.y, tl.y) - dflt(h.y, l.y);
+                    const dflt dz = dflt(th.z, tl.z) - dflt(h.z, l.z);
+                    dflt d2 = dfl_sqr(dx) + dfl_sqr(dy) + dfl_sqr(dz);
+                    const bool ok = d2.h > 0.f;
+                    const dflt q = ok ? dflt(h.w, l.w) : dflt(0.f, 0.f);           // mass as (hi, lo)
+                    if (!ok) d2 = dflt(1.f, 0.f);
+                    // 1/d^2: MUFU reciprocal (relative error < 2^-22) and one Newton step
+                    float r0;
+                    asm("rcp.approx.f32 %0, %1;" : "=f"(r0) : "f"(d2.h));
+                    const float e0 = __fmaf_rn(-d2.h, r0, 1.f) - d2.l * r0;
+                    const dflt r = dfl_fast_two_sum(r0, r0 * e0);
+                    const dflt wq = r * q;
+                    ax += wq * dx;
+                    ay += wq * dy;
+                    az += wq * dz;
+                    aq += q;
+                    if (PSI) al += dfl_log(d2, s_tab) * q;
+                }
+            }
+            // combine the lanes of a target in FP64
+            double sx = (double)ax.h + (double)ax.l, sy = (double)ay.h + (double)ay.l, sz = (double)az.h + (double)az.l;
+            double sq = (double)aq.h + (double)aq.l, sl = (double)al.h + (double)al.l;
+            sx = group_sum(sx, lpt);
+            sy = group_sum(sy, lpt);
+            sz = group_sum(sz, lpt);
+            sq = group_sum(sq, lpt);
+            if (PSI) sl = group_sum(sl, lpt);
+            if (!active || sub != 0) continue;
+            // ---- L2P in the leaf frame: frame coordinates in FP64 (as in k_eval),
+            // the Horner recurrences for F(w) and F'(w) in double-float
+            const double4_32a x = A.tgt[tix];
+            const double Dx = x.x - g[0], Dy = x.y - g[1], Dz = x.z - g[2];
+            const double D2 = Dx * Dx + Dy * Dy + Dz * Dz;
+            const double den = 2.0 - 0.5 * D2;
+            const double wu = (Dx * g[3] + Dy * g[4] + Dz * g[5]) / den;
+            const double wv = (Dx * g[6] + Dy * g[7] + Dz * g[8]) / den;
+            const double inv_r = 1.0 / g[10];
+            const dflt ox(wu * inv_r), oy(wv * inv_r);
+            dflt fx(0.f, 0.f), fy(0.f, 0.f), hx(0.f, 0.f), hy(0.f, 0.f);
+            for (int l = A.p; l >= 1; --l) {
+                const dflt cr = L[2 * l], ci = L[2 * l + 1];
+                const dflt nfx = fx * ox - fy * oy + cr, nfy = fx * oy + fy * ox + ci;
+                const dflt nhx = hx * ox - hy * oy + cr * (float)l, nhy = hx * oy + hy * ox + ci * (float)l;
+                fx = nfx; fy = nfy; hx = nhx; hy = nhy;
+            }
+            const cd F = mk((double)(fx * ox - fy * oy), 0.0);      // Re F(w) is all psi needs
+            const cd Fp = mk((double)hx * inv_r, (double)hy * inv_r);
+            const double C = (double)L[0], Q = (double)L[1];
+            const double w2 = wu * wu + wv * wv;
+            const double au = (1.0 + w2) * Fp.x - Q * wu;
+            const double av = -(1.0 + w2) * Fp.y - Q * wv;
+            const double cxx = g[0] + x.x, cyy = g[1] + x.y, czz = g[2] + x.z;
+            double a3x = au * (g[3] - wu * cxx) + av * (g[6] - wv * cxx);
+            double a3y = au * (g[4] - wu * cyy) + av * (g[7] - wv * cyy);
+            double a3z = au * (g[5] - wu * czz) + av * (g[8] - wv * czz);
+            a3x += INV2PI * (sx - 0.5 * x.x * sq);
+            a3y += INV2PI * (sy - 0.5 * x.y * sq);
+            a3z += INV2PI * (sz - 0.5 * x.z * sq);
+            const double rho = sqrt(x.x * x.x + x.y * x.y);
+            double cp = 1.0, sp = 0.0;
+            if (rho > 0.0) { cp = x.x / rho; sp = x.y / rho; }
+            const uint32_t o = A.tperm[tix];
+            if (A.alpha) {
+                A.alpha[2 * (size_t)o] = a3x * (x.z * cp) + a3y * (x.z * sp) - a3z * rho;
+                A.alpha[2 * (size_t)o + 1] = -a3x * sp + a3y * cp;
+            }
+            if (PSI) {
+                const double psi_e = C + Q * (LOG2 + log1p(-0.25 * D2)) + 2.0 * F.x;
+                A.psi[o] = psi_e + INV4PI * (sl - LOG4 * sq) + shift;
+            }
+        }
+    }
+}
+
 // Offsets for the mixed evaluation, formed once in FP64 and split into FP32
 // (hi, lo) pairs: each sorted target from its leaf's centre, and each near
 // leaf's centre from its target leaf's centre (one per direct-act pair).
@@ -463,6 +691,56 @@ cudaError_t launch_eval32(const TreeView& T, const int* leaves, int64_t n_leaves
     if (blocks > 152 * 64) blocks = 152 * 64;
     if (psi) k_eval32<true><<<(unsigned)blocks, 128, 0, s>>>(A);
     else k_eval32<false><<<(unsigned)blocks, 128, 0, s>>>(A);
+    count_launch();
+    return cudaGetLastError();
+}
+
+// Table of the double-float logarithm: entry j < 128 holds log(c_j) and 1/c_j,
+// c_j = 1 + j/128, each as an FP32 (hi, lo) pair rounded from FP64; entry 128
+// holds log 2 the same way.
+void fill_log_table(float* out)
+{
+    auto split = [](double v, float* hl) {
+        hl[0] = (float)v;
+        hl[1] = (float)(v - (double)hl[0]);
+    };
+    for (int j = 0; j < 128; ++j) {
+        const double c = 1.0 + j / 128.0;
+        split(std::log(c), out + 4 * j);
+        split(1.0 / c, out + 4 * j + 2);
+    }
+    split(std::log(2.0), out + 4 * 128);
+    out[4 * 128 + 2] = out[4 * 128 + 3] = 0.f;
+}
+
+cudaError_t launch_eval_df(const TreeView& T, const int* leaves, int64_t n_leaves, const float4* soff,
+                           const float4* toff, const float4* dc, const double4_32a* tgt, const uint32_t* tperm,
+                           const int64_t* p2p_off, const uint32_t* p2p_src, const void* local, const void* mpole,
+                           const float4* log_tab, int p, int zero_mean, double* psi, double* alpha, cudaStream_t s)
+{
+    if (n_leaves == 0) return cudaSuccess;
+    EvalDfArgs A;
+    A.T = T;
+    A.leaves = leaves;
+    A.n_leaves = n_leaves;
+    A.soff = soff;
+    A.toff = toff;
+    A.dc = dc;
+    A.tgt = tgt;
+    A.tperm = tperm;
+    A.p2p_off = p2p_off;
+    A.p2p_src = p2p_src;
+    A.local = static_cast<const dflt*>(local);
+    A.base_mpole = static_cast<const dflt*>(mpole);
+    A.log_tab = log_tab;
+    A.p = p;
+    A.zero_mean = zero_mean;
+    A.psi = psi;
+    A.alpha = alpha;
+    int64_t blocks = (n_leaves + 3) / 4;
+    if (blocks > 152 * 64) blocks = 152 * 64;
+    if (psi) k_eval_df<true><<<(unsigned)blocks, 128, 0, s>>>(A);
+    else k_eval_df<false><<<(unsigned)blocks, 128, 0, s>>>(A);
     count_launch();
     return cudaGetLastError();
 }

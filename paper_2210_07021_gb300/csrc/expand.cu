@@ -1,5 +1,6 @@
 // Expansions: P2M (Lemma 1), M2M (Lemma 2), M2L (Lemma 3), L2L (Lemma 4), in
-// FP64 (the FP64 path) or FP32 (the mixed path).
+// FP64 (the FP64 path), FP32 (the mixed path) or double-float (pairs of FP32
+// numbers on the FP32 pipe, the 1e-10 mixed path).
 //
 // Storage.  An expansion is (C, Q, A_1..A_p) in the frame K_P of its box
 // (zenith e_r(P), azimuth reference e_theta(P), Sec. 3.1), with the variable
@@ -32,6 +33,7 @@
 // (from centre differences), by k_pair_geo / k_child_geo; the translation
 // kernels run in FP64 or FP32 from them.
 #include "common.cuh"
+#include "dfloat.cuh"
 
 namespace sfmm {
 
@@ -56,6 +58,12 @@ struct __align__(16) XGeo32 {
     float rho;
     int big;
     float pad[2];
+};
+
+// The FP64 parameters rounded to double-float pairs (1e-10 mixed path).
+struct __align__(16) XGeoDF {
+    dflt a, b, g, logk;
+    dflt p1x, p1y, p2x, p2y;
 };
 
 enum { K_M2M = 0, K_M2L = 1, K_L2L = 2 };
@@ -131,6 +139,13 @@ __device__ __forceinline__ XGeo make_geo(int kind, const double* gS, const doubl
 }
 
 __device__ __forceinline__ void store_geo(XGeo* out, const XGeo& G) { *out = G; }
+__device__ __forceinline__ void store_geo(XGeoDF* out, const XGeo& G)
+{
+    XGeoDF D;
+    D.a = dflt(G.a); D.b = dflt(G.b); D.g = dflt(G.g); D.logk = dflt(G.logk);
+    D.p1x = dflt(G.p1x); D.p1y = dflt(G.p1y); D.p2x = dflt(G.p2x); D.p2y = dflt(G.p2y);
+    *out = D;
+}
 // Mixed path: the same parameters computed in FP32 from the FP64 centre
 // difference and sum (exact to rounding) and FP32 frame vectors; only the
 // six centre differences/sums use the FP64 pipe.
@@ -247,13 +262,32 @@ template <typename R> __device__ __forceinline__ cx<R> cmul2(cx<R> a, cx<R> b)
     return cmk<R>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 
+__device__ __forceinline__ float shfl_up(float v, int o) { return __shfl_up_sync(FULL, v, o); }
+__device__ __forceinline__ double shfl_up(double v, int o) { return __shfl_up_sync(FULL, v, o); }
+__device__ __forceinline__ dflt shfl_up(dflt v, int o) { return dfl_shfl_up(v, o); }
+__device__ __forceinline__ float shfl_xor(float v, int o) { return __shfl_xor_sync(FULL, v, o); }
+__device__ __forceinline__ double shfl_xor(double v, int o) { return __shfl_xor_sync(FULL, v, o); }
+__device__ __forceinline__ dflt shfl_xor(dflt v, int o) { return dfl_shfl_xor(v, o); }
+
+// Inner products of the translations: acc += a b.  FP32/FP64 contract to one
+// FMA; double-float accumulates lazily and is renormalised once after the loop.
+__device__ __forceinline__ float mul_lazy(float a, float b) { return a * b; }
+__device__ __forceinline__ double mul_lazy(double a, double b) { return a * b; }
+__device__ __forceinline__ dflt mul_lazy(dflt a, dflt b) { return dfl_mul_lazy(a, b); }
+__device__ __forceinline__ void mac(float& acc, float a, float b) { acc += a * b; }
+__device__ __forceinline__ void mac(double& acc, double a, double b) { acc += a * b; }
+__device__ __forceinline__ void mac(dflt& acc, dflt a, dflt b) { dfl_mac(acc, a, b); }
+__device__ __forceinline__ float renorm(float a) { return a; }
+__device__ __forceinline__ double renorm(double a) { return a; }
+__device__ __forceinline__ dflt renorm(dflt a) { return dfl_norm(a); }
+
 // x^(lane+1) for every lane (inclusive prefix product)
 template <typename R> __device__ __forceinline__ R warp_pow(R x, int lane)
 {
     R v = x;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-        const R t = __shfl_up_sync(FULL, v, o);
+        const R t = shfl_up(v, o);
         if (lane >= o) v *= t;
     }
     return v;
@@ -264,8 +298,8 @@ template <typename R> __device__ __forceinline__ cx<R> warp_cpow(cx<R> x, int la
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
         cx<R> t;
-        t.x = __shfl_up_sync(FULL, v.x, o);
-        t.y = __shfl_up_sync(FULL, v.y, o);
+        t.x = shfl_up(v.x, o);
+        t.y = shfl_up(v.y, o);
         if (lane >= o) v = cmul2(v, t);
     }
     return v;
@@ -273,7 +307,7 @@ template <typename R> __device__ __forceinline__ cx<R> warp_cpow(cx<R> x, int la
 template <typename R> __device__ __forceinline__ R warp_sum(R v)
 {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+    for (int o = 16; o > 0; o >>= 1) v += shfl_xor(v, o);
     return v;
 }
 
@@ -317,20 +351,22 @@ __device__ __forceinline__ void warp_translate(int p, int lane, const GR& G, R C
     __syncwarp();
     cx<R> v = cmk<R>(0, 0);
     for (int k = 0; k <= p - l; ++k) {
-        const R c = tb->t1[k * PMAX + lane] * ws->apow[k];
+        const R c = mul_lazy(tb->t1[k * PMAX + lane], ws->apow[k]);
         const cx<R> uu = ws->u[lane + k];
-        v.x += c * uu.x;
-        v.y += c * uu.y;
+        mac(v.x, c, uu.x);
+        mac(v.y, c, uu.y);
     }
+    v = cmk<R>(renorm(v.x), renorm(v.y));
     ws->w[lane] = on ? cmk<R>(v.x * gp, v.y * gp) : cmk<R>(0, 0);
     __syncwarp();
     cx<R> o = cmk<R>(-Qin * bp / (R)l, R(0));
     for (int k = 0; k < l && on; ++k) {
-        const R c = tb->t2[k * PMAX + lane] * ws->bpow[k];
+        const R c = mul_lazy(tb->t2[k * PMAX + lane], ws->bpow[k]);
         const cx<R> ww = ws->w[lane - k];
-        o.x += c * ww.x;
-        o.y += c * ww.y;
+        mac(o.x, c, ww.x);
+        mac(o.y, c, ww.y);
     }
+    o = cmk<R>(renorm(o.x), renorm(o.y));
     if (on) {
         const cx<R> y = cmul2(p2, o);
         accY->x += y.x;
@@ -385,9 +421,9 @@ __device__ __forceinline__ void atomic_exp(ST* e, int lane, int p, R C, R Q, cx<
 
 // ----------------------------------------------------------------- P2M
 // FP64: from the key-sorted FP64 positions.
-template <int P>
+template <int P, typename ST>
 __global__ void k_p2m(TreeView T, const int* __restrict__ leaves, int64_t n_leaves, const double4_32a* __restrict__ src,
-                      double* __restrict__ mpole)
+                      ST* __restrict__ mpole)
 {
     for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < n_leaves; w += (int64_t)gridDim.x * blockDim.x) {
         const int node = leaves[w];
@@ -416,17 +452,17 @@ __global__ void k_p2m(TreeView T, const int* __restrict__ leaves, int64_t n_leav
                 A[l] = cadd(A[l], zp);
             }
         }
-        double* e = mpole + (size_t)node * EXP_STRIDE;
+        ST* e = mpole + (size_t)node * EXP_STRIDE;
         const double Q = INV4PI * Qsum;
-        e[0] = INV4PI * Csum - Q * LOG2;
-        e[1] = Q;
+        e[0] = ST(INV4PI * Csum - Q * LOG2);
+        e[1] = ST(Q);
 #pragma unroll
         for (int l = 0; l < P; ++l) {
             const double s = -INV4PI / (double)(l + 1);
-            e[2 + 2 * l] = s * A[l].x;
-            e[3 + 2 * l] = s * A[l].y;
+            e[2 + 2 * l] = ST(s * A[l].x);
+            e[3 + 2 * l] = ST(s * A[l].y);
         }
-        for (int l = P; l < PMAX; ++l) { e[2 + 2 * l] = 0.0; e[3 + 2 * l] = 0.0; }
+        for (int l = P; l < PMAX; ++l) { e[2 + 2 * l] = ST(0.0); e[3 + 2 * l] = ST(0.0); }
     }
 }
 
@@ -587,7 +623,7 @@ __global__ void k_m2l_list(const uint64_t* __restrict__ ptgt, const uint32_t* __
 
 // FP32 offset of every key-sorted source from the centre of its leaf as an
 // (hi, lo) pair (hi = the FP64 difference rounded, lo = the remainder), plus
-// its mass: off[2j] = (hi, q), off[2j+1] = (lo, 0).
+// its mass split the same way: off[2j] = (hi, q_hi), off[2j+1] = (lo, q_lo).
 __global__ void k_src_offsets(TreeView T, const int* __restrict__ leaves, int64_t n_leaves,
                               const double4_32a* __restrict__ src, float4* __restrict__ off)
 {
@@ -602,9 +638,10 @@ __global__ void k_src_offsets(TreeView T, const int* __restrict__ leaves, int64_
             const double4_32a y = src[j];
             const double dx = y.x - g[0], dy = y.y - g[1], dz = y.z - g[2];
             const float hx = (float)dx, hy = (float)dy, hz = (float)dz;
-            off[2 * (size_t)j] = make_float4(hx, hy, hz, (float)y.w);
+            const float qh = (float)y.w;
+            off[2 * (size_t)j] = make_float4(hx, hy, hz, qh);
             off[2 * (size_t)j + 1] = make_float4((float)(dx - (double)hx), (float)(dy - (double)hy),
-                                                 (float)(dz - (double)hz), 0.f);
+                                                 (float)(dz - (double)hz), (float)(y.w - (double)qh));
         }
     }
 }
@@ -639,7 +676,7 @@ inline unsigned grid_for(int64_t n, int per_block)
 
 }  // namespace
 
-size_t xgeo_bytes(bool fp32) { return fp32 ? sizeof(XGeo32) : sizeof(XGeo); }
+size_t xgeo_bytes(int ek) { return ek == EXP_F32 ? sizeof(XGeo32) : ek == EXP_DF ? sizeof(XGeoDF) : sizeof(XGeo); }
 
 void fill_tables(double* h)   // [2][PMAX][PMAX]
 {
@@ -663,20 +700,22 @@ cudaError_t launch_geom32(int n_nodes, const double* geom, float* g32, cudaStrea
 }
 
 cudaError_t launch_pair_geo(const TreeView& T, const float* g32, const uint64_t* tt, const uint32_t* ss, int64_t n,
-                            void* out, bool fp32, cudaStream_t s)
+                            void* out, int ek, cudaStream_t s)
 {
     if (n == 0) return cudaSuccess;
-    if (fp32) k_pair_geo32<<<grid_for(n, 256), 256, 0, s>>>(T, g32, tt, ss, n, static_cast<XGeo32*>(out));
+    if (ek == EXP_F32) k_pair_geo32<<<grid_for(n, 256), 256, 0, s>>>(T, g32, tt, ss, n, static_cast<XGeo32*>(out));
+    else if (ek == EXP_DF) k_pair_geo<XGeoDF><<<grid_for(n, 256), 256, 0, s>>>(T, tt, ss, n, static_cast<XGeoDF*>(out));
     else k_pair_geo<XGeo><<<grid_for(n, 256), 256, 0, s>>>(T, tt, ss, n, static_cast<XGeo*>(out));
     count_launch();
     return cudaGetLastError();
 }
 
-cudaError_t launch_child_geo(const TreeView& T, const float* g32, void* m2m, void* l2l, bool fp32, cudaStream_t s)
+cudaError_t launch_child_geo(const TreeView& T, const float* g32, void* m2m, void* l2l, int ek, cudaStream_t s)
 {
-    if (fp32) k_child_geo32<<<grid_for(T.n_nodes, 256), 256, 0, s>>>(T, g32, static_cast<XGeo32*>(m2m),
-                                                                     static_cast<XGeo32*>(l2l));
-    else k_child_geo<XGeo><<<grid_for(T.n_nodes, 256), 256, 0, s>>>(T, static_cast<XGeo*>(m2m), static_cast<XGeo*>(l2l));
+    const unsigned g = grid_for(T.n_nodes, 256);
+    if (ek == EXP_F32) k_child_geo32<<<g, 256, 0, s>>>(T, g32, static_cast<XGeo32*>(m2m), static_cast<XGeo32*>(l2l));
+    else if (ek == EXP_DF) k_child_geo<XGeoDF><<<g, 256, 0, s>>>(T, static_cast<XGeoDF*>(m2m), static_cast<XGeoDF*>(l2l));
+    else k_child_geo<XGeo><<<g, 256, 0, s>>>(T, static_cast<XGeo*>(m2m), static_cast<XGeo*>(l2l));
     count_launch();
     return cudaGetLastError();
 }
@@ -689,16 +728,17 @@ cudaError_t launch_src_offsets(const TreeView& T, const int* leaves, int64_t n_l
     return cudaGetLastError();
 }
 
-// mpole: double storage (FP64 path) or float storage (mixed path)
+// mpole: double (FP64 path), float (mixed path) or double-float storage (1e-10 mixed path)
 cudaError_t launch_p2m(const TreeView& T, const int* leaves, int64_t n_leaves, const double4_32a* src,
-                       const float4* off, void* mpole, int p, bool fp32, cudaStream_t s)
+                       const float4* off, void* mpole, int p, int ek, cudaStream_t s)
 {
     if (n_leaves == 0) return cudaSuccess;
     const unsigned g = grid_for(n_leaves, 128);
 #define P2M_CASE(PP)                                                                                       \
     case PP:                                                                                               \
-        if (fp32) k_p2m32<PP><<<g, 128, 0, s>>>(T, leaves, n_leaves, off, static_cast<float*>(mpole));     \
-        else k_p2m<PP><<<g, 128, 0, s>>>(T, leaves, n_leaves, src, static_cast<double*>(mpole));           \
+        if (ek == EXP_F32) k_p2m32<PP><<<g, 128, 0, s>>>(T, leaves, n_leaves, off, static_cast<float*>(mpole)); \
+        else if (ek == EXP_DF) k_p2m<PP, dflt><<<g, 128, 0, s>>>(T, leaves, n_leaves, src, static_cast<dflt*>(mpole)); \
+        else k_p2m<PP, double><<<g, 128, 0, s>>>(T, leaves, n_leaves, src, static_cast<double*>(mpole));   \
         count_launch();                                                                                    \
         break;
     switch ((p + 3) / 4 * 4) {
@@ -710,26 +750,36 @@ cudaError_t launch_p2m(const TreeView& T, const int* leaves, int64_t n_leaves, c
 }
 
 cudaError_t launch_m2m(const TreeView& T, int a, int b, int p, const double* tables, const void* geo, void* mpole,
-                       bool fp32, cudaStream_t s)
+                       int ek, cudaStream_t s)
 {
     if (b <= a) return cudaSuccess;
-    if (fp32) k_m2m<float, XGeo32, float><<<grid_for(b - a, 4), 128, 0, s>>>(
-        T, a, b, p, tables, static_cast<const XGeo32*>(geo), static_cast<float*>(mpole));
-    else k_m2m<double, XGeo, double><<<grid_for(b - a, 4), 128, 0, s>>>(
-        T, a, b, p, tables, static_cast<const XGeo*>(geo), static_cast<double*>(mpole));
+    const unsigned g = grid_for(b - a, 4);
+    if (ek == EXP_F32)
+        k_m2m<float, XGeo32, float><<<g, 128, 0, s>>>(T, a, b, p, tables, static_cast<const XGeo32*>(geo),
+                                                      static_cast<float*>(mpole));
+    else if (ek == EXP_DF)
+        k_m2m<dflt, XGeoDF, dflt><<<g, 128, 0, s>>>(T, a, b, p, tables, static_cast<const XGeoDF*>(geo),
+                                                    static_cast<dflt*>(mpole));
+    else
+        k_m2m<double, XGeo, double><<<g, 128, 0, s>>>(T, a, b, p, tables, static_cast<const XGeo*>(geo),
+                                                      static_cast<double*>(mpole));
     count_launch();
     return cudaGetLastError();
 }
 
 cudaError_t launch_m2l(const TreeView& T, const int64_t* off, const uint32_t* srcs, int p, const double* tables,
-                       const void* geo, const void* mpole, void* local, bool fp32, cudaStream_t s)
+                       const void* geo, const void* mpole, void* local, int ek, cudaStream_t s)
 {
-    if (fp32) k_m2l<float, XGeo32, float><<<grid_for(T.n_nodes, 4), 128, 0, s>>>(
-        T, off, srcs, p, tables, static_cast<const XGeo32*>(geo), static_cast<const float*>(mpole),
-        static_cast<float*>(local));
-    else k_m2l<double, XGeo, double><<<grid_for(T.n_nodes, 4), 128, 0, s>>>(
-        T, off, srcs, p, tables, static_cast<const XGeo*>(geo), static_cast<const double*>(mpole),
-        static_cast<double*>(local));
+    const unsigned g = grid_for(T.n_nodes, 4);
+    if (ek == EXP_F32)
+        k_m2l<float, XGeo32, float><<<g, 128, 0, s>>>(T, off, srcs, p, tables, static_cast<const XGeo32*>(geo),
+                                                      static_cast<const float*>(mpole), static_cast<float*>(local));
+    else if (ek == EXP_DF)
+        k_m2l<dflt, XGeoDF, dflt><<<g, 128, 0, s>>>(T, off, srcs, p, tables, static_cast<const XGeoDF*>(geo),
+                                                    static_cast<const dflt*>(mpole), static_cast<dflt*>(local));
+    else
+        k_m2l<double, XGeo, double><<<g, 128, 0, s>>>(T, off, srcs, p, tables, static_cast<const XGeo*>(geo),
+                                                      static_cast<const double*>(mpole), static_cast<double*>(local));
     count_launch();
     return cudaGetLastError();
 }
@@ -747,24 +797,33 @@ cudaError_t launch_m2l_list(const uint64_t* ptgt, const uint32_t* psrc, const ui
 }
 
 cudaError_t launch_l2l(const TreeView& T, int a, int b, int p, const double* tables, const void* geo, void* local,
-                       bool fp32, cudaStream_t s)
+                       int ek, cudaStream_t s)
 {
     if (b <= a) return cudaSuccess;
-    if (fp32) k_l2l<float, XGeo32, float><<<grid_for(b - a, 4), 128, 0, s>>>(
-        T, a, b, p, tables, static_cast<const XGeo32*>(geo), static_cast<float*>(local));
-    else k_l2l<double, XGeo, double><<<grid_for(b - a, 4), 128, 0, s>>>(
-        T, a, b, p, tables, static_cast<const XGeo*>(geo), static_cast<double*>(local));
+    const unsigned g = grid_for(b - a, 4);
+    if (ek == EXP_F32)
+        k_l2l<float, XGeo32, float><<<g, 128, 0, s>>>(T, a, b, p, tables, static_cast<const XGeo32*>(geo),
+                                                      static_cast<float*>(local));
+    else if (ek == EXP_DF)
+        k_l2l<dflt, XGeoDF, dflt><<<g, 128, 0, s>>>(T, a, b, p, tables, static_cast<const XGeoDF*>(geo),
+                                                    static_cast<dflt*>(local));
+    else
+        k_l2l<double, XGeo, double><<<g, 128, 0, s>>>(T, a, b, p, tables, static_cast<const XGeo*>(geo),
+                                                      static_cast<double*>(local));
     count_launch();
     return cudaGetLastError();
 }
 
 cudaError_t launch_unscale(int n_nodes, const double* geom, const void* in, double* out, int p, int is_local,
-                           bool fp32, cudaStream_t s)
+                           int ek, cudaStream_t s)
 {
-    if (fp32) k_unscale<float><<<grid_for(n_nodes, 256), 256, 0, s>>>(n_nodes, geom, static_cast<const float*>(in),
-                                                                      out, p, is_local);
-    else k_unscale<double><<<grid_for(n_nodes, 256), 256, 0, s>>>(n_nodes, geom, static_cast<const double*>(in),
-                                                                  out, p, is_local);
+    const unsigned g = grid_for(n_nodes, 256);
+    if (ek == EXP_F32)
+        k_unscale<float><<<g, 256, 0, s>>>(n_nodes, geom, static_cast<const float*>(in), out, p, is_local);
+    else if (ek == EXP_DF)
+        k_unscale<dflt><<<g, 256, 0, s>>>(n_nodes, geom, static_cast<const dflt*>(in), out, p, is_local);
+    else
+        k_unscale<double><<<g, 256, 0, s>>>(n_nodes, geom, static_cast<const double*>(in), out, p, is_local);
     count_launch();
     return cudaGetLastError();
 }

@@ -9,7 +9,7 @@
 * the interaction lists: exactly-once coverage, the MAC, and equality with
   the oracle's Algorithm 1 walk;
 * end to end: psi and alpha against the FP64 direct sum, norm-wise relative
-  error <= 1e-10 (reading of the paper's relative error).
+  error <= 1e-10 (the ratio of Euclidean norms over all targets).
 """
 import numpy as np
 import pytest
