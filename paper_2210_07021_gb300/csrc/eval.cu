@@ -391,33 +391,42 @@ __global__ void __launch_bounds__(128) k_eval32(Eval32Args A)
 //   (a table-driven logarithm in the manner of Tang, ACM TOMS 16, 1990),
 //   |r| < 2^-7 so r - r^2/2 + ... + r^6/6 reaches double-float accuracy.
 // L2P (with FP64 local expansions) and the final combination are FP64.
-__device__ __forceinline__ dflt dfl_sqr(dflt a)
-{
-    const float p = __fmul_rn(a.h, a.h);
-    const float e = __fmaf_rn(a.h, a.h, -p);
-    return dfl_fast_two_sum(p, __fmaf_rn(2.f * a.h, a.l, e));
-}
-
-__device__ __forceinline__ dflt dfl_log(dflt x, const float4* __restrict__ tab)
+// log x for a double-float x > 0 (normal leading part), left unnormalised for
+// an accumulation.  x = 2^e m (1 + l'), m in [1, 2); with c_j = 1 + j/128 the
+// leading seven fraction bits of m, log x = e log 2 + log c_j + log1p(r),
+// r = (m - c_j + l 2^-e) / c_j, |r| < 2^-7.  m - c_j is exact; log1p(r) - r is
+// a degree-6 series (remainder below r^7/7 < 2^-52); log 2 is split so that
+// e times its leading part is exact.  The three leading terms meet in two
+// exact two-sums, every tail goes to the low part.
+__device__ __forceinline__ dflt dfl_log_lazy(dflt x, const float4* __restrict__ tab)
 {
     const int bits = __float_as_int(x.h);
-    const int ex = ((bits >> 23) & 0xFF) - 127;
+    const int be = bits >> 23;                                            // biased exponent (x.h > 0)
     const int j = (bits >> 16) & 0x7F;
     const float m = __int_as_float((bits & 0x007FFFFF) | 0x3F800000);     // [1, 2)
-    const float cj = 1.f + (float)j * (1.f / 128.f);
+    const float cj = __int_as_float((bits & 0x007F0000) | 0x3F800000);    // 1 + j/128, exactly
+    const float scale = __int_as_float((254 - be) << 23);                 // 2^-e
     const float4 t = tab[j];                                              // log c_j (hi, lo), 1/c_j (hi, lo)
-    // x = 2^ex (m + l 2^-ex); delta = m - c_j is exact, r = (delta + l 2^-ex) / c_j, |r| < 2^-7
-    const float scale = __int_as_float((127 - ex) << 23);                 // 2^-ex; ex lies in [-126, 127]
-    const dflt delta = dfl_two_sum(__fsub_rn(m, cj), x.l * scale);
-    const dflt r = delta * dflt(t.z, t.w);
+    const dflt delta = dfl_two_sum(__fsub_rn(m, cj), __fmul_rn(x.l, scale));
+    const dflt r = dfl_mul_lazy(delta, dflt(t.z, t.w));
     const float rh = r.h;
-    // log1p(r) - r to within r^7/7 < 2^-52, plus the cross term -r_hi r_lo of -r^2/2
-    float poly = rh * rh * (-0.5f + rh * (1.f / 3.f + rh * (-0.25f + rh * (0.2f + rh * (-1.f / 6.f)))));
-    poly = fmaf(-rh, r.l, poly);
-    dflt lg = r + dflt(poly, 0.f);
-    lg = lg + dflt(t.x, t.y);
-    const float4 l2 = tab[128];                                           // log 2 (hi, lo)
-    return lg + dflt(l2.x, l2.y) * (float)ex;
+    float poly = __fmul_rn(rh, rh) * (-0.5f + rh * (1.f / 3.f + rh * (-0.25f + rh * (0.2f + rh * (-1.f / 6.f)))));
+    poly = __fmaf_rn(-rh, r.l, poly);                                     // cross term of -r^2/2
+    const float4 l2 = tab[128];                                           // log 2: 16-bit leading part, tail
+    const float e = (float)(be - 127);
+    const dflt s1 = dfl_two_sum(__fmul_rn(e, l2.x), t.x);
+    const dflt s2 = dfl_two_sum(s1.h, rh);
+    const float lo = __fmaf_rn(e, l2.y, __fadd_rn(__fadd_rn(s1.l, s2.l), __fadd_rn(__fadd_rn(t.y, r.l), poly)));
+    return dflt(s2.h, lo);
+}
+
+// a - b for double-float a = (ah, al), b = (bh, bl): two-difference of the
+// leading parts, the tails added to its error, then renormalised -- for close
+// points the leading parts cancel and the difference lives in the tails
+__device__ __forceinline__ dflt dfl_diff(float ah, float al, float bh, float bl)
+{
+    const dflt s = dfl_two_sum(ah, -bh);
+    return dfl_fast_two_sum(s.h, __fadd_rn(s.l, __fsub_rn(al, bl)));
 }
 
 struct EvalDfArgs {
@@ -529,25 +538,36 @@ __global__ void __launch_bounds__(128) k_eval_df(EvalDfArgs A)
                 for (int j = sub; j < ns; j += lpt) {
                     const float4 h = yh[j];
                     const float4 l = yl[j];
-                    const dflt dx = dflt(th.x, tl.x) - dflt(h.x, l.x);
-                    const dflt dy = dflt(th.y, tl.y) - dflt(h.y, l.y);
-                    const dflt dz = dflt(th.z, tl.z) - dflt(h.z, l.z);
-                    dflt d2 = dfl_sqr(dx) + dfl_sqr(dy) + dfl_sqr(dz);
+                    // d = t - y
+                    const dflt dx = dfl_diff(th.x, tl.x, h.x, l.x);
+                    const dflt dy = dfl_diff(th.y, tl.y, h.y, l.y);
+                    const dflt dz = dfl_diff(th.z, tl.z, h.z, l.z);
+                    // d^2: exact squares of the leading parts, two exact two-sums
+                    const float px = __fmul_rn(dx.h, dx.h), py = __fmul_rn(dy.h, dy.h), pz = __fmul_rn(dz.h, dz.h);
+                    const float ex2 = __fmaf_rn(__fadd_rn(dx.h, dx.h), dx.l, __fmaf_rn(dx.h, dx.h, -px));
+                    const float ey2 = __fmaf_rn(__fadd_rn(dy.h, dy.h), dy.l, __fmaf_rn(dy.h, dy.h, -py));
+                    const float ez2 = __fmaf_rn(__fadd_rn(dz.h, dz.h), dz.l, __fmaf_rn(dz.h, dz.h, -pz));
+                    const dflt s1 = dfl_two_sum(px, py);
+                    const dflt s2 = dfl_two_sum(s1.h, pz);
+                    dflt d2 = dfl_fast_two_sum(s2.h, __fadd_rn(__fadd_rn(s1.l, s2.l), __fadd_rn(__fadd_rn(ex2, ey2), ez2)));
+                    // coincident pairs (d^2 == 0) contribute nothing
                     const bool ok = d2.h > 0.f;
-                    const dflt q = ok ? dflt(h.w, l.w) : dflt(0.f, 0.f);           // mass as (hi, lo)
+                    const dflt q = ok ? dflt(h.w, l.w) : dflt(0.f, 0.f);
                     if (!ok) d2 = dflt(1.f, 0.f);
                     // 1/d^2: MUFU reciprocal (relative error < 2^-22) and one Newton step
                     float r0;
                     asm("rcp.approx.f32 %0, %1;" : "=f"(r0) : "f"(d2.h));
-                    const float e0 = __fmaf_rn(-d2.h, r0, 1.f) - d2.l * r0;
-                    const dflt r = dfl_fast_two_sum(r0, r0 * e0);
-                    const dflt wq = r * q;
-                    ax += wq * dx;
-                    ay += wq * dy;
-                    az += wq * dz;
-                    aq += q;
-                    if (PSI) al += dfl_log(d2, s_tab) * q;
+                    const float e0 = __fmaf_rn(-d2.l, r0, __fmaf_rn(-d2.h, r0, 1.f));
+                    const dflt wq = dfl_mul_lazy(dflt(r0, __fmul_rn(r0, e0)), q);
+                    dfl_mac(ax, wq, dx);
+                    dfl_mac(ay, wq, dy);
+                    dfl_mac(az, wq, dz);
+                    const dflt sq = dfl_two_sum(aq.h, q.h);
+                    aq = dflt(sq.h, __fadd_rn(aq.l, __fadd_rn(sq.l, q.l)));
+                    if (PSI) dfl_mac(al, dfl_log_lazy(d2, s_tab), q);
                 }
+                ax = dfl_norm(ax); ay = dfl_norm(ay); az = dfl_norm(az); aq = dfl_norm(aq);
+                if (PSI) al = dfl_norm(al);
             }
             // combine the lanes of a target in FP64
             double sx = (double)ax.h + (double)ax.l, sy = (double)ay.h + (double)ay.l, sz = (double)az.h + (double)az.l;
@@ -697,7 +717,7 @@ cudaError_t launch_eval32(const TreeView& T, const int* leaves, int64_t n_leaves
 
 // Table of the double-float logarithm: entry j < 128 holds log(c_j) and 1/c_j,
 // c_j = 1 + j/128, each as an FP32 (hi, lo) pair rounded from FP64; entry 128
-// holds log 2 the same way.
+// holds log 2 as a 16-bit leading part and the FP32 rounding of the rest.
 void fill_log_table(float* out)
 {
     auto split = [](double v, float* hl) {
@@ -709,7 +729,10 @@ void fill_log_table(float* out)
         split(std::log(c), out + 4 * j);
         split(1.0 / c, out + 4 * j + 2);
     }
-    split(std::log(2.0), out + 4 * 128);
+    // log 2 with a 16-bit leading part: e times it is exact in FP32 for |e| < 2^7
+    const double l2h = std::ldexp(std::nearbyint(std::ldexp(std::log(2.0), 16)), -16);
+    out[4 * 128] = (float)l2h;
+    out[4 * 128 + 1] = (float)(std::log(2.0) - l2h);
     out[4 * 128 + 2] = out[4 * 128 + 3] = 0.f;
 }
 
