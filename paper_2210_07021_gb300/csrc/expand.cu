@@ -377,6 +377,108 @@ __device__ __forceinline__ void warp_translate(int p, int lane, const GR& G, R C
     __syncwarp();
 }
 
+// ---------------------------------------------- pipelined list translation
+// Lane l-1 of a translation spends p-l+1 terms on the first recurrence (v_l)
+// and l terms on the second (Y_l), so each recurrence alone takes p lockstep
+// steps although every lane has only p+1 terms in all.  For a list of
+// translations into one expansion (the M2L list of a target box, the children
+// of a parent in M2M) the second recurrence of translation i and the first of
+// translation i+1 share one loop of p+1 steps: lane l takes its l terms of the
+// second, then its p-l+1 terms of the first.  All lanes run one instruction
+// stream; the operands are chosen per lane by index arithmetic:
+//   binomial  tc[j][l-1] = C(l-1, j) for j < l, C(j, l) for j >= l (fixed),
+//   power     pw[j] = b^j (second) or pw[33 + j - l] = a^(j-l) (first),
+//   vector    vec[l-1-j] = w (second) or vec[32 + j - 1] = u (first).
+template <typename R> struct FusedTables {
+    R tc[(PMAX + 1) * PMAX];
+};
+template <typename R> struct FusedSmem {
+    cx<R> vec[2 * PMAX];       // w of the pending translation, then u of the next
+    R pw[2 * (PMAX + 1)];      // b^0..b^32 of the pending translation, then a^0..a^32 of the next
+    cx<R> snap[PMAX];          // each lane's second-recurrence sum at its switch step
+};
+
+template <typename R> __device__ __forceinline__ void load_fused_tables(FusedTables<R>* st, const double* g)
+{
+    // g holds T1[k][n-1] = C(n+k, n) and T2[k][l-1] = C(l-1, k)
+    for (int i = threadIdx.x; i < (PMAX + 1) * PMAX; i += blockDim.x) {
+        const int j = i / PMAX, lane = i % PMAX, l = lane + 1;
+        double v = 0.0;
+        if (j < l) v = g[PMAX * PMAX + j * PMAX + lane];
+        else if (j - l < PMAX) v = g[(j - l) * PMAX + lane];
+        st->tc[i] = (R)v;
+    }
+    __syncthreads();
+}
+
+// Translations 0..n-1 of a list, accumulated into (accC, accQ, accY).
+// fetch(i, &G, &C, &Q, &X) loads translation i's parameters and input.
+template <typename R, typename GR, typename Fetch>
+__device__ __forceinline__ void warp_translate_list(int p, int lane, int n, Fetch fetch, const FusedTables<R>* tb,
+                                                    FusedSmem<R>* ws, R* accC, R* accQ, cx<R>* accY)
+{
+    const int l = lane + 1;
+    const bool on = l <= p;
+    cx<R> p2prev = cmk<R>(0, 0);                  // state of the translation whose second recurrence is pending
+    R bpprev = 0, Qprev = 0;
+    ws->vec[lane] = cmk<R>(0, 0);
+    ws->pw[lane] = R(0);
+    if (lane == 0) ws->pw[PMAX] = R(0);
+    for (int i = 0; i <= n; ++i) {
+        const bool has_next = i < n, has_prev = i > 0;
+        R gp = 0, bp = 0, Q = 0;
+        cx<R> p2 = cmk<R>(0, 0);
+        if (has_next) {
+            GR G;
+            R C;
+            cx<R> X;
+            fetch(i, &G, &C, &Q, &X);
+            const R ap = warp_pow<R>((R)G.a, lane);
+            gp = warp_pow<R>((R)G.g, lane);
+            bp = warp_pow<R>((R)G.b, lane);
+            const cx<R> p1 = warp_cpow<R>(cmk<R>((R)G.p1x, (R)G.p1y), lane);
+            p2 = warp_cpow<R>(cmk<R>((R)G.p2x, (R)G.p2y), lane);
+            const cx<R> u = on ? cmul2(p1, X) : cmk<R>(0, 0);
+            const R csum = warp_sum<R>(on ? ap * u.x : R(0));
+            *accC += C + R(2) * Q * (R)G.logk + R(2) * csum;
+            *accQ += Q;
+            ws->vec[PMAX + lane] = u;
+            ws->pw[PMAX + 2 + lane] = ap;
+            if (lane == 0) ws->pw[PMAX + 1] = R(1);
+        }
+        __syncwarp();
+        cx<R> acc = (has_prev && on) ? cmk<R>(-Qprev * bpprev / (R)l, R(0)) : cmk<R>(0, 0);
+        const cx<R> zero = cmk<R>(0, 0);
+        for (int j = 0; j <= p; ++j) {
+            const bool second = j < l;
+            if (j == l) { ws->snap[lane] = acc; acc = zero; }
+            const R t = tb->tc[j * PMAX + lane];
+            const R pw = ws->pw[second ? j : PMAX + 1 + j - l];
+            const cx<R> vv = ws->vec[second ? lane - j : PMAX - 1 + j];
+            const R c = mul_lazy(t, pw);
+            mac(acc.x, c, vv.x);
+            mac(acc.y, c, vv.y);
+        }
+        __syncwarp();
+        if (has_prev && on) {
+            const cx<R> o = ws->snap[lane];
+            const cx<R> y = cmul2(p2prev, cmk<R>(renorm(o.x), renorm(o.y)));
+            accY->x += y.x;
+            accY->y += y.y;
+        }
+        if (has_next) {
+            const cx<R> v = cmk<R>(renorm(acc.x), renorm(acc.y));
+            ws->vec[lane] = on ? cmk<R>(v.x * gp, v.y * gp) : cmk<R>(0, 0);
+            ws->pw[lane + 1] = bp;
+            if (lane == 0) ws->pw[0] = R(1);
+            p2prev = p2;
+            bpprev = bp;
+            Qprev = Q;
+        }
+        __syncwarp();
+    }
+}
+
 template <typename R, typename ST>
 __device__ __forceinline__ void load_exp(const ST* e, int lane, int p, R* C, R* Q, cx<R>* X)
 {
@@ -514,56 +616,57 @@ __global__ void k_p2m32(TreeView T, const int* __restrict__ leaves, int64_t n_le
 }
 
 // ----------------------------------------------------------------- M2M
-// One warp per internal node of one level: sum of its 4 children's multipoles.
+// One warp per internal node of one level: sum of its children's multipoles
+// (pipelined over the non-empty children).
 template <typename R, typename GR, typename ST>
 __global__ void k_m2m(TreeView T, int a, int b, int p, const double* __restrict__ tables, const GR* __restrict__ geo,
                       ST* __restrict__ mpole)
 {
-    __shared__ Tables<R> tb;
-    __shared__ WarpSmem<R> ws[4];
-    load_tables<R>(&tb, tables);
+    __shared__ FusedTables<R> tb;
+    __shared__ FusedSmem<R> ws[4];
+    load_fused_tables<R>(&tb, tables);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     for (int64_t node = a + (int64_t)blockIdx.x * 4 + wid; node < b; node += (int64_t)gridDim.x * 4) {
         const int c0 = T.child0[node];
         if (c0 < 0 || T.count[node] == 0) continue;
+        unsigned mask = 0;                 // non-empty children
+        for (int k = 0; k < 4; ++k)
+            if (T.count[c0 + k] > 0) mask |= 1u << k;
         R accC = 0, accQ = 0;
         cx<R> accY = cmk<R>(0, 0);
-        for (int c = c0; c < c0 + 4; ++c) {
-            if (T.count[c] == 0) continue;
-            const GR G = geo[c];
-            R C, Q;
-            cx<R> X;
-            load_exp<R>(mpole + (size_t)c * EXP_STRIDE, lane, p, &C, &Q, &X);
-            warp_translate<R>(p, lane, G, C, Q, X, &tb, &ws[wid], &accC, &accQ, &accY);
-        }
+        auto fetch = [&](int i, GR* G, R* C, R* Q, cx<R>* X) {
+            const int c = c0 + (int)__fns(mask, 0, i + 1);
+            *G = geo[c];
+            load_exp<R>(mpole + (size_t)c * EXP_STRIDE, lane, p, C, Q, X);
+        };
+        warp_translate_list<R, GR>(p, lane, __popc(mask), fetch, &tb, &ws[wid], &accC, &accQ, &accY);
         store_exp<R>(mpole + (size_t)node * EXP_STRIDE, lane, p, accC, accQ, accY, false);
     }
 }
 
 // ----------------------------------------------------------------- M2L
-// One warp per target box with a non-empty list; writes local = sum of M2Ls.
+// One warp per target box with a non-empty list; writes local = sum of M2Ls
+// (pipelined over the list).
 template <typename R, typename GR, typename ST>
 __global__ void k_m2l(TreeView T, const int64_t* __restrict__ off, const uint32_t* __restrict__ srcs, int p,
                       const double* __restrict__ tables, const GR* __restrict__ geo, const ST* __restrict__ mpole,
                       ST* __restrict__ local)
 {
-    __shared__ Tables<R> tb;
-    __shared__ WarpSmem<R> ws[4];
-    load_tables<R>(&tb, tables);
+    __shared__ FusedTables<R> tb;
+    __shared__ FusedSmem<R> ws[4];
+    load_fused_tables<R>(&tb, tables);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     for (int64_t node = (int64_t)blockIdx.x * 4 + wid; node < T.n_nodes; node += (int64_t)gridDim.x * 4) {
         const int64_t lo = off[node], hi = off[node + 1];
         if (lo == hi) continue;
         R accC = 0, accQ = 0;
         cx<R> accY = cmk<R>(0, 0);
-        for (int64_t k = lo; k < hi; ++k) {
-            const int s = (int)srcs[k];
-            const GR G = geo[k];
-            R C, Q;
-            cx<R> X;
-            load_exp<R>(mpole + (size_t)s * EXP_STRIDE, lane, p, &C, &Q, &X);
-            warp_translate<R>(p, lane, G, C, Q, X, &tb, &ws[wid], &accC, &accQ, &accY);
-        }
+        auto fetch = [&](int i, GR* G, R* C, R* Q, cx<R>* X) {
+            const int64_t k = lo + i;
+            *G = geo[k];
+            load_exp<R>(mpole + (size_t)srcs[k] * EXP_STRIDE, lane, p, C, Q, X);
+        };
+        warp_translate_list<R, GR>(p, lane, (int)(hi - lo), fetch, &tb, &ws[wid], &accC, &accQ, &accY);
         store_exp<R>(local + (size_t)node * EXP_STRIDE, lane, p, accC, accQ, accY, false);
     }
 }
