@@ -16,9 +16,12 @@
 //   alpha_i = (1/2pi) [ sum_j q_j (x - y_j) / d_j^2 - (x/2) sum_j q_j ]
 // with d^2 = |x - y|^2 from coordinate differences; d^2 == 0 pairs are skipped.
 //
-// One warp per target leaf.  The leaf's targets are taken in groups of tpw
-// (a power of two >= the target count, at most 32); each target gets
-// 32/tpw lanes that split its sources and are combined by xor shuffles.
+// One warp per target leaf.  The leaf's targets are taken in groups of tpw,
+// the largest power of two not above the targets left (at most 32), so that
+// no lane idles; each target of a group gets 32/tpw lanes that split its
+// sources and are combined by xor shuffles.  (The FP32 kernel, whose pair loop
+// is cheap next to restaging its sources per group, keeps one group size per
+// leaf: the power of two not below the leaf's targets.)
 #include "common.cuh"
 #include "dfloat.cuh"
 
@@ -71,11 +74,10 @@ __global__ void __launch_bounds__(128) k_eval(EvalArgs A)
         const double* g = A.T.geom + (size_t)leaf * GEOM_STRIDE;
         const double* L = A.local + (size_t)leaf * EXP_STRIDE;
         const int64_t nb0 = A.p2p_off[leaf], nb1 = A.p2p_off[leaf + 1];
-        int tpw = 1;
-        while (tpw < tc && tpw < 32) tpw <<= 1;
-        const int lpt = 32 / tpw;
-        const int slot = lane / lpt, sub = lane % lpt;
-        for (int tb = 0; tb < tc; tb += tpw) {
+        for (int tb = 0, tpw = 0; tb < tc; tb += tpw) {
+            tpw = min(32, 1 << (31 - __clz(tc - tb)));     // largest power of two <= the targets left
+            const int lpt = 32 / tpw;
+            const int slot = lane / lpt, sub = lane % lpt;
             const int ti = tb + slot;
             const bool active = ti < tc;
             const double4_32a x = A.tgt[tf + (active ? ti : 0)];
@@ -233,6 +235,8 @@ __global__ void __launch_bounds__(128) k_eval32(Eval32Args A)
         const double* g = A.T.geom + (size_t)leaf * GEOM_STRIDE;
         const float* L = A.local + (size_t)leaf * EXP_STRIDE;
         const int64_t nb0 = A.p2p_off[leaf], nb1 = A.p2p_off[leaf + 1];
+        // the FP32 pair loop is cheap next to restaging the sources, so here one
+        // group size serves the whole leaf (the power of two >= its targets)
         int tpw = 1;
         while (tpw < tc && tpw < 32) tpw <<= 1;
         const int lpt = 32 / tpw;
@@ -476,11 +480,10 @@ __global__ void __launch_bounds__(128) k_eval_df(EvalDfArgs A)
         const double* g = A.T.geom + (size_t)leaf * GEOM_STRIDE;
         const dflt* L = A.local + (size_t)leaf * EXP_STRIDE;
         const int64_t nb0 = A.p2p_off[leaf], nb1 = A.p2p_off[leaf + 1];
-        int tpw = 1;
-        while (tpw < tc && tpw < 32) tpw <<= 1;
-        const int lpt = 32 / tpw;
-        const int slot = lane / lpt, sub = lane % lpt;
-        for (int tb = 0; tb < tc; tb += tpw) {
+        for (int tb = 0, tpw = 0; tb < tc; tb += tpw) {
+            tpw = min(32, 1 << (31 - __clz(tc - tb)));     // largest power of two <= the targets left
+            const int lpt = 32 / tpw;
+            const int slot = lane / lpt, sub = lane % lpt;
             const int ti = tb + slot;
             const bool active = ti < tc;
             const size_t tix = (size_t)tf + (active ? ti : 0);
