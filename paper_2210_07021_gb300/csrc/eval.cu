@@ -211,6 +211,98 @@ __device__ __forceinline__ void two_sum(float a, float b, float* s, float* e)
     *s = x;
 }
 
+// Near-field sums of one target over the staged sources j = sub, sub + lpt, ...:
+// blocks of 16 pairs per lane in FP32, then the outer FP32 level.
+template <bool PSI>
+__device__ __forceinline__ void pair_sums32(const float4* __restrict__ yh, const float4* __restrict__ yl, int ns,
+                                            int sub, int lpt, const float4& th, const float4& tl, float* acc)
+{
+    for (int j0 = sub; j0 < ns; j0 += 16 * lpt) {
+        float ix = 0.f, iy = 0.f, iz = 0.f, iq = 0.f, il = 0.f;   // inner FP32 level
+#pragma unroll 4
+        for (int u = 0; u < 16; ++u) {
+            const int j = j0 + u * lpt;
+            if (j < ns) {
+                const float4 h = yh[j];
+                const float4 l = yl[j];
+                const float dx = (th.x - h.x) + (tl.x - l.x);
+                const float dy = (th.y - h.y) + (tl.y - l.y);
+                const float dz = (th.z - h.z) + (tl.z - l.z);
+                const float d2 = dx * dx + dy * dy + dz * dz;
+                const bool ok = d2 > 0.f;
+                const float q = ok ? h.w : 0.f;
+                const float den = ok ? d2 : 1.f;
+                const float wq = __fdividef(q, den);
+                ix += wq * dx;
+                iy += wq * dy;
+                iz += wq * dz;
+                iq += q;
+                if (PSI) il += q * __logf(den);
+            }
+        }
+        acc[0] += ix; acc[1] += iy; acc[2] += iz; acc[3] += iq; acc[4] += il;
+    }
+}
+
+// L2P in the leaf frame (FP32 Horner, FP64 final psi) plus the near-field sums
+// acc, written for sorted target tix.
+template <bool PSI>
+__device__ __forceinline__ void finish_target32(const Eval32Args& A, const double* g, const float* L, size_t tix,
+                                                const float4& th, const float4& tl, const float* acc, double shift)
+{
+    const float ox = acc[0], oy = acc[1], oz = acc[2], oq = acc[3], ol = acc[4];
+    const float tx = th.x + tl.x, ty = th.y + tl.y, tz = th.z + tl.z;
+    const float D2 = tx * tx + ty * ty + tz * tz;
+    const float den = 2.f - 0.5f * D2;
+    const float wu = (tx * (float)g[3] + ty * (float)g[4] + tz * (float)g[5]) / den;
+    const float wv = (tx * (float)g[6] + ty * (float)g[7] + tz * (float)g[8]) / den;
+    const float inv_r = (float)(1.0 / g[10]);
+    const float omx = wu * inv_r, omy = wv * inv_r;
+    float frx = 0.f, fry = 0.f, fdx = 0.f, fdy = 0.f;
+    for (int l = A.p; l >= 1; --l) {
+        const float ax = L[2 * l], ay = L[2 * l + 1];
+        const float nfx = frx * omx - fry * omy + ax;
+        const float nfy = frx * omy + fry * omx + ay;
+        const float ndx = fdx * omx - fdy * omy + ax * (float)l;
+        const float ndy = fdx * omy + fdy * omx + ay * (float)l;
+        frx = nfx; fry = nfy; fdx = ndx; fdy = ndy;
+    }
+    const float Fx = frx * omx - fry * omy;
+    const float Fpx = fdx * inv_r, Fpy = fdy * inv_r;
+    const float Qf = L[1];
+    const float w2 = wu * wu + wv * wv;
+    const float au = (1.f + w2) * Fpx - Qf * wu;
+    const float av = -(1.f + w2) * Fpy - Qf * wv;
+    // c + x = 2c + (x - c)
+    const float cxx = 2.f * (float)g[0] + tx, cyy = 2.f * (float)g[1] + ty, czz = 2.f * (float)g[2] + tz;
+    const double4_32a x = A.tgt[tix];
+    const float xx = (float)x.x, xy = (float)x.y, xz = (float)x.z;
+    float a3x = au * ((float)g[3] - wu * cxx) + av * ((float)g[6] - wv * cxx);
+    float a3y = au * ((float)g[4] - wu * cyy) + av * ((float)g[7] - wv * cyy);
+    float a3z = au * ((float)g[5] - wu * czz) + av * ((float)g[8] - wv * czz);
+    const float i2p = (float)INV2PI;
+    a3x += i2p * (ox - 0.5f * xx * oq);
+    a3y += i2p * (oy - 0.5f * xy * oq);
+    a3z += i2p * (oz - 0.5f * xz * oq);
+    const float rho = sqrtf(xx * xx + xy * xy);
+    float cp = 1.f, sp = 0.f;
+    if (rho > 0.f) { cp = xx / rho; sp = xy / rho; }
+    const uint32_t o = A.tperm[tix];
+    if (A.alpha) {
+        A.alpha[2 * (size_t)o] = (double)(a3x * (xz * cp) + a3y * (xz * sp) - a3z * rho);
+        A.alpha[2 * (size_t)o + 1] = (double)(-a3x * sp + a3y * cp);
+    }
+    if (PSI) {
+        const double psi_e = (double)L[0] + (double)L[1] * (LOG2 + (double)log1pf(-0.25f * D2)) + 2.0 * (double)Fx;
+        A.psi[o] = psi_e + INV4PI * ((double)ol - LOG4 * (double)oq) + shift;
+    }
+}
+
+// One warp per target leaf.  The FP32 pair loop is cheap next to staging the
+// sources, so each pass over the near sources serves two groups of targets at
+// once: group a takes the largest power of two <= the targets left (at most
+// 32), group b the power of two >= what a leaves (at most 32), e.g. 18 = 16 + 2
+// and 40 = 32 + 8; each target of a group gets 32/size lanes.
 template <bool PSI>
 __global__ void __launch_bounds__(128) k_eval32(Eval32Args A)
 {
@@ -235,20 +327,20 @@ __global__ void __launch_bounds__(128) k_eval32(Eval32Args A)
         const double* g = A.T.geom + (size_t)leaf * GEOM_STRIDE;
         const float* L = A.local + (size_t)leaf * EXP_STRIDE;
         const int64_t nb0 = A.p2p_off[leaf], nb1 = A.p2p_off[leaf + 1];
-        // the FP32 pair loop is cheap next to restaging the sources, so here one
-        // group size serves the whole leaf (the power of two >= its targets)
-        int tpw = 1;
-        while (tpw < tc && tpw < 32) tpw <<= 1;
-        const int lpt = 32 / tpw;
-        const int slot = lane / lpt, sub = lane % lpt;
-        for (int tb = 0; tb < tc; tb += tpw) {
-            const int ti = tb + slot;
-            const bool active = ti < tc;
-            const size_t tix = (size_t)tf + (active ? ti : 0);
-            const float4 th = A.toff[2 * tix], tl = A.toff[2 * tix + 1];
-            const float txh = th.x, tyh = th.y, tzh = th.z;
-            const float txl = tl.x, tyl = tl.y, tzl = tl.z;
-            float ox = 0.f, oy = 0.f, oz = 0.f, oq = 0.f, ol = 0.f;      // outer FP32 level
+        for (int tb = 0; tb < tc;) {
+            const int rem = tc - tb;
+            const int na = min(32, 1 << (31 - __clz(rem)));
+            const int rb = rem - na;
+            const int nb = rb <= 0 ? 0 : min(32, 1 << (32 - __clz(rb - 1)));   // power of two >= rb
+            const int lpa = 32 / na, sa = lane % lpa;
+            const int lpb = nb ? 32 / nb : 32, sb = lane % lpb;
+            const size_t ta = (size_t)tf + tb + lane / lpa;
+            const int ib = tb + na + lane / lpb;
+            const bool act_b = nb > 0 && ib < tc;
+            const size_t tbx = (size_t)tf + (act_b ? ib : tb);
+            const float4 tha = A.toff[2 * ta], tla = A.toff[2 * ta + 1];
+            const float4 thb = A.toff[2 * tbx], tlb = A.toff[2 * tbx + 1];
+            float acc_a[5] = {0.f, 0.f, 0.f, 0.f, 0.f}, acc_b[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
             int64_t kn = nb0;
             int jn = 0;                // sources of near leaf kn already done
             while (kn < nb1) {
@@ -300,85 +392,17 @@ __global__ void __launch_bounds__(128) k_eval32(Eval32Args A)
                 if (nfit == 0) jn += STAGE;
                 else { kn += nfit; jn = 0; }
                 __syncwarp();
-                // ---- pair loop: blocks of 16 pairs per lane in FP32, then the outer level
-                for (int j0 = sub; j0 < ns; j0 += 16 * lpt) {
-                    float ix = 0.f, iy = 0.f, iz = 0.f, iq = 0.f, il = 0.f;   // inner FP32 level
-#pragma unroll 4
-                    for (int u = 0; u < 16; ++u) {
-                        const int j = j0 + u * lpt;
-                        if (j < ns) {
-                            const float4 h = yh[j];
-                            const float4 l = yl[j];
-                            const float dx = (txh - h.x) + (txl - l.x);
-                            const float dy = (tyh - h.y) + (tyl - l.y);
-                            const float dz = (tzh - h.z) + (tzl - l.z);
-                            const float d2 = dx * dx + dy * dy + dz * dz;
-                            const bool ok = d2 > 0.f;
-                            const float q = ok ? h.w : 0.f;
-                            const float den = ok ? d2 : 1.f;
-                            const float wq = __fdividef(q, den);
-                            ix += wq * dx;
-                            iy += wq * dy;
-                            iz += wq * dz;
-                            iq += q;
-                            if (PSI) il += q * __logf(den);
-                        }
-                    }
-                    ox += ix; oy += iy; oz += iz; oq += iq; ol += il;
-                }
+                pair_sums32<PSI>(yh, yl, ns, sa, lpa, tha, tla, acc_a);
+                if (nb) pair_sums32<PSI>(yh, yl, ns, sb, lpb, thb, tlb, acc_b);
             }
-            ox = group_sumf(ox, lpt);
-            oy = group_sumf(oy, lpt);
-            oz = group_sumf(oz, lpt);
-            oq = group_sumf(oq, lpt);
-            if (PSI) ol = group_sumf(ol, lpt);
-            if (!active || sub != 0) continue;
-            // ---- L2P in the leaf frame: FP32 Horner, FP64 final psi
-            const float tx = txh + txl, ty = tyh + tyl, tz = tzh + tzl;
-            const float D2 = tx * tx + ty * ty + tz * tz;
-            const float den = 2.f - 0.5f * D2;
-            const float wu = (tx * (float)g[3] + ty * (float)g[4] + tz * (float)g[5]) / den;
-            const float wv = (tx * (float)g[6] + ty * (float)g[7] + tz * (float)g[8]) / den;
-            const float inv_r = (float)(1.0 / g[10]);
-            const float omx = wu * inv_r, omy = wv * inv_r;
-            float frx = 0.f, fry = 0.f, fdx = 0.f, fdy = 0.f;
-            for (int l = A.p; l >= 1; --l) {
-                const float ax = L[2 * l], ay = L[2 * l + 1];
-                const float nfx = frx * omx - fry * omy + ax;
-                const float nfy = frx * omy + fry * omx + ay;
-                const float ndx = fdx * omx - fdy * omy + ax * (float)l;
-                const float ndy = fdx * omy + fdy * omx + ay * (float)l;
-                frx = nfx; fry = nfy; fdx = ndx; fdy = ndy;
+#pragma unroll
+            for (int c = 0; c < 5; ++c) {
+                acc_a[c] = group_sumf(acc_a[c], lpa);
+                acc_b[c] = group_sumf(acc_b[c], lpb);
             }
-            const float Fx = frx * omx - fry * omy;
-            const float Fpx = fdx * inv_r, Fpy = fdy * inv_r;
-            const float Qf = L[1];
-            const float w2 = wu * wu + wv * wv;
-            const float au = (1.f + w2) * Fpx - Qf * wu;
-            const float av = -(1.f + w2) * Fpy - Qf * wv;
-            // c + x = 2c + (x - c)
-            const float cxx = 2.f * (float)g[0] + tx, cyy = 2.f * (float)g[1] + ty, czz = 2.f * (float)g[2] + tz;
-            const double4_32a x = A.tgt[tix];
-            const float xx = (float)x.x, xy = (float)x.y, xz = (float)x.z;
-            float a3x = au * ((float)g[3] - wu * cxx) + av * ((float)g[6] - wv * cxx);
-            float a3y = au * ((float)g[4] - wu * cyy) + av * ((float)g[7] - wv * cyy);
-            float a3z = au * ((float)g[5] - wu * czz) + av * ((float)g[8] - wv * czz);
-            const float i2p = (float)INV2PI;
-            a3x += i2p * (ox - 0.5f * xx * oq);
-            a3y += i2p * (oy - 0.5f * xy * oq);
-            a3z += i2p * (oz - 0.5f * xz * oq);
-            const float rho = sqrtf(xx * xx + xy * xy);
-            float cp = 1.f, sp = 0.f;
-            if (rho > 0.f) { cp = xx / rho; sp = xy / rho; }
-            const uint32_t o = A.tperm[tf + ti];
-            if (A.alpha) {
-                A.alpha[2 * (size_t)o] = (double)(a3x * (xz * cp) + a3y * (xz * sp) - a3z * rho);
-                A.alpha[2 * (size_t)o + 1] = (double)(-a3x * sp + a3y * cp);
-            }
-            if (PSI) {
-                const double psi_e = (double)L[0] + (double)L[1] * (LOG2 + (double)log1pf(-0.25f * D2)) + 2.0 * (double)Fx;
-                A.psi[o] = psi_e + INV4PI * ((double)ol - LOG4 * (double)oq) + shift;
-            }
+            if (sa == 0) finish_target32<PSI>(A, g, L, ta, tha, tla, acc_a, shift);
+            if (act_b && sb == 0) finish_target32<PSI>(A, g, L, tbx, thb, tlb, acc_b, shift);
+            tb += na + nb;
         }
     }
 }
