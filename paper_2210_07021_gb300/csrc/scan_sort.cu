@@ -2,9 +2,10 @@
 //
 // Scan: reduce-then-scan in three launches (per-tile sums, a single-CTA scan of
 // the tile sums, per-tile scans with the tile offset added).
-// Sort: 8-bit digits; per pass one histogram launch (per tile of 2048 keys),
+// Sort: 8-bit digits; per pass one histogram launch (per tile of 4096 keys),
 // one scan of the digit-major histogram, and one scatter launch that ranks the
-// keys of each tile stably with warp match-any and per-warp digit counters.
+// keys of each tile stably (warp match-any, per-warp digit counters), reorders
+// the tile by digit in shared memory and writes runs of equal digits.
 #include "common.cuh"
 
 namespace sfmm {
@@ -116,10 +117,14 @@ cudaError_t exclusive_scan_t(const T* in, T* out, int64_t n, T* total, void* tmp
 }
 
 // ---------------------------------------------------------------- radix sort
-constexpr int RS_T = 256, RS_I = 8, RS_TILE = RS_T * RS_I, RS_W = RS_T / 32;
+// Tiles of RS_TILE = 4096 keys, 256 threads, 16 keys per thread.  Warp w owns
+// keys [512 w, 512 w + 512) of its tile, loaded in 16 coalesced rounds of 32.
+constexpr int RS_T = 256, RS_I = 16, RS_TILE = RS_T * RS_I, RS_W = RS_T / 32;
+constexpr int RS_WC = 257;                        // per-warp digit counters (+1 slot for keys past n)
+constexpr size_t RS_SMEM = (size_t)RS_TILE * 12 + (size_t)RS_W * RS_WC * 4 + 3 * 256 * 4 + 64;
 
-__global__ void k_rs_hist(const uint64_t* __restrict__ keys, int64_t n, int shift, uint32_t* __restrict__ hist,
-                          int64_t ntiles)
+__global__ void __launch_bounds__(RS_T) k_rs_hist(const uint64_t* __restrict__ keys, int64_t n, int shift,
+                                                 uint32_t* __restrict__ hist, int64_t ntiles)
 {
     __shared__ uint32_t cnt[256];
     cnt[threadIdx.x] = 0;
@@ -133,40 +138,100 @@ __global__ void k_rs_hist(const uint64_t* __restrict__ keys, int64_t n, int shif
     hist[(int64_t)threadIdx.x * ntiles + blockIdx.x] = cnt[threadIdx.x];
 }
 
-__global__ void k_rs_scatter(const uint64_t* __restrict__ kin, const uint32_t* __restrict__ vin,
-                             uint64_t* __restrict__ kout, uint32_t* __restrict__ vout, int64_t n, int shift,
-                             const uint32_t* __restrict__ offs, int64_t ntiles)
+// One tile: stable rank of every key among the tile's keys of its digit
+// (warp-private counters advanced round by round, match-any within a round),
+// counts turned into per-warp offsets by a scan over (digit, warp), the tile
+// reordered by digit in shared memory, then written out as runs per digit at
+// the tile's global digit offsets (the scanned histogram).
+__global__ void __launch_bounds__(RS_T) k_rs_scatter(const uint64_t* __restrict__ kin, const uint32_t* __restrict__ vin,
+                                                    uint64_t* __restrict__ kout, uint32_t* __restrict__ vout,
+                                                    int64_t n, int shift, const uint32_t* __restrict__ offs,
+                                                    int64_t ntiles)
 {
-    __shared__ uint32_t base[256];
-    __shared__ uint32_t wc[RS_W][256];
+    extern __shared__ __align__(16) unsigned char rs_smem[];
+    uint64_t* sk = reinterpret_cast<uint64_t*>(rs_smem);
+    uint32_t* sv = reinterpret_cast<uint32_t*>(sk + RS_TILE);
+    uint32_t* wc = sv + RS_TILE;                          // [RS_W][RS_WC]
+    uint32_t* tbase = wc + RS_W * RS_WC;                  // tile-local start of each digit
+    uint32_t* gbase = tbase + 256;                        // global start of this tile's keys of each digit
+    uint32_t* s_warp = gbase + 256;                       // scan scratch
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    base[tid] = offs[(int64_t)tid * ntiles + blockIdx.x];
     const int64_t tile0 = (int64_t)blockIdx.x * RS_TILE;
-    const unsigned lt = (1u << lane) - 1u;
+    const int64_t w0 = tile0 + (int64_t)warp * (32 * RS_I);
+    uint64_t k[RS_I];
+    uint32_t v[RS_I];
+    uint32_t loc[RS_I];
+#pragma unroll
     for (int r = 0; r < RS_I; ++r) {
-        for (int k = tid; k < RS_W * 256; k += RS_T) (&wc[0][0])[k] = 0;
-        __syncthreads();
-        const int64_t e = tile0 + (int64_t)r * RS_T + tid;
-        const bool valid = e < n;
-        const uint64_t key = valid ? kin[e] : 0ull;
-        const uint32_t val = valid ? vin[e] : 0u;
-        const int d = valid ? (int)((key >> shift) & 255u) : 256;
+        const int64_t e = w0 + r * 32 + lane;
+        k[r] = e < n ? kin[e] : 0ull;
+        v[r] = e < n ? vin[e] : 0u;
+    }
+    for (int d = lane; d < RS_WC; d += 32) wc[warp * RS_WC + d] = 0;
+    gbase[tid] = offs[(int64_t)tid * ntiles + blockIdx.x];
+    __syncwarp();
+    const unsigned lt = (1u << lane) - 1u;
+#pragma unroll
+    for (int r = 0; r < RS_I; ++r) {
+        const int64_t e = w0 + r * 32 + lane;
+        const int d = e < n ? (int)((k[r] >> shift) & 255u) : 256;
         const unsigned peers = __match_any_sync(FULL, d);
-        const int rank = __popc(peers & lt);
-        if (valid && rank == 0) wc[warp][d] = __popc(peers);
-        __syncthreads();
-        {
-            uint32_t acc = base[tid];
-            for (int w = 0; w < RS_W; ++w) { uint32_t c = wc[w][tid]; wc[w][tid] = acc; acc += c; }
-            base[tid] = acc;
+        const uint32_t before = wc[warp * RS_WC + d];
+        __syncwarp();
+        if ((peers & lt) == 0) wc[warp * RS_WC + d] = before + (uint32_t)__popc(peers);
+        loc[r] = before + (uint32_t)__popc(peers & lt);
+        __syncwarp();
+    }
+    __syncthreads();
+    // thread tid = digit: per-warp exclusive offsets, then the tile's digit starts
+    uint32_t tot = 0;
+#pragma unroll
+    for (int w = 0; w < RS_W; ++w) {
+        const uint32_t c = wc[w * RS_WC + tid];
+        wc[w * RS_WC + tid] = tot;
+        tot += c;
+    }
+    uint32_t inc = tot;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(FULL, inc, o);
+        if (lane >= o) inc += t;
+    }
+    if (lane == 31) s_warp[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        const uint32_t wv = lane < RS_W ? s_warp[lane] : 0u;
+        uint32_t wi = wv;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(FULL, wi, o);
+            if (lane >= o) wi += t;
         }
-        __syncthreads();
-        if (valid) {
-            const uint32_t p = wc[warp][d] + (uint32_t)rank;
-            kout[p] = key;
-            vout[p] = val;
+        if (lane < RS_W) s_warp[lane] = wi - wv;
+    }
+    __syncthreads();
+    tbase[tid] = inc - tot + s_warp[warp];
+    __syncthreads();
+    // reorder the tile by digit in shared memory
+#pragma unroll
+    for (int r = 0; r < RS_I; ++r) {
+        const int64_t e = w0 + r * 32 + lane;
+        if (e < n) {
+            const int d = (int)((k[r] >> shift) & 255u);
+            const uint32_t pos = tbase[d] + wc[warp * RS_WC + d] + loc[r];
+            sk[pos] = k[r];
+            sv[pos] = v[r];
         }
-        __syncthreads();
+    }
+    __syncthreads();
+    // runs of equal digits go to consecutive global positions
+    const int cnt = (int)((n - tile0) < RS_TILE ? (n - tile0) : RS_TILE);
+    for (int i = tid; i < cnt; i += RS_T) {
+        const uint64_t key = sk[i];
+        const int d = (int)((key >> shift) & 255u);
+        const uint32_t p = gbase[d] + (uint32_t)i - tbase[d];
+        kout[p] = key;
+        vout[p] = sv[i];
     }
 }
 
@@ -210,11 +275,13 @@ cudaError_t radix_sort(uint64_t* k1, uint32_t* v1, uint64_t* k2, uint32_t* v2, i
     uint64_t *ka = k1, *kb = k2;
     uint32_t *va = v1, *vb = v2;
     bool alt = false;
+    cudaError_t e = cudaFuncSetAttribute(k_rs_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RS_SMEM);
+    if (e != cudaSuccess) return e;
     for (int shift = 0; shift < bits; shift += 8) {
         k_rs_hist<<<(unsigned)ntiles, RS_T, 0, s>>>(ka, n, shift, hist, ntiles); count_launch();
-        cudaError_t e = exclusive_scan_u32(hist, offs, nh, nullptr, stmp, s);
+        e = exclusive_scan_u32(hist, offs, nh, nullptr, stmp, s);
         if (e != cudaSuccess) return e;
-        k_rs_scatter<<<(unsigned)ntiles, RS_T, 0, s>>>(ka, va, kb, vb, n, shift, offs, ntiles); count_launch();
+        k_rs_scatter<<<(unsigned)ntiles, RS_T, RS_SMEM, s>>>(ka, va, kb, vb, n, shift, offs, ntiles); count_launch();
         std::swap(ka, kb);
         std::swap(va, vb);
         alt = !alt;
