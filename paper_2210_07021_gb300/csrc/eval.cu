@@ -212,33 +212,31 @@ __device__ __forceinline__ void two_sum(float a, float b, float* s, float* e)
 }
 
 // Near-field sums of one target over the staged sources j = sub, sub + lpt, ...:
-// blocks of 16 pairs per lane in FP32, then the outer FP32 level.
+// blocks of (up to) 16 pairs per lane in FP32, then the outer FP32 level.
 template <bool PSI>
 __device__ __forceinline__ void pair_sums32(const float4* __restrict__ yh, const float4* __restrict__ yl, int ns,
                                             int sub, int lpt, const float4& th, const float4& tl, float* acc)
 {
-    for (int j0 = sub; j0 < ns; j0 += 16 * lpt) {
+    for (int j = sub; j < ns;) {
+        const int jend = min(ns, j + 16 * lpt);
         float ix = 0.f, iy = 0.f, iz = 0.f, iq = 0.f, il = 0.f;   // inner FP32 level
 #pragma unroll 4
-        for (int u = 0; u < 16; ++u) {
-            const int j = j0 + u * lpt;
-            if (j < ns) {
-                const float4 h = yh[j];
-                const float4 l = yl[j];
-                const float dx = (th.x - h.x) + (tl.x - l.x);
-                const float dy = (th.y - h.y) + (tl.y - l.y);
-                const float dz = (th.z - h.z) + (tl.z - l.z);
-                const float d2 = dx * dx + dy * dy + dz * dz;
-                const bool ok = d2 > 0.f;
-                const float q = ok ? h.w : 0.f;
-                const float den = ok ? d2 : 1.f;
-                const float wq = __fdividef(q, den);
-                ix += wq * dx;
-                iy += wq * dy;
-                iz += wq * dz;
-                iq += q;
-                if (PSI) il += q * __logf(den);
-            }
+        for (; j < jend; j += lpt) {
+            const float4 h = yh[j];
+            const float4 l = yl[j];
+            const float dx = (th.x - h.x) + (tl.x - l.x);
+            const float dy = (th.y - h.y) + (tl.y - l.y);
+            const float dz = (th.z - h.z) + (tl.z - l.z);
+            const float d2 = dx * dx + dy * dy + dz * dz;
+            const bool ok = d2 > 0.f;
+            const float q = ok ? h.w : 0.f;
+            const float den = ok ? d2 : 1.f;
+            const float wq = __fdividef(q, den);
+            ix += wq * dx;
+            iy += wq * dy;
+            iz += wq * dz;
+            iq += q;
+            if (PSI) il += q * __logf(den);
         }
         acc[0] += ix; acc[1] += iy; acc[2] += iz; acc[3] += iq; acc[4] += il;
     }
@@ -246,17 +244,23 @@ __device__ __forceinline__ void pair_sums32(const float4* __restrict__ yh, const
 
 // L2P in the leaf frame (FP32 Horner, FP64 final psi) plus the near-field sums
 // acc, written for sorted target tix.
+// A leaf's frame in FP32, formed once per leaf: e_theta, e_phi, 2 c, 1/r.
+struct LeafFrame32 {
+    float et[3], ep[3], c2[3], inv_r;
+};
+
 template <bool PSI>
-__device__ __forceinline__ void finish_target32(const Eval32Args& A, const double* g, const float* L, size_t tix,
-                                                const float4& th, const float4& tl, const float* acc, double shift)
+__device__ __forceinline__ void finish_target32(const Eval32Args& A, const LeafFrame32& G, const float* L,
+                                                size_t tix, const float4& th, const float4& tl, const float* acc,
+                                                double shift)
 {
     const float ox = acc[0], oy = acc[1], oz = acc[2], oq = acc[3], ol = acc[4];
     const float tx = th.x + tl.x, ty = th.y + tl.y, tz = th.z + tl.z;
     const float D2 = tx * tx + ty * ty + tz * tz;
     const float den = 2.f - 0.5f * D2;
-    const float wu = (tx * (float)g[3] + ty * (float)g[4] + tz * (float)g[5]) / den;
-    const float wv = (tx * (float)g[6] + ty * (float)g[7] + tz * (float)g[8]) / den;
-    const float inv_r = (float)(1.0 / g[10]);
+    const float wu = (tx * G.et[0] + ty * G.et[1] + tz * G.et[2]) / den;
+    const float wv = (tx * G.ep[0] + ty * G.ep[1] + tz * G.ep[2]) / den;
+    const float inv_r = G.inv_r;
     const float omx = wu * inv_r, omy = wv * inv_r;
     float frx = 0.f, fry = 0.f, fdx = 0.f, fdy = 0.f;
     for (int l = A.p; l >= 1; --l) {
@@ -273,13 +277,12 @@ __device__ __forceinline__ void finish_target32(const Eval32Args& A, const doubl
     const float w2 = wu * wu + wv * wv;
     const float au = (1.f + w2) * Fpx - Qf * wu;
     const float av = -(1.f + w2) * Fpy - Qf * wv;
-    // c + x = 2c + (x - c)
-    const float cxx = 2.f * (float)g[0] + tx, cyy = 2.f * (float)g[1] + ty, czz = 2.f * (float)g[2] + tz;
-    const double4_32a x = A.tgt[tix];
-    const float xx = (float)x.x, xy = (float)x.y, xz = (float)x.z;
-    float a3x = au * ((float)g[3] - wu * cxx) + av * ((float)g[6] - wv * cxx);
-    float a3y = au * ((float)g[4] - wu * cyy) + av * ((float)g[7] - wv * cyy);
-    float a3z = au * ((float)g[5] - wu * czz) + av * ((float)g[8] - wv * czz);
+    // c + x = 2c + (x - c); x itself to FP32 accuracy as c + (x - c)
+    const float cxx = G.c2[0] + tx, cyy = G.c2[1] + ty, czz = G.c2[2] + tz;
+    const float xx = 0.5f * G.c2[0] + tx, xy = 0.5f * G.c2[1] + ty, xz = 0.5f * G.c2[2] + tz;
+    float a3x = au * (G.et[0] - wu * cxx) + av * (G.ep[0] - wv * cxx);
+    float a3y = au * (G.et[1] - wu * cyy) + av * (G.ep[1] - wv * cyy);
+    float a3z = au * (G.et[2] - wu * czz) + av * (G.ep[2] - wv * czz);
     const float i2p = (float)INV2PI;
     a3x += i2p * (ox - 0.5f * xx * oq);
     a3y += i2p * (oy - 0.5f * xy * oq);
@@ -311,6 +314,7 @@ __global__ void __launch_bounds__(128) k_eval32(Eval32Args A)
     __shared__ float s_dc[4][32][6];
     __shared__ int s_pre[4][33];
     __shared__ int s_first[4][32];
+    __shared__ LeafFrame32 s_frame[4];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -326,6 +330,16 @@ __global__ void __launch_bounds__(128) k_eval32(Eval32Args A)
         const int tf = A.T.tfirst[leaf], tc = A.T.tcount[leaf];
         const double* g = A.T.geom + (size_t)leaf * GEOM_STRIDE;
         const float* L = A.local + (size_t)leaf * EXP_STRIDE;
+        // the leaf frame in FP32, once per leaf, kept in shared memory
+        LeafFrame32& G = s_frame[wid];
+        __syncwarp();
+        if (lane < 3) {
+            G.et[lane] = (float)g[3 + lane];
+            G.ep[lane] = (float)g[6 + lane];
+            G.c2[lane] = (float)(2.0 * g[lane]);
+        }
+        if (lane == 3) G.inv_r = 1.f / (float)g[10];
+        __syncwarp();
         const int64_t nb0 = A.p2p_off[leaf], nb1 = A.p2p_off[leaf + 1];
         for (int tb = 0; tb < tc;) {
             const int rem = tc - tb;
@@ -400,8 +414,8 @@ __global__ void __launch_bounds__(128) k_eval32(Eval32Args A)
                 acc_a[c] = group_sumf(acc_a[c], lpa);
                 acc_b[c] = group_sumf(acc_b[c], lpb);
             }
-            if (sa == 0) finish_target32<PSI>(A, g, L, ta, tha, tla, acc_a, shift);
-            if (act_b && sb == 0) finish_target32<PSI>(A, g, L, tbx, thb, tlb, acc_b, shift);
+            if (sa == 0) finish_target32<PSI>(A, G, L, ta, tha, tla, acc_a, shift);
+            if (act_b && sb == 0) finish_target32<PSI>(A, G, L, tbx, thb, tlb, acc_b, shift);
             tb += na + nb;
         }
     }
