@@ -233,7 +233,24 @@ sfmm_status solve(sfmm_plan_s* P, const double* src, const void* q, int64_t N, c
     if ((e = ensure(P->tkeys, M * 8)) || (e = ensure(P->tkeys2, M * 8)) || (e = ensure(P->tperm, M * 4)) ||
         (e = ensure(P->tperm2, M * 4)) || (e = ensure(P->tgt4, M * 32)))
         return cuda_fail(P, e, "alloc targets");
-    if ((e = ensure(P->tmp, radix_tmp_bytes(std::max(N, M))))) return cuda_fail(P, e, "alloc");
+    if ((e = ensure(P->tmp, radix_tmp_bytes(std::max(N, M)))) || (e = ensure(P->ttmp, radix_tmp_bytes(M))))
+        return cuda_fail(P, e, "alloc");
+    // The targets' keys, sort and gather need nothing from the sources: they run
+    // on the auxiliary stream (forked from and joined back into the plan's
+    // stream by events, with their own sort scratch) while the plan's stream
+    // sorts the sources, builds the tree (one host synchronisation per level)
+    // and runs the up-pass.
+    cudaStream_t s2 = P->aux;
+    if ((e = cudaEventRecord(P->ev_fork, s)) || (e = cudaStreamWaitEvent(s2, P->ev_fork, 0)))
+        return cuda_fail(P, e, "fork");
+    if ((e = launch_keys(tgt, M, P->tkeys.as<uint64_t>(), P->tperm.as<uint32_t>(), s2))) return cuda_fail(P, e, "tkeys");
+    if ((e = radix_sort(P->tkeys.as<uint64_t>(), P->tperm.as<uint32_t>(), P->tkeys2.as<uint64_t>(),
+                        P->tperm2.as<uint32_t>(), M, 62, P->ttmp.p, s2, &P->tkeys_alt)))
+        return cuda_fail(P, e, "sort targets");
+    const uint64_t* tkeys = P->tkeys_alt ? P->tkeys2.as<uint64_t>() : P->tkeys.as<uint64_t>();
+    const uint32_t* tperm = P->tkeys_alt ? P->tperm2.as<uint32_t>() : P->tperm.as<uint32_t>();
+    k_gather_tgt<<<grid_for(M), 256, 0, s2>>>(tgt, tperm, M, P->tgt4.as<double4_32a>()); count_launch();
+    if ((e = cudaGetLastError()) || (e = cudaEventRecord(P->ev_join, s2))) return cuda_fail(P, e, "gather targets");
     if ((e = launch_keys(src, N, P->skeys.as<uint64_t>(), P->sperm.as<uint32_t>(), s))) return cuda_fail(P, e, "keys");
     if ((e = radix_sort(P->skeys.as<uint64_t>(), P->sperm.as<uint32_t>(), P->skeys2.as<uint64_t>(),
                         P->sperm2.as<uint32_t>(), N, 62, P->tmp.p, s, &P->skeys_alt)))
@@ -241,23 +258,14 @@ sfmm_status solve(sfmm_plan_s* P, const double* src, const void* q, int64_t N, c
     const uint64_t* skeys = P->skeys_alt ? P->skeys2.as<uint64_t>() : P->skeys.as<uint64_t>();
     const uint32_t* sperm = P->skeys_alt ? P->sperm2.as<uint32_t>() : P->sperm.as<uint32_t>();
     k_gather_src<<<grid_for(N), 256, 0, s>>>(src, q, P->opt.q_f32, sperm, N, P->src4.as<double4_32a>()); count_launch();
-    if ((e = launch_keys(tgt, M, P->tkeys.as<uint64_t>(), P->tperm.as<uint32_t>(), s))) return cuda_fail(P, e, "tkeys");
-    if ((e = radix_sort(P->tkeys.as<uint64_t>(), P->tperm.as<uint32_t>(), P->tkeys2.as<uint64_t>(),
-                        P->tperm2.as<uint32_t>(), M, 62, P->tmp.p, s, &P->tkeys_alt)))
-        return cuda_fail(P, e, "sort targets");
-    const uint64_t* tkeys = P->tkeys_alt ? P->tkeys2.as<uint64_t>() : P->tkeys.as<uint64_t>();
-    const uint32_t* tperm = P->tkeys_alt ? P->tperm2.as<uint32_t>() : P->tperm.as<uint32_t>();
-    k_gather_tgt<<<grid_for(M), 256, 0, s>>>(tgt, tperm, M, P->tgt4.as<double4_32a>()); count_launch();
     if ((e = cudaGetLastError())) return cuda_fail(P, e, "gather");
     tm.mark();
-    // ---- tree and geometry
+    // ---- tree and geometry (sources)
     if ((e = build_tree(P, skeys, N, P->opt.leaf_size, P->max_depth))) return cuda_fail(P, e, "tree");
     const int64_t nn = P->n_nodes;
     if ((e = tree_geometry(P))) return cuda_fail(P, e, "geometry");
-    if ((e = tree_target_ranges(P, tkeys, M))) return cuda_fail(P, e, "target ranges");
     TreeView T = view(P);
     if ((e = collect_leaves(P, T.count, P->leaves_src, &P->n_leaves))) return cuda_fail(P, e, "leaves");
-    if ((e = collect_leaves(P, T.tcount, P->leaves_tgt, &P->n_leaves_tgt))) return cuda_fail(P, e, "target leaves");
     tm.mark();
     // ---- up-pass
     const bool fp32 = P->opt.precision == SFMM_MIXED;
@@ -292,7 +300,11 @@ sfmm_status solve(sfmm_plan_s* P, const double* src, const void* q, int64_t N, c
                             P->mpole.p, ek, s)))
             return cuda_fail(P, e, "M2M");
     tm.mark();
-    // ---- lists
+    // ---- join the targets; target ranges (Sec. 3.7 lookup) and target leaves; lists
+    if ((e = cudaStreamWaitEvent(s, P->ev_join, 0))) return cuda_fail(P, e, "join");
+    if ((e = tree_target_ranges(P, tkeys, M))) return cuda_fail(P, e, "target ranges");
+    T = view(P);
+    if ((e = collect_leaves(P, T.tcount, P->leaves_tgt, &P->n_leaves_tgt))) return cuda_fail(P, e, "target leaves");
     if ((e = build_lists(P, T, P->opt.c_s, P->opt.c_t))) return cuda_fail(P, e, "lists");
     tm.mark();
     // ---- M2L
@@ -448,6 +460,14 @@ sfmm_status sfmm_plan(sfmm_plan_t* out, int max_depth, int order_p, double tol, 
     float lt[129 * 4];
     fill_log_table(lt);
     cudaError_t e;
+    if ((e = cudaStreamCreateWithFlags(&P->aux, cudaStreamNonBlocking)) ||
+        (e = cudaEventCreateWithFlags(&P->ev_fork, cudaEventDisableTiming)) ||
+        (e = cudaEventCreateWithFlags(&P->ev_join, cudaEventDisableTiming))) {
+        std::lock_guard<std::mutex> g(g_err_mu);
+        g_plan_err = std::string("CUDA error at plan time: ") + cudaGetErrorString(e);
+        sfmm_destroy(P);
+        return SFMM_ECUDA;
+    }
     if ((e = ensure(P->tables, h.size() * 8)) ||
         (e = cudaMemcpy(P->tables.p, h.data(), h.size() * 8, cudaMemcpyHostToDevice)) ||
         (e = ensure(P->logtab, sizeof lt)) || (e = cudaMemcpy(P->logtab.p, lt, sizeof lt, cudaMemcpyHostToDevice))) {
@@ -461,7 +481,8 @@ sfmm_status sfmm_plan(sfmm_plan_t* out, int max_depth, int order_p, double tol, 
         if ((e = ensure(P->skeys, N * 8)) || (e = ensure(P->skeys2, N * 8)) || (e = ensure(P->sperm, N * 4)) ||
             (e = ensure(P->sperm2, N * 4)) || (e = ensure(P->src4, N * 32)) || (e = ensure(P->tkeys, M * 8)) ||
             (e = ensure(P->tkeys2, M * 8)) || (e = ensure(P->tperm, M * 4)) || (e = ensure(P->tperm2, M * 4)) ||
-            (e = ensure(P->tgt4, M * 32)) || (e = ensure(P->tmp, radix_tmp_bytes(std::max(N, M))))) {
+            (e = ensure(P->tgt4, M * 32)) || (e = ensure(P->tmp, radix_tmp_bytes(std::max(N, M)))) ||
+            (e = ensure(P->ttmp, radix_tmp_bytes(M)))) {
             std::lock_guard<std::mutex> g(g_err_mu);
             g_plan_err = std::string("workspace allocation failed: ") + cudaGetErrorString(e);
             sfmm_destroy(P);
@@ -534,8 +555,13 @@ void sfmm_destroy(sfmm_plan_t plan)
                   &plan->m2l_t, &plan->m2l_s, &plan->m2l_t2, &plan->m2l_s2, &plan->p2p_t, &plan->p2p_s,
                   &plan->p2p_t2, &plan->p2p_s2, &plan->m2l_off, &plan->p2p_off, &plan->leaves_src,
                   &plan->leaves_tgt, &plan->m2l_geo, &plan->m2m_geo, &plan->l2l_geo, &plan->soff,
-                  &plan->toff, &plan->dc, &plan->leftover, &plan->geom32, &plan->macn};
+                  &plan->toff, &plan->dc, &plan->leftover, &plan->geom32, &plan->macn, &plan->logtab,
+                  &plan->ttmp};
+    if (plan->aux) cudaStreamSynchronize(plan->aux);
     for (Buf* b : all) release(*b);
+    if (plan->ev_fork) cudaEventDestroy(plan->ev_fork);
+    if (plan->ev_join) cudaEventDestroy(plan->ev_join);
+    if (plan->aux) cudaStreamDestroy(plan->aux);
     delete plan;
 }
 

@@ -88,6 +88,8 @@ struct sfmm_plan_s {
     double tol = 0;
     sfmm_options opt{};
     cudaStream_t stream = nullptr;
+    cudaStream_t aux = nullptr;            // target keys + sort run here, overlapping the source tree
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     std::string err;
     bool timing = false;
     sfmm_stats stats{};
@@ -100,6 +102,7 @@ struct sfmm_plan_s {
     sfmm::Buf h_src, h_q, h_tgt, h_psi, h_alpha;
     // scratch
     sfmm::Buf tmp, flags, pos, small;   // small: a few int64 counters (device)
+    sfmm::Buf ttmp;                     // scratch of the target sort (auxiliary stream)
     // tree (node arrays)
     sfmm::Buf n_prefix, n_level, n_first, n_count, n_child0, n_parent, n_geom, n_tfirst, n_tcount;
     int64_t node_cap = 0;

@@ -12,7 +12,23 @@
 // |t| <= tan(pi/16) where 12 terms reach double precision.
 // ang2pix_nest: the equatorial / polar-cap formulas of Gorski et al. (2005),
 // with 1 - |z| = (x^2 + y^2)/(1 + |z|) in the caps.
+//
+// Fast path.  The same quantities are first computed in double-float
+// arithmetic on the FP32 pipe (about 46 significant bits; FP64 division and
+// square root on this GPU run at 1/64 of the FP32 rate): the ratio by a
+// double-float division, atan by a 33-entry table of atan(j/32) (rounded from
+// the host's FP64 atan) and atan(r) = r - r^3/3 + r^5/5 - r^7/7 for
+// |r| <= 1/64, then the equatorial or polar formula.  Every integer the key
+// depends on is a floor of a non-negative value v (v = N_side (1/2 + tt -+ 3z/4),
+// N_side tp sqrt(3(1-|z|)), ..., and tt itself in the caps); the fast path keeps
+// floor(v) only when v lies at least KEY_MARGIN from an integer.  Both its own
+// error and that of the FP64 routine are below 2^-15 in these units, so the
+// floors then agree; otherwise the point takes the FP64 routine above.  The
+// keys are therefore those of the FP64 routine, bit for bit.
 #include "common.cuh"
+#include "dfloat.cuh"
+
+#include <cmath>
 
 namespace sfmm {
 
@@ -107,14 +123,122 @@ __device__ __forceinline__ uint64_t key29(double x, double y, double z)
     return ((uint64_t)face << (2 * ORDER_MAX)) | spread_bits((uint64_t)ix) | (spread_bits((uint64_t)iy) << 1);
 }
 
+// ------------------------------------------------------------- fast path
+constexpr float KEY_MARGIN = 1.0f / 4096.0f;
+
+// floor of a double-float v >= 0 (|v| < 2^40); *ok = false when v is within
+// KEY_MARGIN of an integer
+__device__ __forceinline__ int64_t dfl_floor_checked(dflt v, bool* ok)
+{
+    const float fh = floorf(v.h);
+    const float g = __fadd_rn(__fsub_rn(v.h, fh), v.l);    // fractional part, to 2^-24
+    const float k = floorf(g);
+    const float fr = __fsub_rn(g, k);
+    if (fr < KEY_MARGIN || fr > 1.f - KEY_MARGIN) *ok = false;
+    return (int64_t)__float2ll_rz(fh) + (int64_t)k;
+}
+
+__device__ __forceinline__ dflt dfl_sqrt(dflt a)
+{
+    const float s0 = sqrtf(a.h);
+    // one Newton correction from the double-float residual a - s0^2
+    const float p = __fmul_rn(s0, s0);
+    const float e = __fmaf_rn(s0, s0, -p);
+    const float r = __fadd_rn(__fsub_rn(__fsub_rn(a.h, p), e), a.l);
+    return dfl_fast_two_sum(s0, __fdiv_rn(r, __fadd_rn(s0, s0)));
+}
+
+struct KeyTables {
+    float4 atan_c[33];     // atan(j/32) as (hi, lo), then (unused, unused)
+    float4 two_over_pi;    // 2/pi as (hi, lo)
+};
+
+// Order-29 key by the double-float fast path; *ok = false when a floor decision
+// is too close to call (the caller then uses key29).
+__device__ __forceinline__ uint64_t key29_fast(double x, double y, double z, const KeyTables& kt, bool* ok)
+{
+    const int64_t ns = int64_t(1) << ORDER_MAX;
+    const float nside = (float)ns;
+    const double ax = fabs(x), ay = fabs(y);
+    const bool swap = ay > ax;
+    const double num = swap ? ax : ay, den = swap ? ay : ax;
+    dflt tt(0.f, 0.f);
+    // within 2^-60 of the axis the float conversions lose the ratio: FP64 routine
+    if (den != 0.0 && den < 8.673617379884035e-19) { *ok = false; return 0; }
+    if (den != 0.0) {
+        const dflt T = dflt(num) / dflt(den);                       // t in [0, 1]
+        const int j = min(32, max(0, (int)__fadd_rn(__fmul_rn(T.h, 32.f), 0.5f)));
+        const float c = (float)j * (1.f / 32.f);
+        // r = (t - c) / (1 + t c), |r| <= 1/64: atan t = atan c + atan r
+        const dflt R = (T - dflt(c, 0.f)) / (dflt(1.f, 0.f) + T * c);
+        const float rh = R.h, s2 = __fmul_rn(rh, rh);
+        const float tail = __fmul_rn(__fmul_rn(rh, s2), -1.f / 3.f + s2 * (0.2f - s2 * (1.f / 7.f)));
+        const float4 a = kt.atan_c[j];
+        const dflt A = dflt(a.x, a.y) + (R + dflt(tail, 0.f));
+        const dflt u = A * dflt(kt.two_over_pi.x, kt.two_over_pi.y);   // quarter turns, [0, 1/2]
+        const dflt v = swap ? dflt(1.f, 0.f) - u : u;
+        const bool xpos = x >= 0.0, ypos = y >= 0.0;
+        if (xpos && ypos) tt = v;
+        else if (!xpos && ypos) tt = dflt(2.f, 0.f) - v;
+        else if (!xpos && !ypos) tt = dflt(2.f, 0.f) + v;
+        else tt = dflt(4.f, 0.f) - v;
+        // tt wraps from 4 to 0 at phi = 2 pi: too close to the wrap, let the FP64 routine decide
+        if (__fsub_rn(4.f, tt.h) < 1.f / 1073741824.f) *ok = false;
+        if (tt.h >= 4.f) tt = tt - dflt(4.f, 0.f);
+    }
+    const double za = fabs(z);
+    int64_t face, ix, iy;
+    if (za <= 2.0 / 3.0) {
+        const dflt W = dflt(0.5f, 0.f) + tt;
+        const dflt Z = dflt(z) * 0.75f;
+        const int64_t jp = dfl_floor_checked((W - Z) * nside, ok);
+        const int64_t jm = dfl_floor_checked((W + Z) * nside, ok);
+        const int64_t ifp = jp >> ORDER_MAX, ifm = jm >> ORDER_MAX;
+        face = (ifp == ifm) ? (ifp | 4) : ((ifp < ifm) ? ifp : (ifm + 8));
+        ix = jm & (ns - 1);
+        iy = ns - (jp & (ns - 1)) - 1;
+    } else {
+        int64_t ntt = dfl_floor_checked(tt * nside, ok) >> ORDER_MAX;   // floor(tt), decided at N_side resolution
+        if (ntt > 3) ntt = 3;
+        const dflt tp = tt - dflt((float)ntt, 0.f);
+        const dflt X(x), Y(y);
+        const dflt one_m_za = (X * X + Y * Y) / (dflt(1.f, 0.f) + dflt(za));
+        const dflt tmp = dfl_sqrt(one_m_za * 3.f) * nside;
+        int64_t jp = dfl_floor_checked(tp * tmp, ok);
+        int64_t jm = dfl_floor_checked((dflt(1.f, 0.f) - tp) * tmp, ok);
+        if (jp > ns - 1) jp = ns - 1;
+        if (jm > ns - 1) jm = ns - 1;
+        if (z > 0.0) { face = ntt; ix = ns - jm - 1; iy = ns - jp - 1; }
+        else         { face = ntt + 8; ix = jp; iy = jm; }
+    }
+    return ((uint64_t)face << (2 * ORDER_MAX)) | spread_bits((uint64_t)ix) | (spread_bits((uint64_t)iy) << 1);
+}
+
 __global__ void k_keys(const double* __restrict__ xyz, int64_t n, uint64_t* __restrict__ keys,
-                       uint32_t* __restrict__ iota)
+                       uint32_t* __restrict__ iota, KeyTables kt)
 {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const double x = xyz[3 * i], y = xyz[3 * i + 1], z = xyz[3 * i + 2];
-        keys[i] = key29(x, y, z);
+        bool ok = true;
+        uint64_t k = key29_fast(x, y, z, kt, &ok);
+        if (!ok) k = key29(x, y, z);
+        keys[i] = k;
         if (iota) iota[i] = (uint32_t)i;
     }
+}
+
+KeyTables make_key_tables()
+{
+    KeyTables kt;
+    for (int j = 0; j <= 32; ++j) {
+        const double a = std::atan(j / 32.0);
+        const float h = (float)a;
+        kt.atan_c[j] = make_float4(h, (float)(a - (double)h), 0.f, 0.f);
+    }
+    const double tp = 2.0 / 3.14159265358979323846;
+    const float h = (float)tp;
+    kt.two_over_pi = make_float4(h, (float)(tp - (double)h), 0.f, 0.f);
+    return kt;
 }
 
 }  // namespace
@@ -124,7 +248,8 @@ cudaError_t launch_keys(const double* xyz, int64_t n, uint64_t* keys, uint32_t* 
     if (n <= 0) return cudaSuccess;
     int64_t blocks = (n + 255) / 256;
     if (blocks > 152 * 32) blocks = 152 * 32;
-    k_keys<<<(unsigned)blocks, 256, 0, s>>>(xyz, n, keys, iota); count_launch();
+    static const KeyTables kt = make_key_tables();
+    k_keys<<<(unsigned)blocks, 256, 0, s>>>(xyz, n, keys, iota, kt); count_launch();
     return cudaGetLastError();
 }
 

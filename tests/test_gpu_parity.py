@@ -77,6 +77,48 @@ def test_keys_bit_exact():
     assert bad.size == 0, (bad[:10], x[bad[:3]], got[bad[:3]], want[bad[:3]])
 
 
+def test_keys_bit_exact_near_decision_boundaries():
+    """The key kernel's double-float fast path defers to the FP64 routine near
+    every floor decision; points placed on and within rounding of the decisions
+    (order-29 pixel edges and corners, the phi = 0 wrap, octant and quadrant
+    lines, the polar-cap and equatorial ring boundaries) must still give the
+    oracle's keys bit for bit."""
+    rng = np.random.default_rng(5)
+    pts = []
+    # order-29 pixel corners and edge midpoints, nudged by a few ulp in each coordinate
+    o = 29
+    pix = rng.integers(0, 12 * 4 ** o, 20000, dtype=np.int64).astype(np.uint64)
+    f, ix, iy = hp.pix2face_xy(o, pix)
+    for dx, dy in ((0.0, 0.0), (0.5, 0.0), (0.0, 0.5)):
+        c = unit(hp.facexy2vec(o, f, ix.astype(float) + dx, iy.astype(float) + dy))
+        for k in (0, 1, 4):
+            pts.append(unit(c + k * 2.2e-16 * rng.choice([-1.0, 1.0], size=c.shape)))
+    # phi just below 2 pi (x > 0, y -> 0-), on the octant and quadrant lines
+    t = np.geomspace(1e-17, 1e-6, 3000)
+    for zz in (0.0, 0.5, 0.9, -0.95):
+        st = np.sqrt(1 - zz * zz)
+        pts.append(np.stack([st * np.cos(-t), st * np.sin(-t), np.full_like(t, zz)], 1))
+        pts.append(np.stack([st * np.cos(np.pi / 4 + t), st * np.sin(np.pi / 4 + t), np.full_like(t, zz)], 1))
+        pts.append(np.stack([st * np.cos(np.pi / 2 - t), st * np.sin(np.pi / 2 - t), np.full_like(t, zz)], 1))
+        pts.append(np.stack([st * np.cos(np.pi + t), st * np.sin(np.pi + t), np.full_like(t, zz)], 1))
+    # the polar-cap boundary |z| = 2/3 from both sides, near the poles
+    zb = np.concatenate([2 / 3 + np.geomspace(1e-17, 1e-9, 2000), 2 / 3 - np.geomspace(1e-17, 1e-9, 2000),
+                         1 - np.geomspace(1e-18, 1e-12, 2000)])
+    ph = rng.uniform(0, 2 * np.pi, zb.size)
+    for sgn in (1.0, -1.0):
+        z = sgn * zb
+        st = np.sqrt(np.maximum(0, 1 - z * z))
+        pts.append(np.stack([st * np.cos(ph), st * np.sin(ph), z], 1))
+    # near the axis: tiny x, y
+    tiny = np.geomspace(1e-300, 1e-15, 500)
+    pts.append(np.stack([tiny, -tiny * 0.5, np.sqrt(1 - 1.25 * tiny ** 2)], 1))
+    x = np.vstack(pts)
+    got = sfmm.keys(dev(x)).cpu().numpy().view(np.uint64)
+    want = hp.key29(x)
+    bad = np.nonzero(got != want)[0]
+    assert bad.size == 0, (bad.size, bad[:10], x[bad[:3]], got[bad[:3]], want[bad[:3]])
+
+
 # ------------------------------------------------------------------- tree --
 @pytest.fixture(scope="module")
 def small_solve():
