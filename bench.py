@@ -38,7 +38,7 @@ FP32_PEAK_DERIVED = 152 * 128 * 2 * 2.07e9  # SMs x FP32 FMA/clk/SM x 2 flop x m
 # (path name, precision enum value, order p, stated relative error, leaf size m, c_s, c_t):
 # per path the fastest setting measured on the clustered 1.6e7 workload that keeps
 # the error vs the oracle well inside the stated error
-MODES = [("mixed", 1, 16, 1e-6, 32, 2.0, 0.5), ("mixed_df", 2, 26, 1e-10, 64, 2.0, 0.45),
+MODES = [("mixed", 1, 16, 1e-6, 64, 2.0, 0.5), ("mixed_df", 2, 26, 1e-10, 64, 2.0, 0.45),
          ("fp64", 0, 32, 1e-10, 32, 2.0, 0.5)]
 # algorithmic FP64 flops per near-field pair: d^2 (3 sub, 3 mul, 2 add), 1/d^2
 # (counted as 4), q/d^2 (1), alpha sums (3 mul + 3 add), sum q (1); psi adds the

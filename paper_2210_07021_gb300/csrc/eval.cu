@@ -174,7 +174,8 @@ __global__ void k_count_pairs(TreeView T, const int* __restrict__ leaves, int64_
 // are kept in two FP32 levels (blocks of 16 pairs) and combined per target in
 // FP32 across lanes, then in FP64.  Exactly coincident pairs are skipped.
 // L2P: FP32 Horner, FP64 final combination of psi.
-constexpr int STAGE = 256;
+constexpr int STAGE = 256;     // sources staged per warp (double-float kernel)
+constexpr int STAGE32 = 192;   // FP32 kernel: smaller stage, 7 blocks of 4 warps per SM
 
 struct Eval32Args {
     TreeView T;
@@ -307,10 +308,10 @@ __device__ __forceinline__ void finish_target32(const Eval32Args& A, const LeafF
 // 32), group b the power of two >= what a leaves (at most 32), e.g. 18 = 16 + 2
 // and 40 = 32 + 8; each target of a group gets 32/size lanes.
 template <bool PSI>
-__global__ void __launch_bounds__(128) k_eval32(Eval32Args A)
+__global__ void __launch_bounds__(128, 7) k_eval32(Eval32Args A)
 {
-    __shared__ float4 s_hi[4][STAGE];
-    __shared__ float4 s_lo[4][STAGE];
+    __shared__ float4 s_hi[4][STAGE32];
+    __shared__ float4 s_lo[4][STAGE32];
     __shared__ float s_dc[4][32][6];
     __shared__ int s_pre[4][33];
     __shared__ int s_first[4][32];
@@ -375,10 +376,10 @@ __global__ void __launch_bounds__(128) k_eval32(Eval32Args A)
                     const int t = __shfl_up_sync(FULL, inc, o);
                     if (lane >= o) inc += t;
                 }
-                const unsigned fit = __ballot_sync(FULL, k < nb1 && inc <= STAGE);
+                const unsigned fit = __ballot_sync(FULL, k < nb1 && inc <= STAGE32);
                 const int nfit = __popc(fit);
                 int ns, nl;
-                if (nfit == 0) { ns = STAGE; nl = 1; }        // one leaf larger than the stage: a chunk of it
+                if (nfit == 0) { ns = STAGE32; nl = 1; }        // one leaf larger than the stage: a chunk of it
                 else { ns = __shfl_sync(FULL, inc, nfit - 1); nl = nfit; }
                 pre[lane] = inc - cnt;
                 fst[lane] = first;
@@ -403,7 +404,7 @@ __global__ void __launch_bounds__(128) k_eval32(Eval32Args A)
                     yh[idx] = make_float4(sx, sy, sz, h.w);
                     yl[idx] = make_float4(ex_ + (l.x + d[3]), ey_ + (l.y + d[4]), ez_ + (l.z + d[5]), 0.f);
                 }
-                if (nfit == 0) jn += STAGE;
+                if (nfit == 0) jn += STAGE32;
                 else { kn += nfit; jn = 0; }
                 __syncwarp();
                 pair_sums32<PSI>(yh, yl, ns, sa, lpa, tha, tla, acc_a);
