@@ -25,7 +25,7 @@ cudaError_t launch_child_geo(const TreeView& T, const float* g32, void* m2m, voi
 cudaError_t launch_src_offsets(const TreeView& T, const int* leaves, int64_t n_leaves, const double4_32a* src,
                                float4* off, cudaStream_t s);
 cudaError_t launch_p2m(const TreeView& T, const int* leaves, int64_t n_leaves, const double4_32a* src,
-                       const float4* off, void* mpole, int p, int ek, cudaStream_t s);
+                       const float4* off, const float4* log_tab, void* mpole, int p, int ek, cudaStream_t s);
 cudaError_t launch_m2m(const TreeView& T, int a, int b, int p, const double* tables, const void* geo, void* mpole,
                        int ek, cudaStream_t s);
 cudaError_t launch_m2l(const TreeView& T, const int64_t* off, const uint32_t* srcs, int p, const double* tables,
@@ -292,7 +292,7 @@ sfmm_status solve(sfmm_plan_s* P, const double* src, const void* q, int64_t N, c
             return cuda_fail(P, e, "offsets");
     }
     if ((e = launch_p2m(T, P->leaves_src.as<int>(), P->n_leaves, P->src4.as<double4_32a>(), P->soff.as<float4>(),
-                        P->mpole.p, p, ek, s)))
+                        P->logtab.as<float4>(), P->mpole.p, p, ek, s)))
         return cuda_fail(P, e, "P2M");
     const int depth = (int)P->level_start.size() - 2;
     for (int l = depth - 1; l >= 0; --l)

@@ -93,6 +93,37 @@ __device__ __forceinline__ void dfl_mac(dflt& acc, dflt a, dflt b)
     acc.l = __fadd_rn(acc.l, __fadd_rn(s.l, e));
 }
 
+// log x for a double-float x > 0 (normal leading part), left unnormalised for
+// an accumulation.  tab[j] (j < 128) holds log c_j and 1/c_j as (hi, lo) pairs,
+// tab[128] log 2 as a 16-bit leading part and the rest; the tables are rounded
+// from FP64 on the host.  x = 2^e m (1 + l'), m in [1, 2); with c_j = 1 + j/128 the
+// leading seven fraction bits of m, log x = e log 2 + log c_j + log1p(r),
+// r = (m - c_j + l 2^-e) / c_j, |r| < 2^-7.  m - c_j is exact; log1p(r) - r is
+// a degree-6 series (remainder below r^7/7 < 2^-52); log 2 is split so that
+// e times its leading part is exact.  The three leading terms meet in two
+// exact two-sums, every tail goes to the low part.
+__device__ __forceinline__ dflt dfl_log_lazy(dflt x, const float4* __restrict__ tab)
+{
+    const int bits = __float_as_int(x.h);
+    const int be = bits >> 23;                                            // biased exponent (x.h > 0)
+    const int j = (bits >> 16) & 0x7F;
+    const float m = __int_as_float((bits & 0x007FFFFF) | 0x3F800000);     // [1, 2)
+    const float cj = __int_as_float((bits & 0x007F0000) | 0x3F800000);    // 1 + j/128, exactly
+    const float scale = __int_as_float((254 - be) << 23);                 // 2^-e
+    const float4 t = tab[j];                                              // log c_j (hi, lo), 1/c_j (hi, lo)
+    const dflt delta = dfl_two_sum(__fsub_rn(m, cj), __fmul_rn(x.l, scale));
+    const dflt r = dfl_mul_lazy(delta, dflt(t.z, t.w));
+    const float rh = r.h;
+    float poly = __fmul_rn(rh, rh) * (-0.5f + rh * (1.f / 3.f + rh * (-0.25f + rh * (0.2f + rh * (-1.f / 6.f)))));
+    poly = __fmaf_rn(-rh, r.l, poly);                                     // cross term of -r^2/2
+    const float4 l2 = tab[128];                                           // log 2: 16-bit leading part, tail
+    const float e = (float)(be - 127);
+    const dflt s1 = dfl_two_sum(__fmul_rn(e, l2.x), t.x);
+    const dflt s2 = dfl_two_sum(s1.h, rh);
+    const float lo = __fmaf_rn(e, l2.y, __fadd_rn(__fadd_rn(s1.l, s2.l), __fadd_rn(__fadd_rn(t.y, r.l), poly)));
+    return dflt(s2.h, lo);
+}
+
 __device__ __forceinline__ dflt dfl_shfl_up(dflt v, int o)
 {
     return dflt(__shfl_up_sync(0xffffffffu, v.h, o), __shfl_up_sync(0xffffffffu, v.l, o));

@@ -568,6 +568,63 @@ __global__ void k_p2m(TreeView T, const int* __restrict__ leaves, int64_t n_leav
     }
 }
 
+// Double-float (1e-10 mixed path): from each source's (hi, lo) offset to its
+// leaf centre, z^l by repeated double-float products, log(1 - d^2/4) = 2 log
+// cos(theta/2) by the table-driven double-float logarithm (tab: as in the
+// evaluation).  One thread per leaf.
+template <int P>
+__global__ void __launch_bounds__(128) k_p2m_df(TreeView T, const int* __restrict__ leaves, int64_t n_leaves,
+                                                const float4* __restrict__ off, const float4* __restrict__ log_tab,
+                                                dflt* __restrict__ mpole)
+{
+    __shared__ float4 s_tab[129];
+    for (int i = threadIdx.x; i < 129; i += blockDim.x) s_tab[i] = log_tab[i];
+    __syncthreads();
+    for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < n_leaves; w += (int64_t)gridDim.x * blockDim.x) {
+        const int node = leaves[w];
+        const double* g = T.geom + (size_t)node * GEOM_STRIDE;
+        const dflt etx(g[3]), ety(g[4]), etz(g[5]), epx(g[6]), epy(g[7]), epz(g[8]);
+        const dflt inv_r(1.0 / g[10]);
+        dflt Ar[P], Ai[P];
+#pragma unroll
+        for (int l = 0; l < P; ++l) { Ar[l] = dflt(0.f, 0.f); Ai[l] = dflt(0.f, 0.f); }
+        dflt Csum(0.f, 0.f), Qsum(0.f, 0.f);
+        const int f = T.first[node], n = T.count[node];
+        for (int j = f; j < f + n; ++j) {
+            const float4 h = off[2 * (size_t)j], lo = off[2 * (size_t)j + 1];
+            const dflt dx(h.x, lo.x), dy(h.y, lo.y), dz(h.z, lo.z), q(h.w, lo.w);
+            const dflt d2 = dx * dx + dy * dy + dz * dz;
+            const dflt sc = inv_r / (dflt(2.f, 0.f) - d2 * 0.5f);            // 1/(r (1 + y.c))
+            const dflt zr = (dx * etx + dy * ety + dz * etz) * sc;
+            const dflt zi = (dx * epx + dy * epy + dz * epz) * sc;
+            Qsum += q;
+            dfl_mac(Csum, q, dfl_log_lazy(dflt(1.f, 0.f) - d2 * 0.25f, s_tab));   // 2 log cos(theta/2)
+            dflt pr = q, pi(0.f, 0.f);
+#pragma unroll
+            for (int l = 0; l < P; ++l) {
+                const dflt nr = pr * zr - pi * zi, ni = pr * zi + pi * zr;
+                pr = nr;
+                pi = ni;
+                Ar[l] += pr;
+                Ai[l] += pi;
+            }
+        }
+        Csum = dfl_norm(Csum);
+        dflt* e = mpole + (size_t)node * EXP_STRIDE;
+        const dflt i4p(INV4PI), l2(LOG2);
+        const dflt Q = i4p * Qsum;
+        e[0] = i4p * Csum - Q * l2;
+        e[1] = Q;
+#pragma unroll
+        for (int l = 0; l < P; ++l) {
+            const dflt sl = -(i4p / dflt(l + 1));
+            e[2 + 2 * l] = sl * Ar[l];
+            e[3 + 2 * l] = sl * Ai[l];
+        }
+        for (int l = P; l < PMAX; ++l) { e[2 + 2 * l] = dflt(0.f, 0.f); e[3 + 2 * l] = dflt(0.f, 0.f); }
+    }
+}
+
 // FP32: from each source's FP32 offset to its leaf centre (the recentring was
 // done in FP64 when the offsets were formed).
 template <int P>
@@ -833,14 +890,14 @@ cudaError_t launch_src_offsets(const TreeView& T, const int* leaves, int64_t n_l
 
 // mpole: double (FP64 path), float (mixed path) or double-float storage (1e-10 mixed path)
 cudaError_t launch_p2m(const TreeView& T, const int* leaves, int64_t n_leaves, const double4_32a* src,
-                       const float4* off, void* mpole, int p, int ek, cudaStream_t s)
+                       const float4* off, const float4* log_tab, void* mpole, int p, int ek, cudaStream_t s)
 {
     if (n_leaves == 0) return cudaSuccess;
     const unsigned g = grid_for(n_leaves, 128);
 #define P2M_CASE(PP)                                                                                       \
     case PP:                                                                                               \
         if (ek == EXP_F32) k_p2m32<PP><<<g, 128, 0, s>>>(T, leaves, n_leaves, off, static_cast<float*>(mpole)); \
-        else if (ek == EXP_DF) k_p2m<PP, dflt><<<g, 128, 0, s>>>(T, leaves, n_leaves, src, static_cast<dflt*>(mpole)); \
+        else if (ek == EXP_DF) k_p2m_df<PP><<<g, 128, 0, s>>>(T, leaves, n_leaves, off, log_tab, static_cast<dflt*>(mpole)); \
         else k_p2m<PP, double><<<g, 128, 0, s>>>(T, leaves, n_leaves, src, static_cast<double*>(mpole));   \
         count_launch();                                                                                    \
         break;

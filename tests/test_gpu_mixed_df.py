@@ -113,3 +113,25 @@ def test_df_empty():
     psi, alpha = plan.deflection(dev(np.zeros((0, 3))), dev(np.zeros(0)), dev(unit(np.ones((3, 3)))))
     torch.cuda.synchronize()
     assert np.all(psi.cpu().numpy() == 0) and np.all(alpha.cpu().numpy() == 0)
+
+
+@pytest.mark.parametrize("p", [8, 26, 32])
+def test_df_multipoles_match_fp64(p):
+    """The double-float P2M (from (hi, lo) offsets, table logarithm) and M2M give
+    the FP64 path's multipoles to double-float accuracy, node by node."""
+    rng = np.random.default_rng(30 + p)
+    src = workloads.clustered(rng, 50000, 25)
+    tgt = unit(rng.normal(size=(2000, 3)))
+    q = rng.lognormal(0, 0.5, 50000)
+    pm, _, _ = solve(src, q, tgt, p=p, leaf=64)
+    pd, _, _ = solve(src, q, tgt, precision=sfmm.SFMM_FP64, p=p, leaf=64)
+    m_df = pm.debug(sfmm.ARR_MULTIPOLE, np.float64, 2 * p + 2)
+    m_64 = pd.debug(sfmm.ARR_MULTIPOLE, np.float64, 2 * p + 2)
+    r = pd.debug(sfmm.ARR_NODE_GEOM, np.float64, 11)[:, 10]
+    ell = np.arange(1, p + 1)
+    # compare the scaled coefficients A_l / r^l, which are O(|Q|) at every level
+    s_df = (m_df[:, 2::2] + 1j * m_df[:, 3::2]) / r[:, None] ** ell
+    s_64 = (m_64[:, 2::2] + 1j * m_64[:, 3::2]) / r[:, None] ** ell
+    scale = np.abs(m_64[:, 1]).max()
+    assert np.abs(s_df - s_64).max() < 1e-12 * scale
+    assert np.abs(m_df[:, :2] - m_64[:, :2]).max() < 1e-12 * np.abs(m_64[:, :2]).max()
