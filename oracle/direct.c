@@ -91,6 +91,58 @@ int64_t oracle_direct(const double* src, const double* q, int64_t N,
     return skipped;
 }
 
+/* Potential and covariant gradient, at the points y[N], of charges h[M] and
+ * tangent dipoles g[M][3] (g_i . x_i = 0) placed at the points x[M]:
+ *
+ *   Phi(y)       = sum_i h_i G(x_i, y) + g_i . grad_x G(x_i, y)
+ *                = sum_i h_i (1/4pi) log(r^2/4) + g_i . (x_i - y) / (2 pi r^2),
+ *   grad_S Phi   = P_y sum_i [ h_i (y - x_i) / (2 pi r^2)
+ *                              + ( -g_i / r^2 + 2 (g_i . (x_i - y)) (x_i - y) / r^4 ) / (2 pi) ],
+ *
+ * r^2 = |x_i - y|^2.  The dipole term is the derivative of the point-mass
+ * potential (Eq. GRE_FUN) with respect to the mass position along g_i, and
+ * grad_x G = P_x (x - y)/(2 pi r^2) reduces to (x - y)/(2 pi r^2) on g_i
+ * because g_i is tangent at x_i.  It is what the gradient of a loss of psi and
+ * alpha with respect to the masses and their positions needs (the adjoint
+ * problem).  Pairs with r^2 == 0 are skipped.  Either output may be NULL;
+ * grad3 is the tangent 3-vector at y.  Returns the skipped pairs. */
+int64_t oracle_dipole(const double* x, const double* h, const double* g, int64_t M,
+                      const double* y, int64_t N, double* phi, double* grad3)
+{
+    const double inv4pi = 1.0 / (4.0 * M_PI);
+    const double inv2pi = 1.0 / (2.0 * M_PI);
+    int64_t skipped = 0;
+#pragma omp parallel for schedule(dynamic, 1) reduction(+:skipped)
+    for (int64_t j = 0; j < N; ++j) {
+        const double y0 = y[3 * j], y1 = y[3 * j + 1], y2 = y[3 * j + 2];
+        nsum sp = {0, 0}, v0 = {0, 0}, v1 = {0, 0}, v2 = {0, 0};
+        for (int64_t i = 0; i < M; ++i) {
+            /* e = x_i - y */
+            const double e0 = x[3 * i] - y0, e1 = x[3 * i + 1] - y1, e2 = x[3 * i + 2] - y2;
+            const double r2 = e0 * e0 + e1 * e1 + e2 * e2;
+            if (r2 == 0.0) { ++skipped; continue; }
+            const double hi = h ? h[i] : 0.0;
+            const double g0 = g ? g[3 * i] : 0.0, g1 = g ? g[3 * i + 1] : 0.0, g2 = g ? g[3 * i + 2] : 0.0;
+            const double ge = g0 * e0 + g1 * e1 + g2 * e2;
+            nadd(&sp, hi * inv4pi * log(0.25 * r2) + ge * inv2pi / r2);
+            const double wm = -hi * inv2pi / r2;              /* h (y - x) / (2 pi r^2) = -h e / (2 pi r^2) */
+            const double wd = 2.0 * ge * inv2pi / (r2 * r2);
+            nadd(&v0, wm * e0 - g0 * inv2pi / r2 + wd * e0);
+            nadd(&v1, wm * e1 - g1 * inv2pi / r2 + wd * e1);
+            nadd(&v2, wm * e2 - g2 * inv2pi / r2 + wd * e2);
+        }
+        if (phi) phi[j] = nval(&sp);
+        if (grad3) {
+            const double a0 = nval(&v0), a1 = nval(&v1), a2 = nval(&v2);
+            const double yv = y0 * a0 + y1 * a1 + y2 * a2;     /* P_y v = v - (y . v) y */
+            grad3[3 * j] = a0 - yv * y0;
+            grad3[3 * j + 1] = a1 - yv * y1;
+            grad3[3 * j + 2] = a2 - yv * y2;
+        }
+    }
+    return skipped;
+}
+
 /* Number of OpenMP threads the direct sum will use (for reporting). */
 int oracle_threads(void)
 {

@@ -24,6 +24,8 @@ def _load():
         dp = ctypes.POINTER(ctypes.c_double)
         lib.oracle_direct.argtypes = [dp, dp, ctypes.c_int64, dp, ctypes.c_int64, dp, dp, dp]
         lib.oracle_direct.restype = ctypes.c_int64
+        lib.oracle_dipole.argtypes = [dp, dp, dp, ctypes.c_int64, dp, ctypes.c_int64, dp, dp]
+        lib.oracle_dipole.restype = ctypes.c_int64
         lib.oracle_threads.argtypes = []
         lib.oracle_threads.restype = ctypes.c_int
         _lib = lib
@@ -59,6 +61,57 @@ def direct_sum(src, q, tgt, want=("psi", "alpha")):
     if a3 is not None:
         out["alpha3"] = a3
     return out
+
+
+def tangent_basis(x):
+    """(e_theta, e_phi) at the unit vectors x [M,3], with phi = atan2(0, 0) = 0 at
+    the poles: e_theta = (cos t cos p, cos t sin p, -sin t), e_phi = (-sin p, cos p, 0)."""
+    x = np.asarray(x, dtype=np.float64).reshape(-1, 3)
+    rho = np.hypot(x[:, 0], x[:, 1])
+    safe = np.where(rho > 0, rho, 1.0)
+    cp = np.where(rho > 0, x[:, 0] / safe, 1.0)
+    sp = np.where(rho > 0, x[:, 1] / safe, 0.0)
+    e_th = np.stack([x[:, 2] * cp, x[:, 2] * sp, -rho], 1)
+    e_ph = np.stack([-sp, cp, np.zeros_like(cp)], 1)
+    return e_th, e_ph
+
+
+def dipole_field(x, h, g, y):
+    """Phi [N] and its covariant gradient [N,3] at y of charges h [M] and tangent
+    dipoles g [M,3] at x (either may be None); see oracle_dipole in direct.c."""
+    lib = _load()
+    x = np.ascontiguousarray(x, dtype=np.float64).reshape(-1, 3)
+    y = np.ascontiguousarray(y, dtype=np.float64).reshape(-1, 3)
+    hh = None if h is None else np.ascontiguousarray(h, dtype=np.float64).reshape(-1)
+    gg = None if g is None else np.ascontiguousarray(g, dtype=np.float64).reshape(-1, 3)
+    phi = np.empty(y.shape[0])
+    grad = np.empty((y.shape[0], 3))
+    lib.oracle_dipole(_ptr(x), _ptr(hh), _ptr(gg), x.shape[0], _ptr(y), y.shape[0], _ptr(phi), _ptr(grad))
+    return phi, grad
+
+
+def adjoint(src, q, tgt, g_alpha=None, g_psi=None, zero_mean=False):
+    """Gradients of a loss L(psi, alpha) of the direct-sum outputs at the targets,
+    given dL/dalpha [M,2] (components on (e_theta, e_phi) at each target) and
+    dL/dpsi [M]:
+
+      dL/dq_j = sum_i dL/dpsi_i G(x_i, y_j) + g_i . grad_x G(x_i, y_j)   (+ sum dL/dpsi / 4pi with zero_mean)
+      dL/dy_j = q_j grad_S [ the same sum as a function of y ] (y = y_j), a tangent 3-vector,
+
+    g_i = dL/dalpha_i[0] e_theta(x_i) + dL/dalpha_i[1] e_phi(x_i), because
+    alpha_i = sum_j q_j grad_x G(x_i, y_j) is linear in q and G is symmetric.
+    Returns (dL/dq [N], dL/dy [N,3])."""
+    tgt = np.asarray(tgt, dtype=np.float64).reshape(-1, 3)
+    q = np.asarray(q, dtype=np.float64).reshape(-1)
+    g = None
+    if g_alpha is not None:
+        ga = np.asarray(g_alpha, dtype=np.float64).reshape(-1, 2)
+        e_th, e_ph = tangent_basis(tgt)
+        g = ga[:, :1] * e_th + ga[:, 1:] * e_ph
+    phi, grad = dipole_field(tgt, g_psi, g, src)
+    if zero_mean and g_psi is not None:
+        phi = phi + np.sum(g_psi) / (4 * np.pi)
+    return phi, q[:, None] * grad
 
 
 def threads() -> int:
