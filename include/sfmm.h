@@ -118,6 +118,29 @@ sfmm_status sfmm_deflection(sfmm_plan_t plan, const double* src_xyz, const void*
 sfmm_status sfmm_deflection_host(sfmm_plan_t plan, const double* src_xyz, const void* q, int64_t N,
                                  const double* tgt_xyz, int64_t M, double* psi, double* alpha);
 
+/*
+ * Adjoint: gradients of a loss L(psi, alpha) of sfmm_deflection's outputs with
+ * respect to the masses and the source positions, given dL/dpsi and
+ * dL/dalpha at the targets.  With g_i = g_alpha[i][0] e_theta(x_i) +
+ * g_alpha[i][1] e_phi(x_i) (the basis alpha is written in) and
+ * Phi(y) = sum_i g_psi[i] G(x_i, y) + g_i . grad_x G(x_i, y):
+ *   grad_q[j]   = dL/dq_j = Phi(y_j)   (+ sum_i g_psi[i] / 4pi with opt.zero_mean),
+ *   grad_src[j] = dL/dy_j = q_j grad_S Phi(y_j), the covariant (tangent)
+ *                 gradient on the sphere as a 3-vector [N][3].
+ * This is one more sFMM: charges g_psi and tangent dipoles g at the targets
+ * (the dipole multipole is Lemma 1 differentiated along g), evaluated at the
+ * sources; M2M, M2L and L2L are those of the forward solve.  It runs in FP64
+ * whatever opt.precision is, with the plan's p, leaf size and MAC.  Arguments
+ * as for sfmm_deflection (device pointers; q float32 when opt.q_f32); g_psi
+ * [M] and g_alpha [M][2] may be NULL (treated as zero); at least one of
+ * grad_q [N], grad_src [N][3] must be non-NULL.  Gradients with respect to the
+ * target positions are not formed.  The paper has no adjoint; this follows
+ * from Eqs. SUM, GRE_FUN and ALP_PSI by linearity in q and symmetry of G.
+ */
+sfmm_status sfmm_adjoint(sfmm_plan_t plan, const double* src_xyz, const void* q, int64_t N,
+                         const double* tgt_xyz, int64_t M, const double* g_psi, const double* g_alpha,
+                         double* grad_q, double* grad_src);
+
 /* Release the plan and its workspace.  NULL is ignored. */
 void sfmm_destroy(sfmm_plan_t plan);
 

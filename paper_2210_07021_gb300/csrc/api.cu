@@ -54,6 +54,12 @@ cudaError_t launch_eval_df(const TreeView& T, const int* leaves, int64_t n_leave
                            const float4* toff, const float4* dc, const double4_32a* tgt, const uint32_t* tperm,
                            const int64_t* p2p_off, const uint32_t* p2p_src, const void* local, const void* mpole,
                            const float4* log_tab, int p, int zero_mean, double* psi, double* alpha, cudaStream_t s);
+cudaError_t launch_p2m_adj(const TreeView& T, const int* leaves, int64_t n_leaves, const double4_32a* src,
+                           const double4_32a* dip, double* mpole, int p, cudaStream_t s);
+cudaError_t launch_eval_adj(const TreeView& T, const int* leaves, int64_t n_leaves, const double4_32a* src,
+                            const double4_32a* dip, const double4_32a* tgt, const uint32_t* tperm,
+                            const int64_t* p2p_off, const uint32_t* p2p_src, const double* local, const double* mpole,
+                            int p, int zero_mean, const void* w, int w_f32, double* phi, double* grad3, cudaStream_t s);
 cudaError_t launch_eval(const TreeView& T, const int* leaves, int64_t n_leaves, const double4_32a* src, const double4_32a* tgt,
                         const uint32_t* tperm, const int64_t* p2p_off, const uint32_t* p2p_src, const double* local,
                         const double* mpole, int p, int zero_mean, double* psi, double* alpha, cudaStream_t s);
@@ -112,6 +118,36 @@ __global__ void k_gather_src(const double* __restrict__ xyz, const void* __restr
         const uint32_t j = perm[i];
         const double qq = q_f32 ? (double)static_cast<const float*>(q)[j] : static_cast<const double*>(q)[j];
         out[i] = make_double4_32a(xyz[3 * (size_t)j], xyz[3 * (size_t)j + 1], xyz[3 * (size_t)j + 2], qq);
+    }
+}
+
+// tangent dipoles of the adjoint into key order (g_x, g_y, g_z, 0)
+__global__ void k_gather_dip(const double* __restrict__ g, const uint32_t* __restrict__ perm, int64_t n,
+                             double4_32a* __restrict__ out)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t j = perm[i];
+        out[i] = make_double4_32a(g[3 * (size_t)j], g[3 * (size_t)j + 1], g[3 * (size_t)j + 2], 0.0);
+    }
+}
+
+// Adjoint sources at the forward targets x_i: charge h_i = dL/dpsi_i (0 without
+// one) and tangent dipole g_i = dL/dalpha_i[0] e_theta(x_i) + dL/dalpha_i[1]
+// e_phi(x_i), the basis the forward path writes alpha in (phi = 0 at the poles).
+__global__ void k_adjoint_prep(const double* __restrict__ x, int64_t m, const double* __restrict__ g_psi,
+                               const double* __restrict__ g_alpha, double* __restrict__ h, double* __restrict__ dip)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+        const double x0 = x[3 * i], x1 = x[3 * i + 1], x2 = x[3 * i + 2];
+        h[i] = g_psi ? g_psi[i] : 0.0;
+        double a = 0.0, b = 0.0;
+        if (g_alpha) { a = g_alpha[2 * i]; b = g_alpha[2 * i + 1]; }
+        const double rho = sqrt(x0 * x0 + x1 * x1);
+        double cp = 1.0, sp = 0.0;
+        if (rho > 0.0) { cp = x0 / rho; sp = x1 / rho; }
+        dip[3 * i] = a * (x2 * cp) - b * sp;
+        dip[3 * i + 1] = a * (x2 * sp) + b * cp;
+        dip[3 * i + 2] = -a * rho;
     }
 }
 
@@ -204,10 +240,21 @@ struct PhaseTimer {
     }
 };
 
+// The adjoint's extra inputs and outputs: tangent dipoles at the sources,
+// weights of the targets' gradient output and that output ([M][3]).
+struct AdjIO {
+    const double* dip;
+    const void* w;
+    int w_f32;
+    double* grad3;
+};
+
 sfmm_status solve(sfmm_plan_s* P, const double* src, const void* q, int64_t N, const double* tgt, int64_t M,
-                  double* psi, double* alpha)
+                  double* psi, double* alpha, const AdjIO* adj = nullptr)
 {
     cudaStream_t s = P->stream;
+    const int precision = adj ? SFMM_FP64 : P->opt.precision;       // the adjoint runs in FP64
+    const int q_f32 = adj ? 0 : P->opt.q_f32;
     cudaError_t e;
     const int p = P->p;
     P->err.clear();
@@ -219,6 +266,8 @@ sfmm_status solve(sfmm_plan_s* P, const double* src, const void* q, int64_t N, c
     if (M > 0 && N == 0) {
         if (psi && (e = cudaMemsetAsync(psi, 0, (size_t)M * 8, s))) return cuda_fail(P, e, "memset psi");
         if (alpha && (e = cudaMemsetAsync(alpha, 0, (size_t)M * 16, s))) return cuda_fail(P, e, "memset alpha");
+        if (adj && adj->grad3 && (e = cudaMemsetAsync(adj->grad3, 0, (size_t)M * 24, s)))
+            return cuda_fail(P, e, "memset gradient");
         if ((e = cudaStreamSynchronize(s))) return cuda_fail(P, e, "sync");
         return SFMM_OK;
     }
@@ -257,7 +306,11 @@ sfmm_status solve(sfmm_plan_s* P, const double* src, const void* q, int64_t N, c
         return cuda_fail(P, e, "sort sources");
     const uint64_t* skeys = P->skeys_alt ? P->skeys2.as<uint64_t>() : P->skeys.as<uint64_t>();
     const uint32_t* sperm = P->skeys_alt ? P->sperm2.as<uint32_t>() : P->sperm.as<uint32_t>();
-    k_gather_src<<<grid_for(N), 256, 0, s>>>(src, q, P->opt.q_f32, sperm, N, P->src4.as<double4_32a>()); count_launch();
+    k_gather_src<<<grid_for(N), 256, 0, s>>>(src, q, q_f32, sperm, N, P->src4.as<double4_32a>()); count_launch();
+    if (adj) {
+        if ((e = ensure(P->dip4, (size_t)N * 32))) return cuda_fail(P, e, "alloc dipoles");
+        k_gather_dip<<<grid_for(N), 256, 0, s>>>(adj->dip, sperm, N, P->dip4.as<double4_32a>()); count_launch();
+    }
     if ((e = cudaGetLastError())) return cuda_fail(P, e, "gather");
     tm.mark();
     // ---- tree and geometry (sources)
@@ -268,8 +321,8 @@ sfmm_status solve(sfmm_plan_s* P, const double* src, const void* q, int64_t N, c
     if ((e = collect_leaves(P, T.count, P->leaves_src, &P->n_leaves))) return cuda_fail(P, e, "leaves");
     tm.mark();
     // ---- up-pass
-    const bool fp32 = P->opt.precision == SFMM_MIXED;
-    const bool dfe = P->opt.precision == SFMM_MIXED_DF;
+    const bool fp32 = precision == SFMM_MIXED;
+    const bool dfe = precision == SFMM_MIXED_DF;
     const bool offsets = fp32 || dfe;                  // FP32 (hi, lo) offsets feed the near field
     const int ek = fp32 ? EXP_F32 : dfe ? EXP_DF : EXP_F64;
     const size_t esz = fp32 ? 4 : 8;                   // expansion storage: float, double or double-float
@@ -291,9 +344,11 @@ sfmm_status solve(sfmm_plan_s* P, const double* src, const void* q, int64_t N, c
                                     P->soff.as<float4>(), s)))
             return cuda_fail(P, e, "offsets");
     }
-    if ((e = launch_p2m(T, P->leaves_src.as<int>(), P->n_leaves, P->src4.as<double4_32a>(), P->soff.as<float4>(),
-                        P->logtab.as<float4>(), P->mpole.p, p, ek, s)))
-        return cuda_fail(P, e, "P2M");
+    if (adj) e = launch_p2m_adj(T, P->leaves_src.as<int>(), P->n_leaves, P->src4.as<double4_32a>(),
+                                P->dip4.as<double4_32a>(), P->mpole.as<double>(), p, s);
+    else e = launch_p2m(T, P->leaves_src.as<int>(), P->n_leaves, P->src4.as<double4_32a>(), P->soff.as<float4>(),
+                        P->logtab.as<float4>(), P->mpole.p, p, ek, s);
+    if (e) return cuda_fail(P, e, "P2M");
     const int depth = (int)P->level_start.size() - 2;
     for (int l = depth - 1; l >= 0; --l)
         if ((e = launch_m2m(T, P->level_start[l], P->level_start[l + 1], p, P->tables.as<double>(), P->m2m_geo.p,
@@ -347,7 +402,11 @@ sfmm_status solve(sfmm_plan_s* P, const double* src, const void* q, int64_t N, c
                                     P->toff.as<float4>(), p2p_t, p2p_s, P->n_p2p, P->dc.as<float4>(), s)))
             return cuda_fail(P, e, "offsets");
     }
-    if (fp32) e = launch_eval32(T, P->leaves_tgt.as<int>(), P->n_leaves_tgt, P->soff.as<float4>(),
+    if (adj) e = launch_eval_adj(T, P->leaves_tgt.as<int>(), P->n_leaves_tgt, P->src4.as<double4_32a>(),
+                                 P->dip4.as<double4_32a>(), P->tgt4.as<double4_32a>(), tperm, P->p2p_off.as<int64_t>(),
+                                 p2p_s, P->local.as<double>(), P->mpole.as<double>(), p, P->opt.zero_mean, adj->w,
+                                 adj->w_f32, psi, adj->grad3, s);
+    else if (fp32) e = launch_eval32(T, P->leaves_tgt.as<int>(), P->n_leaves_tgt, P->soff.as<float4>(),
                                 P->toff.as<float4>(), P->dc.as<float4>(), P->tgt4.as<double4_32a>(), tperm, P->p2p_off.as<int64_t>(), p2p_s,
                                 P->local.as<float>(), P->mpole.as<float>(), p, P->opt.zero_mean, psi, alpha, s);
     else if (dfe) e = launch_eval_df(T, P->leaves_tgt.as<int>(), P->n_leaves_tgt, P->soff.as<float4>(),
@@ -511,6 +570,32 @@ sfmm_status sfmm_deflection(sfmm_plan_t plan, const double* src_xyz, const void*
     return solve(plan, src_xyz, q, N, tgt_xyz, M, psi, alpha);
 }
 
+sfmm_status sfmm_adjoint(sfmm_plan_t plan, const double* src_xyz, const void* q, int64_t N, const double* tgt_xyz,
+                         int64_t M, const double* g_psi, const double* g_alpha, double* grad_q, double* grad_src)
+{
+    sfmm_status st = check_args(plan, src_xyz, q, N, tgt_xyz, M);
+    if (st != SFMM_OK) return st;
+    if (N > 0 && !grad_q && !grad_src) return fail(plan, SFMM_EINVAL, "grad_q or grad_src must be non-NULL");
+    if (N == 0) return SFMM_OK;
+    cudaStream_t s = plan->stream;
+    cudaError_t e;
+    if (M == 0 || (!g_psi && !g_alpha)) {           // no loss terms: zero gradients
+        if (grad_q && (e = cudaMemsetAsync(grad_q, 0, (size_t)N * 8, s))) return cuda_fail(plan, e, "memset");
+        if (grad_src && (e = cudaMemsetAsync(grad_src, 0, (size_t)N * 24, s))) return cuda_fail(plan, e, "memset");
+        if ((e = cudaStreamSynchronize(s))) return cuda_fail(plan, e, "sync");
+        return SFMM_OK;
+    }
+    if ((e = ensure(plan->adj_h, (size_t)M * 8)) || (e = ensure(plan->adj_g, (size_t)M * 24)))
+        return cuda_fail(plan, e, "alloc adjoint sources");
+    k_adjoint_prep<<<grid_for(M), 256, 0, s>>>(tgt_xyz, M, g_psi, g_alpha, plan->adj_h.as<double>(),
+                                               plan->adj_g.as<double>());
+    count_launch();
+    if ((e = cudaGetLastError())) return cuda_fail(plan, e, "adjoint sources");
+    // the forward targets carry the charges and dipoles; the field is evaluated at the forward sources
+    AdjIO adj{plan->adj_g.as<double>(), q, plan->opt.q_f32, grad_src};
+    return solve(plan, tgt_xyz, plan->adj_h.p, M, src_xyz, N, grad_q, nullptr, &adj);
+}
+
 sfmm_status sfmm_deflection_host(sfmm_plan_t plan, const double* src_xyz, const void* q, int64_t N,
                                  const double* tgt_xyz, int64_t M, double* psi, double* alpha)
 {
@@ -556,7 +641,7 @@ void sfmm_destroy(sfmm_plan_t plan)
                   &plan->p2p_t2, &plan->p2p_s2, &plan->m2l_off, &plan->p2p_off, &plan->leaves_src,
                   &plan->leaves_tgt, &plan->m2l_geo, &plan->m2m_geo, &plan->l2l_geo, &plan->soff,
                   &plan->toff, &plan->dc, &plan->leftover, &plan->geom32, &plan->macn, &plan->logtab,
-                  &plan->ttmp};
+                  &plan->ttmp, &plan->dip4, &plan->adj_h, &plan->adj_g};
     if (plan->aux) cudaStreamSynchronize(plan->aux);
     for (Buf* b : all) release(*b);
     if (plan->ev_fork) cudaEventDestroy(plan->ev_fork);

@@ -149,6 +149,124 @@ __global__ void __launch_bounds__(128) k_eval(EvalArgs A)
     }
 }
 
+// ------------------------------------------------------------------------
+// Adjoint evaluation (FP64): the field of charges h_j (src.w) and tangent
+// dipoles g_j (dip) at the sources, at the targets: Phi = psi-like sum plus
+//   sum_j g_j . (y_j - x) / (2 pi r^2)                        (dipole potential)
+// and its covariant gradient, the L2P part as in k_eval plus, per near pair,
+//   P_x [ h_j (x - y_j) / (2 pi r^2) + ( -g_j / r^2 - 2 (g_j . (y_j - x)) (x - y_j) / r^4 ) / (2 pi) ].
+// Writes Phi (if phi) and w_i times the gradient 3-vector (if grad3), at the
+// caller's index of each target; w is float32 when w_f32.
+struct EvalAdjArgs {
+    EvalArgs E;
+    const double4_32a* dip;   // key-sorted tangent dipoles (gx, gy, gz, -)
+    const void* w;
+    int w_f32;
+    double* grad3;
+};
+
+__global__ void __launch_bounds__(128) k_eval_adj(EvalAdjArgs AA)
+{
+    const EvalArgs& A = AA.E;
+    const int lane = threadIdx.x & 31;
+    const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    double shift = 0.0;
+    if (A.zero_mean)
+        for (int b = 0; b < 12; ++b) shift += A.base_mpole[(size_t)b * EXP_STRIDE + 1];
+    for (int64_t w = warp0; w < A.n_leaves; w += nwarps) {
+        const int leaf = A.leaves[w];
+        const int tf = A.T.tfirst[leaf], tc = A.T.tcount[leaf];
+        const double* g = A.T.geom + (size_t)leaf * GEOM_STRIDE;
+        const double* L = A.local + (size_t)leaf * EXP_STRIDE;
+        const int64_t nb0 = A.p2p_off[leaf], nb1 = A.p2p_off[leaf + 1];
+        for (int tb = 0, tpw = 0; tb < tc; tb += tpw) {
+            tpw = min(32, 1 << (31 - __clz(tc - tb)));
+            const int lpt = 32 / tpw;
+            const int slot = lane / lpt, sub = lane % lpt;
+            const int ti = tb + slot;
+            const double4_32a x = A.tgt[tf + ti];
+            double sl = 0.0, sx = 0.0, sy = 0.0, sz = 0.0, sq = 0.0;     // charges (as k_eval)
+            double sd = 0.0, vx = 0.0, vy = 0.0, vz = 0.0;               // dipoles
+            for (int64_t k = nb0; k < nb1; ++k) {
+                const int sleaf = (int)A.p2p_src[k];
+                const int f = A.T.first[sleaf], n = A.T.count[sleaf];
+                for (int j = f + sub; j < f + n; j += lpt) {
+                    const double4_32a y = A.src[j];
+                    const double4_32a gd = AA.dip[j];
+                    const double dx = x.x - y.x, dy = x.y - y.y, dz = x.z - y.z;
+                    const double d2 = dx * dx + dy * dy + dz * dz;
+                    if (d2 > 0.0) {
+                        const double inv = 1.0 / d2;
+                        const double wq = y.w * inv;
+                        sx += wq * dx;
+                        sy += wq * dy;
+                        sz += wq * dz;
+                        sq += y.w;
+                        if (A.want_psi) sl += y.w * log(d2);
+                        const double ge = -(gd.x * dx + gd.y * dy + gd.z * dz);   // g . (y - x)
+                        sd += ge * inv;
+                        const double c2 = -2.0 * ge * inv * inv;
+                        vx += c2 * dx - gd.x * inv;
+                        vy += c2 * dy - gd.y * inv;
+                        vz += c2 * dz - gd.z * inv;
+                    }
+                }
+            }
+            sx = group_sum(sx, lpt);
+            sy = group_sum(sy, lpt);
+            sz = group_sum(sz, lpt);
+            sq = group_sum(sq, lpt);
+            sd = group_sum(sd, lpt);
+            vx = group_sum(vx, lpt);
+            vy = group_sum(vy, lpt);
+            vz = group_sum(vz, lpt);
+            if (A.want_psi) sl = group_sum(sl, lpt);
+            if (sub != 0) continue;
+            const double Dx = x.x - g[0], Dy = x.y - g[1], Dz = x.z - g[2];
+            const double D2 = Dx * Dx + Dy * Dy + Dz * Dz;
+            const double den = 2.0 - 0.5 * D2;
+            const double wu = (Dx * g[3] + Dy * g[4] + Dz * g[5]) / den;
+            const double wv = (Dx * g[6] + Dy * g[7] + Dz * g[8]) / den;
+            const double inv_r = 1.0 / g[10];
+            const cd om = mk(wu * inv_r, wv * inv_r);
+            cd f = mk(0.0, 0.0), fd = mk(0.0, 0.0);
+            for (int l = A.p; l >= 1; --l) {
+                const cd a = mk(L[2 * l], L[2 * l + 1]);
+                f = cadd(cmul(f, om), a);
+                fd = cadd(cmul(fd, om), cscale(a, (double)l));
+            }
+            const cd F = cmul(f, om);
+            const cd Fp = cscale(fd, inv_r);
+            const double C = L[0], Q = L[1];
+            const double w2 = wu * wu + wv * wv;
+            const double au = (1.0 + w2) * Fp.x - Q * wu;
+            const double av = -(1.0 + w2) * Fp.y - Q * wv;
+            const double cxx = g[0] + x.x, cyy = g[1] + x.y, czz = g[2] + x.z;
+            double a3x = au * (g[3] - wu * cxx) + av * (g[6] - wv * cxx);
+            double a3y = au * (g[4] - wu * cyy) + av * (g[7] - wv * cyy);
+            double a3z = au * (g[5] - wu * czz) + av * (g[8] - wv * czz);
+            // near field: charges (projected form of k_eval) + dipoles projected by P_x
+            const double xv = x.x * vx + x.y * vy + x.z * vz;
+            a3x += INV2PI * (sx - 0.5 * x.x * sq + vx - xv * x.x);
+            a3y += INV2PI * (sy - 0.5 * x.y * sq + vy - xv * x.y);
+            a3z += INV2PI * (sz - 0.5 * x.z * sq + vz - xv * x.z);
+            const uint32_t o = A.tperm[tf + ti];
+            if (AA.grad3) {
+                const double wt = AA.w_f32 ? (double)static_cast<const float*>(AA.w)[o]
+                                           : static_cast<const double*>(AA.w)[o];
+                AA.grad3[3 * (size_t)o] = wt * a3x;
+                AA.grad3[3 * (size_t)o + 1] = wt * a3y;
+                AA.grad3[3 * (size_t)o + 2] = wt * a3z;
+            }
+            if (A.want_psi) {
+                const double psi_e = C + Q * (LOG2 + log1p(-0.25 * D2)) + 2.0 * F.x;
+                A.psi[o] = psi_e + INV4PI * (sl - LOG4 * sq) + INV2PI * sd + shift;
+            }
+        }
+    }
+}
+
 __global__ void k_count_pairs(TreeView T, const int* __restrict__ leaves, int64_t n, const int64_t* __restrict__ off,
                               const uint32_t* __restrict__ src, unsigned long long* __restrict__ out)
 {
@@ -815,6 +933,39 @@ cudaError_t launch_eval(const TreeView& T, const int* leaves, int64_t n_leaves, 
     int64_t blocks = (n_leaves + 3) / 4;
     if (blocks > 152 * 64) blocks = 152 * 64;
     k_eval<<<(unsigned)blocks, 128, 0, s>>>(A); count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_eval_adj(const TreeView& T, const int* leaves, int64_t n_leaves, const double4_32a* src,
+                            const double4_32a* dip, const double4_32a* tgt, const uint32_t* tperm,
+                            const int64_t* p2p_off, const uint32_t* p2p_src, const double* local, const double* mpole,
+                            int p, int zero_mean, const void* w, int w_f32, double* phi, double* grad3, cudaStream_t s)
+{
+    if (n_leaves == 0) return cudaSuccess;
+    EvalAdjArgs AA;
+    EvalArgs& A = AA.E;
+    A.T = T;
+    A.leaves = leaves;
+    A.n_leaves = n_leaves;
+    A.src = src;
+    A.tgt = tgt;
+    A.tperm = tperm;
+    A.p2p_off = p2p_off;
+    A.p2p_src = p2p_src;
+    A.local = local;
+    A.base_mpole = mpole;
+    A.p = p;
+    A.want_psi = phi != nullptr;
+    A.zero_mean = zero_mean;
+    A.psi = phi;
+    A.alpha = nullptr;
+    AA.dip = dip;
+    AA.w = w;
+    AA.w_f32 = w_f32;
+    AA.grad3 = grad3;
+    int64_t blocks = (n_leaves + 3) / 4;
+    if (blocks > 152 * 64) blocks = 152 * 64;
+    k_eval_adj<<<(unsigned)blocks, 128, 0, s>>>(AA); count_launch();
     return cudaGetLastError();
 }
 

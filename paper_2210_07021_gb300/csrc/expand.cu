@@ -568,6 +568,68 @@ __global__ void k_p2m(TreeView T, const int* __restrict__ leaves, int64_t n_leav
     }
 }
 
+// Adjoint (FP64): charges h and tangent dipoles g at the sources.  A dipole's
+// potential g . grad_x G(x, y) is the derivative of the point-mass potential
+// along g, so its multipole is the derivative of Lemma 1 along g: with
+// D = x - c, 1 + x.c = 2 - |D|^2/2 and z = (D.e_theta + i D.e_phi)/(1 + x.c),
+//   dz = [(g.e_theta + i g.e_phi) - z (g.c)] / (1 + x.c),
+//   dA_l = -(1/4pi) z^(l-1) dz,   dC = (1/4pi) (g.c)/(1 + x.c),   dQ = 0
+// (d log cos^2(theta/2) = d log((1 + x.c)/2); x.g = 0).  Stored scaled like
+// Lemma 1: A_l / r^l.
+template <int P>
+__global__ void k_p2m_adj(TreeView T, const int* __restrict__ leaves, int64_t n_leaves,
+                          const double4_32a* __restrict__ src, const double4_32a* __restrict__ dip,
+                          double* __restrict__ mpole)
+{
+    for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < n_leaves; w += (int64_t)gridDim.x * blockDim.x) {
+        const int node = leaves[w];
+        const double* g = T.geom + (size_t)node * GEOM_STRIDE;
+        const double cx_ = g[0], cy = g[1], cz = g[2];
+        const double inv_r = 1.0 / g[10];
+        cd A[P], B[P];
+#pragma unroll
+        for (int l = 0; l < P; ++l) { A[l] = mk(0.0, 0.0); B[l] = mk(0.0, 0.0); }
+        double Csum = 0.0, Qsum = 0.0, Cdip = 0.0;
+        const int f = T.first[node], n = T.count[node];
+        for (int j = f; j < f + n; ++j) {
+            const double4_32a y = src[j];
+            const double4_32a gd = dip[j];
+            const double dx = y.x - cx_, dy = y.y - cy, dz = y.z - cz;
+            const double d2 = dx * dx + dy * dy + dz * dz;
+            const double inv = 1.0 / (2.0 - 0.5 * d2);          // 1/(1 + x.c)
+            const double zr = (dx * g[3] + dy * g[4] + dz * g[5]) * inv;
+            const double zi = (dx * g[6] + dy * g[7] + dz * g[8]) * inv;
+            const double gc = gd.x * cx_ + gd.y * cy + gd.z * cz;
+            const double dzr = ((gd.x * g[3] + gd.y * g[4] + gd.z * g[5]) - zr * gc) * inv * inv_r;
+            const double dzi = ((gd.x * g[6] + gd.y * g[7] + gd.z * g[8]) - zi * gc) * inv * inv_r;
+            const cd zs = mk(zr * inv_r, zi * inv_r);
+            const double h = y.w;
+            Qsum += h;
+            Csum += h * log1p(-0.25 * d2);
+            Cdip += gc * inv;
+            cd zp = mk(h, 0.0), zq = mk(dzr, dzi);
+#pragma unroll
+            for (int l = 0; l < P; ++l) {
+                zp = cmul(zp, zs);
+                A[l] = cadd(A[l], zp);          // h zs^(l+1)
+                B[l] = cadd(B[l], zq);          // zs^l dzs
+                zq = cmul(zq, zs);
+            }
+        }
+        double* e = mpole + (size_t)node * EXP_STRIDE;
+        const double Q = INV4PI * Qsum;
+        e[0] = INV4PI * (Csum + Cdip) - Q * LOG2;
+        e[1] = Q;
+#pragma unroll
+        for (int l = 0; l < P; ++l) {
+            const double s = 1.0 / (double)(l + 1);
+            e[2 + 2 * l] = -INV4PI * (s * A[l].x + B[l].x);
+            e[3 + 2 * l] = -INV4PI * (s * A[l].y + B[l].y);
+        }
+        for (int l = P; l < PMAX; ++l) { e[2 + 2 * l] = 0.0; e[3 + 2 * l] = 0.0; }
+    }
+}
+
 // Double-float (1e-10 mixed path): from each source's (hi, lo) offset to its
 // leaf centre, z^l by repeated double-float products, log(1 - d^2/4) = 2 log
 // cos(theta/2) by the table-driven double-float logarithm (tab: as in the
@@ -906,6 +968,24 @@ cudaError_t launch_p2m(const TreeView& T, const int* leaves, int64_t n_leaves, c
         default: return cudaErrorInvalidValue;
     }
 #undef P2M_CASE
+    return cudaGetLastError();
+}
+
+cudaError_t launch_p2m_adj(const TreeView& T, const int* leaves, int64_t n_leaves, const double4_32a* src,
+                           const double4_32a* dip, double* mpole, int p, cudaStream_t s)
+{
+    if (n_leaves == 0) return cudaSuccess;
+    const unsigned g = grid_for(n_leaves, 128);
+#define P2MA_CASE(PP)                                                                     \
+    case PP:                                                                              \
+        k_p2m_adj<PP><<<g, 128, 0, s>>>(T, leaves, n_leaves, src, dip, mpole);            \
+        count_launch();                                                                   \
+        break;
+    switch ((p + 3) / 4 * 4) {
+        P2MA_CASE(4) P2MA_CASE(8) P2MA_CASE(12) P2MA_CASE(16) P2MA_CASE(20) P2MA_CASE(24) P2MA_CASE(28) P2MA_CASE(32)
+        default: return cudaErrorInvalidValue;
+    }
+#undef P2MA_CASE
     return cudaGetLastError();
 }
 

@@ -18,6 +18,7 @@ SFMM_FP64, SFMM_MIXED, SFMM_MIXED_DF = 0, 1, 2
  ARR_NODE_GEOM, ARR_MULTIPOLE, ARR_LOCAL, ARR_M2L, ARR_P2P, ARR_TGT_KEYS, ARR_NODE_TRANGE) = range(14)
 
 EXPORTS = ["sfmm_default_options", "sfmm_plan", "sfmm_potential", "sfmm_deflection", "sfmm_deflection_host",
+           "sfmm_adjoint",
            "sfmm_destroy", "sfmm_last_error", "sfmm_order", "sfmm_get_stats", "sfmm_set_timing",
            "sfmm_debug_copy", "sfmm_keys", "sfmm_sort_keys_static"]
 STATIC_SORT_MAX_N = 1 << 18
@@ -69,6 +70,8 @@ def load(build_if_missing=True):
     L.sfmm_deflection.restype = ci
     L.sfmm_deflection_host.argtypes = [vp, vp, vp, i64, vp, i64, vp, vp]
     L.sfmm_deflection_host.restype = ci
+    L.sfmm_adjoint.argtypes = [vp, vp, vp, i64, vp, i64, vp, vp, vp, vp]
+    L.sfmm_adjoint.restype = ci
     L.sfmm_destroy.argtypes = [vp]
     L.sfmm_destroy.restype = None
     L.sfmm_last_error.argtypes = [vp]
@@ -191,6 +194,21 @@ class Plan:
                                     _dptr(alpha, torch.float64, 2, "alpha"))
         _check(st, self._h)
         return (psi if with_psi else None), alpha
+
+    def adjoint(self, src, q, tgt, g_psi=None, g_alpha=None, want_q=True, want_src=True):
+        """(dL/dq [N] or None, dL/dy [N, 3] or None) for a loss of this plan's
+        deflection outputs, given dL/dpsi [M] and/or dL/dalpha [M, 2] (device
+        tensors; FP64 adjoint sFMM, see sfmm_adjoint)."""
+        import torch
+        N = src.shape[0]
+        gq = torch.empty(N, dtype=torch.float64, device=src.device) if want_q else None
+        gs = torch.empty((N, 3), dtype=torch.float64, device=src.device) if want_src else None
+        st = load().sfmm_adjoint(self._h, _dptr(src, torch.float64, 3, "src"), _dptr(q, self._qdtype(), None, "q"),
+                                 N, _dptr(tgt, torch.float64, 3, "tgt"), tgt.shape[0],
+                                 _dptr(g_psi, torch.float64, None, "g_psi"), _dptr(g_alpha, torch.float64, 2, "g_alpha"),
+                                 _dptr(gq, torch.float64, None, "grad_q"), _dptr(gs, torch.float64, 3, "grad_src"))
+        _check(st, self._h)
+        return gq, gs
 
     def deflection_host(self, src, q, tgt, with_psi=True, psi=None, alpha=None):
         """Host-array variant (numpy in, numpy out); copies happen inside the call."""

@@ -1,0 +1,119 @@
+"""GPU parity of the adjoint sFMM (sfmm_adjoint) and its autograd wrapper
+against the oracle's adjoint (pinned by finite differences of the forward
+oracle in test_oracle_adjoint.py).  Stated error 1e-10, norm-wise."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle.direct import adjoint as oracle_adjoint, direct_sum
+from paper_2210_07021_gb300 import autograd as sfa
+from paper_2210_07021_gb300 import sfmm, workloads
+from conftest import unit
+
+TOL = 1e-10
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def dev(a, dtype=torch.float64):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=dtype, device="cuda")
+
+
+def run(src, q, tgt, g_psi, g_alpha, p=32, leaf=32, **kw):
+    plan = sfmm.Plan(p=p, leaf_size=leaf, **kw)
+    qd = torch.float32 if kw.get("q_f32") else torch.float64
+    gq, gs = plan.adjoint(dev(src), dev(q, qd), dev(tgt), g_psi=None if g_psi is None else dev(g_psi),
+                          g_alpha=None if g_alpha is None else dev(g_alpha))
+    torch.cuda.synchronize()
+    return gq.cpu().numpy(), gs.cpu().numpy()
+
+
+@pytest.mark.parametrize("which", ["both", "alpha", "psi"])
+def test_adjoint_random_sky(which):
+    rng = np.random.default_rng(11)
+    src = unit(rng.normal(size=(3000, 3)))
+    tgt = unit(rng.normal(size=(2500, 3)))
+    q = rng.lognormal(0, 0.5, 3000)
+    g_psi = rng.normal(size=2500) if which in ("both", "psi") else None
+    g_alpha = rng.normal(size=(2500, 2)) if which in ("both", "alpha") else None
+    gq, gs = run(src, q, tgt, g_psi, g_alpha)
+    rq, rs = oracle_adjoint(src, q, tgt, g_alpha, g_psi)
+    assert rel(gq, rq) < TOL and rel(gs, rs) < TOL, (rel(gq, rq), rel(gs, rs))
+    assert np.abs(np.sum(gs * src, 1)).max() < 1e-12 * np.abs(gs).max()       # tangent
+
+
+def test_adjoint_clustered_near_field_heavy_and_mixed_plan():
+    """Clustered sources and targets, small leaves; a plan made for the mixed
+    path still runs its adjoint in FP64."""
+    rng = np.random.default_rng(12)
+    clumps = workloads.clump_set(rng, 20)
+    src = workloads.clustered(rng, 40000, 20, clumps=clumps)
+    tgt = workloads.clustered(rng, 30001, 20, clumps=clumps)
+    q = rng.lognormal(0, 0.5, 40000)
+    g_psi = rng.normal(size=30001)
+    g_alpha = rng.normal(size=(30001, 2))
+    for prec in (sfmm.SFMM_FP64, sfmm.SFMM_MIXED):
+        gq, gs = run(src, q, tgt, g_psi, g_alpha, leaf=16, precision=prec)
+        idx = workloads.subsample(40000, 600, 12)
+        rq, rs = oracle_adjoint(src[idx], q[idx], tgt, g_alpha, g_psi)
+        assert rel(gq[idx], rq) < TOL and rel(gs[idx], rs) < TOL, (prec, rel(gq[idx], rq), rel(gs[idx], rs))
+
+
+def test_adjoint_self_targets_zero_mean_f32_masses():
+    """Targets equal to the sources (coincident pairs skipped, as in the
+    forward sum), the zero-mean constant, float32 masses."""
+    rng = np.random.default_rng(13)
+    src = unit(rng.normal(size=(2048, 3)))
+    q = rng.lognormal(0, 0.5, 2048).astype(np.float32)
+    g_psi = rng.normal(size=2048)
+    g_alpha = rng.normal(size=(2048, 2))
+    gq, gs = run(src, q, src, g_psi, g_alpha, q_f32=True, zero_mean=True)
+    rq, rs = oracle_adjoint(src, q.astype(np.float64), src, g_alpha, g_psi, zero_mean=True)
+    assert rel(gq, rq) < TOL and rel(gs, rs) < TOL, (rel(gq, rq), rel(gs, rs))
+
+
+def test_adjoint_edges():
+    rng = np.random.default_rng(14)
+    src = unit(rng.normal(size=(100, 3)))
+    q = np.ones(100)
+    # no targets, or no loss terms: zero gradients
+    gq, gs = run(src, q, np.zeros((0, 3)), None, None)
+    assert np.all(gq == 0) and np.all(gs == 0)
+    tgt = unit(rng.normal(size=(10, 3)))
+    gq, gs = run(src, q, tgt, None, None)
+    assert np.all(gq == 0) and np.all(gs == 0)
+    # a target at a pole: its dipole uses the phi = 0 basis
+    tgt = np.array([[0, 0, 1.0], [0, 0, -1.0], [1.0, 0, 0]])
+    g_alpha = rng.normal(size=(3, 2))
+    gq, gs = run(src, q, tgt, None, g_alpha)
+    rq, rs = oracle_adjoint(src, q, tgt, g_alpha, None)
+    assert rel(gq, rq) < TOL and rel(gs, rs) < TOL
+
+
+def test_autograd_loss_matches_oracle_gradient():
+    """L = sum w |alpha - a_ref|^2 + sum v (psi - p_ref)^2 through torch autograd."""
+    rng = np.random.default_rng(15)
+    src = unit(rng.normal(size=(4096, 3)))
+    tgt = unit(rng.normal(size=(3000, 3)))
+    q = rng.lognormal(0, 0.5, 4096)
+    w = rng.uniform(0.5, 1.5, 3000)
+    v = rng.uniform(0.5, 1.5, 3000)
+    a_ref = rng.normal(size=(3000, 2))
+    p_ref = rng.normal(size=3000)
+    plan = sfmm.Plan(p=32, leaf_size=32)
+    ts = dev(src).requires_grad_(True)
+    tq = dev(q).requires_grad_(True)
+    psi, alpha = sfa.deflection(ts, tq, dev(tgt), plan)
+    L = (dev(w)[:, None] * (alpha - dev(a_ref)) ** 2).sum() + (dev(v) * (psi - dev(p_ref)) ** 2).sum()
+    L.backward()
+    r = direct_sum(src, q, tgt)
+    rq, rs = oracle_adjoint(src, q, tgt, 2 * w[:, None] * (r["alpha"] - a_ref), 2 * v * (r["psi"] - p_ref))
+    assert rel(tq.grad.cpu().numpy(), rq) < TOL and rel(ts.grad.cpu().numpy(), rs) < TOL
+    with pytest.raises(NotImplementedError):
+        tt = dev(tgt).requires_grad_(True)
+        psi, alpha = sfa.deflection(dev(src), dev(q), tt, plan)
+        alpha.sum().backward()
