@@ -61,6 +61,7 @@ def parse():
     ap.add_argument("--check", type=int, default=200, help="targets checked against the oracle")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the oracle CPU baseline")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the gradient (adjoint) measurement")
     return ap.parse_args()
 
 
@@ -134,6 +135,58 @@ def make_workload(args, rank):
     from paper_2210_07021_gb300.shard import rank_config_index
     d = workloads.clustered_pair(n=args.n, n_clumps=args.clumps, config_index=rank_config_index(3, rank))
     return d
+
+
+def run_adjoint(args, dev, clock_sampler):
+    """One training step of the gradient workload: the 1e-10 forward solve, the
+    loss gradient dL/dalpha = 2 w (alpha - alpha_ref) on the device, and the
+    FP64 adjoint sFMM (dL/dq, dL/dy); CUDA events around each part."""
+    import torch
+    from paper_2210_07021_gb300 import sfmm, workloads
+    d = workloads.loss_sky()
+    N, M = d["src"].shape[0], d["tgt"].shape[0]
+    src = torch.as_tensor(d["src"], device=dev)
+    q = torch.as_tensor(d["q"], device=dev)
+    tgt = torch.as_tensor(d["tgt"], device=dev)
+    w = torch.as_tensor(d["w"], device=dev)
+    plan = sfmm.Plan(p=26, leaf_size=64, c_s=2.0, c_t=0.45, precision=sfmm.SFMM_MIXED_DF, n_max=max(N, M), m_max=max(N, M))
+    psi, alpha = plan.deflection(src, q, tgt)
+    s = float(torch.sqrt((alpha ** 2).mean()))
+    a_ref = s * torch.as_tensor(d["xi"], device=dev)
+
+    def step():
+        _, al = plan.deflection(src, q, tgt, with_psi=False)
+        ev_mid.record(torch.cuda.current_stream())
+        g_alpha = (2.0 * w[:, None] * (al - a_ref)).contiguous()
+        gq, gs = plan.adjoint(src, q, tgt, g_alpha=g_alpha)
+        return g_alpha, gq, gs
+
+    ev_mid = torch.cuda.Event(enable_timing=True)
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    t_f, t_b = [], []
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with clock_sampler as clk:
+        for _ in range(args.steps):
+            ev0.record(torch.cuda.current_stream())
+            g_alpha, gq, gs = step()
+            ev1.record(torch.cuda.current_stream())
+            torch.cuda.synchronize()
+            t_f.append(ev0.elapsed_time(ev_mid))
+            t_b.append(ev_mid.elapsed_time(ev1))
+    from oracle.direct import adjoint as oracle_adjoint
+    idx = workloads.subsample(N, args.check, 5, stream=9)
+    rq, rs = oracle_adjoint(d["src"][idx], d["q"][idx], d["tgt"], g_alpha.cpu().numpy(), None)
+    plan.close()
+    ms = float(np.mean(t_f) + np.mean(t_b))
+    return {"workload": d["workload"], "N": N, "M": M, "forward": "mixed_df (stated 1e-10), p=26, m=64, c_t=0.45",
+            "backward": "adjoint sFMM, FP64, same p and tree settings", "steps": args.steps,
+            "ms_per_step": ms, "ms_forward": float(np.mean(t_f)), "ms_backward": float(np.mean(t_b)),
+            "value": (N + M) * 1e-3 / ms, "unit": "Mpts/s (sources + targets per forward+backward step)",
+            "error_vs_oracle": {"dq_rel": rel(gq.cpu().numpy()[idx], rq), "dy_rel": rel(gs.cpu().numpy()[idx], rs),
+                                "sample": int(idx.size), "norm": "l2 over the sampled sources (relative)"},
+            "clocks": clk.summary()}
 
 
 def oracle_rate(src, q, tgt, budget_s, seed_idx):
@@ -286,6 +339,9 @@ def run_sfmm(args):
             dist.barrier()
         return
     head = results[wanted[0][0]]
+    adj = None
+    if ws == 1 and not args.no_adjoint:
+        adj = run_adjoint(args, dev, ClockSampler(local))
     cpu = None
     if ws == 1:
         k, t, cores = oracle_rate(d["src"], d["q"], d["tgt"], args.cpu_seconds, 3)
@@ -326,7 +382,7 @@ def run_sfmm(args):
                        "l2": "inputs larger than L2 (384 MB of positions each), no flush"},
             "error_vs_oracle": head.get("error_vs_oracle"), "roofline": modes[head["precision"]]["roofline"],
             "cpu_baseline": cpu, "e2e": head.get("e2e"), "gpu_launches": head["gpu_launches"],
-            "phase_ms": head["phase_ms"], "clocks": head["clocks"],
+            "phase_ms": head["phase_ms"], "clocks": head["clocks"], "adjoint": adj,
             "modes": {k: {kk: vv for kk, vv in v.items() if kk not in ("phase_ms",)} for k, v in modes.items()}}
     if "fp64" in results and head["precision"] != "fp64":
         line["speedup_vs_fp64"] = head["value"] / results["fp64"]["value"]

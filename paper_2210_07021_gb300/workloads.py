@@ -152,6 +152,23 @@ def clustered_sky(n=1_000_000, n_clumps=2000, nside=512, config_index=2):
                 workload=f"clustered N={n} ({n_clumps} clumps) -> M={tgt.shape[0]} grid (Nside={nside})")
 
 
+def loss_sky(n=1_000_000, n_clumps=2000, nside=256, config_index=5):
+    """The gradient workload: N equal masses on a clustered sky, targets on the
+    N_side grid, per-target loss weights w ~ U[0.5, 1.5] and a reference
+    direction xi ~ N(0, I_2) for the reference deflection alpha_ref = s xi
+    (the caller picks the scale s, e.g. the RMS of alpha)."""
+    rng = rng_for(config_index)
+    src = clustered(rng, n, n_clumps)
+    q = np.full(n, 4.0 * np.pi / n)
+    tgt = healpix_ring_centres(nside)
+    r2 = rng_for(config_index, 1)
+    w = r2.uniform(0.5, 1.5, tgt.shape[0])
+    xi = r2.standard_normal((tgt.shape[0], 2))
+    return dict(src=src, q=q, tgt=tgt, w=w, xi=xi,
+                workload=f"clustered sky N={n} ({n_clumps} clumps), M={tgt.shape[0]} N_side={nside} pixel centres, "
+                         "loss sum w |alpha - s xi|^2")
+
+
 def clustered_pair(n=16_000_000, m=None, n_clumps=20_000, config_index=3, q_dtype=np.float32):
     """N sources and M targets drawn independently from the same clustered
     mix (the same clumps); masses equal, stored as float32 by default."""
