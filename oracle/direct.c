@@ -143,6 +143,47 @@ int64_t oracle_dipole(const double* x, const double* h, const double* g, int64_t
     return skipped;
 }
 
+/* Covariant Hessian of psi = sum_j q_j G(x, y_j) at the targets, in the
+ * orthonormal frame (e_theta, e_phi) (Sec. 2.2: H11 = d^2 psi/dtheta^2,
+ * H12 = d/dtheta((1/sin theta) dpsi/dphi), H22 = (1/sin^2 theta) d^2 psi/dphi^2
+ * + cot theta dpsi/dtheta).  For G = (1/4pi) log(1 - x.y) + const, the ambient
+ * Hessian is -y y^T/(4pi (1 - x.y)^2) and the sphere adds -(x.grad G) P, so
+ *   H_ab = -(e_a.d)(e_b.d)/(pi d^4) + (1 - d^2/2) delta_ab/(2 pi d^2),
+ * d = x - y (e_a.y = -e_a.d because e_a is tangent at x; 1 - x.y = d^2/2).
+ * hess[M][3] = (H_theta_theta, H_phi_phi, H_theta_phi).  Pairs with d^2 == 0
+ * are skipped.  Returns the skipped pairs. */
+int64_t oracle_hessian(const double* src, const double* q, int64_t N,
+                       const double* tgt, int64_t M, double* hess)
+{
+    const double invpi = 1.0 / M_PI;
+    int64_t skipped = 0;
+#pragma omp parallel for schedule(dynamic, 1) reduction(+:skipped)
+    for (int64_t i = 0; i < M; ++i) {
+        const double x0 = tgt[3 * i], x1 = tgt[3 * i + 1], x2 = tgt[3 * i + 2];
+        const double rho = sqrt(x0 * x0 + x1 * x1);
+        double cp = 1.0, sp_ = 0.0;
+        if (rho > 0.0) { cp = x0 / rho; sp_ = x1 / rho; }
+        const double t0 = x2 * cp, t1 = x2 * sp_, t2 = -rho;      /* e_theta */
+        const double f0 = -sp_, f1 = cp;                           /* e_phi */
+        nsum htt = {0, 0}, hff = {0, 0}, htf = {0, 0};
+        for (int64_t j = 0; j < N; ++j) {
+            const double e0 = x0 - src[3 * j], e1 = x1 - src[3 * j + 1], e2 = x2 - src[3 * j + 2];
+            const double d2 = e0 * e0 + e1 * e1 + e2 * e2;
+            if (d2 == 0.0) { ++skipped; continue; }
+            const double dt = t0 * e0 + t1 * e1 + t2 * e2, df = f0 * e0 + f1 * e1;
+            const double iso = q[j] * (1.0 - 0.5 * d2) * 0.5 * invpi / d2;
+            const double w4 = q[j] * invpi / (d2 * d2);
+            nadd(&htt, iso - w4 * dt * dt);
+            nadd(&hff, iso - w4 * df * df);
+            nadd(&htf, -w4 * dt * df);
+        }
+        hess[3 * i] = nval(&htt);
+        hess[3 * i + 1] = nval(&hff);
+        hess[3 * i + 2] = nval(&htf);
+    }
+    return skipped;
+}
+
 /* Number of OpenMP threads the direct sum will use (for reporting). */
 int oracle_threads(void)
 {

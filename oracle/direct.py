@@ -26,6 +26,8 @@ def _load():
         lib.oracle_direct.restype = ctypes.c_int64
         lib.oracle_dipole.argtypes = [dp, dp, dp, ctypes.c_int64, dp, ctypes.c_int64, dp, dp]
         lib.oracle_dipole.restype = ctypes.c_int64
+        lib.oracle_hessian.argtypes = [dp, dp, ctypes.c_int64, dp, ctypes.c_int64, dp]
+        lib.oracle_hessian.restype = ctypes.c_int64
         lib.oracle_threads.argtypes = []
         lib.oracle_threads.restype = ctypes.c_int
         _lib = lib
@@ -112,6 +114,30 @@ def adjoint(src, q, tgt, g_alpha=None, g_psi=None, zero_mean=False):
     if zero_mean and g_psi is not None:
         phi = phi + np.sum(g_psi) / (4 * np.pi)
     return phi, q[:, None] * grad
+
+
+def hessian(src, q, tgt):
+    """Covariant Hessian of psi at the targets in (e_theta, e_phi), [M,3] =
+    (H_theta_theta, H_phi_phi, H_theta_phi) (Sec. 2.2; see direct.c)."""
+    lib = _load()
+    src = np.ascontiguousarray(src, dtype=np.float64).reshape(-1, 3)
+    tgt = np.ascontiguousarray(tgt, dtype=np.float64).reshape(-1, 3)
+    q = np.ascontiguousarray(q, dtype=np.float64).reshape(-1)
+    h = np.empty((tgt.shape[0], 3))
+    lib.oracle_hessian(_ptr(src), _ptr(q), src.shape[0], _ptr(tgt), tgt.shape[0], _ptr(h))
+    return h
+
+
+def lensing(src, q, tgt):
+    """Trace part, shear and magnification from the Hessian (Sec. 2.2, Eq. GAM_DEF):
+    kappa - kappa_bar = tr H, gamma_1 = (H11 - H22)/2, gamma_2 = H12,
+    mu = 1 / ((1 - tr H / 2)^2 - gamma_1^2 - gamma_2^2)."""
+    h = hessian(src, q, tgt)
+    tr = h[:, 0] + h[:, 1]
+    g1 = 0.5 * (h[:, 0] - h[:, 1])
+    g2 = h[:, 2]
+    mu = 1.0 / ((1.0 - 0.5 * tr) ** 2 - g1 ** 2 - g2 ** 2)
+    return dict(kappa=tr, gamma=np.stack([g1, g2], 1), mu=mu)
 
 
 def threads() -> int:
