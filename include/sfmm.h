@@ -119,6 +119,21 @@ sfmm_status sfmm_deflection_host(sfmm_plan_t plan, const double* src_xyz, const 
                                  const double* tgt_xyz, int64_t M, double* psi, double* alpha);
 
 /*
+ * Shear (Sec. 2.2, Eq. GAM_DEF): gamma [M][2] = (gamma_1, gamma_2), the
+ * trace-free part of the covariant Hessian of psi on (e_theta, e_phi) at each
+ * target, gamma_1 = (H11 - H22)/2, gamma_2 = H12; psi and alpha as in
+ * sfmm_deflection (either may be NULL).  For point masses the trace is
+ * kappa - kappa_bar = tr H = -sum(q)/(4 pi) at a target off the masses
+ * (Delta G = delta - 1/(4 pi); a target on a mass skips that mass), so the
+ * magnification mu = 1/((1 - tr H/2)^2 - gamma_1^2 - gamma_2^2) follows from
+ * gamma.  Far field from the second derivative of
+ * each leaf's local expansion (conformal chart), near field from the closed
+ * form of the Hessian of G.  Runs in FP64 whatever opt.precision is.
+ */
+sfmm_status sfmm_shear(sfmm_plan_t plan, const double* src_xyz, const void* q, int64_t N,
+                       const double* tgt_xyz, int64_t M, double* psi, double* alpha, double* gamma);
+
+/*
  * Adjoint: gradients of a loss L(psi, alpha) of sfmm_deflection's outputs with
  * respect to the masses and the source positions, given dL/dpsi and
  * dL/dalpha at the targets.  With g_i = g_alpha[i][0] e_theta(x_i) +

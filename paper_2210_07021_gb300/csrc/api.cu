@@ -62,7 +62,8 @@ cudaError_t launch_eval_adj(const TreeView& T, const int* leaves, int64_t n_leav
                             int p, int zero_mean, const void* w, int w_f32, double* phi, double* grad3, cudaStream_t s);
 cudaError_t launch_eval(const TreeView& T, const int* leaves, int64_t n_leaves, const double4_32a* src, const double4_32a* tgt,
                         const uint32_t* tperm, const int64_t* p2p_off, const uint32_t* p2p_src, const double* local,
-                        const double* mpole, int p, int zero_mean, double* psi, double* alpha, cudaStream_t s);
+                        const double* mpole, int p, int zero_mean, double* psi, double* alpha, double* gamma,
+                        cudaStream_t s);
 
 namespace {
 std::atomic<int64_t> g_launches{0};
@@ -250,10 +251,10 @@ struct AdjIO {
 };
 
 sfmm_status solve(sfmm_plan_s* P, const double* src, const void* q, int64_t N, const double* tgt, int64_t M,
-                  double* psi, double* alpha, const AdjIO* adj = nullptr)
+                  double* psi, double* alpha, const AdjIO* adj = nullptr, double* gamma = nullptr)
 {
     cudaStream_t s = P->stream;
-    const int precision = adj ? SFMM_FP64 : P->opt.precision;       // the adjoint runs in FP64
+    const int precision = (adj || gamma) ? SFMM_FP64 : P->opt.precision;   // adjoint and shear run in FP64
     const int q_f32 = adj ? 0 : P->opt.q_f32;
     cudaError_t e;
     const int p = P->p;
@@ -268,6 +269,7 @@ sfmm_status solve(sfmm_plan_s* P, const double* src, const void* q, int64_t N, c
         if (alpha && (e = cudaMemsetAsync(alpha, 0, (size_t)M * 16, s))) return cuda_fail(P, e, "memset alpha");
         if (adj && adj->grad3 && (e = cudaMemsetAsync(adj->grad3, 0, (size_t)M * 24, s)))
             return cuda_fail(P, e, "memset gradient");
+        if (gamma && (e = cudaMemsetAsync(gamma, 0, (size_t)M * 16, s))) return cuda_fail(P, e, "memset gamma");
         if ((e = cudaStreamSynchronize(s))) return cuda_fail(P, e, "sync");
         return SFMM_OK;
     }
@@ -415,7 +417,7 @@ sfmm_status solve(sfmm_plan_s* P, const double* src, const void* q, int64_t N, c
                                      P->logtab.as<float4>(), p, P->opt.zero_mean, psi, alpha, s);
     else e = launch_eval(T, P->leaves_tgt.as<int>(), P->n_leaves_tgt, P->src4.as<double4_32a>(),
                          P->tgt4.as<double4_32a>(), tperm, P->p2p_off.as<int64_t>(), p2p_s, P->local.as<double>(),
-                         P->mpole.as<double>(), p, P->opt.zero_mean, psi, alpha, s);
+                         P->mpole.as<double>(), p, P->opt.zero_mean, psi, alpha, gamma, s);
     if (e) return cuda_fail(P, e, "evaluation");
     tm.mark();
     if (P->timing) {
@@ -568,6 +570,15 @@ sfmm_status sfmm_deflection(sfmm_plan_t plan, const double* src_xyz, const void*
     if (st != SFMM_OK) return st;
     if (M > 0 && !alpha) return fail(plan, SFMM_EINVAL, "alpha must be non-NULL");
     return solve(plan, src_xyz, q, N, tgt_xyz, M, psi, alpha);
+}
+
+sfmm_status sfmm_shear(sfmm_plan_t plan, const double* src_xyz, const void* q, int64_t N, const double* tgt_xyz,
+                       int64_t M, double* psi, double* alpha, double* gamma)
+{
+    sfmm_status st = check_args(plan, src_xyz, q, N, tgt_xyz, M);
+    if (st != SFMM_OK) return st;
+    if (M > 0 && !gamma) return fail(plan, SFMM_EINVAL, "gamma must be non-NULL");
+    return solve(plan, src_xyz, q, N, tgt_xyz, M, psi, alpha, nullptr, gamma);
 }
 
 sfmm_status sfmm_adjoint(sfmm_plan_t plan, const double* src_xyz, const void* q, int64_t N, const double* tgt_xyz,

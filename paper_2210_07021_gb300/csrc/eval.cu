@@ -32,6 +32,7 @@ namespace sfmm {
 namespace {
 
 constexpr double INV4PI = 0.079577471545947667884;
+constexpr double PI = 3.14159265358979323846;
 constexpr double INV2PI = 0.15915494309189533577;
 constexpr double LOG2 = 0.69314718055994530942;
 constexpr double LOG4 = 1.3862943611198906188;
@@ -52,6 +53,7 @@ struct EvalArgs {
     int zero_mean;
     double* psi;
     double* alpha;
+    double* gamma;            // [M][2] shear (gamma_1, gamma_2) in (e_theta, e_phi), or NULL
 };
 
 __device__ __forceinline__ double group_sum(double v, int lpt)
@@ -60,6 +62,16 @@ __device__ __forceinline__ double group_sum(double v, int lpt)
     return v;
 }
 
+// SHEAR: also the trace-free part of the covariant Hessian (Sec. 2.2, Eq.
+// GAM_DEF).  Near field: H_ab = -(e_a.d)(e_b.d)/(pi d^4) + (isotropic), so the
+// shear needs S = sum q d d^T / d^4.  Far field, in the leaf chart w with
+// metric lambda^2 |dw|^2, lambda = 2/(1 + |w|^2):
+//   (H_uu - H_vv)/2 - i H_uv = (2/lambda^2) [d_w^2 f - 2 (d_w log lambda) d_w f]
+//                            = ((1 + |w|^2)^2 / 2) [F'' + 2 conj(w) F' / (1 + |w|^2)] - Q conj(w)^2 / 2
+// for f = C + Q log(1 + cos theta) + 2 Re F(w) (conformal Christoffel symbols;
+// 1 + cos theta = 2/(1 + |w|^2)); (H_uu, H_vv, H_uv) on the chart's unit
+// vectors e_u, e_v are then projected onto (e_theta, e_phi) at the target.
+template <bool SHEAR>
 __global__ void __launch_bounds__(128) k_eval(EvalArgs A)
 {
     const int lane = threadIdx.x & 31;
@@ -82,6 +94,7 @@ __global__ void __launch_bounds__(128) k_eval(EvalArgs A)
             const bool active = ti < tc;
             const double4_32a x = A.tgt[tf + (active ? ti : 0)];
             double sl = 0.0, sx = 0.0, sy = 0.0, sz = 0.0, sq = 0.0;
+            double Sxx = 0.0, Syy = 0.0, Szz = 0.0, Sxy = 0.0, Sxz = 0.0, Syz = 0.0;
             for (int64_t k = nb0; k < nb1; ++k) {
                 const int sleaf = (int)A.p2p_src[k];
                 const int f = A.T.first[sleaf], n = A.T.count[sleaf];
@@ -96,6 +109,11 @@ __global__ void __launch_bounds__(128) k_eval(EvalArgs A)
                         sz += wq * dz;
                         sq += y.w;
                         if (A.want_psi) sl += y.w * log(d2);
+                        if (SHEAR) {
+                            const double w4 = wq / d2;
+                            Sxx += w4 * dx * dx; Syy += w4 * dy * dy; Szz += w4 * dz * dz;
+                            Sxy += w4 * dx * dy; Sxz += w4 * dx * dz; Syz += w4 * dy * dz;
+                        }
                     }
                 }
             }
@@ -104,6 +122,10 @@ __global__ void __launch_bounds__(128) k_eval(EvalArgs A)
             sz = group_sum(sz, lpt);
             sq = group_sum(sq, lpt);
             if (A.want_psi) sl = group_sum(sl, lpt);
+            if (SHEAR) {
+                Sxx = group_sum(Sxx, lpt); Syy = group_sum(Syy, lpt); Szz = group_sum(Szz, lpt);
+                Sxy = group_sum(Sxy, lpt); Sxz = group_sum(Sxz, lpt); Syz = group_sum(Syz, lpt);
+            }
             if (!active || sub != 0) continue;
             // ---- L2P in the leaf frame
             const double Dx = x.x - g[0], Dy = x.y - g[1], Dz = x.z - g[2];
@@ -113,11 +135,12 @@ __global__ void __launch_bounds__(128) k_eval(EvalArgs A)
             const double wv = (Dx * g[6] + Dy * g[7] + Dz * g[8]) / den;
             const double inv_r = 1.0 / g[10];
             const cd om = mk(wu * inv_r, wv * inv_r);
-            cd f = mk(0.0, 0.0), fd = mk(0.0, 0.0);
+            cd f = mk(0.0, 0.0), fd = mk(0.0, 0.0), fdd = mk(0.0, 0.0);
             for (int l = A.p; l >= 1; --l) {
                 const cd a = mk(L[2 * l], L[2 * l + 1]);
                 f = cadd(cmul(f, om), a);
                 fd = cadd(cmul(fd, om), cscale(a, (double)l));
+                if (SHEAR && l >= 2) fdd = cadd(cmul(fdd, om), cscale(a, (double)(l * (l - 1))));
             }
             const cd F = cmul(f, om);
             const cd Fp = cscale(fd, inv_r);                    // dF/dw
@@ -144,6 +167,33 @@ __global__ void __launch_bounds__(128) k_eval(EvalArgs A)
             if (A.want_psi) {
                 const double psi_e = C + Q * (LOG2 + log1p(-0.25 * D2)) + 2.0 * F.x;
                 A.psi[o] = psi_e + INV4PI * (sl - LOG4 * sq) + shift;
+            }
+            if (SHEAR) {
+                // far field: chart-frame trace-free Hessian, then onto (e_theta, e_phi)
+                const cd Fpp = cscale(fdd, inv_r * inv_r);
+                const double opw = 1.0 + w2;
+                const cd wb = mk(wu, -wv);
+                const cd t1 = cadd(Fpp, cscale(cmul(wb, Fp), 2.0 / opw));
+                const cd wb2 = cmul(wb, wb);
+                const double gr = 0.5 * opw * opw * t1.x - 0.5 * Q * wb2.x;
+                const double gi = 0.5 * opw * opw * t1.y - 0.5 * Q * wb2.y;
+                const double huu = gr, huv = -gi;                        // H_vv = -H_uu (trace-free part)
+                const double eux = g[3] - wu * cxx, euy = g[4] - wu * cyy, euz = g[5] - wu * czz;
+                const double evx = g[6] - wv * cxx, evy = g[7] - wv * cyy, evz = g[8] - wv * czz;
+                const double etx = x.z * cp, ety = x.z * sp, etz = -rho, epx = -sp, epy = cp;
+                const double c1 = eux * etx + euy * ety + euz * etz, s1 = eux * epx + euy * epy;
+                const double c2 = evx * etx + evy * ety + evz * etz, s2 = evx * epx + evy * epy;
+                double g1 = 0.5 * (huu * (c1 * c1 - s1 * s1 - c2 * c2 + s2 * s2)) + huv * (c1 * c2 - s1 * s2);
+                double g2 = huu * (c1 * s1 - c2 * s2) + huv * (c1 * s2 + c2 * s1);
+                // near field: -(e_a^T S e_b)/pi
+                const double stt = etx * (Sxx * etx + Sxy * ety + Sxz * etz) + ety * (Sxy * etx + Syy * ety + Syz * etz) +
+                                   etz * (Sxz * etx + Syz * ety + Szz * etz);
+                const double spp = epx * (Sxx * epx + Sxy * epy) + epy * (Sxy * epx + Syy * epy);
+                const double stp = epx * (Sxx * etx + Sxy * ety + Sxz * etz) + epy * (Sxy * etx + Syy * ety + Syz * etz);
+                g1 -= 0.5 * (stt - spp) / PI;
+                g2 -= stp / PI;
+                A.gamma[2 * (size_t)o] = g1;
+                A.gamma[2 * (size_t)o + 1] = g2;
             }
         }
     }
@@ -911,7 +961,8 @@ cudaError_t launch_count_pairs(const TreeView& T, const int* leaves, int64_t n_l
 
 cudaError_t launch_eval(const TreeView& T, const int* leaves, int64_t n_leaves, const double4_32a* src, const double4_32a* tgt,
                         const uint32_t* tperm, const int64_t* p2p_off, const uint32_t* p2p_src, const double* local,
-                        const double* mpole, int p, int zero_mean, double* psi, double* alpha, cudaStream_t s)
+                        const double* mpole, int p, int zero_mean, double* psi, double* alpha, double* gamma,
+                        cudaStream_t s)
 {
     if (n_leaves == 0) return cudaSuccess;
     EvalArgs A;
@@ -930,9 +981,12 @@ cudaError_t launch_eval(const TreeView& T, const int* leaves, int64_t n_leaves, 
     A.zero_mean = zero_mean;
     A.psi = psi;
     A.alpha = alpha;
+    A.gamma = gamma;
     int64_t blocks = (n_leaves + 3) / 4;
     if (blocks > 152 * 64) blocks = 152 * 64;
-    k_eval<<<(unsigned)blocks, 128, 0, s>>>(A); count_launch();
+    if (gamma) k_eval<true><<<(unsigned)blocks, 128, 0, s>>>(A);
+    else k_eval<false><<<(unsigned)blocks, 128, 0, s>>>(A);
+    count_launch();
     return cudaGetLastError();
 }
 
@@ -959,6 +1013,7 @@ cudaError_t launch_eval_adj(const TreeView& T, const int* leaves, int64_t n_leav
     A.zero_mean = zero_mean;
     A.psi = phi;
     A.alpha = nullptr;
+    A.gamma = nullptr;
     AA.dip = dip;
     AA.w = w;
     AA.w_f32 = w_f32;

@@ -18,7 +18,7 @@ SFMM_FP64, SFMM_MIXED, SFMM_MIXED_DF = 0, 1, 2
  ARR_NODE_GEOM, ARR_MULTIPOLE, ARR_LOCAL, ARR_M2L, ARR_P2P, ARR_TGT_KEYS, ARR_NODE_TRANGE) = range(14)
 
 EXPORTS = ["sfmm_default_options", "sfmm_plan", "sfmm_potential", "sfmm_deflection", "sfmm_deflection_host",
-           "sfmm_adjoint",
+           "sfmm_adjoint", "sfmm_shear",
            "sfmm_destroy", "sfmm_last_error", "sfmm_order", "sfmm_get_stats", "sfmm_set_timing",
            "sfmm_debug_copy", "sfmm_keys", "sfmm_sort_keys_static"]
 STATIC_SORT_MAX_N = 1 << 18
@@ -72,6 +72,8 @@ def load(build_if_missing=True):
     L.sfmm_deflection_host.restype = ci
     L.sfmm_adjoint.argtypes = [vp, vp, vp, i64, vp, i64, vp, vp, vp, vp]
     L.sfmm_adjoint.restype = ci
+    L.sfmm_shear.argtypes = [vp, vp, vp, i64, vp, i64, vp, vp, vp]
+    L.sfmm_shear.restype = ci
     L.sfmm_destroy.argtypes = [vp]
     L.sfmm_destroy.restype = None
     L.sfmm_last_error.argtypes = [vp]
@@ -90,6 +92,14 @@ def load(build_if_missing=True):
     L.sfmm_sort_keys_static.restype = ci
     _lib = L
     return L
+
+
+def magnification(gamma, trace):
+    """mu = 1/((1 - tr H/2)^2 - |gamma|^2) (Sec. 2.2).  For point masses
+    tr H = kappa - kappa_bar = -sum(q)/(4 pi) at any target that is not on a
+    mass (at a target on a mass, whose own term is skipped, leave that mass
+    out of the sum); `trace` is a scalar or one value per target."""
+    return 1.0 / ((1.0 - 0.5 * np.asarray(trace)) ** 2 - (gamma ** 2).sum(-1))
 
 
 def _check(st, plan=None):
@@ -194,6 +204,20 @@ class Plan:
                                     _dptr(alpha, torch.float64, 2, "alpha"))
         _check(st, self._h)
         return (psi if with_psi else None), alpha
+
+    def shear(self, src, q, tgt, with_psi=False, with_alpha=False):
+        """(gamma [M, 2], psi or None, alpha or None) at the targets (FP64 path; see sfmm_shear)."""
+        import torch
+        M = tgt.shape[0]
+        gamma = torch.empty((M, 2), dtype=torch.float64, device=tgt.device)
+        psi = torch.empty(M, dtype=torch.float64, device=tgt.device) if with_psi else None
+        alpha = torch.empty((M, 2), dtype=torch.float64, device=tgt.device) if with_alpha else None
+        st = load().sfmm_shear(self._h, _dptr(src, torch.float64, 3, "src"), _dptr(q, self._qdtype(), None, "q"),
+                               src.shape[0], _dptr(tgt, torch.float64, 3, "tgt"), M,
+                               _dptr(psi, torch.float64, None, "psi"), _dptr(alpha, torch.float64, 2, "alpha"),
+                               _dptr(gamma, torch.float64, 2, "gamma"))
+        _check(st, self._h)
+        return gamma, psi, alpha
 
     def adjoint(self, src, q, tgt, g_psi=None, g_alpha=None, want_q=True, want_src=True):
         """(dL/dq [N] or None, dL/dy [N, 3] or None) for a loss of this plan's
