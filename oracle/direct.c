@@ -91,6 +91,73 @@ int64_t oracle_direct(const double* src, const double* q, int64_t N,
     return skipped;
 }
 
+/* Near Particle Model (Sec. 3.2 and Sec. 4.2, Eq. KERNEL): each mass spread
+ * over a cap of angular radius sigma with the generalised Epanechnikov
+ * profile W = [1 - sin^2(t/2)/sin^2(sigma/2)] / (2 pi sin^2(sigma/2)).
+ * With u = sin^2(t/2) = d^2/4 and s = sin^2(sigma/2), the enclosed fraction
+ * of the mass within angle t is m(u) = 2u/s - u^2/s^2 (u <= s; 1 beyond), and
+ * Gauss's law on the sphere with the uniform background of Delta G = delta -
+ * 1/4pi gives the deflection away from the mass
+ *   2 pi sin t alpha = q (m(u) - u),  i.e. f(u) = (m - u)/(1 - u) times the
+ * point-mass term q P_x(x - y)/(2 pi d^2).  The potential continues the point
+ * mass's (1/4pi) log u inside the cap with the same derivative:
+ *   G_s(u) = (1/4pi) [ log s + (u - s)/s^2 + ((1 - s)^2/s^2) log((1 - u)/(1 - s)) ]
+ *          = (1/4pi) [ log s - (1 - u/s) + ((1 - s)^2/s^2) (log1p(t) - t) ],
+ *   t = (s - u)/(1 - s)   (the second form avoids the cancellation of the two
+ *   O(1/s) terms of the first),
+ * so outside the cap each mass is exactly a point mass (what the far field
+ * assumes).  sigma = 0 is the point-mass sum.  Pairs with d^2 == 0 are
+ * skipped, as in oracle_direct. */
+int64_t oracle_direct_npm(const double* src, const double* q, int64_t N,
+                          const double* tgt, int64_t M, double sigma,
+                          double* psi, double* alpha2, double* alpha3)
+{
+    const double inv4pi = 1.0 / (4.0 * M_PI);
+    const double inv2pi = 1.0 / (2.0 * M_PI);
+    const double sh = sin(0.5 * sigma), s = sh * sh;
+    int64_t skipped = 0;
+#pragma omp parallel for schedule(dynamic, 1) reduction(+:skipped)
+    for (int64_t i = 0; i < M; ++i) {
+        const double x0 = tgt[3 * i], x1 = tgt[3 * i + 1], x2 = tgt[3 * i + 2];
+        nsum sp = {0, 0}, g0 = {0, 0}, g1 = {0, 0}, g2 = {0, 0};
+        for (int64_t j = 0; j < N; ++j) {
+            const double e0 = x0 - src[3 * j];
+            const double e1 = x1 - src[3 * j + 1];
+            const double e2 = x2 - src[3 * j + 2];
+            const double d2 = e0 * e0 + e1 * e1 + e2 * e2;
+            if (d2 == 0.0) { ++skipped; continue; }
+            const double qj = q[j];
+            const double u = 0.25 * d2;
+            double gval, f;
+            if (sigma > 0.0 && u < s) {
+                const double m = 2.0 * u / s - u * u / (s * s);
+                f = (m - u) / (1.0 - u);
+                const double t = (s - u) / (1.0 - s);
+                gval = log(s) - (1.0 - u / s) + (1.0 - s) * (1.0 - s) / (s * s) * (log1p(t) - t);
+            } else {
+                f = 1.0;
+                gval = log(u);
+            }
+            nadd(&sp, qj * inv4pi * gval);
+            const double w = f * qj * inv2pi / d2;
+            nadd(&g0, w * e0 - 0.5 * f * qj * inv2pi * x0);
+            nadd(&g1, w * e1 - 0.5 * f * qj * inv2pi * x1);
+            nadd(&g2, w * e2 - 0.5 * f * qj * inv2pi * x2);
+        }
+        const double a0 = nval(&g0), a1 = nval(&g1), a2 = nval(&g2);
+        if (psi) psi[i] = nval(&sp);
+        if (alpha3) { alpha3[3 * i] = a0; alpha3[3 * i + 1] = a1; alpha3[3 * i + 2] = a2; }
+        if (alpha2) {
+            const double rho = sqrt(x0 * x0 + x1 * x1);
+            double cp = 1.0, sp_ = 0.0;
+            if (rho > 0.0) { cp = x0 / rho; sp_ = x1 / rho; }
+            alpha2[2 * i] = a0 * (x2 * cp) + a1 * (x2 * sp_) - a2 * rho;
+            alpha2[2 * i + 1] = -a0 * sp_ + a1 * cp;
+        }
+    }
+    return skipped;
+}
+
 /* Potential and covariant gradient, at the points y[N], of charges h[M] and
  * tangent dipoles g[M][3] (g_i . x_i = 0) placed at the points x[M]:
  *

@@ -28,6 +28,8 @@ def _load():
         lib.oracle_dipole.restype = ctypes.c_int64
         lib.oracle_hessian.argtypes = [dp, dp, ctypes.c_int64, dp, ctypes.c_int64, dp]
         lib.oracle_hessian.restype = ctypes.c_int64
+        lib.oracle_direct_npm.argtypes = [dp, dp, ctypes.c_int64, dp, ctypes.c_int64, ctypes.c_double, dp, dp, dp]
+        lib.oracle_direct_npm.restype = ctypes.c_int64
         lib.oracle_threads.argtypes = []
         lib.oracle_threads.restype = ctypes.c_int
         _lib = lib
@@ -40,9 +42,11 @@ def _ptr(a):
     return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
 
 
-def direct_sum(src, q, tgt, want=("psi", "alpha")):
+def direct_sum(src, q, tgt, want=("psi", "alpha"), sigma=0.0):
     """Return a dict with 'psi' [M], 'alpha' [M,2] (e_theta, e_phi),
-    'alpha3' [M,3] (tangent 3-vector) as requested, plus 'skipped'."""
+    'alpha3' [M,3] (tangent 3-vector) as requested, plus 'skipped'.
+    sigma > 0: each mass smoothed by the Near Particle Model profile of
+    angular radius sigma (oracle_direct_npm in direct.c)."""
     lib = _load()
     src = np.ascontiguousarray(src, dtype=np.float64).reshape(-1, 3)
     tgt = np.ascontiguousarray(tgt, dtype=np.float64).reshape(-1, 3)
@@ -54,8 +58,12 @@ def direct_sum(src, q, tgt, want=("psi", "alpha")):
     psi = np.empty(M) if "psi" in want else None
     a2 = np.empty((M, 2)) if "alpha" in want else None
     a3 = np.empty((M, 3)) if "alpha3" in want else None
-    out["skipped"] = int(lib.oracle_direct(_ptr(src), _ptr(q), src.shape[0], _ptr(tgt), M,
-                                           _ptr(psi), _ptr(a2), _ptr(a3)))
+    if sigma > 0.0:
+        out["skipped"] = int(lib.oracle_direct_npm(_ptr(src), _ptr(q), src.shape[0], _ptr(tgt), M, float(sigma),
+                                                   _ptr(psi), _ptr(a2), _ptr(a3)))
+    else:
+        out["skipped"] = int(lib.oracle_direct(_ptr(src), _ptr(q), src.shape[0], _ptr(tgt), M,
+                                               _ptr(psi), _ptr(a2), _ptr(a3)))
     if psi is not None:
         out["psi"] = psi
     if a2 is not None:

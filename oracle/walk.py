@@ -13,7 +13,11 @@ are the 12 base boxes (Sec. 3.4):
   * only B_T is a leaf: split B_S;  only B_S is a leaf: split B_T;
   * both leaves: B_S direct-acts on B_T (a P2P pair).
 "Far" is MAC1 d - R_T - c_s R_S > 0 and MAC2 R_T < c_t d, where d is the
-angle between the two box centres and R the box radii (Sec. 3.5).
+angle between the two box centres and R the box radii (Sec. 3.5).  With the
+Near Particle Model (particles of angular radius sigma > 0) a far pair must
+also keep every particle's profile out of the target box, d - R_T - R_S > sigma,
+so that the far field may treat each particle as a point (Sec. 3.5's protected
+area, made explicit for a given sigma).
 
 Two exact prunings, used by the solver too: a pair whose source box holds no
 particle contributes nothing and is dropped; a pair whose target box holds no
@@ -33,7 +37,7 @@ def _angle(a, b):
     return 2.0 * np.arcsin(min(1.0, np.linalg.norm(a - b) / 2.0))
 
 
-def walk(tree, centre, radius, c_s=2.0, c_t=0.5, tcount=None):
+def walk(tree, centre, radius, c_s=2.0, c_t=0.5, tcount=None, sigma=0.0):
     """Return (m2l, p2p): lists of (source node, target node) pairs."""
     child0 = tree["child0"]
     count = tree["count"]
@@ -66,7 +70,7 @@ def walk(tree, centre, radius, c_s=2.0, c_t=0.5, tcount=None):
             return
         d = _angle(centre[s], centre[t])
         rs, rt = radius[s], radius[t]
-        if d - rt - c_s * rs > 0.0 and rt < c_t * d:
+        if d - rt - c_s * rs > 0.0 and rt < c_t * d and d - rt - rs > sigma:
             m2l.append((s, t))
         elif not is_leaf(s) and not is_leaf(t):
             if rs > rt * (1.0 + TIE):
@@ -91,8 +95,11 @@ def walk(tree, centre, radius, c_s=2.0, c_t=0.5, tcount=None):
     return m2l, p2p
 
 
-def mac_margin(centre, radius, s, t, c_s=2.0, c_t=0.5):
-    """Smallest distance of the pair (s, t) from either MAC threshold (used to
+def mac_margin(centre, radius, s, t, c_s=2.0, c_t=0.5, sigma=0.0):
+    """Smallest distance of the pair (s, t) from any MAC threshold (used to
     tell rounding-level disagreements from real ones)."""
     d = _angle(centre[s], centre[t])
-    return min(abs(d - radius[t] - c_s * radius[s]), abs(radius[t] - c_t * d))
+    m = min(abs(d - radius[t] - c_s * radius[s]), abs(radius[t] - c_t * d))
+    if sigma > 0.0:
+        m = min(m, abs(d - radius[t] - radius[s] - sigma))
+    return m
