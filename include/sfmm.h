@@ -77,6 +77,12 @@ typedef struct {
                               at plan time (0 = grow on first use)                                  */
     void* stream;          /* cudaStream_t to enqueue on; NULL = the legacy default stream          */
     int m2l_tensor_cores;  /* SFMM_MIXED only: 1 (default) = M2L as split-BF16 tcgen05 GEMMs, 0 = FP32 warp kernel */
+    double sigma;          /* Near Particle Model (Secs. 3.2, 4.2): each mass spread over a cap of angular
+                              radius sigma with the Epanechnikov profile of Eq. KERNEL; 0 (default) = point
+                              masses.  Inside the cap alpha follows from Gauss's law on the sphere
+                              (f(u) = (m(u) - u)/(1 - u) times the point-mass term, u = sin^2(t/2),
+                              m = 2u/s - u^2/s^2, s = sin^2(sigma/2)) and psi continues the point-mass
+                              potential; far pairs also need d - R_T - R_S > sigma.  SFMM_FP64 only. */
 } sfmm_options;
 
 /* Fill *opt with the defaults listed above.  Returns SFMM_EINVAL if opt is NULL. */

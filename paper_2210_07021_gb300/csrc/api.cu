@@ -62,8 +62,8 @@ cudaError_t launch_eval_adj(const TreeView& T, const int* leaves, int64_t n_leav
                             int p, int zero_mean, const void* w, int w_f32, double* phi, double* grad3, cudaStream_t s);
 cudaError_t launch_eval(const TreeView& T, const int* leaves, int64_t n_leaves, const double4_32a* src, const double4_32a* tgt,
                         const uint32_t* tperm, const int64_t* p2p_off, const uint32_t* p2p_src, const double* local,
-                        const double* mpole, int p, int zero_mean, double* psi, double* alpha, double* gamma,
-                        cudaStream_t s);
+                        const double* mpole, int p, int zero_mean, double sigma, double* psi, double* alpha,
+                        double* gamma, cudaStream_t s);
 
 namespace {
 std::atomic<int64_t> g_launches{0};
@@ -417,7 +417,7 @@ sfmm_status solve(sfmm_plan_s* P, const double* src, const void* q, int64_t N, c
                                      P->logtab.as<float4>(), p, P->opt.zero_mean, psi, alpha, s);
     else e = launch_eval(T, P->leaves_tgt.as<int>(), P->n_leaves_tgt, P->src4.as<double4_32a>(),
                          P->tgt4.as<double4_32a>(), tperm, P->p2p_off.as<int64_t>(), p2p_s, P->local.as<double>(),
-                         P->mpole.as<double>(), p, P->opt.zero_mean, psi, alpha, gamma, s);
+                         P->mpole.as<double>(), p, P->opt.zero_mean, P->opt.sigma, psi, alpha, gamma, s);
     if (e) return cuda_fail(P, e, "evaluation");
     tm.mark();
     if (P->timing) {
@@ -509,6 +509,9 @@ sfmm_status sfmm_plan(sfmm_plan_t* out, int max_depth, int order_p, double tol, 
     if (o.precision != SFMM_FP64 && o.precision != SFMM_MIXED && o.precision != SFMM_MIXED_DF)
         return plan_fail("unknown precision");
     if (o.n_max < 0 || o.m_max < 0) return plan_fail("n_max and m_max must be >= 0");
+    if (!(o.sigma >= 0.0 && o.sigma < 1.5707963267948966)) return plan_fail("sigma must be in [0, pi/2)");
+    if (o.sigma > 0.0 && o.precision != SFMM_FP64)
+        return plan_fail("sigma > 0 (Near Particle Model) runs on the FP64 path only (precision SFMM_FP64)");
     auto* P = new (std::nothrow) sfmm_plan_s();
     if (!P) return SFMM_ENOMEM;
     P->max_depth = max_depth;
@@ -578,6 +581,7 @@ sfmm_status sfmm_shear(sfmm_plan_t plan, const double* src_xyz, const void* q, i
     sfmm_status st = check_args(plan, src_xyz, q, N, tgt_xyz, M);
     if (st != SFMM_OK) return st;
     if (M > 0 && !gamma) return fail(plan, SFMM_EINVAL, "gamma must be non-NULL");
+    if (plan->opt.sigma > 0.0) return fail(plan, SFMM_EINVAL, "sfmm_shear supports point masses only (sigma == 0)");
     return solve(plan, src_xyz, q, N, tgt_xyz, M, psi, alpha, nullptr, gamma);
 }
 
@@ -587,6 +591,7 @@ sfmm_status sfmm_adjoint(sfmm_plan_t plan, const double* src_xyz, const void* q,
     sfmm_status st = check_args(plan, src_xyz, q, N, tgt_xyz, M);
     if (st != SFMM_OK) return st;
     if (N > 0 && !grad_q && !grad_src) return fail(plan, SFMM_EINVAL, "grad_q or grad_src must be non-NULL");
+    if (plan->opt.sigma > 0.0) return fail(plan, SFMM_EINVAL, "sfmm_adjoint supports point masses only (sigma == 0)");
     if (N == 0) return SFMM_OK;
     cudaStream_t s = plan->stream;
     cudaError_t e;

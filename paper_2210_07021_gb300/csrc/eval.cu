@@ -54,6 +54,7 @@ struct EvalArgs {
     double* psi;
     double* alpha;
     double* gamma;            // [M][2] shear (gamma_1, gamma_2) in (e_theta, e_phi), or NULL
+    double npm_s;             // Near Particle Model: sin^2(sigma/2) (NPM kernels only)
 };
 
 __device__ __forceinline__ double group_sum(double v, int lpt)
@@ -71,7 +72,13 @@ __device__ __forceinline__ double group_sum(double v, int lpt)
 // for f = C + Q log(1 + cos theta) + 2 Re F(w) (conformal Christoffel symbols;
 // 1 + cos theta = 2/(1 + |w|^2)); (H_uu, H_vv, H_uv) on the chart's unit
 // vectors e_u, e_v are then projected onto (e_theta, e_phi) at the target.
-template <bool SHEAR>
+//
+// NPM: pairs closer than the particle radius (u = d^2/4 < s = sin^2(sigma/2))
+// use the smoothed particle (Secs. 3.2, 4.2): alpha scaled by
+// f = (m(u) - u)/(1 - u), m = 2u/s - u^2/s^2 (Gauss's law on the sphere), and
+// log u replaced by log s - (1 - u/s) + ((1 - s)^2/s^2)(log1p(t) - t),
+// t = (s - u)/(1 - s) (the point-mass potential continued into the cap).
+template <bool SHEAR, bool NPM>
 __global__ void __launch_bounds__(128) k_eval(EvalArgs A)
 {
     const int lane = threadIdx.x & 31;
@@ -95,6 +102,7 @@ __global__ void __launch_bounds__(128) k_eval(EvalArgs A)
             const double4_32a x = A.tgt[tf + (active ? ti : 0)];
             double sl = 0.0, sx = 0.0, sy = 0.0, sz = 0.0, sq = 0.0;
             double Sxx = 0.0, Syy = 0.0, Szz = 0.0, Sxy = 0.0, Sxz = 0.0, Syz = 0.0;
+            double sqa = 0.0;                 // NPM: sum of f q (the alpha part of sum q)
             for (int64_t k = nb0; k < nb1; ++k) {
                 const int sleaf = (int)A.p2p_src[k];
                 const int f = A.T.first[sleaf], n = A.T.count[sleaf];
@@ -102,7 +110,25 @@ __global__ void __launch_bounds__(128) k_eval(EvalArgs A)
                     const double4_32a y = A.src[j];
                     const double dx = x.x - y.x, dy = x.y - y.y, dz = x.z - y.z;
                     const double d2 = dx * dx + dy * dy + dz * dz;
-                    if (d2 > 0.0) {
+                    if (NPM && d2 > 0.0) {
+                        const double s = A.npm_s, u = 0.25 * d2;
+                        double f = 1.0, lg;
+                        if (u < s) {
+                            const double m = 2.0 * u / s - u * u / (s * s);
+                            f = (m - u) / (1.0 - u);
+                            const double t = (s - u) / (1.0 - s);
+                            lg = LOG4 + log(s) - (1.0 - u / s) + (1.0 - s) * (1.0 - s) / (s * s) * (log1p(t) - t);
+                        } else {
+                            lg = log(d2);
+                        }
+                        const double wq = f * y.w / d2;
+                        sx += wq * dx;
+                        sy += wq * dy;
+                        sz += wq * dz;
+                        sq += y.w;
+                        sqa += f * y.w;
+                        if (A.want_psi) sl += y.w * lg;
+                    } else if (d2 > 0.0) {
                         const double wq = y.w / d2;
                         sx += wq * dx;
                         sy += wq * dy;
@@ -121,6 +147,8 @@ __global__ void __launch_bounds__(128) k_eval(EvalArgs A)
             sy = group_sum(sy, lpt);
             sz = group_sum(sz, lpt);
             sq = group_sum(sq, lpt);
+            if (NPM) sqa = group_sum(sqa, lpt);
+            else sqa = sq;
             if (A.want_psi) sl = group_sum(sl, lpt);
             if (SHEAR) {
                 Sxx = group_sum(Sxx, lpt); Syy = group_sum(Syy, lpt); Szz = group_sum(Szz, lpt);
@@ -153,9 +181,9 @@ __global__ void __launch_bounds__(128) k_eval(EvalArgs A)
             double a3y = au * (g[4] - wu * cyy) + av * (g[7] - wv * cyy);
             double a3z = au * (g[5] - wu * czz) + av * (g[8] - wv * czz);
             // ---- near field
-            a3x += INV2PI * (sx - 0.5 * x.x * sq);
-            a3y += INV2PI * (sy - 0.5 * x.y * sq);
-            a3z += INV2PI * (sz - 0.5 * x.z * sq);
+            a3x += INV2PI * (sx - 0.5 * x.x * sqa);
+            a3y += INV2PI * (sy - 0.5 * x.y * sqa);
+            a3z += INV2PI * (sz - 0.5 * x.z * sqa);
             const double rho = sqrt(x.x * x.x + x.y * x.y);
             double cp = 1.0, sp = 0.0;
             if (rho > 0.0) { cp = x.x / rho; sp = x.y / rho; }
@@ -961,8 +989,8 @@ cudaError_t launch_count_pairs(const TreeView& T, const int* leaves, int64_t n_l
 
 cudaError_t launch_eval(const TreeView& T, const int* leaves, int64_t n_leaves, const double4_32a* src, const double4_32a* tgt,
                         const uint32_t* tperm, const int64_t* p2p_off, const uint32_t* p2p_src, const double* local,
-                        const double* mpole, int p, int zero_mean, double* psi, double* alpha, double* gamma,
-                        cudaStream_t s)
+                        const double* mpole, int p, int zero_mean, double sigma, double* psi, double* alpha,
+                        double* gamma, cudaStream_t s)
 {
     if (n_leaves == 0) return cudaSuccess;
     EvalArgs A;
@@ -982,10 +1010,12 @@ cudaError_t launch_eval(const TreeView& T, const int* leaves, int64_t n_leaves, 
     A.psi = psi;
     A.alpha = alpha;
     A.gamma = gamma;
+    A.npm_s = sin(0.5 * sigma) * sin(0.5 * sigma);
     int64_t blocks = (n_leaves + 3) / 4;
     if (blocks > 152 * 64) blocks = 152 * 64;
-    if (gamma) k_eval<true><<<(unsigned)blocks, 128, 0, s>>>(A);
-    else k_eval<false><<<(unsigned)blocks, 128, 0, s>>>(A);
+    if (gamma) k_eval<true, false><<<(unsigned)blocks, 128, 0, s>>>(A);
+    else if (sigma > 0.0) k_eval<false, true><<<(unsigned)blocks, 128, 0, s>>>(A);
+    else k_eval<false, false><<<(unsigned)blocks, 128, 0, s>>>(A);
     count_launch();
     return cudaGetLastError();
 }

@@ -55,11 +55,15 @@ struct WalkCaps {
 // With the chord k = |c_S - c_T| = 2 sin(d/2), monotone in d on [0, pi]:
 //   MAC1  d > R_T + c_s R_S  <=>  R_T + c_s R_S < pi  and  k > 2 sin((R_T + c_s R_S)/2)
 //   MAC2  d > R_T / c_t      <=>  k > 2 sin(R_T / (2 c_t))
+// and, with the Near Particle Model (particles of angular radius sigma > 0),
+//   MAC3  d > R_T + R_S + sigma  <=>  R_T + R_S + sigma < pi  and
+//         k > 2 sin((R_T + R_S + sigma)/2),  from sin/cos of (R_S + sigma)/2:
+// no particle's profile reaches a target box it acts on by M2L.
 struct __align__(16) MacNode {
-    double s1, c1, s2, c2, t2, R, pad0, pad1;
+    double s1, c1, s2, c2, t2, R, s3, c3;
 };
 
-__global__ void k_mac_nodes(TreeView T, double c_s, double c_t, MacNode* __restrict__ out)
+__global__ void k_mac_nodes(TreeView T, double c_s, double c_t, double sigma, MacNode* __restrict__ out)
 {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < T.n_nodes; i += (int64_t)gridDim.x * blockDim.x) {
         const double R = T.geom[(size_t)i * GEOM_STRIDE + 9];
@@ -69,13 +73,13 @@ __global__ void k_mac_nodes(TreeView T, double c_s, double c_t, MacNode* __restr
         const double a = R / c_t;
         m.t2 = a < 3.141592653589793 ? 2.0 * sin(0.5 * a) : 3.0;
         m.R = R;
-        m.pad0 = m.pad1 = 0.0;
+        sincos(0.5 * (R + sigma), &m.s3, &m.c3);
         out[i] = m;
     }
 }
 
 __device__ __forceinline__ uint8_t classify(const TreeView& T, const MacNode* __restrict__ mac, int s, int t,
-                                            double c_s)
+                                            double c_s, double sigma)
 {
     if (T.count[s] == 0 || T.tcount[t] == 0) return A_DROP;
     const bool ls = T.child0[s] < 0, lt = T.child0[t] < 0;
@@ -89,7 +93,12 @@ __device__ __forceinline__ uint8_t classify(const TreeView& T, const MacNode* __
     const double thr1 = 2.0 * (mt.s1 * ms.c2 + mt.c1 * ms.s2);
     const bool mac1 = (Rt + c_s * Rs < 3.141592653589793) && k2 > thr1 * thr1;
     const bool mac2 = k2 > mt.t2 * mt.t2;
-    if (mac1 && mac2) return A_M2L;
+    bool mac3 = true;
+    if (sigma > 0.0) {
+        const double thr3 = 2.0 * (mt.s1 * ms.c3 + mt.c1 * ms.s3);
+        mac3 = (Rt + Rs + sigma < 3.141592653589793) && k2 > thr3 * thr3;
+    }
+    if (mac1 && mac2 && mac3) return A_M2L;
     if (!ls && !lt) return (Rs > Rt * (1.0 + RADIUS_TIE)) ? A_SPLIT_S : A_SPLIT_T;
     if (!ls) return A_SPLIT_S;
     if (!lt) return A_SPLIT_T;
@@ -148,7 +157,7 @@ __global__ void k_init_frontier(int2* f, int64_t* ctr)
 
 __global__ void __launch_bounds__(WT) k_walk_classify(TreeView T, const MacNode* __restrict__ mac,
                                                       const int2* __restrict__ front,
-                                                      const int64_t* __restrict__ n_front_p, double c_s,
+                                                      const int64_t* __restrict__ n_front_p, double c_s, double sigma,
                                                       uint8_t* __restrict__ act, int3* __restrict__ tile_sums)
 {
     __shared__ int3 s_w[WT / 32];
@@ -161,7 +170,7 @@ __global__ void __launch_bounds__(WT) k_walk_classify(TreeView T, const MacNode*
             const int64_t i = tile * WTILE + (int64_t)r * WT + threadIdx.x;
             if (i < n) {
                 const int2 pr = front[i];
-                const uint8_t a = classify(T, mac, pr.x, pr.y, c_s);
+                const uint8_t a = classify(T, mac, pr.x, pr.y, c_s, sigma);
                 act[i] = a;
                 acc = add3(acc, counts_of(a));
             }
@@ -316,7 +325,7 @@ cudaError_t build_lists(sfmm_plan_s* P, const TreeView& T, double c_s, double c_
     int64_t cap_m2l = std::max<int64_t>(P->walk_cap_m2l, std::max<int64_t>(4096, 48 * P->n_nodes));
     int64_t cap_p2p = std::max<int64_t>(P->walk_cap_p2p, std::max<int64_t>(4096, 16 * P->n_nodes));
     if ((e = ensure(P->macn, (size_t)P->n_nodes * sizeof(MacNode)))) return e;
-    k_mac_nodes<<<grid_for(P->n_nodes), 256, 0, s>>>(T, c_s, c_t, P->macn.as<MacNode>()); count_launch();
+    k_mac_nodes<<<grid_for(P->n_nodes), 256, 0, s>>>(T, c_s, c_t, P->opt.sigma, P->macn.as<MacNode>()); count_launch();
     for (int attempt = 0; attempt < 8; ++attempt) {
         if ((e = ensure(P->fa, (size_t)cap_front * 8)) || (e = ensure(P->fb, (size_t)cap_front * 8)) ||
             (e = ensure(P->act, (size_t)cap_front)) ||
@@ -332,7 +341,8 @@ cudaError_t build_lists(sfmm_plan_s* P, const TreeView& T, double c_s, double c_
             int2* next = (r & 1) ? P->fa.as<int2>() : P->fb.as<int2>();
             int64_t* nf = ctr + ((r & 1) ? C_FRONT1 : C_FRONT0);
             int64_t* nn = ctr + ((r & 1) ? C_FRONT0 : C_FRONT1);
-            k_walk_classify<<<grid, WT, 0, s>>>(T, P->macn.as<MacNode>(), front, nf, c_s, P->act.as<uint8_t>(),
+            k_walk_classify<<<grid, WT, 0, s>>>(T, P->macn.as<MacNode>(), front, nf, c_s, P->opt.sigma,
+                                                P->act.as<uint8_t>(),
                                                 P->c_next.as<int3>());
             count_launch();
             k_walk_top<<<1, WT, 0, s>>>(P->c_next.as<int3>(), nf, nn, ctr, bases, caps); count_launch();

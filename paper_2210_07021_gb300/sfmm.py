@@ -28,7 +28,7 @@ class Options(ctypes.Structure):
     _fields_ = [("leaf_size", ctypes.c_int), ("c_s", ctypes.c_double), ("c_t", ctypes.c_double),
                 ("precision", ctypes.c_int), ("zero_mean", ctypes.c_int), ("q_f32", ctypes.c_int),
                 ("n_max", ctypes.c_int64), ("m_max", ctypes.c_int64), ("stream", ctypes.c_void_p),
-                ("m2l_tensor_cores", ctypes.c_int)]
+                ("m2l_tensor_cores", ctypes.c_int), ("sigma", ctypes.c_double)]
 
 
 class Stats(ctypes.Structure):
@@ -127,7 +127,7 @@ class Plan:
     """An sFMM plan (sfmm_plan): tree depth, order p (or a tolerance) and options."""
 
     def __init__(self, max_depth=29, p=0, tol=1e-10, leaf_size=32, c_s=2.0, c_t=0.5, precision=SFMM_FP64,
-                 zero_mean=False, q_f32=False, n_max=0, m_max=0, stream=None, m2l_tensor_cores=True):
+                 zero_mean=False, q_f32=False, n_max=0, m_max=0, stream=None, m2l_tensor_cores=True, sigma=0.0):
         L = load()
         o = Options()
         L.sfmm_default_options(ctypes.byref(o))
@@ -135,6 +135,7 @@ class Plan:
         o.precision, o.zero_mean, o.q_f32 = precision, int(bool(zero_mean)), int(bool(q_f32))
         o.n_max, o.m_max = n_max, m_max
         o.m2l_tensor_cores = int(bool(m2l_tensor_cores))
+        o.sigma = float(sigma)
         if stream is None:
             try:
                 import torch
