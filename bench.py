@@ -61,7 +61,8 @@ def parse():
     ap.add_argument("--check", type=int, default=200, help="targets checked against the oracle")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the oracle CPU baseline")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--no-adjoint", action="store_true", help="skip the gradient (adjoint) measurement")
+    ap.add_argument("--no-adjoint", action="store_true",
+                    help="skip the gradient, shear and Near Particle Model measurements")
     return ap.parse_args()
 
 
@@ -222,6 +223,42 @@ def run_shear(args, dev, clock_sampler):
             "clocks": clk.summary()}
 
 
+def run_npm(args, dev, clock_sampler):
+    """Near Particle Model solve (sigma = sqrt(4 pi / N), the paper's choice) on
+    the gradient workload's sky, FP64 path at p = 32; error vs the oracle's
+    NPM sum on a target sample."""
+    import torch
+    from paper_2210_07021_gb300 import sfmm, workloads
+    d = workloads.loss_sky()
+    N, M = d["src"].shape[0], d["tgt"].shape[0]
+    sigma = float(np.sqrt(4 * np.pi / N))
+    src = torch.as_tensor(d["src"], device=dev)
+    q = torch.as_tensor(d["q"], device=dev)
+    tgt = torch.as_tensor(d["tgt"], device=dev)
+    plan = sfmm.Plan(p=32, leaf_size=32, sigma=sigma, n_max=N, m_max=M)
+    for _ in range(args.warmup):
+        psi, alpha = plan.deflection(src, q, tgt)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with clock_sampler as clk:
+        ev0.record(torch.cuda.current_stream())
+        for _ in range(args.steps):
+            psi, alpha = plan.deflection(src, q, tgt)
+        ev1.record(torch.cuda.current_stream())
+        torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    from oracle.direct import direct_sum
+    idx = workloads.subsample(M, args.check, 7, stream=9)
+    ref = direct_sum(d["src"], d["q"], d["tgt"][idx], sigma=sigma)
+    plan.close()
+    return {"workload": d["workload"].split(", loss")[0], "N": N, "M": M, "sigma": sigma,
+            "path": "FP64, p=32, m=32, NPM near field", "ms_per_step": ms, "value": M * 1e-3 / ms,
+            "unit": "Mpts/s (targets per solve)",
+            "error_vs_oracle": {"psi_rel": rel(psi.cpu().numpy()[idx], ref["psi"]),
+                                "alpha_rel": rel(alpha.cpu().numpy()[idx], ref["alpha"]), "sample": int(idx.size)},
+            "clocks": clk.summary()}
+
+
 def oracle_rate(src, q, tgt, budget_s, seed_idx):
     """Targets per second of the oracle direct sum on the host cores, timed on
     a seeded sample sized to about budget_s seconds."""
@@ -372,10 +409,11 @@ def run_sfmm(args):
             dist.barrier()
         return
     head = results[wanted[0][0]]
-    adj = shr = None
+    adj = shr = npm = None
     if ws == 1 and not args.no_adjoint:
         adj = run_adjoint(args, dev, ClockSampler(local))
         shr = run_shear(args, dev, ClockSampler(local))
+        npm = run_npm(args, dev, ClockSampler(local))
     cpu = None
     if ws == 1:
         k, t, cores = oracle_rate(d["src"], d["q"], d["tgt"], args.cpu_seconds, 3)
@@ -416,7 +454,7 @@ def run_sfmm(args):
                        "l2": "inputs larger than L2 (384 MB of positions each), no flush"},
             "error_vs_oracle": head.get("error_vs_oracle"), "roofline": modes[head["precision"]]["roofline"],
             "cpu_baseline": cpu, "e2e": head.get("e2e"), "gpu_launches": head["gpu_launches"],
-            "phase_ms": head["phase_ms"], "clocks": head["clocks"], "adjoint": adj, "shear": shr,
+            "phase_ms": head["phase_ms"], "clocks": head["clocks"], "adjoint": adj, "shear": shr, "npm": npm,
             "modes": {k: {kk: vv for kk, vv in v.items() if kk not in ("phase_ms",)} for k, v in modes.items()}}
     if "fp64" in results and head["precision"] != "fp64":
         line["speedup_vs_fp64"] = head["value"] / results["fp64"]["value"]
