@@ -125,6 +125,24 @@ sfmm_status sfmm_deflection_host(sfmm_plan_t plan, const double* src_xyz, const 
                                  const double* tgt_xyz, int64_t M, double* psi, double* alpha);
 
 /*
+ * Batched shells (the multi-layer setting of Sec. 2.1: N_L independent
+ * lensing planes): shell i has its own sources src_xyz[i] [N[i]][3], masses
+ * q[i] and targets tgt_xyz[i] [M[i]][3]; results go to psi[i] (or psi == NULL
+ * / psi[i] == NULL for none) and alpha[i] [M[i]][2].  All pointers inside
+ * the arrays are device pointers; the arrays themselves are host arrays of
+ * n_shells entries.  The shells are solved with the plan's settings by
+ * `lanes` (1..8) internal solvers, each on its own stream driven by its own
+ * host thread, largest shells first, so that one shell's latency-bound
+ * phases (tree levels, list walk) overlap the kernels of another.  Work
+ * queued earlier on the plan's stream happens before, and work queued later
+ * after, all shells.  Each lane keeps a workspace sized for the largest shell
+ * it met.  On failure the first failing shell's status is returned.
+ */
+sfmm_status sfmm_deflection_batch(sfmm_plan_t plan, int n_shells, const double* const* src_xyz,
+                                  const void* const* q, const int64_t* N, const double* const* tgt_xyz,
+                                  const int64_t* M, double* const* psi, double* const* alpha, int lanes);
+
+/*
  * Shear (Sec. 2.2, Eq. GAM_DEF): gamma [M][2] = (gamma_1, gamma_2), the
  * trace-free part of the covariant Hessian of psi on (e_theta, e_phi) at each
  * target, gamma_1 = (H11 - H22)/2, gamma_2 = H12; psi and alpha as in

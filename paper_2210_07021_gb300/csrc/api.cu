@@ -4,6 +4,11 @@
 // (Lemma 4) -> L2P + near field (Sec. 3.6).  Every step runs on the device.
 #include "common.cuh"
 
+#include <algorithm>
+#include <string>
+#include <thread>
+#include <vector>
+
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -575,6 +580,85 @@ sfmm_status sfmm_deflection(sfmm_plan_t plan, const double* src_xyz, const void*
     return solve(plan, src_xyz, q, N, tgt_xyz, M, psi, alpha);
 }
 
+sfmm_status sfmm_deflection_batch(sfmm_plan_t plan, int n_shells, const double* const* src_xyz,
+                                  const void* const* q, const int64_t* N, const double* const* tgt_xyz,
+                                  const int64_t* M, double* const* psi, double* const* alpha, int lanes)
+{
+    if (!plan) return SFMM_EINVAL;
+    if (n_shells < 0) return fail(plan, SFMM_EINVAL, "n_shells must be >= 0");
+    if (n_shells == 0) return SFMM_OK;
+    if (!src_xyz || !q || !N || !tgt_xyz || !M || !alpha) return fail(plan, SFMM_EINVAL, "NULL array of shells");
+    for (int i = 0; i < n_shells; ++i) {
+        sfmm_status st = check_args(plan, src_xyz[i], q[i], N[i], tgt_xyz[i], M[i]);
+        if (st != SFMM_OK) return st;
+        if (M[i] > 0 && !alpha[i]) return fail(plan, SFMM_EINVAL, "alpha must be non-NULL for every shell with M > 0");
+    }
+    lanes = std::max(1, std::min(std::min(lanes, 8), n_shells));
+    cudaError_t e;
+    // lane solvers: the plan's settings, each on its own non-blocking stream
+    while ((int)plan->lanes.size() < lanes) {
+        sfmm_options o = plan->opt;
+        cudaStream_t st = nullptr;
+        if ((e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking))) return cuda_fail(plan, e, "lane stream");
+        o.stream = st;
+        o.n_max = o.m_max = 0;
+        sfmm_plan_t L = nullptr;
+        sfmm_status ps = sfmm_plan(&L, plan->max_depth, plan->p, plan->tol, &o);
+        if (ps != SFMM_OK) {
+            cudaStreamDestroy(st);
+            return fail(plan, ps, "could not create a batch lane");
+        }
+        L->owns_stream = true;
+        plan->lanes.push_back(L);
+    }
+    // the lanes start after the work already queued on the plan's stream
+    cudaEvent_t ev = nullptr;
+    if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) || (e = cudaEventRecord(ev, plan->stream)))
+        return cuda_fail(plan, e, "batch event");
+    for (int l = 0; l < lanes; ++l)
+        if ((e = cudaStreamWaitEvent(plan->lanes[l]->stream, ev, 0))) {
+            cudaEventDestroy(ev);
+            return cuda_fail(plan, e, "batch wait");
+        }
+    // largest shells first; each lane's host thread takes the next shell
+    std::vector<int> order(n_shells);
+    for (int i = 0; i < n_shells; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return N[a] + M[a] > N[b] + M[b]; });
+    std::atomic<int> next{0};
+    std::mutex mu;
+    sfmm_status first = SFMM_OK;
+    std::string msg;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    auto work = [&](sfmm_plan_s* L) {
+        cudaSetDevice(dev);
+        for (;;) {
+            const int k = next.fetch_add(1);
+            if (k >= n_shells) return;
+            const int i = order[k];
+            const sfmm_status st = solve(L, src_xyz[i], q[i], N[i], tgt_xyz[i], M[i], psi ? psi[i] : nullptr, alpha[i]);
+            if (st != SFMM_OK) {
+                std::lock_guard<std::mutex> g(mu);
+                if (first == SFMM_OK) { first = st; msg = "shell " + std::to_string(i) + ": " + L->err; }
+                next.store(n_shells);
+                return;
+            }
+        }
+    };
+    std::vector<std::thread> th;
+    for (int l = 1; l < lanes; ++l) th.emplace_back(work, plan->lanes[l]);
+    work(plan->lanes[0]);
+    for (auto& t : th) t.join();
+    // and the plan's stream continues after all of them
+    for (int l = 0; l < lanes; ++l) {
+        if ((e = cudaEventRecord(ev, plan->lanes[l]->stream)) || (e = cudaStreamWaitEvent(plan->stream, ev, 0))) break;
+    }
+    cudaEventDestroy(ev);
+    if (first != SFMM_OK) return fail(plan, first, msg.c_str());
+    if (e) return cuda_fail(plan, e, "batch join");
+    return SFMM_OK;
+}
+
 sfmm_status sfmm_shear(sfmm_plan_t plan, const double* src_xyz, const void* q, int64_t N, const double* tgt_xyz,
                        int64_t M, double* psi, double* alpha, double* gamma)
 {
@@ -659,6 +743,12 @@ void sfmm_destroy(sfmm_plan_t plan)
                   &plan->toff, &plan->dc, &plan->leftover, &plan->geom32, &plan->macn, &plan->logtab,
                   &plan->ttmp, &plan->dip4, &plan->adj_h, &plan->adj_g};
     if (plan->aux) cudaStreamSynchronize(plan->aux);
+    for (sfmm_plan_s* L : plan->lanes) sfmm_destroy(L);
+    plan->lanes.clear();
+    if (plan->owns_stream && plan->stream) {
+        cudaStreamSynchronize(plan->stream);
+        cudaStreamDestroy(plan->stream);
+    }
     for (Buf* b : all) release(*b);
     if (plan->ev_fork) cudaEventDestroy(plan->ev_fork);
     if (plan->ev_join) cudaEventDestroy(plan->ev_join);

@@ -89,6 +89,8 @@ struct sfmm_plan_s {
     sfmm_options opt{};
     cudaStream_t stream = nullptr;
     cudaStream_t aux = nullptr;            // target keys + sort run here, overlapping the source tree
+    bool owns_stream = false;              // a batch lane's own stream (destroyed with the plan)
+    std::vector<sfmm_plan_s*> lanes;       // batch lanes: solvers on their own streams
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     std::string err;
     bool timing = false;

@@ -18,7 +18,7 @@ SFMM_FP64, SFMM_MIXED, SFMM_MIXED_DF = 0, 1, 2
  ARR_NODE_GEOM, ARR_MULTIPOLE, ARR_LOCAL, ARR_M2L, ARR_P2P, ARR_TGT_KEYS, ARR_NODE_TRANGE) = range(14)
 
 EXPORTS = ["sfmm_default_options", "sfmm_plan", "sfmm_potential", "sfmm_deflection", "sfmm_deflection_host",
-           "sfmm_adjoint", "sfmm_shear",
+           "sfmm_adjoint", "sfmm_shear", "sfmm_deflection_batch",
            "sfmm_destroy", "sfmm_last_error", "sfmm_order", "sfmm_get_stats", "sfmm_set_timing",
            "sfmm_debug_copy", "sfmm_keys", "sfmm_sort_keys_static"]
 STATIC_SORT_MAX_N = 1 << 18
@@ -72,6 +72,9 @@ def load(build_if_missing=True):
     L.sfmm_deflection_host.restype = ci
     L.sfmm_adjoint.argtypes = [vp, vp, vp, i64, vp, i64, vp, vp, vp, vp]
     L.sfmm_adjoint.restype = ci
+    pp = ctypes.POINTER(ctypes.c_void_p)
+    L.sfmm_deflection_batch.argtypes = [vp, ci, pp, pp, ctypes.POINTER(i64), pp, ctypes.POINTER(i64), pp, pp, ci]
+    L.sfmm_deflection_batch.restype = ci
     L.sfmm_shear.argtypes = [vp, vp, vp, i64, vp, i64, vp, vp, vp]
     L.sfmm_shear.restype = ci
     L.sfmm_destroy.argtypes = [vp]
@@ -205,6 +208,32 @@ class Plan:
                                     _dptr(alpha, torch.float64, 2, "alpha"))
         _check(st, self._h)
         return (psi if with_psi else None), alpha
+
+    def deflection_batch(self, shells, with_psi=True, lanes=4):
+        """Solve independent shells [(src, q, tgt), ...] (device tensors) on
+        `lanes` concurrent internal solvers; returns [(psi or None, alpha), ...]."""
+        import torch
+        n = len(shells)
+        outs = []
+        V = ctypes.c_void_p * max(n, 1)
+        I = ctypes.c_int64 * max(n, 1)
+        a_src, a_q, a_tgt, a_psi, a_alpha = V(), V(), V(), V(), V()
+        a_n, a_m = I(), I()
+        for i, (src, q, tgt) in enumerate(shells):
+            M = tgt.shape[0]
+            alpha = torch.empty((M, 2), dtype=torch.float64, device=tgt.device)
+            psi = torch.empty(M, dtype=torch.float64, device=tgt.device) if with_psi else None
+            a_src[i] = _dptr(src, torch.float64, 3, "src")
+            a_q[i] = _dptr(q, self._qdtype(), None, "q")
+            a_tgt[i] = _dptr(tgt, torch.float64, 3, "tgt")
+            a_psi[i] = _dptr(psi, torch.float64, None, "psi") if with_psi else None
+            a_alpha[i] = _dptr(alpha, torch.float64, 2, "alpha")
+            a_n[i], a_m[i] = src.shape[0], M
+            outs.append((psi, alpha))
+        st = load().sfmm_deflection_batch(self._h, n, a_src, a_q, a_n, a_tgt, a_m, a_psi if with_psi else None,
+                                          a_alpha, lanes)
+        _check(st, self._h)
+        return outs
 
     def shear(self, src, q, tgt, with_psi=False, with_alpha=False):
         """(gamma [M, 2], psi or None, alpha or None) at the targets (FP64 path; see sfmm_shear)."""
