@@ -61,6 +61,8 @@ def parse():
     ap.add_argument("--check", type=int, default=200, help="targets checked against the oracle")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the oracle CPU baseline")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--shells", action="store_true",
+                    help="also time the batched-shell workload (64 shells, 9.3e7 sources; slow to generate)")
     ap.add_argument("--no-adjoint", action="store_true",
                     help="skip the gradient, shear and Near Particle Model measurements")
     return ap.parse_args()
@@ -259,6 +261,43 @@ def run_npm(args, dev, clock_sampler):
             "clocks": clk.summary()}
 
 
+def run_shells(args, dev, clock_sampler):
+    """Batched shells: every shell solved per step, with 4 concurrent lanes and
+    with 1 (sequential), for the 1e-6 and 1e-10 paths; error of one shell vs the
+    oracle on a target sample."""
+    import torch
+    from paper_2210_07021_gb300 import sfmm, workloads
+    d = workloads.shell_set()
+    tgt = torch.as_tensor(d["tgt"], device=dev)
+    sh = [(torch.as_tensor(s, device=dev), torch.as_tensor(q, device=dev), tgt) for s, q in d["shells"]]
+    M = tgt.shape[0]
+    out = {"workload": d["workload"], "n_shells": len(sh), "sum_N": int(d["sizes"].sum()), "M_per_shell": M}
+    from oracle.direct import direct_sum
+    big = int(np.argmax(d["sizes"]))
+    idx = workloads.subsample(M, min(args.check, 100), 8, stream=9)
+    for name, prec, kw in (("mixed", sfmm.SFMM_MIXED, dict(p=16, leaf_size=64, c_t=0.5)),
+                           ("mixed_df", sfmm.SFMM_MIXED_DF, dict(p=26, leaf_size=64, c_t=0.45))):
+        plan = sfmm.Plan(precision=prec, **kw)
+        for lanes in (4, 1):
+            outs = plan.deflection_batch(sh, with_psi=False, lanes=lanes)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            with clock_sampler as clk:
+                e0.record(torch.cuda.current_stream())
+                for _ in range(args.steps):
+                    outs = plan.deflection_batch(sh, with_psi=False, lanes=lanes)
+                e1.record(torch.cuda.current_stream())
+                torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / args.steps
+            out[f"{name}_lanes{lanes}"] = {"ms_per_step": ms, "value": len(sh) * M * 1e-3 / ms,
+                                           "unit": "Mpts/s (targets of all shells per step)", "clocks": clk.summary()}
+        ref = direct_sum(d["shells"][big][0], d["shells"][big][1], d["tgt"][idx])
+        out[f"{name}_error_vs_oracle"] = {"alpha_rel": rel(outs[big][1].cpu().numpy()[idx], ref["alpha"]),
+                                          "shell": big, "sample": int(idx.size)}
+        plan.close()
+    return out
+
+
 def oracle_rate(src, q, tgt, budget_s, seed_idx):
     """Targets per second of the oracle direct sum on the host cores, timed on
     a seeded sample sized to about budget_s seconds."""
@@ -409,11 +448,12 @@ def run_sfmm(args):
             dist.barrier()
         return
     head = results[wanted[0][0]]
-    adj = shr = npm = None
+    adj = shr = npm = shl = None
     if ws == 1 and not args.no_adjoint:
         adj = run_adjoint(args, dev, ClockSampler(local))
         shr = run_shear(args, dev, ClockSampler(local))
         npm = run_npm(args, dev, ClockSampler(local))
+    shl = run_shells(args, dev, ClockSampler(local)) if (ws == 1 and args.shells) else None
     cpu = None
     if ws == 1:
         k, t, cores = oracle_rate(d["src"], d["q"], d["tgt"], args.cpu_seconds, 3)
@@ -454,7 +494,7 @@ def run_sfmm(args):
                        "l2": "inputs larger than L2 (384 MB of positions each), no flush"},
             "error_vs_oracle": head.get("error_vs_oracle"), "roofline": modes[head["precision"]]["roofline"],
             "cpu_baseline": cpu, "e2e": head.get("e2e"), "gpu_launches": head["gpu_launches"],
-            "phase_ms": head["phase_ms"], "clocks": head["clocks"], "adjoint": adj, "shear": shr, "npm": npm,
+            "phase_ms": head["phase_ms"], "clocks": head["clocks"], "adjoint": adj, "shear": shr, "npm": npm, "shells": shl,
             "modes": {k: {kk: vv for kk, vv in v.items() if kk not in ("phase_ms",)} for k, v in modes.items()}}
     if "fp64" in results and head["precision"] != "fp64":
         line["speedup_vs_fp64"] = head["value"] / results["fp64"]["value"]
