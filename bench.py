@@ -38,8 +38,8 @@ FP32_PEAK_DERIVED = 152 * 128 * 2 * 2.07e9  # SMs x FP32 FMA/clk/SM x 2 flop x m
 # (path name, precision enum value, order p, stated relative error, leaf size m, c_s, c_t):
 # per path the fastest setting measured on the clustered 1.6e7 workload that keeps
 # the error vs the oracle well inside the stated error
-MODES = [("mixed", 1, 16, 1e-6, 64, 2.0, 0.5), ("mixed_df", 2, 26, 1e-10, 64, 2.0, 0.45),
-         ("fp64", 0, 32, 1e-10, 32, 2.0, 0.5)]
+MODES = [("mixed", 1, 16, 1e-6, 64, 2.0, 0.5), ("mixed_df", 2, 28, 1e-10, 64, 2.0, 0.45),
+         ("fp64", 0, 32, 1e-10, 64, 2.0, 0.45)]
 # algorithmic FP64 flops per near-field pair: d^2 (3 sub, 3 mul, 2 add), 1/d^2
 # (counted as 4), q/d^2 (1), alpha sums (3 mul + 3 add), sum q (1); psi adds the
 # log (counted as 4) and its multiply-add (2)
@@ -152,7 +152,7 @@ def run_adjoint(args, dev, clock_sampler):
     q = torch.as_tensor(d["q"], device=dev)
     tgt = torch.as_tensor(d["tgt"], device=dev)
     w = torch.as_tensor(d["w"], device=dev)
-    plan = sfmm.Plan(p=26, leaf_size=64, c_s=2.0, c_t=0.45, precision=sfmm.SFMM_MIXED_DF, n_max=max(N, M), m_max=max(N, M))
+    plan = sfmm.Plan(p=28, leaf_size=64, c_s=2.0, c_t=0.45, precision=sfmm.SFMM_MIXED_DF, n_max=max(N, M), m_max=max(N, M))
     psi, alpha = plan.deflection(src, q, tgt)
     s = float(torch.sqrt((alpha ** 2).mean()))
     a_ref = s * torch.as_tensor(d["xi"], device=dev)
@@ -183,7 +183,7 @@ def run_adjoint(args, dev, clock_sampler):
     rq, rs = oracle_adjoint(d["src"][idx], d["q"][idx], d["tgt"], g_alpha.cpu().numpy(), None)
     plan.close()
     ms = float(np.mean(t_f) + np.mean(t_b))
-    return {"workload": d["workload"], "N": N, "M": M, "forward": "mixed_df (stated 1e-10), p=26, m=64, c_t=0.45",
+    return {"workload": d["workload"], "N": N, "M": M, "forward": "mixed_df (stated 1e-10), p=28, m=64, c_t=0.45",
             "backward": "adjoint sFMM, FP64, same p and tree settings", "steps": args.steps,
             "ms_per_step": ms, "ms_forward": float(np.mean(t_f)), "ms_backward": float(np.mean(t_b)),
             "value": (N + M) * 1e-3 / ms, "unit": "Mpts/s (sources + targets per forward+backward step)",
@@ -202,7 +202,7 @@ def run_shear(args, dev, clock_sampler):
     src = torch.as_tensor(d["src"], device=dev)
     q = torch.as_tensor(d["q"], device=dev)
     tgt = torch.as_tensor(d["tgt"], device=dev)
-    plan = sfmm.Plan(p=32, leaf_size=32, n_max=N, m_max=M)
+    plan = sfmm.Plan(p=32, leaf_size=64, c_t=0.45, n_max=N, m_max=M)
     for _ in range(args.warmup):
         g, _, _ = plan.shear(src, q, tgt)
     torch.cuda.synchronize()
@@ -218,7 +218,7 @@ def run_shear(args, dev, clock_sampler):
     idx = workloads.subsample(M, args.check, 6, stream=9)
     ref = lensing(d["src"], d["q"], d["tgt"][idx])
     plan.close()
-    return {"workload": d["workload"].split(", loss")[0], "N": N, "M": M, "path": "FP64, p=32, m=32",
+    return {"workload": d["workload"].split(", loss")[0], "N": N, "M": M, "path": "FP64, p=32, m=64, c_t=0.45",
             "ms_per_step": ms, "value": M * 1e-3 / ms, "unit": "Mpts/s (targets per shear solve)",
             "error_vs_oracle": {"gamma_rel": rel(g.cpu().numpy()[idx], ref["gamma"]), "sample": int(idx.size),
                                 "stated": 1e-9},
@@ -237,7 +237,7 @@ def run_npm(args, dev, clock_sampler):
     src = torch.as_tensor(d["src"], device=dev)
     q = torch.as_tensor(d["q"], device=dev)
     tgt = torch.as_tensor(d["tgt"], device=dev)
-    plan = sfmm.Plan(p=32, leaf_size=32, sigma=sigma, n_max=N, m_max=M)
+    plan = sfmm.Plan(p=32, leaf_size=64, c_t=0.45, sigma=sigma, n_max=N, m_max=M)
     for _ in range(args.warmup):
         psi, alpha = plan.deflection(src, q, tgt)
     torch.cuda.synchronize()
@@ -254,7 +254,7 @@ def run_npm(args, dev, clock_sampler):
     ref = direct_sum(d["src"], d["q"], d["tgt"][idx], sigma=sigma)
     plan.close()
     return {"workload": d["workload"].split(", loss")[0], "N": N, "M": M, "sigma": sigma,
-            "path": "FP64, p=32, m=32, NPM near field", "ms_per_step": ms, "value": M * 1e-3 / ms,
+            "path": "FP64, p=32, m=64, c_t=0.45, NPM near field", "ms_per_step": ms, "value": M * 1e-3 / ms,
             "unit": "Mpts/s (targets per solve)",
             "error_vs_oracle": {"psi_rel": rel(psi.cpu().numpy()[idx], ref["psi"]),
                                 "alpha_rel": rel(alpha.cpu().numpy()[idx], ref["alpha"]), "sample": int(idx.size)},
@@ -276,7 +276,7 @@ def run_shells(args, dev, clock_sampler):
     big = int(np.argmax(d["sizes"]))
     idx = workloads.subsample(M, min(args.check, 100), 8, stream=9)
     for name, prec, kw in (("mixed", sfmm.SFMM_MIXED, dict(p=16, leaf_size=64, c_t=0.5)),
-                           ("mixed_df", sfmm.SFMM_MIXED_DF, dict(p=26, leaf_size=64, c_t=0.45))):
+                           ("mixed_df", sfmm.SFMM_MIXED_DF, dict(p=28, leaf_size=64, c_t=0.45))):
         plan = sfmm.Plan(precision=prec, **kw)
         for lanes in (4, 1):
             outs = plan.deflection_batch(sh, with_psi=False, lanes=lanes)
