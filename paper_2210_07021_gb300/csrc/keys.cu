@@ -14,15 +14,17 @@
 // with 1 - |z| = (x^2 + y^2)/(1 + |z|) in the caps.
 //
 // Fast path.  The same quantities are first computed in double-float
-// arithmetic on the FP32 pipe (about 46 significant bits; FP64 division and
-// square root on this GPU run at 1/64 of the FP32 rate): the ratio by a
-// double-float division, atan by a 33-entry table of atan(j/32) (rounded from
-// the host's FP64 atan) and atan(r) = r - r^3/3 + r^5/5 - r^7/7 for
-// |r| <= 1/64, then the equatorial or polar formula.  Every integer the key
+// arithmetic on the FP32 pipe (about 46 significant bits; FP64 arithmetic on
+// this GPU runs at 1/64 of the FP32 rate, so the fast path issues no FP64
+// instruction at all: the coordinates are split into (hi, lo) FP32 pairs and
+// compared through their bit patterns): the ratio by a double-float
+// division, atan by a 129-entry table of atan(j/128) (rounded from the host's
+// FP64 atan) and atan(r) = r - r^3/3 + r^5/5 - r^7/7 for |r| <= 1/256, then
+// the equatorial or polar formula.  Every integer the key
 // depends on is a floor of a non-negative value v (v = N_side (1/2 + tt -+ 3z/4),
 // N_side tp sqrt(3(1-|z|)), ..., and tt itself in the caps); the fast path keeps
 // floor(v) only when v lies at least KEY_MARGIN from an integer.  Both its own
-// error and that of the FP64 routine are below 2^-15 in these units, so the
+// error and that of the FP64 routine are below 2^-16 in these units, so the
 // floors then agree; otherwise the point takes the FP64 routine above.  The
 // keys are therefore those of the FP64 routine, bit for bit.
 #include "common.cuh"
@@ -124,7 +126,34 @@ __device__ __forceinline__ uint64_t key29(double x, double y, double z)
 }
 
 // ------------------------------------------------------------- fast path
-constexpr float KEY_MARGIN = 1.0f / 4096.0f;
+constexpr float KEY_MARGIN = 1.0f / 16384.0f;
+
+// Bit-pattern helpers: for finite doubles, |a| <= |b| exactly when the
+// patterns with the sign cleared compare so as unsigned integers.
+__device__ __forceinline__ uint64_t abs_bits(double v) { return (uint64_t)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFull; }
+__device__ __forceinline__ bool nonneg(double v)        // v >= 0.0 (true for -0.0 too)
+{
+    const uint64_t b = (uint64_t)__double_as_longlong(v);
+    return (b >> 63) == 0 || (b & 0x7FFFFFFFFFFFFFFFull) == 0;
+}
+// |v| as (hi, lo): hi = the leading 24 bits of the significand (truncated),
+// lo = the remaining 29 bits rounded to FP32 (relative error 2^-47), built
+// from the bit pattern without the FP64 pipe.  Values below 2^-60 give 0
+// (the callers only need them to 2^-60 absolute).
+__device__ __forceinline__ dflt dfl_abs_from_bits(uint64_t b)
+{
+    const int e = (int)(b >> 52) - 1023;
+    if (e < -60) return dflt(0.f, 0.f);
+    const uint64_t m = (b & 0x000FFFFFFFFFFFFFull) | 0x0010000000000000ull;
+    const float hi = __int_as_float(((e + 127) << 23) | (int)((m >> 29) & 0x7FFFFF));
+    const float lo = __fmul_rn(__int2float_rn((int)(m & 0x1FFFFFFF)), __int_as_float((e - 52 + 127) << 23));
+    return dflt(hi, lo);
+}
+__device__ __forceinline__ dflt dfl_from_bits(double v)
+{
+    const dflt a = dfl_abs_from_bits(abs_bits(v));
+    return nonneg(v) ? a : -a;
+}
 
 // floor of a double-float v >= 0 (|v| < 2^40); *ok = false when v is within
 // KEY_MARGIN of an integer
@@ -149,7 +178,7 @@ __device__ __forceinline__ dflt dfl_sqrt(dflt a)
 }
 
 struct KeyTables {
-    float4 atan_c[33];     // atan(j/32) as (hi, lo), then (unused, unused)
+    float4 atan_c[129];    // atan(j/128) as (hi, lo), then (unused, unused)
     float4 two_over_pi;    // 2/pi as (hi, lo)
 };
 
@@ -159,17 +188,17 @@ __device__ __forceinline__ uint64_t key29_fast(double x, double y, double z, con
 {
     const int64_t ns = int64_t(1) << ORDER_MAX;
     const float nside = (float)ns;
-    const double ax = fabs(x), ay = fabs(y);
-    const bool swap = ay > ax;
-    const double num = swap ? ax : ay, den = swap ? ay : ax;
+    const uint64_t bx = abs_bits(x), by = abs_bits(y);
+    const bool swap = by > bx;                                        // |y| > |x|
+    const uint64_t bnum = swap ? bx : by, bden = swap ? by : bx;
     dflt tt(0.f, 0.f);
     // within 2^-60 of the axis the float conversions lose the ratio: FP64 routine
-    if (den != 0.0 && den < 8.673617379884035e-19) { *ok = false; return 0; }
-    if (den != 0.0) {
-        const dflt T = dflt(num) / dflt(den);                       // t in [0, 1]
-        const int j = min(32, max(0, (int)__fadd_rn(__fmul_rn(T.h, 32.f), 0.5f)));
-        const float c = (float)j * (1.f / 32.f);
-        // r = (t - c) / (1 + t c), |r| <= 1/64: atan t = atan c + atan r
+    if (bden != 0 && bden < (uint64_t(1023 - 60) << 52)) { *ok = false; return 0; }
+    if (bden != 0) {
+        const dflt T = dfl_abs_from_bits(bnum) / dfl_abs_from_bits(bden);   // t in [0, 1]
+        const int j = min(128, max(0, (int)__fadd_rn(__fmul_rn(T.h, 128.f), 0.5f)));
+        const float c = (float)j * (1.f / 128.f);
+        // r = (t - c) / (1 + t c), |r| <= 1/256: atan t = atan c + atan r
         const dflt R = (T - dflt(c, 0.f)) / (dflt(1.f, 0.f) + T * c);
         const float rh = R.h, s2 = __fmul_rn(rh, rh);
         const float tail = __fmul_rn(__fmul_rn(rh, s2), -1.f / 3.f + s2 * (0.2f - s2 * (1.f / 7.f)));
@@ -177,7 +206,7 @@ __device__ __forceinline__ uint64_t key29_fast(double x, double y, double z, con
         const dflt A = dflt(a.x, a.y) + (R + dflt(tail, 0.f));
         const dflt u = A * dflt(kt.two_over_pi.x, kt.two_over_pi.y);   // quarter turns, [0, 1/2]
         const dflt v = swap ? dflt(1.f, 0.f) - u : u;
-        const bool xpos = x >= 0.0, ypos = y >= 0.0;
+        const bool xpos = nonneg(x), ypos = nonneg(y);
         if (xpos && ypos) tt = v;
         else if (!xpos && ypos) tt = dflt(2.f, 0.f) - v;
         else if (!xpos && !ypos) tt = dflt(2.f, 0.f) + v;
@@ -186,11 +215,11 @@ __device__ __forceinline__ uint64_t key29_fast(double x, double y, double z, con
         if (__fsub_rn(4.f, tt.h) < 1.f / 1073741824.f) *ok = false;
         if (tt.h >= 4.f) tt = tt - dflt(4.f, 0.f);
     }
-    const double za = fabs(z);
+    const uint64_t bz = abs_bits(z);
     int64_t face, ix, iy;
-    if (za <= 2.0 / 3.0) {
+    if (bz <= 0x3FE5555555555555ull) {                               // |z| <= 2/3 (the FP64 constant)
         const dflt W = dflt(0.5f, 0.f) + tt;
-        const dflt Z = dflt(z) * 0.75f;
+        const dflt Z = dfl_from_bits(z) * 0.75f;
         const int64_t jp = dfl_floor_checked((W - Z) * nside, ok);
         const int64_t jm = dfl_floor_checked((W + Z) * nside, ok);
         const int64_t ifp = jp >> ORDER_MAX, ifm = jm >> ORDER_MAX;
@@ -201,15 +230,15 @@ __device__ __forceinline__ uint64_t key29_fast(double x, double y, double z, con
         int64_t ntt = dfl_floor_checked(tt * nside, ok) >> ORDER_MAX;   // floor(tt), decided at N_side resolution
         if (ntt > 3) ntt = 3;
         const dflt tp = tt - dflt((float)ntt, 0.f);
-        const dflt X(x), Y(y);
-        const dflt one_m_za = (X * X + Y * Y) / (dflt(1.f, 0.f) + dflt(za));
+        const dflt X = dfl_abs_from_bits(bx), Y = dfl_abs_from_bits(by);
+        const dflt one_m_za = (X * X + Y * Y) / (dflt(1.f, 0.f) + dfl_abs_from_bits(bz));
         const dflt tmp = dfl_sqrt(one_m_za * 3.f) * nside;
         int64_t jp = dfl_floor_checked(tp * tmp, ok);
         int64_t jm = dfl_floor_checked((dflt(1.f, 0.f) - tp) * tmp, ok);
         if (jp > ns - 1) jp = ns - 1;
         if (jm > ns - 1) jm = ns - 1;
-        if (z > 0.0) { face = ntt; ix = ns - jm - 1; iy = ns - jp - 1; }
-        else         { face = ntt + 8; ix = jp; iy = jm; }
+        if (bz != 0 && nonneg(z)) { face = ntt; ix = ns - jm - 1; iy = ns - jp - 1; }   // z > 0
+        else                      { face = ntt + 8; ix = jp; iy = jm; }
     }
     return ((uint64_t)face << (2 * ORDER_MAX)) | spread_bits((uint64_t)ix) | (spread_bits((uint64_t)iy) << 1);
 }
@@ -230,8 +259,8 @@ __global__ void k_keys(const double* __restrict__ xyz, int64_t n, uint64_t* __re
 KeyTables make_key_tables()
 {
     KeyTables kt;
-    for (int j = 0; j <= 32; ++j) {
-        const double a = std::atan(j / 32.0);
+    for (int j = 0; j <= 128; ++j) {
+        const double a = std::atan(j / 128.0);
         const float h = (float)a;
         kt.atan_c[j] = make_float4(h, (float)(a - (double)h), 0.f, 0.f);
     }
