@@ -741,7 +741,7 @@ void sfmm_destroy(sfmm_plan_t plan)
                   &plan->p2p_t2, &plan->p2p_s2, &plan->m2l_off, &plan->p2p_off, &plan->leaves_src,
                   &plan->leaves_tgt, &plan->m2l_geo, &plan->m2m_geo, &plan->l2l_geo, &plan->soff,
                   &plan->toff, &plan->dc, &plan->leftover, &plan->geom32, &plan->macn, &plan->logtab,
-                  &plan->ttmp, &plan->dip4, &plan->adj_h, &plan->adj_g};
+                  &plan->ttmp, &plan->dip4, &plan->adj_h, &plan->adj_g, &plan->macn32};
     if (plan->aux) cudaStreamSynchronize(plan->aux);
     for (sfmm_plan_s* L : plan->lanes) sfmm_destroy(L);
     plan->lanes.clear();

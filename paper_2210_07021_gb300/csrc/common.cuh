@@ -120,6 +120,7 @@ struct sfmm_plan_s {
     sfmm::Buf logtab;                      // double-float evaluation: log(1 + j/128), 128/(128 + j), log 2
     sfmm::Buf geom32;                      // FP32 frame vectors and scale per node (mixed path)
     sfmm::Buf macn;                        // per-node sin/cos of the radii for the MAC
+    sfmm::Buf macn32;                      // the same in FP32 with the centre as (hi, lo) pairs (first decision)
     // lists
     sfmm::Buf fa, fb, act, c_next, c_m2l, c_p2p, o_next, o_m2l, o_p2p;
     sfmm::Buf m2l_t, m2l_s, m2l_t2, m2l_s2, p2p_t, p2p_s, p2p_t2, p2p_s2, m2l_off, p2p_off;

@@ -63,7 +63,16 @@ struct __align__(16) MacNode {
     double s1, c1, s2, c2, t2, R, s3, c3;
 };
 
-__global__ void k_mac_nodes(TreeView T, double c_s, double c_t, double sigma, MacNode* __restrict__ out)
+// FP32 copy for the walk's first decision: centre as (hi, lo) pairs (so that
+// centre differences keep their relative accuracy), sines and cosines,
+// counts and the first child, in one 64-byte record.
+struct __align__(64) MacNode32 {
+    float hx, hy, hz, lx, ly, lz, s1, c1, s2, c2, t2, R;
+    int count, tcount, child0, pad;
+};
+
+__global__ void k_mac_nodes(TreeView T, double c_s, double c_t, double sigma, MacNode* __restrict__ out,
+                            MacNode32* __restrict__ out32)
 {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < T.n_nodes; i += (int64_t)gridDim.x * blockDim.x) {
         const double R = T.geom[(size_t)i * GEOM_STRIDE + 9];
@@ -75,11 +84,19 @@ __global__ void k_mac_nodes(TreeView T, double c_s, double c_t, double sigma, Ma
         m.R = R;
         sincos(0.5 * (R + sigma), &m.s3, &m.c3);
         out[i] = m;
+        const double* g = T.geom + (size_t)i * GEOM_STRIDE;
+        MacNode32 f;
+        f.hx = (float)g[0]; f.hy = (float)g[1]; f.hz = (float)g[2];
+        f.lx = (float)(g[0] - (double)f.hx); f.ly = (float)(g[1] - (double)f.hy); f.lz = (float)(g[2] - (double)f.hz);
+        f.s1 = (float)m.s1; f.c1 = (float)m.c1; f.s2 = (float)m.s2; f.c2 = (float)m.c2;
+        f.t2 = (float)m.t2; f.R = (float)R;
+        f.count = T.count[i]; f.tcount = T.tcount[i]; f.child0 = T.child0[i]; f.pad = 0;
+        out32[i] = f;
     }
 }
 
-__device__ __forceinline__ uint8_t classify(const TreeView& T, const MacNode* __restrict__ mac, int s, int t,
-                                            double c_s, double sigma)
+__device__ __forceinline__ uint8_t classify64(const TreeView& T, const MacNode* __restrict__ mac, int s, int t,
+                                              double c_s, double sigma)
 {
     if (T.count[s] == 0 || T.tcount[t] == 0) return A_DROP;
     const bool ls = T.child0[s] < 0, lt = T.child0[t] < 0;
@@ -100,6 +117,40 @@ __device__ __forceinline__ uint8_t classify(const TreeView& T, const MacNode* __
     }
     if (mac1 && mac2 && mac3) return A_M2L;
     if (!ls && !lt) return (Rs > Rt * (1.0 + RADIUS_TIE)) ? A_SPLIT_S : A_SPLIT_T;
+    if (!ls) return A_SPLIT_S;
+    if (!lt) return A_SPLIT_T;
+    return A_P2P;
+}
+
+// The decision of classify64, taken in FP32 when every comparison it rests on
+// has a relative margin of at least 1e-5 (the FP32 quantities are accurate to
+// a few 1e-7: centre differences from (hi, lo) pairs, rounded sines and
+// cosines), else by classify64 itself, so the outcome is classify64's.  The
+// classification is otherwise bound by the FP64 pipe, which this GPU runs at
+// 1/64 of the FP32 rate.
+__device__ __forceinline__ uint8_t classify(const TreeView& T, const MacNode* __restrict__ mac,
+                                            const MacNode32* __restrict__ mac32, int s, int t, double c_s,
+                                            double sigma)
+{
+    const MacNode32 a = mac32[s], b = mac32[t];
+    if (a.count == 0 || b.tcount == 0) return A_DROP;
+    const bool ls = a.child0 < 0, lt = b.child0 < 0;
+    if (s == t) return ls ? A_LEAFSELF : A_SELF;
+    if (sigma > 0.0) return classify64(T, mac, s, t, c_s, sigma);
+    constexpr float EPS = 1e-5f;
+    const float dx = (a.hx - b.hx) + (a.lx - b.lx), dy = (a.hy - b.hy) + (a.ly - b.ly), dz = (a.hz - b.hz) + (a.lz - b.lz);
+    const float k2 = dx * dx + dy * dy + dz * dz;
+    const float thr1 = 2.f * (b.s1 * a.c2 + b.c1 * a.s2);
+    const float th2 = thr1 * thr1, t22 = b.t2 * b.t2;
+    const float sum1 = b.R + (float)c_s * a.R;
+    const float pi = 3.14159265f;
+    if (fabsf(k2 - th2) <= EPS * (k2 + th2) || fabsf(k2 - t22) <= EPS * (k2 + t22) || fabsf(sum1 - pi) <= EPS * pi)
+        return classify64(T, mac, s, t, c_s, sigma);
+    if (sum1 < pi && k2 > th2 && k2 > t22) return A_M2L;
+    if (!ls && !lt) {
+        if (fabsf(a.R - b.R) <= EPS * b.R) return classify64(T, mac, s, t, c_s, sigma);
+        return a.R > b.R ? A_SPLIT_S : A_SPLIT_T;
+    }
     if (!ls) return A_SPLIT_S;
     if (!lt) return A_SPLIT_T;
     return A_P2P;
@@ -156,6 +207,7 @@ __global__ void k_init_frontier(int2* f, int64_t* ctr)
 }
 
 __global__ void __launch_bounds__(WT) k_walk_classify(TreeView T, const MacNode* __restrict__ mac,
+                                                      const MacNode32* __restrict__ mac32,
                                                       const int2* __restrict__ front,
                                                       const int64_t* __restrict__ n_front_p, double c_s, double sigma,
                                                       uint8_t* __restrict__ act, int3* __restrict__ tile_sums)
@@ -170,7 +222,7 @@ __global__ void __launch_bounds__(WT) k_walk_classify(TreeView T, const MacNode*
             const int64_t i = tile * WTILE + (int64_t)r * WT + threadIdx.x;
             if (i < n) {
                 const int2 pr = front[i];
-                const uint8_t a = classify(T, mac, pr.x, pr.y, c_s, sigma);
+                const uint8_t a = classify(T, mac, mac32, pr.x, pr.y, c_s, sigma);
                 act[i] = a;
                 acc = add3(acc, counts_of(a));
             }
@@ -324,8 +376,12 @@ cudaError_t build_lists(sfmm_plan_s* P, const TreeView& T, double c_s, double c_
     int64_t cap_front = std::max<int64_t>(P->walk_cap_front, std::max<int64_t>(4096, 32 * P->n_nodes));
     int64_t cap_m2l = std::max<int64_t>(P->walk_cap_m2l, std::max<int64_t>(4096, 48 * P->n_nodes));
     int64_t cap_p2p = std::max<int64_t>(P->walk_cap_p2p, std::max<int64_t>(4096, 16 * P->n_nodes));
-    if ((e = ensure(P->macn, (size_t)P->n_nodes * sizeof(MacNode)))) return e;
-    k_mac_nodes<<<grid_for(P->n_nodes), 256, 0, s>>>(T, c_s, c_t, P->opt.sigma, P->macn.as<MacNode>()); count_launch();
+    if ((e = ensure(P->macn, (size_t)P->n_nodes * sizeof(MacNode))) ||
+        (e = ensure(P->macn32, (size_t)P->n_nodes * sizeof(MacNode32))))
+        return e;
+    k_mac_nodes<<<grid_for(P->n_nodes), 256, 0, s>>>(T, c_s, c_t, P->opt.sigma, P->macn.as<MacNode>(),
+                                                     P->macn32.as<MacNode32>());
+    count_launch();
     for (int attempt = 0; attempt < 8; ++attempt) {
         if ((e = ensure(P->fa, (size_t)cap_front * 8)) || (e = ensure(P->fb, (size_t)cap_front * 8)) ||
             (e = ensure(P->act, (size_t)cap_front)) ||
@@ -341,7 +397,8 @@ cudaError_t build_lists(sfmm_plan_s* P, const TreeView& T, double c_s, double c_
             int2* next = (r & 1) ? P->fa.as<int2>() : P->fb.as<int2>();
             int64_t* nf = ctr + ((r & 1) ? C_FRONT1 : C_FRONT0);
             int64_t* nn = ctr + ((r & 1) ? C_FRONT0 : C_FRONT1);
-            k_walk_classify<<<grid, WT, 0, s>>>(T, P->macn.as<MacNode>(), front, nf, c_s, P->opt.sigma,
+            k_walk_classify<<<grid, WT, 0, s>>>(T, P->macn.as<MacNode>(), P->macn32.as<MacNode32>(), front, nf, c_s,
+                                                P->opt.sigma,
                                                 P->act.as<uint8_t>(),
                                                 P->c_next.as<int3>());
             count_launch();
