@@ -38,7 +38,7 @@ FP32_PEAK_DERIVED = 152 * 128 * 2 * 2.07e9  # SMs x FP32 FMA/clk/SM x 2 flop x m
 # (path name, precision enum value, order p, stated relative error, leaf size m, c_s, c_t):
 # per path the fastest setting measured on the clustered 1.6e7 workload that keeps
 # the error vs the oracle well inside the stated error
-MODES = [("mixed", 1, 16, 1e-6, 64, 2.0, 0.5), ("mixed_df", 2, 28, 1e-10, 64, 2.0, 0.45),
+MODES = [("mixed", 1, 20, 1e-6, 64, 1.3, 0.5), ("mixed_df", 2, 28, 1e-10, 64, 2.0, 0.45),
          ("fp64", 0, 32, 1e-10, 64, 2.0, 0.45)]
 # algorithmic FP64 flops per near-field pair: d^2 (3 sub, 3 mul, 2 add), 1/d^2
 # (counted as 4), q/d^2 (1), alpha sums (3 mul + 3 add), sum q (1); psi adds the
@@ -275,7 +275,7 @@ def run_shells(args, dev, clock_sampler):
     from oracle.direct import direct_sum
     big = int(np.argmax(d["sizes"]))
     idx = workloads.subsample(M, min(args.check, 100), 8, stream=9)
-    for name, prec, kw in (("mixed", sfmm.SFMM_MIXED, dict(p=16, leaf_size=64, c_t=0.5)),
+    for name, prec, kw in (("mixed", sfmm.SFMM_MIXED, dict(p=20, leaf_size=64, c_s=1.3, c_t=0.5)),
                            ("mixed_df", sfmm.SFMM_MIXED_DF, dict(p=28, leaf_size=64, c_t=0.45))):
         plan = sfmm.Plan(precision=prec, **kw)
         for lanes in (4, 1):

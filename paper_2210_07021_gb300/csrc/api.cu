@@ -40,7 +40,7 @@ cudaError_t launch_m2l_list(const uint64_t* ptgt, const uint32_t* psrc, const ui
                             void* local, cudaStream_t s);
 cudaError_t launch_m2l_tc(int64_t n_pairs, const uint64_t* ptgt, const uint32_t* psrc, const void* geo,
                           const void* mpole, void* local, int p, uint32_t* leftover, uint32_t* n_leftover,
-                          int* status, cudaStream_t s);
+                          uint32_t* tile_ctr, int* status, cudaStream_t s);
 cudaError_t launch_l2l(const TreeView& T, int a, int b, int p, const double* tables, const void* geo, void* local,
                        int ek, cudaStream_t s);
 cudaError_t launch_unscale(int n_nodes, const double* geom, const void* in, double* out, int p, int is_local,
@@ -380,10 +380,11 @@ sfmm_status solve(sfmm_plan_s* P, const double* src, const void* q, int64_t N, c
     if (fp32 && P->opt.m2l_tensor_cores) {
         // tensor-core M2L; pairs it cannot take (centres near antipodes) go to a list for the warp kernel
         uint32_t* n_left = reinterpret_cast<uint32_t*>(P->small.as<int64_t>() + 21);
+        uint32_t* tile_ctr = n_left + 1;              // zeroed by the same memset
         if ((e = ensure(P->leftover, (size_t)std::max<int64_t>(P->n_m2l, 1) * 4))) return cuda_fail(P, e, "alloc");
         if ((e = cudaMemsetAsync(P->small.as<int64_t>() + 20, 0, 16, s))) return cuda_fail(P, e, "memset");
         if ((e = launch_m2l_tc(P->n_m2l, m2l_t, m2l_s, P->m2l_geo.p, P->mpole.p, P->local.p, p, P->leftover.as<uint32_t>(),
-                               n_left, status, s)))
+                               n_left, tile_ctr, status, s)))
             return cuda_fail(P, e, "M2L (tensor cores)");
         if ((e = launch_m2l_list(m2l_t, m2l_s, P->leftover.as<uint32_t>(), n_left, P->n_m2l, p, P->tables.as<double>(),
                                  P->m2l_geo.p, P->mpole.p, P->local.p, s)))

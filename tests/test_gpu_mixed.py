@@ -82,7 +82,7 @@ def test_mixed_float32_masses_zero_mean():
     assert rel(alpha, ref["alpha"]) < TOL_MIXED
 
 
-@pytest.mark.parametrize("p", [12, 16, 24, 32])
+@pytest.mark.parametrize("p", [6, 12, 16, 20, 24, 27, 32])
 def test_tensor_core_m2l_matches_warp_kernel(p):
     """The tcgen05 M2L (split-BF16 GEMMs, FP32 accumulation) and the FP32 warp
     kernel produce the same local expansions and results to FP32 accuracy."""
