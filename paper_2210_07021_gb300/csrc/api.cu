@@ -51,7 +51,7 @@ cudaError_t launch_eval32_prep(const TreeView& T, const int* leaves, int64_t n_l
 cudaError_t launch_eval32(const TreeView& T, const int* leaves, int64_t n_leaves, const float4* soff,
                           const float4* toff, const float4* dc, const double4_32a* tgt, const uint32_t* tperm, const int64_t* p2p_off,
                           const uint32_t* p2p_src, const float* local, const float* mpole, int p, int zero_mean,
-                          double* psi, double* alpha, cudaStream_t s);
+                          double* psi, double* alpha, bool coincide, cudaStream_t s);
 cudaError_t launch_count_pairs(const TreeView& T, const int* leaves, int64_t n_leaves, const int64_t* p2p_off,
                                const uint32_t* p2p_src, unsigned long long* out, cudaStream_t s);
 void fill_log_table(float* out);
@@ -416,7 +416,8 @@ sfmm_status solve(sfmm_plan_s* P, const double* src, const void* q, int64_t N, c
                                  adj->w_f32, psi, adj->grad3, s);
     else if (fp32) e = launch_eval32(T, P->leaves_tgt.as<int>(), P->n_leaves_tgt, P->soff.as<float4>(),
                                 P->toff.as<float4>(), P->dc.as<float4>(), P->tgt4.as<double4_32a>(), tperm, P->p2p_off.as<int64_t>(), p2p_s,
-                                P->local.as<float>(), P->mpole.as<float>(), p, P->opt.zero_mean, psi, alpha, s);
+                                P->local.as<float>(), P->mpole.as<float>(), p, P->opt.zero_mean, psi, alpha,
+                                src == tgt, s);
     else if (dfe) e = launch_eval_df(T, P->leaves_tgt.as<int>(), P->n_leaves_tgt, P->soff.as<float4>(),
                                      P->toff.as<float4>(), P->dc.as<float4>(), P->tgt4.as<double4_32a>(), tperm,
                                      P->p2p_off.as<int64_t>(), p2p_s, P->local.p, P->mpole.p,

@@ -409,31 +409,66 @@ __device__ __forceinline__ void two_sum(float a, float b, float* s, float* e)
 }
 
 // Near-field sums of one target over the staged sources j = sub, sub + lpt, ...:
-// blocks of (up to) 16 pairs per lane in FP32, then the outer FP32 level.
+// blocks of (up to) 16 pairs per lane in FP32, then the outer FP32 level.  The
+// logarithm is accumulated in base 2 (acc[4] = sum q log2 d^2).
+//
+// A source at the target's own position (d^2 = 0) is left out.  The masked
+// block tests every pair for it; the plain block does not: there 1/d^2 = inf
+// and its x sum turns inf or NaN (d = 0 gives inf * 0), so a plain block whose
+// x sum is not finite is summed again masked.  When the targets are the
+// sources themselves every target meets one such block; there (MASK) every
+// block is masked.
 template <bool PSI>
+__device__ __forceinline__ void masked_pair(const float4& h, const float4& l, const float4& th, const float4& tl,
+                                            float& ix, float& iy, float& iz, float& iq, float& il)
+{
+    const float dx = (th.x - h.x) + (tl.x - l.x);
+    const float dy = (th.y - h.y) + (tl.y - l.y);
+    const float dz = (th.z - h.z) + (tl.z - l.z);
+    const float d2 = dx * dx + dy * dy + dz * dz;
+    const bool ok = d2 > 0.f;
+    const float q = ok ? h.w : 0.f;
+    const float den = ok ? d2 : 1.f;
+    const float wq = __fdividef(q, den);
+    ix += wq * dx;
+    iy += wq * dy;
+    iz += wq * dz;
+    iq += q;
+    if (PSI) il += q * __log2f(den);
+}
+
+template <bool PSI, bool MASK>
 __device__ __forceinline__ void pair_sums32(const float4* __restrict__ yh, const float4* __restrict__ yl, int ns,
                                             int sub, int lpt, const float4& th, const float4& tl, float* acc)
 {
     for (int j = sub; j < ns;) {
         const int jend = min(ns, j + 16 * lpt);
         float ix = 0.f, iy = 0.f, iz = 0.f, iq = 0.f, il = 0.f;   // inner FP32 level
+        if (MASK) {
 #pragma unroll 4
-        for (; j < jend; j += lpt) {
-            const float4 h = yh[j];
-            const float4 l = yl[j];
-            const float dx = (th.x - h.x) + (tl.x - l.x);
-            const float dy = (th.y - h.y) + (tl.y - l.y);
-            const float dz = (th.z - h.z) + (tl.z - l.z);
-            const float d2 = dx * dx + dy * dy + dz * dz;
-            const bool ok = d2 > 0.f;
-            const float q = ok ? h.w : 0.f;
-            const float den = ok ? d2 : 1.f;
-            const float wq = __fdividef(q, den);
-            ix += wq * dx;
-            iy += wq * dy;
-            iz += wq * dz;
-            iq += q;
-            if (PSI) il += q * __logf(den);
+            for (; j < jend; j += lpt) masked_pair<PSI>(yh[j], yl[j], th, tl, ix, iy, iz, iq, il);
+        } else {
+            const int j0 = j;
+#pragma unroll 4
+            for (; j < jend; j += lpt) {
+                const float4 h = yh[j];
+                const float4 l = yl[j];
+                const float dx = (th.x - h.x) + (tl.x - l.x);
+                const float dy = (th.y - h.y) + (tl.y - l.y);
+                const float dz = (th.z - h.z) + (tl.z - l.z);
+                const float d2 = dx * dx + dy * dy + dz * dz;
+                const float wq = __fdividef(h.w, d2);
+                ix += wq * dx;
+                iy += wq * dy;
+                iz += wq * dz;
+                iq += h.w;
+                if (PSI) il += h.w * __log2f(d2);
+            }
+            if (!(fabsf(ix) < INFINITY)) {
+                ix = 0.f; iy = 0.f; iz = 0.f; iq = 0.f; il = 0.f;
+#pragma unroll 1
+                for (int jj = j0; jj < jend; jj += lpt) masked_pair<PSI>(yh[jj], yl[jj], th, tl, ix, iy, iz, iq, il);
+            }
         }
         acc[0] += ix; acc[1] += iy; acc[2] += iz; acc[3] += iq; acc[4] += il;
     }
@@ -494,7 +529,7 @@ __device__ __forceinline__ void finish_target32(const Eval32Args& A, const LeafF
     }
     if (PSI) {
         const double psi_e = (double)L[0] + (double)L[1] * (LOG2 + (double)log1pf(-0.25f * D2)) + 2.0 * (double)Fx;
-        A.psi[o] = psi_e + INV4PI * ((double)ol - LOG4 * (double)oq) + shift;
+        A.psi[o] = psi_e + INV4PI * (LOG2 * (double)ol - LOG4 * (double)oq) + shift;
     }
 }
 
@@ -503,7 +538,7 @@ __device__ __forceinline__ void finish_target32(const Eval32Args& A, const LeafF
 // once: group a takes the largest power of two <= the targets left (at most
 // 32), group b the power of two >= what a leaves (at most 32), e.g. 18 = 16 + 2
 // and 40 = 32 + 8; each target of a group gets 32/size lanes.
-template <bool PSI>
+template <bool PSI, bool MASK>
 __global__ void __launch_bounds__(128, 7) k_eval32(Eval32Args A)
 {
     __shared__ float4 s_hi[4][STAGE32];
@@ -603,8 +638,8 @@ __global__ void __launch_bounds__(128, 7) k_eval32(Eval32Args A)
                 if (nfit == 0) jn += STAGE32;
                 else { kn += nfit; jn = 0; }
                 __syncwarp();
-                pair_sums32<PSI>(yh, yl, ns, sa, lpa, tha, tla, acc_a);
-                if (nb) pair_sums32<PSI>(yh, yl, ns, sb, lpb, thb, tlb, acc_b);
+                pair_sums32<PSI, MASK>(yh, yl, ns, sa, lpa, tha, tla, acc_a);
+                if (nb) pair_sums32<PSI, MASK>(yh, yl, ns, sb, lpb, thb, tlb, acc_b);
             }
 #pragma unroll
             for (int c = 0; c < 5; ++c) {
@@ -895,7 +930,7 @@ cudaError_t launch_eval32_prep(const TreeView& T, const int* leaves, int64_t n_l
 cudaError_t launch_eval32(const TreeView& T, const int* leaves, int64_t n_leaves, const float4* soff,
                           const float4* toff, const float4* dc, const double4_32a* tgt, const uint32_t* tperm, const int64_t* p2p_off,
                           const uint32_t* p2p_src, const float* local, const float* mpole, int p, int zero_mean,
-                          double* psi, double* alpha, cudaStream_t s)
+                          double* psi, double* alpha, bool coincide, cudaStream_t s)
 {
     if (n_leaves == 0) return cudaSuccess;
     Eval32Args A;
@@ -918,8 +953,13 @@ cudaError_t launch_eval32(const TreeView& T, const int* leaves, int64_t n_leaves
     A.alpha = alpha;
     int64_t blocks = (n_leaves + 3) / 4;
     if (blocks > 152 * 64) blocks = 152 * 64;
-    if (psi) k_eval32<true><<<(unsigned)blocks, 128, 0, s>>>(A);
-    else k_eval32<false><<<(unsigned)blocks, 128, 0, s>>>(A);
+    if (coincide) {
+        if (psi) k_eval32<true, true><<<(unsigned)blocks, 128, 0, s>>>(A);
+        else k_eval32<false, true><<<(unsigned)blocks, 128, 0, s>>>(A);
+    } else {
+        if (psi) k_eval32<true, false><<<(unsigned)blocks, 128, 0, s>>>(A);
+        else k_eval32<false, false><<<(unsigned)blocks, 128, 0, s>>>(A);
+    }
     count_launch();
     return cudaGetLastError();
 }

@@ -71,6 +71,25 @@ def test_mixed_coincident_points_and_poles():
     assert rel(psi, ref["psi"]) < TOL_MIXED and rel(alpha, ref["alpha"]) < TOL_MIXED
 
 
+def test_mixed_targets_are_the_sources_same_or_copied_array():
+    """Targets that are the sources: passed as the very same array the pair loop
+    tests every pair for d = 0; passed as a copy it finds each target's own
+    source by the non-finite block sum and sums that block again.  Both agree
+    with each other and with the oracle (which leaves out d = 0)."""
+    d = workloads.random_sky(4096, config_index=11)
+    plan = sfmm.Plan(p=20, leaf_size=32, precision=sfmm.SFMM_MIXED, c_s=1.3)
+    x, q = dev(d["src"]), dev(d["q"])
+    psi_s, al_s = plan.deflection(x, q, x)
+    psi_c, al_c = plan.deflection(x, q, x.clone())
+    torch.cuda.synchronize()
+    psi_s, al_s, psi_c, al_c = (t.cpu().numpy() for t in (psi_s, al_s, psi_c, al_c))
+    assert np.all(np.isfinite(psi_c)) and np.all(np.isfinite(al_c))
+    assert rel(psi_s, psi_c) < 1e-12 and rel(al_s, al_c) < 1e-12
+    ref = direct_sum(d["src"], d["q"], d["src"])
+    for psi, al in ((psi_s, al_s), (psi_c, al_c)):
+        assert rel(psi, ref["psi"]) < TOL_MIXED and rel(al, ref["alpha"]) < TOL_MIXED
+
+
 def test_mixed_float32_masses_zero_mean():
     rng = np.random.default_rng(10)
     src = workloads.clustered(rng, 30000, 20)
