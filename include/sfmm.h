@@ -230,12 +230,16 @@ sfmm_status sfmm_set_timing(sfmm_plan_t plan, int on);
  *   SFMM_ARR_P2P           int32  [n_p2p][2]  (source leaf, target leaf) grouped by target
  *   SFMM_ARR_TGT_KEYS      uint64 [M]      sorted keys of the targets
  *   SFMM_ARR_NODE_TRANGE   int32  [nodes][2]  first, count in the sorted targets
+ *   SFMM_ARR_SRC_OFFSETS   float  [N][8]   (SFMM_MIXED / SFMM_MIXED_DF only; else 0 bytes) per sorted
+ *                                          source: hi x, y, z, q, then lo x, y, z, q of its offset from
+ *                                          its leaf's centre and of its mass (value = hi + lo)
+ *   SFMM_ARR_TGT_OFFSETS   float  [M][8]   (as above) per sorted target: hi x, y, z, 0, lo x, y, z, 0
  */
 enum {
     SFMM_ARR_SRC_KEYS = 0, SFMM_ARR_SRC_PERM, SFMM_ARR_NODE_PREFIX, SFMM_ARR_NODE_LEVEL,
     SFMM_ARR_NODE_RANGE, SFMM_ARR_NODE_CHILD0, SFMM_ARR_NODE_PARENT, SFMM_ARR_NODE_GEOM,
     SFMM_ARR_MULTIPOLE, SFMM_ARR_LOCAL, SFMM_ARR_M2L, SFMM_ARR_P2P, SFMM_ARR_TGT_KEYS,
-    SFMM_ARR_NODE_TRANGE
+    SFMM_ARR_NODE_TRANGE, SFMM_ARR_SRC_OFFSETS, SFMM_ARR_TGT_OFFSETS
 };
 sfmm_status sfmm_debug_copy(sfmm_plan_t plan, int which, void* dst, int64_t bytes, int64_t* bytes_needed);
 

@@ -806,6 +806,14 @@ sfmm_status sfmm_debug_copy(sfmm_plan_t plan, int which, void* dst, int64_t byte
     case SFMM_ARR_MULTIPOLE: case SFMM_ARR_LOCAL: need = nn * (2 * p + 2) * 8; break;
     case SFMM_ARR_M2L: need = P->n_m2l * 8; break;
     case SFMM_ARR_P2P: need = P->n_p2p * 8; break;
+    case SFMM_ARR_SRC_OFFSETS:
+        srcp = P->soff.p;
+        need = P->opt.precision == SFMM_FP64 || !srcp ? 0 : N * 32;
+        break;
+    case SFMM_ARR_TGT_OFFSETS:
+        srcp = P->toff.p;
+        need = P->opt.precision == SFMM_FP64 || !srcp ? 0 : M * 32;
+        break;
     default: return fail(P, SFMM_EINVAL, "unknown array");
     }
     if (bytes_needed) *bytes_needed = need;

@@ -124,6 +124,60 @@ __device__ __forceinline__ dflt dfl_log_lazy(dflt x, const float4* __restrict__ 
     return dflt(s2.h, lo);
 }
 
+// The float m 2^e for an integer 2^23 <= m < 2^24, built from its bits; zero
+// (with the sign) below the normal range.
+__device__ __forceinline__ float dfl_float_m24(uint32_t m, int e, uint32_t sign)
+{
+    const int be = e + 23 + 127;
+    if (m == 0u || be <= 0) return __uint_as_float(sign);
+    return __uint_as_float(sign | ((uint32_t)be << 23) | (m & 0x7FFFFFu));
+}
+
+// a - b for FP64 a, b as a normalised double-float, with integer and FP32
+// instructions only (this GPU's FP64 pipe issues 1/64 of the FP32 rate, so
+// bulk conversions of FP64 data are faster this way).  The mantissas are
+// brought to the larger exponent lowered by up to 9 bits; their difference is
+// then exact in a 64-bit integer unless the exponents differ by more than 9,
+// when the smaller operand is below 2^-9 of the larger and the bits shifted
+// out lie under 2^-61 of the result.  The leading 24 bits of the difference
+// give hi, the next 24 lo, and a fast two-sum rounds the pair to normal form:
+// hi + lo equals a - b to 2^-47 relative (exactly when it has <= 48 bits, e.g.
+// a point and a box centre 2^-5 apart on the unit sphere), up to an absolute
+// 2^-126: parts below the normal range are flushed to zero.
+__device__ __forceinline__ dflt dfl_sub_exact(double a, double b)
+{
+    const long long ua = __double_as_longlong(a), ub = __double_as_longlong(b);
+    int ea = (int)((ua >> 52) & 0x7FF), eb = (int)((ub >> 52) & 0x7FF);
+    long long ma = ua & 0x000FFFFFFFFFFFFFLL, mb = ub & 0x000FFFFFFFFFFFFFLL;
+    if (ea) ma |= 1LL << 52; else ea = 1;            // subnormal: exponent 1, no leading bit
+    if (eb) mb |= 1LL << 52; else eb = 1;
+    if (ua < 0) ma = -ma;
+    if (ub < 0) mb = -mb;
+    const bool swap = eb > ea;                       // make ea >= eb; the difference changes sign
+    if (swap) {
+        const int te = ea; ea = eb; eb = te;
+        const long long tm = ma; ma = mb; mb = tm;
+    }
+    const int k = min(9, ea - eb);
+    const int r = ea - eb - k;
+    const long long d0 = ma * (1LL << k) - (r < 63 ? (mb >> r) : 0LL);   // |d0| < 2^62 + 2^53
+    if (d0 == 0) return dflt(0.f, 0.f);
+    const long long d = swap ? -d0 : d0;             // a - b = d 2^(ea - k - 1075)
+    const uint32_t sign = d < 0 ? 0x80000000u : 0u;
+    unsigned long long u = (unsigned long long)(d < 0 ? -d : d);
+    const int lz = __clzll((long long)u);
+    u <<= lz;                                        // leading bit at 2^63: a - b = u 2^(e0 - lz)
+    const int e0 = ea - k - 1075;
+    const float hi = dfl_float_m24((uint32_t)(u >> 40), e0 - lz + 40, sign);
+    const unsigned long long rest = u & ((1ULL << 40) - 1ULL);
+    float lo = 0.f;
+    if (rest != 0ULL) {
+        const int lz2 = __clzll((long long)rest);
+        lo = dfl_float_m24((uint32_t)((rest << lz2) >> 40), e0 - lz - lz2 + 40, sign);
+    }
+    return dfl_fast_two_sum(hi, lo);
+}
+
 __device__ __forceinline__ dflt dfl_shfl_up(dflt v, int o)
 {
     return dflt(__shfl_up_sync(0xffffffffu, v.h, o), __shfl_up_sync(0xffffffffu, v.l, o));

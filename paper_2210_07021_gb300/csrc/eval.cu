@@ -868,9 +868,10 @@ __global__ void __launch_bounds__(128) k_eval_df(EvalDfArgs A)
     }
 }
 
-// Offsets for the mixed evaluation, formed once in FP64 and split into FP32
-// (hi, lo) pairs: each sorted target from its leaf's centre, and each near
-// leaf's centre from its target leaf's centre (one per direct-act pair).
+// Offsets for the mixed evaluation as FP32 (hi, lo) pairs, formed without FP64
+// instructions (the difference to 2^-47): each sorted target from its leaf's
+// centre, and each near leaf's centre from its target leaf's centre (one per
+// direct-act pair).
 __global__ void k_tgt_offsets(TreeView T, const int* __restrict__ leaves, int64_t n_leaves,
                               const double4_32a* __restrict__ tgt, float4* __restrict__ off)
 {
@@ -883,11 +884,9 @@ __global__ void k_tgt_offsets(TreeView T, const int* __restrict__ leaves, int64_
         const int f = T.tfirst[node], n = T.tcount[node];
         for (int j = f + lane; j < f + n; j += 32) {
             const double4_32a x = tgt[j];
-            const double dx = x.x - g[0], dy = x.y - g[1], dz = x.z - g[2];
-            const float hx = (float)dx, hy = (float)dy, hz = (float)dz;
-            off[2 * (size_t)j] = make_float4(hx, hy, hz, 0.f);
-            off[2 * (size_t)j + 1] = make_float4((float)(dx - (double)hx), (float)(dy - (double)hy),
-                                                 (float)(dz - (double)hz), 0.f);
+            const dflt dx = dfl_sub_exact(x.x, g[0]), dy = dfl_sub_exact(x.y, g[1]), dz = dfl_sub_exact(x.z, g[2]);
+            off[2 * (size_t)j] = make_float4(dx.h, dy.h, dz.h, 0.f);
+            off[2 * (size_t)j + 1] = make_float4(dx.l, dy.l, dz.l, 0.f);
         }
     }
 }
@@ -900,11 +899,9 @@ __global__ void k_pair_offsets(TreeView T, const uint64_t* __restrict__ tt, cons
         const uint32_t sl = ss[k];
         const double* gs = T.geom + (size_t)sl * GEOM_STRIDE;
         const double* gt = T.geom + (size_t)tt[k] * GEOM_STRIDE;
-        const double dx = gs[0] - gt[0], dy = gs[1] - gt[1], dz = gs[2] - gt[2];
-        const float hx = (float)dx, hy = (float)dy, hz = (float)dz;
-        dc[2 * k] = make_float4(hx, hy, hz, __int_as_float(T.first[sl]));
-        dc[2 * k + 1] = make_float4((float)(dx - (double)hx), (float)(dy - (double)hy), (float)(dz - (double)hz),
-                                    __int_as_float(T.count[sl]));
+        const dflt dx = dfl_sub_exact(gs[0], gt[0]), dy = dfl_sub_exact(gs[1], gt[1]), dz = dfl_sub_exact(gs[2], gt[2]);
+        dc[2 * k] = make_float4(dx.h, dy.h, dz.h, __int_as_float(T.first[sl]));
+        dc[2 * k + 1] = make_float4(dx.l, dy.l, dz.l, __int_as_float(T.count[sl]));
     }
 }
 

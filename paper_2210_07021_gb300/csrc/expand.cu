@@ -844,8 +844,8 @@ __global__ void k_m2l_list(const uint64_t* __restrict__ ptgt, const uint32_t* __
 }
 
 // FP32 offset of every key-sorted source from the centre of its leaf as an
-// (hi, lo) pair (hi = the FP64 difference rounded, lo = the remainder), plus
-// its mass split the same way: off[2j] = (hi, q_hi), off[2j+1] = (lo, q_lo).
+// (hi, lo) pair (the difference to 2^-47, formed without FP64 instructions),
+// plus its mass split the same way: off[2j] = (hi, q_hi), off[2j+1] = (lo, q_lo).
 __global__ void k_src_offsets(TreeView T, const int* __restrict__ leaves, int64_t n_leaves,
                               const double4_32a* __restrict__ src, float4* __restrict__ off)
 {
@@ -858,12 +858,10 @@ __global__ void k_src_offsets(TreeView T, const int* __restrict__ leaves, int64_
         const int f = T.first[node], n = T.count[node];
         for (int j = f + lane; j < f + n; j += 32) {
             const double4_32a y = src[j];
-            const double dx = y.x - g[0], dy = y.y - g[1], dz = y.z - g[2];
-            const float hx = (float)dx, hy = (float)dy, hz = (float)dz;
-            const float qh = (float)y.w;
-            off[2 * (size_t)j] = make_float4(hx, hy, hz, qh);
-            off[2 * (size_t)j + 1] = make_float4((float)(dx - (double)hx), (float)(dy - (double)hy),
-                                                 (float)(dz - (double)hz), (float)(y.w - (double)qh));
+            const dflt dx = dfl_sub_exact(y.x, g[0]), dy = dfl_sub_exact(y.y, g[1]), dz = dfl_sub_exact(y.z, g[2]);
+            const dflt q = dfl_sub_exact(y.w, 0.0);
+            off[2 * (size_t)j] = make_float4(dx.h, dy.h, dz.h, q.h);
+            off[2 * (size_t)j + 1] = make_float4(dx.l, dy.l, dz.l, q.l);
         }
     }
 }
