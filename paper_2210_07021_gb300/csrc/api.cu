@@ -51,24 +51,27 @@ cudaError_t launch_eval32_prep(const TreeView& T, const int* leaves, int64_t n_l
 cudaError_t launch_eval32(const TreeView& T, const int* leaves, int64_t n_leaves, const float4* soff,
                           const float4* toff, const float4* dc, const double4_32a* tgt, const uint32_t* tperm, const int64_t* p2p_off,
                           const uint32_t* p2p_src, const float* local, const float* mpole, int p, int zero_mean,
-                          double* psi, double* alpha, bool coincide, cudaStream_t s);
+                          double* psi, double* alpha, bool coincide, unsigned long long* leaf_ctr,
+                          cudaStream_t s);
 cudaError_t launch_count_pairs(const TreeView& T, const int* leaves, int64_t n_leaves, const int64_t* p2p_off,
                                const uint32_t* p2p_src, unsigned long long* out, cudaStream_t s);
 void fill_log_table(float* out);
 cudaError_t launch_eval_df(const TreeView& T, const int* leaves, int64_t n_leaves, const float4* soff,
                            const float4* toff, const float4* dc, const double4_32a* tgt, const uint32_t* tperm,
                            const int64_t* p2p_off, const uint32_t* p2p_src, const void* local, const void* mpole,
-                           const float4* log_tab, int p, int zero_mean, double* psi, double* alpha, cudaStream_t s);
+                           const float4* log_tab, int p, int zero_mean, double* psi, double* alpha,
+                           unsigned long long* leaf_ctr, cudaStream_t s);
 cudaError_t launch_p2m_adj(const TreeView& T, const int* leaves, int64_t n_leaves, const double4_32a* src,
                            const double4_32a* dip, double* mpole, int p, cudaStream_t s);
 cudaError_t launch_eval_adj(const TreeView& T, const int* leaves, int64_t n_leaves, const double4_32a* src,
                             const double4_32a* dip, const double4_32a* tgt, const uint32_t* tperm,
                             const int64_t* p2p_off, const uint32_t* p2p_src, const double* local, const double* mpole,
-                            int p, int zero_mean, const void* w, int w_f32, double* phi, double* grad3, cudaStream_t s);
+                            int p, int zero_mean, const void* w, int w_f32, double* phi, double* grad3,
+                            unsigned long long* leaf_ctr, cudaStream_t s);
 cudaError_t launch_eval(const TreeView& T, const int* leaves, int64_t n_leaves, const double4_32a* src, const double4_32a* tgt,
                         const uint32_t* tperm, const int64_t* p2p_off, const uint32_t* p2p_src, const double* local,
                         const double* mpole, int p, int zero_mean, double sigma, double* psi, double* alpha,
-                        double* gamma, cudaStream_t s);
+                        double* gamma, unsigned long long* leaf_ctr, cudaStream_t s);
 
 namespace {
 std::atomic<int64_t> g_launches{0};
@@ -410,21 +413,22 @@ sfmm_status solve(sfmm_plan_s* P, const double* src, const void* q, int64_t N, c
                                     P->toff.as<float4>(), p2p_t, p2p_s, P->n_p2p, P->dc.as<float4>(), s)))
             return cuda_fail(P, e, "offsets");
     }
+    unsigned long long* leaf_ctr = reinterpret_cast<unsigned long long*>(P->small.as<int64_t>() + 40);
     if (adj) e = launch_eval_adj(T, P->leaves_tgt.as<int>(), P->n_leaves_tgt, P->src4.as<double4_32a>(),
                                  P->dip4.as<double4_32a>(), P->tgt4.as<double4_32a>(), tperm, P->p2p_off.as<int64_t>(),
                                  p2p_s, P->local.as<double>(), P->mpole.as<double>(), p, P->opt.zero_mean, adj->w,
-                                 adj->w_f32, psi, adj->grad3, s);
+                                 adj->w_f32, psi, adj->grad3, leaf_ctr, s);
     else if (fp32) e = launch_eval32(T, P->leaves_tgt.as<int>(), P->n_leaves_tgt, P->soff.as<float4>(),
                                 P->toff.as<float4>(), P->dc.as<float4>(), P->tgt4.as<double4_32a>(), tperm, P->p2p_off.as<int64_t>(), p2p_s,
                                 P->local.as<float>(), P->mpole.as<float>(), p, P->opt.zero_mean, psi, alpha,
-                                src == tgt, s);
+                                src == tgt, leaf_ctr, s);
     else if (dfe) e = launch_eval_df(T, P->leaves_tgt.as<int>(), P->n_leaves_tgt, P->soff.as<float4>(),
                                      P->toff.as<float4>(), P->dc.as<float4>(), P->tgt4.as<double4_32a>(), tperm,
                                      P->p2p_off.as<int64_t>(), p2p_s, P->local.p, P->mpole.p,
-                                     P->logtab.as<float4>(), p, P->opt.zero_mean, psi, alpha, s);
+                                     P->logtab.as<float4>(), p, P->opt.zero_mean, psi, alpha, leaf_ctr, s);
     else e = launch_eval(T, P->leaves_tgt.as<int>(), P->n_leaves_tgt, P->src4.as<double4_32a>(),
                          P->tgt4.as<double4_32a>(), tperm, P->p2p_off.as<int64_t>(), p2p_s, P->local.as<double>(),
-                         P->mpole.as<double>(), p, P->opt.zero_mean, P->opt.sigma, psi, alpha, gamma, s);
+                         P->mpole.as<double>(), p, P->opt.zero_mean, P->opt.sigma, psi, alpha, gamma, leaf_ctr, s);
     if (e) return cuda_fail(P, e, "evaluation");
     tm.mark();
     if (P->timing) {

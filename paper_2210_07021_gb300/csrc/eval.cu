@@ -54,6 +54,7 @@ struct EvalArgs {
     double* psi;
     double* alpha;
     double* gamma;            // [M][2] shear (gamma_1, gamma_2) in (e_theta, e_phi), or NULL
+    unsigned long long* leaf_ctr;   // zero at launch: the warps take target leaves from it one at a time
     double npm_s;             // Near Particle Model: sin^2(sigma/2) (NPM kernels only)
 };
 
@@ -78,16 +79,24 @@ __device__ __forceinline__ double group_sum(double v, int lpt)
 // f = (m(u) - u)/(1 - u), m = 2u/s - u^2/s^2 (Gauss's law on the sphere), and
 // log u replaced by log s - (1 - u/s) + ((1 - s)^2/s^2)(log1p(t) - t),
 // t = (s - u)/(1 - s) (the point-mass potential continued into the cap).
+// The next target leaf of a warp, taken from a global counter by lane 0.
+__device__ __forceinline__ int64_t next_leaf(unsigned long long* ctr, int lane)
+{
+    unsigned long long w = 0;
+    if (lane == 0) w = atomicAdd(ctr, 1ull);
+    return (int64_t)__shfl_sync(FULL, w, 0);
+}
+
 template <bool SHEAR, bool NPM>
 __global__ void __launch_bounds__(128) k_eval(EvalArgs A)
 {
     const int lane = threadIdx.x & 31;
-    const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     double shift = 0.0;
     if (A.zero_mean)
         for (int b = 0; b < 12; ++b) shift += A.base_mpole[(size_t)b * EXP_STRIDE + 1];
-    for (int64_t w = warp0; w < A.n_leaves; w += nwarps) {
+    for (;;) {
+        const int64_t w = next_leaf(A.leaf_ctr, lane);
+        if (w >= A.n_leaves) break;
         const int leaf = A.leaves[w];
         const int tf = A.T.tfirst[leaf], tc = A.T.tcount[leaf];
         const double* g = A.T.geom + (size_t)leaf * GEOM_STRIDE;
@@ -247,12 +256,12 @@ __global__ void __launch_bounds__(128) k_eval_adj(EvalAdjArgs AA)
 {
     const EvalArgs& A = AA.E;
     const int lane = threadIdx.x & 31;
-    const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     double shift = 0.0;
     if (A.zero_mean)
         for (int b = 0; b < 12; ++b) shift += A.base_mpole[(size_t)b * EXP_STRIDE + 1];
-    for (int64_t w = warp0; w < A.n_leaves; w += nwarps) {
+    for (;;) {
+        const int64_t w = next_leaf(A.leaf_ctr, lane);
+        if (w >= A.n_leaves) break;
         const int leaf = A.leaves[w];
         const int tf = A.T.tfirst[leaf], tc = A.T.tcount[leaf];
         const double* g = A.T.geom + (size_t)leaf * GEOM_STRIDE;
@@ -391,7 +400,17 @@ struct Eval32Args {
     int zero_mean;
     double* psi;
     double* alpha;
+    unsigned long long* leaf_ctr;   // zero at launch: the warps take target leaves from it one at a time
 };
+
+// 16-byte asynchronous copy from global to shared memory (cached in L1 and L2),
+// and the wait for all of this thread's copies
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;"
+                 :: "r"((uint32_t)__cvta_generic_to_shared(smem)), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 __device__ __forceinline__ float group_sumf(float v, int lpt)
 {
@@ -548,8 +567,6 @@ __global__ void __launch_bounds__(128, 7) k_eval32(Eval32Args A)
     __shared__ int s_first[4][32];
     __shared__ LeafFrame32 s_frame[4];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     double shift = 0.0;
     if (A.zero_mean)
         for (int b = 0; b < 12; ++b) shift += (double)A.base_mpole[(size_t)b * EXP_STRIDE + 1];
@@ -557,7 +574,9 @@ __global__ void __launch_bounds__(128, 7) k_eval32(Eval32Args A)
     float4* yl = s_lo[wid];
     int* pre = s_pre[wid];
     int* fst = s_first[wid];
-    for (int64_t w = warp0; w < A.n_leaves; w += nwarps) {
+    for (;;) {
+        const int64_t w = next_leaf(A.leaf_ctr, lane);
+        if (w >= A.n_leaves) break;
         const int leaf = A.leaves[w];
         const int tf = A.T.tfirst[leaf], tc = A.T.tcount[leaf];
         const double* g = A.T.geom + (size_t)leaf * GEOM_STRIDE;
@@ -617,16 +636,25 @@ __global__ void __launch_bounds__(128, 7) k_eval32(Eval32Args A)
                 s_dc[wid][lane][0] = rh.x; s_dc[wid][lane][1] = rh.y; s_dc[wid][lane][2] = rh.z;
                 s_dc[wid][lane][3] = rl.x; s_dc[wid][lane][4] = rl.y; s_dc[wid][lane][5] = rl.z;
                 __syncwarp();
-                // ---- flattened staging: position idx -> (leaf i, source) by binary search of pre
-                for (int idx = lane; idx < ns; idx += 32) {
-                    int lo = 0, hi = nl;            // largest i < nl with pre[i] <= idx
-                    while (hi - lo > 1) {
-                        const int mid = (lo + hi) >> 1;
-                        if (pre[mid] <= idx) lo = mid; else hi = mid;
+                // ---- flattened staging: position idx belongs to the largest leaf i < nl with
+                // pre[i] <= idx, found by stepping on from the previous position's leaf.  First
+                // every lane starts asynchronous 16-byte copies of its sources' (hi, lo) offsets
+                // into the stage, all in flight at once; after the wait each offset is moved from
+                // its leaf's centre to the target leaf's.
+                {
+                    int lo = 0;
+                    for (int idx = lane; idx < ns; idx += 32) {
+                        while (lo + 1 < nl && pre[lo + 1] <= idx) ++lo;
+                        const size_t j = (size_t)(fst[lo] + (idx - pre[lo]));
+                        cp_async16(&yh[idx], &A.soff[2 * j]);
+                        cp_async16(&yl[idx], &A.soff[2 * j + 1]);
                     }
-                    const size_t j = (size_t)(fst[lo] + (idx - pre[lo]));
-                    const float4 h = A.soff[2 * j];
-                    const float4 l = A.soff[2 * j + 1];
+                    cp_async_wait_all();
+                }
+                for (int idx = lane, lo = 0; idx < ns; idx += 32) {
+                    while (lo + 1 < nl && pre[lo + 1] <= idx) ++lo;
+                    const float4 h = yh[idx];            // this lane's own copies: complete after the wait
+                    const float4 l = yl[idx];
                     const float* d = s_dc[wid][lo];
                     float sx, ex_, sy, ey_, sz, ez_;
                     two_sum(h.x, d[0], &sx, &ex_);
@@ -692,6 +720,7 @@ struct EvalDfArgs {
     int zero_mean;
     double* psi;
     double* alpha;
+    unsigned long long* leaf_ctr;   // zero at launch: the warps take target leaves from it one at a time
 };
 
 template <bool PSI>
@@ -706,8 +735,6 @@ __global__ void __launch_bounds__(128) k_eval_df(EvalDfArgs A)
     for (int i = threadIdx.x; i < 129; i += blockDim.x) s_tab[i] = A.log_tab[i];
     __syncthreads();
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     double shift = 0.0;
     if (A.zero_mean)
         for (int b = 0; b < 12; ++b) shift += (double)A.base_mpole[(size_t)b * EXP_STRIDE + 1];
@@ -715,7 +742,9 @@ __global__ void __launch_bounds__(128) k_eval_df(EvalDfArgs A)
     float4* yl = s_lo[wid];
     int* pre = s_pre[wid];
     int* fst = s_first[wid];
-    for (int64_t w = warp0; w < A.n_leaves; w += nwarps) {
+    for (;;) {
+        const int64_t w = next_leaf(A.leaf_ctr, lane);
+        if (w >= A.n_leaves) break;
         const int leaf = A.leaves[w];
         const int tf = A.T.tfirst[leaf], tc = A.T.tcount[leaf];
         const double* g = A.T.geom + (size_t)leaf * GEOM_STRIDE;
@@ -905,6 +934,23 @@ __global__ void k_pair_offsets(TreeView T, const uint64_t* __restrict__ tt, cons
     }
 }
 
+// Zero the leaf counter and size a persistent grid of 4-warp CTAs: up to
+// per_sm per SM (the CTAs an SM holds at once); every warp takes target leaves
+// from the counter until none are left, so uneven leaves leave no slot idle
+// (CTAs beyond what the SMs hold start when others exit and find little or
+// nothing left).
+cudaError_t leaf_grid(unsigned long long* ctr, int64_t n_leaves, int per_sm, cudaStream_t s, int64_t* blocks)
+{
+    cudaError_t e;
+    int dev = 0, sms = 0;
+    if ((e = cudaMemsetAsync(ctr, 0, sizeof(unsigned long long), s)) || (e = cudaGetDevice(&dev)) ||
+        (e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)))
+        return e;
+    const int64_t want = (n_leaves + 3) / 4;
+    *blocks = want < (int64_t)sms * per_sm ? want : (int64_t)sms * per_sm;
+    return cudaSuccess;
+}
+
 }  // namespace
 
 cudaError_t launch_eval32_prep(const TreeView& T, const int* leaves, int64_t n_leaves, const double4_32a* tgt,
@@ -927,7 +973,7 @@ cudaError_t launch_eval32_prep(const TreeView& T, const int* leaves, int64_t n_l
 cudaError_t launch_eval32(const TreeView& T, const int* leaves, int64_t n_leaves, const float4* soff,
                           const float4* toff, const float4* dc, const double4_32a* tgt, const uint32_t* tperm, const int64_t* p2p_off,
                           const uint32_t* p2p_src, const float* local, const float* mpole, int p, int zero_mean,
-                          double* psi, double* alpha, bool coincide, cudaStream_t s)
+                          double* psi, double* alpha, bool coincide, unsigned long long* leaf_ctr, cudaStream_t s)
 {
     if (n_leaves == 0) return cudaSuccess;
     Eval32Args A;
@@ -948,8 +994,10 @@ cudaError_t launch_eval32(const TreeView& T, const int* leaves, int64_t n_leaves
     A.zero_mean = zero_mean;
     A.psi = psi;
     A.alpha = alpha;
-    int64_t blocks = (n_leaves + 3) / 4;
-    if (blocks > 152 * 64) blocks = 152 * 64;
+    A.leaf_ctr = leaf_ctr;
+    int64_t blocks = 0;
+    cudaError_t e;
+    if ((e = leaf_grid(leaf_ctr, n_leaves, 7, s, &blocks))) return e;     // 7 per SM: __launch_bounds__
     if (coincide) {
         if (psi) k_eval32<true, true><<<(unsigned)blocks, 128, 0, s>>>(A);
         else k_eval32<false, true><<<(unsigned)blocks, 128, 0, s>>>(A);
@@ -985,7 +1033,8 @@ void fill_log_table(float* out)
 cudaError_t launch_eval_df(const TreeView& T, const int* leaves, int64_t n_leaves, const float4* soff,
                            const float4* toff, const float4* dc, const double4_32a* tgt, const uint32_t* tperm,
                            const int64_t* p2p_off, const uint32_t* p2p_src, const void* local, const void* mpole,
-                           const float4* log_tab, int p, int zero_mean, double* psi, double* alpha, cudaStream_t s)
+                           const float4* log_tab, int p, int zero_mean, double* psi, double* alpha,
+                           unsigned long long* leaf_ctr, cudaStream_t s)
 {
     if (n_leaves == 0) return cudaSuccess;
     EvalDfArgs A;
@@ -1006,8 +1055,10 @@ cudaError_t launch_eval_df(const TreeView& T, const int* leaves, int64_t n_leave
     A.zero_mean = zero_mean;
     A.psi = psi;
     A.alpha = alpha;
-    int64_t blocks = (n_leaves + 3) / 4;
-    if (blocks > 152 * 64) blocks = 152 * 64;
+    A.leaf_ctr = leaf_ctr;
+    int64_t blocks = 0;
+    cudaError_t e;
+    if ((e = leaf_grid(leaf_ctr, n_leaves, 16, s, &blocks))) return e;
     if (psi) k_eval_df<true><<<(unsigned)blocks, 128, 0, s>>>(A);
     else k_eval_df<false><<<(unsigned)blocks, 128, 0, s>>>(A);
     count_launch();
@@ -1027,7 +1078,7 @@ cudaError_t launch_count_pairs(const TreeView& T, const int* leaves, int64_t n_l
 cudaError_t launch_eval(const TreeView& T, const int* leaves, int64_t n_leaves, const double4_32a* src, const double4_32a* tgt,
                         const uint32_t* tperm, const int64_t* p2p_off, const uint32_t* p2p_src, const double* local,
                         const double* mpole, int p, int zero_mean, double sigma, double* psi, double* alpha,
-                        double* gamma, cudaStream_t s)
+                        double* gamma, unsigned long long* leaf_ctr, cudaStream_t s)
 {
     if (n_leaves == 0) return cudaSuccess;
     EvalArgs A;
@@ -1048,8 +1099,10 @@ cudaError_t launch_eval(const TreeView& T, const int* leaves, int64_t n_leaves, 
     A.alpha = alpha;
     A.gamma = gamma;
     A.npm_s = sin(0.5 * sigma) * sin(0.5 * sigma);
-    int64_t blocks = (n_leaves + 3) / 4;
-    if (blocks > 152 * 64) blocks = 152 * 64;
+    A.leaf_ctr = leaf_ctr;
+    int64_t blocks = 0;
+    cudaError_t e;
+    if ((e = leaf_grid(leaf_ctr, n_leaves, 16, s, &blocks))) return e;
     if (gamma) k_eval<true, false><<<(unsigned)blocks, 128, 0, s>>>(A);
     else if (sigma > 0.0) k_eval<false, true><<<(unsigned)blocks, 128, 0, s>>>(A);
     else k_eval<false, false><<<(unsigned)blocks, 128, 0, s>>>(A);
@@ -1060,7 +1113,8 @@ cudaError_t launch_eval(const TreeView& T, const int* leaves, int64_t n_leaves, 
 cudaError_t launch_eval_adj(const TreeView& T, const int* leaves, int64_t n_leaves, const double4_32a* src,
                             const double4_32a* dip, const double4_32a* tgt, const uint32_t* tperm,
                             const int64_t* p2p_off, const uint32_t* p2p_src, const double* local, const double* mpole,
-                            int p, int zero_mean, const void* w, int w_f32, double* phi, double* grad3, cudaStream_t s)
+                            int p, int zero_mean, const void* w, int w_f32, double* phi, double* grad3,
+                            unsigned long long* leaf_ctr, cudaStream_t s)
 {
     if (n_leaves == 0) return cudaSuccess;
     EvalAdjArgs AA;
@@ -1085,8 +1139,10 @@ cudaError_t launch_eval_adj(const TreeView& T, const int* leaves, int64_t n_leav
     AA.w = w;
     AA.w_f32 = w_f32;
     AA.grad3 = grad3;
-    int64_t blocks = (n_leaves + 3) / 4;
-    if (blocks > 152 * 64) blocks = 152 * 64;
+    A.leaf_ctr = leaf_ctr;
+    int64_t blocks = 0;
+    cudaError_t e;
+    if ((e = leaf_grid(leaf_ctr, n_leaves, 16, s, &blocks))) return e;
     k_eval_adj<<<(unsigned)blocks, 128, 0, s>>>(AA); count_launch();
     return cudaGetLastError();
 }
