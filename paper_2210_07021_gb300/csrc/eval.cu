@@ -403,15 +403,6 @@ struct Eval32Args {
     unsigned long long* leaf_ctr;   // zero at launch: the warps take target leaves from it one at a time
 };
 
-// 16-byte asynchronous copy from global to shared memory (cached in L1 and L2),
-// and the wait for all of this thread's copies
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem)
-{
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;"
-                 :: "r"((uint32_t)__cvta_generic_to_shared(smem)), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
-
 __device__ __forceinline__ float group_sumf(float v, int lpt)
 {
     for (int o = lpt >> 1; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
@@ -427,9 +418,30 @@ __device__ __forceinline__ void two_sum(float a, float b, float* s, float* e)
     *s = x;
 }
 
-// Near-field sums of one target over the staged sources j = sub, sub + lpt, ...:
-// blocks of (up to) 16 pairs per lane in FP32, then the outer FP32 level.  The
-// logarithm is accumulated in base 2 (acc[4] = sum q log2 d^2).
+// The staged near sources of one warp, packed by pairs of sources (a, b) =
+// (2P, 2P+1) and negated, so that one 16-byte load yields (x_a, x_b, y_a, y_b)
+// and the pair loop runs on packed FP32x2 instructions: hi offsets (x, y), (z,
+// mass), lo offsets (x, y), (z), all from the target leaf's centre.
+struct Stage32 {
+    float4 hxy[STAGE32 / 2];
+    float4 hzq[STAGE32 / 2];
+    float4 lxy[STAGE32 / 2];
+    float2 lz[STAGE32 / 2];
+};
+
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// Near-field sums of one target over the staged source pairs P = sub, sub + lpt,
+// ...: blocks of (up to) 16 pairs per lane in packed FP32 (the two halves sum
+// the even and the odd sources), then the outer FP32 level acc.  The logarithm
+// is accumulated in base 2 (acc[4] = sum q log2 d^2).  1/d^2 is the
+// approximate reciprocal (as in __fdividef).
 //
 // A source at the target's own position (d^2 = 0) is left out.  The masked
 // block tests every pair for it; the plain block does not: there 1/d^2 = inf
@@ -437,59 +449,53 @@ __device__ __forceinline__ void two_sum(float a, float b, float* s, float* e)
 // x sum is not finite is summed again masked.  When the targets are the
 // sources themselves every target meets one such block; there (MASK) every
 // block is masked.
-template <bool PSI>
-__device__ __forceinline__ void masked_pair(const float4& h, const float4& l, const float4& th, const float4& tl,
-                                            float& ix, float& iy, float& iz, float& iq, float& il)
+template <bool PSI, bool MASKED>
+__device__ __forceinline__ void pair_block32(const Stage32& S, int P0, int P1, int lpt, const float2& tx,
+                                             const float2& ty, const float2& tz, const float2& ux, const float2& uy,
+                                             const float2& uz, float2& ix, float2& iy, float2& iz, float2& iq,
+                                             float2& il)
 {
-    const float dx = (th.x - h.x) + (tl.x - l.x);
-    const float dy = (th.y - h.y) + (tl.y - l.y);
-    const float dz = (th.z - h.z) + (tl.z - l.z);
-    const float d2 = dx * dx + dy * dy + dz * dz;
-    const bool ok = d2 > 0.f;
-    const float q = ok ? h.w : 0.f;
-    const float den = ok ? d2 : 1.f;
-    const float wq = __fdividef(q, den);
-    ix += wq * dx;
-    iy += wq * dy;
-    iz += wq * dz;
-    iq += q;
-    if (PSI) il += q * __log2f(den);
+#pragma unroll 2
+    for (int P = P0; P < P1; P += lpt) {
+        const float4 a = S.hxy[P], b = S.hzq[P], c = S.lxy[P];
+        const float2 d = S.lz[P];
+        const float2 dx = __fadd2_rn(__fadd2_rn(tx, f2(a.x, a.y)), __fadd2_rn(ux, f2(c.x, c.y)));
+        const float2 dy = __fadd2_rn(__fadd2_rn(ty, f2(a.z, a.w)), __fadd2_rn(uy, f2(c.z, c.w)));
+        const float2 dz = __fadd2_rn(__fadd2_rn(tz, f2(b.x, b.y)), __fadd2_rn(uz, d));
+        const float2 d2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
+        float2 q = f2(b.z, b.w);
+        float2 den = d2;
+        if (MASKED) {
+            const bool oka = d2.x > 0.f, okb = d2.y > 0.f;
+            q = f2(oka ? q.x : 0.f, okb ? q.y : 0.f);
+            den = f2(oka ? d2.x : 1.f, okb ? d2.y : 1.f);
+        }
+        const float2 wq = __fmul2_rn(q, f2(rcp_approx(den.x), rcp_approx(den.y)));
+        ix = __ffma2_rn(wq, dx, ix);
+        iy = __ffma2_rn(wq, dy, iy);
+        iz = __ffma2_rn(wq, dz, iz);
+        iq = __fadd2_rn(iq, q);
+        if (PSI) il = __ffma2_rn(q, f2(__log2f(den.x), __log2f(den.y)), il);
+    }
 }
 
 template <bool PSI, bool MASK>
-__device__ __forceinline__ void pair_sums32(const float4* __restrict__ yh, const float4* __restrict__ yl, int ns,
-                                            int sub, int lpt, const float4& th, const float4& tl, float* acc)
+__device__ __forceinline__ void pair_sums32(const Stage32& S, int npair, int sub, int lpt, const float4& th,
+                                            const float4& tl, float* acc)
 {
-    for (int j = sub; j < ns;) {
-        const int jend = min(ns, j + 16 * lpt);
-        float ix = 0.f, iy = 0.f, iz = 0.f, iq = 0.f, il = 0.f;   // inner FP32 level
-        if (MASK) {
-#pragma unroll 4
-            for (; j < jend; j += lpt) masked_pair<PSI>(yh[j], yl[j], th, tl, ix, iy, iz, iq, il);
-        } else {
-            const int j0 = j;
-#pragma unroll 4
-            for (; j < jend; j += lpt) {
-                const float4 h = yh[j];
-                const float4 l = yl[j];
-                const float dx = (th.x - h.x) + (tl.x - l.x);
-                const float dy = (th.y - h.y) + (tl.y - l.y);
-                const float dz = (th.z - h.z) + (tl.z - l.z);
-                const float d2 = dx * dx + dy * dy + dz * dz;
-                const float wq = __fdividef(h.w, d2);
-                ix += wq * dx;
-                iy += wq * dy;
-                iz += wq * dz;
-                iq += h.w;
-                if (PSI) il += h.w * __log2f(d2);
-            }
-            if (!(fabsf(ix) < INFINITY)) {
-                ix = 0.f; iy = 0.f; iz = 0.f; iq = 0.f; il = 0.f;
-#pragma unroll 1
-                for (int jj = j0; jj < jend; jj += lpt) masked_pair<PSI>(yh[jj], yl[jj], th, tl, ix, iy, iz, iq, il);
-            }
+    const float2 tx = f2(th.x, th.x), ty = f2(th.y, th.y), tz = f2(th.z, th.z);
+    const float2 ux = f2(tl.x, tl.x), uy = f2(tl.y, tl.y), uz = f2(tl.z, tl.z);
+    for (int P = sub; P < npair;) {
+        const int pend = min(npair, P + 16 * lpt);
+        float2 ix = f2(0.f, 0.f), iy = ix, iz = ix, iq = ix, il = ix;   // inner FP32 level
+        pair_block32<PSI, MASK>(S, P, pend, lpt, tx, ty, tz, ux, uy, uz, ix, iy, iz, iq, il);
+        if (!MASK && !(fabsf(ix.x) < INFINITY && fabsf(ix.y) < INFINITY)) {
+            ix = f2(0.f, 0.f); iy = ix; iz = ix; iq = ix; il = ix;
+            pair_block32<PSI, true>(S, P, pend, lpt, tx, ty, tz, ux, uy, uz, ix, iy, iz, iq, il);
         }
-        acc[0] += ix; acc[1] += iy; acc[2] += iz; acc[3] += iq; acc[4] += il;
+        acc[0] += ix.x + ix.y; acc[1] += iy.x + iy.y; acc[2] += iz.x + iz.y;
+        acc[3] += iq.x + iq.y; acc[4] += il.x + il.y;
+        P = pend;
     }
 }
 
@@ -560,8 +566,7 @@ __device__ __forceinline__ void finish_target32(const Eval32Args& A, const LeafF
 template <bool PSI, bool MASK>
 __global__ void __launch_bounds__(128, 7) k_eval32(Eval32Args A)
 {
-    __shared__ float4 s_hi[4][STAGE32];
-    __shared__ float4 s_lo[4][STAGE32];
+    __shared__ Stage32 s_stage[4];
     __shared__ float s_dc[4][32][6];
     __shared__ int s_pre[4][33];
     __shared__ int s_first[4][32];
@@ -570,8 +575,7 @@ __global__ void __launch_bounds__(128, 7) k_eval32(Eval32Args A)
     double shift = 0.0;
     if (A.zero_mean)
         for (int b = 0; b < 12; ++b) shift += (double)A.base_mpole[(size_t)b * EXP_STRIDE + 1];
-    float4* yh = s_hi[wid];
-    float4* yl = s_lo[wid];
+    Stage32& S = s_stage[wid];
     int* pre = s_pre[wid];
     int* fst = s_first[wid];
     for (;;) {
@@ -637,37 +641,47 @@ __global__ void __launch_bounds__(128, 7) k_eval32(Eval32Args A)
                 s_dc[wid][lane][3] = rl.x; s_dc[wid][lane][4] = rl.y; s_dc[wid][lane][5] = rl.z;
                 __syncwarp();
                 // ---- flattened staging: position idx belongs to the largest leaf i < nl with
-                // pre[i] <= idx, found by stepping on from the previous position's leaf.  First
-                // every lane starts asynchronous 16-byte copies of its sources' (hi, lo) offsets
-                // into the stage, all in flight at once; after the wait each offset is moved from
-                // its leaf's centre to the target leaf's.
-                {
-                    int lo = 0;
-                    for (int idx = lane; idx < ns; idx += 32) {
-                        while (lo + 1 < nl && pre[lo + 1] <= idx) ++lo;
-                        const size_t j = (size_t)(fst[lo] + (idx - pre[lo]));
-                        cp_async16(&yh[idx], &A.soff[2 * j]);
-                        cp_async16(&yl[idx], &A.soff[2 * j + 1]);
-                    }
-                    cp_async_wait_all();
-                }
+                // pre[i] <= idx, found by stepping on from the previous position's leaf; its
+                // offset is moved from its leaf's centre to the target leaf's (two-sum with the
+                // near leaf's centre offset) and stored negated in the pair-packed stage
                 for (int idx = lane, lo = 0; idx < ns; idx += 32) {
                     while (lo + 1 < nl && pre[lo + 1] <= idx) ++lo;
-                    const float4 h = yh[idx];            // this lane's own copies: complete after the wait
-                    const float4 l = yl[idx];
+                    const size_t j = (size_t)(fst[lo] + (idx - pre[lo]));
+                    const float4 h = A.soff[2 * j];
+                    const float4 l = A.soff[2 * j + 1];
                     const float* d = s_dc[wid][lo];
                     float sx, ex_, sy, ey_, sz, ez_;
                     two_sum(h.x, d[0], &sx, &ex_);
                     two_sum(h.y, d[1], &sy, &ey_);
                     two_sum(h.z, d[2], &sz, &ez_);
-                    yh[idx] = make_float4(sx, sy, sz, h.w);
-                    yl[idx] = make_float4(ex_ + (l.x + d[3]), ey_ + (l.y + d[4]), ez_ + (l.z + d[5]), 0.f);
+                    const int P = idx >> 1, c = idx & 1;
+                    float* pa = reinterpret_cast<float*>(&S.hxy[P]);
+                    float* pb = reinterpret_cast<float*>(&S.hzq[P]);
+                    float* pc = reinterpret_cast<float*>(&S.lxy[P]);
+                    float* pd = reinterpret_cast<float*>(&S.lz[P]);
+                    pa[c] = -sx;
+                    pa[2 + c] = -sy;
+                    pb[c] = -sz;
+                    pb[2 + c] = h.w;
+                    pc[c] = -(ex_ + (l.x + d[3]));
+                    pc[2 + c] = -(ey_ + (l.y + d[4]));
+                    pd[c] = -(ez_ + (l.z + d[5]));
+                }
+                if ((ns & 1) && lane == 0) {        // an odd count: a massless partner 4 away
+                    const int P = ns >> 1;
+                    reinterpret_cast<float*>(&S.hxy[P])[1] = -4.f;
+                    reinterpret_cast<float*>(&S.hxy[P])[3] = 0.f;
+                    reinterpret_cast<float*>(&S.hzq[P])[1] = 0.f;
+                    reinterpret_cast<float*>(&S.hzq[P])[3] = 0.f;
+                    reinterpret_cast<float*>(&S.lxy[P])[1] = 0.f;
+                    reinterpret_cast<float*>(&S.lxy[P])[3] = 0.f;
+                    reinterpret_cast<float*>(&S.lz[P])[1] = 0.f;
                 }
                 if (nfit == 0) jn += STAGE32;
                 else { kn += nfit; jn = 0; }
                 __syncwarp();
-                pair_sums32<PSI, MASK>(yh, yl, ns, sa, lpa, tha, tla, acc_a);
-                if (nb) pair_sums32<PSI, MASK>(yh, yl, ns, sb, lpb, thb, tlb, acc_b);
+                pair_sums32<PSI, MASK>(S, (ns + 1) >> 1, sa, lpa, tha, tla, acc_a);
+                if (nb) pair_sums32<PSI, MASK>(S, (ns + 1) >> 1, sb, lpb, thb, tlb, acc_b);
             }
 #pragma unroll
             for (int c = 0; c < 5; ++c) {
