@@ -43,6 +43,7 @@ namespace sfmm {
 namespace {
 
 constexpr int TILE = 64;                 // pairs per tile
+constexpr int TC_CTAS = 5;               // CTAs per SM: registers capped for 5; 5 x 64 TMEM columns <= 512
 constexpr int WAIT_LIMIT = 1 << 26;
 
 struct __align__(16) XGeo32T {             // same layout as expand.cu's XGeo32
@@ -79,20 +80,34 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity)
     return done != 0;
 }
 
-// Binomial coefficients C(n, k), n, k <= 33, from Pascal's rule at compile time.
+// Binomial coefficients C(n, k), n, k <= 33 (all below 2^31), from Pascal's rule
+// at compile time.
 struct BinomTable {
-    double c[34][34];
+    uint32_t c[34][34];
 };
 constexpr BinomTable make_binom()
 {
     BinomTable b{};
     for (int n = 0; n < 34; ++n) {
-        b.c[n][0] = 1.0;
+        b.c[n][0] = 1u;
         for (int k = 1; k <= n; ++k) b.c[n][k] = b.c[n - 1][k - 1] + b.c[n - 1][k];
     }
     return b;
 }
 __constant__ BinomTable kBinom = make_binom();
+
+// An integer below 2^31 as up to three BF16 terms (hi, mid, lo) whose sum is the
+// integer to 24 bits (exactly when it has at most 24 significant bits): each
+// term is the BF16 rounding of the remainder, taken in integer arithmetic.
+__device__ __forceinline__ void split_int_bf16(uint32_t c, int n, __nv_bfloat16* t)
+{
+    int64_t rem = c;
+    for (int i = 0; i < n; ++i) {
+        const float f = (float)rem;                      // |rem| < 2^31: one rounding to 24 bits
+        t[i] = __float2bfloat16_rn(f);
+        rem -= (int64_t)__bfloat162float(t[i]);           // the term is an integer (|term| >= 1) or 0
+    }
+}
 
 // PK: padded order of the GEMMs (16 or 32).  PL: the orders the threads form
 // (a multiple of 8, p <= PL <= PK); columns PL..PK-1 of the A tiles are zero.
@@ -218,7 +233,7 @@ __device__ __forceinline__ void tc_sync()
 }
 
 template <int PK, int PL>
-__global__ void __launch_bounds__(128) k_m2l_tc(int64_t n_pairs, const uint64_t* __restrict__ ptgt,
+__global__ void __launch_bounds__(128, TC_CTAS) k_m2l_tc(int64_t n_pairs, const uint64_t* __restrict__ ptgt,
                                                 const uint32_t* __restrict__ psrc, const XGeo32T* __restrict__ geo,
                                                 const float* __restrict__ mpole, float* __restrict__ local, int p,
                                                 uint32_t* __restrict__ leftover, uint32_t* __restrict__ n_leftover,
@@ -239,15 +254,14 @@ __global__ void __launch_bounds__(128) k_m2l_tc(int64_t n_pairs, const uint64_t*
     // zero outside p x p; each split into BF16 terms of the FP64 integer (exact for p <= 16)
     for (int e = tid; e < PK * PK; e += blockDim.x) {
         const int r = e / PK, k = e % PK;
-        double c2 = kBinom.c[k + 1][r + 1], c1 = kBinom.c[r][k];     // C(k+1, r+1), C(r, k) (0 when k < r / k > r)
-        if (r >= p || k >= p) { c2 = 0.0; c1 = 0.0; }
-        double rem2 = c2, rem1 = c1;
+        uint32_t c2 = kBinom.c[k + 1][r + 1], c1 = kBinom.c[r][k];   // C(k+1, r+1), C(r, k) (0 when k < r / k > r)
+        if (r >= p || k >= p) { c2 = 0u; c1 = 0u; }
+        __nv_bfloat16 t2[SB], t1[SB];
+        split_int_bf16(c2, SB, t2);
+        split_int_bf16(c1, SB, t1);
         for (int sp = 0; sp < SB; ++sp) {
-            const __nv_bfloat16 h2 = __float2bfloat16_rn((float)rem2), h1 = __float2bfloat16_rn((float)rem1);
-            *(__nv_bfloat16*)(S->b2[sp] + kmaj_off(r, k, SBO)) = h2;
-            *(__nv_bfloat16*)(S->b1[sp] + kmaj_off(r, k, SBO)) = h1;
-            rem2 -= (double)__bfloat162float(h2);
-            rem1 -= (double)__bfloat162float(h1);
+            *(__nv_bfloat16*)(S->b2[sp] + kmaj_off(r, k, SBO)) = t2[sp];
+            *(__nv_bfloat16*)(S->b1[sp] + kmaj_off(r, k, SBO)) = t1[sp];
         }
     }
     if (tid == 0) {
@@ -419,12 +433,11 @@ cudaError_t launch_inst(int64_t n_pairs, const uint64_t* ptgt, const uint32_t* p
                                   (int)cudaSharedmemCarveoutMaxShared)) ||
         (e = cudaGetDevice(&dev)) || (e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)))
         return e;
-    // As many CTAs per SM as their tensor-memory columns allow (512 per SM):
-    // those the registers and shared memory do not hold at once start when
-    // others exit, and every CTA takes tiles from the counter until none are
-    // left, so the work balances whatever the residency.
+    // TC_CTAS per SM (what __launch_bounds__ sizes the registers for); every CTA
+    // takes tiles from the counter until none are left, so the work balances
+    // whatever the residency (CTAs an SM cannot hold yet start when others exit)
     const int64_t n_tiles = (n_pairs + TILE - 1) / TILE;
-    const int64_t cap = (int64_t)sms * (512 / (PK <= 16 ? 32 : 64));
+    const int64_t cap = (int64_t)sms * TC_CTAS;
     const int64_t grid = n_tiles < cap ? n_tiles : cap;
     k_m2l_tc<PK, PL><<<(unsigned)grid, 128, smem, s>>>(n_pairs, ptgt, psrc, geo, mpole, local, p, leftover, n_leftover,
                                                         tile_ctr, status);
