@@ -121,7 +121,9 @@ cudaError_t exclusive_scan_t(const T* in, T* out, int64_t n, T* total, void* tmp
 // keys [512 w, 512 w + 512) of its tile, loaded in 16 coalesced rounds of 32.
 constexpr int RS_T = 256, RS_I = 16, RS_TILE = RS_T * RS_I, RS_W = RS_T / 32;
 constexpr int RS_WC = 257;                        // per-warp digit counters (+1 slot for keys past n)
-constexpr size_t RS_SMEM = (size_t)RS_TILE * 12 + (size_t)RS_W * RS_WC * 4 + 3 * 256 * 4 + 64;
+// the tile's keys, then its values, reordered through one 8-byte-per-key buffer,
+// plus the digit of every reordered slot
+constexpr size_t RS_SMEM = (size_t)RS_TILE * 9 + (size_t)RS_W * RS_WC * 4 + 3 * 256 * 4 + 64;
 
 __global__ void __launch_bounds__(RS_T) k_rs_hist(const uint64_t* __restrict__ keys, int64_t n, int shift,
                                                  uint32_t* __restrict__ hist, int64_t ntiles)
@@ -139,33 +141,41 @@ __global__ void __launch_bounds__(RS_T) k_rs_hist(const uint64_t* __restrict__ k
 }
 
 // One tile: stable rank of every key among the tile's keys of its digit
-// (warp-private counters advanced round by round, match-any within a round),
-// counts turned into per-warp offsets by a scan over (digit, warp), the tile
-// reordered by digit in shared memory, then written out as runs per digit at
-// the tile's global digit offsets (the scanned histogram).
-__global__ void __launch_bounds__(RS_T) k_rs_scatter(const uint64_t* __restrict__ kin, const uint32_t* __restrict__ vin,
+// (warp-private counters advanced round by round; within a round the lanes of
+// equal digit are found with eight ballots, one per digit bit), counts turned
+// into per-warp offsets by a scan over (digit, warp), then the tile's keys and
+// afterwards its values reordered by digit through one shared buffer and
+// written out as runs per digit at the tile's global digit offsets (the
+// scanned histogram).  Only the digits (packed four to a register) and the
+// ranks stay in registers between the phases; keys and values are read again
+// (from L2) when they are reordered, which keeps four CTAs on an SM.
+__global__ void __launch_bounds__(RS_T, 4) k_rs_scatter(const uint64_t* __restrict__ kin, const uint32_t* __restrict__ vin,
                                                     uint64_t* __restrict__ kout, uint32_t* __restrict__ vout,
                                                     int64_t n, int shift, const uint32_t* __restrict__ offs,
                                                     int64_t ntiles)
 {
     extern __shared__ __align__(16) unsigned char rs_smem[];
     uint64_t* sk = reinterpret_cast<uint64_t*>(rs_smem);
-    uint32_t* sv = reinterpret_cast<uint32_t*>(sk + RS_TILE);
-    uint32_t* wc = sv + RS_TILE;                          // [RS_W][RS_WC]
+    uint32_t* sv = reinterpret_cast<uint32_t*>(rs_smem);   // the same bytes, once the keys are out
+    uint32_t* wc = reinterpret_cast<uint32_t*>(sk + RS_TILE);   // [RS_W][RS_WC]
     uint32_t* tbase = wc + RS_W * RS_WC;                  // tile-local start of each digit
     uint32_t* gbase = tbase + 256;                        // global start of this tile's keys of each digit
     uint32_t* s_warp = gbase + 256;                       // scan scratch
+    uint8_t* sdig = reinterpret_cast<uint8_t*>(s_warp + 16);   // digit of each reordered slot
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t tile0 = (int64_t)blockIdx.x * RS_TILE;
     const int64_t w0 = tile0 + (int64_t)warp * (32 * RS_I);
-    uint64_t k[RS_I];
-    uint32_t v[RS_I];
-    uint32_t loc[RS_I];
+    uint32_t dig[RS_I / 4];                               // digits, four to a register
+    uint32_t loc[RS_I / 2];                               // slots (< 2^13), two to a register
+#pragma unroll
+    for (int r = 0; r < RS_I / 4; ++r) dig[r] = 0u;
+#pragma unroll
+    for (int r = 0; r < RS_I / 2; ++r) loc[r] = 0u;
 #pragma unroll
     for (int r = 0; r < RS_I; ++r) {
         const int64_t e = w0 + r * 32 + lane;
-        k[r] = e < n ? kin[e] : 0ull;
-        v[r] = e < n ? vin[e] : 0u;
+        const uint32_t d = e < n ? (uint32_t)((kin[e] >> shift) & 255u) : 0u;
+        dig[r >> 2] |= d << (8 * (r & 3));
     }
     for (int d = lane; d < RS_WC; d += 32) wc[warp * RS_WC + d] = 0;
     gbase[tid] = offs[(int64_t)tid * ntiles + blockIdx.x];
@@ -174,12 +184,20 @@ __global__ void __launch_bounds__(RS_T) k_rs_scatter(const uint64_t* __restrict_
 #pragma unroll
     for (int r = 0; r < RS_I; ++r) {
         const int64_t e = w0 + r * 32 + lane;
-        const int d = e < n ? (int)((k[r] >> shift) & 255u) : 256;
-        const unsigned peers = __match_any_sync(FULL, d);
+        const bool in = e < n;
+        const int d = in ? (int)((dig[r >> 2] >> (8 * (r & 3))) & 255u) : 256;
+        // lanes holding the same digit (keys past n: their own slot 256)
+        unsigned peers = __ballot_sync(FULL, !in);
+        peers = in ? ~peers : peers;
+#pragma unroll
+        for (int b = 0; b < 8; ++b) {
+            const unsigned m = __ballot_sync(FULL, (d >> b) & 1);
+            peers &= ((d >> b) & 1) ? m : ~m;
+        }
         const uint32_t before = wc[warp * RS_WC + d];
         __syncwarp();
         if ((peers & lt) == 0) wc[warp * RS_WC + d] = before + (uint32_t)__popc(peers);
-        loc[r] = before + (uint32_t)__popc(peers & lt);
+        loc[r >> 1] |= (before + (uint32_t)__popc(peers & lt)) << (16 * (r & 1));
         __syncwarp();
     }
     __syncthreads();
@@ -212,26 +230,35 @@ __global__ void __launch_bounds__(RS_T) k_rs_scatter(const uint64_t* __restrict_
     __syncthreads();
     tbase[tid] = inc - tot + s_warp[warp];
     __syncthreads();
-    // reorder the tile by digit in shared memory
+    // keys to their places in the tile's digit order (read again, from L2)
 #pragma unroll
     for (int r = 0; r < RS_I; ++r) {
         const int64_t e = w0 + r * 32 + lane;
         if (e < n) {
-            const int d = (int)((k[r] >> shift) & 255u);
-            const uint32_t pos = tbase[d] + wc[warp * RS_WC + d] + loc[r];
-            sk[pos] = k[r];
-            sv[pos] = v[r];
+            const int d = (int)((dig[r >> 2] >> (8 * (r & 3))) & 255u);
+            loc[r >> 1] += (tbase[d] + wc[warp * RS_WC + d]) << (16 * (r & 1));
+            const uint32_t slot = (loc[r >> 1] >> (16 * (r & 1))) & 0xFFFFu;
+            sk[slot] = kin[e];
+            sdig[slot] = (uint8_t)d;
         }
     }
     __syncthreads();
-    // runs of equal digits go to consecutive global positions
+    // runs of equal digits go to consecutive global positions: keys, then values
     const int cnt = (int)((n - tile0) < RS_TILE ? (n - tile0) : RS_TILE);
     for (int i = tid; i < cnt; i += RS_T) {
-        const uint64_t key = sk[i];
-        const int d = (int)((key >> shift) & 255u);
-        const uint32_t p = gbase[d] + (uint32_t)i - tbase[d];
-        kout[p] = key;
-        vout[p] = sv[i];
+        const int d = sdig[i];
+        kout[gbase[d] + (uint32_t)i - tbase[d]] = sk[i];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < RS_I; ++r) {
+        const int64_t e = w0 + r * 32 + lane;
+        if (e < n) sv[(loc[r >> 1] >> (16 * (r & 1))) & 0xFFFFu] = vin[e];
+    }
+    __syncthreads();
+    for (int i = tid; i < cnt; i += RS_T) {
+        const int d = sdig[i];
+        vout[gbase[d] + (uint32_t)i - tbase[d]] = sv[i];
     }
 }
 
