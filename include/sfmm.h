@@ -196,7 +196,7 @@ int sfmm_order(sfmm_plan_t plan);
  *   n_nodes, n_leaves, depth : the tree of Sec. 3.1 (depth = deepest level used)
  *   n_m2l, n_p2p             : FMM-act and direct-act pairs of Algorithm 1
  *   p2p_interactions         : source-target point pairs evaluated directly (counted
- *                              only while timing is on, else 0)
+ *                              only while timing is at level 2, else 0)
  *   launches                 : kernel launches of the solve
  *   ms[8]                    : device time of the phases (only while timing is on):
  *                              keys+sort, tree+geometry, up-pass, lists, M2L, L2L,
@@ -208,7 +208,9 @@ typedef struct {
 } sfmm_stats;
 sfmm_status sfmm_get_stats(sfmm_plan_t plan, sfmm_stats* out);
 
-/* Record per-phase device times (CUDA events) in later solves: 1 on, 0 off (default off). */
+/* Record per-phase device times (CUDA events) in later solves: 0 off (default), 1 phase
+ * times, 2 phase times and the count of near-field point pairs (one more kernel and a
+ * host synchronisation per solve, inside the evaluation phase's time). */
 sfmm_status sfmm_set_timing(sfmm_plan_t plan, int on);
 
 /*

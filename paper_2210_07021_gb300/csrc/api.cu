@@ -431,7 +431,7 @@ sfmm_status solve(sfmm_plan_s* P, const double* src, const void* q, int64_t N, c
                          P->mpole.as<double>(), p, P->opt.zero_mean, P->opt.sigma, psi, alpha, gamma, leaf_ctr, s);
     if (e) return cuda_fail(P, e, "evaluation");
     tm.mark();
-    if (P->timing) {
+    if (P->timing >= 2) {
         // near-field source-target pairs (for the throughput of the evaluation kernel)
         unsigned long long* cnt = reinterpret_cast<unsigned long long*>(P->small.as<int64_t>() + 16);
         if ((e = cudaMemsetAsync(cnt, 0, 8, s))) return cuda_fail(P, e, "memset");
@@ -783,7 +783,8 @@ sfmm_status sfmm_get_stats(sfmm_plan_t plan, sfmm_stats* out)
 sfmm_status sfmm_set_timing(sfmm_plan_t plan, int on)
 {
     if (!plan) return SFMM_EINVAL;
-    plan->timing = on != 0;
+    if (on < 0 || on > 2) return fail(plan, SFMM_EINVAL, "timing level must be 0, 1 or 2");
+    plan->timing = on;
     return SFMM_OK;
 }
 

@@ -93,7 +93,7 @@ struct sfmm_plan_s {
     std::vector<sfmm_plan_s*> lanes;       // batch lanes: solvers on their own streams
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     std::string err;
-    bool timing = false;
+    int timing = 0;                        // 0 off, 1 phase times, 2 also the near-field pair count
     sfmm_stats stats{};
 
     // sources (key-sorted)

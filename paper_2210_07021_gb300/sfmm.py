@@ -170,6 +170,7 @@ class Plan:
         return load().sfmm_order(self._h)
 
     def set_timing(self, on=True):
+        """0/False off, 1/True per-phase device times, 2 also the near-field pair count."""
         _check(load().sfmm_set_timing(self._h, int(on)), self._h)
 
     def stats(self):
