@@ -300,7 +300,8 @@ sfmm_status solve(sfmm_plan_s* P, const double* src, const void* q, int64_t N, c
     // sorts the sources, builds the tree (one host synchronisation per level)
     // and runs the up-pass.
     cudaStream_t s2 = P->aux;
-    if ((e = cudaEventRecord(P->ev_fork, s)) || (e = cudaStreamWaitEvent(s2, P->ev_fork, 0)))
+    if (P->forked) P->forked = false;
+    else if ((e = cudaEventRecord(P->ev_fork, s)) || (e = cudaStreamWaitEvent(s2, P->ev_fork, 0)))
         return cuda_fail(P, e, "fork");
     if ((e = launch_keys(tgt, M, P->tkeys.as<uint64_t>(), P->tperm.as<uint32_t>(), s2))) return cuda_fail(P, e, "tkeys");
     if ((e = radix_sort(P->tkeys.as<uint64_t>(), P->tperm.as<uint32_t>(), P->tkeys2.as<uint64_t>(),
@@ -716,13 +717,24 @@ sfmm_status sfmm_deflection_host(sfmm_plan_t plan, const double* src_xyz, const 
         (e = ensure(P->h_tgt, std::max<int64_t>(M, 1) * 24)) || (e = ensure(P->h_alpha, std::max<int64_t>(M, 1) * 16)) ||
         (psi && (e = ensure(P->h_psi, std::max<int64_t>(M, 1) * 8))))
         return cuda_fail(P, e, "alloc staging");
-    if (N > 0 && ((e = cudaMemcpyAsync(P->h_src.p, src_xyz, N * 24, cudaMemcpyHostToDevice, s)) ||
-                  (e = cudaMemcpyAsync(P->h_q.p, q, N * qb, cudaMemcpyHostToDevice, s))))
-        return cuda_fail(P, e, "copy inputs");
-    if (M > 0 && (e = cudaMemcpyAsync(P->h_tgt.p, tgt_xyz, M * 24, cudaMemcpyHostToDevice, s)))
+    // The targets are copied on the auxiliary stream, where the solve handles them
+    // (forked here, after earlier work on the plan's stream), so that copy overlaps
+    // the source copies and the sources' keys and sort.
+    if ((e = cudaEventRecord(P->ev_fork, s)) || (e = cudaStreamWaitEvent(P->aux, P->ev_fork, 0)))
+        return cuda_fail(P, e, "fork");
+    if (M > 0 && (e = cudaMemcpyAsync(P->h_tgt.p, tgt_xyz, M * 24, cudaMemcpyHostToDevice, P->aux)))
         return cuda_fail(P, e, "copy targets");
+    if (N > 0 && ((e = cudaMemcpyAsync(P->h_src.p, src_xyz, N * 24, cudaMemcpyHostToDevice, s)) ||
+                  (e = cudaMemcpyAsync(P->h_q.p, q, N * qb, cudaMemcpyHostToDevice, s)))) {
+        cudaStreamSynchronize(P->aux);
+        return cuda_fail(P, e, "copy inputs");
+    }
+    P->forked = true;
     st = solve(P, P->h_src.as<double>(), P->h_q.p, N, P->h_tgt.as<double>(), M, psi ? P->h_psi.as<double>() : nullptr,
                P->h_alpha.as<double>());
+    P->forked = false;
+    // every path out of the solve leaves no copy of the caller's targets in flight
+    if ((e = cudaStreamSynchronize(P->aux)) && st == SFMM_OK) return cuda_fail(P, e, "sync");
     if (st != SFMM_OK) return st;
     if (M > 0) {
         if ((e = cudaMemcpyAsync(alpha, P->h_alpha.p, M * 16, cudaMemcpyDeviceToHost, s)))

@@ -92,6 +92,8 @@ struct sfmm_plan_s {
     bool owns_stream = false;              // a batch lane's own stream (destroyed with the plan)
     std::vector<sfmm_plan_s*> lanes;       // batch lanes: solvers on their own streams
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    bool forked = false;                   // the next solve finds the auxiliary stream already forked
+                                           // (the host entry point copies the targets there)
     std::string err;
     int timing = 0;                        // 0 off, 1 phase times, 2 also the near-field pair count
     sfmm_stats stats{};

@@ -124,3 +124,25 @@ def test_tensor_core_m2l_matches_warp_kernel(p):
     if p >= 16:   # at p = 12 the truncation error of this sky is above 1e-6 for both paths
         ref = direct_sum(src, q, tgt[:2000])
         assert rel(psi_t[:2000], ref["psi"]) < TOL_MIXED and rel(al_t[:2000], ref["alpha"]) < TOL_MIXED
+
+
+def test_mixed_host_entry_point_matches_device_and_survives_empty_calls():
+    """The host-array entry point (targets copied on the auxiliary stream while
+    the sources are copied and sorted) gives the device path's results bit for
+    bit, also after calls that return early (no sources; no targets)."""
+    rng = np.random.default_rng(31)
+    clumps = workloads.clump_set(rng, 20)
+    src = workloads.clustered(rng, 50000, 20, clumps=clumps)
+    tgt = workloads.clustered(rng, 30001, 20, clumps=clumps)
+    q = np.full(50000, 4 * np.pi / 50000, dtype=np.float32)
+    plan = sfmm.Plan(p=20, leaf_size=64, c_s=1.3, precision=sfmm.SFMM_MIXED, q_f32=True)
+    psi, alpha = plan.deflection(dev(src), dev(q, torch.float32), dev(tgt))
+    torch.cuda.synchronize()
+    psi, alpha = psi.cpu().numpy(), alpha.cpu().numpy()
+    e_psi, e_al = plan.deflection_host(np.zeros((0, 3)), np.zeros(0, dtype=np.float32), tgt)
+    assert np.all(e_psi == 0) and np.all(e_al == 0)
+    plan.deflection_host(src, q, np.zeros((0, 3)))
+    for _ in range(2):
+        hpsi, halpha = plan.deflection_host(src, q, tgt)
+        np.testing.assert_array_equal(hpsi, psi)
+        np.testing.assert_array_equal(halpha, alpha)
