@@ -20,7 +20,7 @@ cudaError_t build_tree(sfmm_plan_s* P, const uint64_t* keys, int64_t n, int m, i
 cudaError_t tree_geometry(sfmm_plan_s* P);
 cudaError_t tree_target_ranges(sfmm_plan_s* P, const uint64_t* tkeys, int64_t M);
 cudaError_t collect_leaves(sfmm_plan_s* P, const int* cnt, Buf& out, int64_t* n_out);
-cudaError_t build_lists(sfmm_plan_s* P, const TreeView& T, double c_s, double c_t);
+cudaError_t build_lists(sfmm_plan_s* P, const TreeView& T, double c_s, double c_t, cudaStream_t s);
 void fill_tables(double* h);
 size_t xgeo_bytes(int ek);
 cudaError_t launch_geom32(int n_nodes, const double* geom, float* g32, cudaStream_t s);
@@ -331,7 +331,14 @@ sfmm_status solve(sfmm_plan_s* P, const double* src, const void* q, int64_t N, c
     TreeView T = view(P);
     if ((e = collect_leaves(P, T.count, P->leaves_src, &P->n_leaves))) return cuda_fail(P, e, "leaves");
     tm.mark();
-    // ---- up-pass
+    // ---- join the targets; target ranges (Sec. 3.7 lookup) and target leaves
+    if ((e = cudaStreamWaitEvent(s, P->ev_join, 0))) return cuda_fail(P, e, "join");
+    if ((e = tree_target_ranges(P, tkeys, M))) return cuda_fail(P, e, "target ranges");
+    T = view(P);
+    if ((e = collect_leaves(P, T.tcount, P->leaves_tgt, &P->n_leaves_tgt))) return cuda_fail(P, e, "target leaves");
+    // ---- up-pass on the plan's stream while the lists (Algorithm 1) are built on
+    // the auxiliary stream: neither needs the other's results, and the small
+    // levels of the one leave room on the GPU for the other
     const bool fp32 = precision == SFMM_MIXED;
     const bool dfe = precision == SFMM_MIXED_DF;
     const bool offsets = fp32 || dfe;                  // FP32 (hi, lo) offsets feed the near field
@@ -349,6 +356,8 @@ sfmm_status solve(sfmm_plan_s* P, const double* src, const void* q, int64_t N, c
     }
     if ((e = launch_child_geo(T, P->geom32.as<float>(), P->m2m_geo.p, P->l2l_geo.p, ek, s)))
         return cuda_fail(P, e, "child geometry");
+    if ((e = cudaEventRecord(P->ev_fork, s)) || (e = cudaStreamWaitEvent(P->aux, P->ev_fork, 0)))
+        return cuda_fail(P, e, "fork lists");
     if (offsets) {
         if ((e = ensure(P->soff, (size_t)N * 32))) return cuda_fail(P, e, "alloc");
         if ((e = launch_src_offsets(T, P->leaves_src.as<int>(), P->n_leaves, P->src4.as<double4_32a>(),
@@ -366,12 +375,15 @@ sfmm_status solve(sfmm_plan_s* P, const double* src, const void* q, int64_t N, c
                             P->mpole.p, ek, s)))
             return cuda_fail(P, e, "M2M");
     tm.mark();
-    // ---- join the targets; target ranges (Sec. 3.7 lookup) and target leaves; lists
-    if ((e = cudaStreamWaitEvent(s, P->ev_join, 0))) return cuda_fail(P, e, "join");
-    if ((e = tree_target_ranges(P, tkeys, M))) return cuda_fail(P, e, "target ranges");
-    T = view(P);
-    if ((e = collect_leaves(P, T.tcount, P->leaves_tgt, &P->n_leaves_tgt))) return cuda_fail(P, e, "target leaves");
-    if ((e = build_lists(P, T, P->opt.c_s, P->opt.c_t))) return cuda_fail(P, e, "lists");
+    // ---- lists on the auxiliary stream (its host synchronisation waits for the
+    // walk only), joined back before M2L; the "lists" phase is the part of the walk
+    // the up-pass did not hide
+    if ((e = build_lists(P, T, P->opt.c_s, P->opt.c_t, P->aux))) {
+        cudaStreamSynchronize(s);
+        return cuda_fail(P, e, "lists");
+    }
+    if ((e = cudaEventRecord(P->ev_join, P->aux)) || (e = cudaStreamWaitEvent(s, P->ev_join, 0)))
+        return cuda_fail(P, e, "join lists");
     tm.mark();
     // ---- M2L
     if ((e = cudaMemsetAsync(P->local.p, 0, (size_t)nn * EXP_STRIDE * esz, s))) return cuda_fail(P, e, "memset");

@@ -364,9 +364,8 @@ inline int bits_for(int64_t n)
 }  // namespace
 
 // Run Algorithm 1 and build the grouped M2L and P2P lists in the plan.
-cudaError_t build_lists(sfmm_plan_s* P, const TreeView& T, double c_s, double c_t)
+cudaError_t build_lists(sfmm_plan_s* P, const TreeView& T, double c_s, double c_t, cudaStream_t s)
 {
-    cudaStream_t s = P->stream;
     cudaError_t e;
     const int depth = (int)P->level_start.size() - 2;
     const int rounds = 2 * depth + 4;
