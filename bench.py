@@ -43,6 +43,12 @@ MODES = [("mixed", 1, 20, 1e-6, 64, 1.3, 0.5), ("mixed_df", 2, 28, 1e-10, 64, 2.
 # algorithmic FP64 flops per near-field pair: d^2 (3 sub, 3 mul, 2 add), 1/d^2
 # (counted as 4), q/d^2 (1), alpha sums (3 mul + 3 add), sum q (1); psi adds the
 # log (counted as 4) and its multiply-add (2)
+# DRAM bytes of one k_eval32 launch (near field + L2P, 1e-6 path) at the
+# benchmark workload (N = M = 1.6e7, p = 20, m = 64, c_s = 1.3, c_t = 0.5),
+# measured by ncu (dram__bytes_read.sum 5.33 GB + dram__bytes_write.sum 1.01 GB):
+# about 3.6x the bytes the kernel must move (sources re-staged by neighbouring
+# target leaves; 16- and 8-byte output writes at scattered positions)
+K_EVAL32_TRAFFIC = 5.33e9 + 1.01e9
 FLOPS_PER_PAIR_DEFL = 20
 FLOPS_PER_PAIR_PSI = 26
 DTYPES = {"mixed": "f32+f64", "mixed_df": "f32x2+f64", "fp64": "f64"}
@@ -500,10 +506,16 @@ def run_sfmm(args):
                 "derived: 152 SMs x 128 FP32 FMA/clk x 2 flop x 2.07 GHz (not in MEASURED_PEAKS.json; " \
                 "an FMA loop measured 73 TFLOP/s)"
         ach = r["pairs"] * FLOPS_PER_PAIR_PSI / (r["eval_ms"] / 1e3)
-        return {"bound": bound, "kernel": kern, "achieved": ach / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
-                "frac": ach / peak, "peak_source": src_,
-                "work_per_unit": f"{FLOPS_PER_PAIR_PSI} flop per near-field pair (1/d^2 and log counted as 4)",
-                "pairs_per_launch": r["pairs"], "launch_ms": r["eval_ms"], "traffic": None}
+        out = {"bound": bound, "kernel": kern, "achieved": ach / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
+               "frac": ach / peak, "peak_source": src_,
+               "work_per_unit": f"{FLOPS_PER_PAIR_PSI} flop per near-field pair (1/d^2 and log counted as 4)",
+               "pairs_per_launch": r["pairs"], "launch_ms": r["eval_ms"], "traffic": None}
+        if (r["precision"] == "mixed" and r["leaf_size"] == 64 and N == 16_000_000 and M == 16_000_000
+                and args.clumps == 20_000):
+            out["traffic"] = K_EVAL32_TRAFFIC
+            out["traffic_source"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch of k_eval32 "
+                                     "at this workload (5.33 GB read + 1.01 GB written)")
+        return out
 
     modes = {}
     for name, *_ in wanted:
