@@ -73,3 +73,24 @@ def test_autotune_meets_its_stated_error():
     idx = workloads.subsample(tgt.shape[0], 300, 43)
     ref = direct_sum(src, q, tgt[idx])
     assert rel(alpha.cpu().numpy()[idx], ref["alpha"]) < 1e-6 and rel(psi.cpu().numpy()[idx], ref["psi"]) < 1e-6
+
+
+def test_autotune_falls_back_to_a_format_that_reaches_the_target():
+    """A target below the FP32 path's reach (1e-9): its candidates all fail, the
+    double-float fallback is tuned instead and its choice meets the target."""
+    rng = np.random.default_rng(44)
+    clumps = workloads.clump_set(rng, 20)
+    src = workloads.clustered(rng, 60000, 20, clumps=clumps)
+    tgt = workloads.clustered(rng, 30000, 20, clumps=clumps)
+    q = np.full(60000, 4 * np.pi / 60000)
+    r = tune.autotune(dev(src), dev(q), dev(tgt), sfmm.SFMM_MIXED, 1e-9, sample=300,
+                      candidates=[dict(p=20, leaf_size=64, c_s=1.3, c_t=0.5)], fallback=sfmm.SFMM_MIXED_DF,
+                      fallback_candidates=[dict(p=28, leaf_size=64, c_s=2.0, c_t=0.45)])
+    assert r["precision"] == sfmm.SFMM_MIXED_DF
+    assert [row["precision"] for row in r["table"]] == [sfmm.SFMM_MIXED, sfmm.SFMM_MIXED_DF]
+    assert not r["table"][0]["ok"] and r["table"][1]["ok"]
+    plan = sfmm.Plan(precision=r["precision"], **r["best"])
+    psi, alpha = plan.deflection(dev(src), dev(q), dev(tgt))
+    idx = workloads.subsample(tgt.shape[0], 200, 44)
+    ref = direct_sum(src, q, tgt[idx])
+    assert rel(alpha.cpu().numpy()[idx], ref["alpha"]) < 1e-9 and rel(psi.cpu().numpy()[idx], ref["psi"]) < 1e-9
