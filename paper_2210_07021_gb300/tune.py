@@ -67,7 +67,8 @@ def _tune(src, q, tgt, precision, stated, cands, idx, r_psi, r_alpha, repeats, s
     best = None
     for c in cands:
         kw = dict(c)
-        kw.setdefault("c_s", 2.0)
+        kw.setdefault("c_s", 2.0)                 # the library's default MAC constants
+        kw.setdefault("c_t", 0.5)
         plan = sfmm.Plan(precision=precision, q_f32=q_f32, **kw)
         psi, alpha = plan.deflection(src, q, tgt)
         stream = torch.cuda.current_stream()
