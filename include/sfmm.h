@@ -60,10 +60,17 @@ typedef enum {
 
 enum {
     SFMM_FP64 = 0,         /* every step in float64                                                */
-    SFMM_MIXED = 1,        /* relative error near 1e-6: expansions, translations and the near field
-                              in float32, M2L on the tensor cores as split-bfloat16 products       */
-    SFMM_MIXED_DF = 2      /* relative error near 1e-10: expansions and translations in float64,
-                              the near field in double-float (pairs of float32) on the FP32 pipe   */
+    SFMM_MIXED = 1,        /* stated relative error 1e-6: the near field (the bulk of the pairs) in
+                              float32 on (hi, lo) offsets with compensated sums; the far field
+                              (P2M, M2M, M2L, L2L, L2P) and its combination with the near field in
+                              double-float (pairs of float32, about 48 bits) on the FP32 pipe      */
+    SFMM_MIXED_DF = 2,     /* stated relative error 1e-10: as SFMM_MIXED with the near field in
+                              double-float too                                                     */
+    SFMM_FP32 = 3          /* everything in float32, M2L on the tensor cores as split-bfloat16
+                              products: fastest; error about 1e-6 where the targets follow the
+                              mass, but a floor of roughly eps_f32 * Q / |alpha| (up to ~1e-5)
+                              on targets in smooth or empty sky, where the near and far fields
+                              nearly cancel                                                        */
 };
 
 typedef struct {
@@ -76,7 +83,7 @@ typedef struct {
     int64_t n_max, m_max;  /* optional: size the workspace for up to n_max sources and m_max targets
                               at plan time (0 = grow on first use)                                  */
     void* stream;          /* cudaStream_t to enqueue on; NULL = the legacy default stream          */
-    int m2l_tensor_cores;  /* SFMM_MIXED only: 1 (default) = M2L as split-BF16 tcgen05 GEMMs, 0 = FP32 warp kernel */
+    int m2l_tensor_cores;  /* SFMM_FP32 only: 1 (default) = M2L as split-BF16 tcgen05 GEMMs, 0 = FP32 warp kernel */
     double sigma;          /* Near Particle Model (Secs. 3.2, 4.2): each mass spread over a cap of angular
                               radius sigma with the Epanechnikov profile of Eq. KERNEL; 0 (default) = point
                               masses.  Inside the cap alpha follows from Gauss's law on the sphere
@@ -232,7 +239,7 @@ sfmm_status sfmm_set_timing(sfmm_plan_t plan, int on);
  *   SFMM_ARR_P2P           int32  [n_p2p][2]  (source leaf, target leaf) grouped by target
  *   SFMM_ARR_TGT_KEYS      uint64 [M]      sorted keys of the targets
  *   SFMM_ARR_NODE_TRANGE   int32  [nodes][2]  first, count in the sorted targets
- *   SFMM_ARR_SRC_OFFSETS   float  [N][8]   (SFMM_MIXED / SFMM_MIXED_DF only; else 0 bytes) per sorted
+ *   SFMM_ARR_SRC_OFFSETS   float  [N][8]   (every format but SFMM_FP64; else 0 bytes) per sorted
  *                                          source: hi x, y, z, q, then lo x, y, z, q of its offset from
  *                                          its leaf's centre and of its mass (value = hi + lo)
  *   SFMM_ARR_TGT_OFFSETS   float  [M][8]   (as above) per sorted target: hi x, y, z, 0, lo x, y, z, 0

@@ -43,6 +43,15 @@ cudaError_t launch_m2l_tc(int64_t n_pairs, const uint64_t* ptgt, const uint32_t*
                           uint32_t* tile_ctr, int* status, cudaStream_t s);
 cudaError_t launch_l2l(const TreeView& T, int a, int b, int p, const double* tables, const void* geo, void* local,
                        int ek, cudaStream_t s);
+cudaError_t launch_pair_geo_rho(const TreeView& T, const uint64_t* tt, const uint32_t* ss, int64_t n, void* out,
+                                cudaStream_t s);
+cudaError_t launch_m2l_pair(int64_t n_pairs, const uint64_t* ptgt, const uint32_t* psrc, const void* geo,
+                            const void* mpole, int p, double* acc, uint32_t* leftover, uint32_t* n_left,
+                            cudaStream_t s);
+cudaError_t launch_m2l_left_df(const TreeView& T, const uint64_t* ptgt, const uint32_t* psrc, const uint32_t* list,
+                               const uint32_t* n_list, int64_t max_list, int p, const double* tables,
+                               const void* mpole, double* acc, cudaStream_t s);
+cudaError_t launch_acc_to_df(int64_t n, const double* acc, void* out, cudaStream_t s);
 cudaError_t launch_unscale(int n_nodes, const double* geom, const void* in, double* out, int p, int is_local,
                            int ek, cudaStream_t s);
 cudaError_t launch_eval32_prep(const TreeView& T, const int* leaves, int64_t n_leaves, const double4_32a* tgt,
@@ -50,7 +59,7 @@ cudaError_t launch_eval32_prep(const TreeView& T, const int* leaves, int64_t n_l
                                cudaStream_t s);
 cudaError_t launch_eval32(const TreeView& T, const int* leaves, int64_t n_leaves, const float4* soff,
                           const float4* toff, const float4* dc, const double4_32a* tgt, const uint32_t* tperm, const int64_t* p2p_off,
-                          const uint32_t* p2p_src, const float* local, const float* mpole, int p, int zero_mean,
+                          const uint32_t* p2p_src, const void* local, const void* mpole, bool dfar, int p, int zero_mean,
                           double* psi, double* alpha, bool coincide, unsigned long long* leaf_ctr,
                           cudaStream_t s);
 cudaError_t launch_count_pairs(const TreeView& T, const int* leaves, int64_t n_leaves, const int64_t* p2p_off,
@@ -339,8 +348,9 @@ sfmm_status solve(sfmm_plan_s* P, const double* src, const void* q, int64_t N, c
     // ---- up-pass on the plan's stream while the lists (Algorithm 1) are built on
     // the auxiliary stream: neither needs the other's results, and the small
     // levels of the one leave room on the GPU for the other
-    const bool fp32 = precision == SFMM_MIXED;
-    const bool dfe = precision == SFMM_MIXED_DF;
+    const bool fp32 = precision == SFMM_FP32;          // expansions and translations in FP32
+    const bool dfe = precision == SFMM_MIXED || precision == SFMM_MIXED_DF;   // ... in double-float
+    const bool near32 = precision == SFMM_FP32 || precision == SFMM_MIXED;    // FP32 near field
     const bool offsets = fp32 || dfe;                  // FP32 (hi, lo) offsets feed the near field
     const int ek = fp32 ? EXP_F32 : dfe ? EXP_DF : EXP_F64;
     const size_t esz = fp32 ? 4 : 8;                   // expansion storage: float, double or double-float
@@ -386,14 +396,33 @@ sfmm_status solve(sfmm_plan_s* P, const double* src, const void* q, int64_t N, c
         return cuda_fail(P, e, "join lists");
     tm.mark();
     // ---- M2L
-    if ((e = cudaMemsetAsync(P->local.p, 0, (size_t)nn * EXP_STRIDE * esz, s))) return cuda_fail(P, e, "memset");
     const uint32_t* m2l_s = P->m2l_alt ? P->m2l_s2.as<uint32_t>() : P->m2l_s.as<uint32_t>();
     const uint64_t* m2l_t = P->m2l_alt ? P->m2l_t2.as<uint64_t>() : P->m2l_t.as<uint64_t>();
     if ((e = ensure(P->m2l_geo, (size_t)std::max<int64_t>(P->n_m2l, 1) * xgeo_bytes(ek)))) return cuda_fail(P, e, "alloc");
-    if ((e = launch_pair_geo(T, P->geom32.as<float>(), m2l_t, m2l_s, P->n_m2l, P->m2l_geo.p, ek, s)))
-        return cuda_fail(P, e, "pair geometry");
     int* status = reinterpret_cast<int*>(P->small.as<int64_t>() + 20);
-    if (fp32 && P->opt.m2l_tensor_cores) {
+    if (dfe) {
+        // double-float M2L, one thread per pair, summed per target box in FP64
+        // accumulators; pairs with centres near antipodes go to the warp kernel
+        const size_t nacc = (size_t)nn * EXP_STRIDE;
+        uint32_t* n_left = reinterpret_cast<uint32_t*>(P->small.as<int64_t>() + 21);
+        if ((e = ensure(P->m2l_acc, nacc * 8)) || (e = ensure(P->leftover, (size_t)std::max<int64_t>(P->n_m2l, 1) * 4)))
+            return cuda_fail(P, e, "alloc");
+        if ((e = cudaMemsetAsync(P->m2l_acc.p, 0, nacc * 8, s)) || (e = cudaMemsetAsync(n_left, 0, 4, s)))
+            return cuda_fail(P, e, "memset");
+        if ((e = launch_pair_geo_rho(T, m2l_t, m2l_s, P->n_m2l, P->m2l_geo.p, s)))
+            return cuda_fail(P, e, "pair geometry");
+        if ((e = launch_m2l_pair(P->n_m2l, m2l_t, m2l_s, P->m2l_geo.p, P->mpole.p, p, P->m2l_acc.as<double>(),
+                                 P->leftover.as<uint32_t>(), n_left, s)))
+            return cuda_fail(P, e, "M2L");
+        if ((e = launch_m2l_left_df(T, m2l_t, m2l_s, P->leftover.as<uint32_t>(), n_left, P->n_m2l, p,
+                                    P->tables.as<double>(), P->mpole.p, P->m2l_acc.as<double>(), s)))
+            return cuda_fail(P, e, "M2L (pairs near antipodes)");
+        if ((e = launch_acc_to_df((int64_t)nacc, P->m2l_acc.as<double>(), P->local.p, s)))
+            return cuda_fail(P, e, "M2L sums");
+    } else if ((e = cudaMemsetAsync(P->local.p, 0, (size_t)nn * EXP_STRIDE * esz, s)) ||
+               (e = launch_pair_geo(T, P->geom32.as<float>(), m2l_t, m2l_s, P->n_m2l, P->m2l_geo.p, ek, s))) {
+        return cuda_fail(P, e, "pair geometry");
+    } else if (fp32 && P->opt.m2l_tensor_cores) {
         // tensor-core M2L; pairs it cannot take (centres near antipodes) go to a list for the warp kernel
         uint32_t* n_left = reinterpret_cast<uint32_t*>(P->small.as<int64_t>() + 21);
         uint32_t* tile_ctr = n_left + 1;              // zeroed by the same memset
@@ -431,9 +460,9 @@ sfmm_status solve(sfmm_plan_s* P, const double* src, const void* q, int64_t N, c
                                  P->dip4.as<double4_32a>(), P->tgt4.as<double4_32a>(), tperm, P->p2p_off.as<int64_t>(),
                                  p2p_s, P->local.as<double>(), P->mpole.as<double>(), p, P->opt.zero_mean, adj->w,
                                  adj->w_f32, psi, adj->grad3, leaf_ctr, s);
-    else if (fp32) e = launch_eval32(T, P->leaves_tgt.as<int>(), P->n_leaves_tgt, P->soff.as<float4>(),
+    else if (near32) e = launch_eval32(T, P->leaves_tgt.as<int>(), P->n_leaves_tgt, P->soff.as<float4>(),
                                 P->toff.as<float4>(), P->dc.as<float4>(), P->tgt4.as<double4_32a>(), tperm, P->p2p_off.as<int64_t>(), p2p_s,
-                                P->local.as<float>(), P->mpole.as<float>(), p, P->opt.zero_mean, psi, alpha,
+                                P->local.p, P->mpole.p, !fp32, p, P->opt.zero_mean, psi, alpha,
                                 src == tgt, leaf_ctr, s);
     else if (dfe) e = launch_eval_df(T, P->leaves_tgt.as<int>(), P->n_leaves_tgt, P->soff.as<float4>(),
                                      P->toff.as<float4>(), P->dc.as<float4>(), P->tgt4.as<double4_32a>(), tperm,
@@ -530,7 +559,8 @@ sfmm_status sfmm_plan(sfmm_plan_t* out, int max_depth, int order_p, double tol, 
     if (o.leaf_size < 1) return plan_fail("leaf_size must be >= 1");
     if (!(o.c_s > 1.0)) return plan_fail("c_s must be > 1 (Sec. 3.5)");
     if (!(o.c_t > 0.0 && o.c_t < 1.0)) return plan_fail("c_t must be in (0, 1) (Sec. 3.5)");
-    if (o.precision != SFMM_FP64 && o.precision != SFMM_MIXED && o.precision != SFMM_MIXED_DF)
+    if (o.precision != SFMM_FP64 && o.precision != SFMM_MIXED && o.precision != SFMM_MIXED_DF &&
+        o.precision != SFMM_FP32)
         return plan_fail("unknown precision");
     if (o.n_max < 0 || o.m_max < 0) return plan_fail("n_max and m_max must be >= 0");
     if (!(o.sigma >= 0.0 && o.sigma < 1.5707963267948966)) return plan_fail("sigma must be in [0, pi/2)");
@@ -771,7 +801,7 @@ void sfmm_destroy(sfmm_plan_t plan)
                   &plan->p2p_t2, &plan->p2p_s2, &plan->m2l_off, &plan->p2p_off, &plan->leaves_src,
                   &plan->leaves_tgt, &plan->m2l_geo, &plan->m2m_geo, &plan->l2l_geo, &plan->soff,
                   &plan->toff, &plan->dc, &plan->leftover, &plan->geom32, &plan->macn, &plan->logtab,
-                  &plan->ttmp, &plan->dip4, &plan->adj_h, &plan->adj_g, &plan->macn32};
+                  &plan->ttmp, &plan->dip4, &plan->adj_h, &plan->adj_g, &plan->macn32, &plan->m2l_acc};
     if (plan->aux) cudaStreamSynchronize(plan->aux);
     for (sfmm_plan_s* L : plan->lanes) sfmm_destroy(L);
     plan->lanes.clear();
@@ -881,7 +911,7 @@ sfmm_status sfmm_debug_copy(sfmm_plan_t plan, int which, void* dst, int64_t byte
         const Buf& in = which == SFMM_ARR_MULTIPOLE ? P->mpole : P->local;
         if ((e = launch_unscale((int)nn, P->n_geom.as<double>(), in.p, tmpbuf.as<double>(), p,
                                 which == SFMM_ARR_LOCAL,
-                                P->opt.precision == SFMM_MIXED ? EXP_F32 : P->opt.precision == SFMM_MIXED_DF ? EXP_DF : EXP_F64,
+                                P->opt.precision == SFMM_FP32 ? EXP_F32 : P->opt.precision == SFMM_FP64 ? EXP_F64 : EXP_DF,
                                 P->stream)) ||
             (e = cudaStreamSynchronize(P->stream)) || (e = cudaMemcpy(dst, tmpbuf.p, need, cudaMemcpyDeviceToHost))) {
             release(tmpbuf);

@@ -393,8 +393,10 @@ struct Eval32Args {
     const uint32_t* tperm;
     const int64_t* p2p_off;
     const uint32_t* p2p_src;
-    const float* local;       // FP32 local expansions (mixed path)
+    const float* local;       // FP32 local expansions (FP32 far field)
     const float* base_mpole;
+    const dflt* local_df;     // double-float local expansions (double-float far field)
+    const dflt* base_mpole_df;
     int p;
     int want_psi;
     int zero_mean;
@@ -479,9 +481,12 @@ __device__ __forceinline__ void pair_block32(const Stage32& S, int P0, int P1, i
     }
 }
 
-template <bool PSI, bool MASK>
+// COMP: the outer level of the three alpha sums is compensated (two-sum of
+// each block's sum into acc, the rounding errors collected in accl), for the
+// path whose far field is carried in double-float.
+template <bool PSI, bool MASK, bool COMP>
 __device__ __forceinline__ void pair_sums32(const Stage32& S, int npair, int sub, int lpt, const float4& th,
-                                            const float4& tl, float* acc)
+                                            const float4& tl, float* acc, float* accl)
 {
     const float2 tx = f2(th.x, th.x), ty = f2(th.y, th.y), tz = f2(th.z, th.z);
     const float2 ux = f2(tl.x, tl.x), uy = f2(tl.y, tl.y), uz = f2(tl.z, tl.z);
@@ -493,7 +498,15 @@ __device__ __forceinline__ void pair_sums32(const Stage32& S, int npair, int sub
             ix = f2(0.f, 0.f); iy = ix; iz = ix; iq = ix; il = ix;
             pair_block32<PSI, true>(S, P, pend, lpt, tx, ty, tz, ux, uy, uz, ix, iy, iz, iq, il);
         }
-        acc[0] += ix.x + ix.y; acc[1] += iy.x + iy.y; acc[2] += iz.x + iz.y;
+        if (COMP) {
+            float e0, e1, e2;
+            two_sum(acc[0], ix.x + ix.y, &acc[0], &e0);
+            two_sum(acc[1], iy.x + iy.y, &acc[1], &e1);
+            two_sum(acc[2], iz.x + iz.y, &acc[2], &e2);
+            accl[0] += e0; accl[1] += e1; accl[2] += e2;
+        } else {
+            acc[0] += ix.x + ix.y; acc[1] += iy.x + iy.y; acc[2] += iz.x + iz.y;
+        }
         acc[3] += iq.x + iq.y; acc[4] += il.x + il.y;
         P = pend;
     }
@@ -558,12 +571,106 @@ __device__ __forceinline__ void finish_target32(const Eval32Args& A, const LeafF
     }
 }
 
+// Far field in double-float (the 1e-6 path).  The far field at a target and
+// the near field of its direct-act leaves are both large next to their sum
+// wherever the mass is spread smoothly (the near leaves' field and the field
+// of the hole they leave in the far mass nearly cancel), so both are formed
+// and combined in double-float before the result is rounded.  L2P: w from
+// the (hi, lo) target offset and the leaf frame in double-float, F'(w) by a
+// double-float Horner recurrence, alpha on the chart's unit vectors
+// e_u = e_theta(L) - u (c + x), e_v = e_phi(L) - v (c + x), where the near
+// field's sums are projected (their radial part, x sum q / 2, projects to
+// zero and is left out), then one FP32 rotation onto (e_theta, e_phi) at the
+// target.  psi: F(w) by an FP32 Horner recurrence, the final sum in FP64.
+struct LeafFrameDF {
+    dflt et[3], ep[3], inv_r;   // e_theta, e_phi of the leaf frame and 1/r, rounded from FP64
+    float c2[3];                // 2 c
+};
+
+// a / b for a double-float a and an FP32 b with ib = 1/b: the leading quotient
+// and one correction from the exact remainder
+__device__ __forceinline__ dflt dfl_div_f(dflt a, float b, float ib)
+{
+    const float q1 = __fmul_rn(a.h, ib);
+    const float r = __fadd_rn(__fmaf_rn(-q1, b, a.h), a.l);
+    return dfl_fast_two_sum(q1, __fmul_rn(r, ib));
+}
+
+template <bool PSI>
+__device__ __forceinline__ void finish_target_dfar(const Eval32Args& A, const LeafFrameDF& G, const dflt* L,
+                                                   size_t tix, const float4& th, const float4& tl, const dflt* nf,
+                                                   float oq, float ol, double shift)
+{
+    const dflt tx(th.x, tl.x), ty(th.y, tl.y), tz(th.z, tl.z);
+    const float D2 = th.x * th.x + th.y * th.y + th.z * th.z;
+    const float den = 2.f - 0.5f * D2;                     // 1 + x.c
+    const float iden = 1.f / den;
+    const dflt wu = dfl_div_f(tx * G.et[0] + ty * G.et[1] + tz * G.et[2], den, iden);
+    const dflt wv = dfl_div_f(tx * G.ep[0] + ty * G.ep[1] + tz * G.ep[2], den, iden);
+    const dflt ox = wu * G.inv_r, oy = wv * G.inv_r;
+    const float oxf = ox.h, oyf = oy.h;
+    dflt hx(0.f, 0.f), hy(0.f, 0.f);
+    float frx = 0.f, fry = 0.f;
+    for (int l = A.p; l >= 1; --l) {
+        const dflt cr = L[2 * l], ci = L[2 * l + 1];
+        const dflt nhx = hx * ox - hy * oy + cr * (float)l;
+        const dflt nhy = hx * oy + hy * ox + ci * (float)l;
+        hx = nhx;
+        hy = nhy;
+        if (PSI) {
+            const float nfx = frx * oxf - fry * oyf + cr.h;
+            const float nfy = frx * oyf + fry * oxf + ci.h;
+            frx = nfx;
+            fry = nfy;
+        }
+    }
+    const dflt Fpx = hx * G.inv_r, Fpy = hy * G.inv_r;    // F'(w)
+    const dflt opw = dfl_two_sum(1.f, wu.h * wu.h + wv.h * wv.h);
+    const dflt Q = L[1];
+    const dflt au = opw * Fpx - Q * wu;
+    const dflt av = -(opw * Fpy) - Q * wv;
+    // the chart's unit vectors at the target (c + x = 2c + t)
+    const float cxx = G.c2[0] + th.x, cyy = G.c2[1] + th.y, czz = G.c2[2] + th.z;
+    const dflt eux = G.et[0] - dflt(wu.h * cxx), euy = G.et[1] - dflt(wu.h * cyy), euz = G.et[2] - dflt(wu.h * czz);
+    const dflt evx = G.ep[0] - dflt(wv.h * cxx), evy = G.ep[1] - dflt(wv.h * cyy), evz = G.ep[2] - dflt(wv.h * czz);
+    const dflt i2p(INV2PI);
+    const dflt su = au + i2p * (nf[0] * eux + nf[1] * euy + nf[2] * euz);
+    const dflt sv = av + i2p * (nf[0] * evx + nf[1] * evy + nf[2] * evz);
+    const float alu = su.h + su.l, alv = sv.h + sv.l;
+    // rotate onto (e_theta, e_phi) at the target x = c + t
+    const float xx = 0.5f * G.c2[0] + th.x, xy = 0.5f * G.c2[1] + th.y, xz = 0.5f * G.c2[2] + th.z;
+    const float rho = sqrtf(xx * xx + xy * xy);
+    float cp = 1.f, sp = 0.f;
+    if (rho > 0.f) { cp = xx / rho; sp = xy / rho; }
+    const float etx = xz * cp, ety = xz * sp, etz = -rho;
+    const float c11 = eux.h * etx + euy.h * ety + euz.h * etz, c12 = -eux.h * sp + euy.h * cp;
+    const float c21 = evx.h * etx + evy.h * ety + evz.h * etz, c22 = -evx.h * sp + evy.h * cp;
+    const uint32_t o = A.tperm[tix];
+    if (A.alpha) {
+        A.alpha[2 * (size_t)o] = (double)(alu * c11 + alv * c21);
+        A.alpha[2 * (size_t)o + 1] = (double)(alu * c12 + alv * c22);
+    }
+    if (PSI) {
+        const float Fx = frx * oxf - fry * oyf;
+        const double psi_e = (double)L[0] + (double)Q * (LOG2 + (double)log1pf(-0.25f * D2)) + 2.0 * (double)Fx;
+        A.psi[o] = psi_e + INV4PI * (LOG2 * (double)ol - LOG4 * (double)oq) + shift;
+    }
+}
+
+__device__ __forceinline__ dflt group_sum_df(dflt v, int lpt)
+{
+    for (int o = lpt >> 1; o > 0; o >>= 1) v = v + dfl_shfl_xor(v, o);
+    return v;
+}
+
 // One warp per target leaf.  The FP32 pair loop is cheap next to staging the
 // sources, so each pass over the near sources serves two groups of targets at
 // once: group a takes the largest power of two <= the targets left (at most
 // 32), group b the power of two >= what a leaves (at most 32), e.g. 18 = 16 + 2
 // and 40 = 32 + 8; each target of a group gets 32/size lanes.
-template <bool PSI, bool MASK>
+// DFAR: the far field (local expansions, L2P) in double-float and the outer
+// level of the near field's alpha sums compensated (finish_target_dfar).
+template <bool PSI, bool MASK, bool DFAR>
 __global__ void __launch_bounds__(128, 7) k_eval32(Eval32Args A)
 {
     __shared__ Stage32 s_stage[4];
@@ -571,10 +678,13 @@ __global__ void __launch_bounds__(128, 7) k_eval32(Eval32Args A)
     __shared__ int s_pre[4][33];
     __shared__ int s_first[4][32];
     __shared__ LeafFrame32 s_frame[4];
+    __shared__ LeafFrameDF s_framed[4];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     double shift = 0.0;
     if (A.zero_mean)
-        for (int b = 0; b < 12; ++b) shift += (double)A.base_mpole[(size_t)b * EXP_STRIDE + 1];
+        for (int b = 0; b < 12; ++b)
+            shift += DFAR ? (double)A.base_mpole_df[(size_t)b * EXP_STRIDE + 1]
+                          : (double)A.base_mpole[(size_t)b * EXP_STRIDE + 1];
     Stage32& S = s_stage[wid];
     int* pre = s_pre[wid];
     int* fst = s_first[wid];
@@ -585,15 +695,26 @@ __global__ void __launch_bounds__(128, 7) k_eval32(Eval32Args A)
         const int tf = A.T.tfirst[leaf], tc = A.T.tcount[leaf];
         const double* g = A.T.geom + (size_t)leaf * GEOM_STRIDE;
         const float* L = A.local + (size_t)leaf * EXP_STRIDE;
-        // the leaf frame in FP32, once per leaf, kept in shared memory
+        const dflt* Ld = A.local_df + (size_t)leaf * EXP_STRIDE;
+        // the leaf frame in FP32 (or double-float), once per leaf, kept in shared memory
         LeafFrame32& G = s_frame[wid];
+        LeafFrameDF& GD = s_framed[wid];
         __syncwarp();
-        if (lane < 3) {
-            G.et[lane] = (float)g[3 + lane];
-            G.ep[lane] = (float)g[6 + lane];
-            G.c2[lane] = (float)(2.0 * g[lane]);
+        if (DFAR) {
+            if (lane < 3) {
+                GD.et[lane] = dflt(g[3 + lane]);
+                GD.ep[lane] = dflt(g[6 + lane]);
+                GD.c2[lane] = (float)(2.0 * g[lane]);
+            }
+            if (lane == 3) GD.inv_r = dflt(1.0 / g[10]);
+        } else {
+            if (lane < 3) {
+                G.et[lane] = (float)g[3 + lane];
+                G.ep[lane] = (float)g[6 + lane];
+                G.c2[lane] = (float)(2.0 * g[lane]);
+            }
+            if (lane == 3) G.inv_r = 1.f / (float)g[10];
         }
-        if (lane == 3) G.inv_r = 1.f / (float)g[10];
         __syncwarp();
         const int64_t nb0 = A.p2p_off[leaf], nb1 = A.p2p_off[leaf + 1];
         for (int tb = 0; tb < tc;) {
@@ -610,6 +731,7 @@ __global__ void __launch_bounds__(128, 7) k_eval32(Eval32Args A)
             const float4 tha = A.toff[2 * ta], tla = A.toff[2 * ta + 1];
             const float4 thb = A.toff[2 * tbx], tlb = A.toff[2 * tbx + 1];
             float acc_a[5] = {0.f, 0.f, 0.f, 0.f, 0.f}, acc_b[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+            float accl_a[3] = {0.f, 0.f, 0.f}, accl_b[3] = {0.f, 0.f, 0.f};
             int64_t kn = nb0;
             int jn = 0;                // sources of near leaf kn already done
             while (kn < nb1) {
@@ -680,16 +802,33 @@ __global__ void __launch_bounds__(128, 7) k_eval32(Eval32Args A)
                 if (nfit == 0) jn += STAGE32;
                 else { kn += nfit; jn = 0; }
                 __syncwarp();
-                pair_sums32<PSI, MASK>(S, (ns + 1) >> 1, sa, lpa, tha, tla, acc_a);
-                if (nb) pair_sums32<PSI, MASK>(S, (ns + 1) >> 1, sb, lpb, thb, tlb, acc_b);
+                pair_sums32<PSI, MASK, DFAR>(S, (ns + 1) >> 1, sa, lpa, tha, tla, acc_a, accl_a);
+                if (nb) pair_sums32<PSI, MASK, DFAR>(S, (ns + 1) >> 1, sb, lpb, thb, tlb, acc_b, accl_b);
             }
+            if (DFAR) {
+                dflt nfa[3], nfb[3];
 #pragma unroll
-            for (int c = 0; c < 5; ++c) {
-                acc_a[c] = group_sumf(acc_a[c], lpa);
-                acc_b[c] = group_sumf(acc_b[c], lpb);
+                for (int c = 0; c < 3; ++c) {
+                    nfa[c] = group_sum_df(dfl_two_sum(acc_a[c], accl_a[c]), lpa);
+                    nfb[c] = group_sum_df(dfl_two_sum(acc_b[c], accl_b[c]), lpb);
+                }
+#pragma unroll
+                for (int c = 3; c < 5; ++c) {
+                    acc_a[c] = group_sumf(acc_a[c], lpa);
+                    acc_b[c] = group_sumf(acc_b[c], lpb);
+                }
+                if (sa == 0) finish_target_dfar<PSI>(A, GD, Ld, ta, tha, tla, nfa, acc_a[3], acc_a[4], shift);
+                if (act_b && sb == 0)
+                    finish_target_dfar<PSI>(A, GD, Ld, tbx, thb, tlb, nfb, acc_b[3], acc_b[4], shift);
+            } else {
+#pragma unroll
+                for (int c = 0; c < 5; ++c) {
+                    acc_a[c] = group_sumf(acc_a[c], lpa);
+                    acc_b[c] = group_sumf(acc_b[c], lpb);
+                }
+                if (sa == 0) finish_target32<PSI>(A, G, L, ta, tha, tla, acc_a, shift);
+                if (act_b && sb == 0) finish_target32<PSI>(A, G, L, tbx, thb, tlb, acc_b, shift);
             }
-            if (sa == 0) finish_target32<PSI>(A, G, L, ta, tha, tla, acc_a, shift);
-            if (act_b && sb == 0) finish_target32<PSI>(A, G, L, tbx, thb, tlb, acc_b, shift);
             tb += na + nb;
         }
     }
@@ -984,9 +1123,10 @@ cudaError_t launch_eval32_prep(const TreeView& T, const int* leaves, int64_t n_l
     return cudaGetLastError();
 }
 
+// local/mpole: FP32 expansions, or double-float ones when dfar (the 1e-6 path)
 cudaError_t launch_eval32(const TreeView& T, const int* leaves, int64_t n_leaves, const float4* soff,
                           const float4* toff, const float4* dc, const double4_32a* tgt, const uint32_t* tperm, const int64_t* p2p_off,
-                          const uint32_t* p2p_src, const float* local, const float* mpole, int p, int zero_mean,
+                          const uint32_t* p2p_src, const void* local, const void* mpole, bool dfar, int p, int zero_mean,
                           double* psi, double* alpha, bool coincide, unsigned long long* leaf_ctr, cudaStream_t s)
 {
     if (n_leaves == 0) return cudaSuccess;
@@ -1001,8 +1141,10 @@ cudaError_t launch_eval32(const TreeView& T, const int* leaves, int64_t n_leaves
     A.tperm = tperm;
     A.p2p_off = p2p_off;
     A.p2p_src = p2p_src;
-    A.local = local;
-    A.base_mpole = mpole;
+    A.local = dfar ? nullptr : static_cast<const float*>(local);
+    A.base_mpole = dfar ? nullptr : static_cast<const float*>(mpole);
+    A.local_df = dfar ? static_cast<const dflt*>(local) : nullptr;
+    A.base_mpole_df = dfar ? static_cast<const dflt*>(mpole) : nullptr;
     A.p = p;
     A.want_psi = psi != nullptr;
     A.zero_mean = zero_mean;
@@ -1012,13 +1154,17 @@ cudaError_t launch_eval32(const TreeView& T, const int* leaves, int64_t n_leaves
     int64_t blocks = 0;
     cudaError_t e;
     if ((e = leaf_grid(leaf_ctr, n_leaves, 7, s, &blocks))) return e;     // 7 per SM: __launch_bounds__
+#define EVAL32_LAUNCH(PSI, MASK)                                                  \
+    if (dfar) k_eval32<PSI, MASK, true><<<(unsigned)blocks, 128, 0, s>>>(A);      \
+    else k_eval32<PSI, MASK, false><<<(unsigned)blocks, 128, 0, s>>>(A);
     if (coincide) {
-        if (psi) k_eval32<true, true><<<(unsigned)blocks, 128, 0, s>>>(A);
-        else k_eval32<false, true><<<(unsigned)blocks, 128, 0, s>>>(A);
+        if (psi) { EVAL32_LAUNCH(true, true) }
+        else { EVAL32_LAUNCH(false, true) }
     } else {
-        if (psi) k_eval32<true, false><<<(unsigned)blocks, 128, 0, s>>>(A);
-        else k_eval32<false, false><<<(unsigned)blocks, 128, 0, s>>>(A);
+        if (psi) { EVAL32_LAUNCH(true, false) }
+        else { EVAL32_LAUNCH(false, false) }
     }
+#undef EVAL32_LAUNCH
     count_launch();
     return cudaGetLastError();
 }

@@ -34,6 +34,7 @@
 // kernels run in FP64 or FP32 from them.
 #include "common.cuh"
 #include "dfloat.cuh"
+#include "xgeo.cuh"
 
 namespace sfmm {
 
@@ -41,30 +42,6 @@ namespace {
 
 constexpr double INV4PI = 0.079577471545947667884;   // 1/(4 pi)
 constexpr double LOG2 = 0.69314718055994530942;
-
-// 64 bytes of translation parameters, formed in FP64.
-struct __align__(16) XGeo {
-    double a, b, g, logk;
-    double p1x, p1y, p2x, p2y;
-};
-
-// The same parameters rounded to FP32 for the mixed path, plus the fields of
-// the tensor-core M2L (u = (a ph1)^l X, Y = (b ph2)^l ..., rho = g/(a b)):
-// big = 1 when rho^32 exceeds 2^100 (centres near antipodes).
-struct __align__(16) XGeo32 {
-    float a, b, g, logk;
-    float p1x, p1y, p2x, p2y;
-    float ar, ai, br, bi;
-    float rho;
-    int big;
-    float pad[2];
-};
-
-// The FP64 parameters rounded to double-float pairs (1e-10 mixed path).
-struct __align__(16) XGeoDF {
-    dflt a, b, g, logk;
-    dflt p1x, p1y, p2x, p2y;
-};
 
 enum { K_M2M = 0, K_M2L = 1, K_L2L = 2 };
 
@@ -237,6 +214,34 @@ __global__ void k_pair_geo(TreeView T, const uint64_t* __restrict__ tt, const ui
         const double* gS = T.geom + (size_t)ss[k] * GEOM_STRIDE;
         const double* gT = T.geom + (size_t)tt[k] * GEOM_STRIDE;
         store_geo(out + k, make_geo(K_M2L, gS, gT));
+    }
+}
+
+// M2L parameters of the thread-per-pair double-float kernel (m2l_pair.cu):
+// a ph1, b ph2, rho = g/(a b) = 1/cos^2(theta/2), log sin(theta/2), in FP64 and
+// rounded once to double-float.
+__global__ void k_pair_geo_rho(TreeView T, const uint64_t* __restrict__ tt, const uint32_t* __restrict__ ss,
+                               int64_t n, XGeoRho* __restrict__ out)
+{
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+        const double* gS = T.geom + (size_t)ss[k] * GEOM_STRIDE;
+        const double* gT = T.geom + (size_t)tt[k] * GEOM_STRIDE;
+        double sh, ch;
+        cd eT, eS;
+        pair_geometry(gS, gT, &sh, &ch, &eT, &eS);
+        const double c = ch / sh;
+        const double a = c * gS[10], b = c * gT[10];
+        const double rho = ch > 0.0 ? 1.0 / (ch * ch) : 0.0;
+        XGeoRho R;
+        R.ar = dflt(a * eT.x);             // a e^{-i phi_T^(S)}
+        R.ai = dflt(-a * eT.y);
+        R.br = dflt(b * eS.x);             // b e^{-i phi_S^(T)}
+        R.bi = dflt(-b * eS.y);
+        R.rho = dflt(rho);
+        R.logk = dflt(log(sh));
+        R.big = (!(ch > 0.0) || rho > 8.7) ? 1 : 0;
+        R.pad[0] = R.pad[1] = R.pad[2] = 0;
+        out[k] = R;
     }
 }
 
@@ -843,6 +848,44 @@ __global__ void k_m2l_list(const uint64_t* __restrict__ ptgt, const uint32_t* __
     }
 }
 
+// M2L of the pairs the thread-per-pair double-float kernel leaves out (centres
+// at or near antipodes): one warp per listed pair, in double-float from the
+// a, b, g form, its parameters formed from the node centres in FP64; the
+// result is added to the FP64 accumulators of the target box.
+__global__ void k_m2l_left_df(TreeView T, const uint64_t* __restrict__ ptgt, const uint32_t* __restrict__ psrc,
+                              const uint32_t* __restrict__ list, const uint32_t* __restrict__ n_list, int p,
+                              const double* __restrict__ tables, const dflt* __restrict__ mpole,
+                              double* __restrict__ acc)
+{
+    __shared__ Tables<dflt> tb;
+    __shared__ WarpSmem<dflt> ws[4];
+    load_tables<dflt>(&tb, tables);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int64_t n = *n_list;
+    for (int64_t w = (int64_t)blockIdx.x * 4 + wid; w < n; w += (int64_t)gridDim.x * 4) {
+        const uint32_t k = list[w];
+        const int s = (int)psrc[k], t = (int)ptgt[k];
+        XGeoDF G;
+        store_geo(&G, make_geo(K_M2L, T.geom + (size_t)s * GEOM_STRIDE, T.geom + (size_t)t * GEOM_STRIDE));
+        dflt C, Q;
+        cx<dflt> X;
+        load_exp<dflt>(mpole + (size_t)s * EXP_STRIDE, lane, p, &C, &Q, &X);
+        dflt accC(0.f, 0.f), accQ(0.f, 0.f);
+        cx<dflt> accY = cmk<dflt>(dflt(0.f, 0.f), dflt(0.f, 0.f));
+        warp_translate<dflt>(p, lane, G, C, Q, X, &tb, &ws[wid], &accC, &accQ, &accY);
+        double* e = acc + (size_t)t * EXP_STRIDE;
+        if (lane == 0) { atomicAdd(e, (double)accC); atomicAdd(e + 1, (double)accQ); }
+        if (lane < p) { atomicAdd(e + 2 + 2 * lane, (double)accY.x); atomicAdd(e + 3 + 2 * lane, (double)accY.y); }
+    }
+}
+
+// FP64 accumulators -> double-float expansions (every entry)
+__global__ void k_acc_to_df(int64_t n, const double* __restrict__ acc, dflt* __restrict__ out)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = dflt(acc[i]);
+}
+
 // FP32 offset of every key-sorted source from the centre of its leaf as an
 // (hi, lo) pair (the difference to 2^-47, formed without FP64 instructions),
 // plus its mass split the same way: off[2j] = (hi, q_hi), off[2j+1] = (lo, q_lo).
@@ -1030,6 +1073,34 @@ cudaError_t launch_m2l_list(const uint64_t* ptgt, const uint32_t* psrc, const ui
     k_m2l_list<float, XGeo32, float><<<grid_for(max_list < 152 * 64 ? max_list : 152 * 64, 4), 128, 0, s>>>(
         ptgt, psrc, list, n_list, p, tables, static_cast<const XGeo32*>(geo), static_cast<const float*>(mpole),
         static_cast<float*>(local));
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pair_geo_rho(const TreeView& T, const uint64_t* tt, const uint32_t* ss, int64_t n, void* out,
+                                cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    k_pair_geo_rho<<<grid_for(n, 256), 256, 0, s>>>(T, tt, ss, n, static_cast<XGeoRho*>(out));
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_m2l_left_df(const TreeView& T, const uint64_t* ptgt, const uint32_t* psrc, const uint32_t* list,
+                               const uint32_t* n_list, int64_t max_list, int p, const double* tables,
+                               const void* mpole, double* acc, cudaStream_t s)
+{
+    if (max_list == 0) return cudaSuccess;
+    k_m2l_left_df<<<grid_for(max_list < 152 * 64 ? max_list : 152 * 64, 4), 128, 0, s>>>(
+        T, ptgt, psrc, list, n_list, p, tables, static_cast<const dflt*>(mpole), acc);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_acc_to_df(int64_t n, const double* acc, void* out, cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    k_acc_to_df<<<grid_for(n, 256), 256, 0, s>>>(n, acc, static_cast<dflt*>(out));
     count_launch();
     return cudaGetLastError();
 }

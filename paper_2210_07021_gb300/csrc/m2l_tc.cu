@@ -32,6 +32,7 @@
 // Every mbarrier wait is bounded; on time-out the kernel sets an error word,
 // waits (bounded) for its own MMAs, frees its tensor memory and returns.
 #include "common.cuh"
+#include "xgeo.cuh"
 
 #include <cuda_bf16.h>
 
@@ -45,15 +46,6 @@ namespace {
 constexpr int TILE = 64;                 // pairs per tile
 constexpr int TC_CTAS = 5;               // CTAs per SM: registers capped for 5; 5 x 64 TMEM columns <= 512
 constexpr int WAIT_LIMIT = 1 << 26;
-
-struct __align__(16) XGeo32T {             // same layout as expand.cu's XGeo32
-    float a, b, g, logk;
-    float p1x, p1y, p2x, p2y;
-    float ar, ai, br, bi;
-    float rho;
-    int big;
-    float pad[2];
-};
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -234,7 +226,7 @@ __device__ __forceinline__ void tc_sync()
 
 template <int PK, int PL>
 __global__ void __launch_bounds__(128, TC_CTAS) k_m2l_tc(int64_t n_pairs, const uint64_t* __restrict__ ptgt,
-                                                const uint32_t* __restrict__ psrc, const XGeo32T* __restrict__ geo,
+                                                const uint32_t* __restrict__ psrc, const XGeo32* __restrict__ geo,
                                                 const float* __restrict__ mpole, float* __restrict__ local, int p,
                                                 uint32_t* __restrict__ leftover, uint32_t* __restrict__ n_leftover,
                                                 uint32_t* __restrict__ tile_ctr, int* __restrict__ status)
@@ -294,7 +286,7 @@ __global__ void __launch_bounds__(128, TC_CTAS) k_m2l_tc(int64_t n_pairs, const 
         bool big = false;
         int t_node = -1;
         if (valid) {
-            const XGeo32T G = geo[k];
+            const XGeo32 G = geo[k];
             const int s = (int)psrc[k];
             t_node = (int)ptgt[k];
             const float* e = mpole + (size_t)s * EXP_STRIDE;     // rows are 8-byte aligned: float2 loads
@@ -421,7 +413,7 @@ __global__ void __launch_bounds__(128, TC_CTAS) k_m2l_tc(int64_t n_pairs, const 
 }
 
 template <int PK, int PL>
-cudaError_t launch_inst(int64_t n_pairs, const uint64_t* ptgt, const uint32_t* psrc, const XGeo32T* geo,
+cudaError_t launch_inst(int64_t n_pairs, const uint64_t* ptgt, const uint32_t* psrc, const XGeo32* geo,
                         const float* mpole, float* local, int p, uint32_t* leftover, uint32_t* n_leftover,
                         uint32_t* tile_ctr, int* status, cudaStream_t s)
 {
@@ -452,7 +444,7 @@ cudaError_t launch_m2l_tc(int64_t n_pairs, const uint64_t* ptgt, const uint32_t*
                           uint32_t* tile_ctr, int* status, cudaStream_t s)
 {
     if (n_pairs == 0) return cudaSuccess;
-    const XGeo32T* G = static_cast<const XGeo32T*>(geo);
+    const XGeo32* G = static_cast<const XGeo32*>(geo);
     const float* mp = static_cast<const float*>(mpole);
     float* lc = static_cast<float*>(local);
     if (p <= 8) return launch_inst<16, 8>(n_pairs, ptgt, psrc, G, mp, lc, p, leftover, n_leftover, tile_ctr, status, s);

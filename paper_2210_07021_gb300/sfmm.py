@@ -13,7 +13,7 @@ import numpy as np
 from . import build as _build
 
 SFMM_OK, SFMM_EINVAL, SFMM_ENOMEM, SFMM_ECUDA, SFMM_ETIMEOUT, SFMM_EDEGENERATE = range(6)
-SFMM_FP64, SFMM_MIXED, SFMM_MIXED_DF = 0, 1, 2
+SFMM_FP64, SFMM_MIXED, SFMM_MIXED_DF, SFMM_FP32 = 0, 1, 2, 3
 (ARR_SRC_KEYS, ARR_SRC_PERM, ARR_NODE_PREFIX, ARR_NODE_LEVEL, ARR_NODE_RANGE, ARR_NODE_CHILD0, ARR_NODE_PARENT,
  ARR_NODE_GEOM, ARR_MULTIPOLE, ARR_LOCAL, ARR_M2L, ARR_P2P, ARR_TGT_KEYS, ARR_NODE_TRANGE,
  ARR_SRC_OFFSETS, ARR_TGT_OFFSETS) = range(16)

@@ -6,27 +6,47 @@ solve) and its psi and alpha are compared, on a sample of targets, with an FP64
 reference solve run with a tighter MAC (c_t = 0.35, p = 32: errors near 1e-13
 on clustered skies).  The fastest candidate whose norm-wise relative error is
 at most `safety` times the stated error wins.  When none does and a fallback
-number format is given (the FP32 path cannot reach 1e-6 where the deflection
-is small next to eps_f32 times the far mass, e.g. targets in empty sky), the
-fallback's candidates are tuned the same way.  The result is a dict of Plan
-keyword arguments, the chosen number format and the measured table.
+number format is given (e.g. the all-FP32 path, whose error has a floor near
+eps_f32 Q / |alpha| on targets in smooth or empty sky, falling back to the
+1e-6 path), the fallback's candidates are tuned the same way.  The result is a
+dict of Plan keyword arguments, the chosen number format and the measured table.
 """
+import inspect
+
 import numpy as np
 
 from . import sfmm
 
+
+def _grid(ps, ms, css, cts):
+    return [dict(p=p, leaf_size=m, c_s=cs, c_t=ct) for p in ps for m in ms for cs in css for ct in cts]
+
+
 DEFAULT_CANDIDATES = {
-    # the benchmark sky's best settings and their neighbours, then smaller leaves and the
-    # default MAC (on skies whose error is set by the FP32 far field, e.g. 6e-7 at every
-    # setting above, the smaller leaves can land below the tuning margin)
-    sfmm.SFMM_MIXED: [dict(p=p, leaf_size=m, c_s=cs, c_t=0.5)
-                      for p, m, cs in ((20, 64, 1.3), (20, 48, 1.3), (20, 80, 1.3), (20, 64, 1.5), (24, 64, 1.3),
-                                       (20, 32, 1.3), (16, 32, 2.0), (16, 48, 2.0), (16, 64, 2.0), (16, 96, 2.0))]
-                     + [dict(p=14, leaf_size=64, c_s=2.0, c_t=0.45)],
-    sfmm.SFMM_MIXED_DF: [dict(p=p, leaf_size=m, c_t=ct) for p, ct in ((24, 0.4), (26, 0.45), (28, 0.5))
-                         for m in (48, 64, 96)],
-    sfmm.SFMM_FP64: [dict(p=p, leaf_size=m, c_t=ct) for p, ct in ((28, 0.45), (32, 0.5)) for m in (16, 32, 64)],
+    # the benchmark sky's best settings first, then their neighbours in p, c_s and leaf size
+    sfmm.SFMM_MIXED: _grid((20,), (64,), (1.5, 1.3, 2.0), (0.5,)) + _grid((16, 24), (64,), (1.5, 2.0), (0.5,))
+                     + _grid((20,), (48, 96), (1.5,), (0.5,)),
+    sfmm.SFMM_FP32: _grid((20,), (64, 48, 80), (1.3,), (0.5,)) + _grid((16,), (32, 64, 96), (2.0,), (0.5,)),
+    sfmm.SFMM_MIXED_DF: _grid((24, 26, 28), (48, 64, 96), (2.0,), (0.45,)) + _grid((28, 32), (64,), (1.5, 1.7), (0.45,)),
+    # FP64: the near field (set by c_s and m) dominates, so c_s is varied with p and c_t
+    sfmm.SFMM_FP64: _grid((24, 28, 32), (32, 64), (1.3, 1.5, 2.0), (0.45,)) + _grid((28, 32), (32, 64), (2.0,), (0.5,)),
 }
+
+
+_PLAN_PARAMS = inspect.signature(sfmm.Plan.__init__).parameters
+
+
+def plan_defaults():
+    """The MAC constants a Plan uses when a candidate does not set them (read
+    from Plan's own signature, so the tuner reports the settings actually run)."""
+    return {"c_s": _PLAN_PARAMS["c_s"].default, "c_t": _PLAN_PARAMS["c_t"].default}
+
+
+def plan_kwargs(candidate):
+    """A candidate's full Plan keyword arguments: its own, then the Plan defaults."""
+    kw = dict(plan_defaults())
+    kw.update(candidate)
+    return kw
 
 
 def _rel(a, b):
@@ -66,9 +86,7 @@ def _tune(src, q, tgt, precision, stated, cands, idx, r_psi, r_alpha, repeats, s
     import torch
     best = None
     for c in cands:
-        kw = dict(c)
-        kw.setdefault("c_s", 2.0)                 # the library's default MAC constants
-        kw.setdefault("c_t", 0.5)
+        kw = plan_kwargs(c)
         plan = sfmm.Plan(precision=precision, q_f32=q_f32, **kw)
         psi, alpha = plan.deflection(src, q, tgt)
         stream = torch.cuda.current_stream()

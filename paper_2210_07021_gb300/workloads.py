@@ -169,18 +169,25 @@ def loss_sky(n=1_000_000, n_clumps=2000, nside=256, config_index=5):
                          "loss sum w |alpha - s xi|^2")
 
 
+def shell_sizes(n_shells=64, n_min=10_000, n_max=10_000_000, config_index=4):
+    """Source counts N_k of the shells, log-uniform in [n_min, n_max]."""
+    rng = rng_for(config_index)
+    return np.exp(rng.uniform(np.log(n_min), np.log(n_max), n_shells)).astype(np.int64)
+
+
+def shell(k, n, config_index=4):
+    """Shell k of the shell set: n clustered sources (n/500 clumps), equal masses 4 pi / n."""
+    src = clustered(rng_for(config_index, 1 + k), int(n), max(1, int(n) // 500))
+    return src, np.full(int(n), 4.0 * np.pi / int(n))
+
+
 def shell_set(n_shells=64, n_min=10_000, n_max=10_000_000, nside=256, config_index=4):
     """Independent lensing shells (the multi-layer setting): shell k has N_k
     clustered sources, N_k log-uniform in [n_min, n_max], N_k/500 clumps,
     equal masses 4 pi / N_k (float64); every shell uses the same targets, the
     12 nside^2 HEALPix pixel centres."""
-    rng = rng_for(config_index)
-    sizes = np.exp(rng.uniform(np.log(n_min), np.log(n_max), n_shells)).astype(np.int64)
-    shells = []
-    for k, n in enumerate(sizes):
-        r = rng_for(config_index, 1 + k)
-        src = clustered(r, int(n), max(1, int(n) // 500))
-        shells.append((src, np.full(int(n), 4.0 * np.pi / int(n))))
+    sizes = shell_sizes(n_shells, n_min, n_max, config_index)
+    shells = [shell(k, n, config_index) for k, n in enumerate(sizes)]
     tgt = healpix_ring_centres(nside)
     return dict(shells=shells, tgt=tgt, sizes=sizes,
                 workload=f"{n_shells} shells, N_k log-uniform in [{n_min:g}, {n_max:g}] (sum {int(sizes.sum())}), "

@@ -31,9 +31,7 @@ def run(monkeypatch, results, precision, stated, fallback=None):
     def fake_tune(src, q, tgt, prec, st, cands, idx, r_psi, r_alpha, repeats, safety, q_f32, table):
         best = None
         for c in cands:
-            kw = dict(c)
-            kw.setdefault("c_s", 2.0)
-            kw.setdefault("c_t", 0.5)
+            kw = tune.plan_kwargs(c)
             ms, err = results[(prec, kw["p"])]
             calls.append((prec, kw["p"]))
             row = dict(kw, precision=prec, ms=ms, error=err, ok=err <= safety * st)
@@ -72,3 +70,24 @@ def test_nothing_reaches_the_target(monkeypatch):
     res = {(sfmm.SFMM_MIXED, 16): (3.0, 6e-7), (sfmm.SFMM_MIXED, 20): (2.5, 7e-7)}
     with pytest.raises(RuntimeError):
         run(monkeypatch, res, sfmm.SFMM_MIXED, 1e-6)
+
+
+def test_candidates_take_the_plan_defaults():
+    """A candidate that leaves out c_s or c_t runs (and is reported) with the
+    defaults of Plan itself, and its own settings win over them."""
+    import inspect
+    sig = inspect.signature(sfmm.Plan.__init__).parameters
+    kw = tune.plan_kwargs(dict(p=20, leaf_size=64))
+    assert kw == dict(p=20, leaf_size=64, c_s=sig["c_s"].default, c_t=sig["c_t"].default)
+    kw = tune.plan_kwargs(dict(p=16, leaf_size=32, c_s=1.3))
+    assert kw["c_s"] == 1.3 and kw["c_t"] == sig["c_t"].default
+
+
+def test_default_candidate_lists_are_valid():
+    """Every default candidate names a known number format's settings within the library's ranges."""
+    for prec, cands in tune.DEFAULT_CANDIDATES.items():
+        assert prec in (sfmm.SFMM_FP64, sfmm.SFMM_MIXED, sfmm.SFMM_MIXED_DF, sfmm.SFMM_FP32)
+        assert len({tuple(sorted(c.items())) for c in cands}) == len(cands)
+        for c in cands:
+            kw = tune.plan_kwargs(c)
+            assert 1 <= kw["p"] <= 32 and kw["leaf_size"] >= 1 and kw["c_s"] > 1 and 0 < kw["c_t"] < 1
