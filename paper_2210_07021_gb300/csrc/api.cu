@@ -43,7 +43,11 @@ cudaError_t launch_m2l_tc(int64_t n_pairs, const uint64_t* ptgt, const uint32_t*
                           uint32_t* tile_ctr, int* status, cudaStream_t s);
 cudaError_t launch_l2l(const TreeView& T, int a, int b, int p, const double* tables, const void* geo, void* local,
                        int ek, cudaStream_t s);
-cudaError_t launch_pair_geo_rho(const TreeView& T, const uint64_t* tt, const uint32_t* ss, int64_t n, void* out,
+size_t frame_df_bytes();
+cudaError_t launch_frame_df(int n_nodes, const double* geom, void* out, cudaStream_t s);
+cudaError_t launch_pair_geo_rho(const TreeView& T, const void* frames, const float4* log_tab, const uint64_t* tt,
+                                const uint32_t* ss, int64_t n, void* out, cudaStream_t s);
+cudaError_t launch_child_geo_df(const TreeView& T, const void* frames, const float4* log_tab, void* m2m, void* l2l,
                                 cudaStream_t s);
 cudaError_t launch_m2l_pair(int64_t n_pairs, const uint64_t* ptgt, const uint32_t* psrc, const void* geo,
                             const void* mpole, int p, double* acc, uint32_t* leftover, uint32_t* n_left,
@@ -52,6 +56,11 @@ cudaError_t launch_m2l_left_df(const TreeView& T, const uint64_t* ptgt, const ui
                                const uint32_t* n_list, int64_t max_list, int p, const double* tables,
                                const void* mpole, double* acc, cudaStream_t s);
 cudaError_t launch_acc_to_df(int64_t n, const double* acc, void* out, cudaStream_t s);
+cudaError_t launch_m2m_df(const TreeView& T, int c0, int c1, int p, const void* geo, void* mpole, cudaStream_t s);
+cudaError_t launch_l2l_df(const TreeView& T, int a, int b, int p, const void* geo, const double* acc, void* local,
+                          cudaStream_t s);
+cudaError_t launch_p2m_df_leaf(const TreeView& T, const int* leaves, int64_t n_leaves, const float4* off,
+                               const float4* log_tab, int p, void* mpole, cudaStream_t s);
 cudaError_t launch_unscale(int n_nodes, const double* geom, const void* in, double* out, int p, int is_local,
                            int ek, cudaStream_t s);
 cudaError_t launch_eval32_prep(const TreeView& T, const int* leaves, int64_t n_leaves, const double4_32a* tgt,
@@ -364,8 +373,15 @@ sfmm_status solve(sfmm_plan_s* P, const double* src, const void* q, int64_t N, c
         if ((e = launch_geom32((int)nn, P->n_geom.as<double>(), P->geom32.as<float>(), s)))
             return cuda_fail(P, e, "geometry32");
     }
-    if ((e = launch_child_geo(T, P->geom32.as<float>(), P->m2m_geo.p, P->l2l_geo.p, ek, s)))
+    if (dfe) {
+        // double-float frames per node, then the M2M / L2L parameters in double-float
+        if ((e = ensure(P->framedf, (size_t)nn * frame_df_bytes()))) return cuda_fail(P, e, "alloc");
+        if ((e = launch_frame_df((int)nn, P->n_geom.as<double>(), P->framedf.p, s)) ||
+            (e = launch_child_geo_df(T, P->framedf.p, P->logtab.as<float4>(), P->m2m_geo.p, P->l2l_geo.p, s)))
+            return cuda_fail(P, e, "child geometry");
+    } else if ((e = launch_child_geo(T, P->geom32.as<float>(), P->m2m_geo.p, P->l2l_geo.p, ek, s))) {
         return cuda_fail(P, e, "child geometry");
+    }
     if ((e = cudaEventRecord(P->ev_fork, s)) || (e = cudaStreamWaitEvent(P->aux, P->ev_fork, 0)))
         return cuda_fail(P, e, "fork lists");
     if (offsets) {
@@ -376,14 +392,18 @@ sfmm_status solve(sfmm_plan_s* P, const double* src, const void* q, int64_t N, c
     }
     if (adj) e = launch_p2m_adj(T, P->leaves_src.as<int>(), P->n_leaves, P->src4.as<double4_32a>(),
                                 P->dip4.as<double4_32a>(), P->mpole.as<double>(), p, s);
+    else if (dfe) e = launch_p2m_df_leaf(T, P->leaves_src.as<int>(), P->n_leaves, P->soff.as<float4>(),
+                                         P->logtab.as<float4>(), p, P->mpole.p, s);
     else e = launch_p2m(T, P->leaves_src.as<int>(), P->n_leaves, P->src4.as<double4_32a>(), P->soff.as<float4>(),
                         P->logtab.as<float4>(), P->mpole.p, p, ek, s);
     if (e) return cuda_fail(P, e, "P2M");
     const int depth = (int)P->level_start.size() - 2;
-    for (int l = depth - 1; l >= 0; --l)
-        if ((e = launch_m2m(T, P->level_start[l], P->level_start[l + 1], p, P->tables.as<double>(), P->m2m_geo.p,
-                            P->mpole.p, ek, s)))
-            return cuda_fail(P, e, "M2M");
+    for (int l = depth - 1; l >= 0; --l) {
+        if (dfe) e = launch_m2m_df(T, P->level_start[l + 1], P->level_start[l + 2], p, P->m2m_geo.p, P->mpole.p, s);
+        else e = launch_m2m(T, P->level_start[l], P->level_start[l + 1], p, P->tables.as<double>(), P->m2m_geo.p,
+                            P->mpole.p, ek, s);
+        if (e) return cuda_fail(P, e, "M2M");
+    }
     tm.mark();
     // ---- lists on the auxiliary stream (its host synchronisation waits for the
     // walk only), joined back before M2L; the "lists" phase is the part of the walk
@@ -409,7 +429,7 @@ sfmm_status solve(sfmm_plan_s* P, const double* src, const void* q, int64_t N, c
             return cuda_fail(P, e, "alloc");
         if ((e = cudaMemsetAsync(P->m2l_acc.p, 0, nacc * 8, s)) || (e = cudaMemsetAsync(n_left, 0, 4, s)))
             return cuda_fail(P, e, "memset");
-        if ((e = launch_pair_geo_rho(T, m2l_t, m2l_s, P->n_m2l, P->m2l_geo.p, s)))
+        if ((e = launch_pair_geo_rho(T, P->framedf.p, P->logtab.as<float4>(), m2l_t, m2l_s, P->n_m2l, P->m2l_geo.p, s)))
             return cuda_fail(P, e, "pair geometry");
         if ((e = launch_m2l_pair(P->n_m2l, m2l_t, m2l_s, P->m2l_geo.p, P->mpole.p, p, P->m2l_acc.as<double>(),
                                  P->leftover.as<uint32_t>(), n_left, s)))
@@ -417,8 +437,6 @@ sfmm_status solve(sfmm_plan_s* P, const double* src, const void* q, int64_t N, c
         if ((e = launch_m2l_left_df(T, m2l_t, m2l_s, P->leftover.as<uint32_t>(), n_left, P->n_m2l, p,
                                     P->tables.as<double>(), P->mpole.p, P->m2l_acc.as<double>(), s)))
             return cuda_fail(P, e, "M2L (pairs near antipodes)");
-        if ((e = launch_acc_to_df((int64_t)nacc, P->m2l_acc.as<double>(), P->local.p, s)))
-            return cuda_fail(P, e, "M2L sums");
     } else if ((e = cudaMemsetAsync(P->local.p, 0, (size_t)nn * EXP_STRIDE * esz, s)) ||
                (e = launch_pair_geo(T, P->geom32.as<float>(), m2l_t, m2l_s, P->n_m2l, P->m2l_geo.p, ek, s))) {
         return cuda_fail(P, e, "pair geometry");
@@ -439,11 +457,18 @@ sfmm_status solve(sfmm_plan_s* P, const double* src, const void* q, int64_t N, c
         return cuda_fail(P, e, "M2L");
     }
     tm.mark();
-    // ---- L2L
-    for (int l = 1; l <= depth; ++l)
-        if ((e = launch_l2l(T, P->level_start[l], P->level_start[l + 1], p, P->tables.as<double>(), P->l2l_geo.p,
-                            P->local.p, ek, s)))
-            return cuda_fail(P, e, "L2L");
+    // ---- L2L (double-float: each node's local is its M2L sum plus its parent's local translated)
+    if (dfe) {
+        for (int l = 0; l <= depth; ++l)
+            if ((e = launch_l2l_df(T, P->level_start[l], P->level_start[l + 1], p, P->l2l_geo.p,
+                                   P->m2l_acc.as<double>(), P->local.p, s)))
+                return cuda_fail(P, e, "L2L");
+    } else {
+        for (int l = 1; l <= depth; ++l)
+            if ((e = launch_l2l(T, P->level_start[l], P->level_start[l + 1], p, P->tables.as<double>(), P->l2l_geo.p,
+                                P->local.p, ek, s)))
+                return cuda_fail(P, e, "L2L");
+    }
     tm.mark();
     // ---- evaluation
     const uint32_t* p2p_s = P->p2p_alt ? P->p2p_s2.as<uint32_t>() : P->p2p_s.as<uint32_t>();
@@ -801,7 +826,8 @@ void sfmm_destroy(sfmm_plan_t plan)
                   &plan->p2p_t2, &plan->p2p_s2, &plan->m2l_off, &plan->p2p_off, &plan->leaves_src,
                   &plan->leaves_tgt, &plan->m2l_geo, &plan->m2m_geo, &plan->l2l_geo, &plan->soff,
                   &plan->toff, &plan->dc, &plan->leftover, &plan->geom32, &plan->macn, &plan->logtab,
-                  &plan->ttmp, &plan->dip4, &plan->adj_h, &plan->adj_g, &plan->macn32, &plan->m2l_acc};
+                  &plan->ttmp, &plan->dip4, &plan->adj_h, &plan->adj_g, &plan->macn32, &plan->m2l_acc,
+                  &plan->framedf};
     if (plan->aux) cudaStreamSynchronize(plan->aux);
     for (sfmm_plan_s* L : plan->lanes) sfmm_destroy(L);
     plan->lanes.clear();

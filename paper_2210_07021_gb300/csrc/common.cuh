@@ -119,6 +119,7 @@ struct sfmm_plan_s {
     sfmm::Buf toff, dc;                    // FP32 (hi, lo) target offsets and near-leaf centre offsets
     sfmm::Buf leftover;                    // M2L pairs left to the warp kernel (centres near antipodes)
     sfmm::Buf m2l_acc;                     // FP64 M2L sums per box (double-float paths)
+    sfmm::Buf framedf;                     // double-float frame vectors and scale per node (double-float paths)
     sfmm::Buf dip4, adj_h, adj_g;          // adjoint: key-sorted dipoles; charges and dipoles in caller order
     sfmm::Buf logtab;                      // double-float evaluation: log(1 + j/128), 128/(128 + j), log 2
     sfmm::Buf geom32;                      // FP32 frame vectors and scale per node (mixed path)

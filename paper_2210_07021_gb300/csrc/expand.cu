@@ -217,31 +217,174 @@ __global__ void k_pair_geo(TreeView T, const uint64_t* __restrict__ tt, const ui
     }
 }
 
-// M2L parameters of the thread-per-pair double-float kernel (m2l_pair.cu):
-// a ph1, b ph2, rho = g/(a b) = 1/cos^2(theta/2), log sin(theta/2), in FP64 and
-// rounded once to double-float.
-__global__ void k_pair_geo_rho(TreeView T, const uint64_t* __restrict__ tt, const uint32_t* __restrict__ ss,
-                               int64_t n, XGeoRho* __restrict__ out)
+// ------------------------------------------- double-float translation geometry
+// The double-float paths form the translation parameters without FP64
+// arithmetic (this GPU's FP64 pipe runs at 1/64 of the FP32 rate): the centre
+// difference D = T - S and sum E = T + S are exact to 2^-47 from the FP64
+// centres by integer arithmetic (dfl_sub_exact), the frames and scales are
+// double-float copies made once per node (k_frame_df), and sqrt, quotients and
+// log sin(theta/2) are double-float (the table logarithm of the evaluation).
+// The azimuths come from the shorter of D and E as in pair_geometry.
+struct __align__(16) FrameDF {
+    dflt et[3], ep[3], r, pad;
+};
+
+__global__ void k_frame_df(int n_nodes, const double* __restrict__ geom, FrameDF* __restrict__ out)
 {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_nodes; i += (int64_t)gridDim.x * blockDim.x) {
+        const double* g = geom + (size_t)i * GEOM_STRIDE;
+        FrameDF F;
+        for (int k = 0; k < 3; ++k) {
+            F.et[k] = dflt(g[3 + k]);
+            F.ep[k] = dflt(g[6 + k]);
+        }
+        F.r = dflt(g[10]);
+        F.pad = dflt(0.f, 0.f);
+        out[i] = F;
+    }
+}
+
+// sqrt of a double-float x >= 0: the FP32 root and one correction from the exact remainder
+__device__ __forceinline__ dflt dfl_sqrt(dflt x)
+{
+    if (!(x.h > 0.f)) return dflt(0.f, 0.f);
+    const float s = sqrtf(x.h);
+    const float r = __fadd_rn(__fmaf_rn(-s, s, x.h), x.l);
+    return dfl_fast_two_sum(s, __fdiv_rn(r, __fmul_rn(2.f, s)));
+}
+
+// 1/k as double-float pairs, k = 1..12 (rounded from FP64 at compile time)
+struct InvTabDF {
+    float h[13], l[13];
+};
+constexpr InvTabDF make_inv_tab()
+{
+    InvTabDF t{};
+    for (int k = 1; k <= 12; ++k) {
+        const double v = 1.0 / k;
+        t.h[k] = (float)v;
+        t.l[k] = (float)(v - (double)(float)v);
+    }
+    return t;
+}
+__constant__ InvTabDF kInvDF = make_inv_tab();
+
+// log(1 - x) for a double-float 0 <= x < 1, to double-float accuracy relative
+// to the result: below x = 2^-5 the series -x (1 + x/2 + ... + x^11/12)
+// (remainder under x^13/13 < 2^-64 x), else the table logarithm of 1 - x
+// (whose absolute error 2^-48 is then below 2^-43 of the result).
+__device__ __forceinline__ dflt dfl_log1m(dflt x, const float4* tab)
+{
+    if (x.h < 0.03125f) {
+        dflt acc(kInvDF.h[12], kInvDF.l[12]);
+        for (int k = 11; k >= 1; --k) acc = dflt(kInvDF.h[k], kInvDF.l[k]) + x * acc;
+        return -(x * acc);
+    }
+    return dfl_norm(dfl_log_lazy(dflt(1.f, 0.f) - x, tab));
+}
+
+struct PairGeoDF {
+    dflt sh, ch;             // sin, cos of half the angle between the centres
+    dflt eTx, eTy, eSx, eSy; // e^{i phi_T^(S)}, e^{i phi_S^(T)}
+};
+
+__device__ __forceinline__ PairGeoDF pair_geometry_df(const double* gS, const double* gT, const FrameDF& FS,
+                                                      const FrameDF& FT)
+{
+    const dflt dx = dfl_sub_exact(gT[0], gS[0]), dy = dfl_sub_exact(gT[1], gS[1]), dz = dfl_sub_exact(gT[2], gS[2]);
+    const dflt ex = dfl_sub_exact(gT[0], -gS[0]), ey = dfl_sub_exact(gT[1], -gS[1]), ez = dfl_sub_exact(gT[2], -gS[2]);
+    const dflt d2 = dx * dx + dy * dy + dz * dz;
+    const dflt s2 = ex * ex + ey * ey + ez * ez;
+    PairGeoDF P;
+    P.sh = dfl_sqrt(d2) * 0.5f;
+    P.ch = dfl_sqrt(s2) * 0.5f;
+    const bool anti = s2.h < d2.h;
+    const dflt vx = anti ? ex : dx, vy = anti ? ey : dy, vz = anti ? ez : dz;
+    const float sg = anti ? 1.f : -1.f;
+    const dflt one(1.f, 0.f), zero(0.f, 0.f);
+    dflt ux = vx * FS.et[0] + vy * FS.et[1] + vz * FS.et[2];
+    dflt uy = vx * FS.ep[0] + vy * FS.ep[1] + vz * FS.ep[2];
+    dflt n = dfl_sqrt(ux * ux + uy * uy);
+    if (n.h > 0.f) { P.eTx = ux / n; P.eTy = uy / n; } else { P.eTx = one; P.eTy = zero; }
+    ux = (vx * FT.et[0] + vy * FT.et[1] + vz * FT.et[2]) * sg;
+    uy = (vx * FT.ep[0] + vy * FT.ep[1] + vz * FT.ep[2]) * sg;
+    n = dfl_sqrt(ux * ux + uy * uy);
+    if (n.h > 0.f) { P.eSx = ux / n; P.eSy = uy / n; } else { P.eSx = one; P.eSy = zero; }
+    return P;
+}
+
+// M2L parameters of the thread-per-pair double-float kernel (m2l_pair.cu):
+// a ph1, b ph2, rho = g/(a b) = 1/cos^2(theta/2), log sin(theta/2).
+__global__ void k_pair_geo_rho(TreeView T, const FrameDF* __restrict__ fr, const float4* __restrict__ log_tab,
+                               const uint64_t* __restrict__ tt, const uint32_t* __restrict__ ss, int64_t n,
+                               XGeoRho* __restrict__ out)
+{
+    __shared__ float4 s_tab[129];
+    for (int i = threadIdx.x; i < 129; i += blockDim.x) s_tab[i] = log_tab[i];
+    __syncthreads();
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
-        const double* gS = T.geom + (size_t)ss[k] * GEOM_STRIDE;
-        const double* gT = T.geom + (size_t)tt[k] * GEOM_STRIDE;
-        double sh, ch;
-        cd eT, eS;
-        pair_geometry(gS, gT, &sh, &ch, &eT, &eS);
-        const double c = ch / sh;
-        const double a = c * gS[10], b = c * gT[10];
-        const double rho = ch > 0.0 ? 1.0 / (ch * ch) : 0.0;
+        const uint32_t si = ss[k], ti = (uint32_t)tt[k];
+        const FrameDF FS = fr[si], FT = fr[ti];
+        const PairGeoDF G = pair_geometry_df(T.geom + (size_t)si * GEOM_STRIDE, T.geom + (size_t)ti * GEOM_STRIDE,
+                                             FS, FT);
         XGeoRho R;
-        R.ar = dflt(a * eT.x);             // a e^{-i phi_T^(S)}
-        R.ai = dflt(-a * eT.y);
-        R.br = dflt(b * eS.x);             // b e^{-i phi_S^(T)}
-        R.bi = dflt(-b * eS.y);
-        R.rho = dflt(rho);
-        R.logk = dflt(log(sh));
-        R.big = (!(ch > 0.0) || rho > 8.7) ? 1 : 0;
+        const dflt zero(0.f, 0.f);
+        R.big = !(G.ch.h > 0.f) || G.ch.h * G.ch.h < 1.f / 8.7f;     // rho = 1/cos^2 > 8.7: near antipodes
+        if (R.big) {
+            R.ar = R.ai = R.br = R.bi = R.rho = R.logk = zero;
+        } else {
+            const dflt c = G.ch / G.sh;
+            const dflt a = c * FS.r, b = c * FT.r;
+            R.ar = a * G.eTx;                      // a e^{-i phi_T^(S)}
+            R.ai = -(a * G.eTy);
+            R.br = b * G.eSx;                      // b e^{-i phi_S^(T)}
+            R.bi = -(b * G.eSy);
+            R.rho = dflt(1.f, 0.f) / (G.ch * G.ch);
+            R.logk = dfl_norm(dfl_log_lazy(G.sh, s_tab));
+        }
         R.pad[0] = R.pad[1] = R.pad[2] = 0;
         out[k] = R;
+    }
+}
+
+// M2M and L2L parameters per node with a parent (the double-float paths)
+__global__ void k_child_geo_df(TreeView T, const FrameDF* __restrict__ fr, const float4* __restrict__ log_tab,
+                               XGeoDF* __restrict__ m2m, XGeoDF* __restrict__ l2l)
+{
+    __shared__ float4 s_tab[129];
+    for (int i = threadIdx.x; i < 129; i += blockDim.x) s_tab[i] = log_tab[i];
+    __syncthreads();
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < T.n_nodes; i += (int64_t)gridDim.x * blockDim.x) {
+        const int par = T.parent[i];
+        if (par < 0) continue;
+        const double* gC = T.geom + (size_t)i * GEOM_STRIDE;
+        const double* gP = T.geom + (size_t)par * GEOM_STRIDE;
+        const FrameDF FC = fr[i], FP = fr[par];
+        const dflt one(1.f, 0.f);
+        {   // M2M: child (S) -> parent (T)
+            const PairGeoDF G = pair_geometry_df(gC, gP, FC, FP);
+            const dflt t = G.sh / G.ch;
+            XGeoDF X;
+            X.a = t * FC.r;
+            X.b = t / FP.r;
+            X.g = (one + t * t) * FC.r / FP.r;
+            X.logk = dfl_log1m(G.sh * G.sh, s_tab) * 0.5f;     // log cos(theta/2)
+            X.p1x = -G.eTx; X.p1y = G.eTy;         // -e^{-i phi_T}
+            X.p2x = G.eSx; X.p2y = G.eSy;          //  e^{ i phi_S}
+            m2m[i] = X;
+        }
+        {   // L2L: parent (S) -> child (T)
+            const PairGeoDF G = pair_geometry_df(gP, gC, FP, FC);
+            const dflt t = G.sh / G.ch;
+            XGeoDF X;
+            X.a = t / FP.r;
+            X.b = t * FC.r;
+            X.g = (one + t * t) * FC.r / FP.r;
+            X.logk = dfl_log1m(G.sh * G.sh, s_tab) * 0.5f;     // log cos(theta/2)
+            X.p1x = G.eTx; X.p1y = G.eTy;          //  e^{ i phi_T}
+            X.p2x = -G.eSx; X.p2y = G.eSy;         // -e^{-i phi_S}
+            l2l[i] = X;
+        }
     }
 }
 
@@ -1077,11 +1220,31 @@ cudaError_t launch_m2l_list(const uint64_t* ptgt, const uint32_t* psrc, const ui
     return cudaGetLastError();
 }
 
-cudaError_t launch_pair_geo_rho(const TreeView& T, const uint64_t* tt, const uint32_t* ss, int64_t n, void* out,
-                                cudaStream_t s)
+size_t frame_df_bytes() { return sizeof(FrameDF); }
+
+cudaError_t launch_frame_df(int n_nodes, const double* geom, void* out, cudaStream_t s)
+{
+    if (n_nodes == 0) return cudaSuccess;
+    k_frame_df<<<grid_for(n_nodes, 256), 256, 0, s>>>(n_nodes, geom, static_cast<FrameDF*>(out));
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pair_geo_rho(const TreeView& T, const void* frames, const float4* log_tab, const uint64_t* tt,
+                                const uint32_t* ss, int64_t n, void* out, cudaStream_t s)
 {
     if (n == 0) return cudaSuccess;
-    k_pair_geo_rho<<<grid_for(n, 256), 256, 0, s>>>(T, tt, ss, n, static_cast<XGeoRho*>(out));
+    k_pair_geo_rho<<<grid_for(n, 256), 256, 0, s>>>(T, static_cast<const FrameDF*>(frames), log_tab, tt, ss, n,
+                                                     static_cast<XGeoRho*>(out));
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_child_geo_df(const TreeView& T, const void* frames, const float4* log_tab, void* m2m, void* l2l,
+                                cudaStream_t s)
+{
+    k_child_geo_df<<<grid_for(T.n_nodes, 256), 256, 0, s>>>(T, static_cast<const FrameDF*>(frames), log_tab,
+                                                             static_cast<XGeoDF*>(m2m), static_cast<XGeoDF*>(l2l));
     count_launch();
     return cudaGetLastError();
 }
