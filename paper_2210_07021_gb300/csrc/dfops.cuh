@@ -117,4 +117,129 @@ __device__ __forceinline__ void pascal_down_mul(dflt* c, dflt b)
     }
 }
 
+// ------------------------------------------------------------------------
+// Packed pairs: the real and imaginary parts of a coefficient as one
+// double-float pair of float2, so that each FP32x2 instruction does the work
+// of two (the binomial passes treat both parts alike).  x - y is taken as
+// fma(y, -1, x), exact in its product, so the error-free transformations keep
+// their exactness.
+struct dflt2 {
+    float2 h, l;
+};
+
+__device__ __forceinline__ float2 f2s(float v) { return make_float2(v, v); }
+__device__ __forceinline__ float2 sub2(float2 x, float2 y) { return __ffma2_rn(y, f2s(-1.f), x); }
+
+__device__ __forceinline__ dflt2 two_sum2(float2 a, float2 b)
+{
+    const float2 s = __fadd2_rn(a, b);
+    const float2 bb = sub2(s, a);
+    const float2 e = __fadd2_rn(sub2(a, sub2(s, bb)), sub2(b, bb));
+    return dflt2{s, e};
+}
+__device__ __forceinline__ dflt2 fast_two_sum2(float2 a, float2 b)     // |a| >= |b| per part
+{
+    const float2 s = __fadd2_rn(a, b);
+    return dflt2{s, sub2(b, sub2(s, a))};
+}
+__device__ __forceinline__ dflt2 renorm2(dflt2 a) { return two_sum2(a.h, a.l); }
+
+// a + b, low parts unnormalised (as add_lazy)
+__device__ __forceinline__ dflt2 add_lazy2(dflt2 a, dflt2 b)
+{
+    const dflt2 s = two_sum2(a.h, b.h);
+    return dflt2{s.h, __fadd2_rn(__fadd2_rn(a.l, b.l), s.l)};
+}
+
+// the error-free product of the leading parts plus the cross terms, for a
+// double-float scalar m times both parts of a
+__device__ __forceinline__ void mul2_parts(dflt2 a, dflt m, float2* p, float2* e)
+{
+    const float2 mh = f2s(m.h);
+    *p = __fmul2_rn(a.h, mh);
+    const float2 pn = __fmul2_rn(a.h, f2s(-m.h));                        // -p, exactly
+    *e = __ffma2_rn(a.h, f2s(m.l), __ffma2_rn(a.l, mh, __ffma2_rn(a.h, mh, pn)));
+}
+// m a, normalised
+__device__ __forceinline__ dflt2 mul2_df(dflt2 a, dflt m)
+{
+    float2 p, e;
+    mul2_parts(a, m, &p, &e);
+    return fast_two_sum2(p, e);
+}
+// acc + m b, low part unnormalised (as mac_lazy)
+__device__ __forceinline__ dflt2 mac_lazy2(dflt2 acc, dflt m, dflt2 b)
+{
+    float2 p, e;
+    mul2_parts(b, m, &p, &e);
+    const dflt2 s = two_sum2(acc.h, p);
+    return dflt2{s.h, __fadd2_rn(acc.l, __fadd2_rn(s.l, e))};
+}
+
+// the four passes of dfops.cuh on packed pairs (same grouping)
+template <int P>
+__device__ __forceinline__ void pascal_up2(dflt2* c)
+{
+#pragma unroll
+    for (int g = 0; g < P; g += 4) {
+#pragma unroll 1
+        for (int i = g; i < g + 4; ++i) {
+#pragma unroll
+            for (int j = P - 1; j >= g; --j)
+                if (j >= i) c[j] = add_lazy2(c[j], c[j + 1]);
+        }
+    }
+}
+template <int P>
+__device__ __forceinline__ void pascal_down2(dflt2* c)
+{
+#pragma unroll
+    for (int g = 1; g < P; g += 4) {
+#pragma unroll 1
+        for (int i = g; i < g + 4 && i < P; ++i) {
+#pragma unroll
+            for (int j = P - 1; j >= g; --j)
+                if (j >= i) c[j + 1] = add_lazy2(c[j + 1], c[j]);
+        }
+    }
+}
+template <int P>
+__device__ __forceinline__ void pascal_up_mul2(dflt2* c, dflt a)
+{
+#pragma unroll
+    for (int g = 0; g < P; g += 4) {
+#pragma unroll 1
+        for (int i = g; i < g + 4; ++i) {
+#pragma unroll
+            for (int j = P - 1; j >= g; --j)
+                if (j >= i) c[j] = mac_lazy2(c[j], a, c[j + 1]);
+        }
+    }
+}
+template <int P>
+__device__ __forceinline__ void pascal_down_mul2(dflt2* c, dflt b)
+{
+#pragma unroll
+    for (int g = 1; g < P; g += 4) {
+#pragma unroll 1
+        for (int i = g; i < g + 4 && i < P; ++i) {
+#pragma unroll
+            for (int j = P - 1; j >= g; --j)
+                if (j >= i) c[j + 1] = mac_lazy2(c[j + 1], b, c[j]);
+        }
+    }
+}
+
+// coefficient l of a row (Re at 2l, Im at 2l + 1) as a packed pair, and back
+__device__ __forceinline__ dflt2 ld_pair(const dflt* row, int l)
+{
+    const dflt re = row[2 * l], im = row[2 * l + 1];
+    return dflt2{make_float2(re.h, im.h), make_float2(re.l, im.l)};
+}
+__device__ __forceinline__ void st_pair(dflt* row, int l, dflt2 v)
+{
+    row[2 * l] = dflt(v.h.x, v.l.x);
+    row[2 * l + 1] = dflt(v.h.y, v.l.y);
+}
+
 }  // namespace sfmm

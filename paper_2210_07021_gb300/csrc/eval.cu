@@ -817,9 +817,33 @@ __global__ void __launch_bounds__(128, 7) k_eval32(Eval32Args A)
                     acc_a[c] = group_sumf(acc_a[c], lpa);
                     acc_b[c] = group_sumf(acc_b[c], lpb);
                 }
-                if (sa == 0) finish_target_dfar<PSI>(A, GD, Ld, ta, tha, tla, nfa, acc_a[3], acc_a[4], shift);
-                if (act_b && sb == 0)
-                    finish_target_dfar<PSI>(A, GD, Ld, tbx, thb, tlb, nfb, acc_b[3], acc_b[4], shift);
+                // The double-float finish is long next to its inputs: lane t takes target t of the
+                // pass (group a's, then group b's) with its group sums shuffled from the lane that
+                // holds them (lane j * lpa for group a's target j), so that one round finishes all
+                // targets of the pass when they fit in the warp, else one round per group.
+                const int nbv = nb ? min(nb, tc - tb - na) : 0;
+                const int nrounds = na + nbv <= 32 ? 1 : 2;
+                for (int rd = 0; rd < nrounds; ++rd) {
+                    int t = lane, grp = rd;
+                    if (nrounds == 1 && lane >= na) { grp = 1; t = lane - na; }
+                    const bool act = grp == 0 ? t < na : t < nbv;
+                    const int src = act ? (grp == 0 ? t * lpa : t * lpb) : 0;
+                    dflt nf[3];
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        const float ah = __shfl_sync(FULL, nfa[c].h, src), al = __shfl_sync(FULL, nfa[c].l, src);
+                        const float bh = __shfl_sync(FULL, nfb[c].h, src), bl = __shfl_sync(FULL, nfb[c].l, src);
+                        nf[c] = grp == 0 ? dflt(ah, al) : dflt(bh, bl);
+                    }
+                    const float qa = __shfl_sync(FULL, acc_a[3], src), qb = __shfl_sync(FULL, acc_b[3], src);
+                    const float la = __shfl_sync(FULL, acc_a[4], src), lb = __shfl_sync(FULL, acc_b[4], src);
+                    if (act) {
+                        const size_t tix = (size_t)tf + tb + (grp == 0 ? t : na + t);
+                        const float4 th = A.toff[2 * tix], tl = A.toff[2 * tix + 1];
+                        finish_target_dfar<PSI>(A, GD, Ld, tix, th, tl, nf, grp == 0 ? qa : qb, grp == 0 ? la : lb,
+                                                shift);
+                    }
+                }
             } else {
 #pragma unroll
                 for (int c = 0; c < 5; ++c) {

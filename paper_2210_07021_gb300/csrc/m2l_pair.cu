@@ -39,8 +39,10 @@ constexpr int PW = 4;            // warps per CTA
 // memory) holds the pair's scaled vector between the steps and then its
 // output.  The two binomial passes are unrolled once and run for the real and
 // then the imaginary part (a runtime loop), with the part in registers; the
-// O(p) diagonal steps are runtime loops: this keeps the code within the
-// instruction cache and the registers below 80.
+// O(p) diagonal steps are runtime loops.  This keeps the code within the
+// instruction cache and the registers at five CTAs per SM for p <= 20 (the
+// packed FP32x2 form of updown_df.cu measured slower here: it needs twice the
+// registers and the FMA pipe, not the issue rate, bounds this kernel).
 template <int P>
 __global__ void __launch_bounds__(128, (P <= 20 ? 5 : P <= 24 ? 4 : 3)) k_m2l_pair(int64_t n_pairs, const uint64_t* __restrict__ ptgt,
                                                   const uint32_t* __restrict__ psrc,
@@ -93,6 +95,7 @@ __global__ void __launch_bounds__(128, (P <= 20 ? 5 : P <= 24 ? 4 : 3)) k_m2l_pa
                     row[2 * l + 1] = ui;
                 }
             }
+            // both binomial stages, for the real and then the imaginary part (one unrolled copy)
             dflt t0(0.f, 0.f);
 #pragma unroll 1
             for (int part = 0; part < 2; ++part) {

@@ -11,7 +11,7 @@
 // would underflow here: a = tan(theta/2) r_child is tiny at deep levels.)
 // Each thread keeps its translation's vector in a row of shared memory between
 // the O(p) diagonal steps (runtime loops) and the two unrolled passes, which
-// run once for the real and once for the imaginary part.
+// run on (Re, Im) packed pairs (FP32x2 instructions).
 //
 // M2M: one thread per child of a level; the four children of a parent are
 // consecutive (and aligned to four from the level's first node), so four
@@ -51,24 +51,23 @@ __device__ __forceinline__ void translate_row(dflt* row, int p, const XGeoDF& G,
             cmul_df(zr, zi, row[2 * l], row[2 * l + 1], &row[2 * l], &row[2 * l + 1]);
         }
     }
-    dflt v0(0.f, 0.f);
-#pragma unroll 1
-    for (int part = 0; part < 2; ++part) {
-        dflt c[P + 1];
-        c[0] = dflt(0.f, 0.f);
+    dflt v0;
+    {   // both binomial stages on (Re, Im) packed pairs
+        dflt2 c[P + 1];
+        c[0] = dflt2{f2s(0.f), f2s(0.f)};
 #pragma unroll
-        for (int l = 1; l <= P; ++l) c[l] = row[2 * l + part];
-        pascal_up_mul<P>(c, G.a);            // v = shifted by a
-        if (part == 0) v0 = renorm(c[0]);
+        for (int l = 1; l <= P; ++l) c[l] = ld_pair(row, l);
+        pascal_up_mul2<P>(c, G.a);           // v = shifted by a
+        v0 = renorm(dflt(c[0].h.x, c[0].l.x));
         dflt gp = G.g;                        // w_n = g^n v_n, at index n
 #pragma unroll
         for (int n = 1; n <= P; ++n) {
-            c[n] = renorm(c[n]) * gp;
+            c[n] = mul2_df(renorm2(c[n]), gp);
             if (n < P) gp = gp * G.g;
         }
-        pascal_down_mul<P>(c, G.b);          // o_l = sum C(l-1, n-1) b^(l-n) w_n
+        pascal_down_mul2<P>(c, G.b);         // o_l = sum C(l-1, n-1) b^(l-n) w_n
 #pragma unroll
-        for (int l = 1; l <= P; ++l) row[2 * l + part] = renorm(c[l]);
+        for (int l = 1; l <= P; ++l) st_pair(row, l, renorm2(c[l]));
     }
     {   // Y_l = ph2^l (-Q b^l / l + o_l)
         dflt zr = G.p2x, zi = G.p2y, bp = G.b;
