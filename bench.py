@@ -33,25 +33,30 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "sFMM Mpts/s (N=M=1.6e7) FP64 vs mixed precision, at stated relative error"
-FP64_PEAK_DERIVED = 152 * 2 * 2 * 2.07e9   # SMs x FP64 FMA/clk/SM x 2 flop x max SM clock
-FP32_PEAK_DERIVED = 152 * 128 * 2 * 2.07e9  # SMs x FP32 FMA/clk/SM x 2 flop x max SM clock
-# (path name, precision enum value, order p, stated relative error, leaf size m, c_s, c_t):
-# per path the fastest setting measured on the clustered 1.6e7 workload that keeps
-# the error vs the oracle well inside the stated error
-MODES = [("mixed", 1, 20, 1e-6, 64, 1.5, 0.5), ("mixed_df", 2, 28, 1e-10, 64, 2.0, 0.45),
-         ("fp64", 0, 32, 1e-10, 64, 2.0, 0.45), ("fp32", 3, 20, 3e-5, 64, 1.3, 0.5)]
-# algorithmic FP64 flops per near-field pair: d^2 (3 sub, 3 mul, 2 add), 1/d^2
-# (counted as 4), q/d^2 (1), alpha sums (3 mul + 3 add), sum q (1); psi adds the
-# log (counted as 4) and its multiply-add (2)
-# DRAM bytes of one k_eval32 launch (near field + L2P, all-FP32 path) at the
-# benchmark workload (N = M = 1.6e7, p = 20, m = 64, c_s = 1.3, c_t = 0.5),
-# measured by ncu (dram__bytes_read.sum 5.33 GB + dram__bytes_write.sum 1.01 GB):
-# about 3.6x the bytes the kernel must move (sources re-staged by neighbouring
-# target leaves; 16- and 8-byte output writes at scattered positions)
-K_EVAL32_TRAFFIC = 5.33e9 + 1.01e9
-FLOPS_PER_PAIR_DEFL = 20
-FLOPS_PER_PAIR_PSI = 26
+# (path name, precision enum value, order p, stated relative error, leaf size m, c_s, c_t).
+# mixed (1e-6): the setting that holds 1e-6 on every sky of the tests (uniform sky at its own
+#   points, clustered sky on the N_side 512 grid, largest shell on N_side 256), not only on this one
+#   (p = 16 suffices here: 2.8e-7);
+# mixed_df and fp64 (1e-10): the fastest settings within half the stated error on this workload
+#   (tune.autotune over the default candidate grids: errors 2.2e-11 and 3.0e-11);
+# fp32 (3e-5): the all-FP32 path with tensor-core M2L.
+MODES = [("mixed", 1, 20, 1e-6, 64, 1.5, 0.5), ("mixed_df", 2, 32, 1e-10, 64, 1.5, 0.45),
+         ("fp64", 0, 32, 1e-10, 32, 1.5, 0.45), ("fp32", 3, 20, 3e-5, 64, 1.3, 0.5)]
+# the FP64 reference every path is compared with on all M targets: error ~3e-13 on this workload
+REF_SETTINGS = dict(p=32, leaf_size=32, c_s=2.0, c_t=0.45)
+# operations per near-field pair of the unit of the roofline: d^2 (3 sub, 3 mul, 2 add), the
+# alpha accumulation (q/d^2 times 3 components, 3 adds) and sum q: 12 flop, plus one reciprocal
+# and one logarithm (psi): 14 operations
+OPS_PER_PAIR = 14
+MUFU_PER_PAIR = 2           # rcp and lg2 (the FP32 pair loop's special-function operations)
 DTYPES = {"mixed": "f32+f32x2", "mixed_df": "f32x2+f64", "fp64": "f64", "fp32": "f32+bf16"}
+EVAL_KERNEL = {"mixed": "k_eval32 (FP32 near field, double-float L2P and combination)",
+               "mixed_df": "k_eval_df (near field and L2P in double-float)",
+               "fp64": "k_eval (near field and L2P in FP64)",
+               "fp32": "k_eval32 (near field and L2P in FP32)"}
+# DRAM bytes of one k_eval32 launch of the all-FP32 path (p = 20, m = 64, c_s = 1.3) at this
+# workload, from ncu (dram__bytes_read.sum 5.33 GB + dram__bytes_write.sum 1.01 GB)
+K_EVAL32_TRAFFIC = 5.33e9 + 1.01e9
 
 
 def parse():
@@ -62,10 +67,11 @@ def parse():
     ap.add_argument("--impl", default="sfmm", choices=["sfmm", "reference"])
     ap.add_argument("--n", type=int, default=16_000_000, help="N = M")
     ap.add_argument("--clumps", type=int, default=20_000)
-    ap.add_argument("--modes", default="mixed,mixed_df,fp64", help="paths to run; the first is the headline value")
+    ap.add_argument("--modes", default="mixed,mixed_df,fp64,fp32", help="paths to run; the first is the headline value")
     ap.add_argument("--leaf", type=int, default=0, help="leaf size m for every path (0 = each path's own)")
-    ap.add_argument("--check", type=int, default=200, help="targets checked against the oracle")
-    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the oracle CPU baseline")
+    ap.add_argument("--check", type=int, default=1000,
+                    help="oracle targets per stratum (near clump, empty sky) for the error check and CPU baseline")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the oracle CPU baseline (extra legs)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--shells", action="store_true",
                     help="also time the batched-shell workload (64 shells, 9.3e7 sources; slow to generate)")
@@ -83,13 +89,15 @@ class ClockSampler:
     """nvidia-smi samples (every 50 ms) of SM clock and throttle reasons during a
     region: the sampler is running (its first line written) before the region
     opens, and only samples stamped inside the region are summarised (if none
-    are, the one nearest to the region is reported with in_region false)."""
-    Q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    are, the one nearest to the region is reported with in_region false).  The
+    GPU is selected by the UUID of the CUDA device (CUDA ordinals and nvidia-smi
+    indices differ under CUDA_VISIBLE_DEVICES); every sample's UUID is checked."""
+    Q = ("timestamp,uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index):
-        self.idx = gpu_index
+    def __init__(self, cuda_device):
+        self.uuid = device_uuid(cuda_device)
         self.proc = None
         self.f = None
         self.t0 = self.t1 = None
@@ -98,7 +106,7 @@ class ClockSampler:
         try:
             self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
             self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
-                                          "-i", str(self.idx), "-lms", "50"], stdout=self.f,
+                                          "-i", self.uuid, "-lms", "50"], stdout=self.f,
                                          stderr=subprocess.DEVNULL)
             deadline = time.time() + 5.0
             while time.time() < deadline and os.path.getsize(self.f.name) == 0:
@@ -129,12 +137,14 @@ class ClockSampler:
         import datetime
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         parsed = []
+        uuid_ok = True
         for r in rows:
             r = [x.strip() for x in r]
             if len(r) < 10:
                 continue
             try:
                 ts = datetime.datetime.strptime(r[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                uuid_ok &= r[1] == self.uuid
                 parsed.append((ts, float(r[2]), float(r[3]), [n for n, v in zip(names, r[6:10]) if v.lower() == "active"]))
             except ValueError:
                 continue
@@ -147,7 +157,14 @@ class ClockSampler:
             inside = [min(parsed, key=lambda x: abs(x[0] - mid))]
         reasons = sorted({n for x in inside for n in x[3]})
         return {"sm_mhz": float(np.median([x[1] for x in inside])), "sm_max_mhz": inside[-1][2], "reasons": reasons,
-                "samples": len(inside), "in_region": in_region}
+                "samples": len(inside), "in_region": in_region, "gpu_uuid": self.uuid, "uuid_matches": uuid_ok}
+
+
+def device_uuid(cuda_device):
+    """nvidia-smi's UUID string ("GPU-...") of a CUDA device ordinal."""
+    import torch
+    u = str(torch.cuda.get_device_properties(cuda_device).uuid)
+    return u if u.startswith("GPU-") else "GPU-" + u
 
 
 def rel(a, b):
@@ -321,25 +338,6 @@ def run_shells(args, dev, clock_sampler):
     return out
 
 
-def oracle_rate(src, q, tgt, budget_s, seed_idx):
-    """Targets per second of the oracle direct sum on the host cores, timed on
-    a seeded sample sized to about budget_s seconds."""
-    from oracle.direct import direct_sum, threads
-    from paper_2210_07021_gb300 import workloads
-    q64 = q.astype(np.float64)
-    n_probe = 2 * threads()
-    probe = workloads.subsample(tgt.shape[0], n_probe, seed_idx, stream=11)
-    t0 = time.perf_counter()
-    direct_sum(src, q64, tgt[probe])
-    t_probe = max(time.perf_counter() - t0, 1e-3)
-    k = int(max(n_probe, min(tgt.shape[0], n_probe * budget_s / t_probe)))
-    idx = workloads.subsample(tgt.shape[0], k, seed_idx, stream=12)
-    t0 = time.perf_counter()
-    direct_sum(src, q64, tgt[idx])
-    t = time.perf_counter() - t0
-    return k, t, threads()
-
-
 def run_reference(args):
     ws, rank, local = dist_env()
     if ws > 1 and rank != 0:
@@ -374,6 +372,20 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def errors(psi, alpha, ref_psi, ref_alpha):
+    """Norm-wise relative errors of psi and alpha, and the largest pointwise
+    deflection error relative to the largest deflection (numpy or torch)."""
+    if hasattr(psi, "cpu"):
+        import torch
+        e_psi = float(torch.linalg.norm(psi - ref_psi) / torch.linalg.norm(ref_psi))
+        e_al = float(torch.linalg.norm(alpha - ref_alpha) / torch.linalg.norm(ref_alpha))
+        e_max = float((alpha - ref_alpha).norm(dim=1).max() / ref_alpha.norm(dim=1).max())
+    else:
+        e_psi, e_al = rel(psi, ref_psi), rel(alpha, ref_alpha)
+        e_max = float(np.linalg.norm(alpha - ref_alpha, axis=1).max() / np.linalg.norm(ref_alpha, axis=1).max())
+    return {"psi_rel": e_psi, "alpha_rel": e_al, "alpha_max_rel": e_max}
+
+
 def run_sfmm(args):
     import torch
     from paper_2210_07021_gb300 import sfmm, workloads
@@ -404,9 +416,22 @@ def run_sfmm(args):
         from paper_2210_07021_gb300.shard import max_over_ranks as mor
         return mor(v, device=dev)
 
+    # measured arithmetic rates of this GPU: the rooflines' denominators
+    peaks = {k: sfmm.peak_rate(w) for k, w in (("fp32", sfmm.PEAK_FP32), ("fp32x2", sfmm.PEAK_FP32X2),
+                                               ("fp64", sfmm.PEAK_FP64), ("mufu", sfmm.PEAK_MUFU))}
+    # the FP64 reference on every target (untimed)
+    ref_plan = sfmm.Plan(precision=sfmm.SFMM_FP64, q_f32=True, n_max=N, m_max=M, **REF_SETTINGS)
+    ref_psi, ref_alpha = ref_plan.deflection(src, q, tgt)
+    ref_plan.close()
+    # oracle targets: seeded samples near clumps and in empty sky (rank 0)
+    strata = None
+    if rank == 0:
+        near, empty = workloads.clump_strata(d["tgt"], d["clumps"], args.check, 3)
+        strata = {"near_clump": near, "empty_sky": empty}
+
     wanted = [m for m in MODES if m[0] in args.modes.split(",")]
     wanted.sort(key=lambda m: args.modes.split(",").index(m[0]))
-    results = {}
+    results, outputs = {}, {}
     for name, prec, p, stated, leaf, c_s, c_t in wanted:
         leaf = args.leaf or leaf
         plan = sfmm.Plan(p=p, leaf_size=leaf, c_s=c_s, c_t=c_t, precision=prec, q_f32=True, n_max=N, m_max=M)
@@ -420,7 +445,7 @@ def run_sfmm(args):
         plan.set_timing(1)
         stream = torch.cuda.current_stream()
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        eval_ms, pairs, launches, phase = [], [], 0, np.zeros(8)
+        eval_ms, launches, phase = [], 0, np.zeros(8)
         barrier()
         with ClockSampler(local) as clk:
             ev0.record(stream)
@@ -428,7 +453,6 @@ def run_sfmm(args):
                 plan.deflection(src, q, tgt, psi=psi, alpha=alpha)
                 st = plan.stats()
                 eval_ms.append(st["ms"][6])
-                pairs.append(n_pairs)
                 launches += st["launches"]
                 phase += np.array(st["ms"])
             ev1.record(stream)
@@ -437,19 +461,15 @@ def run_sfmm(args):
         plan.set_timing(False)
         r = {"precision": name, "p": p, "stated_error": stated, "leaf_size": leaf, "c_s": c_s, "c_t": c_t,
              "value": M * args.steps * ws / (elapsed_ms / 1e3) / 1e6, "ms_per_step": elapsed_ms / args.steps,
-             "gpu_launches": int(launches), "eval_ms": float(np.mean(eval_ms)), "pairs": float(np.mean(pairs)),
+             "gpu_launches": int(launches), "eval_ms": float(np.mean(eval_ms)), "pairs": float(n_pairs),
              "phase_ms": {k: v / args.steps for k, v in zip(
                  ["keys_sort", "tree_geometry", "up_pass", "lists", "m2l", "l2l", "evaluation", "total"], phase)},
-             "clocks": clk.summary()}
+             "clocks": clk.summary(),
+             "error_vs_fp64_all_M": dict(errors(psi, alpha, ref_psi, ref_alpha), targets=M,
+                                         reference="FP64 sFMM, p=32, m=32, c_s=2, c_t=0.45")}
         if rank == 0:
-            from oracle.direct import direct_sum
-            idx = workloads.subsample(M, args.check, 3, stream=9)
-            if "ref" not in results:
-                results["ref"] = direct_sum(d["src"], d["q"].astype(np.float64), d["tgt"][idx])
-            ref = results["ref"]
-            r["error_vs_oracle"] = {"psi_rel": rel(psi.cpu().numpy()[idx], ref["psi"]),
-                                    "alpha_rel": rel(alpha.cpu().numpy()[idx], ref["alpha"]),
-                                    "sample": int(idx.size), "norm": "l2 over the sample (relative)"}
+            idx = np.concatenate([strata["near_clump"], strata["empty_sky"]])
+            outputs[name] = (psi.cpu().numpy()[idx], alpha.cpu().numpy()[idx])
         # end to end through the host-array entry point (headline path only)
         if not args.no_e2e and name == wanted[0][0]:
             hs = torch.empty((N, 3), dtype=torch.float64, pin_memory=True).numpy()
@@ -471,10 +491,31 @@ def run_sfmm(args):
                         "h2d_bytes_per_step": int(N * 24 + N * 4 + M * 24), "d2h_bytes_per_step": int(M * 8 + M * 16)}
         results[name] = r
         plan.close()
+    del ref_psi, ref_alpha
     if rank != 0:
         if dist:
             dist.barrier()
         return
+    # the oracle on the stratified targets: the error of every path per stratum, and
+    # its own time on the host cores (the CPU baseline)
+    from oracle.direct import direct_sum, threads
+    idx = np.concatenate([strata["near_clump"], strata["empty_sky"]])
+    t0 = time.perf_counter()
+    ref = direct_sum(d["src"], d["q"].astype(np.float64), d["tgt"][idx])
+    t_or = time.perf_counter() - t0
+    n_near = strata["near_clump"].size
+    cpu = {"value": idx.size / t_or / 1e6, "unit": "Mpts/s", "cores": threads(), "kind": "oracle",
+           "sample": f"{idx.size} seeded targets ({n_near} near clumps, {idx.size - n_near} in empty sky) against "
+                     f"all {N} sources, FP64 direct sum, {t_or:.1f} s"}
+    for name, (ps, al) in outputs.items():
+        ev = {"all": errors(ps, al, ref["psi"], ref["alpha"]),
+              "near_clump": errors(ps[:n_near], al[:n_near], ref["psi"][:n_near], ref["alpha"][:n_near]),
+              "empty_sky": errors(ps[n_near:], al[n_near:], ref["psi"][n_near:], ref["alpha"][n_near:])}
+        ev["within_stated"] = bool(max(ev["all"]["psi_rel"], ev["all"]["alpha_rel"],
+                                       ev["near_clump"]["alpha_rel"], ev["empty_sky"]["alpha_rel"])
+                                   < results[name]["stated_error"])
+        ev["targets"] = f"{n_near} near clumps + {idx.size - n_near} in empty sky (norm-wise relative errors)"
+        results[name]["error_vs_oracle"] = ev
     head = results[wanted[0][0]]
     adj = shr = npm = shl = None
     if ws == 1 and not args.no_adjoint:
@@ -482,32 +523,20 @@ def run_sfmm(args):
         shr = run_shear(args, dev, ClockSampler(local))
         npm = run_npm(args, dev, ClockSampler(local))
     shl = run_shells(args, dev, ClockSampler(local)) if (ws == 1 and args.shells) else None
-    cpu = None
-    if ws == 1:
-        k, t, cores = oracle_rate(d["src"], d["q"], d["tgt"], args.cpu_seconds, 3)
-        cpu = {"value": k / t / 1e6, "unit": "Mpts/s", "cores": cores, "kind": "oracle",
-               "sample": f"{k} seeded targets against all {N} sources, FP64 direct sum, {t:.1f} s"}
 
     def roofline_of(r):
-        if r["precision"] == "fp64":
-            peak, bound, kern, src_ = FP64_PEAK_DERIVED, "alu", "k_eval (near field + L2P, FP64)", \
-                "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (not in MEASURED_PEAKS.json; " \
-                "an FMA loop measured 1.19 TFLOP/s)"
-        elif r["precision"] == "mixed_df":
-            peak, bound, kern, src_ = FP32_PEAK_DERIVED, "alu", "k_eval_df (near field in double-float + L2P)", \
-                "derived: 152 SMs x 128 FP32 FMA/clk x 2 flop x 2.07 GHz (not in MEASURED_PEAKS.json; " \
-                "an FMA loop measured 73 TFLOP/s)"
-        else:
-            kern = ("k_eval32 (near field in FP32 + L2P in double-float)" if r["precision"] == "mixed"
-                    else "k_eval32 (near field + L2P, FP32)")
-            peak, bound, src_ = FP32_PEAK_DERIVED, "alu", \
-                "derived: 152 SMs x 128 FP32 FMA/clk x 2 flop x 2.07 GHz (not in MEASURED_PEAKS.json; " \
-                "an FMA loop measured 73 TFLOP/s)"
-        ach = r["pairs"] * FLOPS_PER_PAIR_PSI / (r["eval_ms"] / 1e3)
-        out = {"bound": bound, "kernel": kern, "achieved": ach / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
-               "frac": ach / peak, "peak_source": src_,
-               "work_per_unit": f"{FLOPS_PER_PAIR_PSI} flop per near-field pair (1/d^2 and log counted as 4)",
+        fp64 = r["precision"] == "fp64"
+        peak = peaks["fp64"] if fp64 else peaks["fp32"]
+        secs = r["eval_ms"] / 1e3
+        ach = r["pairs"] * OPS_PER_PAIR / secs
+        out = {"bound": "alu", "kernel": EVAL_KERNEL[r["precision"]], "achieved": ach / 1e12, "peak": peak / 1e12,
+               "unit": "TFLOP/s", "frac": ach / peak,
+               "peak_source": ("measured in this run: sfmm_peak_rate, a loop of independent "
+                               + ("FP64" if fp64 else "FP32") + " FMA chains on a full grid"),
+               "work_per_unit": f"{OPS_PER_PAIR} operations per near-field pair (12 flop + 1 reciprocal + 1 log)",
                "pairs_per_launch": r["pairs"], "launch_ms": r["eval_ms"], "traffic": None}
+        if not fp64:
+            out["mufu_frac"] = r["pairs"] * MUFU_PER_PAIR / secs / peaks["mufu"]
         if (r["precision"] == "fp32" and r["leaf_size"] == 64 and r["c_s"] == 1.3 and N == 16_000_000
                 and M == 16_000_000 and args.clumps == 20_000):
             out["traffic"] = K_EVAL32_TRAFFIC
@@ -528,12 +557,16 @@ def run_sfmm(args):
                        "stated_error": head["stated_error"], "leaf_size": head["leaf_size"], "c_s": head["c_s"],
                        "c_t": head["c_t"],
                        "l2": "inputs larger than L2 (384 MB of positions each), no flush"},
-            "error_vs_oracle": head.get("error_vs_oracle"), "roofline": modes[head["precision"]]["roofline"],
+            "error_vs_oracle": head.get("error_vs_oracle"), "error_vs_fp64_all_M": head["error_vs_fp64_all_M"],
+            "roofline": modes[head["precision"]]["roofline"],
             "cpu_baseline": cpu, "e2e": head.get("e2e"), "gpu_launches": head["gpu_launches"],
-            "phase_ms": head["phase_ms"], "clocks": head["clocks"], "adjoint": adj, "shear": shr, "npm": npm, "shells": shl,
-            "modes": {k: {kk: vv for kk, vv in v.items() if kk not in ("phase_ms",)} for k, v in modes.items()}}
-    if "fp64" in results and head["precision"] != "fp64":
-        line["speedup_vs_fp64"] = head["value"] / results["fp64"]["value"]
+            "phase_ms": head["phase_ms"], "clocks": head["clocks"],
+            "peaks_measured": {k: v / 1e12 for k, v in peaks.items()},
+            "peaks_unit": "TFLOP/s (FMA = 2 flop); mufu: Tops/s (rcp + lg2)",
+            "adjoint": adj, "shear": shr, "npm": npm, "shells": shl,
+            "modes": {k: {kk: vv for kk, vv in v.items()} for k, v in modes.items()}}
+    if "fp64" in results:
+        line["speedup_vs_fp64"] = {k: results[k]["value"] / results["fp64"]["value"] for k in results if k != "fp64"}
     print(json.dumps(line), flush=True)
     if dist:
         dist.barrier()

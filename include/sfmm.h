@@ -281,6 +281,18 @@ sfmm_status sfmm_keys(const double* xyz, int64_t n, uint64_t* keys, void* stream
  */
 sfmm_status sfmm_sort_keys_static(const double* xyz, int64_t n, uint64_t* keys, uint32_t* perm, void* stream);
 
+/*
+ * Measured arithmetic rate of this GPU (the denominators of the evaluation
+ * kernels' rooflines; the paper has no counterpart): which = 0 FP32 FMA,
+ * 1 packed FP32x2 FMA, 2 FP64 FMA (flop/s, an FMA counted as 2), 3 MUFU
+ * reciprocal + base-2 logarithm (operations/s).  A loop of independent chains on
+ * a full grid, timed with CUDA events on `stream` (cudaStream_t or NULL) after
+ * a warm-up launch; about half a second each.  Allocates 16 bytes of device
+ * memory for the duration of the call.  SFMM_EINVAL for another `which` or a
+ * NULL ops_per_s.
+ */
+sfmm_status sfmm_peak_rate(int which, double* ops_per_s, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -21,7 +21,7 @@ SFMM_FP64, SFMM_MIXED, SFMM_MIXED_DF, SFMM_FP32 = 0, 1, 2, 3
 EXPORTS = ["sfmm_default_options", "sfmm_plan", "sfmm_potential", "sfmm_deflection", "sfmm_deflection_host",
            "sfmm_adjoint", "sfmm_shear", "sfmm_deflection_batch",
            "sfmm_destroy", "sfmm_last_error", "sfmm_order", "sfmm_get_stats", "sfmm_set_timing",
-           "sfmm_debug_copy", "sfmm_keys", "sfmm_sort_keys_static"]
+           "sfmm_debug_copy", "sfmm_keys", "sfmm_sort_keys_static", "sfmm_peak_rate"]
 STATIC_SORT_MAX_N = 1 << 18
 
 
@@ -94,6 +94,8 @@ def load(build_if_missing=True):
     L.sfmm_keys.restype = ci
     L.sfmm_sort_keys_static.argtypes = [vp, i64, vp, vp, vp]
     L.sfmm_sort_keys_static.restype = ci
+    L.sfmm_peak_rate.argtypes = [ci, ctypes.POINTER(ctypes.c_double), vp]
+    L.sfmm_peak_rate.restype = ci
     _lib = L
     return L
 
@@ -321,3 +323,15 @@ def sort_keys_static(xyz, keys=None, perm=None):
                                       ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
     _check(st)
     return keys, perm
+
+
+PEAK_FP32, PEAK_FP32X2, PEAK_FP64, PEAK_MUFU = range(4)
+
+
+def peak_rate(which):
+    """Measured FP32 / packed FP32x2 / FP64 FMA rate (flop/s) or MUFU rate
+    (rcp + lg2 operations/s) of the current GPU (sfmm_peak_rate)."""
+    import torch
+    v = ctypes.c_double()
+    _check(load().sfmm_peak_rate(which, ctypes.byref(v), ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)))
+    return v.value

@@ -202,8 +202,27 @@ def clustered_pair(n=16_000_000, m=None, n_clumps=20_000, config_index=3, q_dtyp
     src = clustered(rng_for(config_index, 0), n, n_clumps, clumps=clumps)
     tgt = clustered(rng_for(config_index, 1), m, n_clumps, clumps=clumps)
     q = np.full(n, 4.0 * np.pi / n, dtype=q_dtype)
-    return dict(src=src, q=q, tgt=tgt,
+    return dict(src=src, q=q, tgt=tgt, clumps=clumps,
                 workload=f"clustered sources and targets N=M={n} ({n_clumps} shared clumps), q {np.dtype(q_dtype).name}")
+
+
+def clump_strata(tgt, clumps, k_each, config_index, trunc=20.0, pool=40_000):
+    """Seeded target samples of two strata: k_each targets inside some clump's
+    truncation radius (trunc scale radii: near-clump) and k_each outside every
+    clump's (empty sky, where only the uniform background lies), drawn from a
+    seeded pool of candidate targets.  Returns (near, empty) index arrays."""
+    centres, rs = clumps
+    cand = subsample(tgt.shape[0], min(pool, tgt.shape[0]), config_index, stream=21)
+    inside = np.zeros(cand.size, dtype=bool)
+    cos_lim = np.cos(np.minimum(trunc * rs, np.pi))
+    for i in range(0, cand.size, 2048):
+        dots = tgt[cand[i:i + 2048]] @ centres.T             # [chunk, clumps]
+        inside[i:i + 2048] = (dots > cos_lim[None, :]).any(axis=1)
+    near, empty = cand[inside], cand[~inside]
+    rng = rng_for(config_index, 22)
+    near = np.sort(rng.choice(near, size=min(k_each, near.size), replace=False))
+    empty = np.sort(rng.choice(empty, size=min(k_each, empty.size), replace=False))
+    return near, empty
 
 
 def subsample(n, k, config_index, stream=7):
