@@ -96,8 +96,8 @@ class ClockSampler:
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, cuda_device):
-        self.uuid = device_uuid(cuda_device)
+    def __init__(self, cuda_device, uuid=None):
+        self.uuid = uuid or device_uuid(cuda_device)
         self.proc = None
         self.f = None
         self.t0 = self.t1 = None

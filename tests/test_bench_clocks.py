@@ -17,13 +17,16 @@ def stamp(t):
     return datetime.datetime.fromtimestamp(t).strftime("%Y/%m/%d %H:%M:%S.%f")[:-3]
 
 
-def sampler_with(rows, t0, t1):
-    s = bench.ClockSampler(0)
+UUID = "GPU-00000000-1111-2222-3333-444444444444"
+
+
+def sampler_with(rows, t0, t1, uuid=UUID):
+    s = bench.ClockSampler(0, uuid=UUID)
     s.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
     for t, sm, reasons in rows:
         flags = ["Active" if n in reasons else "Not Active"
                  for n in ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")]
-        s.f.write(", ".join([stamp(t), "0", str(sm), "2070", "900.00", "0x0"] + flags) + "\n")
+        s.f.write(", ".join([stamp(t), uuid, str(sm), "2070", "900.00", "0x0"] + flags) + "\n")
     s.f.flush()
     s.t0, s.t1 = t0, t1
     return s
@@ -56,3 +59,13 @@ def test_malformed_lines_are_skipped_and_empty_log_gives_none():
     out = s.summary()
     assert out["samples"] == 1
     assert sampler_with([], t0, t0 + 0.1).summary() is None
+
+
+def test_samples_of_another_gpu_are_flagged():
+    """The sampler asks nvidia-smi for the CUDA device's UUID; a sample that
+    names another GPU (an index/ordinal mix-up) is reported, not hidden."""
+    t0 = 1_800_000_000.0
+    rows = [(t0 + 0.05, 2070, set())]
+    assert sampler_with(rows, t0, t0 + 0.1).summary()["uuid_matches"] is True
+    bad = sampler_with(rows, t0, t0 + 0.1, uuid="GPU-99999999-1111-2222-3333-444444444444").summary()
+    assert bad["uuid_matches"] is False and bad["gpu_uuid"] == UUID
