@@ -231,8 +231,8 @@ def run_adjoint(args, dev, clock_sampler):
 
 
 def run_shear(args, dev, clock_sampler):
-    """Shear (gamma_1, gamma_2) on the gradient workload's sky, FP64 path at
-    p = 32; error vs the oracle's Hessian on a target sample."""
+    """Shear (gamma_1, gamma_2) and magnification on the gradient workload's sky,
+    FP64 path at p = 32; error vs the oracle's Hessian on a target sample."""
     import torch
     from paper_2210_07021_gb300 import sfmm, workloads
     d = workloads.loss_sky()
@@ -242,13 +242,13 @@ def run_shear(args, dev, clock_sampler):
     tgt = torch.as_tensor(d["tgt"], device=dev)
     plan = sfmm.Plan(p=32, leaf_size=64, c_t=0.45, n_max=N, m_max=M)
     for _ in range(args.warmup):
-        g, _, _ = plan.shear(src, q, tgt)
+        g, _, _, mu = plan.shear(src, q, tgt, with_mu=True)
     torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with clock_sampler as clk:
         ev0.record(torch.cuda.current_stream())
         for _ in range(args.steps):
-            g, _, _ = plan.shear(src, q, tgt)
+            g, _, _, mu = plan.shear(src, q, tgt, with_mu=True)
         ev1.record(torch.cuda.current_stream())
         torch.cuda.synchronize()
     ms = ev0.elapsed_time(ev1) / args.steps
@@ -258,7 +258,8 @@ def run_shear(args, dev, clock_sampler):
     plan.close()
     return {"workload": d["workload"].split(", loss")[0], "N": N, "M": M, "path": "FP64, p=32, m=64, c_t=0.45",
             "ms_per_step": ms, "value": M * 1e-3 / ms, "unit": "Mpts/s (targets per shear solve)",
-            "error_vs_oracle": {"gamma_rel": rel(g.cpu().numpy()[idx], ref["gamma"]), "sample": int(idx.size),
+            "error_vs_oracle": {"gamma_rel": rel(g.cpu().numpy()[idx], ref["gamma"]),
+                                "mu_rel": rel(mu.cpu().numpy()[idx], ref["mu"]), "sample": int(idx.size),
                                 "stated": 1e-9},
             "clocks": clk.summary()}
 

@@ -54,7 +54,7 @@ typedef enum {
     SFMM_EINVAL = 1,       /* an argument is out of range                        */
     SFMM_ENOMEM = 2,       /* a device allocation failed                         */
     SFMM_ECUDA = 3,        /* a CUDA call failed (message in sfmm_last_error)    */
-    SFMM_ETIMEOUT = 4,     /* reserved: a bounded device wait gave up            */
+    SFMM_ETIMEOUT = 4,     /* a bounded device wait gave up (its work was drained; the plan stays usable) */
     SFMM_EDEGENERATE = 5   /* reserved: degenerate input (e.g. non-finite data)  */
 } sfmm_status;
 
@@ -90,6 +90,9 @@ typedef struct {
                               (f(u) = (m(u) - u)/(1 - u) times the point-mass term, u = sin^2(t/2),
                               m = 2u/s - u^2/s^2, s = sin^2(sigma/2)) and psi continues the point-mass
                               potential; far pairs also need d - R_T - R_S > sigma.  SFMM_FP64 only. */
+    int wait_limit;        /* polls after which a bounded device wait (the tensor-core M2L's mbarrier waits)
+                              gives up, returning SFMM_ETIMEOUT with the device context intact; 0 (default) =
+                              2^26.  A test hook: a small value makes the time-out path run. */
 } sfmm_options;
 
 /* Fill *opt with the defaults listed above.  Returns SFMM_EINVAL if opt is NULL. */
@@ -150,19 +153,20 @@ sfmm_status sfmm_deflection_batch(sfmm_plan_t plan, int n_shells, const double* 
                                   const int64_t* M, double* const* psi, double* const* alpha, int lanes);
 
 /*
- * Shear (Sec. 2.2, Eq. GAM_DEF): gamma [M][2] = (gamma_1, gamma_2), the
- * trace-free part of the covariant Hessian of psi on (e_theta, e_phi) at each
- * target, gamma_1 = (H11 - H22)/2, gamma_2 = H12; psi and alpha as in
- * sfmm_deflection (either may be NULL).  For point masses the trace is
+ * Shear and magnification (Sec. 2.2, Eq. GAM_DEF): gamma [M][2] = (gamma_1,
+ * gamma_2), the trace-free part of the covariant Hessian H of psi on
+ * (e_theta, e_phi) at each target, gamma_1 = (H11 - H22)/2, gamma_2 = H12, and
+ * (if mu is not NULL) mu [M] = 1/((1 - tr H/2)^2 - gamma_1^2 - gamma_2^2), the
+ * magnification of a small source (Sec. 2.2).  For point masses the trace is
  * kappa - kappa_bar = tr H = -sum(q)/(4 pi) at a target off the masses
- * (Delta G = delta - 1/(4 pi); a target on a mass skips that mass), so the
- * magnification mu = 1/((1 - tr H/2)^2 - gamma_1^2 - gamma_2^2) follows from
- * gamma.  Far field from the second derivative of
- * each leaf's local expansion (conformal chart), near field from the closed
- * form of the Hessian of G.  Runs in FP64 whatever opt.precision is.
+ * (Delta G = delta - 1/(4 pi)); a target on a mass skips that mass, in the
+ * trace as in every output.  psi and alpha as in sfmm_deflection (either may
+ * be NULL).  Far field from the second derivative of each leaf's local
+ * expansion (conformal chart), near field from the closed form of the Hessian
+ * of G.  Runs in FP64 whatever opt.precision is.
  */
 sfmm_status sfmm_shear(sfmm_plan_t plan, const double* src_xyz, const void* q, int64_t N,
-                       const double* tgt_xyz, int64_t M, double* psi, double* alpha, double* gamma);
+                       const double* tgt_xyz, int64_t M, double* psi, double* alpha, double* gamma, double* mu);
 
 /*
  * Adjoint: gradients of a loss L(psi, alpha) of sfmm_deflection's outputs with
@@ -214,6 +218,11 @@ typedef struct {
     double ms[8];
 } sfmm_stats;
 sfmm_status sfmm_get_stats(sfmm_plan_t plan, sfmm_stats* out);
+
+/* Change the plan's wait_limit (sfmm_options.wait_limit) for later solves: 0 = the default
+ * bound; a small value makes the bounded device waits run out (a test hook).  SFMM_EINVAL
+ * for a negative value. */
+sfmm_status sfmm_set_wait_limit(sfmm_plan_t plan, int polls);
 
 /* Record per-phase device times (CUDA events) in later solves: 0 off (default), 1 phase
  * times, 2 phase times and the count of near-field point pairs (one more kernel and a

@@ -40,7 +40,7 @@ cudaError_t launch_m2l_list(const uint64_t* ptgt, const uint32_t* psrc, const ui
                             void* local, cudaStream_t s);
 cudaError_t launch_m2l_tc(int64_t n_pairs, const uint64_t* ptgt, const uint32_t* psrc, const void* geo,
                           const void* mpole, void* local, int p, uint32_t* leftover, uint32_t* n_leftover,
-                          uint32_t* tile_ctr, int* status, cudaStream_t s);
+                          uint32_t* tile_ctr, int* status, int wait_limit, cudaStream_t s);
 cudaError_t launch_l2l(const TreeView& T, int a, int b, int p, const double* tables, const void* geo, void* local,
                        int ek, cudaStream_t s);
 size_t frame_df_bytes();
@@ -89,7 +89,7 @@ cudaError_t launch_eval_adj(const TreeView& T, const int* leaves, int64_t n_leav
 cudaError_t launch_eval(const TreeView& T, const int* leaves, int64_t n_leaves, const double4_32a* src, const double4_32a* tgt,
                         const uint32_t* tperm, const int64_t* p2p_off, const uint32_t* p2p_src, const double* local,
                         const double* mpole, int p, int zero_mean, double sigma, double* psi, double* alpha,
-                        double* gamma, unsigned long long* leaf_ctr, cudaStream_t s);
+                        double* gamma, double* mu, unsigned long long* leaf_ctr, cudaStream_t s);
 
 namespace {
 std::atomic<int64_t> g_launches{0};
@@ -176,6 +176,12 @@ __global__ void k_adjoint_prep(const double* __restrict__ x, int64_t m, const do
         dip[3 * i + 1] = a * (x2 * sp) + b * cp;
         dip[3 * i + 2] = -a * rho;
     }
+}
+
+__global__ void k_fill(double* __restrict__ p, int64_t n, double v)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = v;
 }
 
 __global__ void k_gather_tgt(const double* __restrict__ xyz, const uint32_t* __restrict__ perm, int64_t n,
@@ -277,7 +283,8 @@ struct AdjIO {
 };
 
 sfmm_status solve(sfmm_plan_s* P, const double* src, const void* q, int64_t N, const double* tgt, int64_t M,
-                  double* psi, double* alpha, const AdjIO* adj = nullptr, double* gamma = nullptr)
+                  double* psi, double* alpha, const AdjIO* adj = nullptr, double* gamma = nullptr,
+                  double* mu = nullptr)
 {
     cudaStream_t s = P->stream;
     const int precision = (adj || gamma) ? SFMM_FP64 : P->opt.precision;   // adjoint and shear run in FP64
@@ -296,6 +303,10 @@ sfmm_status solve(sfmm_plan_s* P, const double* src, const void* q, int64_t N, c
         if (adj && adj->grad3 && (e = cudaMemsetAsync(adj->grad3, 0, (size_t)M * 24, s)))
             return cuda_fail(P, e, "memset gradient");
         if (gamma && (e = cudaMemsetAsync(gamma, 0, (size_t)M * 16, s))) return cuda_fail(P, e, "memset gamma");
+        if (mu) {       // no mass: H = 0, mu = 1
+            k_fill<<<grid_for(M), 256, 0, s>>>(mu, M, 1.0); count_launch();
+            if ((e = cudaGetLastError())) return cuda_fail(P, e, "mu");
+        }
         if ((e = cudaStreamSynchronize(s))) return cuda_fail(P, e, "sync");
         return SFMM_OK;
     }
@@ -447,7 +458,7 @@ sfmm_status solve(sfmm_plan_s* P, const double* src, const void* q, int64_t N, c
         if ((e = ensure(P->leftover, (size_t)std::max<int64_t>(P->n_m2l, 1) * 4))) return cuda_fail(P, e, "alloc");
         if ((e = cudaMemsetAsync(P->small.as<int64_t>() + 20, 0, 16, s))) return cuda_fail(P, e, "memset");
         if ((e = launch_m2l_tc(P->n_m2l, m2l_t, m2l_s, P->m2l_geo.p, P->mpole.p, P->local.p, p, P->leftover.as<uint32_t>(),
-                               n_left, tile_ctr, status, s)))
+                               n_left, tile_ctr, status, P->opt.wait_limit, s)))
             return cuda_fail(P, e, "M2L (tensor cores)");
         if ((e = launch_m2l_list(m2l_t, m2l_s, P->leftover.as<uint32_t>(), n_left, P->n_m2l, p, P->tables.as<double>(),
                                  P->m2l_geo.p, P->mpole.p, P->local.p, s)))
@@ -495,7 +506,7 @@ sfmm_status solve(sfmm_plan_s* P, const double* src, const void* q, int64_t N, c
                                      P->logtab.as<float4>(), p, P->opt.zero_mean, psi, alpha, leaf_ctr, s);
     else e = launch_eval(T, P->leaves_tgt.as<int>(), P->n_leaves_tgt, P->src4.as<double4_32a>(),
                          P->tgt4.as<double4_32a>(), tperm, P->p2p_off.as<int64_t>(), p2p_s, P->local.as<double>(),
-                         P->mpole.as<double>(), p, P->opt.zero_mean, P->opt.sigma, psi, alpha, gamma, leaf_ctr, s);
+                         P->mpole.as<double>(), p, P->opt.zero_mean, P->opt.sigma, psi, alpha, gamma, mu, leaf_ctr, s);
     if (e) return cuda_fail(P, e, "evaluation");
     tm.mark();
     if (P->timing >= 2) {
@@ -510,12 +521,13 @@ sfmm_status solve(sfmm_plan_s* P, const double* src, const void* q, int64_t N, c
         if ((e = cudaStreamSynchronize(s))) return cuda_fail(P, e, "sync");
         P->stats.p2p_interactions = (int64_t)h;
     }
+    // the tensor-core M2L's status word comes back with the solve's one synchronisation
+    const bool tc_status = fp32 && P->opt.m2l_tensor_cores;
+    if (tc_status && (e = cudaMemcpyAsync(P->h_status, status, 4, cudaMemcpyDeviceToHost, s)))
+        return cuda_fail(P, e, "status");
     if ((e = cudaStreamSynchronize(s))) return cuda_fail(P, e, "solve");
-    if (fp32 && P->opt.m2l_tensor_cores) {
-        int st = 0;
-        if ((e = cudaMemcpy(&st, status, 4, cudaMemcpyDeviceToHost))) return cuda_fail(P, e, "status");
-        if (st) return fail(P, SFMM_ETIMEOUT, "a bounded wait of the tensor-core M2L kernel ran out");
-    }
+    if (tc_status && *P->h_status)
+        return fail(P, SFMM_ETIMEOUT, "a bounded wait of the tensor-core M2L kernel ran out");
     tm.finish();
     P->stats.n_nodes = nn;
     P->stats.n_leaves = P->n_leaves;
@@ -589,6 +601,7 @@ sfmm_status sfmm_plan(sfmm_plan_t* out, int max_depth, int order_p, double tol, 
         return plan_fail("unknown precision");
     if (o.n_max < 0 || o.m_max < 0) return plan_fail("n_max and m_max must be >= 0");
     if (!(o.sigma >= 0.0 && o.sigma < 1.5707963267948966)) return plan_fail("sigma must be in [0, pi/2)");
+    if (o.wait_limit < 0) return plan_fail("wait_limit must be >= 0");
     if (o.sigma > 0.0 && o.precision != SFMM_FP64)
         return plan_fail("sigma > 0 (Near Particle Model) runs on the FP64 path only (precision SFMM_FP64)");
     auto* P = new (std::nothrow) sfmm_plan_s();
@@ -603,7 +616,7 @@ sfmm_status sfmm_plan(sfmm_plan_t* out, int max_depth, int order_p, double tol, 
     float lt[129 * 4];
     fill_log_table(lt);
     cudaError_t e;
-    if ((e = cudaStreamCreateWithFlags(&P->aux, cudaStreamNonBlocking)) ||
+    if ((e = cudaMallocHost(&P->h_status, sizeof(int))) || (e = cudaStreamCreateWithFlags(&P->aux, cudaStreamNonBlocking)) ||
         (e = cudaEventCreateWithFlags(&P->ev_fork, cudaEventDisableTiming)) ||
         (e = cudaEventCreateWithFlags(&P->ev_join, cudaEventDisableTiming))) {
         std::lock_guard<std::mutex> g(g_err_mu);
@@ -734,13 +747,13 @@ sfmm_status sfmm_deflection_batch(sfmm_plan_t plan, int n_shells, const double* 
 }
 
 sfmm_status sfmm_shear(sfmm_plan_t plan, const double* src_xyz, const void* q, int64_t N, const double* tgt_xyz,
-                       int64_t M, double* psi, double* alpha, double* gamma)
+                       int64_t M, double* psi, double* alpha, double* gamma, double* mu)
 {
     sfmm_status st = check_args(plan, src_xyz, q, N, tgt_xyz, M);
     if (st != SFMM_OK) return st;
     if (M > 0 && !gamma) return fail(plan, SFMM_EINVAL, "gamma must be non-NULL");
     if (plan->opt.sigma > 0.0) return fail(plan, SFMM_EINVAL, "sfmm_shear supports point masses only (sigma == 0)");
-    return solve(plan, src_xyz, q, N, tgt_xyz, M, psi, alpha, nullptr, gamma);
+    return solve(plan, src_xyz, q, N, tgt_xyz, M, psi, alpha, nullptr, gamma, mu);
 }
 
 sfmm_status sfmm_adjoint(sfmm_plan_t plan, const double* src_xyz, const void* q, int64_t N, const double* tgt_xyz,
@@ -839,6 +852,7 @@ void sfmm_destroy(sfmm_plan_t plan)
     if (plan->ev_fork) cudaEventDestroy(plan->ev_fork);
     if (plan->ev_join) cudaEventDestroy(plan->ev_join);
     if (plan->aux) cudaStreamDestroy(plan->aux);
+    if (plan->h_status) cudaFreeHost(plan->h_status);
     delete plan;
 }
 
@@ -857,6 +871,14 @@ sfmm_status sfmm_get_stats(sfmm_plan_t plan, sfmm_stats* out)
 {
     if (!plan || !out) return SFMM_EINVAL;
     *out = plan->stats;
+    return SFMM_OK;
+}
+
+sfmm_status sfmm_set_wait_limit(sfmm_plan_t plan, int polls)
+{
+    if (!plan) return SFMM_EINVAL;
+    if (polls < 0) return fail(plan, SFMM_EINVAL, "wait limit must be >= 0");
+    plan->opt.wait_limit = polls;
     return SFMM_OK;
 }
 

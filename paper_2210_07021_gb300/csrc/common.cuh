@@ -96,6 +96,7 @@ struct sfmm_plan_s {
                                            // (the host entry point copies the targets there)
     std::string err;
     int timing = 0;                        // 0 off, 1 phase times, 2 also the near-field pair count
+    int* h_status = nullptr;               // pinned host word: the tensor-core M2L's status of the last solve
     sfmm_stats stats{};
 
     // sources (key-sorted)

@@ -54,6 +54,7 @@ struct EvalArgs {
     double* psi;
     double* alpha;
     double* gamma;            // [M][2] shear (gamma_1, gamma_2) in (e_theta, e_phi), or NULL
+    double* mu;               // [M] magnification 1/((1 - tr H/2)^2 - |gamma|^2), or NULL (with gamma)
     unsigned long long* leaf_ctr;   // zero at launch: the warps take target leaves from it one at a time
     double npm_s;             // Near Particle Model: sin^2(sigma/2) (NPM kernels only)
 };
@@ -91,9 +92,9 @@ template <bool SHEAR, bool NPM>
 __global__ void __launch_bounds__(128) k_eval(EvalArgs A)
 {
     const int lane = threadIdx.x & 31;
-    double shift = 0.0;
-    if (A.zero_mean)
-        for (int b = 0; b < 12; ++b) shift += A.base_mpole[(size_t)b * EXP_STRIDE + 1];
+    double shift = 0.0, qtot = 0.0;        // qtot = sum q / 4pi (the base boxes' Q)
+    for (int b = 0; b < 12; ++b) qtot += A.base_mpole[(size_t)b * EXP_STRIDE + 1];
+    if (A.zero_mean) shift = qtot;
     for (;;) {
         const int64_t w = next_leaf(A.leaf_ctr, lane);
         if (w >= A.n_leaves) break;
@@ -111,6 +112,7 @@ __global__ void __launch_bounds__(128) k_eval(EvalArgs A)
             const double4_32a x = A.tgt[tf + (active ? ti : 0)];
             double sl = 0.0, sx = 0.0, sy = 0.0, sz = 0.0, sq = 0.0;
             double Sxx = 0.0, Syy = 0.0, Szz = 0.0, Sxy = 0.0, Sxz = 0.0, Syz = 0.0;
+            double sqs = 0.0;                 // SHEAR: masses at the target's position (left out)
             double sqa = 0.0;                 // NPM: sum of f q (the alpha part of sum q)
             for (int64_t k = nb0; k < nb1; ++k) {
                 const int sleaf = (int)A.p2p_src[k];
@@ -149,6 +151,8 @@ __global__ void __launch_bounds__(128) k_eval(EvalArgs A)
                             Sxx += w4 * dx * dx; Syy += w4 * dy * dy; Szz += w4 * dz * dz;
                             Sxy += w4 * dx * dy; Sxz += w4 * dx * dz; Syz += w4 * dy * dz;
                         }
+                    } else if (SHEAR) {
+                        sqs += y.w;
                     }
                 }
             }
@@ -162,6 +166,7 @@ __global__ void __launch_bounds__(128) k_eval(EvalArgs A)
             if (SHEAR) {
                 Sxx = group_sum(Sxx, lpt); Syy = group_sum(Syy, lpt); Szz = group_sum(Szz, lpt);
                 Sxy = group_sum(Sxy, lpt); Sxz = group_sum(Sxz, lpt); Syz = group_sum(Syz, lpt);
+                sqs = group_sum(sqs, lpt);
             }
             if (!active || sub != 0) continue;
             // ---- L2P in the leaf frame
@@ -231,6 +236,11 @@ __global__ void __launch_bounds__(128) k_eval(EvalArgs A)
                 g2 -= stp / PI;
                 A.gamma[2 * (size_t)o] = g1;
                 A.gamma[2 * (size_t)o + 1] = g2;
+                if (A.mu) {       // tr H = kappa - kappa_bar = -(sum q of the masses not at x) / 4pi
+                    const double trh = -qtot + INV4PI * sqs;
+                    const double a = 1.0 - 0.5 * trh;
+                    A.mu[o] = 1.0 / (a * a - g1 * g1 - g2 * g2);
+                }
             }
         }
     }
@@ -1262,7 +1272,7 @@ cudaError_t launch_count_pairs(const TreeView& T, const int* leaves, int64_t n_l
 cudaError_t launch_eval(const TreeView& T, const int* leaves, int64_t n_leaves, const double4_32a* src, const double4_32a* tgt,
                         const uint32_t* tperm, const int64_t* p2p_off, const uint32_t* p2p_src, const double* local,
                         const double* mpole, int p, int zero_mean, double sigma, double* psi, double* alpha,
-                        double* gamma, unsigned long long* leaf_ctr, cudaStream_t s)
+                        double* gamma, double* mu, unsigned long long* leaf_ctr, cudaStream_t s)
 {
     if (n_leaves == 0) return cudaSuccess;
     EvalArgs A;
@@ -1282,6 +1292,7 @@ cudaError_t launch_eval(const TreeView& T, const int* leaves, int64_t n_leaves, 
     A.psi = psi;
     A.alpha = alpha;
     A.gamma = gamma;
+    A.mu = mu;
     A.npm_s = sin(0.5 * sigma) * sin(0.5 * sigma);
     A.leaf_ctr = leaf_ctr;
     int64_t blocks = 0;
@@ -1319,6 +1330,7 @@ cudaError_t launch_eval_adj(const TreeView& T, const int* leaves, int64_t n_leav
     A.psi = phi;
     A.alpha = nullptr;
     A.gamma = nullptr;
+    A.mu = nullptr;
     AA.dip = dip;
     AA.w = w;
     AA.w_f32 = w_f32;

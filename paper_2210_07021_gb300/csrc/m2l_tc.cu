@@ -63,9 +63,19 @@ __device__ __forceinline__ uint64_t umma_desc(uint32_t addr, uint32_t sbo)
     return d;
 }
 
-__device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity)
+// Bounded wait on an mbarrier phase.  With a limit below WAIT_LIMIT (the test
+// hook of sfmm_options.wait_limit) the polls are non-blocking test_wait, so a
+// small limit runs out before the tensor core can finish; otherwise try_wait,
+// which may suspend the thread between polls.
+__device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity, int limit = WAIT_LIMIT)
 {
     uint32_t done = 0;
+    if (limit < WAIT_LIMIT) {
+        for (int it = 0; it < limit && !done; ++it)
+            asm volatile("{\n.reg .pred p;\nmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
+                         : "=r"(done) : "r"(smem_u32(mbar)), "r"(parity) : "memory");
+        return done != 0;
+    }
     for (int it = 0; it < WAIT_LIMIT && !done; ++it)
         asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
                      : "=r"(done) : "r"(smem_u32(mbar)), "r"(parity) : "memory");
@@ -229,7 +239,8 @@ __global__ void __launch_bounds__(128, TC_CTAS) k_m2l_tc(int64_t n_pairs, const 
                                                 const uint32_t* __restrict__ psrc, const XGeo32* __restrict__ geo,
                                                 const float* __restrict__ mpole, float* __restrict__ local, int p,
                                                 uint32_t* __restrict__ leftover, uint32_t* __restrict__ n_leftover,
-                                                uint32_t* __restrict__ tile_ctr, int* __restrict__ status)
+                                                uint32_t* __restrict__ tile_ctr, int* __restrict__ status,
+                                                int wait_limit)
 {
     static_assert(PL % 8 == 0 && PL <= PK, "PL: a multiple of 8 up to PK");
     constexpr int NC = (PL + 15) / 16;            // accumulator chunks of 16 columns read back
@@ -330,7 +341,7 @@ __global__ void __launch_bounds__(128, TC_CTAS) k_m2l_tc(int64_t n_pairs, const 
         // ---------------- stage 1 GEMM: D1 = A * B2^T
         if (tid == 0) issue_stage<PK>(S, S->b2, 0);
         pending = true;
-        if (!mbar_wait(&S->mbar, phase)) { atomicExch(status, SFMM_ETIMEOUT); S->abort_flag = 1; }
+        if (!mbar_wait(&S->mbar, phase, wait_limit)) { atomicExch(status, SFMM_ETIMEOUT); S->abort_flag = 1; }
         else pending = false;
         phase ^= 1u;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -352,7 +363,7 @@ __global__ void __launch_bounds__(128, TC_CTAS) k_m2l_tc(int64_t n_pairs, const 
         // ---------------- stage 2 GEMM: D2 = A * B1^T
         if (tid == 0) issue_stage<PK>(S, S->b1, PK);
         pending = true;
-        if (!mbar_wait(&S->mbar, phase)) { atomicExch(status, SFMM_ETIMEOUT); S->abort_flag = 1; }
+        if (!mbar_wait(&S->mbar, phase, wait_limit)) { atomicExch(status, SFMM_ETIMEOUT); S->abort_flag = 1; }
         else pending = false;
         phase ^= 1u;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -404,7 +415,8 @@ __global__ void __launch_bounds__(128, TC_CTAS) k_m2l_tc(int64_t n_pairs, const 
         __syncthreads();
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     }
-    // an MMA batch may still be in flight after a time-out: wait for it (bounded) before freeing
+    // an MMA batch may still be in flight after a time-out: wait for it (with the full bound,
+    // whatever the limit of the waits above) before freeing the tensor memory it writes
     if (pending) mbar_wait(&S->mbar, phase ^ 1u);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -415,7 +427,7 @@ __global__ void __launch_bounds__(128, TC_CTAS) k_m2l_tc(int64_t n_pairs, const 
 template <int PK, int PL>
 cudaError_t launch_inst(int64_t n_pairs, const uint64_t* ptgt, const uint32_t* psrc, const XGeo32* geo,
                         const float* mpole, float* local, int p, uint32_t* leftover, uint32_t* n_leftover,
-                        uint32_t* tile_ctr, int* status, cudaStream_t s)
+                        uint32_t* tile_ctr, int* status, int wait_limit, cudaStream_t s)
 {
     const size_t smem = sizeof(TcSmem<PK>) + 128;
     cudaError_t e;
@@ -432,7 +444,7 @@ cudaError_t launch_inst(int64_t n_pairs, const uint64_t* ptgt, const uint32_t* p
     const int64_t cap = (int64_t)sms * TC_CTAS;
     const int64_t grid = n_tiles < cap ? n_tiles : cap;
     k_m2l_tc<PK, PL><<<(unsigned)grid, 128, smem, s>>>(n_pairs, ptgt, psrc, geo, mpole, local, p, leftover, n_leftover,
-                                                        tile_ctr, status);
+                                                        tile_ctr, status, wait_limit);
     count_launch();
     return cudaGetLastError();
 }
@@ -441,16 +453,17 @@ cudaError_t launch_inst(int64_t n_pairs, const uint64_t* ptgt, const uint32_t* p
 
 cudaError_t launch_m2l_tc(int64_t n_pairs, const uint64_t* ptgt, const uint32_t* psrc, const void* geo,
                           const void* mpole, void* local, int p, uint32_t* leftover, uint32_t* n_leftover,
-                          uint32_t* tile_ctr, int* status, cudaStream_t s)
+                          uint32_t* tile_ctr, int* status, int wait_limit, cudaStream_t s)
 {
     if (n_pairs == 0) return cudaSuccess;
+    if (wait_limit <= 0 || wait_limit > WAIT_LIMIT) wait_limit = WAIT_LIMIT;
     const XGeo32* G = static_cast<const XGeo32*>(geo);
     const float* mp = static_cast<const float*>(mpole);
     float* lc = static_cast<float*>(local);
-    if (p <= 8) return launch_inst<16, 8>(n_pairs, ptgt, psrc, G, mp, lc, p, leftover, n_leftover, tile_ctr, status, s);
-    if (p <= 16) return launch_inst<16, 16>(n_pairs, ptgt, psrc, G, mp, lc, p, leftover, n_leftover, tile_ctr, status, s);
-    if (p <= 24) return launch_inst<32, 24>(n_pairs, ptgt, psrc, G, mp, lc, p, leftover, n_leftover, tile_ctr, status, s);
-    return launch_inst<32, 32>(n_pairs, ptgt, psrc, G, mp, lc, p, leftover, n_leftover, tile_ctr, status, s);
+    if (p <= 8) return launch_inst<16, 8>(n_pairs, ptgt, psrc, G, mp, lc, p, leftover, n_leftover, tile_ctr, status, wait_limit, s);
+    if (p <= 16) return launch_inst<16, 16>(n_pairs, ptgt, psrc, G, mp, lc, p, leftover, n_leftover, tile_ctr, status, wait_limit, s);
+    if (p <= 24) return launch_inst<32, 24>(n_pairs, ptgt, psrc, G, mp, lc, p, leftover, n_leftover, tile_ctr, status, wait_limit, s);
+    return launch_inst<32, 32>(n_pairs, ptgt, psrc, G, mp, lc, p, leftover, n_leftover, tile_ctr, status, wait_limit, s);
 }
 
 }  // namespace sfmm

@@ -21,7 +21,7 @@ SFMM_FP64, SFMM_MIXED, SFMM_MIXED_DF, SFMM_FP32 = 0, 1, 2, 3
 EXPORTS = ["sfmm_default_options", "sfmm_plan", "sfmm_potential", "sfmm_deflection", "sfmm_deflection_host",
            "sfmm_adjoint", "sfmm_shear", "sfmm_deflection_batch",
            "sfmm_destroy", "sfmm_last_error", "sfmm_order", "sfmm_get_stats", "sfmm_set_timing",
-           "sfmm_debug_copy", "sfmm_keys", "sfmm_sort_keys_static", "sfmm_peak_rate"]
+           "sfmm_debug_copy", "sfmm_keys", "sfmm_sort_keys_static", "sfmm_peak_rate", "sfmm_set_wait_limit"]
 STATIC_SORT_MAX_N = 1 << 18
 
 
@@ -29,7 +29,7 @@ class Options(ctypes.Structure):
     _fields_ = [("leaf_size", ctypes.c_int), ("c_s", ctypes.c_double), ("c_t", ctypes.c_double),
                 ("precision", ctypes.c_int), ("zero_mean", ctypes.c_int), ("q_f32", ctypes.c_int),
                 ("n_max", ctypes.c_int64), ("m_max", ctypes.c_int64), ("stream", ctypes.c_void_p),
-                ("m2l_tensor_cores", ctypes.c_int), ("sigma", ctypes.c_double)]
+                ("m2l_tensor_cores", ctypes.c_int), ("sigma", ctypes.c_double), ("wait_limit", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -76,7 +76,7 @@ def load(build_if_missing=True):
     pp = ctypes.POINTER(ctypes.c_void_p)
     L.sfmm_deflection_batch.argtypes = [vp, ci, pp, pp, ctypes.POINTER(i64), pp, ctypes.POINTER(i64), pp, pp, ci]
     L.sfmm_deflection_batch.restype = ci
-    L.sfmm_shear.argtypes = [vp, vp, vp, i64, vp, i64, vp, vp, vp]
+    L.sfmm_shear.argtypes = [vp, vp, vp, i64, vp, i64, vp, vp, vp, vp]
     L.sfmm_shear.restype = ci
     L.sfmm_destroy.argtypes = [vp]
     L.sfmm_destroy.restype = None
@@ -94,18 +94,12 @@ def load(build_if_missing=True):
     L.sfmm_keys.restype = ci
     L.sfmm_sort_keys_static.argtypes = [vp, i64, vp, vp, vp]
     L.sfmm_sort_keys_static.restype = ci
+    L.sfmm_set_wait_limit.argtypes = [vp, ci]
+    L.sfmm_set_wait_limit.restype = ci
     L.sfmm_peak_rate.argtypes = [ci, ctypes.POINTER(ctypes.c_double), vp]
     L.sfmm_peak_rate.restype = ci
     _lib = L
     return L
-
-
-def magnification(gamma, trace):
-    """mu = 1/((1 - tr H/2)^2 - |gamma|^2) (Sec. 2.2).  For point masses
-    tr H = kappa - kappa_bar = -sum(q)/(4 pi) at any target that is not on a
-    mass (at a target on a mass, whose own term is skipped, leave that mass
-    out of the sum); `trace` is a scalar or one value per target."""
-    return 1.0 / ((1.0 - 0.5 * np.asarray(trace)) ** 2 - (gamma ** 2).sum(-1))
 
 
 def _check(st, plan=None):
@@ -133,7 +127,8 @@ class Plan:
     """An sFMM plan (sfmm_plan): tree depth, order p (or a tolerance) and options."""
 
     def __init__(self, max_depth=29, p=0, tol=1e-10, leaf_size=32, c_s=2.0, c_t=0.5, precision=SFMM_FP64,
-                 zero_mean=False, q_f32=False, n_max=0, m_max=0, stream=None, m2l_tensor_cores=True, sigma=0.0):
+                 zero_mean=False, q_f32=False, n_max=0, m_max=0, stream=None, m2l_tensor_cores=True, sigma=0.0,
+                 wait_limit=0):
         L = load()
         o = Options()
         L.sfmm_default_options(ctypes.byref(o))
@@ -142,6 +137,7 @@ class Plan:
         o.n_max, o.m_max = n_max, m_max
         o.m2l_tensor_cores = int(bool(m2l_tensor_cores))
         o.sigma = float(sigma)
+        o.wait_limit = int(wait_limit)
         if stream is None:
             try:
                 import torch
@@ -170,6 +166,10 @@ class Plan:
     @property
     def order(self):
         return load().sfmm_order(self._h)
+
+    def set_wait_limit(self, polls=0):
+        """Polls after which the bounded device waits give up (0 = default; a test hook)."""
+        _check(load().sfmm_set_wait_limit(self._h, int(polls)), self._h)
 
     def set_timing(self, on=True):
         """0/False off, 1/True per-phase device times, 2 also the near-field pair count."""
@@ -239,19 +239,22 @@ class Plan:
         _check(st, self._h)
         return outs
 
-    def shear(self, src, q, tgt, with_psi=False, with_alpha=False):
-        """(gamma [M, 2], psi or None, alpha or None) at the targets (FP64 path; see sfmm_shear)."""
+    def shear(self, src, q, tgt, with_psi=False, with_alpha=False, with_mu=False):
+        """(gamma [M, 2], psi or None, alpha or None, mu or None) at the targets:
+        the shear, the potential, the deflection and the magnification
+        mu = 1/((1 - tr H/2)^2 - |gamma|^2) (FP64 path; see sfmm_shear)."""
         import torch
         M = tgt.shape[0]
         gamma = torch.empty((M, 2), dtype=torch.float64, device=tgt.device)
         psi = torch.empty(M, dtype=torch.float64, device=tgt.device) if with_psi else None
         alpha = torch.empty((M, 2), dtype=torch.float64, device=tgt.device) if with_alpha else None
+        mu = torch.empty(M, dtype=torch.float64, device=tgt.device) if with_mu else None
         st = load().sfmm_shear(self._h, _dptr(src, torch.float64, 3, "src"), _dptr(q, self._qdtype(), None, "q"),
                                src.shape[0], _dptr(tgt, torch.float64, 3, "tgt"), M,
                                _dptr(psi, torch.float64, None, "psi"), _dptr(alpha, torch.float64, 2, "alpha"),
-                               _dptr(gamma, torch.float64, 2, "gamma"))
+                               _dptr(gamma, torch.float64, 2, "gamma"), _dptr(mu, torch.float64, None, "mu"))
         _check(st, self._h)
-        return gamma, psi, alpha
+        return gamma, psi, alpha, mu
 
     def adjoint(self, src, q, tgt, g_psi=None, g_alpha=None, want_q=True, want_src=True):
         """(dL/dq [N] or None, dL/dy [N, 3] or None) for a loss of this plan's

@@ -150,3 +150,26 @@ def test_fp32_host_entry_point_matches_device_and_survives_empty_calls():
         hpsi, halpha = plan.deflection_host(src, q, tgt)
         np.testing.assert_array_equal(hpsi, psi)
         np.testing.assert_array_equal(halpha, alpha)
+
+
+def test_tensor_core_wait_time_out_is_reported_and_the_plan_recovers():
+    """The tensor-core M2L's mbarrier waits are bounded.  With a limit of one
+    non-blocking poll they run out: the solve returns SFMM_ETIMEOUT (the kernel
+    drains its MMAs with the full bound and frees its tensor memory, so the
+    context stays usable), and the same plan with the default bound then solves
+    correctly."""
+    rng = np.random.default_rng(77)
+    src = workloads.clustered(rng, 40000, 25)
+    tgt = unit(rng.normal(size=(5000, 3)))
+    q = rng.lognormal(0, 0.5, 40000)
+    plan = sfmm.Plan(p=20, leaf_size=32, precision=sfmm.SFMM_FP32)
+    plan.set_wait_limit(1)
+    for _ in range(2):
+        with pytest.raises(sfmm.SfmmError, match=f"status {sfmm.SFMM_ETIMEOUT}:"):
+            plan.deflection(dev(src), dev(q), dev(tgt))
+    plan.set_wait_limit(0)
+    psi, alpha = plan.deflection(dev(src), dev(q), dev(tgt))
+    torch.cuda.synchronize()
+    ref = direct_sum(src, q, tgt[:1000])
+    assert rel(psi.cpu().numpy()[:1000], ref["psi"]) < TOL_FP32
+    assert rel(alpha.cpu().numpy()[:1000], ref["alpha"]) < TOL_FP32

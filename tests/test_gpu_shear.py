@@ -26,29 +26,29 @@ def dev(a, dtype=torch.float64):
     return torch.as_tensor(np.ascontiguousarray(a), dtype=dtype, device="cuda")
 
 
-def shear(src, q, tgt, p=32, leaf=32, **kw):
+def shear(src, q, tgt, p=32, leaf=32, with_mu=False, **kw):
     plan = sfmm.Plan(p=p, leaf_size=leaf, **kw)
-    g, psi, alpha = plan.shear(dev(src), dev(q), dev(tgt), with_psi=True, with_alpha=True)
+    g, psi, alpha, mu = plan.shear(dev(src), dev(q), dev(tgt), with_psi=True, with_alpha=True, with_mu=with_mu)
     torch.cuda.synchronize()
-    return g.cpu().numpy(), psi.cpu().numpy(), alpha.cpu().numpy()
+    out = (g.cpu().numpy(), psi.cpu().numpy(), alpha.cpu().numpy())
+    return out + (mu.cpu().numpy(),) if with_mu else out
 
 
 def test_shear_random_sky_and_outputs_unchanged():
     d = workloads.random_sky(4096)
-    g, psi, alpha = shear(d["src"], d["q"], d["tgt"])
+    g, psi, alpha, mu = shear(d["src"], d["q"], d["tgt"], with_mu=True)
     ref = lensing(d["src"], d["q"], d["tgt"])
     assert rel(g, ref["gamma"]) < TOL, rel(g, ref["gamma"])
     r = direct_sum(d["src"], d["q"], d["tgt"])
     assert rel(psi, r["psi"]) < TOL and rel(alpha, r["alpha"]) < TOL
-    # targets on the masses: each skips its own mass in the trace
-    mu = sfmm.magnification(g, -(d["q"].sum() - d["q"]) / (4 * np.pi))
+    # targets on the masses: each skips its own mass, in the trace as everywhere (the library's mu)
     assert rel(mu, ref["mu"]) < TOL
     # targets off the masses: tr H = -sum q / 4pi
     tgt = unit(np.random.default_rng(20).normal(size=(3000, 3)))
-    g2, _, _ = shear(d["src"], d["q"], tgt)
+    g2, _, _, mu2 = shear(d["src"], d["q"], tgt, with_mu=True)
     ref2 = lensing(d["src"], d["q"], tgt)
     assert rel(g2, ref2["gamma"]) < TOL
-    assert rel(sfmm.magnification(g2, -d["q"].sum() / (4 * np.pi)), ref2["mu"]) < TOL
+    assert rel(mu2, ref2["mu"]) < TOL
 
 
 def test_shear_clustered_small_leaves_and_poles():
@@ -77,3 +77,11 @@ def test_shear_far_field_only_and_near_field_only():
     near = unit(np.array([[0.3, -0.2, 0.93]]) + 1e-3 * rng.normal(size=(200, 3)))
     g, _, _ = shear(src, q, near, leaf=64)
     assert rel(g, lensing(src, q, near)["gamma"]) < TOL
+
+
+def test_no_mass_gives_unit_magnification():
+    tgt = unit(np.random.default_rng(23).normal(size=(100, 3)))
+    plan = sfmm.Plan(p=16)
+    g, _, _, mu = plan.shear(dev(np.zeros((0, 3))), dev(np.zeros(0)), dev(tgt), with_mu=True)
+    torch.cuda.synchronize()
+    assert np.all(g.cpu().numpy() == 0) and np.all(mu.cpu().numpy() == 1.0)
