@@ -300,41 +300,54 @@ def run_npm(args, dev, clock_sampler):
             "clocks": clk.summary()}
 
 
-def run_shells(args, dev, clock_sampler):
-    """Batched shells: every shell solved per step, with 4 concurrent lanes and
-    with 1 (sequential), for the 1e-6 and 1e-10 paths; error of one shell vs the
-    oracle on a target sample."""
+def run_shells(args, dev, clock_sampler, ws=1, rank=0):
+    """Batched shells: the 64-shell set split over the ranks by the longest-first
+    rule (shard.assign_shells; every rank builds and solves only its shells),
+    each rank's shells solved per step with 4 concurrent lanes and with 1, for
+    the 1e-6 and 1e-10 paths; the whole job's targets over the slowest rank's
+    time; error of rank 0's largest shell vs the oracle on a target sample."""
     import torch
-    from paper_2210_07021_gb300 import sfmm, workloads
-    d = workloads.shell_set()
-    tgt = torch.as_tensor(d["tgt"], device=dev)
-    sh = [(torch.as_tensor(s, device=dev), torch.as_tensor(q, device=dev), tgt) for s, q in d["shells"]]
-    M = tgt.shape[0]
-    out = {"workload": d["workload"], "n_shells": len(sh), "sum_N": int(d["sizes"].sum()), "M_per_shell": M}
+    from paper_2210_07021_gb300 import sfmm, shard, workloads
+    sizes = workloads.shell_sizes()
+    tgt_h = workloads.healpix_ring_centres(256)
+    M = tgt_h.shape[0]
+    mine = shard.assign_shells([shard.shell_cost(n, M) for n in sizes], ws)[rank]
+    tgt = torch.as_tensor(tgt_h, device=dev)
+    host = {k: workloads.shell(k, sizes[k]) for k in mine}
+    sh = [(torch.as_tensor(host[k][0], device=dev), torch.as_tensor(host[k][1], device=dev), tgt) for k in mine]
+    out = {"workload": f"{len(sizes)} shells, N_k log-uniform in [1e4, 1e7] (sum {int(sizes.sum())}), clustered "
+                       f"(N_k/500 clumps), M = {M} N_side=256 pixel centres each",
+           "n_shells": len(sizes), "sum_N": int(sizes.sum()), "M_per_shell": M, "ranks": ws,
+           "shells_per_rank_0": len(mine), "split": "longest-first greedy on N_k + M (shard.assign_shells)"}
     from oracle.direct import direct_sum
-    big = int(np.argmax(d["sizes"]))
+    big = mine[int(np.argmax([sizes[k] for k in mine]))] if mine else None
     idx = workloads.subsample(M, min(args.check, 100), 8, stream=9)
     for name, prec, kw in (("mixed", sfmm.SFMM_MIXED, dict(p=20, leaf_size=64, c_s=1.5, c_t=0.5)),
-                           ("mixed_df", sfmm.SFMM_MIXED_DF, dict(p=28, leaf_size=64, c_t=0.45))):
+                           ("mixed_df", sfmm.SFMM_MIXED_DF, dict(p=32, leaf_size=64, c_s=1.5, c_t=0.45))):
         plan = sfmm.Plan(precision=prec, **kw)
         for lanes in (4, 1):
-            outs = plan.deflection_batch(sh, with_psi=False, lanes=lanes)
+            outs = plan.deflection_batch(sh, with_psi=False, lanes=lanes) if sh else []
             torch.cuda.synchronize()
+            if ws > 1:
+                import torch.distributed as dist
+                dist.barrier()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             with clock_sampler as clk:
                 e0.record(torch.cuda.current_stream())
                 for _ in range(args.steps):
-                    outs = plan.deflection_batch(sh, with_psi=False, lanes=lanes)
+                    outs = plan.deflection_batch(sh, with_psi=False, lanes=lanes) if sh else []
                 e1.record(torch.cuda.current_stream())
                 torch.cuda.synchronize()
-            ms = e0.elapsed_time(e1) / args.steps
-            out[f"{name}_lanes{lanes}"] = {"ms_per_step": ms, "value": len(sh) * M * 1e-3 / ms,
-                                           "unit": "Mpts/s (targets of all shells per step)", "clocks": clk.summary()}
-        ref = direct_sum(d["shells"][big][0], d["shells"][big][1], d["tgt"][idx])
-        err = rel(outs[big][1].cpu().numpy()[idx], ref["alpha"])
-        stated = 1e-6 if prec == sfmm.SFMM_MIXED else 1e-10
-        out[f"{name}_error_vs_oracle"] = {"alpha_rel": err, "shell": big, "sample": int(idx.size), "stated": stated,
-                                          "within_stated": bool(err < stated)}
+            ms = shard.max_over_ranks(e0.elapsed_time(e1) / args.steps, device=dev)
+            out[f"{name}_lanes{lanes}"] = {"ms_per_step": ms, "value": len(sizes) * M * 1e-3 / ms,
+                                           "unit": "Mpts/s (targets of all shells per step, whole job)",
+                                           "clocks": clk.summary()}
+        if rank == 0 and big is not None:
+            ref = direct_sum(host[big][0], host[big][1], tgt_h[idx])
+            err = rel(outs[mine.index(big)][1].cpu().numpy()[idx], ref["alpha"])
+            stated = 1e-6 if prec == sfmm.SFMM_MIXED else 1e-10
+            out[f"{name}_error_vs_oracle"] = {"alpha_rel": err, "shell": int(big), "sample": int(idx.size),
+                                              "stated": stated, "within_stated": bool(err < stated)}
         plan.close()
     return out
 
@@ -493,6 +506,7 @@ def run_sfmm(args):
         results[name] = r
         plan.close()
     del ref_psi, ref_alpha
+    shl = run_shells(args, dev, ClockSampler(local), ws, rank) if args.shells else None
     if rank != 0:
         if dist:
             dist.barrier()
@@ -518,12 +532,11 @@ def run_sfmm(args):
         ev["targets"] = f"{n_near} near clumps + {idx.size - n_near} in empty sky (norm-wise relative errors)"
         results[name]["error_vs_oracle"] = ev
     head = results[wanted[0][0]]
-    adj = shr = npm = shl = None
+    adj = shr = npm = None
     if ws == 1 and not args.no_adjoint:
         adj = run_adjoint(args, dev, ClockSampler(local))
         shr = run_shear(args, dev, ClockSampler(local))
         npm = run_npm(args, dev, ClockSampler(local))
-    shl = run_shells(args, dev, ClockSampler(local)) if (ws == 1 and args.shells) else None
 
     def roofline_of(r):
         fp64 = r["precision"] == "fp64"
