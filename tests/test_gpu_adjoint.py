@@ -117,3 +117,92 @@ def test_autograd_loss_matches_oracle_gradient():
         tt = dev(tgt).requires_grad_(True)
         psi, alpha = sfa.deflection(dev(src), dev(q), tt, plan)
         alpha.sum().backward()
+
+
+def test_gradient_workload_matches_central_differences():
+    """The gradient workload (N = 1e6 clustered sources, the 786,432 N_side = 256
+    pixel centres, L = sum_i w_i |alpha_i - alpha_ref,i|^2), gradient through
+    autograd.deflection (forward on the 1e-10 path, backward the adjoint sFMM),
+    on 64 seeded particles:
+
+    * dL/dq_j against central differences with h = 1e-6 of the same forward: L
+      is quadratic in q, so the difference is exact but for rounding (1e-9);
+    * dL/dy_j (the covariant gradient) against the oracle's analytic adjoint
+      evaluated at these particles (1e-10);
+    * dL/dy_j against central differences of the forward along e_theta and
+      e_phi (steps of h = 1e-6 and 2h, renormalised; Richardson combination).
+      Moving one source changes the rounding of every sum above it (its leaf's
+      multipole, their parents', the locals): the forward's L moves by about
+      eps L whatever the step, so a difference resolves a derivative only to
+      about eps L / h.  The particles are taken where the step keeps their
+      cell at the tree's deepest level (same tree and lists on both sides) and
+      at least 1.2e-3 rad from every target (the O((h/d)^4) error of the
+      Richardson combination below 1e-12); the check is that each difference
+      agrees with the analytic gradient within 16 eps L / h."""
+    from oracle.healpix import key29
+    d = workloads.loss_sky()
+    N, M = d["src"].shape[0], d["tgt"].shape[0]
+    plan = sfmm.Plan(p=32, leaf_size=64, c_s=2.0, c_t=0.45, precision=sfmm.SFMM_MIXED_DF)
+    src = dev(d["src"]).requires_grad_(True)
+    q = dev(d["q"]).requires_grad_(True)
+    tgt, w = dev(d["tgt"]), dev(d["w"])
+    with torch.no_grad():
+        _, a0 = plan.deflection(src, q, tgt)
+        a_ref = float(torch.sqrt((a0 ** 2).mean())) * dev(d["xi"])
+
+    def alpha_of(s_, q_):
+        return plan.deflection(s_, q_, tgt, with_psi=False)[1]
+
+    def central(ap, am, step):
+        # (L(+) - L(-)) / (2 step), summed as w (a+ - a-) . (a+ + a- - 2 a_ref): the same difference
+        # without cancelling two losses of ~3 M |alpha|^2
+        return float((w[:, None] * (ap - am) * (ap + am - 2.0 * a_ref)).sum()) / (2 * step)
+
+    _, alpha = sfa.deflection(src, q, tgt, plan)
+    loss = (w[:, None] * (alpha - a_ref) ** 2).sum()
+    loss.backward()
+    L = float(loss)
+    gq, gs = q.grad.cpu().numpy(), src.grad.cpu().numpy()
+    g_alpha = (2.0 * w[:, None] * (alpha.detach() - a_ref)).cpu().numpy()
+    depth = plan.stats()["depth"]
+    h = 1e-6
+    y = d["src"]
+    rng = np.random.default_rng(55)
+    cand = rng.permutation(N)[:400]
+    rho = np.sqrt(y[cand, 0] ** 2 + y[cand, 1] ** 2)
+    et = np.stack([y[cand, 2] * y[cand, 0] / rho, y[cand, 2] * y[cand, 1] / rho, -rho], 1)
+    ep = np.stack([-y[cand, 1] / rho, y[cand, 0] / rho, np.zeros_like(rho)], 1)
+    shift = np.uint64(2 * (29 - depth))
+    k0 = key29(y[cand]) >> shift
+    same = np.ones(cand.size, dtype=bool)
+    for t in (et, ep):
+        for sg in (2.0, 1.0, -1.0, -2.0):
+            same &= (key29(unit(y[cand] + sg * h * t)) >> shift) == k0
+    far = np.array([(d["tgt"] @ y[c]).max() for c in cand]) < np.cos(1.2e-3)
+    sel = np.nonzero(same & far)[0][:64]
+    assert sel.size == 64
+    js = cand[sel]
+    # the position gradient against the oracle's analytic adjoint at these particles
+    _, rs = oracle_adjoint(y[js], d["q"][js], d["tgt"], g_alpha, None)
+    assert rel(gs[js], rs) < 1e-10, rel(gs[js], rs)
+    fd_q, fd_y, ad_y = [], [], []
+    with torch.no_grad():
+        for i in sel:
+            j = int(cand[i])
+            qp, qm = q.detach().clone(), q.detach().clone()
+            qp[j] += h
+            qm[j] -= h
+            fd_q.append(central(alpha_of(src, qp), alpha_of(src, qm), h))
+            for t in (et[i], ep[i]):
+                dd = []
+                for hh in (h, 2 * h):
+                    sp, sm = src.detach().clone(), src.detach().clone()
+                    sp[j] = dev(unit(y[j] + hh * t))
+                    sm[j] = dev(unit(y[j] - hh * t))
+                    dd.append(central(alpha_of(sp, q), alpha_of(sm, q), hh))
+                fd_y.append((4 * dd[0] - dd[1]) / 3)
+                ad_y.append(float(gs[j] @ t))
+    assert rel(gq[js], np.array(fd_q)) < 1e-9, rel(gq[js], np.array(fd_q))
+    bound = 16 * np.finfo(float).eps * L / h
+    dev_y = np.abs(np.array(fd_y) - np.array(ad_y))
+    assert dev_y.max() < bound, (dev_y.max(), bound, L)
