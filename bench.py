@@ -77,6 +77,9 @@ def parse():
                     help="also time the batched-shell workload (64 shells, 9.3e7 sources; slow to generate)")
     ap.add_argument("--no-adjoint", action="store_true",
                     help="skip the gradient, shear and Near Particle Model measurements")
+    ap.add_argument("--solve-only", action="store_true",
+                    help="time the chosen paths only (no reference solve, oracle, e2e or extra legs): "
+                         "the driver of the ncu captures under profiles/")
     return ap.parse_args()
 
 
@@ -400,6 +403,36 @@ def errors(psi, alpha, ref_psi, ref_alpha):
     return {"psi_rel": e_psi, "alpha_rel": e_al, "alpha_max_rel": e_max}
 
 
+def run_solve_only(args):
+    """W untimed and K timed solves of each chosen path on the benchmark sky (or
+    --n), printing one JSON line of times and solver statistics."""
+    import torch
+    from paper_2210_07021_gb300 import sfmm, workloads
+    torch.cuda.set_device(0)
+    d = workloads.clustered_pair(n=args.n, n_clumps=args.clumps)
+    N, M = d["src"].shape[0], d["tgt"].shape[0]
+    src, q, tgt = (torch.as_tensor(d[k], device="cuda") for k in ("src", "q", "tgt"))
+    out = {"workload": d["workload"], "steps": args.steps, "warmup": args.warmup, "paths": {}}
+    for name, prec, p, stated, leaf, c_s, c_t in [m for m in MODES if m[0] in args.modes.split(",")]:
+        plan = sfmm.Plan(p=p, leaf_size=args.leaf or leaf, c_s=c_s, c_t=c_t, precision=prec, q_f32=True,
+                         n_max=N, m_max=M)
+        for _ in range(args.warmup):
+            plan.deflection(src, q, tgt)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            plan.deflection(src, q, tgt)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / max(args.steps, 1)
+        plan.set_timing(2)                    # one more solve: phase times and the near-field pair count
+        plan.deflection(src, q, tgt)
+        out["paths"][name] = {"ms_per_step": ms, "stats": plan.stats()}
+        plan.close()
+    print(json.dumps(out), flush=True)
+
+
 def run_sfmm(args):
     import torch
     from paper_2210_07021_gb300 import sfmm, workloads
@@ -590,6 +623,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.solve_only:
+        run_solve_only(args)
     else:
         run_sfmm(args)
 
