@@ -153,6 +153,48 @@ sfmm_status sfmm_deflection_batch(sfmm_plan_t plan, int n_shells, const double* 
                                   const int64_t* M, double* const* psi, double* const* alpha, int lanes);
 
 /*
+ * Graph-launched shells (the N_L lensing planes of Sec. 2.1, as for
+ * sfmm_deflection_batch, replayed as one CUDA graph).
+ *
+ * sfmm_graph_capture binds the plan to a batch of shells: the same arrays as
+ * sfmm_deflection_batch (device pointers in host arrays of n_shells entries;
+ * psi may be NULL).  It solves every shell once, synchronously (the results
+ * are valid on return), plans each shell's capacities (nodes, level width,
+ * levels, M2L and P2P pairs) as its counts times (1 + slack) plus a margin
+ * (slack in [0, 16]; 0 selects 0.25), and records the solves of all shells,
+ * with no host synchronisation inside, into one CUDA graph: each shell on its
+ * own stream and workspace, its tree, lists and launches sized by its
+ * capacities and its counts read on the device.  The sizes N[i], M[i] and the
+ * buffers are fixed by the capture; their CONTENTS may change between
+ * launches (new positions and masses).  The caller keeps the buffers alive
+ * until sfmm_graph_release or sfmm_destroy.  Plans of precision SFMM_MIXED or
+ * SFMM_MIXED_DF only (SFMM_EINVAL otherwise).  A previous capture is released.
+ *
+ * sfmm_graph_launch replays the graph on the plan's stream and waits for it
+ * (one synchronisation for all shells).  A shell whose new data outgrew a
+ * capacity (a deeper or wider tree, more pairs) is detected on the device; it
+ * is solved again synchronously, so the results are valid on return, and the
+ * graph is recorded again with capacities planned from the new data.
+ *
+ * sfmm_graph_info reports the graph (zeros when there is none): kernel nodes
+ * per replay, replays, overflowed shells, re-recordings and the summed counts
+ * of the last replay.  sfmm_graph_release frees the graph and its workspaces.
+ */
+typedef struct {
+    int64_t n_shells;
+    int64_t kernel_nodes;   /* kernels launched by one replay */
+    int64_t launches, overflows, recaptures;
+    int64_t n_nodes, n_leaves, n_m2l, n_p2p;   /* summed over the shells, last replay */
+} sfmm_graph_stats;
+
+sfmm_status sfmm_graph_capture(sfmm_plan_t plan, int n_shells, const double* const* src_xyz, const void* const* q,
+                               const int64_t* N, const double* const* tgt_xyz, const int64_t* M, double* const* psi,
+                               double* const* alpha, double slack);
+sfmm_status sfmm_graph_launch(sfmm_plan_t plan);
+sfmm_status sfmm_graph_info(sfmm_plan_t plan, sfmm_graph_stats* out);
+sfmm_status sfmm_graph_release(sfmm_plan_t plan);
+
+/*
  * Shear and magnification (Sec. 2.2, Eq. GAM_DEF): gamma [M][2] = (gamma_1,
  * gamma_2), the trace-free part of the covariant Hessian H of psi on
  * (e_theta, e_phi) at each target, gamma_1 = (H11 - H22)/2, gamma_2 = H12, and

@@ -19,7 +19,7 @@ namespace sfmm {
 cudaError_t build_tree(sfmm_plan_s* P, const uint64_t* keys, int64_t n, int m, int max_depth);
 cudaError_t tree_geometry(sfmm_plan_s* P);
 cudaError_t tree_target_ranges(sfmm_plan_s* P, const uint64_t* tkeys, int64_t M);
-cudaError_t collect_leaves(sfmm_plan_s* P, const int* cnt, Buf& out, int64_t* n_out);
+cudaError_t collect_leaves(sfmm_plan_s* P, const int* cnt, Buf& out, int64_t* n_out, int64_t* d_out);
 cudaError_t build_lists(sfmm_plan_s* P, const TreeView& T, double c_s, double c_t, cudaStream_t s);
 void fill_tables(double* h);
 size_t xgeo_bytes(int ek);
@@ -27,8 +27,8 @@ cudaError_t launch_geom32(int n_nodes, const double* geom, float* g32, cudaStrea
 cudaError_t launch_pair_geo(const TreeView& T, const float* g32, const uint64_t* tt, const uint32_t* ss, int64_t n,
                             void* out, int ek, cudaStream_t s);
 cudaError_t launch_child_geo(const TreeView& T, const float* g32, void* m2m, void* l2l, int ek, cudaStream_t s);
-cudaError_t launch_src_offsets(const TreeView& T, const int* leaves, int64_t n_leaves, const double4_32a* src,
-                               float4* off, cudaStream_t s);
+cudaError_t launch_src_offsets(const TreeView& T, const int* leaves, int64_t n_leaves, const int64_t* d_nl,
+                               const double4_32a* src, float4* off, cudaStream_t s);
 cudaError_t launch_p2m(const TreeView& T, const int* leaves, int64_t n_leaves, const double4_32a* src,
                        const float4* off, const float4* log_tab, void* mpole, int p, int ek, cudaStream_t s);
 cudaError_t launch_m2m(const TreeView& T, int a, int b, int p, const double* tables, const void* geo, void* mpole,
@@ -44,29 +44,30 @@ cudaError_t launch_m2l_tc(int64_t n_pairs, const uint64_t* ptgt, const uint32_t*
 cudaError_t launch_l2l(const TreeView& T, int a, int b, int p, const double* tables, const void* geo, void* local,
                        int ek, cudaStream_t s);
 size_t frame_df_bytes();
-cudaError_t launch_frame_df(int n_nodes, const double* geom, void* out, cudaStream_t s);
+cudaError_t launch_frame_df(int n_nodes, const int64_t* d_nn, const double* geom, void* out, cudaStream_t s);
 cudaError_t launch_pair_geo_rho(const TreeView& T, const void* frames, const float4* log_tab, const uint64_t* tt,
-                                const uint32_t* ss, int64_t n, void* out, cudaStream_t s);
+                                const uint32_t* ss, int64_t n, const int64_t* d_n, void* out, cudaStream_t s);
 cudaError_t launch_child_geo_df(const TreeView& T, const void* frames, const float4* log_tab, void* m2m, void* l2l,
                                 cudaStream_t s);
-cudaError_t launch_m2l_pair(int64_t n_pairs, const uint64_t* ptgt, const uint32_t* psrc, const void* geo,
+cudaError_t launch_m2l_pair(int64_t n_pairs, const int64_t* d_n, const uint64_t* ptgt, const uint32_t* psrc, const void* geo,
                             const void* mpole, int p, double* acc, uint32_t* leftover, uint32_t* n_left,
                             cudaStream_t s);
 cudaError_t launch_m2l_left_df(const TreeView& T, const uint64_t* ptgt, const uint32_t* psrc, const uint32_t* list,
                                const uint32_t* n_list, int64_t max_list, int p, const double* tables,
                                const void* mpole, double* acc, cudaStream_t s);
 cudaError_t launch_acc_to_df(int64_t n, const double* acc, void* out, cudaStream_t s);
-cudaError_t launch_m2m_df(const TreeView& T, int c0, int c1, int p, const void* geo, void* mpole, cudaStream_t s);
-cudaError_t launch_l2l_df(const TreeView& T, int a, int b, int p, const void* geo, const double* acc, void* local,
+cudaError_t launch_m2m_df(const TreeView& T, int c0, int c1, int lvl, int p, const void* geo, void* mpole,
                           cudaStream_t s);
-cudaError_t launch_p2m_df_leaf(const TreeView& T, const int* leaves, int64_t n_leaves, const float4* off,
+cudaError_t launch_l2l_df(const TreeView& T, int a, int b, int lvl, int p, const void* geo, const double* acc,
+                          void* local, cudaStream_t s);
+cudaError_t launch_p2m_df_leaf(const TreeView& T, const int* leaves, int64_t n_leaves, const int64_t* d_nl, const float4* off,
                                const float4* log_tab, int p, void* mpole, cudaStream_t s);
 cudaError_t launch_unscale(int n_nodes, const double* geom, const void* in, double* out, int p, int is_local,
                            int ek, cudaStream_t s);
-cudaError_t launch_eval32_prep(const TreeView& T, const int* leaves, int64_t n_leaves, const double4_32a* tgt,
-                               float4* toff, const uint64_t* p2p_t, const uint32_t* p2p_s, int64_t n_p2p, float4* dc,
-                               cudaStream_t s);
-cudaError_t launch_eval32(const TreeView& T, const int* leaves, int64_t n_leaves, const float4* soff,
+cudaError_t launch_eval32_prep(const TreeView& T, const int* leaves, int64_t n_leaves, const int64_t* d_nl,
+                               const double4_32a* tgt, float4* toff, const uint64_t* p2p_t, const uint32_t* p2p_s,
+                               int64_t n_p2p, const int64_t* d_np, float4* dc, cudaStream_t s);
+cudaError_t launch_eval32(const TreeView& T, const int* leaves, int64_t n_leaves, const int64_t* d_nl, const float4* soff,
                           const float4* toff, const float4* dc, const double4_32a* tgt, const uint32_t* tperm, const int64_t* p2p_off,
                           const uint32_t* p2p_src, const void* local, const void* mpole, bool dfar, int p, int zero_mean,
                           double* psi, double* alpha, bool coincide, unsigned long long* leaf_ctr,
@@ -74,7 +75,7 @@ cudaError_t launch_eval32(const TreeView& T, const int* leaves, int64_t n_leaves
 cudaError_t launch_count_pairs(const TreeView& T, const int* leaves, int64_t n_leaves, const int64_t* p2p_off,
                                const uint32_t* p2p_src, unsigned long long* out, cudaStream_t s);
 void fill_log_table(float* out);
-cudaError_t launch_eval_df(const TreeView& T, const int* leaves, int64_t n_leaves, const float4* soff,
+cudaError_t launch_eval_df(const TreeView& T, const int* leaves, int64_t n_leaves, const int64_t* d_nl, const float4* soff,
                            const float4* toff, const float4* dc, const double4_32a* tgt, const uint32_t* tperm,
                            const int64_t* p2p_off, const uint32_t* p2p_src, const void* local, const void* mpole,
                            const float4* log_tab, int p, int zero_mean, double* psi, double* alpha,
@@ -86,7 +87,8 @@ cudaError_t launch_eval_adj(const TreeView& T, const int* leaves, int64_t n_leav
                             const int64_t* p2p_off, const uint32_t* p2p_src, const double* local, const double* mpole,
                             int p, int zero_mean, const void* w, int w_f32, double* phi, double* grad3,
                             unsigned long long* leaf_ctr, cudaStream_t s);
-cudaError_t launch_eval(const TreeView& T, const int* leaves, int64_t n_leaves, const double4_32a* src, const double4_32a* tgt,
+cudaError_t launch_eval(const TreeView& T, const int* leaves, int64_t n_leaves, const int64_t* d_nl, const double4_32a* src,
+                        const double4_32a* tgt,
                         const uint32_t* tperm, const int64_t* p2p_off, const uint32_t* p2p_src, const double* local,
                         const double* mpole, int p, int zero_mean, double sigma, double* psi, double* alpha,
                         double* gamma, double* mu, unsigned long long* leaf_ctr, cudaStream_t s);
@@ -228,6 +230,9 @@ TreeView view(sfmm_plan_s* P)
 {
     TreeView T;
     T.n_nodes = (int)P->n_nodes;
+    DevCounts* dc = P->gm ? P->dcnt.as<DevCounts>() : nullptr;
+    T.d_nn = dc ? &dc->nn : nullptr;
+    T.d_level = dc ? dc->level : nullptr;
     T.prefix = P->n_prefix.as<uint64_t>();
     T.level = P->n_level.as<int>();
     T.first = P->n_first.as<int>();
@@ -288,6 +293,8 @@ sfmm_status solve(sfmm_plan_s* P, const double* src, const void* q, int64_t N, c
 {
     cudaStream_t s = P->stream;
     const int precision = (adj || gamma) ? SFMM_FP64 : P->opt.precision;   // adjoint and shear run in FP64
+    if (P->gm && !(precision == SFMM_MIXED || precision == SFMM_MIXED_DF))
+        return fail(P, SFMM_EINVAL, "graph mode runs the double-float far field only (SFMM_MIXED, SFMM_MIXED_DF)");
     const int q_f32 = adj ? 0 : P->opt.q_f32;
     cudaError_t e;
     const int p = P->p;
@@ -307,10 +314,13 @@ sfmm_status solve(sfmm_plan_s* P, const double* src, const void* q, int64_t N, c
             k_fill<<<grid_for(M), 256, 0, s>>>(mu, M, 1.0); count_launch();
             if ((e = cudaGetLastError())) return cuda_fail(P, e, "mu");
         }
-        if ((e = cudaStreamSynchronize(s))) return cuda_fail(P, e, "sync");
+        if (!P->gm && (e = cudaStreamSynchronize(s))) return cuda_fail(P, e, "sync");
         return SFMM_OK;
     }
     if (M == 0) return SFMM_OK;
+    // graph mode: the counts live in the plan's DevCounts (see build_tree); launches
+    // over leaves and pairs are sized by capacities and read the counts there
+    DevCounts* dcnt = P->gm ? P->dcnt.as<DevCounts>() : nullptr;
     PhaseTimer tm(P);
     tm.mark();
     // ---- keys and sort (sources and targets)
@@ -358,13 +368,17 @@ sfmm_status solve(sfmm_plan_s* P, const double* src, const void* q, int64_t N, c
     const int64_t nn = P->n_nodes;
     if ((e = tree_geometry(P))) return cuda_fail(P, e, "geometry");
     TreeView T = view(P);
-    if ((e = collect_leaves(P, T.count, P->leaves_src, &P->n_leaves))) return cuda_fail(P, e, "leaves");
+    if ((e = collect_leaves(P, T.count, P->leaves_src, &P->n_leaves, dcnt ? &dcnt->n_leaves : nullptr)))
+        return cuda_fail(P, e, "leaves");
+    const int64_t* d_nls = dcnt ? &dcnt->n_leaves : nullptr;
+    const int64_t* d_nlt = dcnt ? &dcnt->n_leaves_tgt : nullptr;
     tm.mark();
     // ---- join the targets; target ranges (Sec. 3.7 lookup) and target leaves
     if ((e = cudaStreamWaitEvent(s, P->ev_join, 0))) return cuda_fail(P, e, "join");
     if ((e = tree_target_ranges(P, tkeys, M))) return cuda_fail(P, e, "target ranges");
     T = view(P);
-    if ((e = collect_leaves(P, T.tcount, P->leaves_tgt, &P->n_leaves_tgt))) return cuda_fail(P, e, "target leaves");
+    if ((e = collect_leaves(P, T.tcount, P->leaves_tgt, &P->n_leaves_tgt, dcnt ? &dcnt->n_leaves_tgt : nullptr)))
+        return cuda_fail(P, e, "target leaves");
     // ---- up-pass on the plan's stream while the lists (Algorithm 1) are built on
     // the auxiliary stream: neither needs the other's results, and the small
     // levels of the one leave room on the GPU for the other
@@ -387,7 +401,7 @@ sfmm_status solve(sfmm_plan_s* P, const double* src, const void* q, int64_t N, c
     if (dfe) {
         // double-float frames per node, then the M2M / L2L parameters in double-float
         if ((e = ensure(P->framedf, (size_t)nn * frame_df_bytes()))) return cuda_fail(P, e, "alloc");
-        if ((e = launch_frame_df((int)nn, P->n_geom.as<double>(), P->framedf.p, s)) ||
+        if ((e = launch_frame_df((int)nn, T.d_nn, P->n_geom.as<double>(), P->framedf.p, s)) ||
             (e = launch_child_geo_df(T, P->framedf.p, P->logtab.as<float4>(), P->m2m_geo.p, P->l2l_geo.p, s)))
             return cuda_fail(P, e, "child geometry");
     } else if ((e = launch_child_geo(T, P->geom32.as<float>(), P->m2m_geo.p, P->l2l_geo.p, ek, s))) {
@@ -397,20 +411,24 @@ sfmm_status solve(sfmm_plan_s* P, const double* src, const void* q, int64_t N, c
         return cuda_fail(P, e, "fork lists");
     if (offsets) {
         if ((e = ensure(P->soff, (size_t)N * 32))) return cuda_fail(P, e, "alloc");
-        if ((e = launch_src_offsets(T, P->leaves_src.as<int>(), P->n_leaves, P->src4.as<double4_32a>(),
+        if ((e = launch_src_offsets(T, P->leaves_src.as<int>(), P->n_leaves, d_nls, P->src4.as<double4_32a>(),
                                     P->soff.as<float4>(), s)))
             return cuda_fail(P, e, "offsets");
     }
     if (adj) e = launch_p2m_adj(T, P->leaves_src.as<int>(), P->n_leaves, P->src4.as<double4_32a>(),
                                 P->dip4.as<double4_32a>(), P->mpole.as<double>(), p, s);
-    else if (dfe) e = launch_p2m_df_leaf(T, P->leaves_src.as<int>(), P->n_leaves, P->soff.as<float4>(),
+    else if (dfe) e = launch_p2m_df_leaf(T, P->leaves_src.as<int>(), P->n_leaves, d_nls, P->soff.as<float4>(),
                                          P->logtab.as<float4>(), p, P->mpole.p, s);
     else e = launch_p2m(T, P->leaves_src.as<int>(), P->n_leaves, P->src4.as<double4_32a>(), P->soff.as<float4>(),
                         P->logtab.as<float4>(), P->mpole.p, p, ek, s);
     if (e) return cuda_fail(P, e, "P2M");
-    const int depth = (int)P->level_start.size() - 2;
+    // graph mode: every level up to the capacity, each launch sized by the level-width capacity
+    const int depth = P->gm ? (int)P->cap.levels : (int)P->level_start.size() - 2;
+    const int W = (int)P->cap.width;
     for (int l = depth - 1; l >= 0; --l) {
-        if (dfe) e = launch_m2m_df(T, P->level_start[l + 1], P->level_start[l + 2], p, P->m2m_geo.p, P->mpole.p, s);
+        if (P->gm) e = launch_m2m_df(T, 0, W, l, p, P->m2m_geo.p, P->mpole.p, s);
+        else if (dfe) e = launch_m2m_df(T, P->level_start[l + 1], P->level_start[l + 2], l, p, P->m2m_geo.p,
+                                        P->mpole.p, s);
         else e = launch_m2m(T, P->level_start[l], P->level_start[l + 1], p, P->tables.as<double>(), P->m2m_geo.p,
                             P->mpole.p, ek, s);
         if (e) return cuda_fail(P, e, "M2M");
@@ -440,9 +458,10 @@ sfmm_status solve(sfmm_plan_s* P, const double* src, const void* q, int64_t N, c
             return cuda_fail(P, e, "alloc");
         if ((e = cudaMemsetAsync(P->m2l_acc.p, 0, nacc * 8, s)) || (e = cudaMemsetAsync(n_left, 0, 4, s)))
             return cuda_fail(P, e, "memset");
-        if ((e = launch_pair_geo_rho(T, P->framedf.p, P->logtab.as<float4>(), m2l_t, m2l_s, P->n_m2l, P->m2l_geo.p, s)))
+        if ((e = launch_pair_geo_rho(T, P->framedf.p, P->logtab.as<float4>(), m2l_t, m2l_s, P->n_m2l, P->d_m2l,
+                                     P->m2l_geo.p, s)))
             return cuda_fail(P, e, "pair geometry");
-        if ((e = launch_m2l_pair(P->n_m2l, m2l_t, m2l_s, P->m2l_geo.p, P->mpole.p, p, P->m2l_acc.as<double>(),
+        if ((e = launch_m2l_pair(P->n_m2l, P->d_m2l, m2l_t, m2l_s, P->m2l_geo.p, P->mpole.p, p, P->m2l_acc.as<double>(),
                                  P->leftover.as<uint32_t>(), n_left, s)))
             return cuda_fail(P, e, "M2L");
         if ((e = launch_m2l_left_df(T, m2l_t, m2l_s, P->leftover.as<uint32_t>(), n_left, P->n_m2l, p,
@@ -471,8 +490,9 @@ sfmm_status solve(sfmm_plan_s* P, const double* src, const void* q, int64_t N, c
     // ---- L2L (double-float: each node's local is its M2L sum plus its parent's local translated)
     if (dfe) {
         for (int l = 0; l <= depth; ++l)
-            if ((e = launch_l2l_df(T, P->level_start[l], P->level_start[l + 1], p, P->l2l_geo.p,
-                                   P->m2l_acc.as<double>(), P->local.p, s)))
+            if ((e = P->gm ? launch_l2l_df(T, 0, W, l, p, P->l2l_geo.p, P->m2l_acc.as<double>(), P->local.p, s)
+                           : launch_l2l_df(T, P->level_start[l], P->level_start[l + 1], l, p, P->l2l_geo.p,
+                                           P->m2l_acc.as<double>(), P->local.p, s)))
                 return cuda_fail(P, e, "L2L");
     } else {
         for (int l = 1; l <= depth; ++l)
@@ -487,8 +507,8 @@ sfmm_status solve(sfmm_plan_s* P, const double* src, const void* q, int64_t N, c
         const uint64_t* p2p_t = P->p2p_alt ? P->p2p_t2.as<uint64_t>() : P->p2p_t.as<uint64_t>();
         if ((e = ensure(P->toff, (size_t)M * 32)) || (e = ensure(P->dc, (size_t)std::max<int64_t>(P->n_p2p, 1) * 32)))
             return cuda_fail(P, e, "alloc");
-        if ((e = launch_eval32_prep(T, P->leaves_tgt.as<int>(), P->n_leaves_tgt, P->tgt4.as<double4_32a>(),
-                                    P->toff.as<float4>(), p2p_t, p2p_s, P->n_p2p, P->dc.as<float4>(), s)))
+        if ((e = launch_eval32_prep(T, P->leaves_tgt.as<int>(), P->n_leaves_tgt, d_nlt, P->tgt4.as<double4_32a>(),
+                                    P->toff.as<float4>(), p2p_t, p2p_s, P->n_p2p, P->d_p2p, P->dc.as<float4>(), s)))
             return cuda_fail(P, e, "offsets");
     }
     unsigned long long* leaf_ctr = reinterpret_cast<unsigned long long*>(P->small.as<int64_t>() + 40);
@@ -496,18 +516,22 @@ sfmm_status solve(sfmm_plan_s* P, const double* src, const void* q, int64_t N, c
                                  P->dip4.as<double4_32a>(), P->tgt4.as<double4_32a>(), tperm, P->p2p_off.as<int64_t>(),
                                  p2p_s, P->local.as<double>(), P->mpole.as<double>(), p, P->opt.zero_mean, adj->w,
                                  adj->w_f32, psi, adj->grad3, leaf_ctr, s);
-    else if (near32) e = launch_eval32(T, P->leaves_tgt.as<int>(), P->n_leaves_tgt, P->soff.as<float4>(),
+    else if (near32) e = launch_eval32(T, P->leaves_tgt.as<int>(), P->n_leaves_tgt, d_nlt, P->soff.as<float4>(),
                                 P->toff.as<float4>(), P->dc.as<float4>(), P->tgt4.as<double4_32a>(), tperm, P->p2p_off.as<int64_t>(), p2p_s,
                                 P->local.p, P->mpole.p, !fp32, p, P->opt.zero_mean, psi, alpha,
                                 src == tgt, leaf_ctr, s);
-    else if (dfe) e = launch_eval_df(T, P->leaves_tgt.as<int>(), P->n_leaves_tgt, P->soff.as<float4>(),
+    else if (dfe) e = launch_eval_df(T, P->leaves_tgt.as<int>(), P->n_leaves_tgt, d_nlt, P->soff.as<float4>(),
                                      P->toff.as<float4>(), P->dc.as<float4>(), P->tgt4.as<double4_32a>(), tperm,
                                      P->p2p_off.as<int64_t>(), p2p_s, P->local.p, P->mpole.p,
                                      P->logtab.as<float4>(), p, P->opt.zero_mean, psi, alpha, leaf_ctr, s);
-    else e = launch_eval(T, P->leaves_tgt.as<int>(), P->n_leaves_tgt, P->src4.as<double4_32a>(),
+    else e = launch_eval(T, P->leaves_tgt.as<int>(), P->n_leaves_tgt, d_nlt, P->src4.as<double4_32a>(),
                          P->tgt4.as<double4_32a>(), tperm, P->p2p_off.as<int64_t>(), p2p_s, P->local.as<double>(),
                          P->mpole.as<double>(), p, P->opt.zero_mean, P->opt.sigma, psi, alpha, gamma, mu, leaf_ctr, s);
     if (e) return cuda_fail(P, e, "evaluation");
+    if (P->gm) {          // no synchronisation: the caller reads the overflow flag after the work
+        P->stats.launches = launch_total() - launches0;
+        return SFMM_OK;
+    }
     tm.mark();
     if (P->timing >= 2) {
         // near-field source-target pairs (for the throughput of the evaluation kernel)
@@ -549,6 +573,15 @@ sfmm_status check_args(sfmm_plan_s* P, const double* src, const void* q, int64_t
 }
 
 }  // namespace
+
+// the solve for the other translation units (graph.cu)
+sfmm_status solve_entry(sfmm_plan_s* P, const double* src, const void* q, int64_t N, const double* tgt, int64_t M,
+                        double* psi, double* alpha)
+{
+    return solve(P, src, q, N, tgt, M, psi, alpha);
+}
+
+sfmm_status plan_error(sfmm_plan_s* P, sfmm_status st, const std::string& msg) { return fail(P, st, msg); }
 
 void set_process_error(const std::string& msg)
 {
@@ -840,8 +873,9 @@ void sfmm_destroy(sfmm_plan_t plan)
                   &plan->leaves_tgt, &plan->m2l_geo, &plan->m2m_geo, &plan->l2l_geo, &plan->soff,
                   &plan->toff, &plan->dc, &plan->leftover, &plan->geom32, &plan->macn, &plan->logtab,
                   &plan->ttmp, &plan->dip4, &plan->adj_h, &plan->adj_g, &plan->macn32, &plan->m2l_acc,
-                  &plan->framedf};
+                  &plan->framedf, &plan->dcnt};
     if (plan->aux) cudaStreamSynchronize(plan->aux);
+    graph_release(plan);
     for (sfmm_plan_s* L : plan->lanes) sfmm_destroy(L);
     plan->lanes.clear();
     if (plan->owns_stream && plan->stream) {

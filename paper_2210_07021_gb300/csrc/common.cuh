@@ -67,7 +67,9 @@ enum { EXP_F64 = 0, EXP_F32 = 1, EXP_DF = 2 };
 
 // --------------------------------------------------------------- the tree
 struct TreeView {
-    int n_nodes;
+    int n_nodes;          // node count, or the node capacity when d_nn is set (graph mode)
+    const int64_t* d_nn;  // graph mode: the node count on the device (kernels read it there), else NULL
+    const int64_t* d_level;  // graph mode: the level starts on the device (DevCounts::level), else NULL
     const uint64_t* prefix;
     const int* level;
     const int* first;     // range in key-sorted sources
@@ -79,6 +81,32 @@ struct TreeView {
     const int* tcount;
 };
 
+// A count kept on the device in graph mode (d != NULL), clamped to the capacity h
+// the launch was sized for; else the host value h.
+__device__ __forceinline__ int64_t dcount(const int64_t* d, int64_t h)
+{
+    if (!d) return h;
+    const int64_t v = *d;
+    return v < h ? v : h;
+}
+
+// The counts of a solve run without host synchronisation (graph mode): launches
+// are sized by the plan's capacities and every kernel reads its actual count
+// here; a kernel that would exceed a capacity sets `overflow` instead of
+// writing, and the host discards such a solve.
+struct DevCounts {
+    int64_t nn;             // nodes
+    int64_t n_leaves;       // source leaves (count > 0)
+    int64_t n_leaves_tgt;   // target leaves (tcount > 0)
+    int64_t overflow;       // nonzero: a capacity was exceeded
+    int64_t level[32];      // level starts: nodes of level l are [level[l], level[l + 1])
+};
+
+}  // namespace sfmm
+
+namespace sfmm {
+struct GraphState;
+void graph_release(sfmm_plan_s* P);
 }  // namespace sfmm
 
 // --------------------------------------------------------------- the plan
@@ -97,6 +125,15 @@ struct sfmm_plan_s {
     std::string err;
     int timing = 0;                        // 0 off, 1 phase times, 2 also the near-field pair count
     int* h_status = nullptr;               // pinned host word: the tensor-core M2L's status of the last solve
+    // graph mode: the solve runs without host synchronisation, its launches sized by
+    // these capacities and its counts kept in dcnt (DevCounts)
+    bool gm = false;
+    struct Caps {
+        int64_t nodes = 0, width = 0, levels = 0, m2l = 0, p2p = 0, front = 0;
+    } cap;
+    sfmm::Buf dcnt;
+    int64_t last_max_width = 0;            // widest tree level of the last synchronised solve
+    sfmm::GraphState* graph = nullptr;     // graph-launched shells (graph.cu), or NULL
     sfmm_stats stats{};
 
     // sources (key-sorted)
@@ -129,7 +166,9 @@ struct sfmm_plan_s {
     // lists
     sfmm::Buf fa, fb, act, c_next, c_m2l, c_p2p, o_next, o_m2l, o_p2p;
     sfmm::Buf m2l_t, m2l_s, m2l_t2, m2l_s2, p2p_t, p2p_s, p2p_t2, p2p_s2, m2l_off, p2p_off;
-    int64_t n_m2l = 0, n_p2p = 0;
+    int64_t n_m2l = 0, n_p2p = 0;          // pair counts (graph mode: the list capacities)
+    const int64_t* d_m2l = nullptr;        // graph mode: the pair counts on the device, else NULL
+    const int64_t* d_p2p = nullptr;
     int64_t walk_cap_front = 0, walk_cap_m2l = 0, walk_cap_p2p = 0;   // list capacities that sufficed last time
     bool m2l_alt = false, p2p_alt = false;
     // node work lists

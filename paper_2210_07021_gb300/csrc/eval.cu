@@ -41,6 +41,7 @@ struct EvalArgs {
     TreeView T;
     const int* leaves;        // target leaves (tcount > 0)
     int64_t n_leaves;
+    const int64_t* d_n_leaves;      // graph mode: the leaf count on the device (n_leaves: the capacity)
     const double4_32a* src;       // key-sorted sources (x, y, z, q)
     const double4_32a* tgt;       // key-sorted targets (x, y, z, -)
     const uint32_t* tperm;    // original index of each sorted target
@@ -97,7 +98,7 @@ __global__ void __launch_bounds__(128) k_eval(EvalArgs A)
     if (A.zero_mean) shift = qtot;
     for (;;) {
         const int64_t w = next_leaf(A.leaf_ctr, lane);
-        if (w >= A.n_leaves) break;
+        if (w >= dcount(A.d_n_leaves, A.n_leaves)) break;
         const int leaf = A.leaves[w];
         const int tf = A.T.tfirst[leaf], tc = A.T.tcount[leaf];
         const double* g = A.T.geom + (size_t)leaf * GEOM_STRIDE;
@@ -271,7 +272,7 @@ __global__ void __launch_bounds__(128) k_eval_adj(EvalAdjArgs AA)
         for (int b = 0; b < 12; ++b) shift += A.base_mpole[(size_t)b * EXP_STRIDE + 1];
     for (;;) {
         const int64_t w = next_leaf(A.leaf_ctr, lane);
-        if (w >= A.n_leaves) break;
+        if (w >= dcount(A.d_n_leaves, A.n_leaves)) break;
         const int leaf = A.leaves[w];
         const int tf = A.T.tfirst[leaf], tc = A.T.tcount[leaf];
         const double* g = A.T.geom + (size_t)leaf * GEOM_STRIDE;
@@ -396,6 +397,7 @@ struct Eval32Args {
     TreeView T;
     const int* leaves;
     int64_t n_leaves;
+    const int64_t* d_n_leaves;      // graph mode: the leaf count on the device (n_leaves: the capacity)
     const float4* soff;       // [2N]: (hi offset, q), (lo offset, 0) of each source from its leaf centre
     const float4* toff;       // [2M]: (hi, x.z), (lo, 0) offset of each sorted target from its leaf centre
     const float4* dc;         // [2 n_p2p]: (hi, 0), (lo, 0) offset of each near leaf's centre from the target leaf's
@@ -700,7 +702,7 @@ __global__ void __launch_bounds__(128, 7) k_eval32(Eval32Args A)
     int* fst = s_first[wid];
     for (;;) {
         const int64_t w = next_leaf(A.leaf_ctr, lane);
-        if (w >= A.n_leaves) break;
+        if (w >= dcount(A.d_n_leaves, A.n_leaves)) break;
         const int leaf = A.leaves[w];
         const int tf = A.T.tfirst[leaf], tc = A.T.tcount[leaf];
         const double* g = A.T.geom + (size_t)leaf * GEOM_STRIDE;
@@ -893,6 +895,7 @@ struct EvalDfArgs {
     TreeView T;
     const int* leaves;
     int64_t n_leaves;
+    const int64_t* d_n_leaves;      // graph mode: the leaf count on the device (n_leaves: the capacity)
     const float4* soff;
     const float4* toff;
     const float4* dc;
@@ -931,7 +934,7 @@ __global__ void __launch_bounds__(128) k_eval_df(EvalDfArgs A)
     int* fst = s_first[wid];
     for (;;) {
         const int64_t w = next_leaf(A.leaf_ctr, lane);
-        if (w >= A.n_leaves) break;
+        if (w >= dcount(A.d_n_leaves, A.n_leaves)) break;
         const int leaf = A.leaves[w];
         const int tf = A.T.tfirst[leaf], tc = A.T.tcount[leaf];
         const double* g = A.T.geom + (size_t)leaf * GEOM_STRIDE;
@@ -1088,9 +1091,10 @@ __global__ void __launch_bounds__(128) k_eval_df(EvalDfArgs A)
 // instructions (the difference to 2^-47): each sorted target from its leaf's
 // centre, and each near leaf's centre from its target leaf's centre (one per
 // direct-act pair).
-__global__ void k_tgt_offsets(TreeView T, const int* __restrict__ leaves, int64_t n_leaves,
+__global__ void k_tgt_offsets(TreeView T, const int* __restrict__ leaves, int64_t n_cap, const int64_t* d_nl,
                               const double4_32a* __restrict__ tgt, float4* __restrict__ off)
 {
+    const int64_t n_leaves = dcount(d_nl, n_cap);
     const int lane = threadIdx.x & 31;
     const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -1109,8 +1113,9 @@ __global__ void k_tgt_offsets(TreeView T, const int* __restrict__ leaves, int64_
 
 // per direct-act pair: (hi offset, first source of the near leaf), (lo offset, its source count)
 __global__ void k_pair_offsets(TreeView T, const uint64_t* __restrict__ tt, const uint32_t* __restrict__ ss,
-                               int64_t n, float4* __restrict__ dc)
+                               int64_t n_cap, const int64_t* d_n, float4* __restrict__ dc)
 {
+    const int64_t n = dcount(d_n, n_cap);
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t sl = ss[k];
         const double* gs = T.geom + (size_t)sl * GEOM_STRIDE;
@@ -1140,25 +1145,25 @@ cudaError_t leaf_grid(unsigned long long* ctr, int64_t n_leaves, int per_sm, cud
 
 }  // namespace
 
-cudaError_t launch_eval32_prep(const TreeView& T, const int* leaves, int64_t n_leaves, const double4_32a* tgt,
-                               float4* toff, const uint64_t* p2p_t, const uint32_t* p2p_s, int64_t n_p2p, float4* dc,
-                               cudaStream_t s)
+cudaError_t launch_eval32_prep(const TreeView& T, const int* leaves, int64_t n_leaves, const int64_t* d_nl,
+                               const double4_32a* tgt, float4* toff, const uint64_t* p2p_t, const uint32_t* p2p_s,
+                               int64_t n_p2p, const int64_t* d_np, float4* dc, cudaStream_t s)
 {
     if (n_leaves > 0) {
         int64_t b = (n_leaves + 7) / 8;
         if (b > 152 * 64) b = 152 * 64;
-        k_tgt_offsets<<<(unsigned)b, 256, 0, s>>>(T, leaves, n_leaves, tgt, toff); count_launch();
+        k_tgt_offsets<<<(unsigned)b, 256, 0, s>>>(T, leaves, n_leaves, d_nl, tgt, toff); count_launch();
     }
     if (n_p2p > 0) {
         int64_t b = (n_p2p + 255) / 256;
         if (b > 152 * 64) b = 152 * 64;
-        k_pair_offsets<<<(unsigned)b, 256, 0, s>>>(T, p2p_t, p2p_s, n_p2p, dc); count_launch();
+        k_pair_offsets<<<(unsigned)b, 256, 0, s>>>(T, p2p_t, p2p_s, n_p2p, d_np, dc); count_launch();
     }
     return cudaGetLastError();
 }
 
 // local/mpole: FP32 expansions, or double-float ones when dfar (the 1e-6 path)
-cudaError_t launch_eval32(const TreeView& T, const int* leaves, int64_t n_leaves, const float4* soff,
+cudaError_t launch_eval32(const TreeView& T, const int* leaves, int64_t n_leaves, const int64_t* d_nl, const float4* soff,
                           const float4* toff, const float4* dc, const double4_32a* tgt, const uint32_t* tperm, const int64_t* p2p_off,
                           const uint32_t* p2p_src, const void* local, const void* mpole, bool dfar, int p, int zero_mean,
                           double* psi, double* alpha, bool coincide, unsigned long long* leaf_ctr, cudaStream_t s)
@@ -1168,6 +1173,7 @@ cudaError_t launch_eval32(const TreeView& T, const int* leaves, int64_t n_leaves
     A.T = T;
     A.leaves = leaves;
     A.n_leaves = n_leaves;
+    A.d_n_leaves = d_nl;
     A.soff = soff;
     A.toff = toff;
     A.dc = dc;
@@ -1224,7 +1230,7 @@ void fill_log_table(float* out)
     out[4 * 128 + 2] = out[4 * 128 + 3] = 0.f;
 }
 
-cudaError_t launch_eval_df(const TreeView& T, const int* leaves, int64_t n_leaves, const float4* soff,
+cudaError_t launch_eval_df(const TreeView& T, const int* leaves, int64_t n_leaves, const int64_t* d_nl, const float4* soff,
                            const float4* toff, const float4* dc, const double4_32a* tgt, const uint32_t* tperm,
                            const int64_t* p2p_off, const uint32_t* p2p_src, const void* local, const void* mpole,
                            const float4* log_tab, int p, int zero_mean, double* psi, double* alpha,
@@ -1235,6 +1241,7 @@ cudaError_t launch_eval_df(const TreeView& T, const int* leaves, int64_t n_leave
     A.T = T;
     A.leaves = leaves;
     A.n_leaves = n_leaves;
+    A.d_n_leaves = d_nl;
     A.soff = soff;
     A.toff = toff;
     A.dc = dc;
@@ -1269,7 +1276,8 @@ cudaError_t launch_count_pairs(const TreeView& T, const int* leaves, int64_t n_l
     return cudaGetLastError();
 }
 
-cudaError_t launch_eval(const TreeView& T, const int* leaves, int64_t n_leaves, const double4_32a* src, const double4_32a* tgt,
+cudaError_t launch_eval(const TreeView& T, const int* leaves, int64_t n_leaves, const int64_t* d_nl, const double4_32a* src,
+                        const double4_32a* tgt,
                         const uint32_t* tperm, const int64_t* p2p_off, const uint32_t* p2p_src, const double* local,
                         const double* mpole, int p, int zero_mean, double sigma, double* psi, double* alpha,
                         double* gamma, double* mu, unsigned long long* leaf_ctr, cudaStream_t s)
@@ -1279,6 +1287,7 @@ cudaError_t launch_eval(const TreeView& T, const int* leaves, int64_t n_leaves, 
     A.T = T;
     A.leaves = leaves;
     A.n_leaves = n_leaves;
+    A.d_n_leaves = d_nl;
     A.src = src;
     A.tgt = tgt;
     A.tperm = tperm;
@@ -1317,6 +1326,7 @@ cudaError_t launch_eval_adj(const TreeView& T, const int* leaves, int64_t n_leav
     A.T = T;
     A.leaves = leaves;
     A.n_leaves = n_leaves;
+    A.d_n_leaves = nullptr;
     A.src = src;
     A.tgt = tgt;
     A.tperm = tperm;

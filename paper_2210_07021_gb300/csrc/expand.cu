@@ -229,8 +229,9 @@ struct __align__(16) FrameDF {
     dflt et[3], ep[3], r, pad;
 };
 
-__global__ void k_frame_df(int n_nodes, const double* __restrict__ geom, FrameDF* __restrict__ out)
+__global__ void k_frame_df(int n_cap, const int64_t* d_nn, const double* __restrict__ geom, FrameDF* __restrict__ out)
 {
+    const int64_t n_nodes = dcount(d_nn, n_cap);
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_nodes; i += (int64_t)gridDim.x * blockDim.x) {
         const double* g = geom + (size_t)i * GEOM_STRIDE;
         FrameDF F;
@@ -316,12 +317,13 @@ __device__ __forceinline__ PairGeoDF pair_geometry_df(const double* gS, const do
 // M2L parameters of the thread-per-pair double-float kernel (m2l_pair.cu):
 // a ph1, b ph2, rho = g/(a b) = 1/cos^2(theta/2), log sin(theta/2).
 __global__ void k_pair_geo_rho(TreeView T, const FrameDF* __restrict__ fr, const float4* __restrict__ log_tab,
-                               const uint64_t* __restrict__ tt, const uint32_t* __restrict__ ss, int64_t n,
-                               XGeoRho* __restrict__ out)
+                               const uint64_t* __restrict__ tt, const uint32_t* __restrict__ ss, int64_t n_cap,
+                               const int64_t* d_n, XGeoRho* __restrict__ out)
 {
     __shared__ float4 s_tab[129];
     for (int i = threadIdx.x; i < 129; i += blockDim.x) s_tab[i] = log_tab[i];
     __syncthreads();
+    const int64_t n = dcount(d_n, n_cap);
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t si = ss[k], ti = (uint32_t)tt[k];
         const FrameDF FS = fr[si], FT = fr[ti];
@@ -354,7 +356,8 @@ __global__ void k_child_geo_df(TreeView T, const FrameDF* __restrict__ fr, const
     __shared__ float4 s_tab[129];
     for (int i = threadIdx.x; i < 129; i += blockDim.x) s_tab[i] = log_tab[i];
     __syncthreads();
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < T.n_nodes; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t nn = dcount(T.d_nn, T.n_nodes);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nn; i += (int64_t)gridDim.x * blockDim.x) {
         const int par = T.parent[i];
         if (par < 0) continue;
         const double* gC = T.geom + (size_t)i * GEOM_STRIDE;
@@ -1032,9 +1035,10 @@ __global__ void k_acc_to_df(int64_t n, const double* __restrict__ acc, dflt* __r
 // FP32 offset of every key-sorted source from the centre of its leaf as an
 // (hi, lo) pair (the difference to 2^-47, formed without FP64 instructions),
 // plus its mass split the same way: off[2j] = (hi, q_hi), off[2j+1] = (lo, q_lo).
-__global__ void k_src_offsets(TreeView T, const int* __restrict__ leaves, int64_t n_leaves,
+__global__ void k_src_offsets(TreeView T, const int* __restrict__ leaves, int64_t n_cap, const int64_t* d_nl,
                               const double4_32a* __restrict__ src, float4* __restrict__ off)
 {
+    const int64_t n_leaves = dcount(d_nl, n_cap);
     const int lane = threadIdx.x & 31;
     const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -1126,11 +1130,11 @@ cudaError_t launch_child_geo(const TreeView& T, const float* g32, void* m2m, voi
     return cudaGetLastError();
 }
 
-cudaError_t launch_src_offsets(const TreeView& T, const int* leaves, int64_t n_leaves, const double4_32a* src,
-                               float4* off, cudaStream_t s)
+cudaError_t launch_src_offsets(const TreeView& T, const int* leaves, int64_t n_leaves, const int64_t* d_nl,
+                               const double4_32a* src, float4* off, cudaStream_t s)
 {
     if (n_leaves == 0) return cudaSuccess;
-    k_src_offsets<<<grid_for(n_leaves, 8), 256, 0, s>>>(T, leaves, n_leaves, src, off); count_launch();
+    k_src_offsets<<<grid_for(n_leaves, 8), 256, 0, s>>>(T, leaves, n_leaves, d_nl, src, off); count_launch();
     return cudaGetLastError();
 }
 
@@ -1222,19 +1226,19 @@ cudaError_t launch_m2l_list(const uint64_t* ptgt, const uint32_t* psrc, const ui
 
 size_t frame_df_bytes() { return sizeof(FrameDF); }
 
-cudaError_t launch_frame_df(int n_nodes, const double* geom, void* out, cudaStream_t s)
+cudaError_t launch_frame_df(int n_nodes, const int64_t* d_nn, const double* geom, void* out, cudaStream_t s)
 {
     if (n_nodes == 0) return cudaSuccess;
-    k_frame_df<<<grid_for(n_nodes, 256), 256, 0, s>>>(n_nodes, geom, static_cast<FrameDF*>(out));
+    k_frame_df<<<grid_for(n_nodes, 256), 256, 0, s>>>(n_nodes, d_nn, geom, static_cast<FrameDF*>(out));
     count_launch();
     return cudaGetLastError();
 }
 
 cudaError_t launch_pair_geo_rho(const TreeView& T, const void* frames, const float4* log_tab, const uint64_t* tt,
-                                const uint32_t* ss, int64_t n, void* out, cudaStream_t s)
+                                const uint32_t* ss, int64_t n, const int64_t* d_n, void* out, cudaStream_t s)
 {
     if (n == 0) return cudaSuccess;
-    k_pair_geo_rho<<<grid_for(n, 256), 256, 0, s>>>(T, static_cast<const FrameDF*>(frames), log_tab, tt, ss, n,
+    k_pair_geo_rho<<<grid_for(n, 256), 256, 0, s>>>(T, static_cast<const FrameDF*>(frames), log_tab, tt, ss, n, d_n,
                                                      static_cast<XGeoRho*>(out));
     count_launch();
     return cudaGetLastError();

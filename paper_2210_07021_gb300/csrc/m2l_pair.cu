@@ -44,8 +44,8 @@ constexpr int PW = 4;            // warps per CTA
 // packed FP32x2 form of updown_df.cu measured slower here: it needs twice the
 // registers and the FMA pipe, not the issue rate, bounds this kernel).
 template <int P>
-__global__ void __launch_bounds__(128, (P <= 20 ? 5 : P <= 24 ? 4 : 3)) k_m2l_pair(int64_t n_pairs, const uint64_t* __restrict__ ptgt,
-                                                  const uint32_t* __restrict__ psrc,
+__global__ void __launch_bounds__(128, (P <= 20 ? 5 : P <= 24 ? 4 : 3))
+k_m2l_pair(int64_t n_cap, const int64_t* d_n, const uint64_t* __restrict__ ptgt, const uint32_t* __restrict__ psrc,
                                                   const XGeoRho* __restrict__ geo, const dflt* __restrict__ mpole,
                                                   int p, double* __restrict__ acc, uint32_t* __restrict__ leftover,
                                                   uint32_t* __restrict__ n_left)
@@ -57,6 +57,7 @@ __global__ void __launch_bounds__(128, (P <= 20 ? 5 : P <= 24 ? 4 : 3)) k_m2l_pa
     dflt* rows = reinterpret_cast<dflt*>(smem_raw) + (size_t)wid * 32 * RS;
     dflt* row = rows + lane * RS;
     const int ncol = 2 * p + 2;
+    const int64_t n_pairs = dcount(d_n, n_cap);
     const int64_t stride = (int64_t)gridDim.x * PW * 32;
     for (int64_t base = ((int64_t)blockIdx.x * PW + wid) * 32; base < n_pairs; base += stride) {
         const int64_t k = base + lane;
@@ -165,8 +166,9 @@ __global__ void __launch_bounds__(128, (P <= 20 ? 5 : P <= 24 ? 4 : 3)) k_m2l_pa
 }
 
 template <int P>
-cudaError_t launch_p(int64_t n_pairs, const uint64_t* ptgt, const uint32_t* psrc, const XGeoRho* geo,
-                     const dflt* mpole, int p, double* acc, uint32_t* leftover, uint32_t* n_left, cudaStream_t s)
+cudaError_t launch_p(int64_t n_pairs, const int64_t* d_n, const uint64_t* ptgt, const uint32_t* psrc,
+                     const XGeoRho* geo, const dflt* mpole, int p, double* acc, uint32_t* leftover, uint32_t* n_left,
+                     cudaStream_t s)
 {
     const size_t smem = (size_t)PW * 32 * (2 * P + 3) * sizeof(dflt);
     cudaError_t e;
@@ -178,14 +180,14 @@ cudaError_t launch_p(int64_t n_pairs, const uint64_t* ptgt, const uint32_t* psrc
     const int64_t chunks = (n_pairs + PW * 32 - 1) / (PW * 32);
     const int64_t cap = (int64_t)sms * (per_sm > 0 ? per_sm : 1);
     const int64_t grid = chunks < cap ? chunks : cap;
-    k_m2l_pair<P><<<(unsigned)grid, PW * 32, smem, s>>>(n_pairs, ptgt, psrc, geo, mpole, p, acc, leftover, n_left);
+    k_m2l_pair<P><<<(unsigned)grid, PW * 32, smem, s>>>(n_pairs, d_n, ptgt, psrc, geo, mpole, p, acc, leftover, n_left);
     count_launch();
     return cudaGetLastError();
 }
 
 }  // namespace
 
-cudaError_t launch_m2l_pair(int64_t n_pairs, const uint64_t* ptgt, const uint32_t* psrc, const void* geo,
+cudaError_t launch_m2l_pair(int64_t n_pairs, const int64_t* d_n, const uint64_t* ptgt, const uint32_t* psrc, const void* geo,
                             const void* mpole, int p, double* acc, uint32_t* leftover, uint32_t* n_left,
                             cudaStream_t s)
 {
@@ -193,14 +195,14 @@ cudaError_t launch_m2l_pair(int64_t n_pairs, const uint64_t* ptgt, const uint32_
     const XGeoRho* G = static_cast<const XGeoRho*>(geo);
     const dflt* mp = static_cast<const dflt*>(mpole);
     switch ((p + 3) / 4 * 4) {
-    case 4: return launch_p<4>(n_pairs, ptgt, psrc, G, mp, p, acc, leftover, n_left, s);
-    case 8: return launch_p<8>(n_pairs, ptgt, psrc, G, mp, p, acc, leftover, n_left, s);
-    case 12: return launch_p<12>(n_pairs, ptgt, psrc, G, mp, p, acc, leftover, n_left, s);
-    case 16: return launch_p<16>(n_pairs, ptgt, psrc, G, mp, p, acc, leftover, n_left, s);
-    case 20: return launch_p<20>(n_pairs, ptgt, psrc, G, mp, p, acc, leftover, n_left, s);
-    case 24: return launch_p<24>(n_pairs, ptgt, psrc, G, mp, p, acc, leftover, n_left, s);
-    case 28: return launch_p<28>(n_pairs, ptgt, psrc, G, mp, p, acc, leftover, n_left, s);
-    case 32: return launch_p<32>(n_pairs, ptgt, psrc, G, mp, p, acc, leftover, n_left, s);
+    case 4: return launch_p<4>(n_pairs, d_n, ptgt, psrc, G, mp, p, acc, leftover, n_left, s);
+    case 8: return launch_p<8>(n_pairs, d_n, ptgt, psrc, G, mp, p, acc, leftover, n_left, s);
+    case 12: return launch_p<12>(n_pairs, d_n, ptgt, psrc, G, mp, p, acc, leftover, n_left, s);
+    case 16: return launch_p<16>(n_pairs, d_n, ptgt, psrc, G, mp, p, acc, leftover, n_left, s);
+    case 20: return launch_p<20>(n_pairs, d_n, ptgt, psrc, G, mp, p, acc, leftover, n_left, s);
+    case 24: return launch_p<24>(n_pairs, d_n, ptgt, psrc, G, mp, p, acc, leftover, n_left, s);
+    case 28: return launch_p<28>(n_pairs, d_n, ptgt, psrc, G, mp, p, acc, leftover, n_left, s);
+    case 32: return launch_p<32>(n_pairs, d_n, ptgt, psrc, G, mp, p, acc, leftover, n_left, s);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -16,6 +16,8 @@
 // scale of the stereographic variable z = tan(theta/2) e^{i phi} inside the box.
 #include "common.cuh"
 
+#include <algorithm>
+
 namespace sfmm {
 
 namespace {
@@ -90,17 +92,56 @@ __global__ void k_level0(const uint64_t* __restrict__ keys, int64_t n, uint64_t*
     parent[f] = -1;
 }
 
+// Graph mode (dc != NULL): the level's bounds come from dc->level, the launch
+// covers `width` (the level-width capacity) and the flags beyond the level are
+// zero, so that a scan over the whole capacity is the scan of the level.
 __global__ void k_split_flags(const int* __restrict__ count, int a, int b, int lvl, int m, int max_depth,
-                              int64_t* __restrict__ flags)
+                              int64_t* __restrict__ flags, DevCounts* dc, int64_t width)
 {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < b - a; i += (int64_t)gridDim.x * blockDim.x)
-        flags[i] = (count[a + i] > m && lvl < max_depth) ? 1 : 0;
+    if (dc) {
+        a = (int)dc->level[lvl];
+        b = (int)dc->level[lvl + 1];
+        if (blockIdx.x == 0 && threadIdx.x == 0 && b - a > width) dc->overflow = 1;
+    } else {
+        width = b - a;
+    }
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < width; i += (int64_t)gridDim.x * blockDim.x)
+        flags[i] = (i < b - a && count[a + i] > m && lvl < max_depth) ? 1 : 0;
+}
+
+__global__ void k_counts_init(DevCounts* dc)
+{
+    if (threadIdx.x < 32) dc->level[threadIdx.x] = threadIdx.x == 0 ? 0 : 12;
+    if (threadIdx.x == 0) { dc->nn = 12; dc->n_leaves = 0; dc->n_leaves_tgt = 0; dc->overflow = 0; }
+}
+
+// Graph mode: the next level's end from the scan of the split flags (its total),
+// or an overflow if the nodes would not fit the capacity (`last`: the deepest
+// level the capacity allows; a split there is an overflow too).
+__global__ void k_level_end(DevCounts* dc, int lvl, const int64_t* __restrict__ total, int64_t node_cap, int last)
+{
+    const int64_t b = dc->level[lvl + 1];
+    int64_t nb = b + 4 * *total;
+    // after an overflow the tree stops growing: the nodes built so far stay a
+    // consistent tree (unsplit nodes are leaves), so every later kernel stays in bounds
+    if (dc->overflow || nb > node_cap || (last && *total > 0)) {
+        dc->overflow = 1;
+        nb = b;
+    }
+    dc->level[lvl + 2] = nb;
+    dc->nn = nb;
 }
 
 __global__ void k_make_children(const uint64_t* __restrict__ keys, int a, int b, int lvl,
                                 const int64_t* __restrict__ flags, const int64_t* __restrict__ pos,
-                                uint64_t* prefix, int* level, int* first, int* count, int* child0, int* parent)
+                                uint64_t* prefix, int* level, int* first, int* count, int* child0, int* parent,
+                                const DevCounts* dc)
 {
+    if (dc) {
+        if (dc->overflow) return;
+        a = (int)dc->level[lvl];
+        b = (int)dc->level[lvl + 1];
+    }
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < b - a; i += (int64_t)gridDim.x * blockDim.x) {
         const int node = a + (int)i;
         if (!flags[i]) continue;
@@ -124,9 +165,10 @@ __global__ void k_make_children(const uint64_t* __restrict__ keys, int a, int b,
     }
 }
 
-__global__ void k_geometry(int n_nodes, const uint64_t* __restrict__ prefix, const int* __restrict__ level,
-                           double* __restrict__ geom)
+__global__ void k_geometry(int n_cap, const int64_t* d_nn, const uint64_t* __restrict__ prefix,
+                           const int* __restrict__ level, double* __restrict__ geom)
 {
+    const int64_t n_nodes = dcount(d_nn, n_cap);
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_nodes; i += (int64_t)gridDim.x * blockDim.x) {
         const int order = level[i];
         const uint64_t pix = prefix[i];
@@ -153,10 +195,11 @@ __global__ void k_geometry(int n_nodes, const uint64_t* __restrict__ prefix, con
     }
 }
 
-__global__ void k_target_ranges(int n_nodes, const uint64_t* __restrict__ prefix, const int* __restrict__ level,
-                                const uint64_t* __restrict__ tkeys, int64_t M, int* __restrict__ tfirst,
-                                int* __restrict__ tcount)
+__global__ void k_target_ranges(int n_cap, const int64_t* d_nn, const uint64_t* __restrict__ prefix,
+                                const int* __restrict__ level, const uint64_t* __restrict__ tkeys, int64_t M,
+                                int* __restrict__ tfirst, int* __restrict__ tcount)
 {
+    const int64_t n_nodes = dcount(d_nn, n_cap);
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_nodes; i += (int64_t)gridDim.x * blockDim.x) {
         const int shift = 2 * (ORDER_MAX - level[i]);
         const uint64_t lo = prefix[i] << shift, hi = (prefix[i] + 1ull) << shift;
@@ -167,11 +210,13 @@ __global__ void k_target_ranges(int n_nodes, const uint64_t* __restrict__ prefix
     }
 }
 
-__global__ void k_collect_leaves(int n_nodes, const int* __restrict__ child0, const int* __restrict__ cnt,
-                                 int64_t* __restrict__ flags)
+// flags over the whole capacity n_cap (zero beyond the node count)
+__global__ void k_collect_leaves(int n_cap, const int64_t* d_nn, const int* __restrict__ child0,
+                                 const int* __restrict__ cnt, int64_t* __restrict__ flags)
 {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_nodes; i += (int64_t)gridDim.x * blockDim.x)
-        flags[i] = (child0[i] < 0 && cnt[i] > 0) ? 1 : 0;
+    const int64_t nn = dcount(d_nn, n_cap);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_cap; i += (int64_t)gridDim.x * blockDim.x)
+        flags[i] = (i < nn && child0[i] < 0 && cnt[i] > 0) ? 1 : 0;
 }
 
 __global__ void k_compact(int n, const int64_t* __restrict__ flags, const int64_t* __restrict__ pos, int* __restrict__ out)
@@ -193,6 +238,12 @@ inline unsigned grid_for(int64_t n, int threads = 256)
 // Build the tree from the key-sorted source keys.  Grows the plan's node arrays
 // as needed; fills plan->level_start and plan->n_nodes.  Synchronises the
 // stream once per level (the next level's size is needed on the host).
+//
+// Graph mode (plan->gm): no synchronisation.  Every level up to the plan's level
+// capacity is launched with grids sized by the level-width capacity; the level
+// bounds and the node count live in the plan's DevCounts (k_level_end), and a
+// tree that would not fit (more nodes, a wider level, or a split at the last
+// level) sets the overflow flag.  plan->n_nodes is the node capacity.
 cudaError_t build_tree(sfmm_plan_s* P, const uint64_t* keys, int64_t n, int m, int max_depth)
 {
     cudaStream_t s = P->stream;
@@ -211,6 +262,33 @@ cudaError_t build_tree(sfmm_plan_s* P, const uint64_t* keys, int64_t n, int m, i
         P->node_cap = cap;
         return cudaSuccess;
     };
+    if (P->gm) {
+        DevCounts* dc = P->dcnt.as<DevCounts>();
+        const int64_t width = P->cap.width, levels = P->cap.levels;
+        if ((e = grow(P->cap.nodes)) || (e = ensure(P->flags, (size_t)width * 8)) ||
+            (e = ensure(P->pos, (size_t)width * 8)) || (e = ensure(P->tmp, scan_tmp_bytes(width))))
+            return e;
+        int64_t* flags = P->flags.as<int64_t>();
+        int64_t* pos = P->pos.as<int64_t>();
+        int64_t* total = P->small.as<int64_t>();
+        k_level0<<<1, 32, 0, s>>>(keys, n, P->n_prefix.as<uint64_t>(), P->n_level.as<int>(), P->n_first.as<int>(),
+                                  P->n_count.as<int>(), P->n_child0.as<int>(), P->n_parent.as<int>()); count_launch();
+        k_counts_init<<<1, 32, 0, s>>>(dc); count_launch();
+        for (int lvl = 0; lvl < levels; ++lvl) {
+            k_split_flags<<<grid_for(width), 256, 0, s>>>(P->n_count.as<int>(), 0, 0, lvl, m, max_depth, flags, dc,
+                                                           width); count_launch();
+            if ((e = exclusive_scan_i64(flags, pos, width, total, P->tmp.p, s))) return e;
+            k_level_end<<<1, 1, 0, s>>>(dc, lvl, total, P->cap.nodes, lvl == levels - 1); count_launch();
+            if (lvl < levels - 1) {
+                k_make_children<<<grid_for(width), 256, 0, s>>>(keys, 0, 0, lvl, flags, pos, P->n_prefix.as<uint64_t>(),
+                                                               P->n_level.as<int>(), P->n_first.as<int>(),
+                                                               P->n_count.as<int>(), P->n_child0.as<int>(),
+                                                               P->n_parent.as<int>(), dc); count_launch();
+            }
+        }
+        P->n_nodes = P->cap.nodes;
+        return cudaGetLastError();
+    }
     P->n_nodes = 0;
     if ((e = grow(12 + 4 * 1024))) return e;
     k_level0<<<1, 32, 0, s>>>(keys, n, P->n_prefix.as<uint64_t>(), P->n_level.as<int>(), P->n_first.as<int>(),
@@ -219,16 +297,19 @@ cudaError_t build_tree(sfmm_plan_s* P, const uint64_t* keys, int64_t n, int m, i
     P->level_start.assign(1, 0);
     P->level_start.push_back(12);
     int lvl = 0;
+    int64_t max_width = 12;
     while (true) {
         const int a = P->level_start[lvl], b = P->level_start[lvl + 1];
         const int width = b - a;
         if (width == 0 || lvl >= max_depth) break;
+        max_width = std::max<int64_t>(max_width, width);
         if ((e = ensure(P->flags, (size_t)width * 8))) return e;
         if ((e = ensure(P->pos, (size_t)width * 8))) return e;
         if ((e = ensure(P->tmp, scan_tmp_bytes(width)))) return e;
         int64_t* flags = P->flags.as<int64_t>();
         int64_t* pos = P->pos.as<int64_t>();
-        k_split_flags<<<grid_for(width), 256, 0, s>>>(P->n_count.as<int>(), a, b, lvl, m, max_depth, flags); count_launch();
+        k_split_flags<<<grid_for(width), 256, 0, s>>>(P->n_count.as<int>(), a, b, lvl, m, max_depth, flags, nullptr,
+                                                       0); count_launch();
         int64_t* total = P->small.as<int64_t>();
         if ((e = exclusive_scan_i64(flags, pos, width, total, P->tmp.p, s))) return e;
         int64_t splits = 0;
@@ -239,11 +320,12 @@ cudaError_t build_tree(sfmm_plan_s* P, const uint64_t* keys, int64_t n, int m, i
         k_make_children<<<grid_for(width), 256, 0, s>>>(keys, a, b, lvl, flags, pos, P->n_prefix.as<uint64_t>(),
                                                        P->n_level.as<int>(), P->n_first.as<int>(),
                                                        P->n_count.as<int>(), P->n_child0.as<int>(),
-                                                       P->n_parent.as<int>()); count_launch();
+                                                       P->n_parent.as<int>(), nullptr); count_launch();
         P->n_nodes = b + 4 * splits;
         P->level_start.push_back((int)P->n_nodes);
         ++lvl;
     }
+    P->last_max_width = max_width;
     return cudaGetLastError();
 }
 
@@ -252,7 +334,8 @@ cudaError_t tree_geometry(sfmm_plan_s* P)
     cudaError_t e;
     const int64_t nn = P->n_nodes;
     if ((e = ensure(P->n_geom, (size_t)nn * GEOM_STRIDE * 8))) return e;
-    k_geometry<<<grid_for(nn), 256, 0, P->stream>>>((int)nn, P->n_prefix.as<uint64_t>(), P->n_level.as<int>(),
+    k_geometry<<<grid_for(nn), 256, 0, P->stream>>>((int)nn, P->gm ? &P->dcnt.as<DevCounts>()->nn : nullptr,
+                                                    P->n_prefix.as<uint64_t>(), P->n_level.as<int>(),
                                                     P->n_geom.as<double>()); count_launch();
     return cudaGetLastError();
 }
@@ -263,13 +346,15 @@ cudaError_t tree_target_ranges(sfmm_plan_s* P, const uint64_t* tkeys, int64_t M)
     const int64_t nn = P->n_nodes;
     if ((e = ensure(P->n_tfirst, (size_t)nn * 4))) return e;
     if ((e = ensure(P->n_tcount, (size_t)nn * 4))) return e;
-    k_target_ranges<<<grid_for(nn), 256, 0, P->stream>>>((int)nn, P->n_prefix.as<uint64_t>(), P->n_level.as<int>(),
-                                                         tkeys, M, P->n_tfirst.as<int>(), P->n_tcount.as<int>()); count_launch();
+    k_target_ranges<<<grid_for(nn), 256, 0, P->stream>>>((int)nn, P->gm ? &P->dcnt.as<DevCounts>()->nn : nullptr,
+                                                         P->n_prefix.as<uint64_t>(), P->n_level.as<int>(), tkeys, M,
+                                                         P->n_tfirst.as<int>(), P->n_tcount.as<int>()); count_launch();
     return cudaGetLastError();
 }
 
-// Indices of the leaves whose `cnt` (source or target count) is positive.
-cudaError_t collect_leaves(sfmm_plan_s* P, const int* cnt, sfmm::Buf& out, int64_t* n_out)
+// Indices of the leaves whose `cnt` (source or target count) is positive.  Graph
+// mode: the count goes to *d_out on the device (no synchronisation).
+cudaError_t collect_leaves(sfmm_plan_s* P, const int* cnt, sfmm::Buf& out, int64_t* n_out, int64_t* d_out)
 {
     cudaError_t e;
     const int64_t nn = P->n_nodes;
@@ -278,10 +363,15 @@ cudaError_t collect_leaves(sfmm_plan_s* P, const int* cnt, sfmm::Buf& out, int64
     if ((e = ensure(P->pos, (size_t)nn * 8))) return e;
     if ((e = ensure(P->tmp, scan_tmp_bytes(nn)))) return e;
     if ((e = ensure(out, (size_t)nn * 4))) return e;
-    k_collect_leaves<<<grid_for(nn), 256, 0, s>>>((int)nn, P->n_child0.as<int>(), cnt, P->flags.as<int64_t>()); count_launch();
-    int64_t* total = P->small.as<int64_t>() + 1;
+    const int64_t* d_nn = P->gm ? &P->dcnt.as<DevCounts>()->nn : nullptr;
+    k_collect_leaves<<<grid_for(nn), 256, 0, s>>>((int)nn, d_nn, P->n_child0.as<int>(), cnt, P->flags.as<int64_t>()); count_launch();
+    int64_t* total = P->gm ? d_out : P->small.as<int64_t>() + 1;
     if ((e = exclusive_scan_i64(P->flags.as<int64_t>(), P->pos.as<int64_t>(), nn, total, P->tmp.p, s))) return e;
     k_compact<<<grid_for(nn), 256, 0, s>>>((int)nn, P->flags.as<int64_t>(), P->pos.as<int64_t>(), out.as<int>()); count_launch();
+    if (P->gm) {
+        *n_out = nn;          // the capacity: launches over the leaves read *d_out
+        return cudaGetLastError();
+    }
     if ((e = cudaMemcpyAsync(n_out, total, 8, cudaMemcpyDeviceToHost, s))) return e;
     return cudaStreamSynchronize(s);
 }

@@ -109,9 +109,13 @@ __device__ __forceinline__ void ld_row(dflt* row, const dflt* e, int p, int P)
 
 // ----------------------------------------------------------------- M2M
 template <int P>
-__global__ void __launch_bounds__(128) k_m2m_df(TreeView T, int c0, int c1, int p, const XGeoDF* __restrict__ geo,
-                                                dflt* __restrict__ mpole)
+__global__ void __launch_bounds__(128) k_m2m_df(TreeView T, int c0, int c1, int lvl, int p,
+                                                const XGeoDF* __restrict__ geo, dflt* __restrict__ mpole)
 {
+    if (T.d_level) {              // graph mode: the children are the nodes of level lvl + 1
+        c0 = (int)T.d_level[lvl + 1];
+        c1 = (int)T.d_level[lvl + 2];
+    }
     constexpr int RS = 2 * P + 3;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     dflt* rows = reinterpret_cast<dflt*>(smem_raw);
@@ -148,9 +152,14 @@ __global__ void __launch_bounds__(128) k_m2m_df(TreeView T, int c0, int c1, int 
 
 // ----------------------------------------------------------------- L2L
 template <int P>
-__global__ void __launch_bounds__(128) k_l2l_df(TreeView T, int a, int b, int p, const XGeoDF* __restrict__ geo,
-                                                const double* __restrict__ acc, dflt* __restrict__ local)
+__global__ void __launch_bounds__(128) k_l2l_df(TreeView T, int a, int b, int lvl, int p,
+                                                const XGeoDF* __restrict__ geo, const double* __restrict__ acc,
+                                                dflt* __restrict__ local)
 {
+    if (T.d_level) {              // graph mode: the nodes of level lvl
+        a = (int)T.d_level[lvl];
+        b = (int)T.d_level[lvl + 1];
+    }
     constexpr int RS = 2 * P + 3;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     dflt* row = reinterpret_cast<dflt*>(smem_raw) + threadIdx.x * RS;
@@ -186,10 +195,11 @@ __global__ void __launch_bounds__(128) k_l2l_df(TreeView T, int a, int b, int p,
 // sums columns k and k + 32 over the leaf's sources, and the multipole is
 // Q = sum q / 4pi, C = (1/4pi) sum q log(..) - Q log 2, A_l = -(1/(4 pi l)) sum q z^l.
 template <int P>
-__global__ void __launch_bounds__(128) k_p2m_df_leaf(TreeView T, const int* __restrict__ leaves, int64_t n_leaves,
-                                                     const float4* __restrict__ off, const float4* __restrict__ log_tab,
-                                                     int p, dflt* __restrict__ mpole)
+__global__ void __launch_bounds__(128) k_p2m_df_leaf(TreeView T, const int* __restrict__ leaves, int64_t n_cap,
+                                                     const int64_t* d_nl, const float4* __restrict__ off,
+                                                     const float4* __restrict__ log_tab, int p, dflt* __restrict__ mpole)
 {
+    const int64_t n_leaves = dcount(d_nl, n_cap);
     constexpr int RS = 2 * P + 3;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ float4 s_tab[129];
@@ -269,39 +279,39 @@ cudaError_t smem_attr(K kern, size_t smem)
 }
 
 template <int P>
-cudaError_t m2m_p(const TreeView& T, int c0, int c1, int p, const void* geo, void* mpole, cudaStream_t s)
+cudaError_t m2m_p(const TreeView& T, int c0, int c1, int lvl, int p, const void* geo, void* mpole, cudaStream_t s)
 {
     const size_t smem = (size_t)128 * (2 * P + 3) * sizeof(dflt);
     cudaError_t e;
     if ((e = smem_attr(k_m2m_df<P>, smem))) return e;
-    k_m2m_df<P><<<grid_of(c1 - c0, 128, 152 * 16), 128, smem, s>>>(T, c0, c1, p, static_cast<const XGeoDF*>(geo),
+    k_m2m_df<P><<<grid_of(c1 - c0, 128, 152 * 16), 128, smem, s>>>(T, c0, c1, lvl, p, static_cast<const XGeoDF*>(geo),
                                                                    static_cast<dflt*>(mpole));
     count_launch();
     return cudaGetLastError();
 }
 
 template <int P>
-cudaError_t l2l_p(const TreeView& T, int a, int b, int p, const void* geo, const double* acc, void* local,
+cudaError_t l2l_p(const TreeView& T, int a, int b, int lvl, int p, const void* geo, const double* acc, void* local,
                   cudaStream_t s)
 {
     const size_t smem = (size_t)128 * (2 * P + 3) * sizeof(dflt);
     cudaError_t e;
     if ((e = smem_attr(k_l2l_df<P>, smem))) return e;
-    k_l2l_df<P><<<grid_of(b - a, 128, 152 * 16), 128, smem, s>>>(T, a, b, p, static_cast<const XGeoDF*>(geo), acc,
+    k_l2l_df<P><<<grid_of(b - a, 128, 152 * 16), 128, smem, s>>>(T, a, b, lvl, p, static_cast<const XGeoDF*>(geo), acc,
                                                                  static_cast<dflt*>(local));
     count_launch();
     return cudaGetLastError();
 }
 
 template <int P>
-cudaError_t p2m_p(const TreeView& T, const int* leaves, int64_t n_leaves, const float4* off, const float4* log_tab,
-                  int p, void* mpole, cudaStream_t s)
+cudaError_t p2m_p(const TreeView& T, const int* leaves, int64_t n_leaves, const int64_t* d_nl, const float4* off,
+                  const float4* log_tab, int p, void* mpole, cudaStream_t s)
 {
     const size_t smem = (size_t)UW * 32 * (2 * P + 3) * sizeof(dflt);
     cudaError_t e;
     if ((e = smem_attr(k_p2m_df_leaf<P>, smem))) return e;
-    k_p2m_df_leaf<P><<<grid_of(n_leaves, UW, 152 * 32), UW * 32, smem, s>>>(T, leaves, n_leaves, off, log_tab, p,
-                                                                              static_cast<dflt*>(mpole));
+    k_p2m_df_leaf<P><<<grid_of(n_leaves, UW, 152 * 32), UW * 32, smem, s>>>(T, leaves, n_leaves, d_nl, off, log_tab,
+                                                                              p, static_cast<dflt*>(mpole));
     count_launch();
     return cudaGetLastError();
 }
@@ -315,30 +325,34 @@ cudaError_t p2m_p(const TreeView& T, const int* leaves, int64_t n_leaves, const 
 
 }  // namespace
 
-// children c0..c1-1 (one level) -> their parents' multipoles
-cudaError_t launch_m2m_df(const TreeView& T, int c0, int c1, int p, const void* geo, void* mpole, cudaStream_t s)
-{
-    if (c1 <= c0) return cudaSuccess;
-#define CALL(PP) m2m_p<PP>(T, c0, c1, p, geo, mpole, s)
-    SFMM_P_SWITCH(CALL)
-#undef CALL
-}
-
-// nodes a..b-1 (one level): local = M2L sum (acc) + L2L of the parent's local
-cudaError_t launch_l2l_df(const TreeView& T, int a, int b, int p, const void* geo, const double* acc, void* local,
+// children c0..c1-1 (the nodes of level lvl + 1) -> their parents' multipoles.
+// Graph mode (T.d_level set): the bounds are read on the device and c1 - c0 is
+// the level-width capacity the launch is sized for.
+cudaError_t launch_m2m_df(const TreeView& T, int c0, int c1, int lvl, int p, const void* geo, void* mpole,
                           cudaStream_t s)
 {
-    if (b <= a) return cudaSuccess;
-#define CALL(PP) l2l_p<PP>(T, a, b, p, geo, acc, local, s)
+    if (c1 <= c0) return cudaSuccess;
+#define CALL(PP) m2m_p<PP>(T, c0, c1, lvl, p, geo, mpole, s)
     SFMM_P_SWITCH(CALL)
 #undef CALL
 }
 
-cudaError_t launch_p2m_df_leaf(const TreeView& T, const int* leaves, int64_t n_leaves, const float4* off,
-                               const float4* log_tab, int p, void* mpole, cudaStream_t s)
+// nodes a..b-1 (level lvl): local = M2L sum (acc) + L2L of the parent's local.
+// Graph mode as for launch_m2m_df.
+cudaError_t launch_l2l_df(const TreeView& T, int a, int b, int lvl, int p, const void* geo, const double* acc,
+                          void* local, cudaStream_t s)
+{
+    if (b <= a) return cudaSuccess;
+#define CALL(PP) l2l_p<PP>(T, a, b, lvl, p, geo, acc, local, s)
+    SFMM_P_SWITCH(CALL)
+#undef CALL
+}
+
+cudaError_t launch_p2m_df_leaf(const TreeView& T, const int* leaves, int64_t n_leaves, const int64_t* d_nl,
+                               const float4* off, const float4* log_tab, int p, void* mpole, cudaStream_t s)
 {
     if (n_leaves == 0) return cudaSuccess;
-#define CALL(PP) p2m_p<PP>(T, leaves, n_leaves, off, log_tab, p, mpole, s)
+#define CALL(PP) p2m_p<PP>(T, leaves, n_leaves, d_nl, off, log_tab, p, mpole, s)
     SFMM_P_SWITCH(CALL)
 #undef CALL
 }

@@ -74,7 +74,8 @@ struct __align__(64) MacNode32 {
 __global__ void k_mac_nodes(TreeView T, double c_s, double c_t, double sigma, MacNode* __restrict__ out,
                             MacNode32* __restrict__ out32)
 {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < T.n_nodes; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t nn = dcount(T.d_nn, T.n_nodes);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nn; i += (int64_t)gridDim.x * blockDim.x) {
         const double R = T.geom[(size_t)i * GEOM_STRIDE + 9];
         MacNode m;
         sincos(0.5 * R, &m.s1, &m.c1);
@@ -333,9 +334,10 @@ __global__ void __launch_bounds__(WT) k_walk_emit(TreeView T, const int2* __rest
     }
 }
 
-__global__ void k_csr_offsets(const uint64_t* __restrict__ sorted_t, int64_t n_pairs, int n_nodes,
+__global__ void k_csr_offsets(const uint64_t* __restrict__ sorted_t, int64_t n_cap, const int64_t* d_np, int n_nodes,
                               int64_t* __restrict__ off)
 {
+    const int64_t n_pairs = dcount(d_np, n_cap);
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i <= n_nodes; i += (int64_t)gridDim.x * blockDim.x) {
         int64_t lo = 0, hi = n_pairs;
         while (lo < hi) {
@@ -344,6 +346,24 @@ __global__ void k_csr_offsets(const uint64_t* __restrict__ sorted_t, int64_t n_p
         }
         off[i] = lo;
     }
+}
+
+// Graph mode: the list entries past the walk's count get a target key that sorts
+// after every node (all ones in the sorted bits), so that sorting the whole
+// capacity sorts the list.
+__global__ void k_pad_pairs(uint64_t* __restrict__ t, uint32_t* __restrict__ src, const int64_t* __restrict__ n,
+                            int64_t cap, uint64_t key)
+{
+    for (int64_t i = *n + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cap; i += (int64_t)gridDim.x * blockDim.x) {
+        t[i] = key;
+        src[i] = 0u;
+    }
+}
+
+// Graph mode: a walk that overflowed its capacities or left a frontier voids the solve.
+__global__ void k_walk_check(const int64_t* __restrict__ ctr, int left_slot, DevCounts* dc)
+{
+    if (ctr[C_OVERFLOW] || ctr[left_slot] != 0) dc->overflow = 1;
 }
 
 inline unsigned grid_for(int64_t n, int threads = 256)
@@ -364,10 +384,15 @@ inline int bits_for(int64_t n)
 }  // namespace
 
 // Run Algorithm 1 and build the grouped M2L and P2P lists in the plan.
+//
+// Graph mode (plan->gm): no synchronisation.  The walk runs 2 (level capacity) + 4
+// rounds into buffers of the plan's list capacities; the pair counts stay on the
+// device (plan->d_m2l, plan->d_p2p), the entries past them are padded to sort
+// last and the whole capacity is sorted; an overflow of the walk voids the solve.
 cudaError_t build_lists(sfmm_plan_s* P, const TreeView& T, double c_s, double c_t, cudaStream_t s)
 {
     cudaError_t e;
-    const int depth = (int)P->level_start.size() - 2;
+    const int depth = P->gm ? (int)P->cap.levels : (int)P->level_start.size() - 2;
     const int rounds = 2 * depth + 4;
     int64_t* ctr = P->small.as<int64_t>() + 24;      // [24..29] counters, [30..32] bases
     int64_t* bases = ctr + 6;
@@ -375,6 +400,11 @@ cudaError_t build_lists(sfmm_plan_s* P, const TreeView& T, double c_s, double c_
     int64_t cap_front = std::max<int64_t>(P->walk_cap_front, std::max<int64_t>(4096, 32 * P->n_nodes));
     int64_t cap_m2l = std::max<int64_t>(P->walk_cap_m2l, std::max<int64_t>(4096, 48 * P->n_nodes));
     int64_t cap_p2p = std::max<int64_t>(P->walk_cap_p2p, std::max<int64_t>(4096, 16 * P->n_nodes));
+    if (P->gm) {
+        cap_front = P->cap.front;
+        cap_m2l = P->cap.m2l;
+        cap_p2p = P->cap.p2p;
+    }
     if ((e = ensure(P->macn, (size_t)P->n_nodes * sizeof(MacNode))) ||
         (e = ensure(P->macn32, (size_t)P->n_nodes * sizeof(MacNode32))))
         return e;
@@ -408,6 +438,14 @@ cudaError_t build_lists(sfmm_plan_s* P, const TreeView& T, double c_s, double c_
             count_launch();
         }
         if ((e = cudaGetLastError())) return e;
+        if (P->gm) {
+            k_walk_check<<<1, 1, 0, s>>>(ctr, (rounds & 1) ? C_FRONT1 : C_FRONT0, P->dcnt.as<DevCounts>()); count_launch();
+            P->n_m2l = cap_m2l;
+            P->n_p2p = cap_p2p;
+            P->d_m2l = ctr + C_M2L;
+            P->d_p2p = ctr + C_P2P;
+            break;
+        }
         int64_t h[6];
         if ((e = cudaMemcpyAsync(h, ctr, sizeof h, cudaMemcpyDeviceToHost, s))) return e;
         if ((e = cudaStreamSynchronize(s))) return e;
@@ -429,6 +467,15 @@ cudaError_t build_lists(sfmm_plan_s* P, const TreeView& T, double c_s, double c_
     const int64_t n_m2l = P->n_m2l, n_p2p = P->n_p2p;
     // group by target box (stable), then CSR offsets
     const int bits = bits_for(P->n_nodes);
+    if (P->gm) {
+        const uint64_t pad = (bits >= 64) ? ~0ull : ((1ull << bits) - 1ull);
+        k_pad_pairs<<<grid_for(n_m2l), 256, 0, s>>>(P->m2l_t.as<uint64_t>(), P->m2l_s.as<uint32_t>(), P->d_m2l, n_m2l,
+                                                    pad); count_launch();
+        k_pad_pairs<<<grid_for(n_p2p), 256, 0, s>>>(P->p2p_t.as<uint64_t>(), P->p2p_s.as<uint32_t>(), P->d_p2p, n_p2p,
+                                                    pad); count_launch();
+    } else {
+        P->d_m2l = P->d_p2p = nullptr;
+    }
     if ((e = ensure(P->m2l_t2, (size_t)std::max<int64_t>(n_m2l, 1) * 8)) ||
         (e = ensure(P->m2l_s2, (size_t)std::max<int64_t>(n_m2l, 1) * 4)))
         return e;
@@ -446,8 +493,10 @@ cudaError_t build_lists(sfmm_plan_s* P, const TreeView& T, double c_s, double c_
         return e;
     const uint64_t* mt = P->m2l_alt ? P->m2l_t2.as<uint64_t>() : P->m2l_t.as<uint64_t>();
     const uint64_t* pt = P->p2p_alt ? P->p2p_t2.as<uint64_t>() : P->p2p_t.as<uint64_t>();
-    k_csr_offsets<<<grid_for(P->n_nodes + 1), 256, 0, s>>>(mt, n_m2l, (int)P->n_nodes, P->m2l_off.as<int64_t>()); count_launch();
-    k_csr_offsets<<<grid_for(P->n_nodes + 1), 256, 0, s>>>(pt, n_p2p, (int)P->n_nodes, P->p2p_off.as<int64_t>()); count_launch();
+    k_csr_offsets<<<grid_for(P->n_nodes + 1), 256, 0, s>>>(mt, n_m2l, P->d_m2l, (int)P->n_nodes,
+                                                           P->m2l_off.as<int64_t>()); count_launch();
+    k_csr_offsets<<<grid_for(P->n_nodes + 1), 256, 0, s>>>(pt, n_p2p, P->d_p2p, (int)P->n_nodes,
+                                                           P->p2p_off.as<int64_t>()); count_launch();
     return cudaGetLastError();
 }
 

@@ -21,7 +21,8 @@ SFMM_FP64, SFMM_MIXED, SFMM_MIXED_DF, SFMM_FP32 = 0, 1, 2, 3
 EXPORTS = ["sfmm_default_options", "sfmm_plan", "sfmm_potential", "sfmm_deflection", "sfmm_deflection_host",
            "sfmm_adjoint", "sfmm_shear", "sfmm_deflection_batch",
            "sfmm_destroy", "sfmm_last_error", "sfmm_order", "sfmm_get_stats", "sfmm_set_timing",
-           "sfmm_debug_copy", "sfmm_keys", "sfmm_sort_keys_static", "sfmm_peak_rate", "sfmm_set_wait_limit"]
+           "sfmm_debug_copy", "sfmm_keys", "sfmm_sort_keys_static", "sfmm_peak_rate", "sfmm_set_wait_limit",
+           "sfmm_graph_capture", "sfmm_graph_launch", "sfmm_graph_info", "sfmm_graph_release"]
 STATIC_SORT_MAX_N = 1 << 18
 
 
@@ -37,6 +38,12 @@ class Stats(ctypes.Structure):
                 ("n_m2l", ctypes.c_int64), ("n_p2p", ctypes.c_int64), ("p2p_interactions", ctypes.c_int64),
                 ("launches", ctypes.c_int64),
                 ("ms", ctypes.c_double * 8)]
+
+
+class GraphStats(ctypes.Structure):
+    _fields_ = [("n_shells", ctypes.c_int64), ("kernel_nodes", ctypes.c_int64), ("launches", ctypes.c_int64),
+                ("overflows", ctypes.c_int64), ("recaptures", ctypes.c_int64), ("n_nodes", ctypes.c_int64),
+                ("n_leaves", ctypes.c_int64), ("n_m2l", ctypes.c_int64), ("n_p2p", ctypes.c_int64)]
 
 
 class SfmmError(RuntimeError):
@@ -98,6 +105,14 @@ def load(build_if_missing=True):
     L.sfmm_set_wait_limit.restype = ci
     L.sfmm_peak_rate.argtypes = [ci, ctypes.POINTER(ctypes.c_double), vp]
     L.sfmm_peak_rate.restype = ci
+    L.sfmm_graph_capture.argtypes = [vp, ci, pp, pp, ctypes.POINTER(i64), pp, ctypes.POINTER(i64), pp, pp, cd_]
+    L.sfmm_graph_capture.restype = ci
+    L.sfmm_graph_launch.argtypes = [vp]
+    L.sfmm_graph_launch.restype = ci
+    L.sfmm_graph_info.argtypes = [vp, ctypes.POINTER(GraphStats)]
+    L.sfmm_graph_info.restype = ci
+    L.sfmm_graph_release.argtypes = [vp]
+    L.sfmm_graph_release.restype = ci
     _lib = L
     return L
 
@@ -238,6 +253,50 @@ class Plan:
                                           a_alpha, lanes)
         _check(st, self._h)
         return outs
+
+    def graph_capture(self, shells, with_psi=True, slack=0.25):
+        """Bind this plan to shells [(src, q, tgt), ...] (device tensors, kept
+        referenced by the plan) and record their solves into one CUDA graph
+        (sfmm_graph_capture; the returned outputs already hold one solve).
+        Returns [(psi or None, alpha), ...]: the buffers every graph_launch()
+        rewrites.  Update the shells' tensors in place between launches."""
+        import torch
+        n = len(shells)
+        V = ctypes.c_void_p * max(n, 1)
+        I = ctypes.c_int64 * max(n, 1)
+        a_src, a_q, a_tgt, a_psi, a_alpha = V(), V(), V(), V(), V()
+        a_n, a_m = I(), I()
+        outs = []
+        for i, (src, q, tgt) in enumerate(shells):
+            M = tgt.shape[0]
+            alpha = torch.empty((M, 2), dtype=torch.float64, device=tgt.device)
+            psi = torch.empty(M, dtype=torch.float64, device=tgt.device) if with_psi else None
+            a_src[i] = _dptr(src, torch.float64, 3, "src")
+            a_q[i] = _dptr(q, self._qdtype(), None, "q")
+            a_tgt[i] = _dptr(tgt, torch.float64, 3, "tgt")
+            a_psi[i] = _dptr(psi, torch.float64, None, "psi") if with_psi else None
+            a_alpha[i] = _dptr(alpha, torch.float64, 2, "alpha")
+            a_n[i], a_m[i] = src.shape[0], M
+            outs.append((psi, alpha))
+        self._graph_refs = None
+        st = load().sfmm_graph_capture(self._h, n, a_src, a_q, a_n, a_tgt, a_m, a_psi if with_psi else None,
+                                       a_alpha, float(slack))
+        _check(st, self._h)
+        self._graph_refs = (list(shells), outs)
+        return outs
+
+    def graph_launch(self):
+        """Replay the recorded graph (sfmm_graph_launch); synchronous."""
+        _check(load().sfmm_graph_launch(self._h), self._h)
+
+    def graph_info(self):
+        g = GraphStats()
+        _check(load().sfmm_graph_info(self._h, ctypes.byref(g)), self._h)
+        return {k: getattr(g, k) for k, _ in GraphStats._fields_}
+
+    def graph_release(self):
+        _check(load().sfmm_graph_release(self._h), self._h)
+        self._graph_refs = None
 
     def shear(self, src, q, tgt, with_psi=False, with_alpha=False, with_mu=False):
         """(gamma [M, 2], psi or None, alpha or None, mu or None) at the targets:
