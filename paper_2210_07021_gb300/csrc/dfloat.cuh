@@ -178,6 +178,47 @@ __device__ __forceinline__ dflt dfl_sub_exact(double a, double b)
     return dfl_fast_two_sum(hi, lo);
 }
 
+// sqrt of a double-float x >= 0: the FP32 root and one correction from the exact remainder
+__device__ __forceinline__ dflt dfl_sqrt(dflt x)
+{
+    if (!(x.h > 0.f)) return dflt(0.f, 0.f);
+    const float s = sqrtf(x.h);
+    const float r = __fadd_rn(__fmaf_rn(-s, s, x.h), x.l);
+    return dfl_fast_two_sum(s, __fdiv_rn(r, __fmul_rn(2.f, s)));
+}
+
+// 1/k as double-float pairs, k = 1..12 (rounded from FP64 at compile time)
+struct InvTabDF {
+    float h[13], l[13];
+};
+constexpr InvTabDF make_inv_tab()
+{
+    InvTabDF t{};
+    for (int k = 1; k <= 12; ++k) {
+        const double v = 1.0 / k;
+        t.h[k] = (float)v;
+        t.l[k] = (float)(v - (double)(float)v);
+    }
+    return t;
+}
+namespace {
+__constant__ InvTabDF kInvDF = make_inv_tab();
+}  // namespace
+
+// log(1 - x) for a double-float 0 <= x < 1, to double-float accuracy relative
+// to the result: below x = 2^-5 the series -x (1 + x/2 + ... + x^11/12)
+// (remainder under x^13/13 < 2^-64 x), else the table logarithm of 1 - x
+// (whose absolute error 2^-48 is then below 2^-43 of the result).
+__device__ __forceinline__ dflt dfl_log1m(dflt x, const float4* tab)
+{
+    if (x.h < 0.03125f) {
+        dflt acc(kInvDF.h[12], kInvDF.l[12]);
+        for (int k = 11; k >= 1; --k) acc = dflt(kInvDF.h[k], kInvDF.l[k]) + x * acc;
+        return -(x * acc);
+    }
+    return dfl_norm(dfl_log_lazy(dflt(1.f, 0.f) - x, tab));
+}
+
 __device__ __forceinline__ dflt dfl_shfl_up(dflt v, int o)
 {
     return dflt(__shfl_up_sync(0xffffffffu, v.h, o), __shfl_up_sync(0xffffffffu, v.l, o));

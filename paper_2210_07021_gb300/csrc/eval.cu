@@ -36,6 +36,9 @@ constexpr double PI = 3.14159265358979323846;
 constexpr double INV2PI = 0.15915494309189533577;
 constexpr double LOG2 = 0.69314718055994530942;
 constexpr double LOG4 = 1.3862943611198906188;
+constexpr float FLT_MIN_F = 1.17549435e-38f;     // the smallest normal FP32 number
+constexpr float LN2_H = 0.693147182464599609375f;   // log 2 rounded to FP32
+constexpr float LN2_L = -1.9046542121259336e-09f;   // log 2 - LN2_H
 
 struct EvalArgs {
     TreeView T;
@@ -450,19 +453,30 @@ __device__ __forceinline__ float rcp_approx(float x)
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
     return r;
 }
+// base-2 logarithm, approximate, subnormal input flushed to zero: the pair
+// loop's d^2 is either at least FLT_MIN or the pair is treated as coincident
+__device__ __forceinline__ float lg2_approx(float x)
+{
+    float r;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
 
 // Near-field sums of one target over the staged source pairs P = sub, sub + lpt,
 // ...: blocks of (up to) 16 pairs per lane in packed FP32 (the two halves sum
 // the even and the odd sources), then the outer FP32 level acc.  The logarithm
 // is accumulated in base 2 (acc[4] = sum q log2 d^2).  1/d^2 is the
-// approximate reciprocal (as in __fdividef).
+// approximate reciprocal (as in __fdividef).  The mass sum acc[3] is the same
+// for every target of the stage: it is added once per target from the stage's
+// total (stage_q), less the mass of the sources a target skips.
 //
-// A source at the target's own position (d^2 = 0) is left out.  The masked
-// block tests every pair for it; the plain block does not: there 1/d^2 = inf
-// and its x sum turns inf or NaN (d = 0 gives inf * 0), so a plain block whose
-// x sum is not finite is summed again masked.  When the targets are the
-// sources themselves every target meets one such block; there (MASK) every
-// block is masked.
+// A source at the target's own position (d^2 = 0, or below FLT_MIN, where the
+// flushed reciprocal and logarithm are not finite) is left out.  The masked
+// block tests every pair for it and sums the mass it skips (iq); the plain
+// block does not test: there 1/d^2 = inf and its x sum turns inf or NaN, so a
+// plain block whose x sum is not finite is summed again masked.  When the
+// targets are the sources themselves every target meets one such block; there
+// (MASK) every block is masked.
 template <bool PSI, bool MASKED>
 __device__ __forceinline__ void pair_block32(const Stage32& S, int P0, int P1, int lpt, const float2& tx,
                                              const float2& ty, const float2& tz, const float2& ux, const float2& uy,
@@ -480,7 +494,8 @@ __device__ __forceinline__ void pair_block32(const Stage32& S, int P0, int P1, i
         float2 q = f2(b.z, b.w);
         float2 den = d2;
         if (MASKED) {
-            const bool oka = d2.x > 0.f, okb = d2.y > 0.f;
+            const bool oka = d2.x >= FLT_MIN_F, okb = d2.y >= FLT_MIN_F;
+            iq = __fadd2_rn(iq, f2(oka ? 0.f : q.x, okb ? 0.f : q.y));     // the mass skipped
             q = f2(oka ? q.x : 0.f, okb ? q.y : 0.f);
             den = f2(oka ? d2.x : 1.f, okb ? d2.y : 1.f);
         }
@@ -488,8 +503,7 @@ __device__ __forceinline__ void pair_block32(const Stage32& S, int P0, int P1, i
         ix = __ffma2_rn(wq, dx, ix);
         iy = __ffma2_rn(wq, dy, iy);
         iz = __ffma2_rn(wq, dz, iz);
-        iq = __fadd2_rn(iq, q);
-        if (PSI) il = __ffma2_rn(q, f2(__log2f(den.x), __log2f(den.y)), il);
+        if (PSI) il = __ffma2_rn(q, f2(lg2_approx(den.x), lg2_approx(den.y)), il);
     }
 }
 
@@ -498,10 +512,11 @@ __device__ __forceinline__ void pair_block32(const Stage32& S, int P0, int P1, i
 // path whose far field is carried in double-float.
 template <bool PSI, bool MASK, bool COMP>
 __device__ __forceinline__ void pair_sums32(const Stage32& S, int npair, int sub, int lpt, const float4& th,
-                                            const float4& tl, float* acc, float* accl)
+                                            const float4& tl, float stage_q, float* acc, float* accl)
 {
     const float2 tx = f2(th.x, th.x), ty = f2(th.y, th.y), tz = f2(th.z, th.z);
     const float2 ux = f2(tl.x, tl.x), uy = f2(tl.y, tl.y), uz = f2(tl.z, tl.z);
+    if (sub == 0) acc[3] += stage_q;          // once per target (its lanes' sums are added up)
     for (int P = sub; P < npair;) {
         const int pend = min(npair, P + 16 * lpt);
         float2 ix = f2(0.f, 0.f), iy = ix, iz = ix, iq = ix, il = ix;   // inner FP32 level
@@ -519,7 +534,7 @@ __device__ __forceinline__ void pair_sums32(const Stage32& S, int npair, int sub
         } else {
             acc[0] += ix.x + ix.y; acc[1] += iy.x + iy.y; acc[2] += iz.x + iz.y;
         }
-        acc[3] += iq.x + iq.y; acc[4] += il.x + il.y;
+        acc[3] -= iq.x + iq.y; acc[4] += il.x + il.y;
         P = pend;
     }
 }
@@ -778,6 +793,7 @@ __global__ void __launch_bounds__(128, 7) k_eval32(Eval32Args A)
                 // pre[i] <= idx, found by stepping on from the previous position's leaf; its
                 // offset is moved from its leaf's centre to the target leaf's (two-sum with the
                 // near leaf's centre offset) and stored negated in the pair-packed stage
+                float sq = 0.f;        // mass staged by this lane
                 for (int idx = lane, lo = 0; idx < ns; idx += 32) {
                     while (lo + 1 < nl && pre[lo + 1] <= idx) ++lo;
                     const size_t j = (size_t)(fst[lo] + (idx - pre[lo]));
@@ -797,6 +813,7 @@ __global__ void __launch_bounds__(128, 7) k_eval32(Eval32Args A)
                     pa[2 + c] = -sy;
                     pb[c] = -sz;
                     pb[2 + c] = h.w;
+                    sq += h.w;
                     pc[c] = -(ex_ + (l.x + d[3]));
                     pc[2 + c] = -(ey_ + (l.y + d[4]));
                     pd[c] = -(ez_ + (l.z + d[5]));
@@ -814,8 +831,9 @@ __global__ void __launch_bounds__(128, 7) k_eval32(Eval32Args A)
                 if (nfit == 0) jn += STAGE32;
                 else { kn += nfit; jn = 0; }
                 __syncwarp();
-                pair_sums32<PSI, MASK, DFAR>(S, (ns + 1) >> 1, sa, lpa, tha, tla, acc_a, accl_a);
-                if (nb) pair_sums32<PSI, MASK, DFAR>(S, (ns + 1) >> 1, sb, lpb, thb, tlb, acc_b, accl_b);
+                sq = group_sumf(sq, 32);
+                pair_sums32<PSI, MASK, DFAR>(S, (ns + 1) >> 1, sa, lpa, tha, tla, sq, acc_a, accl_a);
+                if (nb) pair_sums32<PSI, MASK, DFAR>(S, (ns + 1) >> 1, sb, lpb, thb, tlb, sq, acc_b, accl_b);
             }
             if (DFAR) {
                 dflt nfa[3], nfb[3];
@@ -881,10 +899,12 @@ __global__ void __launch_bounds__(128, 7) k_eval32(Eval32Args A)
 //   bits, log c_j and 1/c_j from a 128-entry table computed in FP64 on the host
 //   (a table-driven logarithm in the manner of Tang, ACM TOMS 16, 1990),
 //   |r| < 2^-7 so r - r^2/2 + ... + r^6/6 reaches double-float accuracy.
-// L2P (with FP64 local expansions) and the final combination are FP64.
+// L2P (double-float local expansions) and the final combination in double-float.
 // a - b for double-float a = (ah, al), b = (bh, bl): two-difference of the
 // leading parts, the tails added to its error, then renormalised -- for close
-// points the leading parts cancel and the difference lives in the tails
+// points the leading parts cancel and the difference lives in the tails (the
+// tails of the two offsets can then exceed the difference's own last place,
+// so the renormalisation is needed before its square is formed)
 __device__ __forceinline__ dflt dfl_diff(float ah, float al, float bh, float bl)
 {
     const dflt s = dfl_two_sum(ah, -bh);
@@ -913,6 +933,146 @@ struct EvalDfArgs {
     unsigned long long* leaf_ctr;   // zero at launch: the warps take target leaves from it one at a time
 };
 
+// Near-field sums of one target over the staged sources j = sub, sub + lpt, ...
+// in double-float: acc = (x, y, z sums of q d / d^2, sum q log d^2, the mass
+// skipped at coincident points).  EQM (every staged source has the same mass
+// qm): sum q log d^2 = qm log prod d^2, so per block of up to 16 sources the
+// lane multiplies the d^2 (their mantissas, in double-float, the exponents
+// summed as an integer) and takes one logarithm per block.
+template <bool PSI, bool EQM>
+__device__ __forceinline__ void pair_sums_df(const float4* __restrict__ yh, const float4* __restrict__ yl, int ns,
+                                             int sub, int lpt, const float4& th, const float4& tl, dflt qm,
+                                             const float4* __restrict__ tab, dflt* acc)
+{
+    for (int j0 = sub; j0 < ns; j0 += 16 * lpt) {
+        const int j1 = min(ns, j0 + 16 * lpt);
+        dflt prod(1.f, 0.f);
+        int ecnt = 0;
+        for (int j = j0; j < j1; j += lpt) {
+            const float4 h = yh[j];
+            const float4 l = yl[j];
+            // d = t - y
+            const dflt dx = dfl_diff(th.x, tl.x, h.x, l.x);
+            const dflt dy = dfl_diff(th.y, tl.y, h.y, l.y);
+            const dflt dz = dfl_diff(th.z, tl.z, h.z, l.z);
+            // d^2: exact squares of the leading parts, two exact two-sums
+            const float px = __fmul_rn(dx.h, dx.h), py = __fmul_rn(dy.h, dy.h), pz = __fmul_rn(dz.h, dz.h);
+            const float ex2 = __fmaf_rn(__fadd_rn(dx.h, dx.h), dx.l, __fmaf_rn(dx.h, dx.h, -px));
+            const float ey2 = __fmaf_rn(__fadd_rn(dy.h, dy.h), dy.l, __fmaf_rn(dy.h, dy.h, -py));
+            const float ez2 = __fmaf_rn(__fadd_rn(dz.h, dz.h), dz.l, __fmaf_rn(dz.h, dz.h, -pz));
+            const dflt s1 = dfl_two_sum(px, py);
+            const dflt s2 = dfl_two_sum(s1.h, pz);
+            dflt d2 = dfl_fast_two_sum(s2.h, __fadd_rn(__fadd_rn(s1.l, s2.l), __fadd_rn(__fadd_rn(ex2, ey2), ez2)));
+            // coincident pairs (d^2 below the normal range) contribute nothing; their mass is skipped
+            const bool ok = d2.h >= FLT_MIN_F;
+            dflt q = dflt(h.w, l.w);
+            if (!ok) {
+                acc[4] = acc[4] + q;
+                q = dflt(0.f, 0.f);
+                d2 = dflt(1.f, 0.f);
+            }
+            // 1/d^2: MUFU reciprocal (relative error < 2^-22; d^2 is normal here) and one Newton step
+            const float r0 = rcp_approx(d2.h);
+            const float e0 = __fmaf_rn(-d2.l, r0, __fmaf_rn(-d2.h, r0, 1.f));
+            const dflt wq = dfl_mul_lazy(dflt(r0, __fmul_rn(r0, e0)), q);
+            dfl_mac(acc[0], wq, dx);
+            dfl_mac(acc[1], wq, dy);
+            dfl_mac(acc[2], wq, dz);
+            if (PSI) {
+                if (EQM) {
+                    // d^2 = m 2^k, m in [1, 2): multiply the mantissas, sum the exponents
+                    const int k = (__float_as_int(d2.h) >> 23) - 127;
+                    const float sc = __int_as_float((127 - k) << 23);
+                    prod = prod * dflt(__fmul_rn(d2.h, sc), __fmul_rn(d2.l, sc));
+                    ecnt += k;
+                } else {
+                    dfl_mac(acc[3], dfl_log_lazy(d2, tab), q);
+                }
+            }
+        }
+        if (PSI && EQM) {
+            // log prod + ecnt log 2 (ecnt exact in FP32; log 2 as a double-float)
+            const dflt lg = dfl_norm(dfl_log_lazy(prod, tab)) + dflt((float)ecnt) * dflt(LN2_H, LN2_L);
+            dfl_mac(acc[3], lg, qm);
+        }
+    }
+}
+
+// A leaf's frame in double-float, formed once per leaf: e_theta, e_phi, the
+// centre c and 1/r, rounded from FP64.
+struct LeafFrameD2 {
+    dflt et[3], ep[3], c[3], inv_r;
+};
+
+// L2P in the leaf frame and the combination with the near field's sums for
+// sorted target tix, all in double-float (no FP64 instructions: this GPU's
+// FP64 pipe runs at 1/64 of the FP32 rate).  t = x - c from the target's
+// (hi, lo) offset; w = (t.e_theta + i t.e_phi) / (1 + x.c), 1 + x.c = 2 - |t|^2/2;
+// F(w) and F'(w) by Horner recurrences; alpha on the chart vectors
+// e_u = e_theta - u (c + x), e_v = e_phi - v (c + x) plus the near field's
+// sums, rotated onto (e_theta, e_phi) at x; psi = C + Q (log 2 + log(1 - |t|^2/4))
+// + 2 Re F + (sum q log d^2 - log 4 sum q) / 4pi.
+template <bool PSI>
+__device__ __forceinline__ void finish_target_df(const EvalDfArgs& A, const LeafFrameD2& G, const dflt* L,
+                                                 size_t tix, const float4& th, const float4& tl, const dflt* nf,
+                                                 const float4* __restrict__ tab, double shift)
+{
+    const dflt tx(th.x, tl.x), ty(th.y, tl.y), tz(th.z, tl.z);
+    const dflt D2 = tx * tx + ty * ty + tz * tz;
+    const dflt den = dflt(2.f, 0.f) - D2 * 0.5f;
+    const dflt wu = (tx * G.et[0] + ty * G.et[1] + tz * G.et[2]) / den;
+    const dflt wv = (tx * G.ep[0] + ty * G.ep[1] + tz * G.ep[2]) / den;
+    const dflt ox = wu * G.inv_r, oy = wv * G.inv_r;
+    dflt fx(0.f, 0.f), fy(0.f, 0.f), hx(0.f, 0.f), hy(0.f, 0.f);
+    for (int l = A.p; l >= 1; --l) {
+        const dflt cr = L[2 * l], ci = L[2 * l + 1];
+        if (PSI) {
+            const dflt nfx = fx * ox - fy * oy + cr, nfy = fx * oy + fy * ox + ci;
+            fx = nfx; fy = nfy;
+        }
+        const dflt nhx = hx * ox - hy * oy + cr * (float)l, nhy = hx * oy + hy * ox + ci * (float)l;
+        hx = nhx; hy = nhy;
+    }
+    const dflt Fpx = hx * G.inv_r, Fpy = hy * G.inv_r;    // F'(w)
+    const dflt C = L[0], Q = L[1];
+    const dflt opw = dflt(1.f, 0.f) + (wu * wu + wv * wv);
+    const dflt au = opw * Fpx - Q * wu;
+    const dflt av = -(opw * Fpy) - Q * wv;
+    // x = c + t and c + x = 2c + t
+    const dflt xx = G.c[0] + tx, xy = G.c[1] + ty, xz = G.c[2] + tz;
+    const dflt cxx = G.c[0] + xx, cyy = G.c[1] + xy, czz = G.c[2] + xz;
+    const dflt i2p(INV2PI);
+    const dflt sx = nf[0] - xx * (nf[3] * 0.5f), sy = nf[1] - xy * (nf[3] * 0.5f), sz = nf[2] - xz * (nf[3] * 0.5f);
+    const dflt a3x = au * (G.et[0] - wu * cxx) + av * (G.ep[0] - wv * cxx) + i2p * sx;
+    const dflt a3y = au * (G.et[1] - wu * cyy) + av * (G.ep[1] - wv * cyy) + i2p * sy;
+    const dflt a3z = au * (G.et[2] - wu * czz) + av * (G.ep[2] - wv * czz) + i2p * sz;
+    // rotate onto (e_theta, e_phi) at x (phi = 0 at the poles)
+    const dflt rho = dfl_sqrt(xx * xx + xy * xy);
+    dflt cp(1.f, 0.f), sp(0.f, 0.f);
+    if (rho.h > 0.f) { cp = xx / rho; sp = xy / rho; }
+    const uint32_t o = A.tperm[tix];
+    if (A.alpha) {
+        A.alpha[2 * (size_t)o] = (double)(a3x * (xz * cp) + a3y * (xz * sp) - a3z * rho);
+        A.alpha[2 * (size_t)o + 1] = (double)(a3y * cp - a3x * sp);
+    }
+    if (PSI) {
+        const dflt F = fx * ox - fy * oy;                   // Re F(w)
+        const dflt ln2(LN2_H, LN2_L);
+        const dflt psi_e = C + Q * (ln2 + dfl_log1m(D2 * 0.25f, tab)) + F * 2.f;
+        const dflt near = (nf[4] - nf[3] * (ln2 * 2.f)) * dflt(INV4PI);
+        A.psi[o] = (double)(psi_e + near) + shift;
+    }
+}
+
+__device__ __forceinline__ dflt group_sum_dfl(dflt v, int lpt)
+{
+    for (int o = lpt >> 1; o > 0; o >>= 1) v = v + dfl_shfl_xor(v, o);
+    return v;
+}
+
+// One warp per target leaf; each pass over the near sources serves two groups
+// of targets, as in k_eval32 (group a: the largest power of two <= the targets
+// left, group b: the power of two >= what a leaves; 32 / size lanes per target).
 template <bool PSI>
 __global__ void __launch_bounds__(128) k_eval_df(EvalDfArgs A)
 {
@@ -922,6 +1082,7 @@ __global__ void __launch_bounds__(128) k_eval_df(EvalDfArgs A)
     __shared__ int s_pre[4][33];
     __shared__ int s_first[4][32];
     __shared__ float4 s_tab[129];
+    __shared__ LeafFrameD2 s_frame2[4];
     for (int i = threadIdx.x; i < 129; i += blockDim.x) s_tab[i] = A.log_tab[i];
     __syncthreads();
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -932,6 +1093,7 @@ __global__ void __launch_bounds__(128) k_eval_df(EvalDfArgs A)
     float4* yl = s_lo[wid];
     int* pre = s_pre[wid];
     int* fst = s_first[wid];
+    LeafFrameD2& G = s_frame2[wid];
     for (;;) {
         const int64_t w = next_leaf(A.leaf_ctr, lane);
         if (w >= dcount(A.d_n_leaves, A.n_leaves)) break;
@@ -940,15 +1102,31 @@ __global__ void __launch_bounds__(128) k_eval_df(EvalDfArgs A)
         const double* g = A.T.geom + (size_t)leaf * GEOM_STRIDE;
         const dflt* L = A.local + (size_t)leaf * EXP_STRIDE;
         const int64_t nb0 = A.p2p_off[leaf], nb1 = A.p2p_off[leaf + 1];
-        for (int tb = 0, tpw = 0; tb < tc; tb += tpw) {
-            tpw = min(32, 1 << (31 - __clz(tc - tb)));     // largest power of two <= the targets left
-            const int lpt = 32 / tpw;
-            const int slot = lane / lpt, sub = lane % lpt;
-            const int ti = tb + slot;
-            const bool active = ti < tc;
-            const size_t tix = (size_t)tf + (active ? ti : 0);
-            const float4 th = A.toff[2 * tix], tl = A.toff[2 * tix + 1];
-            dflt ax{0.f, 0.f}, ay{0.f, 0.f}, az{0.f, 0.f}, aq{0.f, 0.f}, al{0.f, 0.f};
+        __syncwarp();
+        if (lane < 3) {
+            G.et[lane] = dflt(g[3 + lane]);
+            G.ep[lane] = dflt(g[6 + lane]);
+            G.c[lane] = dflt(g[lane]);
+        }
+        if (lane == 3) G.inv_r = dflt(1.0 / g[10]);
+        __syncwarp();
+        for (int tb = 0; tb < tc;) {
+            const int rem = tc - tb;
+            const int na = min(32, 1 << (31 - __clz(rem)));
+            const int rb = rem - na;
+            const int nb = rb <= 0 ? 0 : min(32, 1 << (32 - __clz(rb - 1)));   // power of two >= rb
+            const int lpa = 32 / na, sa = lane % lpa;
+            const int lpb = nb ? 32 / nb : 32, sb = lane % lpb;
+            const size_t ta = (size_t)tf + tb + lane / lpa;
+            const int ib = tb + na + lane / lpb;
+            const bool act_b = nb > 0 && ib < tc;
+            const size_t tbx = (size_t)tf + (act_b ? ib : tb);
+            const float4 tha = A.toff[2 * ta], tla = A.toff[2 * ta + 1];
+            const float4 thb = A.toff[2 * tbx], tlb = A.toff[2 * tbx + 1];
+            dflt acc_a[5], acc_b[5];
+#pragma unroll
+            for (int c = 0; c < 5; ++c) acc_a[c] = acc_b[c] = dflt(0.f, 0.f);
+            dflt mass(0.f, 0.f);           // the mass staged so far (the same for every target)
             int64_t kn = nb0;
             int jn = 0;
             while (kn < nb1) {
@@ -978,6 +1156,11 @@ __global__ void __launch_bounds__(128) k_eval_df(EvalDfArgs A)
                 s_dc[wid][lane][0] = rh.x; s_dc[wid][lane][1] = rh.y; s_dc[wid][lane][2] = rh.z;
                 s_dc[wid][lane][3] = rl.x; s_dc[wid][lane][4] = rl.y; s_dc[wid][lane][5] = rl.z;
                 __syncwarp();
+                // the stage's first mass: a stage whose masses all equal it takes the product logarithm
+                const size_t j0 = (size_t)fst[0];
+                const float q0h = A.soff[2 * j0].w, q0l = A.soff[2 * j0 + 1].w;
+                bool same = true;
+                dflt sq(0.f, 0.f);
                 for (int idx = lane; idx < ns; idx += 32) {
                     int lo = 0, hi = nl;
                     while (hi - lo > 1) {
@@ -994,95 +1177,41 @@ __global__ void __launch_bounds__(128) k_eval_df(EvalDfArgs A)
                     two_sum(h.z, d[2], &sz, &ez_);
                     yh[idx] = make_float4(sx, sy, sz, h.w);
                     yl[idx] = make_float4(ex_ + (l.x + d[3]), ey_ + (l.y + d[4]), ez_ + (l.z + d[5]), l.w);
+                    same = same && h.w == q0h && l.w == q0l;
+                    sq = sq + dflt(h.w, l.w);
                 }
+                const bool eqm = __all_sync(FULL, same);
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) sq = sq + dfl_shfl_xor(sq, o);
+                mass = mass + sq;
                 if (nfit == 0) jn += STAGE;
                 else { kn += nfit; jn = 0; }
                 __syncwarp();
-                for (int j = sub; j < ns; j += lpt) {
-                    const float4 h = yh[j];
-                    const float4 l = yl[j];
-                    // d = t - y
-                    const dflt dx = dfl_diff(th.x, tl.x, h.x, l.x);
-                    const dflt dy = dfl_diff(th.y, tl.y, h.y, l.y);
-                    const dflt dz = dfl_diff(th.z, tl.z, h.z, l.z);
-                    // d^2: exact squares of the leading parts, two exact two-sums
-                    const float px = __fmul_rn(dx.h, dx.h), py = __fmul_rn(dy.h, dy.h), pz = __fmul_rn(dz.h, dz.h);
-                    const float ex2 = __fmaf_rn(__fadd_rn(dx.h, dx.h), dx.l, __fmaf_rn(dx.h, dx.h, -px));
-                    const float ey2 = __fmaf_rn(__fadd_rn(dy.h, dy.h), dy.l, __fmaf_rn(dy.h, dy.h, -py));
-                    const float ez2 = __fmaf_rn(__fadd_rn(dz.h, dz.h), dz.l, __fmaf_rn(dz.h, dz.h, -pz));
-                    const dflt s1 = dfl_two_sum(px, py);
-                    const dflt s2 = dfl_two_sum(s1.h, pz);
-                    dflt d2 = dfl_fast_two_sum(s2.h, __fadd_rn(__fadd_rn(s1.l, s2.l), __fadd_rn(__fadd_rn(ex2, ey2), ez2)));
-                    // coincident pairs (d^2 == 0) contribute nothing
-                    const bool ok = d2.h > 0.f;
-                    const dflt q = ok ? dflt(h.w, l.w) : dflt(0.f, 0.f);
-                    if (!ok) d2 = dflt(1.f, 0.f);
-                    // 1/d^2: MUFU reciprocal (relative error < 2^-22) and one Newton step
-                    float r0;
-                    asm("rcp.approx.f32 %0, %1;" : "=f"(r0) : "f"(d2.h));
-                    const float e0 = __fmaf_rn(-d2.l, r0, __fmaf_rn(-d2.h, r0, 1.f));
-                    const dflt wq = dfl_mul_lazy(dflt(r0, __fmul_rn(r0, e0)), q);
-                    dfl_mac(ax, wq, dx);
-                    dfl_mac(ay, wq, dy);
-                    dfl_mac(az, wq, dz);
-                    const dflt sq = dfl_two_sum(aq.h, q.h);
-                    aq = dflt(sq.h, __fadd_rn(aq.l, __fadd_rn(sq.l, q.l)));
-                    if (PSI) dfl_mac(al, dfl_log_lazy(d2, s_tab), q);
+                const dflt qm(q0h, q0l);
+                if (eqm) {
+                    pair_sums_df<PSI, true>(yh, yl, ns, sa, lpa, tha, tla, qm, s_tab, acc_a);
+                    if (nb) pair_sums_df<PSI, true>(yh, yl, ns, sb, lpb, thb, tlb, qm, s_tab, acc_b);
+                } else {
+                    pair_sums_df<PSI, false>(yh, yl, ns, sa, lpa, tha, tla, qm, s_tab, acc_a);
+                    if (nb) pair_sums_df<PSI, false>(yh, yl, ns, sb, lpb, thb, tlb, qm, s_tab, acc_b);
                 }
-                ax = dfl_norm(ax); ay = dfl_norm(ay); az = dfl_norm(az); aq = dfl_norm(aq);
-                if (PSI) al = dfl_norm(al);
             }
-            // combine the lanes of a target in FP64
-            double sx = (double)ax.h + (double)ax.l, sy = (double)ay.h + (double)ay.l, sz = (double)az.h + (double)az.l;
-            double sq = (double)aq.h + (double)aq.l, sl = (double)al.h + (double)al.l;
-            sx = group_sum(sx, lpt);
-            sy = group_sum(sy, lpt);
-            sz = group_sum(sz, lpt);
-            sq = group_sum(sq, lpt);
-            if (PSI) sl = group_sum(sl, lpt);
-            if (!active || sub != 0) continue;
-            // ---- L2P in the leaf frame: frame coordinates in FP64 (as in k_eval),
-            // the Horner recurrences for F(w) and F'(w) in double-float
-            const double4_32a x = A.tgt[tix];
-            const double Dx = x.x - g[0], Dy = x.y - g[1], Dz = x.z - g[2];
-            const double D2 = Dx * Dx + Dy * Dy + Dz * Dz;
-            const double den = 2.0 - 0.5 * D2;
-            const double wu = (Dx * g[3] + Dy * g[4] + Dz * g[5]) / den;
-            const double wv = (Dx * g[6] + Dy * g[7] + Dz * g[8]) / den;
-            const double inv_r = 1.0 / g[10];
-            const dflt ox(wu * inv_r), oy(wv * inv_r);
-            dflt fx(0.f, 0.f), fy(0.f, 0.f), hx(0.f, 0.f), hy(0.f, 0.f);
-            for (int l = A.p; l >= 1; --l) {
-                const dflt cr = L[2 * l], ci = L[2 * l + 1];
-                const dflt nfx = fx * ox - fy * oy + cr, nfy = fx * oy + fy * ox + ci;
-                const dflt nhx = hx * ox - hy * oy + cr * (float)l, nhy = hx * oy + hy * ox + ci * (float)l;
-                fx = nfx; fy = nfy; hx = nhx; hy = nhy;
+            // the staged mass once per target less what it skipped: acc[4] = sum q
+            if (sa == 0) acc_a[4] = mass - acc_a[4];
+            else acc_a[4] = -acc_a[4];
+            if (sb == 0) acc_b[4] = mass - acc_b[4];
+            else acc_b[4] = -acc_b[4];
+            // the sums of each target's lanes, in the order (x, y, z, q, log) the finish takes
+            dflt na_[5], nb_[5];
+#pragma unroll
+            for (int c = 0; c < 5; ++c) {
+                const int cc = c < 3 ? c : 7 - c;            // 3 <- q (acc[4]), 4 <- log (acc[3])
+                na_[c] = group_sum_dfl(dfl_norm(acc_a[cc]), lpa);
+                nb_[c] = group_sum_dfl(dfl_norm(acc_b[cc]), lpb);
             }
-            const cd F = mk((double)(fx * ox - fy * oy), 0.0);      // Re F(w) is all psi needs
-            const cd Fp = mk((double)hx * inv_r, (double)hy * inv_r);
-            const double C = (double)L[0], Q = (double)L[1];
-            const double w2 = wu * wu + wv * wv;
-            const double au = (1.0 + w2) * Fp.x - Q * wu;
-            const double av = -(1.0 + w2) * Fp.y - Q * wv;
-            const double cxx = g[0] + x.x, cyy = g[1] + x.y, czz = g[2] + x.z;
-            double a3x = au * (g[3] - wu * cxx) + av * (g[6] - wv * cxx);
-            double a3y = au * (g[4] - wu * cyy) + av * (g[7] - wv * cyy);
-            double a3z = au * (g[5] - wu * czz) + av * (g[8] - wv * czz);
-            a3x += INV2PI * (sx - 0.5 * x.x * sq);
-            a3y += INV2PI * (sy - 0.5 * x.y * sq);
-            a3z += INV2PI * (sz - 0.5 * x.z * sq);
-            const double rho = sqrt(x.x * x.x + x.y * x.y);
-            double cp = 1.0, sp = 0.0;
-            if (rho > 0.0) { cp = x.x / rho; sp = x.y / rho; }
-            const uint32_t o = A.tperm[tix];
-            if (A.alpha) {
-                A.alpha[2 * (size_t)o] = a3x * (x.z * cp) + a3y * (x.z * sp) - a3z * rho;
-                A.alpha[2 * (size_t)o + 1] = -a3x * sp + a3y * cp;
-            }
-            if (PSI) {
-                const double psi_e = C + Q * (LOG2 + log1p(-0.25 * D2)) + 2.0 * F.x;
-                A.psi[o] = psi_e + INV4PI * (sl - LOG4 * sq) + shift;
-            }
+            if (sa == 0) finish_target_df<PSI>(A, G, L, ta, tha, tla, na_, s_tab, shift);
+            if (act_b && sb == 0) finish_target_df<PSI>(A, G, L, tbx, thb, tlb, nb_, s_tab, shift);
+            tb += na + nb;
         }
     }
 }

@@ -167,7 +167,7 @@ __device__ __forceinline__ int64_t dfl_floor_checked(dflt v, bool* ok)
     return (int64_t)__float2ll_rz(fh) + (int64_t)k;
 }
 
-__device__ __forceinline__ dflt dfl_sqrt(dflt a)
+__device__ __forceinline__ dflt dfl_sqrt_key(dflt a)
 {
     const float s0 = sqrtf(a.h);
     // one Newton correction from the double-float residual a - s0^2
@@ -232,7 +232,7 @@ __device__ __forceinline__ uint64_t key29_fast(double x, double y, double z, con
         const dflt tp = tt - dflt((float)ntt, 0.f);
         const dflt X = dfl_abs_from_bits(bx), Y = dfl_abs_from_bits(by);
         const dflt one_m_za = (X * X + Y * Y) / (dflt(1.f, 0.f) + dfl_abs_from_bits(bz));
-        const dflt tmp = dfl_sqrt(one_m_za * 3.f) * nside;
+        const dflt tmp = dfl_sqrt_key(one_m_za * 3.f) * nside;
         int64_t jp = dfl_floor_checked(tp * tmp, ok);
         int64_t jm = dfl_floor_checked((dflt(1.f, 0.f) - tp) * tmp, ok);
         if (jp > ns - 1) jp = ns - 1;

@@ -74,6 +74,24 @@ def test_df_coincident_points_and_poles():
     check(psi, alpha, direct_sum(src, q, tgt))
 
 
+def test_df_equal_masses_product_logarithm():
+    """Equal masses take the product form of sum q log d^2 (one logarithm per
+    block of sources): targets on the sources themselves (coincident pairs
+    skipped), duplicates, a clump 1e-9 rad wide (d^2 near 1e-18, products of
+    many small mantissas and exponents) and the poles, against the oracle."""
+    rng = np.random.default_rng(29)
+    base = unit(np.array([-0.4, 0.7, 0.2]))
+    src = np.vstack([np.repeat(base[None], 20, 0), unit(base + 1e-9 * rng.normal(size=(60, 3))),
+                     [[0, 0, 1.0], [0, 0, -1.0]], workloads.clustered(rng, 20000, 40)])
+    q = np.full(len(src), 4 * np.pi / len(src))
+    _, psi, alpha = solve(src, q, src, leaf=16)
+    ref = direct_sum(src, q, src)
+    check(psi, alpha, ref)
+    idx = np.arange(100)           # the duplicates and the tight clump, pointwise
+    na = np.linalg.norm(ref["alpha"][idx], axis=1)
+    assert (np.linalg.norm(alpha[idx] - ref["alpha"][idx], axis=1) <= 1e-10 * na.max()).all()
+
+
 def test_df_log_and_reciprocal_over_the_exponent_range():
     """One source, targets from 1e-4 to pi away: every pair in the near field of
     the source's leaf runs the table-driven double-float logarithm and the
