@@ -184,7 +184,7 @@ def make_workload(args, rank):
 def run_adjoint(args, dev, clock_sampler):
     """One training step of the gradient workload: the 1e-10 forward solve, the
     loss gradient dL/dalpha = 2 w (alpha - alpha_ref) on the device, and the
-    FP64 adjoint sFMM (dL/dq, dL/dy); CUDA events around each part."""
+    double-float adjoint sFMM (dL/dq, dL/dy); CUDA events around each part."""
     import torch
     from paper_2210_07021_gb300 import sfmm, workloads
     d = workloads.loss_sky()
@@ -225,7 +225,8 @@ def run_adjoint(args, dev, clock_sampler):
     plan.close()
     ms = float(np.mean(t_f) + np.mean(t_b))
     return {"workload": d["workload"], "N": N, "M": M, "forward": "mixed_df (stated 1e-10), p=28, m=64, c_t=0.45",
-            "backward": "adjoint sFMM, FP64, same p and tree settings", "steps": args.steps,
+            "backward": "adjoint sFMM, double-float (charges and dipoles), same p and tree settings",
+            "backward_over_forward": float(np.mean(t_b) / np.mean(t_f)), "steps": args.steps,
             "ms_per_step": ms, "ms_forward": float(np.mean(t_f)), "ms_backward": float(np.mean(t_b)),
             "value": (N + M) * 1e-3 / ms, "unit": "Mpts/s (sources + targets per forward+backward step)",
             "error_vs_oracle": {"dq_rel": rel(gq.cpu().numpy()[idx], rq), "dy_rel": rel(gs.cpu().numpy()[idx], rs),

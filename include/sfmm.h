@@ -221,8 +221,10 @@ sfmm_status sfmm_shear(sfmm_plan_t plan, const double* src_xyz, const void* q, i
  *                 gradient on the sphere as a 3-vector [N][3].
  * This is one more sFMM: charges g_psi and tangent dipoles g at the targets
  * (the dipole multipole is Lemma 1 differentiated along g), evaluated at the
- * sources; M2M, M2L and L2L are those of the forward solve.  It runs in FP64
- * whatever opt.precision is, with the plan's p, leaf size and MAC.  Arguments
+ * sources; M2M, M2L and L2L are those of the forward solve.  With the plan's
+ * p, leaf size and MAC, it runs in FP64 for an SFMM_FP64 plan and otherwise in
+ * double-float (the far field of SFMM_MIXED_DF, a double-float near field of
+ * charges and dipoles; about 1e-12 relative).  Arguments
  * as for sfmm_deflection (device pointers; q float32 when opt.q_f32); g_psi
  * [M] and g_alpha [M][2] may be NULL (treated as zero); at least one of
  * grad_q [N], grad_src [N][3] must be non-NULL.  Gradients with respect to the

@@ -8,8 +8,8 @@ The gradient with respect to src is the covariant gradient on the sphere
 (a tangent 3-vector at each source), which is what a step that moves the
 sources along the sphere (and renormalises) needs.  Gradients with respect
 to the target positions would need second derivatives of the potential and
-are not formed; asking for them raises.  The backward pass always runs in
-FP64 (see sfmm_adjoint), whatever the plan's precision.
+are not formed; asking for them raises.  The backward pass runs in FP64 for
+an FP64 plan and in double-float otherwise (see sfmm_adjoint).
 """
 import torch
 

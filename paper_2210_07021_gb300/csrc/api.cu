@@ -3,6 +3,7 @@
 // -> interaction lists (Algorithm 1, Sec. 3.4-3.5) -> M2L (Lemma 3) -> L2L
 // (Lemma 4) -> L2P + near field (Sec. 3.6).  Every step runs on the device.
 #include "common.cuh"
+#include "dfloat.cuh"
 
 #include <algorithm>
 #include <string>
@@ -61,7 +62,7 @@ cudaError_t launch_m2m_df(const TreeView& T, int c0, int c1, int lvl, int p, con
 cudaError_t launch_l2l_df(const TreeView& T, int a, int b, int lvl, int p, const void* geo, const double* acc,
                           void* local, cudaStream_t s);
 cudaError_t launch_p2m_df_leaf(const TreeView& T, const int* leaves, int64_t n_leaves, const int64_t* d_nl, const float4* off,
-                               const float4* log_tab, int p, void* mpole, cudaStream_t s);
+                               const float4* doff, const float4* log_tab, int p, void* mpole, cudaStream_t s);
 cudaError_t launch_unscale(int n_nodes, const double* geom, const void* in, double* out, int p, int is_local,
                            int ek, cudaStream_t s);
 cudaError_t launch_eval32_prep(const TreeView& T, const int* leaves, int64_t n_leaves, const int64_t* d_nl,
@@ -79,6 +80,7 @@ cudaError_t launch_eval_df(const TreeView& T, const int* leaves, int64_t n_leave
                            const float4* toff, const float4* dc, const double4_32a* tgt, const uint32_t* tperm,
                            const int64_t* p2p_off, const uint32_t* p2p_src, const void* local, const void* mpole,
                            const float4* log_tab, int p, int zero_mean, double* psi, double* alpha,
+                           const float4* doff, const void* w, int w_f32, double* grad3,
                            unsigned long long* leaf_ctr, cudaStream_t s);
 cudaError_t launch_p2m_adj(const TreeView& T, const int* leaves, int64_t n_leaves, const double4_32a* src,
                            const double4_32a* dip, double* mpole, int p, cudaStream_t s);
@@ -157,6 +159,19 @@ __global__ void k_gather_dip(const double* __restrict__ g, const uint32_t* __res
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t j = perm[i];
         out[i] = make_double4_32a(g[3 * (size_t)j], g[3 * (size_t)j + 1], g[3 * (size_t)j + 2], 0.0);
+    }
+}
+
+// tangent dipoles of the adjoint into key order as (hi, lo) float4 pairs:
+// out[2i] = (g_x, g_y, g_z) leading parts, out[2i + 1] their remainders
+__global__ void k_gather_dip_df(const double* __restrict__ g, const uint32_t* __restrict__ perm, int64_t n,
+                                float4* __restrict__ out)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t j = perm[i];
+        const dflt x(g[3 * (size_t)j]), y(g[3 * (size_t)j + 1]), z(g[3 * (size_t)j + 2]);
+        out[2 * i] = make_float4(x.h, y.h, z.h, 0.f);
+        out[2 * i + 1] = make_float4(x.l, y.l, z.l, 0.f);
     }
 }
 
@@ -292,7 +307,10 @@ sfmm_status solve(sfmm_plan_s* P, const double* src, const void* q, int64_t N, c
                   double* mu = nullptr)
 {
     cudaStream_t s = P->stream;
-    const int precision = (adj || gamma) ? SFMM_FP64 : P->opt.precision;   // adjoint and shear run in FP64
+    // the shear runs in FP64; the adjoint in FP64 for FP64 plans, else with the double-float far
+    // and near fields (its own near-field kernel, charges and dipoles)
+    const bool adj_df = adj && P->opt.precision != SFMM_FP64;
+    const int precision = gamma ? SFMM_FP64 : adj ? (adj_df ? SFMM_MIXED_DF : SFMM_FP64) : P->opt.precision;
     if (P->gm && !(precision == SFMM_MIXED || precision == SFMM_MIXED_DF))
         return fail(P, SFMM_EINVAL, "graph mode runs the double-float far field only (SFMM_MIXED, SFMM_MIXED_DF)");
     const int q_f32 = adj ? 0 : P->opt.q_f32;
@@ -357,7 +375,10 @@ sfmm_status solve(sfmm_plan_s* P, const double* src, const void* q, int64_t N, c
     const uint64_t* skeys = P->skeys_alt ? P->skeys2.as<uint64_t>() : P->skeys.as<uint64_t>();
     const uint32_t* sperm = P->skeys_alt ? P->sperm2.as<uint32_t>() : P->sperm.as<uint32_t>();
     k_gather_src<<<grid_for(N), 256, 0, s>>>(src, q, q_f32, sperm, N, P->src4.as<double4_32a>()); count_launch();
-    if (adj) {
+    if (adj_df) {
+        if ((e = ensure(P->dip4, (size_t)N * 32))) return cuda_fail(P, e, "alloc dipoles");
+        k_gather_dip_df<<<grid_for(N), 256, 0, s>>>(adj->dip, sperm, N, P->dip4.as<float4>()); count_launch();
+    } else if (adj) {
         if ((e = ensure(P->dip4, (size_t)N * 32))) return cuda_fail(P, e, "alloc dipoles");
         k_gather_dip<<<grid_for(N), 256, 0, s>>>(adj->dip, sperm, N, P->dip4.as<double4_32a>()); count_launch();
     }
@@ -415,10 +436,11 @@ sfmm_status solve(sfmm_plan_s* P, const double* src, const void* q, int64_t N, c
                                     P->soff.as<float4>(), s)))
             return cuda_fail(P, e, "offsets");
     }
-    if (adj) e = launch_p2m_adj(T, P->leaves_src.as<int>(), P->n_leaves, P->src4.as<double4_32a>(),
-                                P->dip4.as<double4_32a>(), P->mpole.as<double>(), p, s);
+    if (adj && !adj_df) e = launch_p2m_adj(T, P->leaves_src.as<int>(), P->n_leaves, P->src4.as<double4_32a>(),
+                                           P->dip4.as<double4_32a>(), P->mpole.as<double>(), p, s);
     else if (dfe) e = launch_p2m_df_leaf(T, P->leaves_src.as<int>(), P->n_leaves, d_nls, P->soff.as<float4>(),
-                                         P->logtab.as<float4>(), p, P->mpole.p, s);
+                                         adj_df ? P->dip4.as<float4>() : nullptr, P->logtab.as<float4>(), p,
+                                         P->mpole.p, s);
     else e = launch_p2m(T, P->leaves_src.as<int>(), P->n_leaves, P->src4.as<double4_32a>(), P->soff.as<float4>(),
                         P->logtab.as<float4>(), P->mpole.p, p, ek, s);
     if (e) return cuda_fail(P, e, "P2M");
@@ -512,7 +534,12 @@ sfmm_status solve(sfmm_plan_s* P, const double* src, const void* q, int64_t N, c
             return cuda_fail(P, e, "offsets");
     }
     unsigned long long* leaf_ctr = reinterpret_cast<unsigned long long*>(P->small.as<int64_t>() + 40);
-    if (adj) e = launch_eval_adj(T, P->leaves_tgt.as<int>(), P->n_leaves_tgt, P->src4.as<double4_32a>(),
+    if (adj_df) e = launch_eval_df(T, P->leaves_tgt.as<int>(), P->n_leaves_tgt, d_nlt, P->soff.as<float4>(),
+                                   P->toff.as<float4>(), P->dc.as<float4>(), P->tgt4.as<double4_32a>(), tperm,
+                                   P->p2p_off.as<int64_t>(), p2p_s, P->local.p, P->mpole.p, P->logtab.as<float4>(), p,
+                                   P->opt.zero_mean, psi, nullptr, P->dip4.as<float4>(), adj->w, adj->w_f32,
+                                   adj->grad3, leaf_ctr, s);
+    else if (adj) e = launch_eval_adj(T, P->leaves_tgt.as<int>(), P->n_leaves_tgt, P->src4.as<double4_32a>(),
                                  P->dip4.as<double4_32a>(), P->tgt4.as<double4_32a>(), tperm, P->p2p_off.as<int64_t>(),
                                  p2p_s, P->local.as<double>(), P->mpole.as<double>(), p, P->opt.zero_mean, adj->w,
                                  adj->w_f32, psi, adj->grad3, leaf_ctr, s);
@@ -523,7 +550,8 @@ sfmm_status solve(sfmm_plan_s* P, const double* src, const void* q, int64_t N, c
     else if (dfe) e = launch_eval_df(T, P->leaves_tgt.as<int>(), P->n_leaves_tgt, d_nlt, P->soff.as<float4>(),
                                      P->toff.as<float4>(), P->dc.as<float4>(), P->tgt4.as<double4_32a>(), tperm,
                                      P->p2p_off.as<int64_t>(), p2p_s, P->local.p, P->mpole.p,
-                                     P->logtab.as<float4>(), p, P->opt.zero_mean, psi, alpha, leaf_ctr, s);
+                                     P->logtab.as<float4>(), p, P->opt.zero_mean, psi, alpha, nullptr, nullptr, 0,
+                                     nullptr, leaf_ctr, s);
     else e = launch_eval(T, P->leaves_tgt.as<int>(), P->n_leaves_tgt, d_nlt, P->src4.as<double4_32a>(),
                          P->tgt4.as<double4_32a>(), tperm, P->p2p_off.as<int64_t>(), p2p_s, P->local.as<double>(),
                          P->mpole.as<double>(), p, P->opt.zero_mean, P->opt.sigma, psi, alpha, gamma, mu, leaf_ctr, s);

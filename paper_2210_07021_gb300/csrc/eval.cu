@@ -931,6 +931,13 @@ struct EvalDfArgs {
     double* psi;
     double* alpha;
     unsigned long long* leaf_ctr;   // zero at launch: the warps take target leaves from it one at a time
+    // the adjoint (k_eval_df<PSI, true>): the sources' tangent dipoles as (hi, lo)
+    // float4 pairs, the targets' weights w (the forward masses) and the output
+    // w grad Phi [M][3]; psi then receives Phi
+    const float4* doff;
+    const void* w;
+    int w_f32;
+    double* grad3;
 };
 
 // Near-field sums of one target over the staged sources j = sub, sub + lpt, ...
@@ -1070,14 +1077,156 @@ __device__ __forceinline__ dflt group_sum_dfl(dflt v, int lpt)
     return v;
 }
 
+// The adjoint's near-field sums of one target (a forward source) over the
+// staged adjoint sources (forward targets, charges h and tangent dipoles g):
+// acc[0..3] as pair_sums_df for the charges (CHG: the stage has a non-zero
+// charge), acc[4] the mass skipped at coincident points, and for the dipoles,
+// with G(x, y) = (1/4pi) log |x - y|^2 + const and d = x - y:
+//   acc[5] = sum (g . (y - x)) / d^2      (the potential, times 2 / 4pi)
+//   acc[6..8] = sum 2 (g . d) d / d^4 - g / d^2   (its gradient in x, likewise).
+template <bool PSI, bool CHG, bool EQM>
+__device__ __forceinline__ void pair_sums_adj_df(const float4* __restrict__ yh, const float4* __restrict__ yl,
+                                                 const float4* __restrict__ gh_, const float4* __restrict__ gl_,
+                                                 int ns, int sub, int lpt, const float4& th, const float4& tl,
+                                                 dflt qm, const float4* __restrict__ tab, dflt* acc)
+{
+    for (int j0 = sub; j0 < ns; j0 += 16 * lpt) {
+        const int j1 = min(ns, j0 + 16 * lpt);
+        dflt prod(1.f, 0.f);
+        int ecnt = 0;
+        for (int j = j0; j < j1; j += lpt) {
+            const float4 h = yh[j];
+            const float4 l = yl[j];
+            const dflt dx = dfl_diff(th.x, tl.x, h.x, l.x);
+            const dflt dy = dfl_diff(th.y, tl.y, h.y, l.y);
+            const dflt dz = dfl_diff(th.z, tl.z, h.z, l.z);
+            const float px = __fmul_rn(dx.h, dx.h), py = __fmul_rn(dy.h, dy.h), pz = __fmul_rn(dz.h, dz.h);
+            const float ex2 = __fmaf_rn(__fadd_rn(dx.h, dx.h), dx.l, __fmaf_rn(dx.h, dx.h, -px));
+            const float ey2 = __fmaf_rn(__fadd_rn(dy.h, dy.h), dy.l, __fmaf_rn(dy.h, dy.h, -py));
+            const float ez2 = __fmaf_rn(__fadd_rn(dz.h, dz.h), dz.l, __fmaf_rn(dz.h, dz.h, -pz));
+            const dflt s1 = dfl_two_sum(px, py);
+            const dflt s2 = dfl_two_sum(s1.h, pz);
+            dflt d2 = dfl_fast_two_sum(s2.h, __fadd_rn(__fadd_rn(s1.l, s2.l), __fadd_rn(__fadd_rn(ex2, ey2), ez2)));
+            const bool ok = d2.h >= FLT_MIN_F;
+            dflt q = dflt(h.w, l.w);
+            if (!ok) {
+                acc[4] = acc[4] + q;
+                q = dflt(0.f, 0.f);
+                d2 = dflt(1.f, 0.f);
+            }
+            const float r0 = rcp_approx(d2.h);
+            const float e0 = __fmaf_rn(-d2.l, r0, __fmaf_rn(-d2.h, r0, 1.f));
+            const dflt inv = ok ? dfl_fast_two_sum(r0, __fmul_rn(r0, e0)) : dflt(0.f, 0.f);   // 1/d^2
+            if (CHG) {
+                const dflt wq = dfl_mul_lazy(inv, q);
+                dfl_mac(acc[0], wq, dx);
+                dfl_mac(acc[1], wq, dy);
+                dfl_mac(acc[2], wq, dz);
+                if (PSI) {
+                    if (EQM) {
+                        const int k = (__float_as_int(d2.h) >> 23) - 127;
+                        const float sc = __int_as_float((127 - k) << 23);
+                        prod = prod * dflt(__fmul_rn(d2.h, sc), __fmul_rn(d2.l, sc));
+                        ecnt += k;
+                    } else {
+                        dfl_mac(acc[3], dfl_log_lazy(d2, tab), q);
+                    }
+                }
+            }
+            // dipoles
+            const float4 ga = gh_[j], gb = gl_[j];
+            const dflt gx(ga.x, gb.x), gy(ga.y, gb.y), gz(ga.z, gb.z);
+            const dflt gd = gx * dx + gy * dy + gz * dz;          // g . d = -(g . (y - x))
+            const dflt gdi = gd * inv;
+            if (PSI) acc[5] = acc[5] - gdi;
+            const dflt c2 = (gdi * inv) * 2.f;
+            const dflt ninv = -inv;
+            dfl_mac(acc[6], c2, dx);
+            dfl_mac(acc[6], ninv, gx);
+            dfl_mac(acc[7], c2, dy);
+            dfl_mac(acc[7], ninv, gy);
+            dfl_mac(acc[8], c2, dz);
+            dfl_mac(acc[8], ninv, gz);
+        }
+        if (CHG && PSI && EQM) {
+            const dflt lg = dfl_norm(dfl_log_lazy(prod, tab)) + dflt((float)ecnt) * dflt(LN2_H, LN2_L);
+            dfl_mac(acc[3], lg, qm);
+        }
+    }
+}
+
+// The adjoint's finish for target tix (a forward source): the local expansion's
+// F(w) and F'(w) as in finish_target_df give Phi and its gradient; the near
+// field adds the charges' sums (projected as in the forward) and the dipoles'
+// gradient projected by P_x = I - x x^T; the output is w times the covariant
+// gradient (a 3-vector) and Phi (+ the dipoles' potential).
+template <bool PSI>
+__device__ __forceinline__ void finish_target_adj_df(const EvalDfArgs& A, const LeafFrameD2& G, const dflt* L,
+                                                     size_t tix, const float4& th, const float4& tl, const dflt* nf,
+                                                     const float4* __restrict__ tab, double shift)
+{
+    const dflt tx(th.x, tl.x), ty(th.y, tl.y), tz(th.z, tl.z);
+    const dflt D2 = tx * tx + ty * ty + tz * tz;
+    const dflt den = dflt(2.f, 0.f) - D2 * 0.5f;
+    const dflt wu = (tx * G.et[0] + ty * G.et[1] + tz * G.et[2]) / den;
+    const dflt wv = (tx * G.ep[0] + ty * G.ep[1] + tz * G.ep[2]) / den;
+    const dflt ox = wu * G.inv_r, oy = wv * G.inv_r;
+    dflt fx(0.f, 0.f), fy(0.f, 0.f), hx(0.f, 0.f), hy(0.f, 0.f);
+    for (int l = A.p; l >= 1; --l) {
+        const dflt cr = L[2 * l], ci = L[2 * l + 1];
+        if (PSI) {
+            const dflt nfx = fx * ox - fy * oy + cr, nfy = fx * oy + fy * ox + ci;
+            fx = nfx; fy = nfy;
+        }
+        const dflt nhx = hx * ox - hy * oy + cr * (float)l, nhy = hx * oy + hy * ox + ci * (float)l;
+        hx = nhx; hy = nhy;
+    }
+    const dflt Fpx = hx * G.inv_r, Fpy = hy * G.inv_r;
+    const dflt C = L[0], Q = L[1];
+    const dflt opw = dflt(1.f, 0.f) + (wu * wu + wv * wv);
+    const dflt au = opw * Fpx - Q * wu;
+    const dflt av = -(opw * Fpy) - Q * wv;
+    const dflt xx = G.c[0] + tx, xy = G.c[1] + ty, xz = G.c[2] + tz;
+    const dflt cxx = G.c[0] + xx, cyy = G.c[1] + xy, czz = G.c[2] + xz;
+    const dflt i2p(INV2PI);
+    const dflt xv = xx * nf[6] + xy * nf[7] + xz * nf[8];
+    const dflt hq = nf[3] * 0.5f;
+    const dflt sx = nf[0] - xx * hq + nf[6] - xv * xx;
+    const dflt sy = nf[1] - xy * hq + nf[7] - xv * xy;
+    const dflt sz = nf[2] - xz * hq + nf[8] - xv * xz;
+    const dflt a3x = au * (G.et[0] - wu * cxx) + av * (G.ep[0] - wv * cxx) + i2p * sx;
+    const dflt a3y = au * (G.et[1] - wu * cyy) + av * (G.ep[1] - wv * cyy) + i2p * sy;
+    const dflt a3z = au * (G.et[2] - wu * czz) + av * (G.ep[2] - wv * czz) + i2p * sz;
+    const uint32_t o = A.tperm[tix];
+    if (A.grad3) {
+        const double wt = A.w_f32 ? (double)static_cast<const float*>(A.w)[o] : static_cast<const double*>(A.w)[o];
+        A.grad3[3 * (size_t)o] = wt * (double)a3x;
+        A.grad3[3 * (size_t)o + 1] = wt * (double)a3y;
+        A.grad3[3 * (size_t)o + 2] = wt * (double)a3z;
+    }
+    if (PSI) {
+        const dflt F = fx * ox - fy * oy;
+        const dflt ln2(LN2_H, LN2_L);
+        const dflt psi_e = C + Q * (ln2 + dfl_log1m(D2 * 0.25f, tab)) + F * 2.f;
+        const dflt near = (nf[4] - nf[3] * (ln2 * 2.f)) * dflt(INV4PI) + nf[5] * i2p;
+        A.psi[o] = (double)(psi_e + near) + shift;
+    }
+}
+
 // One warp per target leaf; each pass over the near sources serves two groups
 // of targets, as in k_eval32 (group a: the largest power of two <= the targets
 // left, group b: the power of two >= what a leaves; 32 / size lanes per target).
-template <bool PSI>
+// ADJ: the adjoint (charges and tangent dipoles at the sources, Phi and w grad
+// Phi at the targets), with a stage of half the size (the dipoles are staged too).
+template <bool PSI, bool ADJ>
 __global__ void __launch_bounds__(128) k_eval_df(EvalDfArgs A)
 {
-    __shared__ float4 s_hi[4][STAGE];
-    __shared__ float4 s_lo[4][STAGE];
+    constexpr int ST = ADJ ? STAGE / 2 : STAGE;
+    constexpr int NACC = ADJ ? 9 : 5;
+    __shared__ float4 s_hi[4][ST];
+    __shared__ float4 s_lo[4][ST];
+    __shared__ float4 s_gh[4][ADJ ? ST : 1];
+    __shared__ float4 s_gl[4][ADJ ? ST : 1];
     __shared__ float s_dc[4][32][6];
     __shared__ int s_pre[4][33];
     __shared__ int s_first[4][32];
@@ -1123,9 +1272,9 @@ __global__ void __launch_bounds__(128) k_eval_df(EvalDfArgs A)
             const size_t tbx = (size_t)tf + (act_b ? ib : tb);
             const float4 tha = A.toff[2 * ta], tla = A.toff[2 * ta + 1];
             const float4 thb = A.toff[2 * tbx], tlb = A.toff[2 * tbx + 1];
-            dflt acc_a[5], acc_b[5];
+            dflt acc_a[NACC], acc_b[NACC];
 #pragma unroll
-            for (int c = 0; c < 5; ++c) acc_a[c] = acc_b[c] = dflt(0.f, 0.f);
+            for (int c = 0; c < NACC; ++c) acc_a[c] = acc_b[c] = dflt(0.f, 0.f);
             dflt mass(0.f, 0.f);           // the mass staged so far (the same for every target)
             int64_t kn = nb0;
             int jn = 0;
@@ -1146,10 +1295,10 @@ __global__ void __launch_bounds__(128) k_eval_df(EvalDfArgs A)
                     const int t = __shfl_up_sync(FULL, inc, o);
                     if (lane >= o) inc += t;
                 }
-                const unsigned fit = __ballot_sync(FULL, k < nb1 && inc <= STAGE);
+                const unsigned fit = __ballot_sync(FULL, k < nb1 && inc <= ST);
                 const int nfit = __popc(fit);
                 int ns, nl;
-                if (nfit == 0) { ns = STAGE; nl = 1; }
+                if (nfit == 0) { ns = ST; nl = 1; }
                 else { ns = __shfl_sync(FULL, inc, nfit - 1); nl = nfit; }
                 pre[lane] = inc - cnt;
                 fst[lane] = first;
@@ -1177,6 +1326,10 @@ __global__ void __launch_bounds__(128) k_eval_df(EvalDfArgs A)
                     two_sum(h.z, d[2], &sz, &ez_);
                     yh[idx] = make_float4(sx, sy, sz, h.w);
                     yl[idx] = make_float4(ex_ + (l.x + d[3]), ey_ + (l.y + d[4]), ez_ + (l.z + d[5]), l.w);
+                    if (ADJ) {
+                        s_gh[wid][idx] = A.doff[2 * j];
+                        s_gl[wid][idx] = A.doff[2 * j + 1];
+                    }
                     same = same && h.w == q0h && l.w == q0l;
                     sq = sq + dflt(h.w, l.w);
                 }
@@ -1184,11 +1337,24 @@ __global__ void __launch_bounds__(128) k_eval_df(EvalDfArgs A)
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) sq = sq + dfl_shfl_xor(sq, o);
                 mass = mass + sq;
-                if (nfit == 0) jn += STAGE;
+                if (nfit == 0) jn += ST;
                 else { kn += nfit; jn = 0; }
                 __syncwarp();
                 const dflt qm(q0h, q0l);
-                if (eqm) {
+                if (ADJ) {
+                    const float4* gh = s_gh[wid];
+                    const float4* gl = s_gl[wid];
+                    if (eqm && q0h == 0.f && q0l == 0.f) {        // no charges in the stage: dipoles only
+                        pair_sums_adj_df<PSI, false, true>(yh, yl, gh, gl, ns, sa, lpa, tha, tla, qm, s_tab, acc_a);
+                        if (nb) pair_sums_adj_df<PSI, false, true>(yh, yl, gh, gl, ns, sb, lpb, thb, tlb, qm, s_tab, acc_b);
+                    } else if (eqm) {
+                        pair_sums_adj_df<PSI, true, true>(yh, yl, gh, gl, ns, sa, lpa, tha, tla, qm, s_tab, acc_a);
+                        if (nb) pair_sums_adj_df<PSI, true, true>(yh, yl, gh, gl, ns, sb, lpb, thb, tlb, qm, s_tab, acc_b);
+                    } else {
+                        pair_sums_adj_df<PSI, true, false>(yh, yl, gh, gl, ns, sa, lpa, tha, tla, qm, s_tab, acc_a);
+                        if (nb) pair_sums_adj_df<PSI, true, false>(yh, yl, gh, gl, ns, sb, lpb, thb, tlb, qm, s_tab, acc_b);
+                    }
+                } else if (eqm) {
                     pair_sums_df<PSI, true>(yh, yl, ns, sa, lpa, tha, tla, qm, s_tab, acc_a);
                     if (nb) pair_sums_df<PSI, true>(yh, yl, ns, sb, lpb, thb, tlb, qm, s_tab, acc_b);
                 } else {
@@ -1201,16 +1367,21 @@ __global__ void __launch_bounds__(128) k_eval_df(EvalDfArgs A)
             else acc_a[4] = -acc_a[4];
             if (sb == 0) acc_b[4] = mass - acc_b[4];
             else acc_b[4] = -acc_b[4];
-            // the sums of each target's lanes, in the order (x, y, z, q, log) the finish takes
-            dflt na_[5], nb_[5];
+            // the sums of each target's lanes, in the order (x, y, z, q, log, ...) the finish takes
+            dflt na_[NACC], nb_[NACC];
 #pragma unroll
-            for (int c = 0; c < 5; ++c) {
-                const int cc = c < 3 ? c : 7 - c;            // 3 <- q (acc[4]), 4 <- log (acc[3])
+            for (int c = 0; c < NACC; ++c) {
+                const int cc = c == 3 ? 4 : c == 4 ? 3 : c;     // 3 <- q (acc[4]), 4 <- log (acc[3])
                 na_[c] = group_sum_dfl(dfl_norm(acc_a[cc]), lpa);
                 nb_[c] = group_sum_dfl(dfl_norm(acc_b[cc]), lpb);
             }
-            if (sa == 0) finish_target_df<PSI>(A, G, L, ta, tha, tla, na_, s_tab, shift);
-            if (act_b && sb == 0) finish_target_df<PSI>(A, G, L, tbx, thb, tlb, nb_, s_tab, shift);
+            if (ADJ) {
+                if (sa == 0) finish_target_adj_df<PSI>(A, G, L, ta, tha, tla, na_, s_tab, shift);
+                if (act_b && sb == 0) finish_target_adj_df<PSI>(A, G, L, tbx, thb, tlb, nb_, s_tab, shift);
+            } else {
+                if (sa == 0) finish_target_df<PSI>(A, G, L, ta, tha, tla, na_, s_tab, shift);
+                if (act_b && sb == 0) finish_target_df<PSI>(A, G, L, tbx, thb, tlb, nb_, s_tab, shift);
+            }
             tb += na + nb;
         }
     }
@@ -1363,6 +1534,7 @@ cudaError_t launch_eval_df(const TreeView& T, const int* leaves, int64_t n_leave
                            const float4* toff, const float4* dc, const double4_32a* tgt, const uint32_t* tperm,
                            const int64_t* p2p_off, const uint32_t* p2p_src, const void* local, const void* mpole,
                            const float4* log_tab, int p, int zero_mean, double* psi, double* alpha,
+                           const float4* doff, const void* w, int w_f32, double* grad3,
                            unsigned long long* leaf_ctr, cudaStream_t s)
 {
     if (n_leaves == 0) return cudaSuccess;
@@ -1386,11 +1558,20 @@ cudaError_t launch_eval_df(const TreeView& T, const int* leaves, int64_t n_leave
     A.psi = psi;
     A.alpha = alpha;
     A.leaf_ctr = leaf_ctr;
+    A.doff = doff;
+    A.w = w;
+    A.w_f32 = w_f32;
+    A.grad3 = grad3;
     int64_t blocks = 0;
     cudaError_t e;
     if ((e = leaf_grid(leaf_ctr, n_leaves, 16, s, &blocks))) return e;
-    if (psi) k_eval_df<true><<<(unsigned)blocks, 128, 0, s>>>(A);
-    else k_eval_df<false><<<(unsigned)blocks, 128, 0, s>>>(A);
+    if (doff) {
+        if (psi) k_eval_df<true, true><<<(unsigned)blocks, 128, 0, s>>>(A);
+        else k_eval_df<false, true><<<(unsigned)blocks, 128, 0, s>>>(A);
+    } else {
+        if (psi) k_eval_df<true, false><<<(unsigned)blocks, 128, 0, s>>>(A);
+        else k_eval_df<false, false><<<(unsigned)blocks, 128, 0, s>>>(A);
+    }
     count_launch();
     return cudaGetLastError();
 }

@@ -194,9 +194,17 @@ __global__ void __launch_bounds__(128) k_l2l_df(TreeView T, int a, int b, int lv
 // holds q, q log(1 - |D|^2/4) = 2 q log cos(theta/2), and q z^l; lane k then
 // sums columns k and k + 32 over the leaf's sources, and the multipole is
 // Q = sum q / 4pi, C = (1/4pi) sum q log(..) - Q log 2, A_l = -(1/(4 pi l)) sum q z^l.
-template <int P>
+//
+// DIP (the adjoint): each source also carries a tangent dipole g (doff: its
+// (hi, lo) parts).  A dipole's potential is the derivative of the point mass's
+// along g, so its multipole is Lemma 1 differentiated along g: with
+// 1 + x.c = 2 - |D|^2/2, dz = [(g.e_theta + i g.e_phi) - z (g.c)] / (1 + x.c)
+// (scaled by 1/r like z), dC = (1/4pi) (g.c) / (1 + x.c), dQ = 0 and
+// dA_l = -(1/4pi) z^(l-1) dz; the row holds q z^l + l z^(l-1) dz for column l.
+template <int P, bool DIP>
 __global__ void __launch_bounds__(128) k_p2m_df_leaf(TreeView T, const int* __restrict__ leaves, int64_t n_cap,
                                                      const int64_t* d_nl, const float4* __restrict__ off,
+                                                     const float4* __restrict__ doff,
                                                      const float4* __restrict__ log_tab, int p, dflt* __restrict__ mpole)
 {
     const int64_t n_leaves = dcount(d_nl, n_cap);
@@ -214,6 +222,7 @@ __global__ void __launch_bounds__(128) k_p2m_df_leaf(TreeView T, const int* __re
         const double* g = T.geom + (size_t)node * GEOM_STRIDE;
         const dflt etx(g[3]), ety(g[4]), etz(g[5]), epx(g[6]), epy(g[7]), epz(g[8]);
         const dflt inv_r(1.0 / g[10]);
+        const dflt ccx(g[0]), ccy(g[1]), ccz(g[2]);
         const int f = T.first[node], n = T.count[node];
         dflt sc[3] = {dflt(0.f, 0.f), dflt(0.f, 0.f), dflt(0.f, 0.f)};   // this lane's columns lane + 32 i (2p + 2 <= 66)
         for (int j0 = 0; j0 < n; j0 += 32) {
@@ -222,20 +231,40 @@ __global__ void __launch_bounds__(128) k_p2m_df_leaf(TreeView T, const int* __re
                 const float4 h = off[2 * (size_t)(f + j)], lo = off[2 * (size_t)(f + j) + 1];
                 const dflt dx(h.x, lo.x), dy(h.y, lo.y), dz(h.z, lo.z), q(h.w, lo.w);
                 const dflt d2 = dx * dx + dy * dy + dz * dz;
-                const dflt sc = inv_r / (dflt(2.f, 0.f) - d2 * 0.5f);
+                const dflt opc = dflt(2.f, 0.f) - d2 * 0.5f;                         // 1 + x.c
+                const dflt inv = DIP ? dflt(1.f, 0.f) / opc : dflt(0.f, 0.f);
+                const dflt sc = inv_r / opc;
                 const dflt zr = (dx * etx + dy * ety + dz * etz) * sc;
                 const dflt zi = (dx * epx + dy * epy + dz * epz) * sc;
                 row[0] = q * dfl_norm(dfl_log_lazy(dflt(1.f, 0.f) - d2 * 0.25f, s_tab));
                 row[1] = q;
                 dflt pr = q, pi(0.f, 0.f);
+                dflt qr(0.f, 0.f), qi(0.f, 0.f);     // z^(l-1) dz (DIP)
+                if (DIP) {
+                    const float4 gh = doff[2 * (size_t)(f + j)], gl = doff[2 * (size_t)(f + j) + 1];
+                    const dflt gx(gh.x, gl.x), gy(gh.y, gl.y), gz(gh.z, gl.z);
+                    const dflt gc = gx * ccx + gy * ccy + gz * ccz;
+                    const dflt gci = gc * inv;
+                    row[0] = row[0] + gci;
+                    qr = (gx * etx + gy * ety + gz * etz) * sc - zr * gci;
+                    qi = (gx * epx + gy * epy + gz * epz) * sc - zi * gci;
+                }
 #pragma unroll 1
                 for (int l = 1; l <= p; ++l) {
                     dflt nr, ni;
                     cmul_df(pr, pi, zr, zi, &nr, &ni);
                     pr = nr;
                     pi = ni;
-                    row[2 * l] = pr;
-                    row[2 * l + 1] = pi;
+                    if (DIP) {
+                        row[2 * l] = pr + qr * (float)l;
+                        row[2 * l + 1] = pi + qi * (float)l;
+                        cmul_df(qr, qi, zr, zi, &nr, &ni);
+                        qr = nr;
+                        qi = ni;
+                    } else {
+                        row[2 * l] = pr;
+                        row[2 * l + 1] = pi;
+                    }
                 }
             }
             __syncwarp();
@@ -305,13 +334,20 @@ cudaError_t l2l_p(const TreeView& T, int a, int b, int lvl, int p, const void* g
 
 template <int P>
 cudaError_t p2m_p(const TreeView& T, const int* leaves, int64_t n_leaves, const int64_t* d_nl, const float4* off,
-                  const float4* log_tab, int p, void* mpole, cudaStream_t s)
+                  const float4* doff, const float4* log_tab, int p, void* mpole, cudaStream_t s)
 {
     const size_t smem = (size_t)UW * 32 * (2 * P + 3) * sizeof(dflt);
     cudaError_t e;
-    if ((e = smem_attr(k_p2m_df_leaf<P>, smem))) return e;
-    k_p2m_df_leaf<P><<<grid_of(n_leaves, UW, 152 * 32), UW * 32, smem, s>>>(T, leaves, n_leaves, d_nl, off, log_tab,
-                                                                              p, static_cast<dflt*>(mpole));
+    const unsigned grid = grid_of(n_leaves, UW, 152 * 32);
+    if (doff) {
+        if ((e = smem_attr(k_p2m_df_leaf<P, true>, smem))) return e;
+        k_p2m_df_leaf<P, true><<<grid, UW * 32, smem, s>>>(T, leaves, n_leaves, d_nl, off, doff, log_tab, p,
+                                                           static_cast<dflt*>(mpole));
+    } else {
+        if ((e = smem_attr(k_p2m_df_leaf<P, false>, smem))) return e;
+        k_p2m_df_leaf<P, false><<<grid, UW * 32, smem, s>>>(T, leaves, n_leaves, d_nl, off, nullptr, log_tab, p,
+                                                            static_cast<dflt*>(mpole));
+    }
     count_launch();
     return cudaGetLastError();
 }
@@ -348,11 +384,13 @@ cudaError_t launch_l2l_df(const TreeView& T, int a, int b, int lvl, int p, const
 #undef CALL
 }
 
+// doff: NULL, or the sources' tangent dipoles as (hi, lo) float4 pairs (the adjoint)
 cudaError_t launch_p2m_df_leaf(const TreeView& T, const int* leaves, int64_t n_leaves, const int64_t* d_nl,
-                               const float4* off, const float4* log_tab, int p, void* mpole, cudaStream_t s)
+                               const float4* off, const float4* doff, const float4* log_tab, int p, void* mpole,
+                               cudaStream_t s)
 {
     if (n_leaves == 0) return cudaSuccess;
-#define CALL(PP) p2m_p<PP>(T, leaves, n_leaves, d_nl, off, log_tab, p, mpole, s)
+#define CALL(PP) p2m_p<PP>(T, leaves, n_leaves, d_nl, off, doff, log_tab, p, mpole, s)
     SFMM_P_SWITCH(CALL)
 #undef CALL
 }

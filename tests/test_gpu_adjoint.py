@@ -47,8 +47,8 @@ def test_adjoint_random_sky(which):
 
 
 def test_adjoint_clustered_near_field_heavy_and_mixed_plan():
-    """Clustered sources and targets, small leaves; a plan made for the mixed
-    path still runs its adjoint in FP64."""
+    """Clustered sources and targets, small leaves; the FP64 adjoint and the
+    double-float one (the adjoint of a plan made for the mixed path)."""
     rng = np.random.default_rng(12)
     clumps = workloads.clump_set(rng, 20)
     src = workloads.clustered(rng, 40000, 20, clumps=clumps)
