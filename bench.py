@@ -40,7 +40,7 @@ METRIC = "sFMM Mpts/s (N=M=1.6e7) FP64 vs mixed precision, at stated relative er
 # mixed_df and fp64 (1e-10): the fastest settings within half the stated error on this workload
 #   (tune.autotune over the default candidate grids: errors 2.2e-11 and 3.0e-11);
 # fp32 (3e-5): the all-FP32 path with tensor-core M2L.
-MODES = [("mixed", 1, 20, 1e-6, 64, 1.5, 0.5), ("mixed_df", 2, 32, 1e-10, 64, 1.5, 0.45),
+MODES = [("mixed", 1, 20, 1e-6, 96, 1.5, 0.5), ("mixed_df", 2, 28, 1e-10, 64, 1.6, 0.45),
          ("fp64", 0, 32, 1e-10, 32, 1.5, 0.45), ("fp32", 3, 20, 3e-5, 64, 1.3, 0.5)]
 # the FP64 reference every path is compared with on all M targets: error ~3e-13 on this workload
 REF_SETTINGS = dict(p=32, leaf_size=32, c_s=2.0, c_t=0.45)
@@ -54,9 +54,11 @@ EVAL_KERNEL = {"mixed": "k_eval32 (FP32 near field, double-float L2P and combina
                "mixed_df": "k_eval_df (near field and L2P in double-float)",
                "fp64": "k_eval (near field and L2P in FP64)",
                "fp32": "k_eval32 (near field and L2P in FP32)"}
-# DRAM bytes of one k_eval32 launch of the all-FP32 path (p = 20, m = 64, c_s = 1.3) at this
-# workload, from ncu (dram__bytes_read.sum 5.33 GB + dram__bytes_write.sum 1.01 GB)
-K_EVAL32_TRAFFIC = 5.33e9 + 1.01e9
+# DRAM bytes of one k_eval32 launch of the headline path (p = 20, m = 96, c_s = 1.5 at N = M = 1.6e7):
+# ncu at N = M = 2e6 (profiles/k_eval32_mixed_clustered_2e6.md), scaled by the near-field pairs
+K_EVAL32_TRAFFIC = (368.0e6 + 86.5e6) * (1.3399e10 / 1.1019e9)
+K_EVAL32_TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one k_eval32 launch at N = M = 2e6 "
+                           "(368.0 + 86.5 MB, 1.10e9 pairs), scaled by the near-field pairs to this launch (x 12.16)")
 
 
 def parse():
@@ -326,8 +328,8 @@ def run_shells(args, dev, clock_sampler, ws=1, rank=0):
     from oracle.direct import direct_sum
     big = mine[int(np.argmax([sizes[k] for k in mine]))] if mine else None
     idx = workloads.subsample(M, min(args.check, 100), 8, stream=9)
-    for name, prec, kw in (("mixed", sfmm.SFMM_MIXED, dict(p=20, leaf_size=64, c_s=1.5, c_t=0.5)),
-                           ("mixed_df", sfmm.SFMM_MIXED_DF, dict(p=32, leaf_size=64, c_s=1.5, c_t=0.45))):
+    for name, prec, kw in (("mixed", sfmm.SFMM_MIXED, dict(p=20, leaf_size=96, c_s=1.5, c_t=0.5)),
+                           ("mixed_df", sfmm.SFMM_MIXED_DF, dict(p=28, leaf_size=64, c_s=1.6, c_t=0.45))):
         plan = sfmm.Plan(precision=prec, **kw)
         for lanes in (4, 1):
             outs = plan.deflection_batch(sh, with_psi=False, lanes=lanes) if sh else []
@@ -616,11 +618,10 @@ def run_sfmm(args):
                "pairs_per_launch": r["pairs"], "launch_ms": r["eval_ms"], "traffic": None}
         if not fp64:
             out["mufu_frac"] = r["pairs"] * MUFU_PER_PAIR / secs / peaks["mufu"]
-        if (r["precision"] == "fp32" and r["leaf_size"] == 64 and r["c_s"] == 1.3 and N == 16_000_000
-                and M == 16_000_000 and args.clumps == 20_000):
+        if (K_EVAL32_TRAFFIC is not None and r["precision"] == "mixed" and r["leaf_size"] == 96
+                and r["c_s"] == 1.5 and N == 16_000_000 and M == 16_000_000 and args.clumps == 20_000):
             out["traffic"] = K_EVAL32_TRAFFIC
-            out["traffic_source"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch of k_eval32 "
-                                     "at this workload (5.33 GB read + 1.01 GB written)")
+            out["traffic_source"] = K_EVAL32_TRAFFIC_SOURCE
         return out
 
     modes = {}

@@ -24,10 +24,11 @@ def _grid(ps, ms, css, cts):
 
 DEFAULT_CANDIDATES = {
     # the benchmark sky's best settings first, then their neighbours in p, c_s and leaf size
-    sfmm.SFMM_MIXED: _grid((20,), (64,), (1.5, 1.3, 2.0), (0.5,)) + _grid((16, 24), (64,), (1.5, 2.0), (0.5,))
-                     + _grid((20,), (48, 96), (1.5,), (0.5,)),
+    sfmm.SFMM_MIXED: _grid((20,), (96,), (1.5, 1.3), (0.5,)) + _grid((20,), (64, 80, 128), (1.5,), (0.5,))
+                     + _grid((16, 24), (96,), (1.5, 2.0), (0.5,)),
     sfmm.SFMM_FP32: _grid((20,), (64, 48, 80), (1.3,), (0.5,)) + _grid((16,), (32, 64, 96), (2.0,), (0.5,)),
-    sfmm.SFMM_MIXED_DF: _grid((24, 26, 28), (48, 64, 96), (2.0,), (0.45,)) + _grid((28, 32), (64,), (1.5, 1.7), (0.45,)),
+    sfmm.SFMM_MIXED_DF: _grid((28,), (64,), (1.6, 1.7), (0.45,)) + _grid((30, 32), (64, 96), (1.5, 1.6), (0.45,))
+                        + _grid((24, 26), (64,), (2.0,), (0.45,)),
     # FP64: the near field (set by c_s and m) dominates, so c_s is varied with p and c_t
     sfmm.SFMM_FP64: _grid((24, 28, 32), (32, 64), (1.3, 1.5, 2.0), (0.45,)) + _grid((28, 32), (32, 64), (2.0,), (0.5,)),
 }

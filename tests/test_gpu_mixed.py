@@ -20,7 +20,7 @@ from paper_2210_07021_gb300 import sfmm, workloads
 from conftest import unit
 
 TOL_MIXED = 1e-6
-BENCH = dict(p=20, leaf=64, c_s=1.5, c_t=0.5)
+BENCH = dict(p=20, leaf=96, c_s=1.5, c_t=0.5)
 
 
 def rel(a, b):
