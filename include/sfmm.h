@@ -167,8 +167,9 @@ sfmm_status sfmm_deflection_batch(sfmm_plan_t plan, int n_shells, const double* 
  * capacities and its counts read on the device.  The sizes N[i], M[i] and the
  * buffers are fixed by the capture; their CONTENTS may change between
  * launches (new positions and masses).  The caller keeps the buffers alive
- * until sfmm_graph_release or sfmm_destroy.  Plans of precision SFMM_MIXED or
- * SFMM_MIXED_DF only (SFMM_EINVAL otherwise).  A previous capture is released.
+ * until sfmm_graph_release or sfmm_destroy.  Plans of precision SFMM_FP64,
+ * SFMM_MIXED or SFMM_MIXED_DF with point masses (sigma == 0); SFMM_EINVAL
+ * otherwise.  A previous capture is released.
  *
  * sfmm_graph_launch replays the graph on the plan's stream and waits for it
  * (one synchronisation for all shells).  A shell whose new data outgrew a

@@ -26,14 +26,15 @@ void fill_tables(double* h);
 size_t xgeo_bytes(int ek);
 cudaError_t launch_geom32(int n_nodes, const double* geom, float* g32, cudaStream_t s);
 cudaError_t launch_pair_geo(const TreeView& T, const float* g32, const uint64_t* tt, const uint32_t* ss, int64_t n,
-                            void* out, int ek, cudaStream_t s);
+                            const int64_t* d_n, void* out, int ek, cudaStream_t s);
 cudaError_t launch_child_geo(const TreeView& T, const float* g32, void* m2m, void* l2l, int ek, cudaStream_t s);
 cudaError_t launch_src_offsets(const TreeView& T, const int* leaves, int64_t n_leaves, const int64_t* d_nl,
                                const double4_32a* src, float4* off, cudaStream_t s);
-cudaError_t launch_p2m(const TreeView& T, const int* leaves, int64_t n_leaves, const double4_32a* src,
-                       const float4* off, const float4* log_tab, void* mpole, int p, int ek, cudaStream_t s);
-cudaError_t launch_m2m(const TreeView& T, int a, int b, int p, const double* tables, const void* geo, void* mpole,
-                       int ek, cudaStream_t s);
+cudaError_t launch_p2m(const TreeView& T, const int* leaves, int64_t n_leaves, const int64_t* d_nl,
+                       const double4_32a* src, const float4* off, const float4* log_tab, void* mpole, int p, int ek,
+                       cudaStream_t s);
+cudaError_t launch_m2m(const TreeView& T, int a, int b, int lvl, int p, const double* tables, const void* geo,
+                       void* mpole, int ek, cudaStream_t s);
 cudaError_t launch_m2l(const TreeView& T, const int64_t* off, const uint32_t* srcs, int p, const double* tables,
                        const void* geo, const void* mpole, void* local, int ek, cudaStream_t s);
 cudaError_t launch_m2l_list(const uint64_t* ptgt, const uint32_t* psrc, const uint32_t* list, const uint32_t* n_list,
@@ -42,8 +43,8 @@ cudaError_t launch_m2l_list(const uint64_t* ptgt, const uint32_t* psrc, const ui
 cudaError_t launch_m2l_tc(int64_t n_pairs, const uint64_t* ptgt, const uint32_t* psrc, const void* geo,
                           const void* mpole, void* local, int p, uint32_t* leftover, uint32_t* n_leftover,
                           uint32_t* tile_ctr, int* status, int wait_limit, cudaStream_t s);
-cudaError_t launch_l2l(const TreeView& T, int a, int b, int p, const double* tables, const void* geo, void* local,
-                       int ek, cudaStream_t s);
+cudaError_t launch_l2l(const TreeView& T, int a, int b, int lvl, int p, const double* tables, const void* geo,
+                       void* local, int ek, cudaStream_t s);
 size_t frame_df_bytes();
 cudaError_t launch_frame_df(int n_nodes, const int64_t* d_nn, const double* geom, void* out, cudaStream_t s);
 cudaError_t launch_pair_geo_rho(const TreeView& T, const void* frames, const float4* log_tab, const uint64_t* tt,
@@ -311,8 +312,8 @@ sfmm_status solve(sfmm_plan_s* P, const double* src, const void* q, int64_t N, c
     // and near fields (its own near-field kernel, charges and dipoles)
     const bool adj_df = adj && P->opt.precision != SFMM_FP64;
     const int precision = gamma ? SFMM_FP64 : adj ? (adj_df ? SFMM_MIXED_DF : SFMM_FP64) : P->opt.precision;
-    if (P->gm && !(precision == SFMM_MIXED || precision == SFMM_MIXED_DF))
-        return fail(P, SFMM_EINVAL, "graph mode runs the double-float far field only (SFMM_MIXED, SFMM_MIXED_DF)");
+    if (P->gm && !(precision == SFMM_MIXED || precision == SFMM_MIXED_DF || precision == SFMM_FP64))
+        return fail(P, SFMM_EINVAL, "graph mode runs SFMM_FP64, SFMM_MIXED and SFMM_MIXED_DF plans");
     const int q_f32 = adj ? 0 : P->opt.q_f32;
     cudaError_t e;
     const int p = P->p;
@@ -441,18 +442,19 @@ sfmm_status solve(sfmm_plan_s* P, const double* src, const void* q, int64_t N, c
     else if (dfe) e = launch_p2m_df_leaf(T, P->leaves_src.as<int>(), P->n_leaves, d_nls, P->soff.as<float4>(),
                                          adj_df ? P->dip4.as<float4>() : nullptr, P->logtab.as<float4>(), p,
                                          P->mpole.p, s);
-    else e = launch_p2m(T, P->leaves_src.as<int>(), P->n_leaves, P->src4.as<double4_32a>(), P->soff.as<float4>(),
-                        P->logtab.as<float4>(), P->mpole.p, p, ek, s);
+    else e = launch_p2m(T, P->leaves_src.as<int>(), P->n_leaves, d_nls, P->src4.as<double4_32a>(),
+                        P->soff.as<float4>(), P->logtab.as<float4>(), P->mpole.p, p, ek, s);
     if (e) return cuda_fail(P, e, "P2M");
     // graph mode: every level up to the capacity, each launch sized by the level-width capacity
     const int depth = P->gm ? (int)P->cap.levels : (int)P->level_start.size() - 2;
     const int W = (int)P->cap.width;
     for (int l = depth - 1; l >= 0; --l) {
-        if (P->gm) e = launch_m2m_df(T, 0, W, l, p, P->m2m_geo.p, P->mpole.p, s);
-        else if (dfe) e = launch_m2m_df(T, P->level_start[l + 1], P->level_start[l + 2], l, p, P->m2m_geo.p,
-                                        P->mpole.p, s);
-        else e = launch_m2m(T, P->level_start[l], P->level_start[l + 1], p, P->tables.as<double>(), P->m2m_geo.p,
-                            P->mpole.p, ek, s);
+        if (dfe) e = P->gm ? launch_m2m_df(T, 0, W, l, p, P->m2m_geo.p, P->mpole.p, s)
+                           : launch_m2m_df(T, P->level_start[l + 1], P->level_start[l + 2], l, p, P->m2m_geo.p,
+                                           P->mpole.p, s);
+        else e = P->gm ? launch_m2m(T, 0, W, l, p, P->tables.as<double>(), P->m2m_geo.p, P->mpole.p, ek, s)
+                       : launch_m2m(T, P->level_start[l], P->level_start[l + 1], l, p, P->tables.as<double>(),
+                                    P->m2m_geo.p, P->mpole.p, ek, s);
         if (e) return cuda_fail(P, e, "M2M");
     }
     tm.mark();
@@ -490,7 +492,8 @@ sfmm_status solve(sfmm_plan_s* P, const double* src, const void* q, int64_t N, c
                                     P->tables.as<double>(), P->mpole.p, P->m2l_acc.as<double>(), s)))
             return cuda_fail(P, e, "M2L (pairs near antipodes)");
     } else if ((e = cudaMemsetAsync(P->local.p, 0, (size_t)nn * EXP_STRIDE * esz, s)) ||
-               (e = launch_pair_geo(T, P->geom32.as<float>(), m2l_t, m2l_s, P->n_m2l, P->m2l_geo.p, ek, s))) {
+               (e = launch_pair_geo(T, P->geom32.as<float>(), m2l_t, m2l_s, P->n_m2l, P->d_m2l, P->m2l_geo.p, ek,
+                                    s))) {
         return cuda_fail(P, e, "pair geometry");
     } else if (fp32 && P->opt.m2l_tensor_cores) {
         // tensor-core M2L; pairs it cannot take (centres near antipodes) go to a list for the warp kernel
@@ -518,8 +521,9 @@ sfmm_status solve(sfmm_plan_s* P, const double* src, const void* q, int64_t N, c
                 return cuda_fail(P, e, "L2L");
     } else {
         for (int l = 1; l <= depth; ++l)
-            if ((e = launch_l2l(T, P->level_start[l], P->level_start[l + 1], p, P->tables.as<double>(), P->l2l_geo.p,
-                                P->local.p, ek, s)))
+            if ((e = P->gm ? launch_l2l(T, 0, W, l, p, P->tables.as<double>(), P->l2l_geo.p, P->local.p, ek, s)
+                           : launch_l2l(T, P->level_start[l], P->level_start[l + 1], l, p, P->tables.as<double>(),
+                                        P->l2l_geo.p, P->local.p, ek, s)))
                 return cuda_fail(P, e, "L2L");
     }
     tm.mark();

@@ -184,8 +184,10 @@ __global__ void k_geom32(int n_nodes, const double* __restrict__ geom, float* __
 }
 
 __global__ void k_pair_geo32(TreeView T, const float* __restrict__ g32, const uint64_t* __restrict__ tt,
-                             const uint32_t* __restrict__ ss, int64_t n, XGeo32* __restrict__ out)
+                             const uint32_t* __restrict__ ss, int64_t n_cap, const int64_t* d_n,
+                             XGeo32* __restrict__ out)
 {
+    const int64_t n = dcount(d_n, n_cap);
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t s = ss[k], t = (uint32_t)tt[k];
         out[k] = make_geo32(K_M2L, T.geom + (size_t)s * GEOM_STRIDE, T.geom + (size_t)t * GEOM_STRIDE,
@@ -196,7 +198,8 @@ __global__ void k_pair_geo32(TreeView T, const float* __restrict__ g32, const ui
 __global__ void k_child_geo32(TreeView T, const float* __restrict__ g32, XGeo32* __restrict__ m2m,
                               XGeo32* __restrict__ l2l)
 {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < T.n_nodes; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t nn = dcount(T.d_nn, T.n_nodes);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nn; i += (int64_t)gridDim.x * blockDim.x) {
         const int par = T.parent[i];
         if (par < 0) continue;
         const double* gC = T.geom + (size_t)i * GEOM_STRIDE;
@@ -207,9 +210,10 @@ __global__ void k_child_geo32(TreeView T, const float* __restrict__ g32, XGeo32*
 }
 
 template <typename GR>
-__global__ void k_pair_geo(TreeView T, const uint64_t* __restrict__ tt, const uint32_t* __restrict__ ss, int64_t n,
-                           GR* __restrict__ out)
+__global__ void k_pair_geo(TreeView T, const uint64_t* __restrict__ tt, const uint32_t* __restrict__ ss, int64_t n_cap,
+                           const int64_t* d_n, GR* __restrict__ out)
 {
+    const int64_t n = dcount(d_n, n_cap);
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
         const double* gS = T.geom + (size_t)ss[k] * GEOM_STRIDE;
         const double* gT = T.geom + (size_t)tt[k] * GEOM_STRIDE;
@@ -356,7 +360,8 @@ __global__ void k_child_geo_df(TreeView T, const FrameDF* __restrict__ fr, const
 template <typename GR>
 __global__ void k_child_geo(TreeView T, GR* __restrict__ m2m, GR* __restrict__ l2l)
 {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < T.n_nodes; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t nn = dcount(T.d_nn, T.n_nodes);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nn; i += (int64_t)gridDim.x * blockDim.x) {
         const int par = T.parent[i];
         if (par < 0) continue;
         const double* gC = T.geom + (size_t)i * GEOM_STRIDE;
@@ -636,9 +641,10 @@ __device__ __forceinline__ void atomic_exp(ST* e, int lane, int p, R C, R Q, cx<
 // ----------------------------------------------------------------- P2M
 // FP64: from the key-sorted FP64 positions.
 template <int P, typename ST>
-__global__ void k_p2m(TreeView T, const int* __restrict__ leaves, int64_t n_leaves, const double4_32a* __restrict__ src,
-                      ST* __restrict__ mpole)
+__global__ void k_p2m(TreeView T, const int* __restrict__ leaves, int64_t n_cap, const int64_t* d_nl,
+                      const double4_32a* __restrict__ src, ST* __restrict__ mpole)
 {
+    const int64_t n_leaves = dcount(d_nl, n_cap);
     for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < n_leaves; w += (int64_t)gridDim.x * blockDim.x) {
         const int node = leaves[w];
         const double* g = T.geom + (size_t)node * GEOM_STRIDE;
@@ -850,9 +856,13 @@ __global__ void k_p2m32(TreeView T, const int* __restrict__ leaves, int64_t n_le
 // One warp per internal node of one level: sum of its children's multipoles
 // (pipelined over the non-empty children).
 template <typename R, typename GR, typename ST>
-__global__ void k_m2m(TreeView T, int a, int b, int p, const double* __restrict__ tables, const GR* __restrict__ geo,
-                      ST* __restrict__ mpole)
+__global__ void k_m2m(TreeView T, int a, int b, int lvl, int p, const double* __restrict__ tables,
+                      const GR* __restrict__ geo, ST* __restrict__ mpole)
 {
+    if (T.d_level) {              // graph mode: the parents are the nodes of level lvl
+        a = (int)T.d_level[lvl];
+        b = (int)T.d_level[lvl + 1];
+    }
     __shared__ FusedTables<R> tb;
     __shared__ FusedSmem<R> ws[4];
     load_fused_tables<R>(&tb, tables);
@@ -905,9 +915,13 @@ __global__ void k_m2l(TreeView T, const int64_t* __restrict__ off, const uint32_
 // ----------------------------------------------------------------- L2L
 // One warp per node of one level holding targets: local += L2L(parent local).
 template <typename R, typename GR, typename ST>
-__global__ void k_l2l(TreeView T, int a, int b, int p, const double* __restrict__ tables, const GR* __restrict__ geo,
-                      ST* __restrict__ local)
+__global__ void k_l2l(TreeView T, int a, int b, int lvl, int p, const double* __restrict__ tables,
+                      const GR* __restrict__ geo, ST* __restrict__ local)
 {
+    if (T.d_level) {              // graph mode: the nodes of level lvl
+        a = (int)T.d_level[lvl];
+        b = (int)T.d_level[lvl + 1];
+    }
     __shared__ Tables<R> tb;
     __shared__ WarpSmem<R> ws[4];
     load_tables<R>(&tb, tables);
@@ -1071,12 +1085,12 @@ cudaError_t launch_geom32(int n_nodes, const double* geom, float* g32, cudaStrea
 }
 
 cudaError_t launch_pair_geo(const TreeView& T, const float* g32, const uint64_t* tt, const uint32_t* ss, int64_t n,
-                            void* out, int ek, cudaStream_t s)
+                            const int64_t* d_n, void* out, int ek, cudaStream_t s)
 {
     if (n == 0) return cudaSuccess;
-    if (ek == EXP_F32) k_pair_geo32<<<grid_for(n, 256), 256, 0, s>>>(T, g32, tt, ss, n, static_cast<XGeo32*>(out));
-    else if (ek == EXP_DF) k_pair_geo<XGeoDF><<<grid_for(n, 256), 256, 0, s>>>(T, tt, ss, n, static_cast<XGeoDF*>(out));
-    else k_pair_geo<XGeo><<<grid_for(n, 256), 256, 0, s>>>(T, tt, ss, n, static_cast<XGeo*>(out));
+    if (ek == EXP_F32) k_pair_geo32<<<grid_for(n, 256), 256, 0, s>>>(T, g32, tt, ss, n, d_n, static_cast<XGeo32*>(out));
+    else if (ek == EXP_DF) k_pair_geo<XGeoDF><<<grid_for(n, 256), 256, 0, s>>>(T, tt, ss, n, d_n, static_cast<XGeoDF*>(out));
+    else k_pair_geo<XGeo><<<grid_for(n, 256), 256, 0, s>>>(T, tt, ss, n, d_n, static_cast<XGeo*>(out));
     count_launch();
     return cudaGetLastError();
 }
@@ -1100,8 +1114,9 @@ cudaError_t launch_src_offsets(const TreeView& T, const int* leaves, int64_t n_l
 }
 
 // mpole: double (FP64 path), float (mixed path) or double-float storage (1e-10 mixed path)
-cudaError_t launch_p2m(const TreeView& T, const int* leaves, int64_t n_leaves, const double4_32a* src,
-                       const float4* off, const float4* log_tab, void* mpole, int p, int ek, cudaStream_t s)
+cudaError_t launch_p2m(const TreeView& T, const int* leaves, int64_t n_leaves, const int64_t* d_nl,
+                       const double4_32a* src, const float4* off, const float4* log_tab, void* mpole, int p, int ek,
+                       cudaStream_t s)
 {
     if (n_leaves == 0) return cudaSuccess;
     const unsigned g = grid_for(n_leaves, 128);
@@ -1109,7 +1124,7 @@ cudaError_t launch_p2m(const TreeView& T, const int* leaves, int64_t n_leaves, c
     case PP:                                                                                               \
         if (ek == EXP_F32) k_p2m32<PP><<<g, 128, 0, s>>>(T, leaves, n_leaves, off, static_cast<float*>(mpole)); \
         else if (ek == EXP_DF) k_p2m_df<PP><<<g, 128, 0, s>>>(T, leaves, n_leaves, off, log_tab, static_cast<dflt*>(mpole)); \
-        else k_p2m<PP, double><<<g, 128, 0, s>>>(T, leaves, n_leaves, src, static_cast<double*>(mpole));   \
+        else k_p2m<PP, double><<<g, 128, 0, s>>>(T, leaves, n_leaves, d_nl, src, static_cast<double*>(mpole)); \
         count_launch();                                                                                    \
         break;
     switch ((p + 3) / 4 * 4) {
@@ -1138,19 +1153,20 @@ cudaError_t launch_p2m_adj(const TreeView& T, const int* leaves, int64_t n_leave
     return cudaGetLastError();
 }
 
-cudaError_t launch_m2m(const TreeView& T, int a, int b, int p, const double* tables, const void* geo, void* mpole,
-                       int ek, cudaStream_t s)
+// parents a..b-1 (level lvl); graph mode: the bounds from the device, b - a the level-width capacity
+cudaError_t launch_m2m(const TreeView& T, int a, int b, int lvl, int p, const double* tables, const void* geo,
+                       void* mpole, int ek, cudaStream_t s)
 {
     if (b <= a) return cudaSuccess;
     const unsigned g = grid_for(b - a, 4);
     if (ek == EXP_F32)
-        k_m2m<float, XGeo32, float><<<g, 128, 0, s>>>(T, a, b, p, tables, static_cast<const XGeo32*>(geo),
+        k_m2m<float, XGeo32, float><<<g, 128, 0, s>>>(T, a, b, lvl, p, tables, static_cast<const XGeo32*>(geo),
                                                       static_cast<float*>(mpole));
     else if (ek == EXP_DF)
-        k_m2m<dflt, XGeoDF, dflt><<<g, 128, 0, s>>>(T, a, b, p, tables, static_cast<const XGeoDF*>(geo),
+        k_m2m<dflt, XGeoDF, dflt><<<g, 128, 0, s>>>(T, a, b, lvl, p, tables, static_cast<const XGeoDF*>(geo),
                                                     static_cast<dflt*>(mpole));
     else
-        k_m2m<double, XGeo, double><<<g, 128, 0, s>>>(T, a, b, p, tables, static_cast<const XGeo*>(geo),
+        k_m2m<double, XGeo, double><<<g, 128, 0, s>>>(T, a, b, lvl, p, tables, static_cast<const XGeo*>(geo),
                                                       static_cast<double*>(mpole));
     count_launch();
     return cudaGetLastError();
@@ -1233,19 +1249,20 @@ cudaError_t launch_acc_to_df(int64_t n, const double* acc, void* out, cudaStream
     return cudaGetLastError();
 }
 
-cudaError_t launch_l2l(const TreeView& T, int a, int b, int p, const double* tables, const void* geo, void* local,
-                       int ek, cudaStream_t s)
+// nodes a..b-1 (level lvl); graph mode as launch_m2m
+cudaError_t launch_l2l(const TreeView& T, int a, int b, int lvl, int p, const double* tables, const void* geo,
+                       void* local, int ek, cudaStream_t s)
 {
     if (b <= a) return cudaSuccess;
     const unsigned g = grid_for(b - a, 4);
     if (ek == EXP_F32)
-        k_l2l<float, XGeo32, float><<<g, 128, 0, s>>>(T, a, b, p, tables, static_cast<const XGeo32*>(geo),
+        k_l2l<float, XGeo32, float><<<g, 128, 0, s>>>(T, a, b, lvl, p, tables, static_cast<const XGeo32*>(geo),
                                                       static_cast<float*>(local));
     else if (ek == EXP_DF)
-        k_l2l<dflt, XGeoDF, dflt><<<g, 128, 0, s>>>(T, a, b, p, tables, static_cast<const XGeoDF*>(geo),
+        k_l2l<dflt, XGeoDF, dflt><<<g, 128, 0, s>>>(T, a, b, lvl, p, tables, static_cast<const XGeoDF*>(geo),
                                                     static_cast<dflt*>(local));
     else
-        k_l2l<double, XGeo, double><<<g, 128, 0, s>>>(T, a, b, p, tables, static_cast<const XGeo*>(geo),
+        k_l2l<double, XGeo, double><<<g, 128, 0, s>>>(T, a, b, lvl, p, tables, static_cast<const XGeo*>(geo),
                                                       static_cast<double*>(local));
     count_launch();
     return cudaGetLastError();

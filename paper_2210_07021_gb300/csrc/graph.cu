@@ -209,8 +209,10 @@ sfmm_status sfmm_graph_capture(sfmm_plan_t plan, int n_shells, const double* con
     if (!src_xyz || !q || !N || !tgt_xyz || !M || !alpha)
         return plan_error(plan, SFMM_EINVAL, "NULL array of shells");
     if (!(slack >= 0.0 && slack <= 16.0)) return plan_error(plan, SFMM_EINVAL, "slack must be in [0, 16]");
-    if (plan->opt.precision != SFMM_MIXED && plan->opt.precision != SFMM_MIXED_DF)
-        return plan_error(plan, SFMM_EINVAL, "graph-launched shells run SFMM_MIXED or SFMM_MIXED_DF plans");
+    if (plan->opt.precision == SFMM_FP32)
+        return plan_error(plan, SFMM_EINVAL, "graph-launched shells run SFMM_FP64, SFMM_MIXED or SFMM_MIXED_DF plans");
+    if (plan->opt.sigma > 0.0)
+        return plan_error(plan, SFMM_EINVAL, "graph-launched shells run point masses only (sigma == 0)");
     for (int i = 0; i < n_shells; ++i) {
         if (N[i] < 0 || M[i] < 0 || N[i] > 0x7fffffffLL || M[i] > 0x7fffffffLL)
             return plan_error(plan, SFMM_EINVAL, "N and M must be in [0, 2^31)");

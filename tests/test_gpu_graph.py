@@ -162,9 +162,27 @@ def test_empty_shells_and_double_float_path():
     plan.close()
 
 
-def test_graph_refuses_fp64_and_release():
+def test_fp64_graph_matches_per_shell_solves():
+    """The FP64 path through the graph: the same results as per-shell FP64 solves
+    (deterministic kernels, the same lists) and the oracle to 1e-10."""
+    host, sh = make_shells([(51, 40_000, 8_000, 80), (52, 6_000, 3_000, 0), (53, 15_000, 5_000, 30)])
+    kw = dict(p=32, leaf_size=32, c_s=1.5, c_t=0.45)       # the FP64 path's settings for 1e-10
+    plan = sfmm.Plan(precision=sfmm.SFMM_FP64, **kw)
+    outs = plan.graph_capture(sh, with_psi=True)
+    plan.graph_launch()
+    torch.cuda.synchronize()
+    assert_agree(outs, per_shell(sh, sfmm.SFMM_FP64, **kw))
+    for k, ((src, q, tgt), (psi, alpha)) in enumerate(zip(host, outs)):
+        idx = workloads.subsample(tgt.shape[0], 300, 6, stream=k)
+        r = direct_sum(src, q, tgt[idx])
+        a = alpha.cpu().numpy()[idx]
+        assert np.linalg.norm(a - r["alpha"]) / np.linalg.norm(r["alpha"]) < 1e-10, k
+    plan.close()
+
+
+def test_graph_refuses_fp32_and_release():
     sh = make_shells([(41, 2_000, 1_000, 4)])[1]
-    plan = sfmm.Plan(precision=sfmm.SFMM_FP64, p=16)
+    plan = sfmm.Plan(precision=sfmm.SFMM_FP32, p=16)
     with pytest.raises(sfmm.SfmmError):
         plan.graph_capture(sh)
     assert plan.graph_info()["n_shells"] == 0
