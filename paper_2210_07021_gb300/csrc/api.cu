@@ -72,8 +72,8 @@ cudaError_t launch_eval32_prep(const TreeView& T, const int* leaves, int64_t n_l
 cudaError_t launch_eval32(const TreeView& T, const int* leaves, int64_t n_leaves, const int64_t* d_nl, const float4* soff,
                           const float4* toff, const float4* dc, const double4_32a* tgt, const uint32_t* tperm, const int64_t* p2p_off,
                           const uint32_t* p2p_src, const void* local, const void* mpole, bool dfar, int p, int zero_mean,
-                          double* psi, double* alpha, bool coincide, unsigned long long* leaf_ctr,
-                          cudaStream_t s);
+                          double* psi, double* alpha, bool coincide, float4* nf, int* tleaf,
+                          const void* frames, int64_t M, unsigned long long* leaf_ctr, cudaStream_t s);
 cudaError_t launch_count_pairs(const TreeView& T, const int* leaves, int64_t n_leaves, const int64_t* p2p_off,
                                const uint32_t* p2p_src, unsigned long long* out, cudaStream_t s);
 void fill_log_table(float* out);
@@ -547,10 +547,16 @@ sfmm_status solve(sfmm_plan_s* P, const double* src, const void* q, int64_t N, c
                                  P->dip4.as<double4_32a>(), P->tgt4.as<double4_32a>(), tperm, P->p2p_off.as<int64_t>(),
                                  p2p_s, P->local.as<double>(), P->mpole.as<double>(), p, P->opt.zero_mean, adj->w,
                                  adj->w_f32, psi, adj->grad3, leaf_ctr, s);
-    else if (near32) e = launch_eval32(T, P->leaves_tgt.as<int>(), P->n_leaves_tgt, d_nlt, P->soff.as<float4>(),
-                                P->toff.as<float4>(), P->dc.as<float4>(), P->tgt4.as<double4_32a>(), tperm, P->p2p_off.as<int64_t>(), p2p_s,
-                                P->local.p, P->mpole.p, !fp32, p, P->opt.zero_mean, psi, alpha,
-                                src == tgt, leaf_ctr, s);
+    else if (near32) {
+        // the double-float finish runs as its own kernel on the near field's sums
+        if (!fp32 && ((e = ensure(P->nfbuf, (size_t)M * 32)) || (e = ensure(P->tleaf, (size_t)M * 4))))
+            return cuda_fail(P, e, "alloc");
+        e = launch_eval32(T, P->leaves_tgt.as<int>(), P->n_leaves_tgt, d_nlt, P->soff.as<float4>(),
+                          P->toff.as<float4>(), P->dc.as<float4>(), P->tgt4.as<double4_32a>(), tperm,
+                          P->p2p_off.as<int64_t>(), p2p_s, P->local.p, P->mpole.p, !fp32, p, P->opt.zero_mean, psi,
+                          alpha, src == tgt, P->nfbuf.as<float4>(), P->tleaf.as<int>(), P->framedf.p, M, leaf_ctr,
+                          s);
+    }
     else if (dfe) e = launch_eval_df(T, P->leaves_tgt.as<int>(), P->n_leaves_tgt, d_nlt, P->soff.as<float4>(),
                                      P->toff.as<float4>(), P->dc.as<float4>(), P->tgt4.as<double4_32a>(), tperm,
                                      P->p2p_off.as<int64_t>(), p2p_s, P->local.p, P->mpole.p,
@@ -905,7 +911,7 @@ void sfmm_destroy(sfmm_plan_t plan)
                   &plan->leaves_tgt, &plan->m2l_geo, &plan->m2m_geo, &plan->l2l_geo, &plan->soff,
                   &plan->toff, &plan->dc, &plan->leftover, &plan->geom32, &plan->macn, &plan->logtab,
                   &plan->ttmp, &plan->dip4, &plan->adj_h, &plan->adj_g, &plan->macn32, &plan->m2l_acc,
-                  &plan->framedf, &plan->dcnt};
+                  &plan->framedf, &plan->dcnt, &plan->nfbuf, &plan->tleaf};
     if (plan->aux) cudaStreamSynchronize(plan->aux);
     graph_release(plan);
     for (sfmm_plan_s* L : plan->lanes) sfmm_destroy(L);

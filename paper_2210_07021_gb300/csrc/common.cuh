@@ -132,6 +132,7 @@ struct sfmm_plan_s {
         int64_t nodes = 0, width = 0, levels = 0, m2l = 0, p2p = 0, front = 0;
     } cap;
     sfmm::Buf dcnt;
+    sfmm::Buf nfbuf, tleaf;                // 1e-6 path: near-field sums and leaf per sorted target
     int64_t last_max_width = 0;            // widest tree level of the last synchronised solve
     sfmm::GraphState* graph = nullptr;     // graph-launched shells (graph.cu), or NULL
     sfmm_stats stats{};

@@ -24,6 +24,7 @@
 // leaf: the power of two not below the leaf's targets.)
 #include "common.cuh"
 #include "dfloat.cuh"
+#include "xgeo.cuh"
 
 #include <cmath>
 
@@ -418,6 +419,12 @@ struct Eval32Args {
     double* psi;
     double* alpha;
     unsigned long long* leaf_ctr;   // zero at launch: the warps take target leaves from it one at a time
+    // double-float far field: the near field's sums per sorted target, for k_finish_dfar:
+    // nf[2t] = (x.h, x.l, y.h, y.l), nf[2t + 1] = (z.h, z.l, sum q, sum q log2 d^2), and its leaf
+    float4* nf;
+    int* tleaf;
+    const FrameDF* frames;    // the nodes' double-float frames (k_frame_df)
+    int64_t M;                // sorted targets
 };
 
 __device__ __forceinline__ float group_sumf(float v, int lpt)
@@ -684,6 +691,44 @@ __device__ __forceinline__ void finish_target_dfar(const Eval32Args& A, const Le
     }
 }
 
+// The double-float finish of the 1e-6 path, one thread per sorted target: its
+// leaf's frame (the node's double-float frame, 1/r, 2c), the leaf's local
+// expansion and the near field's sums written by k_eval32, then
+// finish_target_dfar.  Every lane works (the pair kernel's groups of 1 to 32
+// targets would leave most lanes idle in this long arithmetic).
+template <bool PSI>
+__global__ void __launch_bounds__(128) k_finish_dfar(Eval32Args A)
+{
+    __shared__ double s_shift;
+    if (threadIdx.x == 0) {
+        double sh = 0.0;
+        if (A.zero_mean)
+            for (int b = 0; b < 12; ++b) sh += (double)A.base_mpole_df[(size_t)b * EXP_STRIDE + 1];
+        s_shift = sh;
+    }
+    __syncthreads();
+    const double shift = s_shift;
+    for (int64_t tix = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; tix < A.M;
+         tix += (int64_t)gridDim.x * blockDim.x) {
+        const int leaf = A.tleaf[tix];
+        const FrameDF F = A.frames[leaf];
+        const double* g = A.T.geom + (size_t)leaf * GEOM_STRIDE;
+        LeafFrameDF G;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            G.et[k] = F.et[k];
+            G.ep[k] = F.ep[k];
+            G.c2[k] = (float)(2.0 * g[k]);
+        }
+        G.inv_r = dflt(1.f, 0.f) / F.r;
+        const float4 a = A.nf[2 * tix], b = A.nf[2 * tix + 1];
+        const dflt nf[3] = {dflt(a.x, a.y), dflt(a.z, a.w), dflt(b.x, b.y)};
+        const float4 th = A.toff[2 * tix], tl = A.toff[2 * tix + 1];
+        finish_target_dfar<PSI>(A, G, A.local_df + (size_t)leaf * EXP_STRIDE, (size_t)tix, th, tl, nf, b.z, b.w,
+                                shift);
+    }
+}
+
 __device__ __forceinline__ dflt group_sum_df(dflt v, int lpt)
 {
     for (int o = lpt >> 1; o > 0; o >>= 1) v = v + dfl_shfl_xor(v, o);
@@ -705,13 +750,10 @@ __global__ void __launch_bounds__(128, 7) k_eval32(Eval32Args A)
     __shared__ int s_pre[4][33];
     __shared__ int s_first[4][32];
     __shared__ LeafFrame32 s_frame[4];
-    __shared__ LeafFrameDF s_framed[4];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     double shift = 0.0;
-    if (A.zero_mean)
-        for (int b = 0; b < 12; ++b)
-            shift += DFAR ? (double)A.base_mpole_df[(size_t)b * EXP_STRIDE + 1]
-                          : (double)A.base_mpole[(size_t)b * EXP_STRIDE + 1];
+    if (A.zero_mean && !DFAR)
+        for (int b = 0; b < 12; ++b) shift += (double)A.base_mpole[(size_t)b * EXP_STRIDE + 1];
     Stage32& S = s_stage[wid];
     int* pre = s_pre[wid];
     int* fst = s_first[wid];
@@ -722,19 +764,11 @@ __global__ void __launch_bounds__(128, 7) k_eval32(Eval32Args A)
         const int tf = A.T.tfirst[leaf], tc = A.T.tcount[leaf];
         const double* g = A.T.geom + (size_t)leaf * GEOM_STRIDE;
         const float* L = A.local + (size_t)leaf * EXP_STRIDE;
-        const dflt* Ld = A.local_df + (size_t)leaf * EXP_STRIDE;
-        // the leaf frame in FP32 (or double-float), once per leaf, kept in shared memory
+        // the leaf frame in FP32, once per leaf, kept in shared memory (the double-float far
+        // field is finished by k_finish_dfar)
         LeafFrame32& G = s_frame[wid];
-        LeafFrameDF& GD = s_framed[wid];
         __syncwarp();
-        if (DFAR) {
-            if (lane < 3) {
-                GD.et[lane] = dflt(g[3 + lane]);
-                GD.ep[lane] = dflt(g[6 + lane]);
-                GD.c2[lane] = (float)(2.0 * g[lane]);
-            }
-            if (lane == 3) GD.inv_r = dflt(1.0 / g[10]);
-        } else {
+        if (!DFAR) {
             if (lane < 3) {
                 G.et[lane] = (float)g[3 + lane];
                 G.ep[lane] = (float)g[6 + lane];
@@ -836,6 +870,8 @@ __global__ void __launch_bounds__(128, 7) k_eval32(Eval32Args A)
                 if (nb) pair_sums32<PSI, MASK, DFAR>(S, (ns + 1) >> 1, sb, lpb, thb, tlb, sq, acc_b, accl_b);
             }
             if (DFAR) {
+                // the sums go to k_finish_dfar (one thread per target, every lane busy in the
+                // long double-float finish): the lane that holds a target's group sums writes them
                 dflt nfa[3], nfb[3];
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
@@ -847,32 +883,15 @@ __global__ void __launch_bounds__(128, 7) k_eval32(Eval32Args A)
                     acc_a[c] = group_sumf(acc_a[c], lpa);
                     acc_b[c] = group_sumf(acc_b[c], lpb);
                 }
-                // The double-float finish is long next to its inputs: lane t takes target t of the
-                // pass (group a's, then group b's) with its group sums shuffled from the lane that
-                // holds them (lane j * lpa for group a's target j), so that one round finishes all
-                // targets of the pass when they fit in the warp, else one round per group.
-                const int nbv = nb ? min(nb, tc - tb - na) : 0;
-                const int nrounds = na + nbv <= 32 ? 1 : 2;
-                for (int rd = 0; rd < nrounds; ++rd) {
-                    int t = lane, grp = rd;
-                    if (nrounds == 1 && lane >= na) { grp = 1; t = lane - na; }
-                    const bool act = grp == 0 ? t < na : t < nbv;
-                    const int src = act ? (grp == 0 ? t * lpa : t * lpb) : 0;
-                    dflt nf[3];
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) {
-                        const float ah = __shfl_sync(FULL, nfa[c].h, src), al = __shfl_sync(FULL, nfa[c].l, src);
-                        const float bh = __shfl_sync(FULL, nfb[c].h, src), bl = __shfl_sync(FULL, nfb[c].l, src);
-                        nf[c] = grp == 0 ? dflt(ah, al) : dflt(bh, bl);
-                    }
-                    const float qa = __shfl_sync(FULL, acc_a[3], src), qb = __shfl_sync(FULL, acc_b[3], src);
-                    const float la = __shfl_sync(FULL, acc_a[4], src), lb = __shfl_sync(FULL, acc_b[4], src);
-                    if (act) {
-                        const size_t tix = (size_t)tf + tb + (grp == 0 ? t : na + t);
-                        const float4 th = A.toff[2 * tix], tl = A.toff[2 * tix + 1];
-                        finish_target_dfar<PSI>(A, GD, Ld, tix, th, tl, nf, grp == 0 ? qa : qb, grp == 0 ? la : lb,
-                                                shift);
-                    }
+                if (sa == 0) {
+                    A.nf[2 * ta] = make_float4(nfa[0].h, nfa[0].l, nfa[1].h, nfa[1].l);
+                    A.nf[2 * ta + 1] = make_float4(nfa[2].h, nfa[2].l, acc_a[3], acc_a[4]);
+                    A.tleaf[ta] = leaf;
+                }
+                if (act_b && sb == 0) {
+                    A.nf[2 * tbx] = make_float4(nfb[0].h, nfb[0].l, nfb[1].h, nfb[1].l);
+                    A.nf[2 * tbx + 1] = make_float4(nfb[2].h, nfb[2].l, acc_b[3], acc_b[4]);
+                    A.tleaf[tbx] = leaf;
                 }
             } else {
 #pragma unroll
@@ -1466,7 +1485,8 @@ cudaError_t launch_eval32_prep(const TreeView& T, const int* leaves, int64_t n_l
 cudaError_t launch_eval32(const TreeView& T, const int* leaves, int64_t n_leaves, const int64_t* d_nl, const float4* soff,
                           const float4* toff, const float4* dc, const double4_32a* tgt, const uint32_t* tperm, const int64_t* p2p_off,
                           const uint32_t* p2p_src, const void* local, const void* mpole, bool dfar, int p, int zero_mean,
-                          double* psi, double* alpha, bool coincide, unsigned long long* leaf_ctr, cudaStream_t s)
+                          double* psi, double* alpha, bool coincide, float4* nf, int* tleaf,
+                          const void* frames, int64_t M, unsigned long long* leaf_ctr, cudaStream_t s)
 {
     if (n_leaves == 0) return cudaSuccess;
     Eval32Args A;
@@ -1491,6 +1511,10 @@ cudaError_t launch_eval32(const TreeView& T, const int* leaves, int64_t n_leaves
     A.psi = psi;
     A.alpha = alpha;
     A.leaf_ctr = leaf_ctr;
+    A.nf = nf;
+    A.tleaf = tleaf;
+    A.frames = static_cast<const FrameDF*>(frames);
+    A.M = M;
     int64_t blocks = 0;
     cudaError_t e;
     if ((e = leaf_grid(leaf_ctr, n_leaves, 7, s, &blocks))) return e;     // 7 per SM: __launch_bounds__
@@ -1506,6 +1530,13 @@ cudaError_t launch_eval32(const TreeView& T, const int* leaves, int64_t n_leaves
     }
 #undef EVAL32_LAUNCH
     count_launch();
+    if (dfar && M > 0) {
+        int64_t fb = (M + 127) / 128;
+        if (fb > 152 * 16) fb = 152 * 16;
+        if (psi) k_finish_dfar<true><<<(unsigned)fb, 128, 0, s>>>(A);
+        else k_finish_dfar<false><<<(unsigned)fb, 128, 0, s>>>(A);
+        count_launch();
+    }
     return cudaGetLastError();
 }
 

@@ -229,9 +229,6 @@ __global__ void k_pair_geo(TreeView T, const uint64_t* __restrict__ tt, const ui
 // double-float copies made once per node (k_frame_df), and sqrt, quotients and
 // log sin(theta/2) are double-float (the table logarithm of the evaluation).
 // The azimuths come from the shorter of D and E as in pair_geometry.
-struct __align__(16) FrameDF {
-    dflt et[3], ep[3], r, pad;
-};
 
 __global__ void k_frame_df(int n_cap, const int64_t* d_nn, const double* __restrict__ geom, FrameDF* __restrict__ out)
 {

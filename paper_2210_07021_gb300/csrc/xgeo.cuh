@@ -12,6 +12,12 @@
 
 namespace sfmm {
 
+// A node's frame in double-float, rounded from FP64 once per node (k_frame_df):
+// e_theta, e_phi and the scale r = tan(R/2).
+struct __align__(16) FrameDF {
+    dflt et[3], ep[3], r, pad;
+};
+
 // 64 bytes of translation parameters, formed in FP64.
 struct __align__(16) XGeo {
     double a, b, g, logk;
