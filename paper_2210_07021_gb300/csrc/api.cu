@@ -465,7 +465,19 @@ sfmm_status solve(sfmm_plan_s* P, const double* src, const void* q, int64_t N, c
         cudaStreamSynchronize(s);
         return cuda_fail(P, e, "lists");
     }
-    if ((e = cudaEventRecord(P->ev_join, P->aux)) || (e = cudaStreamWaitEvent(s, P->ev_join, 0)))
+    // the evaluation's target and near-leaf offsets follow the P2P list on the auxiliary
+    // stream (joined before the evaluation); M2L starts once its own list is sorted
+    const uint32_t* p2p_s = P->p2p_alt ? P->p2p_s2.as<uint32_t>() : P->p2p_s.as<uint32_t>();
+    if (offsets) {
+        const uint64_t* p2p_t = P->p2p_alt ? P->p2p_t2.as<uint64_t>() : P->p2p_t.as<uint64_t>();
+        if ((e = ensure(P->toff, (size_t)M * 32)) || (e = ensure(P->dc, (size_t)std::max<int64_t>(P->n_p2p, 1) * 32)))
+            return cuda_fail(P, e, "alloc");
+        if ((e = launch_eval32_prep(T, P->leaves_tgt.as<int>(), P->n_leaves_tgt, d_nlt, P->tgt4.as<double4_32a>(),
+                                    P->toff.as<float4>(), p2p_t, p2p_s, P->n_p2p, P->d_p2p, P->dc.as<float4>(),
+                                    P->aux)))
+            return cuda_fail(P, e, "offsets");
+    }
+    if ((e = cudaEventRecord(P->ev_join, P->aux)) || (e = cudaStreamWaitEvent(s, P->ev_m2l, 0)))
         return cuda_fail(P, e, "join lists");
     tm.mark();
     // ---- M2L
@@ -527,16 +539,8 @@ sfmm_status solve(sfmm_plan_s* P, const double* src, const void* q, int64_t N, c
                 return cuda_fail(P, e, "L2L");
     }
     tm.mark();
-    // ---- evaluation
-    const uint32_t* p2p_s = P->p2p_alt ? P->p2p_s2.as<uint32_t>() : P->p2p_s.as<uint32_t>();
-    if (offsets) {
-        const uint64_t* p2p_t = P->p2p_alt ? P->p2p_t2.as<uint64_t>() : P->p2p_t.as<uint64_t>();
-        if ((e = ensure(P->toff, (size_t)M * 32)) || (e = ensure(P->dc, (size_t)std::max<int64_t>(P->n_p2p, 1) * 32)))
-            return cuda_fail(P, e, "alloc");
-        if ((e = launch_eval32_prep(T, P->leaves_tgt.as<int>(), P->n_leaves_tgt, d_nlt, P->tgt4.as<double4_32a>(),
-                                    P->toff.as<float4>(), p2p_t, p2p_s, P->n_p2p, P->d_p2p, P->dc.as<float4>(), s)))
-            return cuda_fail(P, e, "offsets");
-    }
+    // ---- evaluation (after the P2P list and the offsets of the auxiliary stream)
+    if ((e = cudaStreamWaitEvent(s, P->ev_join, 0))) return cuda_fail(P, e, "join offsets");
     unsigned long long* leaf_ctr = reinterpret_cast<unsigned long long*>(P->small.as<int64_t>() + 40);
     if (adj_df) e = launch_eval_df(T, P->leaves_tgt.as<int>(), P->n_leaves_tgt, d_nlt, P->soff.as<float4>(),
                                    P->toff.as<float4>(), P->dc.as<float4>(), P->tgt4.as<double4_32a>(), tperm,
@@ -689,7 +693,8 @@ sfmm_status sfmm_plan(sfmm_plan_t* out, int max_depth, int order_p, double tol, 
     cudaError_t e;
     if ((e = cudaMallocHost(&P->h_status, sizeof(int))) || (e = cudaStreamCreateWithFlags(&P->aux, cudaStreamNonBlocking)) ||
         (e = cudaEventCreateWithFlags(&P->ev_fork, cudaEventDisableTiming)) ||
-        (e = cudaEventCreateWithFlags(&P->ev_join, cudaEventDisableTiming))) {
+        (e = cudaEventCreateWithFlags(&P->ev_join, cudaEventDisableTiming)) ||
+        (e = cudaEventCreateWithFlags(&P->ev_m2l, cudaEventDisableTiming))) {
         std::lock_guard<std::mutex> g(g_err_mu);
         g_plan_err = std::string("CUDA error at plan time: ") + cudaGetErrorString(e);
         sfmm_destroy(P);
@@ -923,6 +928,7 @@ void sfmm_destroy(sfmm_plan_t plan)
     for (Buf* b : all) release(*b);
     if (plan->ev_fork) cudaEventDestroy(plan->ev_fork);
     if (plan->ev_join) cudaEventDestroy(plan->ev_join);
+    if (plan->ev_m2l) cudaEventDestroy(plan->ev_m2l);
     if (plan->aux) cudaStreamDestroy(plan->aux);
     if (plan->h_status) cudaFreeHost(plan->h_status);
     delete plan;

@@ -120,6 +120,7 @@ struct sfmm_plan_s {
     bool owns_stream = false;              // a batch lane's own stream (destroyed with the plan)
     std::vector<sfmm_plan_s*> lanes;       // batch lanes: solvers on their own streams
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaEvent_t ev_m2l = nullptr;          // the M2L list is sorted (recorded by build_lists)
     bool forked = false;                   // the next solve finds the auxiliary stream already forked
                                            // (the host entry point copies the targets there)
     std::string err;

@@ -483,18 +483,20 @@ cudaError_t build_lists(sfmm_plan_s* P, const TreeView& T, double c_s, double c_
         (e = ensure(P->p2p_s2, (size_t)std::max<int64_t>(n_p2p, 1) * 4)))
         return e;
     if ((e = ensure(P->tmp, radix_tmp_bytes(std::max(n_m2l, n_p2p))))) return e;
+    if ((e = ensure(P->m2l_off, (size_t)(P->n_nodes + 1) * 8)) || (e = ensure(P->p2p_off, (size_t)(P->n_nodes + 1) * 8)))
+        return e;
+    // the M2L list first: its event (plan->ev_m2l) lets M2L start while the P2P list is sorted
     if ((e = radix_sort(P->m2l_t.as<uint64_t>(), P->m2l_s.as<uint32_t>(), P->m2l_t2.as<uint64_t>(),
                         P->m2l_s2.as<uint32_t>(), n_m2l, bits, P->tmp.p, s, &P->m2l_alt)))
         return e;
+    const uint64_t* mt = P->m2l_alt ? P->m2l_t2.as<uint64_t>() : P->m2l_t.as<uint64_t>();
+    k_csr_offsets<<<grid_for(P->n_nodes + 1), 256, 0, s>>>(mt, n_m2l, P->d_m2l, (int)P->n_nodes,
+                                                           P->m2l_off.as<int64_t>()); count_launch();
+    if ((e = cudaEventRecord(P->ev_m2l, s))) return e;
     if ((e = radix_sort(P->p2p_t.as<uint64_t>(), P->p2p_s.as<uint32_t>(), P->p2p_t2.as<uint64_t>(),
                         P->p2p_s2.as<uint32_t>(), n_p2p, bits, P->tmp.p, s, &P->p2p_alt)))
         return e;
-    if ((e = ensure(P->m2l_off, (size_t)(P->n_nodes + 1) * 8)) || (e = ensure(P->p2p_off, (size_t)(P->n_nodes + 1) * 8)))
-        return e;
-    const uint64_t* mt = P->m2l_alt ? P->m2l_t2.as<uint64_t>() : P->m2l_t.as<uint64_t>();
     const uint64_t* pt = P->p2p_alt ? P->p2p_t2.as<uint64_t>() : P->p2p_t.as<uint64_t>();
-    k_csr_offsets<<<grid_for(P->n_nodes + 1), 256, 0, s>>>(mt, n_m2l, P->d_m2l, (int)P->n_nodes,
-                                                           P->m2l_off.as<int64_t>()); count_launch();
     k_csr_offsets<<<grid_for(P->n_nodes + 1), 256, 0, s>>>(pt, n_p2p, P->d_p2p, (int)P->n_nodes,
                                                            P->p2p_off.as<int64_t>()); count_launch();
     return cudaGetLastError();
