@@ -254,13 +254,17 @@ int sfmm_order(sfmm_plan_t plan);
  *   p2p_interactions         : source-target point pairs evaluated directly (counted
  *                              only while timing is at level 2, else 0)
  *   launches                 : kernel launches of the solve
- *   ms[8]                    : device time of the phases (only while timing is on):
- *                              keys+sort, tree+geometry, up-pass, lists, M2L, L2L,
- *                              evaluation, total
+ *   ms[8]                    : device time of the phases on the plan's stream (only
+ *                              while timing is on): keys+sort, tree+geometry, up-pass,
+ *                              lists, M2L, L2L, evaluation, total
+ *   near_ms                  : SFMM_MIXED: device time of the near-field kernel, which
+ *                              runs on the auxiliary stream beside M2L and L2L (its
+ *                              evaluation phase is then the double-float finish); else 0
  */
 typedef struct {
     int64_t n_nodes, n_leaves, depth, n_m2l, n_p2p, p2p_interactions, launches;
     double ms[8];
+    double near_ms;
 } sfmm_stats;
 sfmm_status sfmm_get_stats(sfmm_plan_t plan, sfmm_stats* out);
 

@@ -73,7 +73,7 @@ cudaError_t launch_eval32(const TreeView& T, const int* leaves, int64_t n_leaves
                           const float4* toff, const float4* dc, const double4_32a* tgt, const uint32_t* tperm, const int64_t* p2p_off,
                           const uint32_t* p2p_src, const void* local, const void* mpole, bool dfar, int p, int zero_mean,
                           double* psi, double* alpha, bool coincide, float4* nf, int* tleaf,
-                          const void* frames, int64_t M, unsigned long long* leaf_ctr, cudaStream_t s);
+                          const void* frames, int64_t M, int what, unsigned long long* leaf_ctr, cudaStream_t s);
 cudaError_t launch_count_pairs(const TreeView& T, const int* leaves, int64_t n_leaves, const int64_t* p2p_off,
                                const uint32_t* p2p_src, unsigned long long* out, cudaStream_t s);
 void fill_log_table(float* out);
@@ -477,6 +477,22 @@ sfmm_status solve(sfmm_plan_s* P, const double* src, const void* q, int64_t N, c
                                     P->aux)))
             return cuda_fail(P, e, "offsets");
     }
+    // 1e-6 path: the near field needs none of the far field (its double-float finish does),
+    // so it runs here, on the auxiliary stream, beside M2L and L2L
+    unsigned long long* leaf_ctr = reinterpret_cast<unsigned long long*>(P->small.as<int64_t>() + 40);
+    const bool near_early = near32 && !fp32 && !adj;
+    if (near_early) {
+        if ((e = ensure(P->nfbuf, (size_t)M * 32)) || (e = ensure(P->tleaf, (size_t)M * 4)))
+            return cuda_fail(P, e, "alloc");
+        if (P->timing) cudaEventRecord(P->ev_near[0], P->aux);
+        if ((e = launch_eval32(T, P->leaves_tgt.as<int>(), P->n_leaves_tgt, d_nlt, P->soff.as<float4>(),
+                               P->toff.as<float4>(), P->dc.as<float4>(), P->tgt4.as<double4_32a>(), tperm,
+                               P->p2p_off.as<int64_t>(), p2p_s, P->local.p, P->mpole.p, true, p, P->opt.zero_mean,
+                               psi, alpha, src == tgt, P->nfbuf.as<float4>(), P->tleaf.as<int>(), P->framedf.p, M,
+                               EVAL32_NEAR, leaf_ctr, P->aux)))
+            return cuda_fail(P, e, "near field");
+        if (P->timing) cudaEventRecord(P->ev_near[1], P->aux);
+    }
     if ((e = cudaEventRecord(P->ev_join, P->aux)) || (e = cudaStreamWaitEvent(s, P->ev_m2l, 0)))
         return cuda_fail(P, e, "join lists");
     tm.mark();
@@ -541,7 +557,6 @@ sfmm_status solve(sfmm_plan_s* P, const double* src, const void* q, int64_t N, c
     tm.mark();
     // ---- evaluation (after the P2P list and the offsets of the auxiliary stream)
     if ((e = cudaStreamWaitEvent(s, P->ev_join, 0))) return cuda_fail(P, e, "join offsets");
-    unsigned long long* leaf_ctr = reinterpret_cast<unsigned long long*>(P->small.as<int64_t>() + 40);
     if (adj_df) e = launch_eval_df(T, P->leaves_tgt.as<int>(), P->n_leaves_tgt, d_nlt, P->soff.as<float4>(),
                                    P->toff.as<float4>(), P->dc.as<float4>(), P->tgt4.as<double4_32a>(), tperm,
                                    P->p2p_off.as<int64_t>(), p2p_s, P->local.p, P->mpole.p, P->logtab.as<float4>(), p,
@@ -552,14 +567,13 @@ sfmm_status solve(sfmm_plan_s* P, const double* src, const void* q, int64_t N, c
                                  p2p_s, P->local.as<double>(), P->mpole.as<double>(), p, P->opt.zero_mean, adj->w,
                                  adj->w_f32, psi, adj->grad3, leaf_ctr, s);
     else if (near32) {
-        // the double-float finish runs as its own kernel on the near field's sums
-        if (!fp32 && ((e = ensure(P->nfbuf, (size_t)M * 32)) || (e = ensure(P->tleaf, (size_t)M * 4))))
-            return cuda_fail(P, e, "alloc");
+        // 1e-6 path: the double-float finish on the near field's sums (the near field ran on the
+        // auxiliary stream); all-FP32 path: the near field with its FP32 finish
         e = launch_eval32(T, P->leaves_tgt.as<int>(), P->n_leaves_tgt, d_nlt, P->soff.as<float4>(),
                           P->toff.as<float4>(), P->dc.as<float4>(), P->tgt4.as<double4_32a>(), tperm,
                           P->p2p_off.as<int64_t>(), p2p_s, P->local.p, P->mpole.p, !fp32, p, P->opt.zero_mean, psi,
-                          alpha, src == tgt, P->nfbuf.as<float4>(), P->tleaf.as<int>(), P->framedf.p, M, leaf_ctr,
-                          s);
+                          alpha, src == tgt, P->nfbuf.as<float4>(), P->tleaf.as<int>(), P->framedf.p, M,
+                          near_early ? EVAL32_FINISH : EVAL32_NEAR | EVAL32_FINISH, leaf_ctr, s);
     }
     else if (dfe) e = launch_eval_df(T, P->leaves_tgt.as<int>(), P->n_leaves_tgt, d_nlt, P->soff.as<float4>(),
                                      P->toff.as<float4>(), P->dc.as<float4>(), P->tgt4.as<double4_32a>(), tperm,
@@ -595,6 +609,10 @@ sfmm_status solve(sfmm_plan_s* P, const double* src, const void* q, int64_t N, c
     if (tc_status && *P->h_status)
         return fail(P, SFMM_ETIMEOUT, "a bounded wait of the tensor-core M2L kernel ran out");
     tm.finish();
+    if (P->timing && near_early) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, P->ev_near[0], P->ev_near[1]) == cudaSuccess) P->stats.near_ms = ms;
+    }
     P->stats.n_nodes = nn;
     P->stats.n_leaves = P->n_leaves;
     P->stats.depth = depth;
@@ -694,7 +712,8 @@ sfmm_status sfmm_plan(sfmm_plan_t* out, int max_depth, int order_p, double tol, 
     if ((e = cudaMallocHost(&P->h_status, sizeof(int))) || (e = cudaStreamCreateWithFlags(&P->aux, cudaStreamNonBlocking)) ||
         (e = cudaEventCreateWithFlags(&P->ev_fork, cudaEventDisableTiming)) ||
         (e = cudaEventCreateWithFlags(&P->ev_join, cudaEventDisableTiming)) ||
-        (e = cudaEventCreateWithFlags(&P->ev_m2l, cudaEventDisableTiming))) {
+        (e = cudaEventCreateWithFlags(&P->ev_m2l, cudaEventDisableTiming)) ||
+        (e = cudaEventCreate(&P->ev_near[0])) || (e = cudaEventCreate(&P->ev_near[1]))) {
         std::lock_guard<std::mutex> g(g_err_mu);
         g_plan_err = std::string("CUDA error at plan time: ") + cudaGetErrorString(e);
         sfmm_destroy(P);
@@ -929,6 +948,8 @@ void sfmm_destroy(sfmm_plan_t plan)
     if (plan->ev_fork) cudaEventDestroy(plan->ev_fork);
     if (plan->ev_join) cudaEventDestroy(plan->ev_join);
     if (plan->ev_m2l) cudaEventDestroy(plan->ev_m2l);
+    for (cudaEvent_t ev : plan->ev_near)
+        if (ev) cudaEventDestroy(ev);
     if (plan->aux) cudaStreamDestroy(plan->aux);
     if (plan->h_status) cudaFreeHost(plan->h_status);
     delete plan;

@@ -64,6 +64,8 @@ cudaError_t launch_keys(const double* xyz, int64_t n, uint64_t* keys, uint32_t* 
 // Number format of the expansions and translations: FP64, FP32 (mixed path)
 // or double-float pairs of FP32 (1e-10 mixed path).
 enum { EXP_F64 = 0, EXP_F32 = 1, EXP_DF = 2 };
+// the parts launch_eval32 launches: the near-field kernel, the double-float finish
+enum { EVAL32_NEAR = 1, EVAL32_FINISH = 2 };
 
 // --------------------------------------------------------------- the tree
 struct TreeView {
@@ -121,6 +123,7 @@ struct sfmm_plan_s {
     std::vector<sfmm_plan_s*> lanes;       // batch lanes: solvers on their own streams
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     cudaEvent_t ev_m2l = nullptr;          // the M2L list is sorted (recorded by build_lists)
+    cudaEvent_t ev_near[2] = {nullptr, nullptr};   // timing: around the 1e-6 path's near-field kernel
     bool forked = false;                   // the next solve finds the auxiliary stream already forked
                                            // (the host entry point copies the targets there)
     std::string err;

@@ -1486,7 +1486,7 @@ cudaError_t launch_eval32(const TreeView& T, const int* leaves, int64_t n_leaves
                           const float4* toff, const float4* dc, const double4_32a* tgt, const uint32_t* tperm, const int64_t* p2p_off,
                           const uint32_t* p2p_src, const void* local, const void* mpole, bool dfar, int p, int zero_mean,
                           double* psi, double* alpha, bool coincide, float4* nf, int* tleaf,
-                          const void* frames, int64_t M, unsigned long long* leaf_ctr, cudaStream_t s)
+                          const void* frames, int64_t M, int what, unsigned long long* leaf_ctr, cudaStream_t s)
 {
     if (n_leaves == 0) return cudaSuccess;
     Eval32Args A;
@@ -1515,22 +1515,24 @@ cudaError_t launch_eval32(const TreeView& T, const int* leaves, int64_t n_leaves
     A.tleaf = tleaf;
     A.frames = static_cast<const FrameDF*>(frames);
     A.M = M;
-    int64_t blocks = 0;
     cudaError_t e;
-    if ((e = leaf_grid(leaf_ctr, n_leaves, 7, s, &blocks))) return e;     // 7 per SM: __launch_bounds__
+    if (what & EVAL32_NEAR) {
+        int64_t blocks = 0;
+        if ((e = leaf_grid(leaf_ctr, n_leaves, 7, s, &blocks))) return e;     // 7 per SM: __launch_bounds__
 #define EVAL32_LAUNCH(PSI, MASK)                                                  \
-    if (dfar) k_eval32<PSI, MASK, true><<<(unsigned)blocks, 128, 0, s>>>(A);      \
-    else k_eval32<PSI, MASK, false><<<(unsigned)blocks, 128, 0, s>>>(A);
-    if (coincide) {
-        if (psi) { EVAL32_LAUNCH(true, true) }
-        else { EVAL32_LAUNCH(false, true) }
-    } else {
-        if (psi) { EVAL32_LAUNCH(true, false) }
-        else { EVAL32_LAUNCH(false, false) }
-    }
+        if (dfar) k_eval32<PSI, MASK, true><<<(unsigned)blocks, 128, 0, s>>>(A);  \
+        else k_eval32<PSI, MASK, false><<<(unsigned)blocks, 128, 0, s>>>(A);
+        if (coincide) {
+            if (psi) { EVAL32_LAUNCH(true, true) }
+            else { EVAL32_LAUNCH(false, true) }
+        } else {
+            if (psi) { EVAL32_LAUNCH(true, false) }
+            else { EVAL32_LAUNCH(false, false) }
+        }
 #undef EVAL32_LAUNCH
-    count_launch();
-    if (dfar && M > 0) {
+        count_launch();
+    }
+    if (dfar && M > 0 && (what & EVAL32_FINISH)) {
         int64_t fb = (M + 127) / 128;
         if (fb > 152 * 16) fb = 152 * 16;
         if (psi) k_finish_dfar<true><<<(unsigned)fb, 128, 0, s>>>(A);

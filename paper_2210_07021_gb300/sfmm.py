@@ -37,7 +37,7 @@ class Stats(ctypes.Structure):
     _fields_ = [("n_nodes", ctypes.c_int64), ("n_leaves", ctypes.c_int64), ("depth", ctypes.c_int64),
                 ("n_m2l", ctypes.c_int64), ("n_p2p", ctypes.c_int64), ("p2p_interactions", ctypes.c_int64),
                 ("launches", ctypes.c_int64),
-                ("ms", ctypes.c_double * 8)]
+                ("ms", ctypes.c_double * 8), ("near_ms", ctypes.c_double)]
 
 
 class GraphStats(ctypes.Structure):
