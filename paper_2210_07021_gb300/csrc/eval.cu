@@ -40,6 +40,8 @@ constexpr double LOG4 = 1.3862943611198906188;
 constexpr float FLT_MIN_F = 1.17549435e-38f;     // the smallest normal FP32 number
 constexpr float LN2_H = 0.693147182464599609375f;   // log 2 rounded to FP32
 constexpr float LN2_L = -1.9046542121259336e-09f;   // log 2 - LN2_H
+constexpr float INV4PI_H = (float)INV4PI;             // 1/(4 pi) as a double-float
+constexpr float INV4PI_L = (float)(INV4PI - (double)INV4PI_H);
 
 struct EvalArgs {
     TreeView T;
@@ -685,9 +687,12 @@ __device__ __forceinline__ void finish_target_dfar(const Eval32Args& A, const Le
         A.alpha[2 * (size_t)o + 1] = (double)(alu * c12 + alv * c22);
     }
     if (PSI) {
+        // in double-float (this GPU's FP64 pipe runs at 1/64 of the FP32 rate), one FP64 add at the end
         const float Fx = frx * oxf - fry * oyf;
-        const double psi_e = (double)L[0] + (double)Q * (LOG2 + (double)log1pf(-0.25f * D2)) + 2.0 * (double)Fx;
-        A.psi[o] = psi_e + INV4PI * (LOG2 * (double)ol - LOG4 * (double)oq) + shift;
+        const dflt ln2(LN2_H, LN2_L);
+        const dflt psi_e = L[0] + Q * (ln2 + dflt(log1pf(-0.25f * D2))) + dflt(Fx) * 2.f;
+        const dflt near = (dflt(ol) * ln2 - dflt(oq) * (ln2 * 2.f)) * dflt(INV4PI_H, INV4PI_L);
+        A.psi[o] = (double)(psi_e + near) + shift;
     }
 }
 
@@ -712,13 +717,12 @@ __global__ void __launch_bounds__(128) k_finish_dfar(Eval32Args A)
          tix += (int64_t)gridDim.x * blockDim.x) {
         const int leaf = A.tleaf[tix];
         const FrameDF F = A.frames[leaf];
-        const double* g = A.T.geom + (size_t)leaf * GEOM_STRIDE;
         LeafFrameDF G;
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
             G.et[k] = F.et[k];
             G.ep[k] = F.ep[k];
-            G.c2[k] = (float)(2.0 * g[k]);
+            G.c2[k] = F.c2[k];
         }
         G.inv_r = dflt(1.f, 0.f) / F.r;
         const float4 a = A.nf[2 * tix], b = A.nf[2 * tix + 1];
