@@ -447,12 +447,14 @@ __device__ __forceinline__ void two_sum(float a, float b, float* s, float* e)
 // The staged near sources of one warp, packed by pairs of sources (a, b) =
 // (2P, 2P+1) and negated, so that one 16-byte load yields (x_a, x_b, y_a, y_b)
 // and the pair loop runs on packed FP32x2 instructions: hi offsets (x, y), (z,
-// mass), lo offsets (x, y), (z), all from the target leaf's centre.
+// mass), lo offsets (x, y), (z, unused), all from the target leaf's centre.
+// Every array has a 16-byte stride, so that the four loads of pair P (and the
+// stores of the staging) share one address with fixed displacements.
 struct Stage32 {
     float4 hxy[STAGE32 / 2];
     float4 hzq[STAGE32 / 2];
     float4 lxy[STAGE32 / 2];
-    float2 lz[STAGE32 / 2];
+    float4 lz[STAGE32 / 2];
 };
 
 __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
@@ -494,11 +496,10 @@ __device__ __forceinline__ void pair_block32(const Stage32& S, int P0, int P1, i
 {
 #pragma unroll 2
     for (int P = P0; P < P1; P += lpt) {
-        const float4 a = S.hxy[P], b = S.hzq[P], c = S.lxy[P];
-        const float2 d = S.lz[P];
+        const float4 a = S.hxy[P], b = S.hzq[P], c = S.lxy[P], d = S.lz[P];
         const float2 dx = __fadd2_rn(__fadd2_rn(tx, f2(a.x, a.y)), __fadd2_rn(ux, f2(c.x, c.y)));
         const float2 dy = __fadd2_rn(__fadd2_rn(ty, f2(a.z, a.w)), __fadd2_rn(uy, f2(c.z, c.w)));
-        const float2 dz = __fadd2_rn(__fadd2_rn(tz, f2(b.x, b.y)), __fadd2_rn(uz, d));
+        const float2 dz = __fadd2_rn(__fadd2_rn(tz, f2(b.x, b.y)), __fadd2_rn(uz, f2(d.x, d.y)));
         const float2 d2 = __ffma2_rn(dz, dz, __ffma2_rn(dy, dy, __fmul2_rn(dx, dx)));
         float2 q = f2(b.z, b.w);
         float2 den = d2;
@@ -750,7 +751,7 @@ template <bool PSI, bool MASK, bool DFAR>
 __global__ void __launch_bounds__(128, 7) k_eval32(Eval32Args A)
 {
     __shared__ Stage32 s_stage[4];
-    __shared__ float s_dc[4][32][6];
+    __shared__ float4 s_dch[4][32], s_dcl[4][32];   // near leaves' centre offsets: hi, lo
     __shared__ int s_pre[4][33];
     __shared__ int s_first[4][32];
     __shared__ LeafFrame32 s_frame[4];
@@ -824,8 +825,8 @@ __global__ void __launch_bounds__(128, 7) k_eval32(Eval32Args A)
                 else { ns = __shfl_sync(FULL, inc, nfit - 1); nl = nfit; }
                 pre[lane] = inc - cnt;
                 fst[lane] = first;
-                s_dc[wid][lane][0] = rh.x; s_dc[wid][lane][1] = rh.y; s_dc[wid][lane][2] = rh.z;
-                s_dc[wid][lane][3] = rl.x; s_dc[wid][lane][4] = rl.y; s_dc[wid][lane][5] = rl.z;
+                s_dch[wid][lane] = rh;
+                s_dcl[wid][lane] = rl;
                 __syncwarp();
                 // ---- flattened staging: position idx belongs to the largest leaf i < nl with
                 // pre[i] <= idx, found by stepping on from the previous position's leaf; its
@@ -837,24 +838,25 @@ __global__ void __launch_bounds__(128, 7) k_eval32(Eval32Args A)
                     const size_t j = (size_t)(fst[lo] + (idx - pre[lo]));
                     const float4 h = A.soff[2 * j];
                     const float4 l = A.soff[2 * j + 1];
-                    const float* d = s_dc[wid][lo];
+                    const float4 dh = s_dch[wid][lo], dl = s_dcl[wid][lo];
+                    // the negated offset, -(y + d) = (-y) + (-d): the same two-sum, negated exactly
                     float sx, ex_, sy, ey_, sz, ez_;
-                    two_sum(h.x, d[0], &sx, &ex_);
-                    two_sum(h.y, d[1], &sy, &ey_);
-                    two_sum(h.z, d[2], &sz, &ez_);
+                    two_sum(-h.x, -dh.x, &sx, &ex_);
+                    two_sum(-h.y, -dh.y, &sy, &ey_);
+                    two_sum(-h.z, -dh.z, &sz, &ez_);
                     const int P = idx >> 1, c = idx & 1;
                     float* pa = reinterpret_cast<float*>(&S.hxy[P]);
                     float* pb = reinterpret_cast<float*>(&S.hzq[P]);
                     float* pc = reinterpret_cast<float*>(&S.lxy[P]);
                     float* pd = reinterpret_cast<float*>(&S.lz[P]);
-                    pa[c] = -sx;
-                    pa[2 + c] = -sy;
-                    pb[c] = -sz;
+                    pa[c] = sx;
+                    pa[2 + c] = sy;
+                    pb[c] = sz;
                     pb[2 + c] = h.w;
                     sq += h.w;
-                    pc[c] = -(ex_ + (l.x + d[3]));
-                    pc[2 + c] = -(ey_ + (l.y + d[4]));
-                    pd[c] = -(ez_ + (l.z + d[5]));
+                    pc[c] = ex_ - (l.x + dl.x);
+                    pc[2 + c] = ey_ - (l.y + dl.y);
+                    pd[c] = ez_ - (l.z + dl.z);
                 }
                 if ((ns & 1) && lane == 0) {        // an odd count: a massless partner 4 away
                     const int P = ns >> 1;
