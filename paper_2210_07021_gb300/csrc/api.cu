@@ -81,8 +81,8 @@ cudaError_t launch_eval_df(const TreeView& T, const int* leaves, int64_t n_leave
                            const float4* toff, const float4* dc, const double4_32a* tgt, const uint32_t* tperm,
                            const int64_t* p2p_off, const uint32_t* p2p_src, const void* local, const void* mpole,
                            const float4* log_tab, int p, int zero_mean, double* psi, double* alpha,
-                           const float4* doff, const void* w, int w_f32, double* grad3,
-                           unsigned long long* leaf_ctr, cudaStream_t s);
+                           const float4* doff, const void* w, int w_f32, double* grad3, float4* nf, int* tleaf,
+                           const void* frames, int64_t M, int what, unsigned long long* leaf_ctr, cudaStream_t s);
 cudaError_t launch_p2m_adj(const TreeView& T, const int* leaves, int64_t n_leaves, const double4_32a* src,
                            const double4_32a* dip, double* mpole, int p, cudaStream_t s);
 cudaError_t launch_eval_adj(const TreeView& T, const int* leaves, int64_t n_leaves, const double4_32a* src,
@@ -477,10 +477,23 @@ sfmm_status solve(sfmm_plan_s* P, const double* src, const void* q, int64_t N, c
                                     P->aux)))
             return cuda_fail(P, e, "offsets");
     }
-    // 1e-6 path: the near field needs none of the far field (its double-float finish does),
-    // so it runs here, on the auxiliary stream, beside M2L and L2L
+    // 1e-6 and 1e-10 paths: the near field needs none of the far field (their double-float
+    // finish does), so it runs here, on the auxiliary stream, beside M2L and L2L
     unsigned long long* leaf_ctr = reinterpret_cast<unsigned long long*>(P->small.as<int64_t>() + 40);
     const bool near_early = near32 && !fp32 && !adj;
+    const bool near_early_df = dfe && !near32 && !adj;
+    if (near_early_df) {
+        if ((e = ensure(P->nfbuf, (size_t)M * 48)) || (e = ensure(P->tleaf, (size_t)M * 4)))
+            return cuda_fail(P, e, "alloc");
+        if (P->timing) cudaEventRecord(P->ev_near[0], P->aux);
+        if ((e = launch_eval_df(T, P->leaves_tgt.as<int>(), P->n_leaves_tgt, d_nlt, P->soff.as<float4>(),
+                                P->toff.as<float4>(), P->dc.as<float4>(), P->tgt4.as<double4_32a>(), tperm,
+                                P->p2p_off.as<int64_t>(), p2p_s, P->local.p, P->mpole.p, P->logtab.as<float4>(), p,
+                                P->opt.zero_mean, psi, alpha, nullptr, nullptr, 0, nullptr, P->nfbuf.as<float4>(),
+                                P->tleaf.as<int>(), P->framedf.p, M, EVAL_NEAR, leaf_ctr, P->aux)))
+            return cuda_fail(P, e, "near field");
+        if (P->timing) cudaEventRecord(P->ev_near[1], P->aux);
+    }
     if (near_early) {
         if ((e = ensure(P->nfbuf, (size_t)M * 32)) || (e = ensure(P->tleaf, (size_t)M * 4)))
             return cuda_fail(P, e, "alloc");
@@ -489,7 +502,7 @@ sfmm_status solve(sfmm_plan_s* P, const double* src, const void* q, int64_t N, c
                                P->toff.as<float4>(), P->dc.as<float4>(), P->tgt4.as<double4_32a>(), tperm,
                                P->p2p_off.as<int64_t>(), p2p_s, P->local.p, P->mpole.p, true, p, P->opt.zero_mean,
                                psi, alpha, src == tgt, P->nfbuf.as<float4>(), P->tleaf.as<int>(), P->framedf.p, M,
-                               EVAL32_NEAR, leaf_ctr, P->aux)))
+                               EVAL_NEAR, leaf_ctr, P->aux)))
             return cuda_fail(P, e, "near field");
         if (P->timing) cudaEventRecord(P->ev_near[1], P->aux);
     }
@@ -561,7 +574,7 @@ sfmm_status solve(sfmm_plan_s* P, const double* src, const void* q, int64_t N, c
                                    P->toff.as<float4>(), P->dc.as<float4>(), P->tgt4.as<double4_32a>(), tperm,
                                    P->p2p_off.as<int64_t>(), p2p_s, P->local.p, P->mpole.p, P->logtab.as<float4>(), p,
                                    P->opt.zero_mean, psi, nullptr, P->dip4.as<float4>(), adj->w, adj->w_f32,
-                                   adj->grad3, leaf_ctr, s);
+                                   adj->grad3, nullptr, nullptr, nullptr, M, EVAL_NEAR | EVAL_FINISH, leaf_ctr, s);
     else if (adj) e = launch_eval_adj(T, P->leaves_tgt.as<int>(), P->n_leaves_tgt, P->src4.as<double4_32a>(),
                                  P->dip4.as<double4_32a>(), P->tgt4.as<double4_32a>(), tperm, P->p2p_off.as<int64_t>(),
                                  p2p_s, P->local.as<double>(), P->mpole.as<double>(), p, P->opt.zero_mean, adj->w,
@@ -573,13 +586,14 @@ sfmm_status solve(sfmm_plan_s* P, const double* src, const void* q, int64_t N, c
                           P->toff.as<float4>(), P->dc.as<float4>(), P->tgt4.as<double4_32a>(), tperm,
                           P->p2p_off.as<int64_t>(), p2p_s, P->local.p, P->mpole.p, !fp32, p, P->opt.zero_mean, psi,
                           alpha, src == tgt, P->nfbuf.as<float4>(), P->tleaf.as<int>(), P->framedf.p, M,
-                          near_early ? EVAL32_FINISH : EVAL32_NEAR | EVAL32_FINISH, leaf_ctr, s);
+                          near_early ? EVAL_FINISH : EVAL_NEAR | EVAL_FINISH, leaf_ctr, s);
     }
     else if (dfe) e = launch_eval_df(T, P->leaves_tgt.as<int>(), P->n_leaves_tgt, d_nlt, P->soff.as<float4>(),
                                      P->toff.as<float4>(), P->dc.as<float4>(), P->tgt4.as<double4_32a>(), tperm,
                                      P->p2p_off.as<int64_t>(), p2p_s, P->local.p, P->mpole.p,
                                      P->logtab.as<float4>(), p, P->opt.zero_mean, psi, alpha, nullptr, nullptr, 0,
-                                     nullptr, leaf_ctr, s);
+                                     nullptr, P->nfbuf.as<float4>(), P->tleaf.as<int>(), P->framedf.p, M,
+                                     near_early_df ? EVAL_FINISH : EVAL_NEAR | EVAL_FINISH, leaf_ctr, s);
     else e = launch_eval(T, P->leaves_tgt.as<int>(), P->n_leaves_tgt, d_nlt, P->src4.as<double4_32a>(),
                          P->tgt4.as<double4_32a>(), tperm, P->p2p_off.as<int64_t>(), p2p_s, P->local.as<double>(),
                          P->mpole.as<double>(), p, P->opt.zero_mean, P->opt.sigma, psi, alpha, gamma, mu, leaf_ctr, s);
@@ -609,7 +623,7 @@ sfmm_status solve(sfmm_plan_s* P, const double* src, const void* q, int64_t N, c
     if (tc_status && *P->h_status)
         return fail(P, SFMM_ETIMEOUT, "a bounded wait of the tensor-core M2L kernel ran out");
     tm.finish();
-    if (P->timing && near_early) {
+    if (P->timing && (near_early || near_early_df)) {
         float ms = 0.f;
         if (cudaEventElapsedTime(&ms, P->ev_near[0], P->ev_near[1]) == cudaSuccess) P->stats.near_ms = ms;
     }

@@ -64,8 +64,9 @@ cudaError_t launch_keys(const double* xyz, int64_t n, uint64_t* keys, uint32_t* 
 // Number format of the expansions and translations: FP64, FP32 (mixed path)
 // or double-float pairs of FP32 (1e-10 mixed path).
 enum { EXP_F64 = 0, EXP_F32 = 1, EXP_DF = 2 };
-// the parts launch_eval32 launches: the near-field kernel, the double-float finish
-enum { EVAL32_NEAR = 1, EVAL32_FINISH = 2 };
+// the parts launch_eval32 / launch_eval_df launch: the near-field kernel, the
+// double-float finish (L2P and the combination, one thread per target)
+enum { EVAL_NEAR = 1, EVAL_FINISH = 2 };
 
 // --------------------------------------------------------------- the tree
 struct TreeView {

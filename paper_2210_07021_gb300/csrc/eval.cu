@@ -723,7 +723,7 @@ __global__ void __launch_bounds__(128) k_finish_dfar(Eval32Args A)
         for (int k = 0; k < 3; ++k) {
             G.et[k] = F.et[k];
             G.ep[k] = F.ep[k];
-            G.c2[k] = F.c2[k];
+            G.c2[k] = 2.f * F.c[k].h;          // (float)(2c): the scaling by 2 is exact
         }
         G.inv_r = dflt(1.f, 0.f) / F.r;
         const float4 a = A.nf[2 * tix], b = A.nf[2 * tix + 1];
@@ -963,6 +963,14 @@ struct EvalDfArgs {
     const void* w;
     int w_f32;
     double* grad3;
+    // the forward (k_eval_df<PSI, false>) writes each sorted target's near-field sums,
+    // nf[3t] = (x.h, x.l, y.h, y.l), nf[3t + 1] = (z.h, z.l, q.h, q.l), nf[3t + 2] =
+    // (log.h, log.l, 0, 0), and its leaf; k_finish_df reads them with the nodes'
+    // double-float frames
+    float4* nf;
+    int* tleaf;
+    const FrameDF* frames;
+    int64_t M;                // sorted targets
 };
 
 // Near-field sums of one target over the staged sources j = sub, sub + lpt, ...
@@ -1243,6 +1251,52 @@ __device__ __forceinline__ void finish_target_adj_df(const EvalDfArgs& A, const 
 // left, group b: the power of two >= what a leaves; 32 / size lanes per target).
 // ADJ: the adjoint (charges and tangent dipoles at the sources, Phi and w grad
 // Phi at the targets), with a stage of half the size (the dipoles are staged too).
+// One target's near-field sums (x, y, z, q, log), written for k_finish_df.
+__device__ __forceinline__ void store_near_df(const EvalDfArgs& A, size_t t, int leaf, const dflt* nf)
+{
+    A.nf[3 * t] = make_float4(nf[0].h, nf[0].l, nf[1].h, nf[1].l);
+    A.nf[3 * t + 1] = make_float4(nf[2].h, nf[2].l, nf[3].h, nf[3].l);
+    A.nf[3 * t + 2] = make_float4(nf[4].h, nf[4].l, 0.f, 0.f);
+    A.tleaf[t] = leaf;
+}
+
+// The double-float finish of the 1e-10 path, one thread per sorted target: its
+// leaf's frame (the node's double-float frame and 1/r), the leaf's local
+// expansion and the near field's sums written by k_eval_df, then
+// finish_target_df.  Every lane works.
+template <bool PSI>
+__global__ void __launch_bounds__(128) k_finish_df(EvalDfArgs A)
+{
+    __shared__ float4 s_tab[129];
+    __shared__ double s_shift;
+    for (int i = threadIdx.x; i < 129; i += blockDim.x) s_tab[i] = A.log_tab[i];
+    if (threadIdx.x == 0) {
+        double sh = 0.0;
+        if (A.zero_mean)
+            for (int b = 0; b < 12; ++b) sh += (double)A.base_mpole[(size_t)b * EXP_STRIDE + 1];
+        s_shift = sh;
+    }
+    __syncthreads();
+    const double shift = s_shift;
+    for (int64_t tix = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; tix < A.M;
+         tix += (int64_t)gridDim.x * blockDim.x) {
+        const int leaf = A.tleaf[tix];
+        const FrameDF F = A.frames[leaf];
+        LeafFrameD2 G;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            G.et[k] = F.et[k];
+            G.ep[k] = F.ep[k];
+            G.c[k] = F.c[k];
+        }
+        G.inv_r = dflt(1.f, 0.f) / F.r;
+        const float4 a = A.nf[3 * tix], b = A.nf[3 * tix + 1], c = A.nf[3 * tix + 2];
+        const dflt nf[5] = {dflt(a.x, a.y), dflt(a.z, a.w), dflt(b.x, b.y), dflt(b.z, b.w), dflt(c.x, c.y)};
+        const float4 th = A.toff[2 * tix], tl = A.toff[2 * tix + 1];
+        finish_target_df<PSI>(A, G, A.local + (size_t)leaf * EXP_STRIDE, (size_t)tix, th, tl, nf, s_tab, shift);
+    }
+}
+
 template <bool PSI, bool ADJ>
 __global__ void __launch_bounds__(128) k_eval_df(EvalDfArgs A)
 {
@@ -1276,14 +1330,16 @@ __global__ void __launch_bounds__(128) k_eval_df(EvalDfArgs A)
         const double* g = A.T.geom + (size_t)leaf * GEOM_STRIDE;
         const dflt* L = A.local + (size_t)leaf * EXP_STRIDE;
         const int64_t nb0 = A.p2p_off[leaf], nb1 = A.p2p_off[leaf + 1];
-        __syncwarp();
-        if (lane < 3) {
-            G.et[lane] = dflt(g[3 + lane]);
-            G.ep[lane] = dflt(g[6 + lane]);
-            G.c[lane] = dflt(g[lane]);
+        if (ADJ) {            // the adjoint finishes here; the forward in k_finish_df
+            __syncwarp();
+            if (lane < 3) {
+                G.et[lane] = dflt(g[3 + lane]);
+                G.ep[lane] = dflt(g[6 + lane]);
+                G.c[lane] = dflt(g[lane]);
+            }
+            if (lane == 3) G.inv_r = dflt(1.0 / g[10]);
+            __syncwarp();
         }
-        if (lane == 3) G.inv_r = dflt(1.0 / g[10]);
-        __syncwarp();
         for (int tb = 0; tb < tc;) {
             const int rem = tc - tb;
             const int na = min(32, 1 << (31 - __clz(rem)));
@@ -1404,8 +1460,10 @@ __global__ void __launch_bounds__(128) k_eval_df(EvalDfArgs A)
                 if (sa == 0) finish_target_adj_df<PSI>(A, G, L, ta, tha, tla, na_, s_tab, shift);
                 if (act_b && sb == 0) finish_target_adj_df<PSI>(A, G, L, tbx, thb, tlb, nb_, s_tab, shift);
             } else {
-                if (sa == 0) finish_target_df<PSI>(A, G, L, ta, tha, tla, na_, s_tab, shift);
-                if (act_b && sb == 0) finish_target_df<PSI>(A, G, L, tbx, thb, tlb, nb_, s_tab, shift);
+                // the sums go to k_finish_df (one thread per target: the long double-float
+                // L2P would leave the lanes of small target groups idle here)
+                if (sa == 0) store_near_df(A, ta, leaf, na_);
+                if (act_b && sb == 0) store_near_df(A, tbx, leaf, nb_);
             }
             tb += na + nb;
         }
@@ -1522,7 +1580,7 @@ cudaError_t launch_eval32(const TreeView& T, const int* leaves, int64_t n_leaves
     A.frames = static_cast<const FrameDF*>(frames);
     A.M = M;
     cudaError_t e;
-    if (what & EVAL32_NEAR) {
+    if (what & EVAL_NEAR) {
         int64_t blocks = 0;
         if ((e = leaf_grid(leaf_ctr, n_leaves, 7, s, &blocks))) return e;     // 7 per SM: __launch_bounds__
 #define EVAL32_LAUNCH(PSI, MASK)                                                  \
@@ -1538,7 +1596,7 @@ cudaError_t launch_eval32(const TreeView& T, const int* leaves, int64_t n_leaves
 #undef EVAL32_LAUNCH
         count_launch();
     }
-    if (dfar && M > 0 && (what & EVAL32_FINISH)) {
+    if (dfar && M > 0 && (what & EVAL_FINISH)) {
         int64_t fb = (M + 127) / 128;
         if (fb > 152 * 16) fb = 152 * 16;
         if (psi) k_finish_dfar<true><<<(unsigned)fb, 128, 0, s>>>(A);
@@ -1573,10 +1631,9 @@ cudaError_t launch_eval_df(const TreeView& T, const int* leaves, int64_t n_leave
                            const float4* toff, const float4* dc, const double4_32a* tgt, const uint32_t* tperm,
                            const int64_t* p2p_off, const uint32_t* p2p_src, const void* local, const void* mpole,
                            const float4* log_tab, int p, int zero_mean, double* psi, double* alpha,
-                           const float4* doff, const void* w, int w_f32, double* grad3,
-                           unsigned long long* leaf_ctr, cudaStream_t s)
+                           const float4* doff, const void* w, int w_f32, double* grad3, float4* nf, int* tleaf,
+                           const void* frames, int64_t M, int what, unsigned long long* leaf_ctr, cudaStream_t s)
 {
-    if (n_leaves == 0) return cudaSuccess;
     EvalDfArgs A;
     A.T = T;
     A.leaves = leaves;
@@ -1601,17 +1658,30 @@ cudaError_t launch_eval_df(const TreeView& T, const int* leaves, int64_t n_leave
     A.w = w;
     A.w_f32 = w_f32;
     A.grad3 = grad3;
-    int64_t blocks = 0;
+    A.nf = nf;
+    A.tleaf = tleaf;
+    A.frames = static_cast<const FrameDF*>(frames);
+    A.M = M;
     cudaError_t e;
-    if ((e = leaf_grid(leaf_ctr, n_leaves, 16, s, &blocks))) return e;
-    if (doff) {
-        if (psi) k_eval_df<true, true><<<(unsigned)blocks, 128, 0, s>>>(A);
-        else k_eval_df<false, true><<<(unsigned)blocks, 128, 0, s>>>(A);
-    } else {
-        if (psi) k_eval_df<true, false><<<(unsigned)blocks, 128, 0, s>>>(A);
-        else k_eval_df<false, false><<<(unsigned)blocks, 128, 0, s>>>(A);
+    if (n_leaves > 0 && (doff || (what & EVAL_NEAR))) {
+        int64_t blocks = 0;
+        if ((e = leaf_grid(leaf_ctr, n_leaves, 16, s, &blocks))) return e;
+        if (doff) {                // the adjoint: near field and finish in one kernel
+            if (psi) k_eval_df<true, true><<<(unsigned)blocks, 128, 0, s>>>(A);
+            else k_eval_df<false, true><<<(unsigned)blocks, 128, 0, s>>>(A);
+        } else {
+            if (psi) k_eval_df<true, false><<<(unsigned)blocks, 128, 0, s>>>(A);
+            else k_eval_df<false, false><<<(unsigned)blocks, 128, 0, s>>>(A);
+        }
+        count_launch();
     }
-    count_launch();
+    if (!doff && M > 0 && (what & EVAL_FINISH)) {
+        int64_t fb = (M + 127) / 128;
+        if (fb > 152 * 16) fb = 152 * 16;
+        if (psi) k_finish_df<true><<<(unsigned)fb, 128, 0, s>>>(A);
+        else k_finish_df<false><<<(unsigned)fb, 128, 0, s>>>(A);
+        count_launch();
+    }
     return cudaGetLastError();
 }
 

@@ -241,8 +241,7 @@ __global__ void k_frame_df(int n_cap, const int64_t* d_nn, const double* __restr
             F.ep[k] = dflt(g[6 + k]);
         }
         F.r = dflt(g[10]);
-        for (int k = 0; k < 3; ++k) F.c2[k] = (float)(2.0 * g[k]);
-        F.pad = 0.f;
+        for (int k = 0; k < 3; ++k) F.c[k] = dflt(g[k]);
         out[i] = F;
     }
 }

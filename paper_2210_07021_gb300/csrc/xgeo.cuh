@@ -13,11 +13,9 @@
 namespace sfmm {
 
 // A node's frame in double-float, rounded from FP64 once per node (k_frame_df):
-// e_theta, e_phi, the scale r = tan(R/2), and twice the centre in FP32.
+// e_theta, e_phi, the scale r = tan(R/2) and the centre c.
 struct __align__(16) FrameDF {
-    dflt et[3], ep[3], r;
-    float c2[3];
-    float pad;
+    dflt et[3], ep[3], r, c[3];
 };
 
 // 64 bytes of translation parameters, formed in FP64.
