@@ -973,69 +973,156 @@ struct EvalDfArgs {
     int64_t M;                // sorted targets
 };
 
-// Near-field sums of one target over the staged sources j = sub, sub + lpt, ...
-// in double-float: acc = (x, y, z sums of q d / d^2, sum q log d^2, the mass
-// skipped at coincident points).  EQM (every staged source has the same mass
-// qm): sum q log d^2 = qm log prod d^2, so per block of up to 16 sources the
-// lane multiplies the d^2 (their mantissas, in double-float, the exponents
-// summed as an integer) and takes one logarithm per block.
-template <bool PSI, bool EQM>
-__device__ __forceinline__ void pair_sums_df(const float4* __restrict__ yh, const float4* __restrict__ yl, int ns,
-                                             int sub, int lpt, const float4& th, const float4& tl, dflt qm,
-                                             const float4* __restrict__ tab, dflt* acc)
+// ---- packed double-float: the two halves of every FP32x2 register pair carry
+// two sources' double-float quantities (h + l), with the same operations as the
+// scalar double-float helpers; a - b is fma(b, -1, a), exact like a subtraction.
+struct df2 {
+    float2 h, l;
+};
+__device__ __forceinline__ float2 p_add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 p_sub(float2 a, float2 b) { return __ffma2_rn(b, f2(-1.f, -1.f), a); }
+__device__ __forceinline__ float2 p_mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 p_fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 p_neg(float2 a) { return f2(-a.x, -a.y); }
+__device__ __forceinline__ df2 p_fast_two_sum(float2 a, float2 b)        // |a| >= |b| (or a == 0)
 {
-    for (int j0 = sub; j0 < ns; j0 += 16 * lpt) {
-        const int j1 = min(ns, j0 + 16 * lpt);
-        dflt prod(1.f, 0.f);
+    const float2 s = p_add(a, b);
+    return df2{s, p_sub(b, p_sub(s, a))};
+}
+// (t - y) for double-float t, y: the two-difference of the leading parts, the
+// tails added to its error, renormalised (as dfl_diff)
+__device__ __forceinline__ df2 p_diff(float2 th, float2 tl, float2 yh, float2 yl)
+{
+    const float2 s = p_sub(th, yh);
+    const float2 bb = p_sub(s, th);
+    const float2 e = p_sub(p_sub(th, p_sub(s, bb)), p_add(yh, bb));     // (th - (s - bb)) + (-yh - bb)
+    return p_fast_two_sum(s, p_add(e, p_sub(tl, yl)));
+}
+__device__ __forceinline__ df2 p_two_sum(float2 a, float2 b)
+{
+    const float2 s = p_add(a, b);
+    const float2 bb = p_sub(s, a);
+    return df2{s, p_add(p_sub(a, p_sub(s, bb)), p_sub(b, bb))};
+}
+// acc += a * b, acc left unnormalised (as dfl_mac)
+__device__ __forceinline__ void p_mac(df2& acc, const df2& a, const df2& b)
+{
+    const float2 pr = p_mul(a.h, b.h);
+    const float2 e = p_fma(a.h, b.l, p_fma(a.l, b.h, p_fma(a.h, b.h, p_neg(pr))));
+    const df2 s = p_two_sum(acc.h, pr);
+    acc.h = s.h;
+    acc.l = p_add(acc.l, p_add(s.l, e));
+}
+__device__ __forceinline__ df2 p_mul_lazy(const df2& a, const df2& b)
+{
+    const float2 pr = p_mul(a.h, b.h);
+    return df2{pr, p_fma(a.h, b.l, p_fma(a.l, b.h, p_fma(a.h, b.h, p_neg(pr))))};
+}
+__device__ __forceinline__ df2 p_mul(const df2& a, const df2& b)
+{
+    const float2 pr = p_mul(a.h, b.h);
+    const float2 e = p_fma(a.h, b.h, p_neg(pr));
+    return p_fast_two_sum(pr, p_fma(a.h, b.l, p_fma(a.l, b.h, e)));
+}
+__device__ __forceinline__ dflt p_lo_half(const df2& a) { return dflt(a.h.x, a.l.x); }
+__device__ __forceinline__ dflt p_hi_half(const df2& a) { return dflt(a.h.y, a.l.y); }
+
+// The forward double-float stage of one warp, packed by pairs of sources (a, b) =
+// (2P, 2P + 1): xy[P] = (x_a, x_b, y_a, y_b), zq[P] = (z_a, z_b, q_a, q_b), leading
+// parts (h) and tails (l), the offsets from the target leaf's centre.  It fills
+// the same shared memory as the per-source stage of the adjoint.
+struct StageDF {
+    const float4* hxy;
+    const float4* hzq;
+    const float4* lxy;
+    const float4* lzq;
+};
+
+// Near-field sums of one target in double-float over the packed stage: np pairs
+// P = sub, sub + lpt, ... (ptail: the pair whose second source is the massless
+// partner of an odd count, or -1), in blocks of up to 16 pairs (32 sources) per
+// lane; the packed sums are added to acc = (x, y, z sums of q d / d^2, sum q log
+// d^2, the mass skipped at coincident points) at the end.  EQM (every staged
+// source has the same mass qm): sum q log d^2 = qm log prod d^2, so per block the
+// lane multiplies the d^2 (their mantissas, in double-float, the exponents summed
+// as an integer) and takes one logarithm per block.
+template <bool PSI, bool EQM>
+__device__ __forceinline__ void pair_sums_df2(const StageDF& S, int np, int ptail, int sub, int lpt, const float4& th,
+                                              const float4& tl, dflt qm, const float4* __restrict__ tab, dflt* acc)
+{
+    const float2 txh = f2(th.x, th.x), tyh = f2(th.y, th.y), tzh = f2(th.z, th.z);
+    const float2 txl = f2(tl.x, tl.x), tyl = f2(tl.y, tl.y), tzl = f2(tl.z, tl.z);
+    const float2 z2 = f2(0.f, 0.f);
+    df2 ax{z2, z2}, ay{z2, z2}, az{z2, z2}, al{z2, z2};
+    dflt skip(0.f, 0.f);
+    for (int P0 = sub; P0 < np; P0 += 16 * lpt) {
+        const int P1 = min(np, P0 + 16 * lpt);
+        df2 prod{f2(1.f, 1.f), z2};
         int ecnt = 0;
-        for (int j = j0; j < j1; j += lpt) {
-            const float4 h = yh[j];
-            const float4 l = yl[j];
-            // d = t - y
-            const dflt dx = dfl_diff(th.x, tl.x, h.x, l.x);
-            const dflt dy = dfl_diff(th.y, tl.y, h.y, l.y);
-            const dflt dz = dfl_diff(th.z, tl.z, h.z, l.z);
+        for (int P = P0; P < P1; P += lpt) {
+            const float4 A = S.hxy[P], B = S.hzq[P], C = S.lxy[P], D = S.lzq[P];
+            const df2 dx = p_diff(txh, txl, f2(A.x, A.y), f2(C.x, C.y));
+            const df2 dy = p_diff(tyh, tyl, f2(A.z, A.w), f2(C.z, C.w));
+            const df2 dz = p_diff(tzh, tzl, f2(B.x, B.y), f2(D.x, D.y));
             // d^2: exact squares of the leading parts, two exact two-sums
-            const float px = __fmul_rn(dx.h, dx.h), py = __fmul_rn(dy.h, dy.h), pz = __fmul_rn(dz.h, dz.h);
-            const float ex2 = __fmaf_rn(__fadd_rn(dx.h, dx.h), dx.l, __fmaf_rn(dx.h, dx.h, -px));
-            const float ey2 = __fmaf_rn(__fadd_rn(dy.h, dy.h), dy.l, __fmaf_rn(dy.h, dy.h, -py));
-            const float ez2 = __fmaf_rn(__fadd_rn(dz.h, dz.h), dz.l, __fmaf_rn(dz.h, dz.h, -pz));
-            const dflt s1 = dfl_two_sum(px, py);
-            const dflt s2 = dfl_two_sum(s1.h, pz);
-            dflt d2 = dfl_fast_two_sum(s2.h, __fadd_rn(__fadd_rn(s1.l, s2.l), __fadd_rn(__fadd_rn(ex2, ey2), ez2)));
+            const float2 px = p_mul(dx.h, dx.h), py = p_mul(dy.h, dy.h), pz = p_mul(dz.h, dz.h);
+            const float2 ex2 = p_fma(p_add(dx.h, dx.h), dx.l, p_fma(dx.h, dx.h, p_neg(px)));
+            const float2 ey2 = p_fma(p_add(dy.h, dy.h), dy.l, p_fma(dy.h, dy.h, p_neg(py)));
+            const float2 ez2 = p_fma(p_add(dz.h, dz.h), dz.l, p_fma(dz.h, dz.h, p_neg(pz)));
+            const df2 s1 = p_two_sum(px, py);
+            const df2 s2 = p_two_sum(s1.h, pz);
+            df2 d2 = p_fast_two_sum(s2.h, p_add(p_add(s1.l, s2.l), p_add(p_add(ex2, ey2), ez2)));
+            df2 q{f2(B.z, B.w), f2(D.z, D.w)};
             // coincident pairs (d^2 below the normal range) contribute nothing; their mass is skipped
-            const bool ok = d2.h >= FLT_MIN_F;
-            dflt q = dflt(h.w, l.w);
-            if (!ok) {
-                acc[4] = acc[4] + q;
-                q = dflt(0.f, 0.f);
-                d2 = dflt(1.f, 0.f);
+            const bool oka = d2.h.x >= FLT_MIN_F, okb = d2.h.y >= FLT_MIN_F;
+            if (!(oka && okb)) {
+                if (!oka) {
+                    skip = skip + dflt(q.h.x, q.l.x);
+                    q.h.x = 0.f; q.l.x = 0.f; d2.h.x = 1.f; d2.l.x = 0.f;
+                }
+                if (!okb) {
+                    skip = skip + dflt(q.h.y, q.l.y);
+                    q.h.y = 0.f; q.l.y = 0.f; d2.h.y = 1.f; d2.l.y = 0.f;
+                }
             }
-            // 1/d^2: MUFU reciprocal (relative error < 2^-22; d^2 is normal here) and one Newton step
-            const float r0 = rcp_approx(d2.h);
-            const float e0 = __fmaf_rn(-d2.l, r0, __fmaf_rn(-d2.h, r0, 1.f));
-            const dflt wq = dfl_mul_lazy(dflt(r0, __fmul_rn(r0, e0)), q);
-            dfl_mac(acc[0], wq, dx);
-            dfl_mac(acc[1], wq, dy);
-            dfl_mac(acc[2], wq, dz);
+            // 1/d^2: MUFU reciprocal and one Newton step
+            const float2 r0 = f2(rcp_approx(d2.h.x), rcp_approx(d2.h.y));
+            const float2 e0 = p_fma(p_neg(d2.l), r0, p_fma(p_neg(d2.h), r0, f2(1.f, 1.f)));
+            const df2 wq = p_mul_lazy(df2{r0, p_mul(r0, e0)}, q);
+            p_mac(ax, wq, dx);
+            p_mac(ay, wq, dy);
+            p_mac(az, wq, dz);
             if (PSI) {
                 if (EQM) {
-                    // d^2 = m 2^k, m in [1, 2): multiply the mantissas, sum the exponents
-                    const int k = (__float_as_int(d2.h) >> 23) - 127;
-                    const float sc = __int_as_float((127 - k) << 23);
-                    prod = prod * dflt(__fmul_rn(d2.h, sc), __fmul_rn(d2.l, sc));
-                    ecnt += k;
+                    // d^2 = m 2^k, m in [1, 2): multiply the mantissas, sum the exponents; the
+                    // massless partner of an odd count multiplies by 1
+                    const int ba = __float_as_int(d2.h.x) >> 23, bb = __float_as_int(d2.h.y) >> 23;
+                    const float2 sc = f2(__int_as_float((254 - ba) << 23), __int_as_float((254 - bb) << 23));
+                    df2 m{p_mul(d2.h, sc), p_mul(d2.l, sc)};
+                    int kb = bb - 127;
+                    if (P == ptail) {
+                        m.h.y = 1.f; m.l.y = 0.f; kb = 0;
+                    }
+                    prod = p_mul(prod, m);
+                    ecnt += (ba - 127) + kb;
                 } else {
-                    dfl_mac(acc[3], dfl_log_lazy(d2, tab), q);
+                    const dflt la = dfl_log_lazy(dflt(d2.h.x, d2.l.x), tab), lb = dfl_log_lazy(dflt(d2.h.y, d2.l.y), tab);
+                    p_mac(al, df2{f2(la.h, lb.h), f2(la.l, lb.l)}, q);
                 }
             }
         }
         if (PSI && EQM) {
-            // log prod + ecnt log 2 (ecnt exact in FP32; log 2 as a double-float)
-            const dflt lg = dfl_norm(dfl_log_lazy(prod, tab)) + dflt((float)ecnt) * dflt(LN2_H, LN2_L);
+            // log of the product of both halves + ecnt log 2 (ecnt exact in FP32)
+            const dflt pr = p_lo_half(prod) * p_hi_half(prod);
+            const dflt lg = dfl_norm(dfl_log_lazy(pr, tab)) + dflt((float)ecnt) * dflt(LN2_H, LN2_L);
             dfl_mac(acc[3], lg, qm);
         }
     }
+    acc[0] = acc[0] + dfl_norm(p_lo_half(ax)) + dfl_norm(p_hi_half(ax));
+    acc[1] = acc[1] + dfl_norm(p_lo_half(ay)) + dfl_norm(p_hi_half(ay));
+    acc[2] = acc[2] + dfl_norm(p_lo_half(az)) + dfl_norm(p_hi_half(az));
+    if (PSI && !EQM) acc[3] = acc[3] + dfl_norm(p_lo_half(al)) + dfl_norm(p_hi_half(al));
+    acc[4] = acc[4] + skip;
 }
 
 // A leaf's frame in double-float, formed once per leaf: e_theta, e_phi, the
@@ -1112,8 +1199,8 @@ __device__ __forceinline__ dflt group_sum_dfl(dflt v, int lpt)
 
 // The adjoint's near-field sums of one target (a forward source) over the
 // staged adjoint sources (forward targets, charges h and tangent dipoles g):
-// acc[0..3] as pair_sums_df for the charges (CHG: the stage has a non-zero
-// charge), acc[4] the mass skipped at coincident points, and for the dipoles,
+// acc[0..3] as pair_sums_df2 (per source) for the charges (CHG: the stage has a
+// non-zero charge), acc[4] the mass skipped at coincident points, and for the dipoles,
 // with G(x, y) = (1/4pi) log |x - y|^2 + const and d = x - y:
 //   acc[5] = sum (g . (y - x)) / d^2      (the potential, times 2 / 4pi)
 //   acc[6..8] = sum 2 (g . d) d / d^4 - g / d^2   (its gradient in x, likewise).
@@ -1297,8 +1384,11 @@ __global__ void __launch_bounds__(128) k_finish_df(EvalDfArgs A)
     }
 }
 
+// 5 CTAs of 4 warps per SM for the forward (96 registers; its packed loop
+// spills 72 bytes there and still runs faster than at 4), 4 for the adjoint (128
+// registers without spills; at 5 it spills and ran 13 % slower)
 template <bool PSI, bool ADJ>
-__global__ void __launch_bounds__(128) k_eval_df(EvalDfArgs A)
+__global__ void __launch_bounds__(128, ADJ ? 4 : 5) k_eval_df(EvalDfArgs A)
 {
     constexpr int ST = ADJ ? STAGE / 2 : STAGE;
     constexpr int NACC = ADJ ? 9 : 5;
@@ -1405,14 +1495,32 @@ __global__ void __launch_bounds__(128) k_eval_df(EvalDfArgs A)
                     two_sum(h.x, d[0], &sx, &ex_);
                     two_sum(h.y, d[1], &sy, &ey_);
                     two_sum(h.z, d[2], &sz, &ez_);
-                    yh[idx] = make_float4(sx, sy, sz, h.w);
-                    yl[idx] = make_float4(ex_ + (l.x + d[3]), ey_ + (l.y + d[4]), ez_ + (l.z + d[5]), l.w);
+                    const float lx = ex_ + (l.x + d[3]), ly = ey_ + (l.y + d[4]), lz = ez_ + (l.z + d[5]);
                     if (ADJ) {
+                        yh[idx] = make_float4(sx, sy, sz, h.w);
+                        yl[idx] = make_float4(lx, ly, lz, l.w);
                         s_gh[wid][idx] = A.doff[2 * j];
                         s_gl[wid][idx] = A.doff[2 * j + 1];
+                    } else {               // packed by pairs of sources (StageDF)
+                        const int P = idx >> 1, c = idx & 1;
+                        float* pa = reinterpret_cast<float*>(yh + P);
+                        float* pb = reinterpret_cast<float*>(yh + ST / 2 + P);
+                        float* pc = reinterpret_cast<float*>(yl + P);
+                        float* pd = reinterpret_cast<float*>(yl + ST / 2 + P);
+                        pa[c] = sx; pa[2 + c] = sy; pb[c] = sz; pb[2 + c] = h.w;
+                        pc[c] = lx; pc[2 + c] = ly; pd[c] = lz; pd[2 + c] = l.w;
                     }
                     same = same && h.w == q0h && l.w == q0l;
                     sq = sq + dflt(h.w, l.w);
+                }
+                if (!ADJ && (ns & 1) && lane == 0) {    // an odd count: a massless partner 4 away
+                    const int P = ns >> 1;
+                    float* pa = reinterpret_cast<float*>(yh + P);
+                    float* pb = reinterpret_cast<float*>(yh + ST / 2 + P);
+                    float* pc = reinterpret_cast<float*>(yl + P);
+                    float* pd = reinterpret_cast<float*>(yl + ST / 2 + P);
+                    pa[1] = 4.f; pa[3] = 0.f; pb[1] = 0.f; pb[3] = 0.f;
+                    pc[1] = 0.f; pc[3] = 0.f; pd[1] = 0.f; pd[3] = 0.f;
                 }
                 const bool eqm = __all_sync(FULL, same);
 #pragma unroll
@@ -1435,12 +1543,16 @@ __global__ void __launch_bounds__(128) k_eval_df(EvalDfArgs A)
                         pair_sums_adj_df<PSI, true, false>(yh, yl, gh, gl, ns, sa, lpa, tha, tla, qm, s_tab, acc_a);
                         if (nb) pair_sums_adj_df<PSI, true, false>(yh, yl, gh, gl, ns, sb, lpb, thb, tlb, qm, s_tab, acc_b);
                     }
-                } else if (eqm) {
-                    pair_sums_df<PSI, true>(yh, yl, ns, sa, lpa, tha, tla, qm, s_tab, acc_a);
-                    if (nb) pair_sums_df<PSI, true>(yh, yl, ns, sb, lpb, thb, tlb, qm, s_tab, acc_b);
                 } else {
-                    pair_sums_df<PSI, false>(yh, yl, ns, sa, lpa, tha, tla, qm, s_tab, acc_a);
-                    if (nb) pair_sums_df<PSI, false>(yh, yl, ns, sb, lpb, thb, tlb, qm, s_tab, acc_b);
+                    const StageDF SD{yh, yh + ST / 2, yl, yl + ST / 2};
+                    const int np = (ns + 1) >> 1, ptail = (ns & 1) ? ns >> 1 : -1;
+                    if (eqm) {
+                        pair_sums_df2<PSI, true>(SD, np, ptail, sa, lpa, tha, tla, qm, s_tab, acc_a);
+                        if (nb) pair_sums_df2<PSI, true>(SD, np, ptail, sb, lpb, thb, tlb, qm, s_tab, acc_b);
+                    } else {
+                        pair_sums_df2<PSI, false>(SD, np, ptail, sa, lpa, tha, tla, qm, s_tab, acc_a);
+                        if (nb) pair_sums_df2<PSI, false>(SD, np, ptail, sb, lpb, thb, tlb, qm, s_tab, acc_b);
+                    }
                 }
             }
             // the staged mass once per target less what it skipped: acc[4] = sum q
