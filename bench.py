@@ -56,9 +56,9 @@ EVAL_KERNEL = {"mixed": "k_eval32 (FP32 near field; its double-float L2P and com
                "fp32": "k_eval32 (near field and L2P in FP32)"}
 # DRAM bytes of one k_eval32 launch of the headline path (p = 20, m = 96, c_s = 1.5 at N = M = 1.6e7):
 # ncu at N = M = 2e6 (profiles/k_eval32_mixed_clustered_2e6.md), scaled by the near-field pairs
-K_EVAL32_TRAFFIC = (225.6e6 + 56.7e6) * (1.3399e10 / 1.1019e9)
+K_EVAL32_TRAFFIC = (225.2e6 + 55.6e6) * (1.3399e10 / 1.1019e9)
 K_EVAL32_TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one k_eval32 launch at N = M = 2e6 "
-                           "(225.6 + 56.7 MB, 1.10e9 pairs), scaled by the near-field pairs to this launch (x 12.16)")
+                           "(225.2 + 55.6 MB, 1.10e9 pairs), scaled by the near-field pairs to this launch (x 12.16)")
 
 
 def parse():
