@@ -92,6 +92,30 @@ def test_df_equal_masses_product_logarithm():
     assert (np.linalg.norm(alpha[idx] - ref["alpha"][idx], axis=1) <= 1e-10 * na.max()).all()
 
 
+def test_df_without_psi_odd_stages_and_both_mass_forms():
+    """The near field without psi (no logarithm, the PSI = false kernels) gives
+    the alpha of the solve with psi.  The sources sit in clumps of odd sizes, so
+    stages of odd counts (a massless partner in the packed loop's last pair) meet
+    both mass forms: equal masses (the product logarithm) and lognormal ones."""
+    rng = np.random.default_rng(19)
+    centres = unit(rng.normal(size=(37, 3)))
+    sizes = rng.integers(1, 40, size=37) * 2 + 1
+    src = unit(np.concatenate([c + 2e-3 * rng.normal(size=(k, 3)) for c, k in zip(centres, sizes)]))
+    tgt = unit(np.concatenate([src[::7] + 1e-4 * rng.normal(size=(len(src[::7]), 3)), rng.normal(size=(3001, 3))]))
+    for q in (np.full(len(src), 4 * np.pi / len(src)), rng.lognormal(0.0, 0.5, len(src))):
+        plan = sfmm.Plan(p=32, leaf_size=32, precision=sfmm.SFMM_MIXED_DF)
+        psi, alpha = plan.deflection(dev(src), dev(q), dev(tgt))
+        none, alpha2 = plan.deflection(dev(src), dev(q), dev(tgt), with_psi=False)
+        torch.cuda.synchronize()
+        assert none is None
+        a1, a2 = alpha.cpu().numpy(), alpha2.cpu().numpy()
+        # the far field reaches each box through FP64 atomic additions: equal to their rounding
+        assert rel(a2, a1) < 1e-13
+        ref = direct_sum(src, q, tgt)
+        check(psi.cpu().numpy(), a1, ref)
+        assert rel(a2, ref["alpha"]) < TOL_DF
+
+
 def test_df_log_and_reciprocal_over_the_exponent_range():
     """One source, targets from 1e-4 to pi away: every pair in the near field of
     the source's leaf runs the table-driven double-float logarithm and the
